@@ -1,0 +1,223 @@
+/*
+ * nvdb.h -- C ABI of libnvdb.so, a B300 (sm_103a) implementation of the
+ * NeuralVDB hot path (Kim, Lee & Museth, "NeuralVDB: High-resolution Sparse
+ * Volume Representation using Hierarchical Neural Networks").
+ *
+ * NeuralVDB keeps the root and level-2 nodes of a VDB [Hash,5,4,3] tree
+ * explicit and replaces the two lower levels by coordinate networks
+ * (Section 3.3.1): a level-1 mask classifier, a level-0 (voxel) mask
+ * classifier and a voxel value regressor, each a Fourier-feature encoding
+ * (Section 3.2.2, Eq. 2) followed by a ReLU MLP.  Misclassified candidates are
+ * stored as patches (Section 3.3.2), so decoding restores the topology
+ * exactly; values are lossy.
+ *
+ * Conventions for every call:
+ *  - Pointers named d_* are DEVICE pointers (CUDA global memory of the current
+ *    device); every other pointer is a HOST pointer.  The caller owns all
+ *    buffers it passes; the library owns the nvdb_grid / nvdb_model handles
+ *    (free them with nvdb_grid_free / nvdb_model_free) and the device memory
+ *    inside them.
+ *  - Work is enqueued on the given stream and ordered with it.  Calls that
+ *    return counts or device-detected errors synchronise that stream before
+ *    returning; the others (noted per call) return without synchronising.
+ *  - No C++ exception crosses this boundary.  A call returns NVDB_OK or an
+ *    error status; nvdb_last_error() gives a message for the calling thread.
+ *  - Voxel coordinates are int32 triples (i, j, k) in [0, 2^21).
+ *  - Mask bits: bit b of a node mask is bit (b & 63) of 64-bit word (b >> 6).
+ *    Slot / offset numbering follows the dense VDB node layout (Section 3.1):
+ *    level-2 slot = ((i>>7)&31)<<10 | ((j>>7)&31)<<5 | ((k>>7)&31),
+ *    leaf slot    = ((i>>3)&15)<<8  | ((j>>3)&15)<<4 | ((k>>3)&15),
+ *    voxel offset = (i&7)<<6 | (j&7)<<3 | (k&7).
+ *    Canonical voxel order is lexicographic on (level-2 origin, level-1 slot,
+ *    leaf slot, voxel offset).
+ */
+#ifndef NVDB_H
+#define NVDB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* nvdb_stream;   /* a cudaStream_t; NULL = legacy default stream */
+
+typedef enum {
+  NVDB_OK = 0,
+  NVDB_ERR_INVALID_ARG = 1,     /* NULL pointer, bad size, coordinate out of range, unknown option */
+  NVDB_ERR_DUPLICATE_VOXEL = 2, /* nvdb_build: the same (i,j,k) appears twice */
+  NVDB_ERR_OUT_OF_MEMORY = 3,   /* a device or host allocation failed */
+  NVDB_ERR_CAPACITY = 4,        /* caller's output buffer too small; counts hold the need */
+  NVDB_ERR_CUDA = 5,            /* a CUDA runtime call failed (message names it) */
+  NVDB_ERR_TIMEOUT = 6,         /* a device-side wait gave up (bounded spin) */
+  NVDB_ERR_UNSUPPORTED = 7,     /* valid but not implemented (width, precision, ...) */
+  NVDB_ERR_CORRUPT = 8          /* blob or decoded counts inconsistent with the model header */
+} nvdb_status;
+
+/* Arithmetic of the hidden layers when evaluating networks. */
+typedef enum {
+  NVDB_FP32 = 0,      /* plain FP32 on CUDA cores (FFMA), FP32 encoding */
+  NVDB_BF16 = 1,      /* BF16 operands on tcgen05 tensor cores, FP32 accumulate in TMEM */
+  NVDB_FP8_E4M3 = 2   /* FP8 E4M3 hidden layers on tcgen05 (reserved; returns UNSUPPORTED) */
+} nvdb_precision;
+
+/* Network indices (Section 3.3.1). */
+enum { NVDB_NET_L1_CLASSIFIER = 0, NVDB_NET_L0_CLASSIFIER = 1, NVDB_NET_REGRESSOR = 2 };
+/* Losses (Eq. 1 is MSE; BCE is used for the classifiers, Section 3.3.1). */
+enum { NVDB_LOSS_MSE = 0, NVDB_LOSS_L1 = 1, NVDB_LOSS_BCE = 2 };
+
+typedef struct nvdb_grid nvdb_grid;    /* explicit [Hash,5,4,3] tree, device resident */
+typedef struct nvdb_model nvdb_model;  /* [Hash,5,NN(4),NN(3)]: upper tree + 3 networks + patches */
+
+typedef struct {
+  int32_t grid_class;   /* 0 = narrow-band level set (SDF), 1 = fog (density) */
+  float half_width;     /* level sets: band half-width w in voxels (values lie in (-w, w)); fog: ignored */
+} nvdb_build_opts;
+
+typedef struct {
+  uint64_t seed;        /* seeds the initial weights, the Fourier matrix and the sample stream */
+  int32_t width[3];     /* hidden width per network (supported: 32, 64) */
+  int32_t layers[3];    /* hidden layers per network (1..8) */
+  int32_t ffm_size[2];  /* encoding size n of level 1 and level 0 (supported: 32, 64); 0 = max width */
+  float ffm_sigma;      /* std of the Fourier matrix B, in cycles over the domain extent E */
+  int32_t steps;        /* Adam steps per network */
+  int32_t batch;        /* samples per step (uniform with replacement, Section 3.2.1) */
+  float lr;             /* learning rate */
+  float lr_decay;       /* gamma: lr_t = lr * gamma^floor((t-1)/lr_interval) */
+  int32_t lr_interval;  /* 0 = constant learning rate */
+  int32_t loss;         /* regressor loss: NVDB_LOSS_MSE or NVDB_LOSS_L1 */
+  int32_t train_prec;   /* arithmetic of training: NVDB_FP32 */
+  uint32_t patch_precs; /* bit p set = store patches for decoding at precision p (default: FP32|BF16) */
+} nvdb_train_opts;
+
+typedef struct {
+  int32_t grid_class;
+  float background, half_width;
+  int32_t origin[3];     /* encoding domain origin (multiple of 128) */
+  int32_t log2_extent;   /* encoding domain extent E = 2^log2_extent voxels */
+  int64_t n_active, n_leaf, n_l1, n_l2;
+} nvdb_info;
+
+/* ------------------------------------------------------------------------ */
+
+/* Build the explicit VDB [Hash,5,4,3] tree (Section 3.1, Fig. 1) from n sparse
+ * voxels: d_ijk int32 [n][3], d_val float [n], any order.  The grid copies the
+ * voxels in canonical order plus leaf/level-1/level-2 origins and masks.
+ * Errors: INVALID_ARG (n < 0, NULL, coordinate outside [0,2^21)),
+ * DUPLICATE_VOXEL.  Synchronises the stream (node counts size the tree). */
+nvdb_status nvdb_build(const int32_t* d_ijk, const float* d_val, int64_t n,
+                       const nvdb_build_opts* opts, nvdb_stream stream, nvdb_grid** out);
+
+nvdb_status nvdb_grid_info(const nvdb_grid* grid, nvdb_info* out);
+
+/* Copy the grid's canonical arrays to HOST buffers (any pointer may be NULL):
+ * ijk [n][3], val [n], leaf_origin [n_leaf][3], leaf_mask [n_leaf][8],
+ * l1_origin [n_l1][3], l1_mask [n_l1][64].  Synchronises the stream. */
+nvdb_status nvdb_grid_read(const nvdb_grid* grid, int32_t* ijk, float* val, int32_t* leaf_origin,
+                           uint64_t* leaf_mask, int32_t* l1_origin, uint64_t* l1_mask,
+                           nvdb_stream stream);
+
+nvdb_status nvdb_grid_free(nvdb_grid* grid);
+
+/* Fill opts with the defaults: widths 32, 3 layers, ffm_size 0, sigma 1.25,
+ * 200 steps, batch 4096, lr 1e-3, decay 0.975 every 100 steps, MSE, FP32
+ * training, patches for FP32 and BF16, seed 1. */
+void nvdb_train_opts_default(nvdb_train_opts* opts);
+
+/* Encode a grid (Sections 3.2-3.3): initialise the three networks (Xavier
+ * weights and the Fourier matrix B ~ N(0, sigma^2), drawn from SplitMix64
+ * streams of opts->seed) or copy them from `warm` (temporally coherent warm
+ * start, Section 3.6; warm may be NULL), train each for opts->steps Adam steps
+ * on uniformly sampled candidates (Philox4x32-10 sample stream; regressor on
+ * active voxels only, Section 3.2.1), then classify every candidate at each
+ * precision of opts->patch_precs and store the mismatches as patches
+ * (Section 3.3.2).  Synchronises the stream. */
+nvdb_status nvdb_compress(const nvdb_grid* grid, const nvdb_train_opts* opts, const nvdb_model* warm,
+                          nvdb_stream stream, nvdb_model** out);
+
+/* Per-step mean training loss of network `net` of the last compress
+ * (HOST buffer of cap floats); *count receives the number of steps. */
+nvdb_status nvdb_model_losses(const nvdb_model* model, int net, float* losses, int64_t cap,
+                              int64_t* count);
+
+/* Decode models back to voxels (Section 3.5, offline sequential access; Fig. 5):
+ * level-1 node origins from the level-2 child masks, level-1 classification +
+ * patches -> child leaves, level-0 classification + patches -> active voxels,
+ * regression of the active voxels -> values (x half_width for level sets).
+ * Outputs are concatenated per model in canonical order: d_ijk int32 [cap][3],
+ * d_val float [cap]; counts (HOST, n_models entries) receives each model's
+ * active count.  If d_ijk is NULL only counts are filled (from the headers).
+ * Errors: CAPACITY (sum of counts > capacity; nothing written), UNSUPPORTED
+ * (no patch set for prec), CORRUPT (decoded counts differ from the header).
+ * Synchronises the stream. */
+nvdb_status nvdb_decompress(const nvdb_model* const* models, int n_models, nvdb_precision prec,
+                            int32_t* d_ijk, float* d_val, int64_t capacity, int64_t* counts,
+                            nvdb_stream stream);
+
+/* Random access on [Hash,5,4,NN(3)] (Section 3.5, online random access): for
+ * each point p (float32 [n][3], index space) the 8 corners of the cell
+ * floor(p) are looked up in the explicit topology (decoded once and cached in
+ * the model); active corners are regressed, inactive corners take the
+ * background (+half_width for level sets, 0 for fog); the result is the
+ * trilinear blend with weights (w_x w_y) w_z, corners summed in the order
+ * c = 4a + 2b + d for offset (a, b, d).  d_out float [n]; d_active (may be
+ * NULL) uint8 [n] receives the active-corner bitmask (bit c).
+ * Does not synchronise unless the topology cache is built by this call. */
+nvdb_status nvdb_query(const nvdb_model* model, const float* d_xyz, int64_t n, nvdb_precision prec,
+                       float* d_out, uint8_t* d_active, nvdb_stream stream);
+
+/* Raw output (logit or unscaled value) of network `net` at n voxel
+ * coordinates d_ijk int32 [n][3]; the level-1 classifier takes leaf origins
+ * (its input is ijk >> 3).  d_out float [n].  Does not synchronise. */
+nvdb_status nvdb_mlp_eval(const nvdb_model* model, int net, nvdb_precision prec, const int32_t* d_ijk,
+                          int64_t n, float* d_out, nvdb_stream stream);
+
+/* Gradient of the mean loss over n samples (d_ijk int32 [n][3], d_target
+ * float [n]) w.r.t. the parameters of network `net`, FP32 (Section 3.2).
+ * d_grad float [nvdb_net_param_count] in storage order (W_0, b_0, ...,
+ * W_{L-1}, b_{L-1}, w_h, b_h; W row-major [out][in]); *loss (HOST) the mean
+ * loss.  loss_kind: NVDB_LOSS_*.  Synchronises the stream. */
+nvdb_status nvdb_mlp_grad(const nvdb_model* model, int net, const int32_t* d_ijk, const float* d_target,
+                          int64_t n, int loss_kind, float* d_grad, float* loss, nvdb_stream stream);
+
+int64_t nvdb_net_param_count(const nvdb_model* model, int net);
+
+nvdb_status nvdb_model_info(const nvdb_model* model, nvdb_info* out);
+
+/* Serialise a model to a HOST buffer (format "NVDBMDL1", described below).
+ * With buf == NULL, *bytes receives the size.  Synchronises the device. */
+nvdb_status nvdb_model_export(const nvdb_model* model, void* buf, size_t* bytes);
+
+/* Create a model from a HOST blob.  Errors: CORRUPT, UNSUPPORTED.
+ * Synchronises the stream. */
+nvdb_status nvdb_model_import(const void* buf, size_t bytes, nvdb_stream stream, nvdb_model** out);
+
+nvdb_status nvdb_model_free(nvdb_model* model);
+
+/* Message of the last error of the calling thread ("" if none). */
+const char* nvdb_last_error(void);
+
+/*
+ * Model blob "NVDBMDL1" (little-endian; every array starts at an 8-byte
+ * aligned offset from the blob start; padding bytes are zero):
+ *   header, 128 bytes:
+ *     0 char[8] magic | 8 u32 version=1 | 12 u32 grid_class | 16 f32 background
+ *     20 f32 half_width | 24 i32[3] origin | 36 i32 log2_extent
+ *     40 i32[2] ffm_size (level 1, level 0) | 48 i32[3] width | 60 i32[3] layers
+ *     72 i32 n_patch_sets | 76 i32 0 | 80 i64 n_l2 | 88 i64 n_l1 | 96 i64 n_leaf
+ *     104 i64 n_active | 112 u64[2] 0
+ *   u32 q1[m1][3], u32 q0[m0][3]   (m = ffm_size/2; fixed-point Fourier matrix,
+ *        phase of frequency f at level coordinates c: sum_d q[f][d] c_d mod 2^32)
+ *   per network: f32 W_0[w][n], b_0[w], W_1[w][w], b_1[w], ..., w_h[w], b_h
+ *   i32 l2_origin[n_l2][3], u64 l2_mask[n_l2][512]
+ *   per patch set: i32 precision, i32 0, u32 l1_off[n_l1+1], u16 l1_idx[..],
+ *                  u32 l0_off[n_leaf+1], u16 l0_idx[..]
+ * Network 0 (level-1 classifier) sees leaf-index coordinates (ijk - origin) >> 3
+ * with q1; networks 1 and 2 see voxel coordinates ijk - origin with q0.
+ */
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NVDB_H */

@@ -1,0 +1,201 @@
+"""NeuralVDB hot path on B300 -- Python binding of libnvdb.so (include/nvdb.h).
+
+Every function marshals torch CUDA tensors (device pointers) and the current
+torch stream into the C ABI; all computation runs in the library's CUDA
+kernels.  There is no CPU fallback: the binding raises if libnvdb.so is not
+built.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import torch
+
+from . import _native as N
+from ._native import (BF16, FP32, FP8_E4M3, LOSS_BCE, LOSS_L1, LOSS_MSE, NET_L0_CLASSIFIER,  # noqa: F401
+                      NET_L1_CLASSIFIER, NET_REGRESSOR)
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    global _lib
+    if _lib is None:
+        _lib = N.load()
+    return _lib
+
+
+class NvdbError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"nvdb status {status}: {msg}")
+        self.status = status
+
+
+def _check(st: int):
+    if st != N.OK:
+        raise NvdbError(st, lib().nvdb_last_error().decode())
+
+
+def _stream(stream=None) -> C.c_void_p:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _dptr(t: torch.Tensor, dtype, name: str) -> C.c_void_p:
+    if not t.is_cuda or t.dtype != dtype or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous CUDA tensor of {dtype}")
+    return C.c_void_p(t.data_ptr())
+
+
+def _info(fn, h) -> dict:
+    i = N.Info()
+    _check(fn(h, C.byref(i)))
+    return dict(grid_class=i.grid_class, background=i.background, half_width=i.half_width,
+                origin=list(i.origin), log2_extent=i.log2_extent, n_active=i.n_active, n_leaf=i.n_leaf,
+                n_l1=i.n_l1, n_l2=i.n_l2)
+
+
+class Grid:
+    """Explicit VDB [Hash,5,4,3] tree on the device (nvdb_grid)."""
+
+    def __init__(self, handle: C.c_void_p):
+        self._h = handle
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self) -> dict:
+        return _info(lib().nvdb_grid_info, self._h)
+
+    def read(self) -> dict:
+        """Canonical arrays as host numpy arrays."""
+        import numpy as np
+        i = self.info()
+        a = dict(ijk=np.empty((i["n_active"], 3), np.int32), val=np.empty(i["n_active"], np.float32),
+                 leaf_origin=np.empty((i["n_leaf"], 3), np.int32), leaf_mask=np.empty((i["n_leaf"], 8), np.uint64),
+                 l1_origin=np.empty((i["n_l1"], 3), np.int32), l1_mask=np.empty((i["n_l1"], 64), np.uint64))
+        p = [a[k].ctypes.data_as(C.c_void_p) for k in ("ijk", "val", "leaf_origin", "leaf_mask", "l1_origin", "l1_mask")]
+        _check(lib().nvdb_grid_read(self._h, *p, _stream()))
+        return a
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.nvdb_grid_free(self._h)
+            self._h = None
+
+
+class Model:
+    """NeuralVDB [Hash,5,NN(4),NN(3)] model (nvdb_model)."""
+
+    def __init__(self, handle: C.c_void_p):
+        self._h = handle
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self) -> dict:
+        return _info(lib().nvdb_model_info, self._h)
+
+    def losses(self, net: int):
+        import numpy as np
+        n = C.c_int64()
+        _check(lib().nvdb_model_losses(self._h, net, None, 0, C.byref(n)))
+        out = np.empty(n.value, np.float32)
+        _check(lib().nvdb_model_losses(self._h, net, out.ctypes.data_as(C.POINTER(C.c_float)), n.value, None))
+        return out
+
+    def param_count(self, net: int) -> int:
+        return int(lib().nvdb_net_param_count(self._h, net))
+
+    def export(self) -> bytes:
+        n = C.c_size_t()
+        _check(lib().nvdb_model_export(self._h, None, C.byref(n)))
+        buf = C.create_string_buffer(n.value)
+        _check(lib().nvdb_model_export(self._h, buf, C.byref(n)))
+        return buf.raw[: n.value]
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.nvdb_model_free(self._h)
+            self._h = None
+
+
+def build(ijk: torch.Tensor, val: torch.Tensor, grid_class: int = 0, half_width: float = 3.0, stream=None) -> Grid:
+    n = ijk.shape[0]
+    o = N.BuildOpts(grid_class, half_width)
+    h = C.c_void_p()
+    _check(lib().nvdb_build(_dptr(ijk, torch.int32, "ijk"), _dptr(val, torch.float32, "val"), n, C.byref(o),
+                            _stream(stream), C.byref(h)))
+    return Grid(h)
+
+
+def train_opts(**kw) -> N.TrainOpts:
+    o = N.TrainOpts()
+    lib().nvdb_train_opts_default(C.byref(o))
+    for k, v in kw.items():
+        if k in ("width", "layers", "ffm_size"):
+            arr = getattr(o, k)
+            for i, x in enumerate(v):
+                arr[i] = int(x)
+        else:
+            setattr(o, k, v)
+    return o
+
+
+def compress(grid: Grid, opts=None, warm: "Model | None" = None, stream=None, **kw) -> Model:
+    o = opts if opts is not None else train_opts(**kw)
+    h = C.c_void_p()
+    _check(lib().nvdb_compress(grid.handle, C.byref(o), warm.handle if warm else None, _stream(stream), C.byref(h)))
+    return Model(h)
+
+
+def decompress(models, prec: int = FP32, out=None, stream=None):
+    """Decode models -> (ijk int32 [n,3], val float32 [n], counts list).  `out` = (ijk, val) to reuse buffers."""
+    if isinstance(models, Model):
+        models = [models]
+    arr = (C.c_void_p * len(models))(*[m.handle for m in models])
+    counts = (C.c_int64 * len(models))()
+    _check(lib().nvdb_decompress(arr, len(models), prec, None, None, 0, counts, _stream(stream)))
+    total = sum(counts)
+    if out is None:
+        ijk = torch.empty((total, 3), dtype=torch.int32, device="cuda")
+        val = torch.empty(total, dtype=torch.float32, device="cuda")
+    else:
+        ijk, val = out
+    _check(lib().nvdb_decompress(arr, len(models), prec, _dptr(ijk, torch.int32, "ijk"),
+                                 _dptr(val, torch.float32, "val"), ijk.shape[0], counts, _stream(stream)))
+    return ijk[:total], val[:total], list(counts)
+
+
+def query(model: Model, xyz: torch.Tensor, prec: int = FP32, active: bool = False, out=None, stream=None):
+    n = xyz.shape[0]
+    res = out if out is not None else torch.empty(n, dtype=torch.float32, device="cuda")
+    act = torch.empty(n, dtype=torch.uint8, device="cuda") if active else None
+    _check(lib().nvdb_query(model.handle, _dptr(xyz, torch.float32, "xyz"), n, prec, _dptr(res, torch.float32, "out"),
+                            _dptr(act, torch.uint8, "active") if act is not None else None, _stream(stream)))
+    return (res, act) if active else res
+
+
+def mlp_eval(model: Model, net: int, ijk: torch.Tensor, prec: int = FP32, stream=None) -> torch.Tensor:
+    n = ijk.shape[0]
+    out = torch.empty(n, dtype=torch.float32, device="cuda")
+    _check(lib().nvdb_mlp_eval(model.handle, net, prec, _dptr(ijk, torch.int32, "ijk"), n,
+                               _dptr(out, torch.float32, "out"), _stream(stream)))
+    return out
+
+
+def mlp_grad(model: Model, net: int, ijk: torch.Tensor, target: torch.Tensor, loss: int, stream=None):
+    g = torch.empty(model.param_count(net), dtype=torch.float32, device="cuda")
+    lv = C.c_float()
+    _check(lib().nvdb_mlp_grad(model.handle, net, _dptr(ijk, torch.int32, "ijk"), _dptr(target, torch.float32, "target"),
+                               ijk.shape[0], loss, _dptr(g, torch.float32, "grad"), C.byref(lv), _stream(stream)))
+    return g, lv.value
+
+
+def model_import(blob: bytes, stream=None) -> Model:
+    h = C.c_void_p()
+    buf = C.create_string_buffer(blob, len(blob))
+    _check(lib().nvdb_model_import(buf, len(blob), _stream(stream), C.byref(h)))
+    return Model(h)

@@ -1,0 +1,234 @@
+// Stream compaction of classifier bitmasks into canonical lists (Section 3.5:
+// child masks -> leaf list, active masks -> voxel list) and the patch
+// correction of Section 3.3.2.  Deterministic: a three-phase exclusive scan
+// (block scans, one scan of the block sums, add-back) and warp-level popcount
+// prefixes; the output order is the canonical bit order.
+#pragma once
+#include "common.cuh"
+
+namespace nvdb {
+
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 4;
+constexpr int kScanBlock = kScanThreads * kScanItems;   // elements per scan block
+
+__device__ __forceinline__ int64_t warp_excl_scan(int64_t v, int lane, int64_t& total) {
+  int64_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  total = __shfl_sync(0xffffffffu, x, 31);
+  return x - v;
+}
+
+// Exclusive scan over the threads of a block (blockDim multiple of 32, <= 1024).
+__device__ __forceinline__ int64_t block_excl_scan(int64_t v, int64_t* sh /* >= 33 */, int64_t& total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  int64_t wt;
+  const int64_t ex = warp_excl_scan(v, lane, wt);
+  if (lane == 31) sh[warp] = wt;
+  __syncthreads();
+  if (warp == 0) {
+    const int64_t s = lane < nw ? sh[lane] : 0;
+    int64_t t;
+    const int64_t e = warp_excl_scan(s, lane, t);
+    if (lane < nw) sh[lane] = e;
+    if (lane == 0) sh[32] = t;
+  }
+  __syncthreads();
+  const int64_t r = ex + sh[warp];
+  total = sh[32];
+  __syncthreads();
+  return r;
+}
+
+// Phase 1: per-block exclusive scans of u32 counts; block totals to `sums`.
+__global__ void scan_blocks_kernel(const uint32_t* in, int64_t n, int64_t* out, int64_t* sums) {
+  __shared__ int64_t sh[33];
+  const int64_t base = (int64_t)blockIdx.x * kScanBlock + (int64_t)threadIdx.x * kScanItems;
+  uint32_t v[kScanItems];
+  int64_t local = 0;
+#pragma unroll
+  for (int i = 0; i < kScanItems; ++i) {
+    v[i] = base + i < n ? in[base + i] : 0u;
+    local += v[i];
+  }
+  int64_t tot;
+  int64_t run = block_excl_scan(local, sh, tot);
+#pragma unroll
+  for (int i = 0; i < kScanItems; ++i) {
+    if (base + i < n) out[base + i] = run;
+    run += v[i];
+  }
+  if (threadIdx.x == 0) sums[blockIdx.x] = tot;
+}
+
+// Phase 2: exclusive scan of the block totals by one block; grand total to out_total.
+__global__ void scan_sums_kernel(int64_t* sums, int64_t nb, int64_t* out_total) {
+  __shared__ int64_t sh[33];
+  int64_t carry = 0;
+  for (int64_t b0 = 0; b0 < nb; b0 += blockDim.x) {
+    const int64_t i = b0 + threadIdx.x;
+    const int64_t v = i < nb ? sums[i] : 0;
+    int64_t tot;
+    const int64_t e = block_excl_scan(v, sh, tot);
+    if (i < nb) sums[i] = e + carry;
+    carry += tot;
+  }
+  if (threadIdx.x == 0) *out_total = carry;
+}
+
+// Phase 3: add the block offsets.
+__global__ void scan_add_kernel(int64_t* out, int64_t n, const int64_t* sums) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] += sums[i / kScanBlock];
+}
+
+// Apply the patch list of every item (XOR, Section 3.3.2) to its candidate
+// words and count the resulting set bits.  One thread per item.
+__global__ void patch_count_kernel(uint32_t* words, int wpi, int64_t n_items, const uint32_t* poff,
+                                   const uint16_t* pidx, uint32_t* counts) {
+  const int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (it >= n_items) return;
+  uint32_t* w = words + it * wpi;
+  if (poff) {
+    for (uint32_t p = poff[it]; p < poff[it + 1]; ++p) {
+      const uint32_t b = pidx[p];
+      w[b >> 5] ^= 1u << (b & 31);
+    }
+  }
+  uint32_t c = 0;
+  for (int i = 0; i < wpi; ++i) c += __popc(w[i]);
+  counts[it] = c;
+}
+
+// Level-1 child words -> leaf origins in canonical order.  One warp per node,
+// lane l owns words 4l..4l+3 (bits in slot order).
+__global__ void emit_leaves_kernel(const uint32_t* words, const int4* l1_origin, int64_t n_l1,
+                                   const int64_t* off, int4* leaf_origin, int64_t cap, uint32_t* status) {
+  const int64_t node = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (node >= n_l1) return;
+  const uint4 w = reinterpret_cast<const uint4*>(words + node * 128)[lane];
+  const uint32_t ww[4] = {w.x, w.y, w.z, w.w};
+  const int64_t cnt = __popc(w.x) + __popc(w.y) + __popc(w.z) + __popc(w.w);
+  int64_t tot;
+  int64_t pos = off[node] + warp_excl_scan(cnt, lane, tot);
+  const int4 o = l1_origin[node];
+  bool over = false;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    uint32_t b = ww[q];
+    while (b) {
+      const int bit = __ffs(b) - 1;
+      b &= b - 1;
+      const int s = (lane * 4 + q) * 32 + bit;
+      if (pos < cap)
+        leaf_origin[pos] = make_int4(o.x + 8 * (s >> 8), o.y + 8 * ((s >> 4) & 15), o.z + 8 * (s & 15), 0);
+      else
+        over = true;
+      ++pos;
+    }
+  }
+  if (over) set_status(status, ST_CORRUPT);
+}
+
+// Leaf active words -> voxel coordinates in canonical order.  One warp per
+// leaf, lanes 0..15 own one word each.
+__global__ void emit_voxels_kernel(const uint32_t* words, const int4* leaf_origin, int64_t n_leaf,
+                                   const int64_t* off, int32_t* ijk, int64_t cap, uint32_t* status) {
+  const int64_t leaf = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (leaf >= n_leaf) return;
+  uint32_t b = lane < 16 ? words[leaf * 16 + lane] : 0u;
+  int64_t tot;
+  int64_t pos = off[leaf] + warp_excl_scan(__popc(b), lane, tot);
+  const int4 o = leaf_origin[leaf];
+  bool over = false;
+  while (b) {
+    const int bit = __ffs(b) - 1;
+    b &= b - 1;
+    const int v = lane * 32 + bit;
+    if (pos < cap) {
+      ijk[3 * pos] = o.x + (v >> 6);
+      ijk[3 * pos + 1] = o.y + ((v >> 3) & 7);
+      ijk[3 * pos + 2] = o.z + (v & 7);
+    } else {
+      over = true;
+    }
+    ++pos;
+  }
+  if (over) set_status(status, ST_CAPACITY);
+}
+
+// Level-1 node origins from the level-2 child masks (Section 3.5: the
+// coordinates of level-1 nodes follow from the level-2 child masks).
+// counts pass: one block (512 threads) per level-2 node.
+__global__ void l2_count_kernel(const uint64_t* l2_mask, int64_t n_l2, uint32_t* counts) {
+  __shared__ int64_t sh[33];
+  const int64_t n = blockIdx.x;
+  const int64_t c = __popcll(l2_mask[n * 512 + threadIdx.x]);
+  int64_t tot;
+  block_excl_scan(c, sh, tot);
+  if (threadIdx.x == 0) counts[n] = (uint32_t)tot;
+}
+
+__global__ void l2_emit_kernel(const uint64_t* l2_mask, const int4* l2_origin, int64_t n_l2, const int64_t* off,
+                               int4* l1_origin, int64_t cap, uint32_t* status) {
+  __shared__ int64_t sh[33];
+  const int64_t n = blockIdx.x;
+  uint64_t w = l2_mask[n * 512 + threadIdx.x];
+  int64_t tot;
+  int64_t pos = off[n] + block_excl_scan(__popcll(w), sh, tot);
+  const int4 o = l2_origin[n];
+  bool over = false;
+  while (w) {
+    const int bit = __ffsll((long long)w) - 1;
+    w &= w - 1;
+    const int s = threadIdx.x * 64 + bit;
+    if (pos < cap)
+      l1_origin[pos] = make_int4(o.x + 128 * (s >> 10), o.y + 128 * ((s >> 5) & 31), o.z + 128 * (s & 31), 0);
+    else
+      over = true;
+    ++pos;
+  }
+  if (over) set_status(status, ST_CORRUPT);
+}
+
+__global__ void check_total_kernel(const int64_t* total, int64_t expect, uint32_t* status) {
+  if (*total != expect) set_status(status, ST_CORRUPT);
+}
+
+// XOR of two word arrays (prediction vs truth) -> mismatch words, counted per item.
+__global__ void mismatch_count_kernel(uint32_t* pred, const uint32_t* truth, int wpi, int64_t n_items,
+                                      uint32_t* counts) {
+  const int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (it >= n_items) return;
+  uint32_t c = 0;
+  for (int i = 0; i < wpi; ++i) {
+    const uint32_t m = pred[it * wpi + i] ^ truth[it * wpi + i];
+    pred[it * wpi + i] = m;
+    c += __popc(m);
+  }
+  counts[it] = c;
+}
+
+// Mismatch words -> patch indices (uint16 local candidate index), CSR order.
+__global__ void emit_patches_kernel(const uint32_t* mis, int wpi, int64_t n_items, const int64_t* off,
+                                    uint16_t* idx) {
+  const int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (it >= n_items) return;
+  int64_t pos = off[it];
+  for (int i = 0; i < wpi; ++i) {
+    uint32_t b = mis[it * wpi + i];
+    while (b) {
+      const int bit = __ffs(b) - 1;
+      b &= b - 1;
+      idx[pos++] = (uint16_t)(i * 32 + bit);
+    }
+  }
+}
+
+}  // namespace nvdb

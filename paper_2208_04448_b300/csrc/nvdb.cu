@@ -1,0 +1,1185 @@
+// libnvdb: C ABI of the NeuralVDB hot path on B300 (sm_103a).  Host-side
+// orchestration of the kernels in build.cuh (tree build), mlp.cuh (fused
+// encode + MLP, FP32 and BF16 tcgen05), compact.cuh (threshold / patch /
+// compaction), train.cuh (backward + Adam) and query.cuh (random access).
+#include "nvdb.h"
+
+#include <cub/cub.cuh>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "build.cuh"
+#include "common.cuh"
+#include "compact.cuh"
+#include "mlp.cuh"
+#include "query.cuh"
+#include "train.cuh"
+
+using namespace nvdb;
+
+// ============================================================================ errors
+namespace {
+thread_local std::string g_err;
+
+nvdb_status fail(nvdb_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return s;
+}
+
+#define CU(call)                                                                                   \
+  do {                                                                                             \
+    cudaError_t e_ = (call);                                                                       \
+    if (e_ != cudaSuccess) {                                                                       \
+      if (e_ == cudaErrorMemoryAllocation) return fail(NVDB_ERR_OUT_OF_MEMORY, "%s: out of memory", #call); \
+      return fail(NVDB_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_));                         \
+    }                                                                                              \
+  } while (0)
+
+#define TRY(expr)                         \
+  do {                                    \
+    nvdb_status s_ = (expr);              \
+    if (s_ != NVDB_OK) return s_;         \
+  } while (0)
+
+template <class T>
+nvdb_status dalloc(T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) return NVDB_OK;
+  CU(cudaMalloc((void**)p, count * sizeof(T)));
+  return NVDB_OK;
+}
+
+template <class T>
+void dfree(T*& p) {
+  if (p) cudaFree((void*)p);
+  p = nullptr;
+}
+
+int num_sms() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 1;
+  }
+  return n;
+}
+
+inline unsigned blocks_for(int64_t n, int per) { return (unsigned)((n + per - 1) / per); }
+
+// ============================================================================ scan helper
+struct Scan {
+  int64_t* sums = nullptr;
+  int64_t cap = 0;
+  int64_t* total = nullptr;   // one device int64
+  ~Scan() { dfree(sums); dfree(total); }
+  nvdb_status reserve(int64_t n) {
+    const int64_t nb = (n + kScanBlock - 1) / kScanBlock + 1;
+    if (!total) TRY(dalloc(&total, 1));
+    if (nb <= cap) return NVDB_OK;
+    dfree(sums);
+    TRY(dalloc(&sums, (size_t)nb));
+    cap = nb;
+    return NVDB_OK;
+  }
+  // out[i] = sum_{j<i} in[j]; *total = sum of all.
+  nvdb_status run(const uint32_t* in, int64_t n, int64_t* out, cudaStream_t s) {
+    TRY(reserve(n));
+    if (n == 0) {
+      CU(cudaMemsetAsync(total, 0, sizeof(int64_t), s));
+      return NVDB_OK;
+    }
+    const int64_t nb = (n + kScanBlock - 1) / kScanBlock;
+    scan_blocks_kernel<<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, out, sums);
+    scan_sums_kernel<<<1, 1024, 0, s>>>(sums, nb, total);
+    scan_add_kernel<<<blocks_for(n, 256), 256, 0, s>>>(out, n, sums);
+    CU(cudaGetLastError());
+    return NVDB_OK;
+  }
+};
+
+__global__ void offsets_to_u32_kernel(const int64_t* off, const int64_t* total, int64_t n, uint32_t* out) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) out[t] = (uint32_t)off[t];
+  if (t == n) out[n] = (uint32_t)*total;
+}
+
+// ============================================================================ host init (SplitMix64)
+constexpr uint64_t kGolden = 0x9E3779B97F4A7C15ull;
+constexpr uint64_t kNetStream = 0x632BE59BD9B4E019ull;
+constexpr uint64_t kFfmStream = 0x8CB92BA72F3D8DD7ull;
+
+uint64_t mix64(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+// Draw i of the SplitMix64 stream started at state s (Steele, Lea & Flood 2014).
+double uniform01(uint64_t s, uint64_t i) { return (double)(mix64(s + (i + 1) * kGolden) >> 11) * (1.0 / 9007199254740992.0); }
+
+// Xavier-uniform weights, zero biases; draw order W_0 (row-major), ..., W_{L-1}, w_h.
+std::vector<float> xavier_params(uint64_t seed, int net, int nin, int w, int L) {
+  const uint64_t s = seed + kNetStream * (uint64_t)(net + 1);
+  std::vector<float> p((size_t)net_param_count(nin, w, L), 0.f);
+  uint64_t i = 0;
+  size_t o = 0;
+  for (int l = 0; l < L; ++l) {
+    const int fan = l == 0 ? nin : w;
+    const double a = std::sqrt(6.0 / (double)(fan + w));
+    for (int r = 0; r < w; ++r)
+      for (int c = 0; c < fan; ++c) p[o++] = (float)((2.0 * uniform01(s, i++) - 1.0) * a);
+    o += w;   // bias = 0
+  }
+  const double a = std::sqrt(6.0 / (double)(w + 1));
+  for (int c = 0; c < w; ++c) p[o++] = (float)((2.0 * uniform01(s, i++) - 1.0) * a);
+  return p;   // b_h = 0
+}
+
+// Fixed-point Fourier matrix q = rint(2^32 B / E) mod 2^32, B = sigma * N(0,1) (Box-Muller).
+std::vector<uint32_t> ffm_increments(uint64_t seed, int level, int m, double sigma, double extent) {
+  const uint64_t s = seed + kFfmStream * (uint64_t)(level + 1);
+  std::vector<uint32_t> q((size_t)m * 3);
+  for (int f = 0; f < m; ++f)
+    for (int d = 0; d < 3; ++d) {
+      const uint64_t i = (uint64_t)(3 * f + d);
+      const double u1 = uniform01(s, 2 * i), u2 = uniform01(s, 2 * i + 1);
+      const double z = std::sqrt(-2.0 * std::log(1.0 - u1)) * std::cos(2.0 * M_PI * u2);
+      const double t = std::ldexp(sigma * z, 32) / extent;
+      q[(size_t)3 * f + d] = (uint32_t)(int64_t)std::rint(t);
+    }
+  return q;
+}
+}  // namespace
+
+// ============================================================================ handles
+struct nvdb_grid {
+  int grid_class = 0;
+  float half_width = 0.f, background = 0.f;
+  int64_t n = 0, n_leaf = 0, n_l1 = 0, n_l2 = 0;
+  int32_t origin[3] = {0, 0, 0};
+  int log2e = 7;
+  int32_t* ijk = nullptr;
+  float* val = nullptr;
+  int4* leaf_origin = nullptr;
+  int64_t* leaf_first = nullptr;
+  unsigned long long* leaf_mask = nullptr;
+  int4* l1_origin = nullptr;
+  unsigned long long* l1_mask = nullptr;
+  int4* l2_origin = nullptr;
+  unsigned long long* l2_mask = nullptr;
+  ~nvdb_grid() {
+    dfree(ijk); dfree(val); dfree(leaf_origin); dfree(leaf_first); dfree(leaf_mask);
+    dfree(l1_origin); dfree(l1_mask); dfree(l2_origin); dfree(l2_mask);
+  }
+};
+
+namespace {
+struct DevNet {
+  int n_in = 0, width = 0, layers = 0;
+  int64_t P = 0;
+  float* p32 = nullptr;
+  __nv_bfloat16* wpk = nullptr;
+  float* m = nullptr;
+  float* v = nullptr;
+  ~DevNet() { dfree(p32); dfree(wpk); dfree(m); dfree(v); }
+};
+
+struct PatchSet {
+  int prec = 0;
+  std::vector<uint32_t> l1_off, l0_off;
+  std::vector<uint16_t> l1_idx, l0_idx;
+  uint32_t* d_l1_off = nullptr;
+  uint32_t* d_l0_off = nullptr;
+  uint16_t* d_l1_idx = nullptr;
+  uint16_t* d_l0_idx = nullptr;
+  void release() { dfree(d_l1_off); dfree(d_l0_off); dfree(d_l1_idx); dfree(d_l0_idx); }
+};
+
+// Device scratch of the top-down decode of one model.
+struct DecodeScratch {
+  int64_t n_l1 = -1, n_leaf = -1;
+  uint32_t* l2_counts = nullptr;
+  int64_t* l2_off = nullptr;
+  int4* l1_origin = nullptr;
+  uint32_t* l1_words = nullptr;
+  uint32_t* l1_counts = nullptr;
+  int64_t* l1_off = nullptr;
+  int4* leaf_origin = nullptr;
+  uint32_t* leaf_words = nullptr;
+  uint32_t* leaf_counts = nullptr;
+  int64_t* leaf_off = nullptr;
+  void release() {
+    dfree(l2_counts); dfree(l2_off); dfree(l1_origin); dfree(l1_words); dfree(l1_counts); dfree(l1_off);
+    dfree(leaf_origin); dfree(leaf_words); dfree(leaf_counts); dfree(leaf_off);
+    n_l1 = n_leaf = -1;
+  }
+};
+
+// Topology cache of [Hash,5,4,NN(3)] plus the per-batch query scratch.
+struct QueryCache {
+  bool ready = false;
+  uint64_t* l2_key = nullptr;
+  uint32_t* l2_pre = nullptr;
+  uint32_t* l1_pre = nullptr;
+  int64_t batch = 0;
+  uint8_t* qmask = nullptr;
+  uint32_t* counts = nullptr;
+  int64_t* off = nullptr;
+  int32_t* list = nullptr;
+  float* vals = nullptr;
+  void release() {
+    dfree(l2_key); dfree(l2_pre); dfree(l1_pre);
+    dfree(qmask); dfree(counts); dfree(off); dfree(list); dfree(vals);
+    ready = false;
+    batch = 0;
+  }
+};
+}  // namespace
+
+struct nvdb_model {
+  int grid_class = 0;
+  float background = 0.f, half_width = 0.f;
+  int32_t origin[3] = {0, 0, 0};
+  int log2e = 7;
+  int ffm[2] = {32, 32};
+  int width[3] = {32, 32, 32}, layers[3] = {3, 3, 3};
+  int64_t n_l2 = 0, n_l1 = 0, n_leaf = 0, n_active = 0;
+  std::vector<uint32_t> q_host[2];
+  uint32_t* q_dev[2] = {nullptr, nullptr};
+  DevNet net[3];
+  std::vector<int32_t> l2_origin_host;
+  std::vector<uint64_t> l2_mask_host;
+  int4* l2_origin = nullptr;
+  unsigned long long* l2_mask = nullptr;
+  std::vector<PatchSet> patches;
+  std::vector<float> losses[3];
+  uint32_t* status = nullptr;
+  DecodeScratch ds;
+  QueryCache qc;
+  Scan scan;
+  float* partial = nullptr;
+  int64_t partial_cap = 0;
+  ~nvdb_model() {
+    dfree(q_dev[0]); dfree(q_dev[1]); dfree(l2_origin); dfree(l2_mask); dfree(status); dfree(partial);
+    for (auto& p : patches) p.release();
+    ds.release();
+    qc.release();
+  }
+  const PatchSet* patch_set(int prec) const {
+    for (auto& p : patches)
+      if (p.prec == prec) return &p;
+    return nullptr;
+  }
+  float value_scale() const { return grid_class == 0 ? half_width : 1.f; }
+};
+
+// ============================================================================ kernel dispatch
+namespace {
+bool supported_shape(int nin, int w) { return (nin == 32 || nin == 64) && (w == 32 || w == 64); }
+
+NetView net_view(const nvdb_model* m, int k) {
+  NetView v;
+  v.n_in = m->net[k].n_in;
+  v.width = m->net[k].width;
+  v.layers = m->net[k].layers;
+  v.p32 = m->net[k].p32;
+  v.wpk = m->net[k].wpk;
+  v.q = m->q_dev[k == 0 ? 0 : 1];
+  return v;
+}
+
+template <int NIN, int W>
+nvdb_status launch_eval_t(const NetView& nv, const EvalJob& job, nvdb_precision prec, cudaStream_t s) {
+  const int64_t ntiles = job_tiles(job.mode, job.n_items);
+  if (ntiles == 0) return NVDB_OK;
+  int occ = 0;
+  if (prec == NVDB_FP32) {
+    const size_t smem = f32_smem_bytes<NIN, W>(nv.layers);
+    CU(cudaFuncSetAttribute(mlp_f32_kernel<NIN, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, mlp_f32_kernel<NIN, W>, kTile, smem));
+    const int64_t grid = std::min<int64_t>(ntiles, (int64_t)num_sms() * std::max(occ, 1));
+    mlp_f32_kernel<NIN, W><<<(unsigned)grid, kTile, smem, s>>>(nv, job);
+  } else if (prec == NVDB_BF16) {
+    const TcLayout<NIN, W> lay(nv.layers);
+    CU(cudaFuncSetAttribute(mlp_tc_kernel<NIN, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lay.total));
+    CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, mlp_tc_kernel<NIN, W>, kTile, lay.total));
+    if (occ < 1) return fail(NVDB_ERR_UNSUPPORTED, "tensor-core kernel does not fit on an SM");
+    const int64_t grid = std::min<int64_t>(ntiles, (int64_t)num_sms() * occ);
+    mlp_tc_kernel<NIN, W><<<(unsigned)grid, kTile, lay.total, s>>>(nv, job);
+  } else {
+    return fail(NVDB_ERR_UNSUPPORTED, "precision %d not implemented", (int)prec);
+  }
+  CU(cudaGetLastError());
+  return NVDB_OK;
+}
+
+nvdb_status launch_eval(const nvdb_model* m, int k, nvdb_precision prec, EvalJob job, cudaStream_t s) {
+  const NetView nv = net_view(m, k);
+  job.ox = m->origin[0];
+  job.oy = m->origin[1];
+  job.oz = m->origin[2];
+  job.status = m->status;
+  if (nv.n_in == 32 && nv.width == 32) return launch_eval_t<32, 32>(nv, job, prec, s);
+  if (nv.n_in == 32 && nv.width == 64) return launch_eval_t<32, 64>(nv, job, prec, s);
+  if (nv.n_in == 64 && nv.width == 32) return launch_eval_t<64, 32>(nv, job, prec, s);
+  if (nv.n_in == 64 && nv.width == 64) return launch_eval_t<64, 64>(nv, job, prec, s);
+  return fail(NVDB_ERR_UNSUPPORTED, "network shape n=%d w=%d", nv.n_in, nv.width);
+}
+
+template <int NIN, int W>
+nvdb_status launch_train_t(const NetView& nv, const TrainJob& job, int grid, cudaStream_t s) {
+  const size_t smem = TrainSmem<NIN, W>::bytes(nv.layers);
+  CU(cudaFuncSetAttribute(train_fwd_bwd_kernel<NIN, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  train_fwd_bwd_kernel<NIN, W><<<grid, kTile, smem, s>>>(nv, job);
+  CU(cudaGetLastError());
+  return NVDB_OK;
+}
+
+nvdb_status launch_train(const nvdb_model* m, int k, TrainJob job, int grid, cudaStream_t s) {
+  const NetView nv = net_view(m, k);
+  job.ox = m->origin[0];
+  job.oy = m->origin[1];
+  job.oz = m->origin[2];
+  if (nv.n_in == 32 && nv.width == 32) return launch_train_t<32, 32>(nv, job, grid, s);
+  if (nv.n_in == 32 && nv.width == 64) return launch_train_t<32, 64>(nv, job, grid, s);
+  if (nv.n_in == 64 && nv.width == 32) return launch_train_t<64, 32>(nv, job, grid, s);
+  if (nv.n_in == 64 && nv.width == 64) return launch_train_t<64, 64>(nv, job, grid, s);
+  return fail(NVDB_ERR_UNSUPPORTED, "network shape n=%d w=%d", nv.n_in, nv.width);
+}
+
+nvdb_status read_status(uint32_t* d_status, cudaStream_t s, uint32_t* out) {
+  uint32_t h = 0;
+  CU(cudaMemcpyAsync(&h, d_status, sizeof h, cudaMemcpyDeviceToHost, s));
+  CU(cudaStreamSynchronize(s));
+  *out = h;
+  return NVDB_OK;
+}
+
+nvdb_status status_to_error(uint32_t st) {
+  if (st & ST_TIMEOUT) return fail(NVDB_ERR_TIMEOUT, "a device-side wait timed out");
+  if (st & ST_CAPACITY) return fail(NVDB_ERR_CAPACITY, "output capacity exceeded on the device");
+  if (st & ST_CORRUPT) return fail(NVDB_ERR_CORRUPT, "decoded counts differ from the model header");
+  return NVDB_OK;
+}
+
+nvdb_status upload_net(nvdb_model* m, int k, const float* host_params, cudaStream_t s) {
+  DevNet& d = m->net[k];
+  d.n_in = k == 0 ? m->ffm[0] : m->ffm[1];
+  d.width = m->width[k];
+  d.layers = m->layers[k];
+  d.P = net_param_count(d.n_in, d.width, d.layers);
+  dfree(d.p32); dfree(d.wpk); dfree(d.m); dfree(d.v);
+  TRY(dalloc(&d.p32, (size_t)d.P));
+  TRY(dalloc(&d.wpk, (size_t)(d.width * d.n_in + (d.layers - 1) * d.width * d.width) + 8));
+  if (host_params) CU(cudaMemcpyAsync(d.p32, host_params, d.P * 4, cudaMemcpyHostToDevice, s));
+  return NVDB_OK;
+}
+
+nvdb_status pack_net(nvdb_model* m, int k, cudaStream_t s) {
+  DevNet& d = m->net[k];
+  pack_weights_kernel<<<64, 256, 0, s>>>(d.p32, d.wpk, d.n_in, d.width, d.layers);
+  CU(cudaGetLastError());
+  return NVDB_OK;
+}
+
+nvdb_status upload_patch_set(PatchSet& p) {
+  TRY(dalloc(&p.d_l1_off, p.l1_off.size()));
+  TRY(dalloc(&p.d_l0_off, p.l0_off.size()));
+  TRY(dalloc(&p.d_l1_idx, p.l1_idx.size() + 1));
+  TRY(dalloc(&p.d_l0_idx, p.l0_idx.size() + 1));
+  CU(cudaMemcpy(p.d_l1_off, p.l1_off.data(), p.l1_off.size() * 4, cudaMemcpyHostToDevice));
+  CU(cudaMemcpy(p.d_l0_off, p.l0_off.data(), p.l0_off.size() * 4, cudaMemcpyHostToDevice));
+  if (!p.l1_idx.empty()) CU(cudaMemcpy(p.d_l1_idx, p.l1_idx.data(), p.l1_idx.size() * 2, cudaMemcpyHostToDevice));
+  if (!p.l0_idx.empty()) CU(cudaMemcpy(p.d_l0_idx, p.l0_idx.data(), p.l0_idx.size() * 2, cudaMemcpyHostToDevice));
+  return NVDB_OK;
+}
+
+nvdb_status check_model_shapes(const nvdb_model* m) {
+  for (int k = 0; k < 3; ++k) {
+    const int nin = k == 0 ? m->ffm[0] : m->ffm[1];
+    if (!supported_shape(nin, m->width[k]))
+      return fail(NVDB_ERR_UNSUPPORTED, "network %d: encoding size %d / width %d (supported: 32, 64)", k, nin,
+                  m->width[k]);
+    if (m->layers[k] < 1 || m->layers[k] > kMaxLayers)
+      return fail(NVDB_ERR_UNSUPPORTED, "network %d: %d hidden layers (supported: 1..%d)", k, m->layers[k], kMaxLayers);
+  }
+  return NVDB_OK;
+}
+}  // namespace
+
+// ============================================================================ build
+extern "C" nvdb_status nvdb_build(const int32_t* d_ijk, const float* d_val, int64_t n, const nvdb_build_opts* opts,
+                                  nvdb_stream stream, nvdb_grid** out) {
+  if (!out || !opts || n < 0 || (n > 0 && (!d_ijk || !d_val))) return fail(NVDB_ERR_INVALID_ARG, "nvdb_build: bad arguments");
+  if (opts->grid_class != 0 && opts->grid_class != 1) return fail(NVDB_ERR_INVALID_ARG, "grid_class must be 0 or 1");
+  if (opts->grid_class == 0 && !(opts->half_width > 0.f)) return fail(NVDB_ERR_INVALID_ARG, "half_width must be > 0");
+  if (n >= (int64_t)INT32_MAX) return fail(NVDB_ERR_UNSUPPORTED, "nvdb_build: n >= 2^31");
+  *out = nullptr;
+  cudaStream_t s = (cudaStream_t)stream;
+  auto* g = new nvdb_grid();
+  g->grid_class = opts->grid_class;
+  g->half_width = opts->grid_class == 0 ? opts->half_width : 0.f;
+  g->background = opts->grid_class == 0 ? opts->half_width : 0.f;
+  g->n = n;
+  nvdb_status st = NVDB_OK;
+  uint64_t *k0 = nullptr, *k1 = nullptr;
+  uint32_t *i0 = nullptr, *i1 = nullptr, *h = nullptr, *status = nullptr;
+  int64_t* e = nullptr;
+  void* tmp = nullptr;
+  auto cleanup = [&]() {
+    dfree(k0); dfree(k1); dfree(i0); dfree(i1); dfree(h); dfree(e); dfree(status);
+    if (tmp) cudaFree(tmp);
+  };
+  auto run = [&]() -> nvdb_status {
+    if (n == 0) return NVDB_OK;
+    TRY(dalloc(&k0, n)); TRY(dalloc(&k1, n)); TRY(dalloc(&i0, n)); TRY(dalloc(&i1, n));
+    TRY(dalloc(&h, 3 * (size_t)n)); TRY(dalloc(&e, 3 * (size_t)n)); TRY(dalloc(&status, 1));
+    TRY(dalloc(&g->ijk, 3 * (size_t)n)); TRY(dalloc(&g->val, n));
+    CU(cudaMemsetAsync(status, 0, 4, s));
+    build_keys_kernel<<<blocks_for(n, 256), 256, 0, s>>>(d_ijk, n, k0, i0, status);
+    size_t tb = 0;
+    CU(cub::DeviceRadixSort::SortPairs(nullptr, tb, k0, k1, i0, i1, (int)n, 0, 63, s));
+    CU(cudaMalloc(&tmp, tb));
+    CU(cub::DeviceRadixSort::SortPairs(tmp, tb, k0, k1, i0, i1, (int)n, 0, 63, s));
+    build_gather_kernel<<<blocks_for(n, 256), 256, 0, s>>>(k1, i1, n, d_ijk, d_val, g->ijk, g->val, h, h + n,
+                                                            h + 2 * n, status);
+    CU(cudaGetLastError());
+    Scan sc;
+    int64_t tot[3];
+    for (int l = 0; l < 3; ++l) {
+      TRY(sc.run(h + l * n, n, e + l * n, s));
+      CU(cudaMemcpyAsync(&tot[l], sc.total, 8, cudaMemcpyDeviceToHost, s));
+      CU(cudaStreamSynchronize(s));
+    }
+    uint32_t hst = 0;
+    TRY(read_status(status, s, &hst));
+    if (hst & ST_RANGE) return fail(NVDB_ERR_INVALID_ARG, "nvdb_build: coordinate outside [0, 2^21)");
+    if (hst & ST_DUP) return fail(NVDB_ERR_DUPLICATE_VOXEL, "nvdb_build: duplicate voxel");
+    g->n_leaf = tot[0];
+    g->n_l1 = tot[1];
+    g->n_l2 = tot[2];
+    TRY(dalloc(&g->leaf_origin, g->n_leaf)); TRY(dalloc(&g->leaf_first, g->n_leaf + 1));
+    TRY(dalloc(&g->leaf_mask, 8 * g->n_leaf)); TRY(dalloc(&g->l1_origin, g->n_l1));
+    TRY(dalloc(&g->l1_mask, 64 * g->n_l1)); TRY(dalloc(&g->l2_origin, g->n_l2)); TRY(dalloc(&g->l2_mask, 512 * g->n_l2));
+    CU(cudaMemsetAsync(g->leaf_mask, 0, 64 * g->n_leaf, s));
+    CU(cudaMemsetAsync(g->l1_mask, 0, 512 * g->n_l1, s));
+    CU(cudaMemsetAsync(g->l2_mask, 0, 4096 * g->n_l2, s));
+    build_fill_kernel<<<blocks_for(n, 256), 256, 0, s>>>(g->ijk, n, h, h + n, h + 2 * n, e, e + n, e + 2 * n,
+                                                          g->leaf_origin, g->leaf_first, g->leaf_mask, g->l1_origin,
+                                                          g->l1_mask, g->l2_origin, g->l2_mask);
+    CU(cudaGetLastError());
+    CU(cudaMemcpyAsync(g->leaf_first + g->n_leaf, &g->n, 8, cudaMemcpyHostToDevice, s));
+    // encoding domain: level-1 aligned bounding box, power-of-two extent >= 128
+    std::vector<int4> l1(g->n_l1);
+    CU(cudaMemcpyAsync(l1.data(), g->l1_origin, g->n_l1 * sizeof(int4), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    int lo[3] = {INT32_MAX, INT32_MAX, INT32_MAX}, hi[3] = {0, 0, 0};
+    for (auto& o : l1) {
+      const int v[3] = {o.x, o.y, o.z};
+      for (int d = 0; d < 3; ++d) { lo[d] = std::min(lo[d], v[d]); hi[d] = std::max(hi[d], v[d] + 128); }
+    }
+    int ext = 0;
+    for (int d = 0; d < 3; ++d) { g->origin[d] = lo[d]; ext = std::max(ext, hi[d] - lo[d]); }
+    g->log2e = 7;
+    while ((1 << g->log2e) < ext) ++g->log2e;
+    return NVDB_OK;
+  };
+  st = run();
+  cleanup();
+  if (st != NVDB_OK) { delete g; return st; }
+  *out = g;
+  return NVDB_OK;
+}
+
+extern "C" nvdb_status nvdb_grid_info(const nvdb_grid* g, nvdb_info* out) {
+  if (!g || !out) return fail(NVDB_ERR_INVALID_ARG, "nvdb_grid_info: NULL");
+  out->grid_class = g->grid_class;
+  out->background = g->background;
+  out->half_width = g->half_width;
+  for (int d = 0; d < 3; ++d) out->origin[d] = g->origin[d];
+  out->log2_extent = g->log2e;
+  out->n_active = g->n;
+  out->n_leaf = g->n_leaf;
+  out->n_l1 = g->n_l1;
+  out->n_l2 = g->n_l2;
+  return NVDB_OK;
+}
+
+static nvdb_status copy_int4_to3(const int4* d, int64_t n, int32_t* host, cudaStream_t s) {
+  std::vector<int4> t(n);
+  if (n) CU(cudaMemcpyAsync(t.data(), d, n * sizeof(int4), cudaMemcpyDeviceToHost, s));
+  CU(cudaStreamSynchronize(s));
+  for (int64_t i = 0; i < n; ++i) { host[3 * i] = t[i].x; host[3 * i + 1] = t[i].y; host[3 * i + 2] = t[i].z; }
+  return NVDB_OK;
+}
+
+extern "C" nvdb_status nvdb_grid_read(const nvdb_grid* g, int32_t* ijk, float* val, int32_t* leaf_origin,
+                                      uint64_t* leaf_mask, int32_t* l1_origin, uint64_t* l1_mask, nvdb_stream stream) {
+  if (!g) return fail(NVDB_ERR_INVALID_ARG, "nvdb_grid_read: NULL grid");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (ijk && g->n) CU(cudaMemcpyAsync(ijk, g->ijk, 12 * g->n, cudaMemcpyDeviceToHost, s));
+  if (val && g->n) CU(cudaMemcpyAsync(val, g->val, 4 * g->n, cudaMemcpyDeviceToHost, s));
+  if (leaf_mask && g->n_leaf) CU(cudaMemcpyAsync(leaf_mask, g->leaf_mask, 64 * g->n_leaf, cudaMemcpyDeviceToHost, s));
+  if (l1_mask && g->n_l1) CU(cudaMemcpyAsync(l1_mask, g->l1_mask, 512 * g->n_l1, cudaMemcpyDeviceToHost, s));
+  if (leaf_origin) TRY(copy_int4_to3(g->leaf_origin, g->n_leaf, leaf_origin, s));
+  if (l1_origin) TRY(copy_int4_to3(g->l1_origin, g->n_l1, l1_origin, s));
+  CU(cudaStreamSynchronize(s));
+  return NVDB_OK;
+}
+
+extern "C" nvdb_status nvdb_grid_free(nvdb_grid* g) {
+  delete g;
+  return NVDB_OK;
+}
+
+// ============================================================================ compress
+extern "C" void nvdb_train_opts_default(nvdb_train_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof *o);
+  o->seed = 1;
+  for (int k = 0; k < 3; ++k) { o->width[k] = 32; o->layers[k] = 3; }
+  o->ffm_sigma = 1.25f;
+  o->steps = 200;
+  o->batch = 4096;
+  o->lr = 1e-3f;
+  o->lr_decay = 0.975f;
+  o->lr_interval = 100;
+  o->loss = NVDB_LOSS_MSE;
+  o->train_prec = NVDB_FP32;
+  o->patch_precs = (1u << NVDB_FP32) | (1u << NVDB_BF16);
+}
+
+namespace {
+nvdb_status ensure_partial(nvdb_model* m, int64_t count) {
+  if (count <= m->partial_cap) return NVDB_OK;
+  dfree(m->partial);
+  TRY(dalloc(&m->partial, (size_t)count));
+  m->partial_cap = count;
+  return NVDB_OK;
+}
+
+TrainJob grid_train_job(const nvdb_grid* g, int net, const nvdb_train_opts* o) {
+  TrainJob j{};
+  j.net = net;
+  j.loss = net == 2 ? o->loss : LOSS_BCE;
+  j.seed = o->seed;
+  j.batch = o->batch;
+  j.l1_origin = g->l1_origin; j.l1_mask = g->l1_mask; j.n_l1 = g->n_l1;
+  j.leaf_origin = g->leaf_origin; j.leaf_mask = g->leaf_mask; j.n_leaf = g->n_leaf;
+  j.ijk = g->ijk; j.val = g->val; j.n = g->n;
+  j.tscale = g->grid_class == 0 ? 1.f / g->half_width : 1.f;
+  return j;
+}
+
+// Classify every candidate of the grid at `prec`; mismatches with the explicit
+// masks become the patch lists (Section 3.3.2).
+nvdb_status make_patches(nvdb_model* m, const nvdb_grid* g, int prec, cudaStream_t s) {
+  PatchSet ps;
+  ps.prec = prec;
+  for (int lev = 0; lev < 2; ++lev) {
+    const int64_t items = lev == 0 ? g->n_l1 : g->n_leaf;
+    const int wpi = lev == 0 ? 128 : 16;
+    uint32_t *words = nullptr, *counts = nullptr, *off32 = nullptr;
+    int64_t* off = nullptr;
+    uint16_t* idx = nullptr;
+    auto run = [&]() -> nvdb_status {
+      TRY(dalloc(&words, (size_t)items * wpi + 1));
+      TRY(dalloc(&counts, items + 1));
+      TRY(dalloc(&off, items + 1));
+      TRY(dalloc(&off32, items + 1));
+      EvalJob job{};
+      job.mode = lev == 0 ? MODE_L1 : MODE_L0;
+      job.nodes = lev == 0 ? g->l1_origin : g->leaf_origin;
+      job.n_items = items;
+      job.words = words;
+      TRY(launch_eval(m, lev == 0 ? 0 : 1, (nvdb_precision)prec, job, s));
+      const uint32_t* truth = reinterpret_cast<const uint32_t*>(lev == 0 ? g->l1_mask : g->leaf_mask);
+      if (items) mismatch_count_kernel<<<blocks_for(items, 128), 128, 0, s>>>(words, truth, wpi, items, counts);
+      TRY(m->scan.run(counts, items, off, s));
+      offsets_to_u32_kernel<<<blocks_for(items + 1, 256), 256, 0, s>>>(off, m->scan.total, items, off32);
+      int64_t total = 0;
+      CU(cudaMemcpyAsync(&total, m->scan.total, 8, cudaMemcpyDeviceToHost, s));
+      CU(cudaStreamSynchronize(s));
+      TRY(dalloc(&idx, (size_t)total + 1));
+      if (items) emit_patches_kernel<<<blocks_for(items, 128), 128, 0, s>>>(words, wpi, items, off, idx);
+      CU(cudaGetLastError());
+      std::vector<uint32_t>& ho = lev == 0 ? ps.l1_off : ps.l0_off;
+      std::vector<uint16_t>& hi = lev == 0 ? ps.l1_idx : ps.l0_idx;
+      ho.resize(items + 1);
+      hi.resize(total);
+      CU(cudaMemcpyAsync(ho.data(), off32, (items + 1) * 4, cudaMemcpyDeviceToHost, s));
+      if (total) CU(cudaMemcpyAsync(hi.data(), idx, total * 2, cudaMemcpyDeviceToHost, s));
+      CU(cudaStreamSynchronize(s));
+      return NVDB_OK;
+    };
+    const nvdb_status st = run();
+    dfree(words); dfree(counts); dfree(off); dfree(off32); dfree(idx);
+    if (st != NVDB_OK) return st;
+  }
+  TRY(upload_patch_set(ps));
+  for (auto& p : m->patches)
+    if (p.prec == prec) { p.release(); p = ps; return NVDB_OK; }
+  m->patches.push_back(ps);
+  return NVDB_OK;
+}
+}  // namespace
+
+extern "C" nvdb_status nvdb_compress(const nvdb_grid* g, const nvdb_train_opts* o, const nvdb_model* warm,
+                                     nvdb_stream stream, nvdb_model** out) {
+  if (!g || !o || !out) return fail(NVDB_ERR_INVALID_ARG, "nvdb_compress: NULL argument");
+  if (o->steps < 0 || o->batch <= 0 || !(o->lr >= 0.f) || o->lr_interval < 0)
+    return fail(NVDB_ERR_INVALID_ARG, "nvdb_compress: bad steps/batch/lr");
+  if (o->loss != NVDB_LOSS_MSE && o->loss != NVDB_LOSS_L1) return fail(NVDB_ERR_INVALID_ARG, "loss must be MSE or L1");
+  if (o->train_prec != NVDB_FP32) return fail(NVDB_ERR_UNSUPPORTED, "training precision %d", o->train_prec);
+  if (g->n == 0) return fail(NVDB_ERR_INVALID_ARG, "nvdb_compress: empty grid");
+  if ((uint64_t)g->n_leaf * 512 >= (1ull << 32) || (uint64_t)g->n_l1 * 4096 >= (1ull << 32))
+    return fail(NVDB_ERR_UNSUPPORTED, "candidate population >= 2^32");
+  *out = nullptr;
+  cudaStream_t s = (cudaStream_t)stream;
+  auto* m = new nvdb_model();
+  auto run = [&]() -> nvdb_status {
+    m->grid_class = g->grid_class;
+    m->background = g->background;
+    m->half_width = g->half_width;
+    for (int d = 0; d < 3; ++d) m->origin[d] = g->origin[d];
+    m->log2e = g->log2e;
+    m->n_l2 = g->n_l2; m->n_l1 = g->n_l1; m->n_leaf = g->n_leaf; m->n_active = g->n;
+    if (warm) {
+      m->ffm[0] = warm->ffm[0]; m->ffm[1] = warm->ffm[1];
+      for (int k = 0; k < 3; ++k) { m->width[k] = warm->width[k]; m->layers[k] = warm->layers[k]; }
+    } else {
+      for (int k = 0; k < 3; ++k) { m->width[k] = o->width[k]; m->layers[k] = o->layers[k]; }
+      m->ffm[0] = o->ffm_size[0] ? o->ffm_size[0] : o->width[0];
+      m->ffm[1] = o->ffm_size[1] ? o->ffm_size[1] : std::max(o->width[1], o->width[2]);
+    }
+    TRY(check_model_shapes(m));
+    TRY(dalloc(&m->status, 1));
+    CU(cudaMemsetAsync(m->status, 0, 4, s));
+    const double E = std::ldexp(1.0, m->log2e);
+    for (int lev = 0; lev < 2; ++lev) {
+      m->q_host[lev] = warm ? warm->q_host[lev]
+                            : ffm_increments(o->seed, lev == 0 ? 1 : 0, m->ffm[lev] / 2, (double)o->ffm_sigma,
+                                             lev == 0 ? E / 8 : E);
+      TRY(dalloc(&m->q_dev[lev], m->q_host[lev].size()));
+      CU(cudaMemcpy(m->q_dev[lev], m->q_host[lev].data(), m->q_host[lev].size() * 4, cudaMemcpyHostToDevice));
+    }
+    for (int k = 0; k < 3; ++k) {
+      if (warm) {
+        TRY(upload_net(m, k, nullptr, s));
+        CU(cudaMemcpyAsync(m->net[k].p32, warm->net[k].p32, m->net[k].P * 4, cudaMemcpyDeviceToDevice, s));
+      } else {
+        const std::vector<float> p = xavier_params(o->seed, k, k == 0 ? m->ffm[0] : m->ffm[1], m->width[k], m->layers[k]);
+        TRY(upload_net(m, k, p.data(), s));
+        CU(cudaStreamSynchronize(s));
+      }
+      TRY(dalloc(&m->net[k].m, m->net[k].P));
+      TRY(dalloc(&m->net[k].v, m->net[k].P));
+      CU(cudaMemsetAsync(m->net[k].m, 0, m->net[k].P * 4, s));
+      CU(cudaMemsetAsync(m->net[k].v, 0, m->net[k].P * 4, s));
+    }
+    // explicit upper tree (root + level-2 nodes) is kept as is (Section 3.3.1)
+    TRY(dalloc(&m->l2_origin, g->n_l2));
+    TRY(dalloc(&m->l2_mask, 512 * g->n_l2));
+    CU(cudaMemcpyAsync(m->l2_origin, g->l2_origin, g->n_l2 * sizeof(int4), cudaMemcpyDeviceToDevice, s));
+    CU(cudaMemcpyAsync(m->l2_mask, g->l2_mask, g->n_l2 * 4096, cudaMemcpyDeviceToDevice, s));
+    m->l2_origin_host.resize(3 * g->n_l2);
+    m->l2_mask_host.resize(512 * g->n_l2);
+    TRY(copy_int4_to3(g->l2_origin, g->n_l2, m->l2_origin_host.data(), s));
+    CU(cudaMemcpyAsync(m->l2_mask_host.data(), g->l2_mask, g->n_l2 * 4096, cudaMemcpyDeviceToHost, s));
+    // training: each network for `steps` Adam steps
+    const int grid = (int)std::min<int64_t>((o->batch + kTile - 1) / kTile, num_sms());
+    float* d_loss = nullptr;
+    TRY(dalloc(&d_loss, (size_t)std::max(1, o->steps)));
+    nvdb_status st = NVDB_OK;
+    for (int k = 0; k < 3 && st == NVDB_OK; ++k) {
+      DevNet& d = m->net[k];
+      if ((st = ensure_partial(m, (int64_t)grid * (d.P + 1))) != NVDB_OK) break;
+      TrainJob job = grid_train_job(g, k, o);
+      job.partial = m->partial;
+      for (int t = 1; t <= o->steps && st == NVDB_OK; ++t) {
+        job.step = t;
+        st = launch_train(m, k, job, grid, s);
+        if (st != NVDB_OK) break;
+        const float lr_t = o->lr_interval > 0 ? (float)((double)o->lr * std::pow((double)o->lr_decay, (double)((t - 1) / o->lr_interval)))
+                                              : o->lr;
+        adam_reduce_kernel<<<blocks_for(d.P + 1, 256), 256, 0, s>>>(m->partial, grid, d.P, d.p32, d.m, d.v, t, lr_t,
+                                                                    nullptr, d_loss + (t - 1), 1.f / (float)o->batch);
+        if (cudaGetLastError() != cudaSuccess) st = fail(NVDB_ERR_CUDA, "adam launch failed");
+      }
+      if (st == NVDB_OK) {
+        m->losses[k].resize(o->steps);
+        if (o->steps) {
+          cudaError_t e = cudaMemcpyAsync(m->losses[k].data(), d_loss, o->steps * 4, cudaMemcpyDeviceToHost, s);
+          if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+          if (e != cudaSuccess) st = fail(NVDB_ERR_CUDA, "loss readback: %s", cudaGetErrorString(e));
+        }
+      }
+    }
+    dfree(d_loss);
+    TRY(st);
+    for (int k = 0; k < 3; ++k) TRY(pack_net(m, k, s));
+    uint32_t pp = o->patch_precs ? o->patch_precs : (1u << NVDB_FP32);
+    for (int p = 0; p < 3; ++p)
+      if (pp & (1u << p)) {
+        if (p == NVDB_FP8_E4M3) return fail(NVDB_ERR_UNSUPPORTED, "FP8 patches not implemented");
+        TRY(make_patches(m, g, p, s));
+      }
+    uint32_t hst = 0;
+    TRY(read_status(m->status, s, &hst));
+    TRY(status_to_error(hst));
+    return NVDB_OK;
+  };
+  const nvdb_status st = run();
+  if (st != NVDB_OK) { delete m; return st; }
+  *out = m;
+  return NVDB_OK;
+}
+
+extern "C" nvdb_status nvdb_model_losses(const nvdb_model* m, int net, float* losses, int64_t cap, int64_t* count) {
+  if (!m || net < 0 || net > 2 || (cap > 0 && !losses)) return fail(NVDB_ERR_INVALID_ARG, "nvdb_model_losses: bad arguments");
+  const auto& l = m->losses[net];
+  if (count) *count = (int64_t)l.size();
+  for (int64_t i = 0; i < cap && i < (int64_t)l.size(); ++i) losses[i] = l[i];
+  return NVDB_OK;
+}
+
+// ============================================================================ decompress
+namespace {
+nvdb_status ensure_decode_scratch(nvdb_model* m) {
+  DecodeScratch& d = m->ds;
+  if (d.n_l1 == m->n_l1 && d.n_leaf == m->n_leaf) return NVDB_OK;
+  d.release();
+  TRY(dalloc(&d.l2_counts, m->n_l2 + 1)); TRY(dalloc(&d.l2_off, m->n_l2 + 1));
+  TRY(dalloc(&d.l1_origin, m->n_l1 + 1)); TRY(dalloc(&d.l1_words, 128 * m->n_l1 + 4));
+  TRY(dalloc(&d.l1_counts, m->n_l1 + 1)); TRY(dalloc(&d.l1_off, m->n_l1 + 1));
+  TRY(dalloc(&d.leaf_origin, m->n_leaf + 1)); TRY(dalloc(&d.leaf_words, 16 * m->n_leaf + 4));
+  TRY(dalloc(&d.leaf_counts, m->n_leaf + 1)); TRY(dalloc(&d.leaf_off, m->n_leaf + 1));
+  TRY(m->scan.reserve(std::max<int64_t>(m->n_leaf, std::max(m->n_l1, m->n_l2))));
+  d.n_l1 = m->n_l1;
+  d.n_leaf = m->n_leaf;
+  return NVDB_OK;
+}
+
+// Top-down topology decode (Section 3.5): level-1 origins, child bits, leaf
+// origins, active bits (all patched), leaf offsets of the active voxels.
+nvdb_status decode_topology(nvdb_model* m, const PatchSet* ps, nvdb_precision prec, cudaStream_t s) {
+  TRY(ensure_decode_scratch(m));
+  DecodeScratch& d = m->ds;
+  const uint64_t* l2m = reinterpret_cast<const uint64_t*>(m->l2_mask);
+  if (m->n_l2) {
+    l2_count_kernel<<<(unsigned)m->n_l2, 512, 0, s>>>(l2m, m->n_l2, d.l2_counts);
+    TRY(m->scan.run(d.l2_counts, m->n_l2, d.l2_off, s));
+    check_total_kernel<<<1, 1, 0, s>>>(m->scan.total, m->n_l1, m->status);
+    l2_emit_kernel<<<(unsigned)m->n_l2, 512, 0, s>>>(l2m, m->l2_origin, m->n_l2, d.l2_off, d.l1_origin, m->n_l1,
+                                                     m->status);
+  }
+  EvalJob j1{};
+  j1.mode = MODE_L1;
+  j1.nodes = d.l1_origin;
+  j1.n_items = m->n_l1;
+  j1.words = d.l1_words;
+  TRY(launch_eval(m, 0, prec, j1, s));
+  if (m->n_l1)
+    patch_count_kernel<<<blocks_for(m->n_l1, 128), 128, 0, s>>>(d.l1_words, 128, m->n_l1, ps->d_l1_off, ps->d_l1_idx,
+                                                               d.l1_counts);
+  TRY(m->scan.run(d.l1_counts, m->n_l1, d.l1_off, s));
+  check_total_kernel<<<1, 1, 0, s>>>(m->scan.total, m->n_leaf, m->status);
+  if (m->n_l1)
+    emit_leaves_kernel<<<blocks_for(m->n_l1 * 32, 256), 256, 0, s>>>(d.l1_words, d.l1_origin, m->n_l1, d.l1_off,
+                                                                    d.leaf_origin, m->n_leaf, m->status);
+  EvalJob j0{};
+  j0.mode = MODE_L0;
+  j0.nodes = d.leaf_origin;
+  j0.n_items = m->n_leaf;
+  j0.words = d.leaf_words;
+  TRY(launch_eval(m, 1, prec, j0, s));
+  if (m->n_leaf)
+    patch_count_kernel<<<blocks_for(m->n_leaf, 128), 128, 0, s>>>(d.leaf_words, 16, m->n_leaf, ps->d_l0_off,
+                                                                 ps->d_l0_idx, d.leaf_counts);
+  TRY(m->scan.run(d.leaf_counts, m->n_leaf, d.leaf_off, s));
+  check_total_kernel<<<1, 1, 0, s>>>(m->scan.total, m->n_active, m->status);
+  CU(cudaGetLastError());
+  return NVDB_OK;
+}
+}  // namespace
+
+extern "C" nvdb_status nvdb_decompress(const nvdb_model* const* models, int n_models, nvdb_precision prec,
+                                       int32_t* d_ijk, float* d_val, int64_t capacity, int64_t* counts,
+                                       nvdb_stream stream) {
+  if (!models || n_models < 0 || !counts || capacity < 0) return fail(NVDB_ERR_INVALID_ARG, "nvdb_decompress: bad arguments");
+  if (d_ijk && !d_val) return fail(NVDB_ERR_INVALID_ARG, "nvdb_decompress: d_val is NULL");
+  int64_t need = 0;
+  for (int i = 0; i < n_models; ++i) {
+    if (!models[i]) return fail(NVDB_ERR_INVALID_ARG, "nvdb_decompress: NULL model");
+    counts[i] = models[i]->n_active;
+    need += models[i]->n_active;
+    if (!models[i]->patch_set(prec)) return fail(NVDB_ERR_UNSUPPORTED, "model %d has no patch set for precision %d", i, (int)prec);
+  }
+  if (!d_ijk) return NVDB_OK;
+  if (need > capacity) return fail(NVDB_ERR_CAPACITY, "nvdb_decompress: need %lld voxels, capacity %lld", (long long)need, (long long)capacity);
+  cudaStream_t s = (cudaStream_t)stream;
+  int64_t base = 0;
+  for (int i = 0; i < n_models; ++i) {
+    nvdb_model* m = const_cast<nvdb_model*>(models[i]);
+    CU(cudaMemsetAsync(m->status, 0, 4, s));
+    TRY(decode_topology(m, m->patch_set(prec), prec, s));
+    DecodeScratch& d = m->ds;
+    if (m->n_leaf)
+      emit_voxels_kernel<<<blocks_for(m->n_leaf * 32, 256), 256, 0, s>>>(d.leaf_words, d.leaf_origin, m->n_leaf,
+                                                                        d.leaf_off, d_ijk + 3 * base, m->n_active,
+                                                                        m->status);
+    EvalJob jr{};
+    jr.mode = MODE_LIST;
+    jr.ijk = d_ijk + 3 * base;
+    jr.n_items = m->n_active;
+    jr.out = d_val + base;
+    jr.scale = m->value_scale();
+    TRY(launch_eval(m, 2, prec, jr, s));
+    base += m->n_active;
+  }
+  for (int i = 0; i < n_models; ++i) {
+    uint32_t hst = 0;
+    TRY(read_status(const_cast<nvdb_model*>(models[i])->status, s, &hst));
+    TRY(status_to_error(hst));
+  }
+  return NVDB_OK;
+}
+
+// ============================================================================ query
+namespace {
+constexpr int64_t kQueryBatch = 1 << 20;
+
+nvdb_status build_query_cache(nvdb_model* m, cudaStream_t s) {
+  QueryCache& q = m->qc;
+  if (q.ready) return NVDB_OK;
+  const PatchSet* ps = m->patch_set(NVDB_FP32);
+  int prec = NVDB_FP32;
+  if (!ps && !m->patches.empty()) { ps = &m->patches[0]; prec = ps->prec; }
+  if (!ps) return fail(NVDB_ERR_UNSUPPORTED, "model has no patch set");
+  CU(cudaMemsetAsync(m->status, 0, 4, s));
+  TRY(decode_topology(m, ps, (nvdb_precision)prec, s));
+  TRY(dalloc(&q.l2_key, m->n_l2 + 1)); TRY(dalloc(&q.l2_pre, 512 * m->n_l2 + 1));
+  TRY(dalloc(&q.l1_pre, 128 * m->n_l1 + 1));
+  if (m->n_l2) {
+    l2_keys_kernel<<<blocks_for(m->n_l2, 128), 128, 0, s>>>(m->l2_origin, m->n_l2, q.l2_key);
+    word_prefix64_kernel<<<blocks_for(m->n_l2, 128), 128, 0, s>>>(reinterpret_cast<const uint64_t*>(m->l2_mask), 512,
+                                                                  m->n_l2, q.l2_pre);
+  }
+  if (m->n_l1) word_prefix_kernel<<<blocks_for(m->n_l1, 128), 128, 0, s>>>(m->ds.l1_words, 128, m->n_l1, q.l1_pre);
+  q.batch = kQueryBatch;
+  TRY(dalloc(&q.qmask, q.batch)); TRY(dalloc(&q.counts, q.batch)); TRY(dalloc(&q.off, q.batch + 1));
+  TRY(dalloc(&q.list, 3 * 8 * q.batch)); TRY(dalloc(&q.vals, 8 * q.batch));
+  TRY(m->scan.reserve(q.batch));
+  uint32_t hst = 0;
+  TRY(read_status(m->status, s, &hst));
+  TRY(status_to_error(hst));
+  q.ready = true;
+  return NVDB_OK;
+}
+
+TopoView topo_view(const nvdb_model* m) {
+  TopoView tv;
+  tv.n_l2 = m->n_l2;
+  tv.l2_key = m->qc.l2_key;
+  tv.l2_mask = reinterpret_cast<const uint64_t*>(m->l2_mask);
+  tv.l2_pre = m->qc.l2_pre;
+  tv.l2_base = m->ds.l2_off;
+  tv.l1_words = m->ds.l1_words;
+  tv.l1_pre = m->qc.l1_pre;
+  tv.l1_base = m->ds.l1_off;
+  tv.leaf_words = m->ds.leaf_words;
+  return tv;
+}
+}  // namespace
+
+extern "C" nvdb_status nvdb_query(const nvdb_model* cm, const float* d_xyz, int64_t n, nvdb_precision prec,
+                                  float* d_out, uint8_t* d_active, nvdb_stream stream) {
+  if (!cm || n < 0 || (n > 0 && (!d_xyz || !d_out))) return fail(NVDB_ERR_INVALID_ARG, "nvdb_query: bad arguments");
+  if (prec != NVDB_FP32 && prec != NVDB_BF16) return fail(NVDB_ERR_UNSUPPORTED, "precision %d", (int)prec);
+  nvdb_model* m = const_cast<nvdb_model*>(cm);
+  cudaStream_t s = (cudaStream_t)stream;
+  TRY(build_query_cache(m, s));
+  QueryCache& q = m->qc;
+  const TopoView tv = topo_view(m);
+  for (int64_t b0 = 0; b0 < n; b0 += q.batch) {
+    const int64_t nb = std::min(q.batch, n - b0);
+    const float* xyz = d_xyz + 3 * b0;
+    query_lookup_kernel<<<blocks_for(nb, 256), 256, 0, s>>>(tv, xyz, nb, q.qmask, q.counts,
+                                                             d_active ? d_active + b0 : nullptr);
+    TRY(m->scan.run(q.counts, nb, q.off, s));
+    query_emit_kernel<<<blocks_for(nb, 256), 256, 0, s>>>(xyz, nb, q.qmask, q.off, q.list);
+    EvalJob jr{};
+    jr.mode = MODE_LIST;
+    jr.ijk = q.list;
+    jr.n_items = 8 * nb;
+    jr.n_dev = m->scan.total;
+    jr.out = q.vals;
+    jr.scale = m->value_scale();
+    TRY(launch_eval(m, 2, prec, jr, s));
+    query_blend_kernel<<<blocks_for(nb, 256), 256, 0, s>>>(xyz, nb, q.qmask, q.off, q.vals, m->background, d_out + b0);
+    CU(cudaGetLastError());
+  }
+  return NVDB_OK;
+}
+
+// ============================================================================ network-level calls
+extern "C" nvdb_status nvdb_mlp_eval(const nvdb_model* m, int net, nvdb_precision prec, const int32_t* d_ijk,
+                                     int64_t n, float* d_out, nvdb_stream stream) {
+  if (!m || net < 0 || net > 2 || n < 0 || (n > 0 && (!d_ijk || !d_out))) return fail(NVDB_ERR_INVALID_ARG, "nvdb_mlp_eval: bad arguments");
+  EvalJob j{};
+  j.mode = MODE_LIST;
+  j.ijk = d_ijk;
+  j.n_items = n;
+  j.shift = net == 0 ? 3 : 0;
+  j.out = d_out;
+  j.scale = 1.f;
+  return launch_eval(m, net, prec, j, (cudaStream_t)stream);
+}
+
+extern "C" int64_t nvdb_net_param_count(const nvdb_model* m, int net) {
+  if (!m || net < 0 || net > 2) return -1;
+  return m->net[net].P;
+}
+
+extern "C" nvdb_status nvdb_mlp_grad(const nvdb_model* cm, int net, const int32_t* d_ijk, const float* d_target,
+                                     int64_t n, int loss_kind, float* d_grad, float* loss, nvdb_stream stream) {
+  if (!cm || net < 0 || net > 2 || n <= 0 || !d_ijk || !d_target || !d_grad)
+    return fail(NVDB_ERR_INVALID_ARG, "nvdb_mlp_grad: bad arguments");
+  if (loss_kind < 0 || loss_kind > 2) return fail(NVDB_ERR_INVALID_ARG, "unknown loss %d", loss_kind);
+  if (n > (1ll << 31)) return fail(NVDB_ERR_UNSUPPORTED, "nvdb_mlp_grad: n >= 2^31");
+  nvdb_model* m = const_cast<nvdb_model*>(cm);
+  cudaStream_t s = (cudaStream_t)stream;
+  const DevNet& d = m->net[net];
+  const int grid = (int)std::min<int64_t>((n + kTile - 1) / kTile, num_sms());
+  TRY(ensure_partial(m, (int64_t)grid * (d.P + 1)));
+  TrainJob j{};
+  j.net = net;
+  j.loss = loss_kind;
+  j.step = 1;
+  j.batch = n;
+  j.ijk_list = d_ijk;
+  j.target_list = d_target;
+  j.partial = m->partial;
+  TRY(launch_train(m, net, j, grid, s));
+  float* d_loss = nullptr;
+  TRY(dalloc(&d_loss, 1));
+  adam_reduce_kernel<<<blocks_for(d.P + 1, 256), 256, 0, s>>>(m->partial, grid, d.P, nullptr, nullptr, nullptr, 1, 0.f,
+                                                              d_grad, d_loss, 1.f / (float)n);
+  float h = 0.f;
+  cudaError_t e = cudaMemcpyAsync(&h, d_loss, 4, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  dfree(d_loss);
+  if (e != cudaSuccess) return fail(NVDB_ERR_CUDA, "nvdb_mlp_grad: %s", cudaGetErrorString(e));
+  if (loss) *loss = h;
+  return NVDB_OK;
+}
+
+// ============================================================================ info / export / import
+extern "C" nvdb_status nvdb_model_info(const nvdb_model* m, nvdb_info* out) {
+  if (!m || !out) return fail(NVDB_ERR_INVALID_ARG, "nvdb_model_info: NULL");
+  out->grid_class = m->grid_class;
+  out->background = m->background;
+  out->half_width = m->half_width;
+  for (int d = 0; d < 3; ++d) out->origin[d] = m->origin[d];
+  out->log2_extent = m->log2e;
+  out->n_active = m->n_active;
+  out->n_leaf = m->n_leaf;
+  out->n_l1 = m->n_l1;
+  out->n_l2 = m->n_l2;
+  return NVDB_OK;
+}
+
+namespace {
+struct BlobHeader {
+  char magic[8];
+  uint32_t version, grid_class;
+  float background, half_width;
+  int32_t origin[3], log2_extent, ffm_size[2], width[3], layers[3], n_patch_sets, reserved0;
+  int64_t n_l2, n_l1, n_leaf, n_active;
+  uint64_t reserved1[2];
+};
+static_assert(sizeof(BlobHeader) == 128, "blob header is 128 bytes");
+
+struct Writer {
+  std::vector<uint8_t> b;
+  void put(const void* p, size_t n) {
+    const uint8_t* c = static_cast<const uint8_t*>(p);
+    b.insert(b.end(), c, c + n);
+  }
+  void pad() { b.resize((b.size() + 7) & ~(size_t)7, 0); }
+};
+
+struct Reader {
+  const uint8_t* p;
+  size_t n, o = 0;
+  bool ok = true;
+  const void* take(size_t bytes) {
+    if (!ok || o + bytes > n) { ok = false; return nullptr; }
+    const void* r = p + o;
+    o += bytes;
+    return r;
+  }
+  void pad() { o = (o + 7) & ~(size_t)7; }
+};
+}  // namespace
+
+extern "C" nvdb_status nvdb_model_export(const nvdb_model* m, void* buf, size_t* bytes) {
+  if (!m || !bytes) return fail(NVDB_ERR_INVALID_ARG, "nvdb_model_export: NULL");
+  Writer w;
+  BlobHeader h{};
+  std::memcpy(h.magic, "NVDBMDL1", 8);
+  h.version = 1;
+  h.grid_class = (uint32_t)m->grid_class;
+  h.background = m->background;
+  h.half_width = m->half_width;
+  for (int d = 0; d < 3; ++d) h.origin[d] = m->origin[d];
+  h.log2_extent = m->log2e;
+  h.ffm_size[0] = m->ffm[0];
+  h.ffm_size[1] = m->ffm[1];
+  for (int k = 0; k < 3; ++k) { h.width[k] = m->width[k]; h.layers[k] = m->layers[k]; }
+  h.n_patch_sets = (int32_t)m->patches.size();
+  h.n_l2 = m->n_l2; h.n_l1 = m->n_l1; h.n_leaf = m->n_leaf; h.n_active = m->n_active;
+  w.put(&h, sizeof h);
+  for (int lev = 0; lev < 2; ++lev) { w.put(m->q_host[lev].data(), m->q_host[lev].size() * 4); w.pad(); }
+  CU(cudaDeviceSynchronize());
+  for (int k = 0; k < 3; ++k) {
+    std::vector<float> p(m->net[k].P);
+    CU(cudaMemcpy(p.data(), m->net[k].p32, p.size() * 4, cudaMemcpyDeviceToHost));
+    w.put(p.data(), p.size() * 4);
+    w.pad();
+  }
+  w.put(m->l2_origin_host.data(), m->l2_origin_host.size() * 4); w.pad();
+  w.put(m->l2_mask_host.data(), m->l2_mask_host.size() * 8); w.pad();
+  std::vector<const PatchSet*> sets;
+  for (auto& p : m->patches) sets.push_back(&p);
+  std::sort(sets.begin(), sets.end(), [](const PatchSet* a, const PatchSet* b) { return a->prec < b->prec; });
+  for (const PatchSet* p : sets) {
+    const int32_t hdr[2] = {p->prec, 0};
+    w.put(hdr, 8);
+    w.put(p->l1_off.data(), p->l1_off.size() * 4); w.pad();
+    w.put(p->l1_idx.data(), p->l1_idx.size() * 2); w.pad();
+    w.put(p->l0_off.data(), p->l0_off.size() * 4); w.pad();
+    w.put(p->l0_idx.data(), p->l0_idx.size() * 2); w.pad();
+  }
+  if (!buf) { *bytes = w.b.size(); return NVDB_OK; }
+  if (*bytes < w.b.size()) { *bytes = w.b.size(); return fail(NVDB_ERR_CAPACITY, "nvdb_model_export: buffer too small"); }
+  std::memcpy(buf, w.b.data(), w.b.size());
+  *bytes = w.b.size();
+  return NVDB_OK;
+}
+
+extern "C" nvdb_status nvdb_model_import(const void* buf, size_t bytes, nvdb_stream stream, nvdb_model** out) {
+  if (!buf || !out) return fail(NVDB_ERR_INVALID_ARG, "nvdb_model_import: NULL");
+  *out = nullptr;
+  cudaStream_t s = (cudaStream_t)stream;
+  Reader r{static_cast<const uint8_t*>(buf), bytes};
+  const BlobHeader* h = static_cast<const BlobHeader*>(r.take(sizeof(BlobHeader)));
+  if (!h || std::memcmp(h->magic, "NVDBMDL1", 8) != 0 || h->version != 1) return fail(NVDB_ERR_CORRUPT, "not an NVDBMDL1 blob");
+  if (h->n_l2 < 0 || h->n_l1 < 0 || h->n_leaf < 0 || h->n_active < 0 || h->n_patch_sets < 0 || h->n_patch_sets > 3 ||
+      h->grid_class > 1 || h->log2_extent < 0 || h->log2_extent > 21)
+    return fail(NVDB_ERR_CORRUPT, "bad blob header");
+  auto* m = new nvdb_model();
+  auto run = [&]() -> nvdb_status {
+    m->grid_class = (int)h->grid_class;
+    m->background = h->background;
+    m->half_width = h->half_width;
+    for (int d = 0; d < 3; ++d) m->origin[d] = h->origin[d];
+    m->log2e = h->log2_extent;
+    m->ffm[0] = h->ffm_size[0];
+    m->ffm[1] = h->ffm_size[1];
+    for (int k = 0; k < 3; ++k) { m->width[k] = h->width[k]; m->layers[k] = h->layers[k]; }
+    m->n_l2 = h->n_l2; m->n_l1 = h->n_l1; m->n_leaf = h->n_leaf; m->n_active = h->n_active;
+    TRY(check_model_shapes(m));
+    TRY(dalloc(&m->status, 1));
+    CU(cudaMemsetAsync(m->status, 0, 4, s));
+    for (int lev = 0; lev < 2; ++lev) {
+      const size_t cnt = (size_t)(m->ffm[lev] / 2) * 3;
+      const uint32_t* q = static_cast<const uint32_t*>(r.take(cnt * 4));
+      r.pad();
+      if (!q) return fail(NVDB_ERR_CORRUPT, "blob truncated (Fourier matrix)");
+      m->q_host[lev].assign(q, q + cnt);
+      TRY(dalloc(&m->q_dev[lev], cnt));
+      CU(cudaMemcpy(m->q_dev[lev], q, cnt * 4, cudaMemcpyHostToDevice));
+    }
+    for (int k = 0; k < 3; ++k) {
+      const int64_t P = net_param_count(k == 0 ? m->ffm[0] : m->ffm[1], m->width[k], m->layers[k]);
+      const float* p = static_cast<const float*>(r.take((size_t)P * 4));
+      r.pad();
+      if (!p) return fail(NVDB_ERR_CORRUPT, "blob truncated (network %d)", k);
+      std::vector<float> tmp(p, p + P);
+      TRY(upload_net(m, k, tmp.data(), s));
+      CU(cudaStreamSynchronize(s));
+      TRY(pack_net(m, k, s));
+    }
+    const int32_t* l2o = static_cast<const int32_t*>(r.take((size_t)m->n_l2 * 12));
+    r.pad();
+    const uint64_t* l2m = static_cast<const uint64_t*>(r.take((size_t)m->n_l2 * 4096));
+    r.pad();
+    if (!r.ok) return fail(NVDB_ERR_CORRUPT, "blob truncated (upper tree)");
+    m->l2_origin_host.assign(l2o, l2o + 3 * m->n_l2);
+    m->l2_mask_host.assign(l2m, l2m + 512 * m->n_l2);
+    std::vector<int4> o4(m->n_l2);
+    for (int64_t i = 0; i < m->n_l2; ++i) o4[i] = make_int4(l2o[3 * i], l2o[3 * i + 1], l2o[3 * i + 2], 0);
+    TRY(dalloc(&m->l2_origin, m->n_l2));
+    TRY(dalloc(&m->l2_mask, 512 * m->n_l2));
+    if (m->n_l2) {
+      CU(cudaMemcpy(m->l2_origin, o4.data(), m->n_l2 * sizeof(int4), cudaMemcpyHostToDevice));
+      CU(cudaMemcpy(m->l2_mask, l2m, m->n_l2 * 4096, cudaMemcpyHostToDevice));
+    }
+    for (int i = 0; i < h->n_patch_sets; ++i) {
+      const int32_t* ph = static_cast<const int32_t*>(r.take(8));
+      if (!ph) return fail(NVDB_ERR_CORRUPT, "blob truncated (patch header)");
+      PatchSet ps;
+      ps.prec = ph[0];
+      const uint32_t* o1 = static_cast<const uint32_t*>(r.take((size_t)(m->n_l1 + 1) * 4));
+      r.pad();
+      if (!o1) return fail(NVDB_ERR_CORRUPT, "blob truncated (patches)");
+      ps.l1_off.assign(o1, o1 + m->n_l1 + 1);
+      const uint16_t* i1 = static_cast<const uint16_t*>(r.take((size_t)ps.l1_off.back() * 2));
+      r.pad();
+      if (!i1 && ps.l1_off.back()) return fail(NVDB_ERR_CORRUPT, "blob truncated (patches)");
+      if (i1) ps.l1_idx.assign(i1, i1 + ps.l1_off.back());
+      const uint32_t* o0 = static_cast<const uint32_t*>(r.take((size_t)(m->n_leaf + 1) * 4));
+      r.pad();
+      if (!o0) return fail(NVDB_ERR_CORRUPT, "blob truncated (patches)");
+      ps.l0_off.assign(o0, o0 + m->n_leaf + 1);
+      const uint16_t* i0 = static_cast<const uint16_t*>(r.take((size_t)ps.l0_off.back() * 2));
+      r.pad();
+      if (!i0 && ps.l0_off.back()) return fail(NVDB_ERR_CORRUPT, "blob truncated (patches)");
+      if (i0) ps.l0_idx.assign(i0, i0 + ps.l0_off.back());
+      for (size_t a = 0; a + 1 < ps.l1_off.size(); ++a)
+        if (ps.l1_off[a] > ps.l1_off[a + 1]) return fail(NVDB_ERR_CORRUPT, "patch offsets not monotone");
+      for (size_t a = 0; a + 1 < ps.l0_off.size(); ++a)
+        if (ps.l0_off[a] > ps.l0_off[a + 1]) return fail(NVDB_ERR_CORRUPT, "patch offsets not monotone");
+      for (uint16_t v : ps.l1_idx) if (v >= 4096) return fail(NVDB_ERR_CORRUPT, "level-1 patch index out of range");
+      for (uint16_t v : ps.l0_idx) if (v >= 512) return fail(NVDB_ERR_CORRUPT, "level-0 patch index out of range");
+      TRY(upload_patch_set(ps));
+      m->patches.push_back(ps);
+    }
+    CU(cudaStreamSynchronize(s));
+    return NVDB_OK;
+  };
+  const nvdb_status st = run();
+  if (st != NVDB_OK) { delete m; return st; }
+  *out = m;
+  return NVDB_OK;
+}
+
+extern "C" nvdb_status nvdb_model_free(nvdb_model* m) {
+  delete m;
+  return NVDB_OK;
+}
+
+extern "C" const char* nvdb_last_error(void) { return g_err.c_str(); }

@@ -1,0 +1,255 @@
+// Sparse-field training (Section 3.2, Section 3.2.1): Philox-sampled batches,
+// encode + forward with saved activations, hand-written backward of the mean
+// BCE / MSE / L1 loss, deterministic per-CTA gradient partials, then a
+// fixed-order reduction fused with the Adam update (Kingma & Ba; beta1 0.9,
+// beta2 0.999, eps 1e-8, bias correction, exponentially decayed rate).
+//
+// FP32 on CUDA cores; one thread per sample row, 128 rows per tile.
+// Shared memory holds the activations H_0..H_L and the backward deltas of the
+// tile ([128][K+1] FP32 each, padded against bank conflicts); weights are read
+// through L1 (broadcast loads).
+#pragma once
+#include "common.cuh"
+#include "mlp.cuh"
+
+namespace nvdb {
+
+struct TrainJob {
+  int net;                    // 0 level-1 classifier, 1 level-0 classifier, 2 regressor
+  int loss;                   // LOSS_*
+  int step;                   // Adam step (1-based), keys the sample stream
+  uint64_t seed;
+  int64_t batch;              // samples per step
+  int ox, oy, oz;             // encoding domain origin
+  // explicit list (nvdb_mlp_grad) when ijk_list != nullptr
+  const int32_t* ijk_list;
+  const float* target_list;
+  // population from the explicit grid
+  const int4* l1_origin; const unsigned long long* l1_mask; int64_t n_l1;
+  const int4* leaf_origin; const unsigned long long* leaf_mask; int64_t n_leaf;
+  const int32_t* ijk; const float* val; int64_t n;
+  float tscale;               // regressor target = val * tscale
+  float* partial;             // [gridDim.x][P + 1]: gradient partials, then the loss sum
+};
+
+enum : int { LOSS_MSE = 0, LOSS_L1 = 1, LOSS_BCE = 2 };
+
+__device__ __forceinline__ int64_t train_population(const TrainJob& j) {
+  return j.net == 0 ? j.n_l1 * 4096 : j.net == 1 ? j.n_leaf * 512 : j.n;
+}
+
+// Coordinates (level units) and target of sample s.
+__device__ __forceinline__ void train_sample(const TrainJob& j, int64_t s, int& cx, int& cy, int& cz, float& tgt) {
+  if (j.ijk_list) {
+    const int sh = j.net == 0 ? 3 : 0;
+    cx = (j.ijk_list[3 * s] - j.ox) >> sh;
+    cy = (j.ijk_list[3 * s + 1] - j.oy) >> sh;
+    cz = (j.ijk_list[3 * s + 2] - j.oz) >> sh;
+    tgt = j.target_list[s];
+    return;
+  }
+  const uint64_t idx = sample_index(j.seed, j.net, j.step, (uint32_t)s, (uint64_t)train_population(j));
+  if (j.net == 0) {
+    const int64_t node = (int64_t)(idx >> 12);
+    const int slot = (int)(idx & 4095);
+    const int4 o = j.l1_origin[node];
+    cx = ((o.x - j.ox) >> 3) + (slot >> 8);
+    cy = ((o.y - j.oy) >> 3) + ((slot >> 4) & 15);
+    cz = ((o.z - j.oz) >> 3) + (slot & 15);
+    tgt = (float)((j.l1_mask[node * 64 + (slot >> 6)] >> (slot & 63)) & 1ull);
+  } else if (j.net == 1) {
+    const int64_t leaf = (int64_t)(idx >> 9);
+    const int off = (int)(idx & 511);
+    const int4 o = j.leaf_origin[leaf];
+    cx = (o.x - j.ox) + (off >> 6);
+    cy = (o.y - j.oy) + ((off >> 3) & 7);
+    cz = (o.z - j.oz) + (off & 7);
+    tgt = (float)((j.leaf_mask[leaf * 8 + (off >> 6)] >> (off & 63)) & 1ull);
+  } else {
+    cx = j.ijk[3 * idx] - j.ox;
+    cy = j.ijk[3 * idx + 1] - j.oy;
+    cz = j.ijk[3 * idx + 2] - j.oz;
+    tgt = j.val[idx] * j.tscale;
+  }
+}
+
+// Per-row loss and dL/dy of the batch mean.
+__device__ __forceinline__ void row_loss(int kind, float y, float t, float inv_b, float& l, float& g) {
+  if (kind == LOSS_BCE) {
+    l = fmaxf(y, 0.f) - y * t + log1pf(expf(-fabsf(y)));
+    g = (1.f / (1.f + expf(-y)) - t) * inv_b;
+  } else if (kind == LOSS_MSE) {
+    const float d = y - t;
+    l = d * d;
+    g = 2.f * d * inv_b;
+  } else {
+    const float d = y - t;
+    l = fabsf(d);
+    g = (d > 0.f ? 1.f : d < 0.f ? -1.f : 0.f) * inv_b;
+  }
+}
+
+template <int NIN, int W>
+struct TrainSmem {
+  static constexpr int KP = NIN + 1, WP = W + 1;
+  __host__ __device__ static size_t bytes(int L) {
+    return ((size_t)kTile * KP + (size_t)(L + 1) * kTile * WP + kTile + 3 * (NIN / 2) + 64) * 4;
+  }
+};
+
+// dW[o][i] += sum_r D[r][o] H[r][i] for a [W x K] layer; thread t owns column
+// i = t % K and the OPT output rows starting at (t / K) * OPT.
+template <int K, int W>
+__device__ __forceinline__ void accum_dW(const float* D, int dstride, const float* H, int hstride, float* gW) {
+  constexpr int OB = kTile / K, OPT = W / OB;
+  const int i = threadIdx.x % K, o0 = (threadIdx.x / K) * OPT;
+  float acc[OPT];
+#pragma unroll
+  for (int k = 0; k < OPT; ++k) acc[k] = 0.f;
+  for (int r = 0; r < kTile; ++r) {
+    const float h = H[r * hstride + i];
+#pragma unroll
+    for (int k = 0; k < OPT; ++k) acc[k] = fmaf(D[r * dstride + o0 + k], h, acc[k]);
+  }
+#pragma unroll
+  for (int k = 0; k < OPT; ++k) gW[(o0 + k) * K + i] += acc[k];
+}
+
+template <int NIN, int W>
+__global__ void __launch_bounds__(kTile, 1) train_fwd_bwd_kernel(NetView net, TrainJob job) {
+  extern __shared__ float4 smem_t4[];
+  constexpr int M = NIN / 2, KP = NIN + 1, WP = W + 1;
+  const int L = net.layers;
+  float* H0 = reinterpret_cast<float*>(smem_t4);            // [128][NIN+1] encoding
+  float* Hl = H0 + kTile * KP;                               // H_1..H_L, then delta: [L+1][128][W+1]
+  float* Dl = Hl + (size_t)L * kTile * WP;
+  float* gsh = Dl + kTile * WP;                              // dL/dy per row
+  uint32_t* sq = reinterpret_cast<uint32_t*>(gsh + kTile);
+  float* red = reinterpret_cast<float*>(sq + 3 * M);         // 32 floats for the loss reduction
+  const int r = threadIdx.x;
+  for (int i = r; i < 3 * M; i += kTile) sq[i] = net.q[i];
+  __syncthreads();
+  const float* p = net.p32;
+  const int64_t P = net_param_count(NIN, W, L);
+  float* gpart = job.partial + (int64_t)blockIdx.x * (P + 1);
+  for (int64_t e = r; e <= P; e += kTile) gpart[e] = 0.f;
+  __syncthreads();
+  const float inv_b = 1.f / (float)job.batch;
+  float loss_acc = 0.f;
+  const int64_t ntiles = (job.batch + kTile - 1) / kTile;
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int64_t s = t * kTile + r;
+    const bool valid = s < job.batch;
+    int cx = 0, cy = 0, cz = 0;
+    float tgt = 0.f;
+    if (valid) train_sample(job, s, cx, cy, cz, tgt);
+    // ---- forward, saving activations
+    float h[NIN > W ? NIN : W], a[W];
+    encode_f32<NIN>(sq, cx, cy, cz, h);
+#pragma unroll
+    for (int i = 0; i < NIN; ++i) H0[r * KP + i] = h[i];
+    const float* pl = p;
+    for (int l = 0; l < L; ++l) {
+      if (l == 0) dense_f32<NIN, W>(pl, h, a); else dense_f32<W, W>(pl, h, a);
+      pl += (l == 0 ? W * NIN : W * W) + W;
+      float* Hs = Hl + (size_t)l * kTile * WP + r * WP;
+#pragma unroll
+      for (int o = 0; o < W; ++o) { h[o] = fmaxf(a[o], 0.f); Hs[o] = h[o]; }
+    }
+    const float* wh = pl;
+    float y = wh[W];
+#pragma unroll
+    for (int i = 0; i < W; ++i) y = fmaf(wh[i], h[i], y);
+    float lr_, g;
+    row_loss(job.loss, y, tgt, inv_b, lr_, g);
+    if (!valid) { lr_ = 0.f; g = 0.f; }
+    loss_acc += lr_;
+    gsh[r] = g;
+    // delta_L = g * w_h * [h_L > 0]
+#pragma unroll
+    for (int o = 0; o < W; ++o) Dl[r * WP + o] = h[o] > 0.f ? g * wh[o] : 0.f;
+    __syncthreads();
+    // ---- head gradients
+    {
+      const float* HL = Hl + (size_t)(L - 1) * kTile * WP;
+      float* gwh = gpart + (P - W - 1);
+      if (r < W) {
+        float acc = 0.f;
+        for (int rr = 0; rr < kTile; ++rr) acc = fmaf(gsh[rr], HL[rr * WP + r], acc);
+        gwh[r] += acc;
+      } else if (r == W) {
+        float acc = 0.f;
+        for (int rr = 0; rr < kTile; ++rr) acc += gsh[rr];
+        gwh[W] += acc;
+      }
+    }
+    // ---- hidden layers, top down
+    for (int l = L - 1; l >= 0; --l) {
+      const int64_t woff = l == 0 ? 0 : (int64_t)W * NIN + W + (int64_t)(l - 1) * (W * W + W);
+      const int K = l == 0 ? NIN : W;
+      const float* Hin = l == 0 ? H0 : Hl + (size_t)(l - 1) * kTile * WP;
+      const int hs = l == 0 ? KP : WP;
+      if (l == 0) accum_dW<NIN, W>(Dl, WP, Hin, hs, gpart + woff);
+      else accum_dW<W, W>(Dl, WP, Hin, hs, gpart + woff);
+      if (r < W) {
+        float acc = 0.f;
+        for (int rr = 0; rr < kTile; ++rr) acc += Dl[rr * WP + r];
+        gpart[woff + (int64_t)W * K + r] += acc;
+      }
+      __syncthreads();
+      if (l > 0) {
+        // delta_l = (W_l^T delta_{l+1}) * [h_l > 0], own row only
+        float d[W];
+#pragma unroll
+        for (int o = 0; o < W; ++o) d[o] = Dl[r * WP + o];
+        const float* Wl = p + woff;
+        const float* Hr = Hin + r * hs;
+#pragma unroll 4
+        for (int i = 0; i < W; ++i) {
+          float acc = 0.f;
+#pragma unroll
+          for (int o = 0; o < W; ++o) acc = fmaf(__ldg(Wl + o * W + i), d[o], acc);
+          Dl[r * WP + i] = Hr[i] > 0.f ? acc : 0.f;
+        }
+        __syncthreads();
+      }
+    }
+  }
+  // deterministic loss sum of this CTA
+  float v = loss_acc;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((r & 31) == 0) red[r >> 5] = v;
+  __syncthreads();
+  if (r == 0) {
+    float s = 0.f;
+    for (int w = 0; w < kTile / 32; ++w) s += red[w];
+    gpart[P] = s;
+  }
+}
+
+// Sum the per-CTA partials in CTA order; then Adam (or just write the gradient).
+__global__ void adam_reduce_kernel(const float* partial, int nparts, int64_t P, float* params, float* m, float* v,
+                                   int step, float lr_t, float* grad_out, float* loss_out, float loss_scale) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e > P) return;
+  float g = 0.f;
+  for (int c = 0; c < nparts; ++c) g += partial[(int64_t)c * (P + 1) + e];
+  if (e == P) {
+    if (loss_out) *loss_out = g * loss_scale;
+    return;
+  }
+  if (grad_out) grad_out[e] = g;
+  if (params) {
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float mm = b1 * m[e] + (1.f - b1) * g;
+    const float vv = b2 * v[e] + (1.f - b2) * g * g;
+    m[e] = mm;
+    v[e] = vv;
+    const float mhat = mm / (1.f - powf(b1, (float)step));
+    const float vhat = vv / (1.f - powf(b2, (float)step));
+    params[e] -= lr_t * mhat / (sqrtf(vhat) + 1e-8f);
+  }
+}
+
+}  // namespace nvdb
