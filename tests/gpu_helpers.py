@@ -1,0 +1,27 @@
+"""Shared helpers of the GPU parity tests (no GPU work at import time)."""
+import numpy as np
+
+from oracle import codec
+from oracle import nets as N
+
+
+def oracle_forward_scale(model: dict, net: int, ijk: np.ndarray):
+    """Oracle output and the dot-product error scale sum_i |w_h,i h_i| + |b_h| of the head."""
+    z = N.encode(codec.level_coords(model, net, ijk), codec.level_q(model, net))
+    y, (hs, _) = N.forward(model["nets"][net], z)
+    scale = np.abs(hs[-1] * model["nets"][net]["wh"][None]).sum(1) + abs(model["nets"][net]["bh"])
+    return y, scale
+
+
+def rel_err(gpu: np.ndarray, ref: np.ndarray, scale: np.ndarray) -> np.ndarray:
+    """|gpu - ref| / max(|ref|, scale): relative error normalised by the head's dot-product scale."""
+    return np.abs(np.asarray(gpu, np.float64) - ref) / np.maximum(np.abs(ref), np.maximum(scale, 1e-30))
+
+
+def randomise_biases(model: dict, seed: int, s: float = 0.1):
+    """Give every bias a random FP32-representable value so parity tests exercise them."""
+    r = np.random.default_rng(seed)
+    for net in model["nets"]:
+        net["b"] = [(r.standard_normal(b.shape) * s).astype(np.float32).astype(np.float64) for b in net["b"]]
+        net["bh"] = float(np.float32(r.standard_normal() * s))
+    return model

@@ -1,0 +1,30 @@
+"""The C-ABI library loads and exports every symbol include/nvdb.h declares (CPU only)."""
+import os
+import re
+
+from paper_2208_04448_b300 import _native as N
+
+HDR = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "nvdb.h")
+
+
+def _declared():
+    src = open(HDR).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(nvdb_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_header_and_binding_agree():
+    assert sorted(N.EXPORTS) == _declared()
+
+
+def test_library_exports_every_declared_symbol():
+    lib = N.load()
+    for name in _declared():
+        assert hasattr(lib, name), name
+
+
+def test_struct_layouts():
+    import ctypes as C
+    assert C.sizeof(N.TrainOpts) == 80
+    assert C.sizeof(N.Info) == 64 and N.Info.n_active.offset == 32
+    assert C.sizeof(N.BuildOpts) == 8
