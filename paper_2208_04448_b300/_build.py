@@ -1,6 +1,6 @@
 """Compile libnvdb.so in-tree for B300 (sm_103a) with nvcc.
 
-    python -m paper_2208_04448_b300.build [--force]
+    python -m paper_2208_04448_b300._build [--force]
 """
 from __future__ import annotations
 

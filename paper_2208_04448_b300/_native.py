@@ -58,7 +58,7 @@ EXPORTS = list(SIGNATURES)
 
 def load(path: str = LIB_PATH) -> C.CDLL:
     if not os.path.exists(path):
-        raise RuntimeError(f"libnvdb.so not built ({path}); run `python -m paper_2208_04448_b300.build`")
+        raise RuntimeError(f"libnvdb.so not built ({path}); run `python -m paper_2208_04448_b300._build`")
     lib = C.CDLL(path)
     for name, (args, res) in SIGNATURES.items():
         f = getattr(lib, name)
