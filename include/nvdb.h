@@ -58,8 +58,10 @@ typedef enum {
 /* Arithmetic of the hidden layers when evaluating networks. */
 typedef enum {
   NVDB_FP32 = 0,      /* plain FP32 on CUDA cores (FFMA), FP32 encoding */
-  NVDB_BF16 = 1,      /* BF16 operands on tcgen05 tensor cores, FP32 accumulate in TMEM */
-  NVDB_FP8_E4M3 = 2   /* FP8 E4M3 hidden layers on tcgen05 (reserved; returns UNSUPPORTED) */
+  NVDB_BF16 = 1,      /* tcgen05 tensor cores, BF16 operands: activations and weights carried as
+                         hi + lo BF16 pairs (three MMA terms), FP32 accumulate in TMEM */
+  NVDB_FP8_E4M3 = 2,  /* FP8 E4M3 hidden layers on tcgen05 (reserved; returns UNSUPPORTED) */
+  NVDB_FP16 = 3       /* tcgen05 tensor cores, FP16 operands (one MMA term), FP32 accumulate in TMEM */
 } nvdb_precision;
 
 /* Network indices (Section 3.3.1). */
@@ -88,7 +90,7 @@ typedef struct {
   int32_t lr_interval;  /* 0 = constant learning rate */
   int32_t loss;         /* regressor loss: NVDB_LOSS_MSE or NVDB_LOSS_L1 */
   int32_t train_prec;   /* arithmetic of training: NVDB_FP32 */
-  uint32_t patch_precs; /* bit p set = store patches for decoding at precision p (default: FP32|BF16) */
+  uint32_t patch_precs; /* bit p set = store patches for decoding at precision p (default: FP32|BF16|FP16) */
 } nvdb_train_opts;
 
 typedef struct {
@@ -122,7 +124,7 @@ nvdb_status nvdb_grid_free(nvdb_grid* grid);
 
 /* Fill opts with the defaults: widths 32, 3 layers, ffm_size 0, sigma 1.25,
  * 200 steps, batch 4096, lr 1e-3, decay 0.975 every 100 steps, MSE, FP32
- * training, patches for FP32 and BF16, seed 1. */
+ * training, patches for FP32, BF16 and FP16, seed 1. */
 void nvdb_train_opts_default(nvdb_train_opts* opts);
 
 /* Encode a grid (Sections 3.2-3.3): initialise the three networks (Xavier
@@ -197,6 +199,18 @@ nvdb_status nvdb_model_free(nvdb_model* model);
 
 /* Message of the last error of the calling thread ("" if none). */
 const char* nvdb_last_error(void);
+
+/* Tracing (a measurement aid; the paper reports wall-clock times only).
+ * With profiling on, the library records a CUDA event pair on the launching
+ * stream around each of its kernel launches.  nvdb_profile_read waits for
+ * the recorded events, aggregates them per kernel name and clears them:
+ * names (HOST, cap slots of name_len chars, NUL-terminated), launches[i],
+ * ms[i] (summed event time).  Returns the number of distinct names (may
+ * exceed cap).  nvdb_launch_count returns the number of kernel launches the
+ * library has issued since it was loaded (profiling on or off). */
+void nvdb_profile_enable(int on);
+int nvdb_profile_read(char* names, int name_len, int64_t* launches, double* ms, int cap);
+int64_t nvdb_launch_count(void);
 
 /*
  * Model blob "NVDBMDL1" (little-endian; every array starts at an 8-byte

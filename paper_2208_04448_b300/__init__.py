@@ -12,7 +12,7 @@ import ctypes as C
 import torch
 
 from . import _native as N
-from ._native import (BF16, FP32, FP8_E4M3, LOSS_BCE, LOSS_L1, LOSS_MSE, NET_L0_CLASSIFIER,  # noqa: F401
+from ._native import (BF16, FP16, FP32, FP8_E4M3, LOSS_BCE, LOSS_L1, LOSS_MSE, NET_L0_CLASSIFIER,  # noqa: F401
                       NET_L1_CLASSIFIER, NET_REGRESSOR)
 
 _lib = None
@@ -199,3 +199,25 @@ def model_import(blob: bytes, stream=None) -> Model:
     buf = C.create_string_buffer(blob, len(blob))
     _check(lib().nvdb_model_import(buf, len(blob), _stream(stream), C.byref(h)))
     return Model(h)
+
+
+def profile_enable(on: bool = True):
+    lib().nvdb_profile_enable(1 if on else 0)
+
+
+def profile_read() -> dict:
+    """{kernel name: (launches, total ms)} of the launches recorded since the last read."""
+    cap, nl = 64, 64
+    names = C.create_string_buffer(cap * nl)
+    la = (C.c_int64 * cap)()
+    ms = (C.c_double * cap)()
+    n = lib().nvdb_profile_read(names, nl, la, ms, cap)
+    out = {}
+    for i in range(min(n, cap)):
+        nm = names.raw[i * nl:(i + 1) * nl].split(b"\0", 1)[0].decode()
+        out[nm] = (int(la[i]), float(ms[i]))
+    return out
+
+
+def launch_count() -> int:
+    return int(lib().nvdb_launch_count())

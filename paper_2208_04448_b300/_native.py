@@ -9,7 +9,7 @@ LIB_PATH = os.path.join(HERE, "libnvdb.so")
 
 OK, ERR_INVALID_ARG, ERR_DUPLICATE_VOXEL, ERR_OUT_OF_MEMORY, ERR_CAPACITY, ERR_CUDA, ERR_TIMEOUT, \
     ERR_UNSUPPORTED, ERR_CORRUPT = range(9)
-FP32, BF16, FP8_E4M3 = 0, 1, 2
+FP32, BF16, FP8_E4M3, FP16 = 0, 1, 2, 3
 NET_L1_CLASSIFIER, NET_L0_CLASSIFIER, NET_REGRESSOR = 0, 1, 2
 LOSS_MSE, LOSS_L1, LOSS_BCE = 0, 1, 2
 
@@ -52,6 +52,9 @@ SIGNATURES = {
     "nvdb_model_import": ([_vp, C.c_size_t, _vp, C.POINTER(_vp)], _st),
     "nvdb_model_free": ([_vp], _st),
     "nvdb_last_error": ([], C.c_char_p),
+    "nvdb_profile_enable": ([_i32], None),
+    "nvdb_profile_read": ([C.c_char_p, _i32, C.POINTER(C.c_int64), C.POINTER(C.c_double), _i32], _i32),
+    "nvdb_launch_count": ([], C.c_int64),
 }
 EXPORTS = list(SIGNATURES)
 

@@ -5,12 +5,15 @@
 //
 //  * mlp_f32_kernel : plain FP32 on CUDA cores, one thread per coordinate,
 //                     weights in shared memory, activations in registers.
-//  * mlp_tc_kernel  : BF16 tcgen05 tensor cores.  Weights resident in shared
-//                     memory (canonical no-swizzle K-major layout), the 128 x n
+//  * mlp_tc_kernel  : tcgen05 tensor cores (FP16 operands, or compensated
+//                     BF16 hi+lo pairs).  Weights resident in shared memory
+//                     (canonical no-swizzle K-major layout), the 128 x n
 //                     encoding tile written straight into the MMA A operand,
-//                     FP32 accumulators in TMEM, bias + ReLU + BF16 repack in
-//                     the epilogue; the head stays FP32 on CUDA cores.
+//                     FP32 accumulators in TMEM, bias + ReLU + repack in the
+//                     epilogue; the head stays FP32 on CUDA cores.
 #pragma once
+#include <cuda_fp16.h>
+
 #include "common.cuh"
 
 namespace nvdb {
@@ -18,7 +21,7 @@ namespace nvdb {
 struct NetView {
   int n_in, width, layers;
   const float* p32;              // flat FP32 parameters (W_0,b_0,...,W_{L-1},b_{L-1},w_h,b_h)
-  const __nv_bfloat16* wpk;      // BF16 weight tiles in canonical layout, layer after layer
+  const uint8_t* wpk;            // packed 16-bit weight tiles (see pack_weights_kernel)
   const uint32_t* q;             // Fourier matrix, [n_in/2][3]
 };
 
@@ -168,40 +171,78 @@ __global__ void __launch_bounds__(kTile) mlp_f32_kernel(NetView net, EvalJob job
   }
 }
 
-// ============================================================== BF16 tcgen05 path
+// ============================================================== tcgen05 tensor-core path
+// Two operand modes of kind::f16 (same tensor rate):
+//  TC_BF16X3: activations and weights carried as BF16 pairs v = hi + lo
+//             (hi = bf16(v), lo = bf16(v - hi)); D = A_hi W_hi + A_lo W_hi + A_hi W_lo,
+//             three MMAs per K step, error ~2^-16 relative.
+//  TC_FP16  : FP16 activations and weights, one MMA per K step.
+enum TcMode : int { TC_BF16X3 = 0, TC_FP16 = 1 };
 
-// Features of row r written into the A tile (K = NIN): cos then sin, BF16.
-template <int NIN>
-__device__ __forceinline__ void encode_bf16_row(uint8_t* sa, int r, const uint32_t* sq, int cx, int cy, int cz) {
+template <int MODE>
+__device__ __forceinline__ void pack8(const float* v, uint4& hi, uint4& lo) {
+  uint32_t h[4], l[4];
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    if (MODE == TC_FP16) {
+      __half2 x = __floats2half2_rn(v[2 * e], v[2 * e + 1]);
+      h[e] = *reinterpret_cast<uint32_t*>(&x);
+      l[e] = 0u;
+    } else {
+      __nv_bfloat162 x = __floats2bfloat162_rn(v[2 * e], v[2 * e + 1]);
+      const float2 back = __bfloat1622float2(x);
+      __nv_bfloat162 y = __floats2bfloat162_rn(v[2 * e] - back.x, v[2 * e + 1] - back.y);
+      h[e] = *reinterpret_cast<uint32_t*>(&x);
+      l[e] = *reinterpret_cast<uint32_t*>(&y);
+    }
+  }
+  hi = make_uint4(h[0], h[1], h[2], h[3]);
+  lo = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
+// Features of row r written into the A tile(s) (K = NIN): cos then sin.
+template <int NIN, int MODE>
+__device__ __forceinline__ void encode_tc_row(uint8_t* sa, uint8_t* sa_lo, int r, const uint32_t* sq, int cx, int cy,
+                                              int cz) {
   constexpr int M = NIN / 2;
   float c[M], s[M];
 #pragma unroll
   for (int f = 0; f < M; ++f) {
     const uint32_t ph = ffm_phase(sq, f, cx, cy, cz);
-    __sincosf((float)(int32_t)ph * 1.4629180792671596e-09f, &s[f], &c[f]);   // pi / 2^31
+    if (MODE == TC_FP16)
+      __sincosf((float)(int32_t)ph * 1.4629180792671596e-09f, &s[f], &c[f]);   // pi / 2^31
+    else
+      sincospif((float)(int32_t)ph * 0x1p-31f, &s[f], &c[f]);
   }
 #pragma unroll
   for (int g = 0; g < M / 8; ++g) {
-    uint4 v = make_uint4(pack_bf16(c[8 * g], c[8 * g + 1]), pack_bf16(c[8 * g + 2], c[8 * g + 3]),
-                         pack_bf16(c[8 * g + 4], c[8 * g + 5]), pack_bf16(c[8 * g + 6], c[8 * g + 7]));
-    *reinterpret_cast<uint4*>(sa + canon_off(r, 8 * g, NIN)) = v;
-    v = make_uint4(pack_bf16(s[8 * g], s[8 * g + 1]), pack_bf16(s[8 * g + 2], s[8 * g + 3]),
-                   pack_bf16(s[8 * g + 4], s[8 * g + 5]), pack_bf16(s[8 * g + 6], s[8 * g + 7]));
-    *reinterpret_cast<uint4*>(sa + canon_off(r, M + 8 * g, NIN)) = v;
+    uint4 hi, lo;
+    pack8<MODE>(c + 8 * g, hi, lo);
+    *reinterpret_cast<uint4*>(sa + canon_off(r, 8 * g, NIN)) = hi;
+    if (MODE == TC_BF16X3) *reinterpret_cast<uint4*>(sa_lo + canon_off(r, 8 * g, NIN)) = lo;
+    pack8<MODE>(s + 8 * g, hi, lo);
+    *reinterpret_cast<uint4*>(sa + canon_off(r, M + 8 * g, NIN)) = hi;
+    if (MODE == TC_BF16X3) *reinterpret_cast<uint4*>(sa_lo + canon_off(r, M + 8 * g, NIN)) = lo;
   }
 }
 
 constexpr uint32_t kTmemCols = 64;          // FP32 accumulator columns (width <= 64)
 constexpr size_t kTcMinSmem = 33 * 1024;    // caps residency at 6 CTAs/SM -> 6 x 64 <= 512 TMEM columns
 
-template <int NIN, int W>
+// Packed weight tiles per network: [FP16 tiles][BF16 hi tiles][BF16 lo tiles],
+// each set = layer 0 [W x n_in] then layers 1..L-1 [W x W], canonical layout.
+__host__ __device__ inline int64_t wtile_elems(int nin, int w, int L) { return (int64_t)w * nin + (int64_t)(L - 1) * w * w; }
+
+template <int NIN, int W, int MODE>
 struct TcLayout {
   static constexpr int KA = NIN > W ? NIN : W;
-  size_t w_bytes, a_off, b_off, wh_off, q_off, bar_off, slot_off, total;
+  static constexpr int NCOPY = MODE == TC_BF16X3 ? 2 : 1;
+  size_t w_bytes, a_off, alo_off, b_off, wh_off, q_off, bar_off, slot_off, total;
   __host__ __device__ TcLayout(int L) {
-    w_bytes = (size_t)(W * NIN + (L - 1) * W * W) * 2;
-    a_off = (w_bytes + 127) & ~(size_t)127;
-    b_off = a_off + (size_t)kTile * KA * 2;
+    w_bytes = (size_t)wtile_elems(NIN, W, L) * 2;              // one copy
+    a_off = ((NCOPY * w_bytes) + 127) & ~(size_t)127;
+    alo_off = a_off + (size_t)kTile * KA * 2;
+    b_off = a_off + (size_t)NCOPY * kTile * KA * 2;
     wh_off = b_off + (size_t)L * W * 4;
     q_off = wh_off + (size_t)(W + 4) * 4;
     bar_off = (q_off + (size_t)(NIN / 2) * 12 + 7) & ~(size_t)7;
@@ -211,15 +252,17 @@ struct TcLayout {
   }
 };
 
-template <int NIN, int W>
+template <int NIN, int W, int MODE>
 __global__ void __launch_bounds__(kTile, 1) mlp_tc_kernel(NetView net, EvalJob job) {
   static_assert(W == 32 || W == 64, "width");
   static_assert(NIN == 32 || NIN == 64, "encoding size");
   extern __shared__ __align__(1024) uint8_t smem[];
   const int L = net.layers;
-  const TcLayout<NIN, W> lay(L);
-  uint8_t* sw = smem;
+  const TcLayout<NIN, W, MODE> lay(L);
+  uint8_t* sw = smem;                              // hi (or FP16) weights
+  uint8_t* sw_lo = smem + lay.w_bytes;             // lo weights (BF16X3)
   uint8_t* sa = smem + lay.a_off;
+  uint8_t* sa_lo = smem + lay.alo_off;
   float* sb = reinterpret_cast<float*>(smem + lay.b_off);
   float* swh = reinterpret_cast<float*>(smem + lay.wh_off);
   uint32_t* sq = reinterpret_cast<uint32_t*>(smem + lay.q_off);
@@ -227,11 +270,14 @@ __global__ void __launch_bounds__(kTile, 1) mlp_tc_kernel(NetView net, EvalJob j
   uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + lay.slot_off);
   const int tid = threadIdx.x, warp = tid >> 5;
 
-  // stage weights (already BF16 canonical tiles), biases, head, Fourier matrix
+  // stage weight tiles, biases, head and Fourier matrix
   {
-    const uint4* src = reinterpret_cast<const uint4*>(net.wpk);
+    const int64_t te = wtile_elems(NIN, W, L);
+    const uint8_t* base = reinterpret_cast<const uint8_t*>(net.wpk) + (MODE == TC_FP16 ? 0 : te * 2);
+    const uint4* src = reinterpret_cast<const uint4*>(base);
     uint4* dst = reinterpret_cast<uint4*>(sw);
-    for (size_t i = tid; i < lay.w_bytes / 16; i += kTile) dst[i] = __ldg(src + i);
+    const size_t n16 = lay.NCOPY * lay.w_bytes / 16;
+    for (size_t i = tid; i < n16; i += kTile) dst[i] = __ldg(src + i);
     for (int l = 0; l < L; ++l) {
       const int64_t off = l == 0 ? (int64_t)W * NIN : (int64_t)W * NIN + W + (int64_t)(l - 1) * (W * W + W) + W * W;
       for (int o = tid; o < W; o += kTile) sb[l * W + o] = __ldg(net.p32 + off + o);
@@ -249,6 +295,7 @@ __global__ void __launch_bounds__(kTile, 1) mlp_tc_kernel(NetView net, EvalJob j
   const uint32_t tbase = *tslot;
   const uint32_t tlane = tbase + ((uint32_t)(warp * 32) << 16);
   const float bh = swh[W];
+  const uint32_t idesc = MODE == TC_FP16 ? idesc_f16_f32(kTile, W) : idesc_bf16_f32(kTile, W);
 
   uint32_t phase = 0;
   bool failed = false;
@@ -257,7 +304,7 @@ __global__ void __launch_bounds__(kTile, 1) mlp_tc_kernel(NetView net, EvalJob j
   for (int64_t t = blockIdx.x; t < ntiles && !failed; t += gridDim.x) {
     int cx, cy, cz;
     const bool valid = job_coord(job, t, tid, cx, cy, cz);
-    encode_bf16_row<NIN>(sa, tid, sq, cx, cy, cz);
+    encode_tc_row<NIN, MODE>(sa, sa_lo, tid, sq, cx, cy, cz);
     fence_proxy_async_smem();
     __syncthreads();
     float y = 0.f;
@@ -265,12 +312,17 @@ __global__ void __launch_bounds__(kTile, 1) mlp_tc_kernel(NetView net, EvalJob j
       const int K = l == 0 ? NIN : W;
       if (tid == 0) {
         tc_fence_after();
-        const uint32_t a0 = smem_u32(sa);
-        const uint32_t b0 = smem_u32(sw) + (l == 0 ? 0u : (uint32_t)(W * NIN + (l - 1) * W * W) * 2u);
-        const uint32_t idesc = idesc_bf16_f32(kTile, W);
-        for (int ks = 0; ks < K / 16; ++ks)
-          mma_bf16(tbase, smem_desc(a0 + ks * 256, 128, K * 16), smem_desc(b0 + ks * 256, 128, K * 16), idesc,
-                   ks > 0 ? 1u : 0u);
+        const uint32_t woff = l == 0 ? 0u : (uint32_t)(W * NIN + (l - 1) * W * W) * 2u;
+        const uint32_t a0 = smem_u32(sa), b0 = smem_u32(sw) + woff;
+        for (int ks = 0; ks < K / 16; ++ks) {
+          mma_f16kind(tbase, smem_desc(a0 + ks * 256, 128, K * 16), smem_desc(b0 + ks * 256, 128, K * 16), idesc,
+                      ks > 0 ? 1u : 0u);
+          if (MODE == TC_BF16X3) {
+            const uint32_t al = smem_u32(sa_lo), bl = smem_u32(sw_lo) + woff;
+            mma_f16kind(tbase, smem_desc(al + ks * 256, 128, K * 16), smem_desc(b0 + ks * 256, 128, K * 16), idesc, 1u);
+            mma_f16kind(tbase, smem_desc(a0 + ks * 256, 128, K * 16), smem_desc(bl + ks * 256, 128, K * 16), idesc, 1u);
+          }
+        }
         mma_commit(bar);
       }
       const bool ok = mbar_wait_bounded(bar, phase);
@@ -287,8 +339,10 @@ __global__ void __launch_bounds__(kTile, 1) mlp_tc_kernel(NetView net, EvalJob j
           float v[8];
 #pragma unroll
           for (int e = 0; e < 8; ++e) v[e] = fmaxf(acc[8 * g + e] + b[8 * g + e], 0.f);
-          *reinterpret_cast<uint4*>(sa + canon_off(tid, 8 * g, W)) =
-              make_uint4(pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]), pack_bf16(v[4], v[5]), pack_bf16(v[6], v[7]));
+          uint4 hi, lo;
+          pack8<MODE>(v, hi, lo);
+          *reinterpret_cast<uint4*>(sa + canon_off(tid, 8 * g, W)) = hi;
+          if (MODE == TC_BF16X3) *reinterpret_cast<uint4*>(sa_lo + canon_off(tid, 8 * g, W)) = lo;
         }
       } else {
         y = bh;
@@ -309,12 +363,11 @@ __global__ void __launch_bounds__(kTile, 1) mlp_tc_kernel(NetView net, EvalJob j
   if (warp == 0) tmem_dealloc(tbase, kTmemCols);
 }
 
-// FP32 master weights -> BF16 tiles in the canonical K-major layout
-// (layer 0: [W x n_in], layers 1..L-1: [W x W]).
-__global__ void pack_weights_kernel(const float* p32, __nv_bfloat16* wpk, int nin, int W, int L) {
+// FP32 master weights -> FP16 tiles, BF16 hi tiles and BF16 lo tiles in the
+// canonical K-major layout (layer 0: [W x n_in], layers 1..L-1: [W x W]).
+__global__ void pack_weights_kernel(const float* p32, uint8_t* wpk, int nin, int W, int L) {
   const int64_t first = (int64_t)W * nin;
-  const int64_t total = first + (int64_t)(L - 1) * W * W;
-  uint8_t* dst = reinterpret_cast<uint8_t*>(wpk);
+  const int64_t total = wtile_elems(nin, W, L);
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
     float v;
     size_t off;
@@ -330,7 +383,10 @@ __global__ void pack_weights_kernel(const float* p32, __nv_bfloat16* wpk, int ni
       v = p32[first + W + (int64_t)(l - 1) * (W * W + W) + rr];
       off = (size_t)first * 2 + (size_t)(l - 1) * W * W * 2 + canon_off(o, i, W);
     }
-    *reinterpret_cast<__nv_bfloat16*>(dst + off) = __float2bfloat16_rn(v);
+    const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+    *reinterpret_cast<__half*>(wpk + off) = __float2half_rn(v);
+    *reinterpret_cast<__nv_bfloat16*>(wpk + total * 2 + off) = hi;
+    *reinterpret_cast<__nv_bfloat16*>(wpk + total * 4 + off) = __float2bfloat16_rn(v - __bfloat162float(hi));
   }
 }
 

@@ -7,6 +7,9 @@
 #include <cub/cub.cuh>
 
 #include <algorithm>
+#include <atomic>
+#include <map>
+#include <mutex>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -79,6 +82,52 @@ int num_sms() {
 
 inline unsigned blocks_for(int64_t n, int per) { return (unsigned)((n + per - 1) / per); }
 
+// ============================================================================ tracing
+// Optional CUDA events around every kernel launch (on the launching stream)
+// and a running count of launches; read back with nvdb_profile_read.
+namespace prof {
+std::atomic<long long> g_launches{0};
+std::atomic<bool> g_on{false};
+struct Rec {
+  std::string name;
+  cudaEvent_t a, b;
+};
+std::mutex g_mu;
+std::vector<Rec> g_recs;
+struct Scope {
+  cudaEvent_t a = nullptr, b = nullptr;
+  const char* name;
+  cudaStream_t s;
+  Scope(const char* n, cudaStream_t st) : name(n), s(st) {
+    g_launches.fetch_add(1);
+    if (g_on.load() && cudaEventCreate(&a) == cudaSuccess) {
+      cudaEventCreate(&b);
+      cudaEventRecord(a, s);
+    }
+  }
+  ~Scope() {
+    if (!a) return;
+    cudaEventRecord(b, s);
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_recs.push_back({name, a, b});
+  }
+};
+}  // namespace prof
+
+#define KLAUNCH(name, stream, ...)        \
+  do {                                    \
+    prof::Scope prof_scope_(name, stream); \
+    __VA_ARGS__;                          \
+  } while (0)
+
+const char* eval_name(const char* base, int mode) {
+  static const char* names[3][3] = {{"mlp_f32.L1", "mlp_f32.L0", "mlp_f32.list"},
+                                    {"mlp_bf16x3.L1", "mlp_bf16x3.L0", "mlp_bf16x3.list"},
+                                    {"mlp_f16.L1", "mlp_f16.L0", "mlp_f16.list"}};
+  const int b = std::strcmp(base, "mlp_bf16x3") == 0 ? 1 : std::strcmp(base, "mlp_f16") == 0 ? 2 : 0;
+  return names[b][mode];
+}
+
 // ============================================================================ scan helper
 struct Scan {
   int64_t* sums = nullptr;
@@ -102,9 +151,9 @@ struct Scan {
       return NVDB_OK;
     }
     const int64_t nb = (n + kScanBlock - 1) / kScanBlock;
-    scan_blocks_kernel<<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, out, sums);
-    scan_sums_kernel<<<1, 1024, 0, s>>>(sums, nb, total);
-    scan_add_kernel<<<blocks_for(n, 256), 256, 0, s>>>(out, n, sums);
+    KLAUNCH("scan_blocks", s, scan_blocks_kernel<<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, out, sums));
+    KLAUNCH("scan_sums", s, scan_sums_kernel<<<1, 1024, 0, s>>>(sums, nb, total));
+    KLAUNCH("scan_add", s, scan_add_kernel<<<blocks_for(n, 256), 256, 0, s>>>(out, n, sums));
     CU(cudaGetLastError());
     return NVDB_OK;
   }
@@ -190,7 +239,7 @@ struct DevNet {
   int n_in = 0, width = 0, layers = 0;
   int64_t P = 0;
   float* p32 = nullptr;
-  __nv_bfloat16* wpk = nullptr;
+  uint8_t* wpk = nullptr;   // [FP16 | BF16 hi | BF16 lo] weight tiles
   float* m = nullptr;
   float* v = nullptr;
   ~DevNet() { dfree(p32); dfree(wpk); dfree(m); dfree(v); }
@@ -300,6 +349,19 @@ NetView net_view(const nvdb_model* m, int k) {
   return v;
 }
 
+template <int NIN, int W, int MODE>
+nvdb_status launch_tc(const NetView& nv, const EvalJob& job, int64_t ntiles, const char* base, cudaStream_t s) {
+  const TcLayout<NIN, W, MODE> lay(nv.layers);
+  int occ = 0;
+  CU(cudaFuncSetAttribute(mlp_tc_kernel<NIN, W, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lay.total));
+  CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, mlp_tc_kernel<NIN, W, MODE>, kTile, lay.total));
+  if (occ < 1) return fail(NVDB_ERR_UNSUPPORTED, "tensor-core kernel does not fit on an SM");
+  const int64_t grid = std::min<int64_t>(ntiles, (int64_t)num_sms() * occ);
+  KLAUNCH(eval_name(base, job.mode), s,
+          mlp_tc_kernel<NIN, W, MODE><<<(unsigned)grid, kTile, lay.total, s>>>(nv, job));
+  return NVDB_OK;
+}
+
 template <int NIN, int W>
 nvdb_status launch_eval_t(const NetView& nv, const EvalJob& job, nvdb_precision prec, cudaStream_t s) {
   const int64_t ntiles = job_tiles(job.mode, job.n_items);
@@ -310,14 +372,11 @@ nvdb_status launch_eval_t(const NetView& nv, const EvalJob& job, nvdb_precision 
     CU(cudaFuncSetAttribute(mlp_f32_kernel<NIN, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, mlp_f32_kernel<NIN, W>, kTile, smem));
     const int64_t grid = std::min<int64_t>(ntiles, (int64_t)num_sms() * std::max(occ, 1));
-    mlp_f32_kernel<NIN, W><<<(unsigned)grid, kTile, smem, s>>>(nv, job);
+    KLAUNCH(eval_name("mlp_f32", job.mode), s, mlp_f32_kernel<NIN, W><<<(unsigned)grid, kTile, smem, s>>>(nv, job));
   } else if (prec == NVDB_BF16) {
-    const TcLayout<NIN, W> lay(nv.layers);
-    CU(cudaFuncSetAttribute(mlp_tc_kernel<NIN, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lay.total));
-    CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, mlp_tc_kernel<NIN, W>, kTile, lay.total));
-    if (occ < 1) return fail(NVDB_ERR_UNSUPPORTED, "tensor-core kernel does not fit on an SM");
-    const int64_t grid = std::min<int64_t>(ntiles, (int64_t)num_sms() * occ);
-    mlp_tc_kernel<NIN, W><<<(unsigned)grid, kTile, lay.total, s>>>(nv, job);
+    TRY((launch_tc<NIN, W, TC_BF16X3>(nv, job, ntiles, "mlp_bf16x3", s)));
+  } else if (prec == NVDB_FP16) {
+    TRY((launch_tc<NIN, W, TC_FP16>(nv, job, ntiles, "mlp_f16", s)));
   } else {
     return fail(NVDB_ERR_UNSUPPORTED, "precision %d not implemented", (int)prec);
   }
@@ -342,7 +401,7 @@ template <int NIN, int W>
 nvdb_status launch_train_t(const NetView& nv, const TrainJob& job, int grid, cudaStream_t s) {
   const size_t smem = TrainSmem<NIN, W>::bytes(nv.layers);
   CU(cudaFuncSetAttribute(train_fwd_bwd_kernel<NIN, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  train_fwd_bwd_kernel<NIN, W><<<grid, kTile, smem, s>>>(nv, job);
+  KLAUNCH("train_fwd_bwd", s, train_fwd_bwd_kernel<NIN, W><<<grid, kTile, smem, s>>>(nv, job));
   CU(cudaGetLastError());
   return NVDB_OK;
 }
@@ -382,14 +441,14 @@ nvdb_status upload_net(nvdb_model* m, int k, const float* host_params, cudaStrea
   d.P = net_param_count(d.n_in, d.width, d.layers);
   dfree(d.p32); dfree(d.wpk); dfree(d.m); dfree(d.v);
   TRY(dalloc(&d.p32, (size_t)d.P));
-  TRY(dalloc(&d.wpk, (size_t)(d.width * d.n_in + (d.layers - 1) * d.width * d.width) + 8));
+  TRY(dalloc(&d.wpk, (size_t)wtile_elems(d.n_in, d.width, d.layers) * 6 + 64));
   if (host_params) CU(cudaMemcpyAsync(d.p32, host_params, d.P * 4, cudaMemcpyHostToDevice, s));
   return NVDB_OK;
 }
 
 nvdb_status pack_net(nvdb_model* m, int k, cudaStream_t s) {
   DevNet& d = m->net[k];
-  pack_weights_kernel<<<64, 256, 0, s>>>(d.p32, d.wpk, d.n_in, d.width, d.layers);
+  KLAUNCH("pack_weights", s, pack_weights_kernel<<<64, 256, 0, s>>>(d.p32, d.wpk, d.n_in, d.width, d.layers));
   CU(cudaGetLastError());
   return NVDB_OK;
 }
@@ -448,13 +507,13 @@ extern "C" nvdb_status nvdb_build(const int32_t* d_ijk, const float* d_val, int6
     TRY(dalloc(&h, 3 * (size_t)n)); TRY(dalloc(&e, 3 * (size_t)n)); TRY(dalloc(&status, 1));
     TRY(dalloc(&g->ijk, 3 * (size_t)n)); TRY(dalloc(&g->val, n));
     CU(cudaMemsetAsync(status, 0, 4, s));
-    build_keys_kernel<<<blocks_for(n, 256), 256, 0, s>>>(d_ijk, n, k0, i0, status);
+    KLAUNCH("build_keys", s, build_keys_kernel<<<blocks_for(n, 256), 256, 0, s>>>(d_ijk, n, k0, i0, status));
     size_t tb = 0;
     CU(cub::DeviceRadixSort::SortPairs(nullptr, tb, k0, k1, i0, i1, (int)n, 0, 63, s));
     CU(cudaMalloc(&tmp, tb));
     CU(cub::DeviceRadixSort::SortPairs(tmp, tb, k0, k1, i0, i1, (int)n, 0, 63, s));
-    build_gather_kernel<<<blocks_for(n, 256), 256, 0, s>>>(k1, i1, n, d_ijk, d_val, g->ijk, g->val, h, h + n,
-                                                            h + 2 * n, status);
+    KLAUNCH("build_gather", s, build_gather_kernel<<<blocks_for(n, 256), 256, 0, s>>>(k1, i1, n, d_ijk, d_val, g->ijk, g->val, h, h + n,
+                                                            h + 2 * n, status));
     CU(cudaGetLastError());
     Scan sc;
     int64_t tot[3];
@@ -476,9 +535,9 @@ extern "C" nvdb_status nvdb_build(const int32_t* d_ijk, const float* d_val, int6
     CU(cudaMemsetAsync(g->leaf_mask, 0, 64 * g->n_leaf, s));
     CU(cudaMemsetAsync(g->l1_mask, 0, 512 * g->n_l1, s));
     CU(cudaMemsetAsync(g->l2_mask, 0, 4096 * g->n_l2, s));
-    build_fill_kernel<<<blocks_for(n, 256), 256, 0, s>>>(g->ijk, n, h, h + n, h + 2 * n, e, e + n, e + 2 * n,
+    KLAUNCH("build_fill", s, build_fill_kernel<<<blocks_for(n, 256), 256, 0, s>>>(g->ijk, n, h, h + n, h + 2 * n, e, e + n, e + 2 * n,
                                                           g->leaf_origin, g->leaf_first, g->leaf_mask, g->l1_origin,
-                                                          g->l1_mask, g->l2_origin, g->l2_mask);
+                                                          g->l1_mask, g->l2_origin, g->l2_mask));
     CU(cudaGetLastError());
     CU(cudaMemcpyAsync(g->leaf_first + g->n_leaf, &g->n, 8, cudaMemcpyHostToDevice, s));
     // encoding domain: level-1 aligned bounding box, power-of-two extent >= 128
@@ -558,7 +617,7 @@ extern "C" void nvdb_train_opts_default(nvdb_train_opts* o) {
   o->lr_interval = 100;
   o->loss = NVDB_LOSS_MSE;
   o->train_prec = NVDB_FP32;
-  o->patch_precs = (1u << NVDB_FP32) | (1u << NVDB_BF16);
+  o->patch_precs = (1u << NVDB_FP32) | (1u << NVDB_BF16) | (1u << NVDB_FP16);
 }
 
 namespace {
@@ -606,14 +665,14 @@ nvdb_status make_patches(nvdb_model* m, const nvdb_grid* g, int prec, cudaStream
       job.words = words;
       TRY(launch_eval(m, lev == 0 ? 0 : 1, (nvdb_precision)prec, job, s));
       const uint32_t* truth = reinterpret_cast<const uint32_t*>(lev == 0 ? g->l1_mask : g->leaf_mask);
-      if (items) mismatch_count_kernel<<<blocks_for(items, 128), 128, 0, s>>>(words, truth, wpi, items, counts);
+      if (items) KLAUNCH("mismatch_count", s, mismatch_count_kernel<<<blocks_for(items, 128), 128, 0, s>>>(words, truth, wpi, items, counts));
       TRY(m->scan.run(counts, items, off, s));
-      offsets_to_u32_kernel<<<blocks_for(items + 1, 256), 256, 0, s>>>(off, m->scan.total, items, off32);
+      KLAUNCH("offsets_to_u32", s, offsets_to_u32_kernel<<<blocks_for(items + 1, 256), 256, 0, s>>>(off, m->scan.total, items, off32));
       int64_t total = 0;
       CU(cudaMemcpyAsync(&total, m->scan.total, 8, cudaMemcpyDeviceToHost, s));
       CU(cudaStreamSynchronize(s));
       TRY(dalloc(&idx, (size_t)total + 1));
-      if (items) emit_patches_kernel<<<blocks_for(items, 128), 128, 0, s>>>(words, wpi, items, off, idx);
+      if (items) KLAUNCH("emit_patches", s, emit_patches_kernel<<<blocks_for(items, 128), 128, 0, s>>>(words, wpi, items, off, idx));
       CU(cudaGetLastError());
       std::vector<uint32_t>& ho = lev == 0 ? ps.l1_off : ps.l0_off;
       std::vector<uint16_t>& hi = lev == 0 ? ps.l1_idx : ps.l0_idx;
@@ -714,8 +773,8 @@ extern "C" nvdb_status nvdb_compress(const nvdb_grid* g, const nvdb_train_opts* 
         if (st != NVDB_OK) break;
         const float lr_t = o->lr_interval > 0 ? (float)((double)o->lr * std::pow((double)o->lr_decay, (double)((t - 1) / o->lr_interval)))
                                               : o->lr;
-        adam_reduce_kernel<<<blocks_for(d.P + 1, 256), 256, 0, s>>>(m->partial, grid, d.P, d.p32, d.m, d.v, t, lr_t,
-                                                                    nullptr, d_loss + (t - 1), 1.f / (float)o->batch);
+        KLAUNCH("adam_reduce", s, adam_reduce_kernel<<<blocks_for(d.P + 1, 256), 256, 0, s>>>(m->partial, grid, d.P, d.p32, d.m, d.v, t, lr_t,
+                                                                    nullptr, d_loss + (t - 1), 1.f / (float)o->batch));
         if (cudaGetLastError() != cudaSuccess) st = fail(NVDB_ERR_CUDA, "adam launch failed");
       }
       if (st == NVDB_OK) {
@@ -731,7 +790,7 @@ extern "C" nvdb_status nvdb_compress(const nvdb_grid* g, const nvdb_train_opts* 
     TRY(st);
     for (int k = 0; k < 3; ++k) TRY(pack_net(m, k, s));
     uint32_t pp = o->patch_precs ? o->patch_precs : (1u << NVDB_FP32);
-    for (int p = 0; p < 3; ++p)
+    for (int p = 0; p < 4; ++p)
       if (pp & (1u << p)) {
         if (p == NVDB_FP8_E4M3) return fail(NVDB_ERR_UNSUPPORTED, "FP8 patches not implemented");
         TRY(make_patches(m, g, p, s));
@@ -779,11 +838,11 @@ nvdb_status decode_topology(nvdb_model* m, const PatchSet* ps, nvdb_precision pr
   DecodeScratch& d = m->ds;
   const uint64_t* l2m = reinterpret_cast<const uint64_t*>(m->l2_mask);
   if (m->n_l2) {
-    l2_count_kernel<<<(unsigned)m->n_l2, 512, 0, s>>>(l2m, m->n_l2, d.l2_counts);
+    KLAUNCH("l2_count", s, l2_count_kernel<<<(unsigned)m->n_l2, 512, 0, s>>>(l2m, m->n_l2, d.l2_counts));
     TRY(m->scan.run(d.l2_counts, m->n_l2, d.l2_off, s));
-    check_total_kernel<<<1, 1, 0, s>>>(m->scan.total, m->n_l1, m->status);
-    l2_emit_kernel<<<(unsigned)m->n_l2, 512, 0, s>>>(l2m, m->l2_origin, m->n_l2, d.l2_off, d.l1_origin, m->n_l1,
-                                                     m->status);
+    KLAUNCH("check_total", s, check_total_kernel<<<1, 1, 0, s>>>(m->scan.total, m->n_l1, m->status));
+    KLAUNCH("l2_emit", s, l2_emit_kernel<<<(unsigned)m->n_l2, 512, 0, s>>>(l2m, m->l2_origin, m->n_l2, d.l2_off, d.l1_origin, m->n_l1,
+                                                     m->status));
   }
   EvalJob j1{};
   j1.mode = MODE_L1;
@@ -792,13 +851,13 @@ nvdb_status decode_topology(nvdb_model* m, const PatchSet* ps, nvdb_precision pr
   j1.words = d.l1_words;
   TRY(launch_eval(m, 0, prec, j1, s));
   if (m->n_l1)
-    patch_count_kernel<<<blocks_for(m->n_l1, 128), 128, 0, s>>>(d.l1_words, 128, m->n_l1, ps->d_l1_off, ps->d_l1_idx,
-                                                               d.l1_counts);
+    KLAUNCH("patch_count", s, patch_count_kernel<<<blocks_for(m->n_l1, 128), 128, 0, s>>>(d.l1_words, 128, m->n_l1, ps->d_l1_off, ps->d_l1_idx,
+                                                               d.l1_counts));
   TRY(m->scan.run(d.l1_counts, m->n_l1, d.l1_off, s));
-  check_total_kernel<<<1, 1, 0, s>>>(m->scan.total, m->n_leaf, m->status);
+  KLAUNCH("check_total", s, check_total_kernel<<<1, 1, 0, s>>>(m->scan.total, m->n_leaf, m->status));
   if (m->n_l1)
-    emit_leaves_kernel<<<blocks_for(m->n_l1 * 32, 256), 256, 0, s>>>(d.l1_words, d.l1_origin, m->n_l1, d.l1_off,
-                                                                    d.leaf_origin, m->n_leaf, m->status);
+    KLAUNCH("emit_leaves", s, emit_leaves_kernel<<<blocks_for(m->n_l1 * 32, 256), 256, 0, s>>>(d.l1_words, d.l1_origin, m->n_l1, d.l1_off,
+                                                                    d.leaf_origin, m->n_leaf, m->status));
   EvalJob j0{};
   j0.mode = MODE_L0;
   j0.nodes = d.leaf_origin;
@@ -806,10 +865,10 @@ nvdb_status decode_topology(nvdb_model* m, const PatchSet* ps, nvdb_precision pr
   j0.words = d.leaf_words;
   TRY(launch_eval(m, 1, prec, j0, s));
   if (m->n_leaf)
-    patch_count_kernel<<<blocks_for(m->n_leaf, 128), 128, 0, s>>>(d.leaf_words, 16, m->n_leaf, ps->d_l0_off,
-                                                                 ps->d_l0_idx, d.leaf_counts);
+    KLAUNCH("patch_count", s, patch_count_kernel<<<blocks_for(m->n_leaf, 128), 128, 0, s>>>(d.leaf_words, 16, m->n_leaf, ps->d_l0_off,
+                                                                 ps->d_l0_idx, d.leaf_counts));
   TRY(m->scan.run(d.leaf_counts, m->n_leaf, d.leaf_off, s));
-  check_total_kernel<<<1, 1, 0, s>>>(m->scan.total, m->n_active, m->status);
+  KLAUNCH("check_total", s, check_total_kernel<<<1, 1, 0, s>>>(m->scan.total, m->n_active, m->status));
   CU(cudaGetLastError());
   return NVDB_OK;
 }
@@ -837,9 +896,9 @@ extern "C" nvdb_status nvdb_decompress(const nvdb_model* const* models, int n_mo
     TRY(decode_topology(m, m->patch_set(prec), prec, s));
     DecodeScratch& d = m->ds;
     if (m->n_leaf)
-      emit_voxels_kernel<<<blocks_for(m->n_leaf * 32, 256), 256, 0, s>>>(d.leaf_words, d.leaf_origin, m->n_leaf,
+      KLAUNCH("emit_voxels", s, emit_voxels_kernel<<<blocks_for(m->n_leaf * 32, 256), 256, 0, s>>>(d.leaf_words, d.leaf_origin, m->n_leaf,
                                                                         d.leaf_off, d_ijk + 3 * base, m->n_active,
-                                                                        m->status);
+                                                                        m->status));
     EvalJob jr{};
     jr.mode = MODE_LIST;
     jr.ijk = d_ijk + 3 * base;
@@ -873,11 +932,11 @@ nvdb_status build_query_cache(nvdb_model* m, cudaStream_t s) {
   TRY(dalloc(&q.l2_key, m->n_l2 + 1)); TRY(dalloc(&q.l2_pre, 512 * m->n_l2 + 1));
   TRY(dalloc(&q.l1_pre, 128 * m->n_l1 + 1));
   if (m->n_l2) {
-    l2_keys_kernel<<<blocks_for(m->n_l2, 128), 128, 0, s>>>(m->l2_origin, m->n_l2, q.l2_key);
-    word_prefix64_kernel<<<blocks_for(m->n_l2, 128), 128, 0, s>>>(reinterpret_cast<const uint64_t*>(m->l2_mask), 512,
-                                                                  m->n_l2, q.l2_pre);
+    KLAUNCH("l2_keys", s, l2_keys_kernel<<<blocks_for(m->n_l2, 128), 128, 0, s>>>(m->l2_origin, m->n_l2, q.l2_key));
+    KLAUNCH("word_prefix64", s, word_prefix64_kernel<<<blocks_for(m->n_l2, 128), 128, 0, s>>>(reinterpret_cast<const uint64_t*>(m->l2_mask), 512,
+                                                                  m->n_l2, q.l2_pre));
   }
-  if (m->n_l1) word_prefix_kernel<<<blocks_for(m->n_l1, 128), 128, 0, s>>>(m->ds.l1_words, 128, m->n_l1, q.l1_pre);
+  if (m->n_l1) KLAUNCH("word_prefix", s, word_prefix_kernel<<<blocks_for(m->n_l1, 128), 128, 0, s>>>(m->ds.l1_words, 128, m->n_l1, q.l1_pre));
   q.batch = kQueryBatch;
   TRY(dalloc(&q.qmask, q.batch)); TRY(dalloc(&q.counts, q.batch)); TRY(dalloc(&q.off, q.batch + 1));
   TRY(dalloc(&q.list, 3 * 8 * q.batch)); TRY(dalloc(&q.vals, 8 * q.batch));
@@ -907,7 +966,7 @@ TopoView topo_view(const nvdb_model* m) {
 extern "C" nvdb_status nvdb_query(const nvdb_model* cm, const float* d_xyz, int64_t n, nvdb_precision prec,
                                   float* d_out, uint8_t* d_active, nvdb_stream stream) {
   if (!cm || n < 0 || (n > 0 && (!d_xyz || !d_out))) return fail(NVDB_ERR_INVALID_ARG, "nvdb_query: bad arguments");
-  if (prec != NVDB_FP32 && prec != NVDB_BF16) return fail(NVDB_ERR_UNSUPPORTED, "precision %d", (int)prec);
+  if (prec != NVDB_FP32 && prec != NVDB_BF16 && prec != NVDB_FP16) return fail(NVDB_ERR_UNSUPPORTED, "precision %d", (int)prec);
   nvdb_model* m = const_cast<nvdb_model*>(cm);
   cudaStream_t s = (cudaStream_t)stream;
   TRY(build_query_cache(m, s));
@@ -916,10 +975,10 @@ extern "C" nvdb_status nvdb_query(const nvdb_model* cm, const float* d_xyz, int6
   for (int64_t b0 = 0; b0 < n; b0 += q.batch) {
     const int64_t nb = std::min(q.batch, n - b0);
     const float* xyz = d_xyz + 3 * b0;
-    query_lookup_kernel<<<blocks_for(nb, 256), 256, 0, s>>>(tv, xyz, nb, q.qmask, q.counts,
-                                                             d_active ? d_active + b0 : nullptr);
+    KLAUNCH("query_lookup", s, query_lookup_kernel<<<blocks_for(nb, 256), 256, 0, s>>>(tv, xyz, nb, q.qmask, q.counts,
+                                                             d_active ? d_active + b0 : nullptr));
     TRY(m->scan.run(q.counts, nb, q.off, s));
-    query_emit_kernel<<<blocks_for(nb, 256), 256, 0, s>>>(xyz, nb, q.qmask, q.off, q.list);
+    KLAUNCH("query_emit", s, query_emit_kernel<<<blocks_for(nb, 256), 256, 0, s>>>(xyz, nb, q.qmask, q.off, q.list));
     EvalJob jr{};
     jr.mode = MODE_LIST;
     jr.ijk = q.list;
@@ -928,7 +987,7 @@ extern "C" nvdb_status nvdb_query(const nvdb_model* cm, const float* d_xyz, int6
     jr.out = q.vals;
     jr.scale = m->value_scale();
     TRY(launch_eval(m, 2, prec, jr, s));
-    query_blend_kernel<<<blocks_for(nb, 256), 256, 0, s>>>(xyz, nb, q.qmask, q.off, q.vals, m->background, d_out + b0);
+    KLAUNCH("query_blend", s, query_blend_kernel<<<blocks_for(nb, 256), 256, 0, s>>>(xyz, nb, q.qmask, q.off, q.vals, m->background, d_out + b0));
     CU(cudaGetLastError());
   }
   return NVDB_OK;
@@ -975,8 +1034,8 @@ extern "C" nvdb_status nvdb_mlp_grad(const nvdb_model* cm, int net, const int32_
   TRY(launch_train(m, net, j, grid, s));
   float* d_loss = nullptr;
   TRY(dalloc(&d_loss, 1));
-  adam_reduce_kernel<<<blocks_for(d.P + 1, 256), 256, 0, s>>>(m->partial, grid, d.P, nullptr, nullptr, nullptr, 1, 0.f,
-                                                              d_grad, d_loss, 1.f / (float)n);
+  KLAUNCH("adam_reduce", s, adam_reduce_kernel<<<blocks_for(d.P + 1, 256), 256, 0, s>>>(m->partial, grid, d.P, nullptr, nullptr, nullptr, 1, 0.f,
+                                                              d_grad, d_loss, 1.f / (float)n));
   float h = 0.f;
   cudaError_t e = cudaMemcpyAsync(&h, d_loss, 4, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -1087,7 +1146,7 @@ extern "C" nvdb_status nvdb_model_import(const void* buf, size_t bytes, nvdb_str
   Reader r{static_cast<const uint8_t*>(buf), bytes};
   const BlobHeader* h = static_cast<const BlobHeader*>(r.take(sizeof(BlobHeader)));
   if (!h || std::memcmp(h->magic, "NVDBMDL1", 8) != 0 || h->version != 1) return fail(NVDB_ERR_CORRUPT, "not an NVDBMDL1 blob");
-  if (h->n_l2 < 0 || h->n_l1 < 0 || h->n_leaf < 0 || h->n_active < 0 || h->n_patch_sets < 0 || h->n_patch_sets > 3 ||
+  if (h->n_l2 < 0 || h->n_l1 < 0 || h->n_leaf < 0 || h->n_active < 0 || h->n_patch_sets < 0 || h->n_patch_sets > 4 ||
       h->grid_class > 1 || h->log2_extent < 0 || h->log2_extent > 21)
     return fail(NVDB_ERR_CORRUPT, "bad blob header");
   auto* m = new nvdb_model();
@@ -1183,3 +1242,39 @@ extern "C" nvdb_status nvdb_model_free(nvdb_model* m) {
 }
 
 extern "C" const char* nvdb_last_error(void) { return g_err.c_str(); }
+
+extern "C" void nvdb_profile_enable(int on) { prof::g_on.store(on != 0); }
+
+extern "C" int64_t nvdb_launch_count(void) { return (int64_t)prof::g_launches.load(); }
+
+extern "C" int nvdb_profile_read(char* names, int name_len, int64_t* launches, double* ms, int cap) {
+  std::map<std::string, std::pair<int64_t, double>> agg;
+  std::vector<prof::Rec> recs;
+  {
+    std::lock_guard<std::mutex> lk(prof::g_mu);
+    recs.swap(prof::g_recs);
+  }
+  for (auto& r : recs) {
+    float t = 0.f;
+    cudaEventSynchronize(r.b);
+    cudaEventElapsedTime(&t, r.a, r.b);
+    auto& e = agg[r.name];
+    e.first += 1;
+    e.second += t;
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  int i = 0;
+  for (auto& kv : agg) {
+    if (i < cap) {
+      if (names && name_len > 0) {
+        std::strncpy(names + (size_t)i * name_len, kv.first.c_str(), name_len - 1);
+        names[(size_t)i * name_len + name_len - 1] = 0;
+      }
+      if (launches) launches[i] = kv.second.first;
+      if (ms) ms[i] = kv.second.second;
+    }
+    ++i;
+  }
+  return i;
+}

@@ -3,7 +3,8 @@
 Bars (tolerances written per test): bit-exact for the tree build, the initial
 parameters, topology, compacted lists and patch-corrected masks; 1e-5
 relative (normalised by the head's dot-product scale) for FP32 network values;
-1e-4 relative for FP32 gradients; 2e-2 of the band half-width for BF16 values.
+1e-4 relative for FP32 gradients; 2e-2 of the band half-width for the
+tensor-core precisions (compensated BF16 and FP16).
 """
 import numpy as np
 import pytest
@@ -111,7 +112,7 @@ def _imported(ref, seed, width, layers, ffm=None):
 
 @pytest.mark.parametrize("shape", [([32, 32, 32], [3, 3, 3], None), ([32, 64, 64], [2, 4, 4], [32, 64]),
                                    ([64, 32, 64], [3, 3, 4], [64, 64])])
-@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("prec", [0, 1, 3])
 def test_mlp_eval_parity(sphere128, shape, prec):
     ijk, val, ref = sphere128
     om, m = _imported(ref, 5, *shape)
@@ -185,7 +186,7 @@ def test_decompress_parity(name):
     m = nv.compress(_grid(ijk, val), seed=4, ffm_sigma=1.25, steps=50, batch=2048, width=[32, 64, 64],
                     layers=[3, 3, 4])
     om = blob.read(m.export())
-    for prec in (0, 1):
+    for prec in (0, 1, 3):
         dijk, dval, cnt = nv.decompress(m, prec)
         dijk, dval = dijk.cpu().numpy(), dval.cpu().numpy()
         assert cnt == [ref["n"]]
@@ -229,11 +230,14 @@ def test_decompress_errors(sphere128):
     with pytest.raises(nv.NvdbError) as e:
         nv.decompress(m, 1)                               # no BF16 patch set
     assert e.value.status == 7
+    with pytest.raises(nv.NvdbError) as e:
+        nv.compress(_grid(ijk, val), steps=1, batch=512, patch_precs=4)   # FP8 not implemented
+    assert e.value.status == 7
 
 
 # ---------------------------------------------------------------------------- query
 
-@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("prec", [0, 1, 3])
 def test_query_parity(sphere128, prec):
     ijk, val, ref = sphere128
     m = nv.compress(_grid(ijk, val), seed=8, ffm_sigma=1.25, steps=100, batch=4096)
