@@ -1,0 +1,394 @@
+#!/usr/bin/env python
+"""Benchmark of the NeuralVDB hot path on B300: decoded voxels/s (and training samples/s).
+
+Workload (default "union1024"): narrow-band SDF (half-width 3) of the union of
+32 spheres + 32 tori (seed 2) in a 1024^3 grid; three networks of 4 hidden
+layers x 64 (ReLU), Fourier features n = 64, sigma = 10 cycles per 1024 voxels;
+trained on the GPU (FP32, batch 65536, lr 1e-3 decayed 0.975 / 100 steps),
+then decoded in full.
+
+One timed step = one nvdb_decompress of the whole model: level-1 node origins
+from the level-2 masks, level-1 classification of every leaf slot, patch XOR,
+compaction to the leaf list, level-0 classification of every voxel of every
+leaf, patch XOR, compaction to the voxel list, regression of every active voxel
+(all kernels of the library).  Inputs (the model) are resident in HBM; the
+output (16 B per voxel, > L2) is written every step and L2 is flushed between
+steps.  `value` is measured at the precision --prec (default bf16); every
+precision's throughput and its decoded-SDF error against the FP64 oracle on
+sampled voxels are reported under "by_precision".
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+import torch  # noqa: E402
+
+PRECS = {"fp32": 0, "bf16": 1, "fp16": 3}
+WORKLOAD_DESC = ("union of 32 spheres + 32 tori (seed 2), 1024^3, half-band 3; 3 nets 4x64 ReLU, "
+                 "FFM n=64 sigma=10/1024vox; full decompress")
+NET_WIDTH, NET_LAYERS, FFM = [64, 64, 64], [4, 4, 4], [64, 64]
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--prec", choices=list(PRECS), default="bf16")
+    ap.add_argument("--train-steps", type=int, default=2500)
+    ap.add_argument("--train-batch", type=int, default=65536)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def flops_per_eval(n_in: int, w: int, layers: int) -> int:
+    """Algorithmic FLOPs of one network evaluation: 2(n w + (L-1) w^2 + w)."""
+    return 2 * (n_in * w + (layers - 1) * w * w + w)
+
+
+def measured_peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        d["source"] = "measured"
+        return d
+    return dict(hbm_gbs=6400.0, bf16_tflops=1800.0, bf16_tflops_sustained=1400.0, source="fallback")
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        cvd = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+        ids = [x.strip() for x in cvd.split(",") if x.strip()]
+        self.index = ids[index] if index < len(ids) else str(index)
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "100", "-i", str(self.index)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc is not None:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        if not self.out:
+            return None
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return dict(sm_mhz=statistics.median(sm), sm_max_mhz=mx, reasons=sorted(reasons), samples=len(sm))
+
+
+# ----------------------------------------------------------------------------- oracle sample (CPU)
+def oracle_decode_sample(ijk: np.ndarray, val: np.ndarray, model_from_blob, n_nodes: int, seed: int,
+                         time_budget: float | None = None):
+    """Full oracle decode of a seeded sample of level-1 nodes of the workload.
+
+    Returns (active voxels decoded, seconds, nodes, threads).  The sample model keeps
+    the networks of `model_from_blob` (or the oracle's initial networks if None) and
+    the explicit upper tree restricted to the sampled level-1 nodes; its patches are
+    computed by the oracle for those nodes (untimed).
+    """
+    from oracle import codec, vdb
+    node = ijk.astype(np.int64) >> 7
+    key = (node[:, 0] << 28) | (node[:, 1] << 14) | node[:, 2]
+    uk = np.unique(key)
+    rng = np.random.default_rng(seed)
+    done_vox, secs, nodes = 0, 0.0, 0
+    order = rng.permutation(len(uk))
+    for i in order[: max(1, n_nodes)]:
+        sel = key == uk[i]
+        g = vdb.build(ijk[sel], val[sel])
+        if model_from_blob is not None:
+            m = dict(model_from_blob)
+        else:
+            m = codec.init_model(g, 0, 3.0, codec.default_opts(width=NET_WIDTH, layers=NET_LAYERS, ffm_size=FFM,
+                                                               sigma=10.0, seed=1))
+            o, l2e = vdb.domain(ijk)
+            m["origin"], m["log2_extent"] = o, l2e
+        m.update(l2_origin=g["l2_origin"], l2_mask=g["l2_mask"], n_l2=g["l2_origin"].shape[0],
+                 n_l1=g["l1_origin"].shape[0], n_leaf=g["leaf_origin"].shape[0], n_active=g["n"], patches={})
+        codec.make_patches(g, m, 0)
+        t0 = time.perf_counter()
+        dijk, _ = codec.decompress(m, 0)
+        secs += time.perf_counter() - t0
+        done_vox += len(dijk)
+        nodes += 1
+        if time_budget is not None and secs >= time_budget:
+            break
+    return done_vox, secs, nodes
+
+
+def blas_threads() -> int:
+    try:
+        from threadpoolctl import threadpool_info
+        n = [d.get("num_threads", 1) for d in threadpool_info() if d.get("user_api") == "blas"]
+        return int(max(n)) if n else 1
+    except Exception:
+        return os.cpu_count() or 1
+
+
+# ----------------------------------------------------------------------------- reference arm
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from fixtures import workload
+    # input generation only (torch elementwise ops, none of the library); then CPU oracle work
+    ijk, val, _ = workload("union1024", device="cuda" if torch.cuda.is_available() else "cpu")
+    ijk, val = ijk.cpu().numpy(), val.cpu().numpy()
+    times, voxels = [], []
+    for s in range(args.warmup + args.steps):
+        v, t, _ = oracle_decode_sample(ijk, val, None, 1, seed=1000 + s)
+        if s >= args.warmup:
+            times.append(t)
+            voxels.append(v)
+    value = sum(voxels) / sum(times)
+    thr = blas_threads()
+    sample = f"per step: full oracle decode of 1 seeded level-1 node (mean {np.mean(voxels):.0f} voxels); initial weights"
+    line = dict(impl="reference", metric="decoded voxels/s", value=value, unit="voxels/s", n_gpus=args.gpus,
+                steps=args.steps, warmup=args.warmup, ms_per_step=1000.0 * float(np.mean(times)),
+                higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f64", data="synthetic",
+                config=dict(workload=WORKLOAD_DESC),
+                cpu_baseline=dict(value=value, unit="voxels/s", cores=thr, kind="oracle", sample=sample),
+                e2e=dict(value=value, unit="voxels/s", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    print(json.dumps(line))
+    return 0
+
+
+# ----------------------------------------------------------------------------- our arm
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import paper_2208_04448_b300 as nv
+    from fixtures import workload
+    from oracle import blob, codec
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    # ---- setup (untimed): volume, tree, training
+    ijk, val, _ = workload("union1024", device="cuda")
+    ijk, val = ijk.contiguous(), val.contiguous()
+    g = nv.build(ijk, val, 0, 3.0)
+    info = g.info()
+    n_active, n_leaf, n_l1 = info["n_active"], info["n_leaf"], info["n_l1"]
+    opts = dict(seed=1, width=NET_WIDTH, layers=NET_LAYERS, ffm_size=FFM,
+                ffm_sigma=10.0 * (1 << info["log2_extent"]) / 1024.0, steps=args.train_steps,
+                batch=args.train_batch, lr=1e-3, lr_decay=0.975, lr_interval=100, patch_precs=0b1011)
+    nv.profile_read()
+    nv.profile_enable(True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    model = nv.compress(g, **opts)
+    train_wall = time.perf_counter() - t0
+    prof = nv.profile_read()
+    nv.profile_enable(False)
+    train_ms = sum(v[1] for k, v in prof.items() if k in ("train_fwd_bwd", "adam_reduce"))
+    train_samples = 3 * args.train_steps * args.train_batch
+    blob_bytes = model.export()
+
+    out_ijk = torch.empty((n_active, 3), dtype=torch.int32, device="cuda")
+    out_val = torch.empty(n_active, dtype=torch.float32, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")   # 256 MB > 126 MB L2
+    stream = torch.cuda.current_stream()
+
+    def decode(prec):
+        nv.decompress(model, prec, out=(out_ijk, out_val))
+
+    def timed(prec, steps, profile=False):
+        for _ in range(args.warmup):
+            decode(prec)
+        torch.cuda.synchronize()
+        if profile:
+            nv.profile_read()
+            nv.profile_enable(True)
+        ms = []
+        l0 = nv.launch_count()
+        for _ in range(steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            decode(prec)
+            b.record(stream)
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+        launches = nv.launch_count() - l0
+        kern = None
+        if profile:
+            kern = nv.profile_read()
+            nv.profile_enable(False)
+        return ms, launches, kern
+
+    # decoded-value error against the oracle on sampled voxels, per precision
+    om = blob.read(blob_bytes)
+    rs = np.random.default_rng(7)
+
+    def decode_error(prec):
+        decode(prec)
+        torch.cuda.synchronize()
+        idx = rs.choice(n_active, size=min(4096, n_active), replace=False)
+        pi = out_ijk[torch.from_numpy(idx).cuda()].cpu().numpy()
+        pv = out_val[torch.from_numpy(idx).cuda()].cpu().numpy().astype(np.float64)
+        want = codec.evaluate(om, codec.REG, pi) * 3.0
+        return float(np.abs(pv - want).max())
+
+    by_prec = {}
+    head_prec = PRECS[args.prec]
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for name, p in PRECS.items():
+            ms, launches, kern = timed(p, args.steps, profile=(p == head_prec))
+            by_prec[name] = dict(ms_per_step=float(np.mean(ms)), voxels_per_s=n_active / (np.mean(ms) / 1e3),
+                                 launches_per_step=launches / args.steps)
+            if p == head_prec:
+                head_ms, head_launches, head_kern = ms, launches, kern
+    torch.cuda.synchronize()
+    for name, p in PRECS.items():
+        by_prec[name]["max_abs_err_vs_oracle"] = decode_error(p)
+        by_prec[name]["err_bound"] = 0.02 * 3.0
+
+    mean_ms = float(np.mean(head_ms))
+    if dist is not None:
+        t = torch.tensor([mean_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        mean_ms = float(t.item())
+    value = world * n_active / (mean_ms / 1e3)
+
+    # ---- roofline of the dominant kernel (live CUDA events on the launching stream)
+    peaks = measured_peaks()
+    dom = max(head_kern.items(), key=lambda kv: kv[1][1])
+    dname, (dl, dms) = dom
+    n0, w1, L1 = FFM[1], NET_WIDTH[1], NET_LAYERS[1]
+    per_launch = {"L0": n_leaf * 512 * flops_per_eval(FFM[1], NET_WIDTH[1], NET_LAYERS[1]),
+                  "L1": n_l1 * 4096 * flops_per_eval(FFM[0], NET_WIDTH[0], NET_LAYERS[0]),
+                  "list": n_active * flops_per_eval(FFM[1], NET_WIDTH[2], NET_LAYERS[2])}[dname.split(".")[1]]
+    avg_s = dms / dl / 1e3
+    achieved = per_launch / avg_s / 1e12
+    if dname.startswith("mlp_f32"):
+        peak = 148 * 128 * 2 * peaks.get("sm_max_mhz", 2032.0) * 1e6 / 1e12
+        bound, peak_src = "alu", "derived: 148 SMs x 128 FFMA/clk x 2 x max SM clock"
+    else:
+        peak = peaks["bf16_tflops"]
+        bound, peak_src = "tensor", f"{peaks['source']} bf16 burst (16-bit kind::f16 rate)"
+    traffic = None
+    tfile = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tfile):
+        with open(tfile) as f:
+            traffic = json.load(f).get(dname)
+
+    # ---- end to end through the C ABI with host buffers
+    h_ijk = torch.empty((n_active, 3), dtype=torch.int32, pin_memory=True)
+    h_val = torch.empty(n_active, dtype=torch.float32, pin_memory=True)
+    e2e_ms = []
+    for s in range(args.warmup + max(3, args.steps // 5)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        m2 = nv.model_import(blob_bytes)
+        nv.decompress(m2, head_prec, out=(out_ijk, out_val))
+        h_ijk.copy_(out_ijk, non_blocking=True)
+        h_val.copy_(out_val, non_blocking=True)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        del m2
+        if s >= args.warmup:
+            e2e_ms.append(dt * 1e3)
+    e2e_value = world * n_active / (np.mean(e2e_ms) / 1e3)
+
+    # ---- CPU baseline: the oracle on a bounded sample (rank 0, N = 1 only)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        hi, hv = ijk.cpu().numpy(), val.cpu().numpy()
+        v, secs, nodes = oracle_decode_sample(hi, hv, om, 64, seed=11, time_budget=args.cpu_seconds)
+        cpu = dict(value=v / secs, unit="voxels/s", cores=blas_threads(), kind="oracle",
+                   sample=f"full FP64 oracle decode of {nodes} seeded level-1 nodes ({v} voxels, {secs:.1f} s)")
+
+    clocks = clk.summary()
+    line = dict(
+        metric="decoded voxels/s", value=value, unit="voxels/s", n_gpus=world, steps=args.steps,
+        warmup=args.warmup, ms_per_step=mean_ms, higher_is_better=True, scaling="weak", vs_baseline=None,
+        dtype=args.prec, data="synthetic",
+        config=dict(workload=WORKLOAD_DESC, n_active=n_active, n_leaf=n_leaf, n_l1=n_l1,
+                    precision=args.prec, l2="flushed (256 MB write) between timed steps; output 16 B/voxel",
+                    parallelism="replicas only" if world > 1 else "1 GPU"),
+        roofline=dict(kernel=dname, bound=bound, achieved=achieved, peak=peak, unit="TFLOP/s",
+                      frac=achieved / peak, traffic=traffic, flops_per_launch=per_launch,
+                      avg_launch_ms=dms / dl, peak_source=peak_src),
+        cpu_baseline=cpu,
+        e2e=dict(value=e2e_value, unit="voxels/s", h2d_bytes_per_step=len(blob_bytes),
+                 d2h_bytes_per_step=16 * n_active),
+        gpu_launches=int(head_launches),
+        clocks=clocks,
+        train_samples_per_s=train_samples / (train_ms / 1e3) if train_ms > 0 else None,
+        train=dict(steps=args.train_steps, batch=args.train_batch, wall_s=train_wall, kernel_ms=train_ms,
+                   final_loss=[float(np.mean(model.losses(k)[-50:])) for k in range(3)] if args.train_steps else None,
+                   precision="fp32"),
+        by_precision=by_prec,
+        kernels={k: dict(launches=v[0], ms=v[1]) for k, v in sorted(head_kern.items(), key=lambda kv: -kv[1][1])},
+    )
+    if rank == 0:
+        print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())
