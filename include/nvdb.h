@@ -183,6 +183,29 @@ nvdb_status nvdb_mlp_eval(const nvdb_model* model, int net, nvdb_precision prec,
 nvdb_status nvdb_mlp_grad(const nvdb_model* model, int net, const int32_t* d_ijk, const float* d_target,
                           int64_t n, int loss_kind, float* d_grad, float* loss, nvdb_stream stream);
 
+/* Same result as nvdb_mlp_grad, but allocates no device memory.  (The paper
+ * has no counterpart; this exists for callers, not for the method.)  It is for
+ * code that may not call cudaMalloc/cudaFree: applications whose device memory
+ * is owned by their own pool or arena, and latency-critical loops where an
+ * allocation, or the device-wide synchronisation a free can cause, is not
+ * acceptable.  nvdb_mlp_grad keeps its gradient partials in memory the model
+ * allocates on first use; this call keeps them, and the loss, in one static
+ * device array of 2^20 floats (4 MiB) that every GPU loading the library holds
+ * until the library is unloaded.
+ *  - The first call on a device looks the array's device address up (once per
+ *    device, with that device current); make that first call before any stream
+ *    capture begins.
+ *  - All calls share the array, and each call overwrites it (every block clears
+ *    its own part before use).  Calls that can overlap on the GPU -- on
+ *    different streams, or from different threads -- race on it; serialise them.
+ *  - Limit: a network of more than 2^20 - 2 parameters is rejected with
+ *    NVDB_ERR_CAPACITY.  Fewer thread blocks run than in nvdb_mlp_grad when the
+ *    array cannot hold one partial per SM, so the summation order (and the
+ *    last bits of the result) may differ.
+ * Arguments, outputs and synchronisation as for nvdb_mlp_grad. */
+nvdb_status nvdb_mlp_grad_static(const nvdb_model* model, int net, const int32_t* d_ijk, const float* d_target,
+                                 int64_t n, int loss_kind, float* d_grad, float* loss, nvdb_stream stream);
+
 int64_t nvdb_net_param_count(const nvdb_model* model, int net);
 
 nvdb_status nvdb_model_info(const nvdb_model* model, nvdb_info* out);

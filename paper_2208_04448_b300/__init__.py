@@ -194,6 +194,18 @@ def mlp_grad(model: Model, net: int, ijk: torch.Tensor, target: torch.Tensor, lo
     return g, lv.value
 
 
+def mlp_grad_static(model: Model, net: int, ijk: torch.Tensor, target: torch.Tensor, loss: int, out=None,
+                    stream=None):
+    """nvdb_mlp_grad_static: the gradient of mlp_grad computed without any device allocation by the
+    library.  `out` (a float32 CUDA tensor of param_count(net) elements) lets the caller own the output too."""
+    g = out if out is not None else torch.empty(model.param_count(net), dtype=torch.float32, device="cuda")
+    lv = C.c_float()
+    _check(lib().nvdb_mlp_grad_static(model.handle, net, _dptr(ijk, torch.int32, "ijk"),
+                                      _dptr(target, torch.float32, "target"), ijk.shape[0], loss,
+                                      _dptr(g, torch.float32, "grad"), C.byref(lv), _stream(stream)))
+    return g, lv.value
+
+
 def model_import(blob: bytes, stream=None) -> Model:
     h = C.c_void_p()
     buf = C.create_string_buffer(blob, len(blob))

@@ -46,6 +46,7 @@ SIGNATURES = {
     "nvdb_query": ([_vp, _vp, _i64, _i32, _vp, _vp, _vp], _st),
     "nvdb_mlp_eval": ([_vp, _i32, _i32, _vp, _i64, _vp, _vp], _st),
     "nvdb_mlp_grad": ([_vp, _i32, _vp, _vp, _i64, _i32, _vp, _f32p, _vp], _st),
+    "nvdb_mlp_grad_static": ([_vp, _i32, _vp, _vp, _i64, _i32, _vp, _f32p, _vp], _st),
     "nvdb_net_param_count": ([_vp, _i32], C.c_int64),
     "nvdb_model_info": ([_vp, C.POINTER(Info)], _st),
     "nvdb_model_export": ([_vp, _vp, C.POINTER(C.c_size_t)], _st),

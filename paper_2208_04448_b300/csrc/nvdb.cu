@@ -1278,3 +1278,84 @@ extern "C" int nvdb_profile_read(char* names, int name_len, int64_t* launches, d
   }
   return i;
 }
+
+// ============================================================================ allocation-free gradient
+// nvdb_mlp_grad computes its per-CTA gradient partials in device memory that
+// the model allocates with cudaMalloc on first use.  nvdb_mlp_grad_static is
+// the same computation for callers that must not allocate: its partials and
+// loss live in the file-scope array below (4 MiB, present on every device that
+// loads this library for as long as the library stays loaded).
+namespace {
+constexpr int64_t kStaticGradFloats = 1 << 20;
+static __device__ __align__(256) float g_grad_scratch[kStaticGradFloats];
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mu;
+float* g_static_ptr[kMaxDevices] = {};
+
+template <int NIN, int W>
+nvdb_status launch_train_static(const NetView& nv, const TrainJob& job, int grid, cudaStream_t s) {
+  const size_t smem = TrainSmem<NIN, W>::bytes(nv.layers);
+  CU(cudaFuncSetAttribute(train_fwd_bwd_kernel<NIN, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  train_fwd_bwd_kernel<NIN, W><<<grid, kTile, smem, s>>>(nv, job);
+  CU(cudaGetLastError());
+  return NVDB_OK;
+}
+}  // namespace
+
+extern "C" nvdb_status nvdb_mlp_grad_static(const nvdb_model* m, int net, const int32_t* d_ijk, const float* d_target,
+                                            int64_t n, int loss_kind, float* d_grad, float* loss, nvdb_stream stream) {
+  if (!m || net < 0 || net > 2 || n <= 0 || !d_ijk || !d_target || !d_grad)
+    return fail(NVDB_ERR_INVALID_ARG, "nvdb_mlp_grad_static: bad arguments");
+  if (loss_kind < 0 || loss_kind > 2) return fail(NVDB_ERR_INVALID_ARG, "unknown loss %d", loss_kind);
+  if (n > (1ll << 31)) return fail(NVDB_ERR_UNSUPPORTED, "nvdb_mlp_grad_static: n >= 2^31");
+  const DevNet& d = m->net[net];
+  // one CTA needs P + 1 floats of partials, plus one float for the loss
+  if (d.P + 2 > kStaticGradFloats)
+    return fail(NVDB_ERR_CAPACITY, "nvdb_mlp_grad_static: network %d has %lld parameters; the static scratch "
+                "holds %lld floats (at most %lld parameters)", net, (long long)d.P, (long long)kStaticGradFloats,
+                (long long)(kStaticGradFloats - 2));
+  int dev = 0;
+  CU(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return fail(NVDB_ERR_UNSUPPORTED, "device index %d", dev);
+  float* scratch = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_static_mu);
+    if (!g_static_ptr[dev]) {
+      void* p = nullptr;
+      const cudaError_t e = cudaGetSymbolAddress(&p, g_grad_scratch);
+      if (e != cudaSuccess)
+        return fail(NVDB_ERR_CUDA, "cudaGetSymbolAddress(static gradient scratch): %s", cudaGetErrorString(e));
+      g_static_ptr[dev] = static_cast<float*>(p);
+    }
+    scratch = g_static_ptr[dev];
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t fit = (kStaticGradFloats - 1) / (d.P + 1);
+  const int grid = (int)std::min<int64_t>(std::min<int64_t>((n + kTile - 1) / kTile, num_sms()), fit);
+  float* loss_slot = scratch + (kStaticGradFloats - 1);
+  TrainJob j{};
+  j.net = net;
+  j.loss = loss_kind;
+  j.step = 1;
+  j.batch = n;
+  j.ijk_list = d_ijk;
+  j.target_list = d_target;
+  j.partial = scratch;   // every CTA zeroes its own slot before accumulating
+  j.ox = m->origin[0];
+  j.oy = m->origin[1];
+  j.oz = m->origin[2];
+  const NetView nv = net_view(m, net);
+  if (nv.n_in == 32 && nv.width == 32) TRY((launch_train_static<32, 32>(nv, j, grid, s)));
+  else if (nv.n_in == 32 && nv.width == 64) TRY((launch_train_static<32, 64>(nv, j, grid, s)));
+  else if (nv.n_in == 64 && nv.width == 32) TRY((launch_train_static<64, 32>(nv, j, grid, s)));
+  else if (nv.n_in == 64 && nv.width == 64) TRY((launch_train_static<64, 64>(nv, j, grid, s)));
+  else return fail(NVDB_ERR_UNSUPPORTED, "network shape n=%d w=%d", nv.n_in, nv.width);
+  adam_reduce_kernel<<<blocks_for(d.P + 1, 256), 256, 0, s>>>(scratch, grid, d.P, nullptr, nullptr, nullptr, 1, 0.f,
+                                                              d_grad, loss_slot, 1.f / (float)n);
+  CU(cudaGetLastError());
+  float h = 0.f;
+  CU(cudaMemcpyAsync(&h, loss_slot, sizeof h, cudaMemcpyDeviceToHost, s));
+  CU(cudaStreamSynchronize(s));
+  if (loss) *loss = h;
+  return NVDB_OK;
+}
