@@ -69,6 +69,8 @@ void dfree(T*& p) {
   p = nullptr;
 }
 
+constexpr size_t kSmemPerSm = 233472;   // shared memory per SM on sm_103 (228 KiB)
+
 int num_sms() {
   static int n = 0;
   if (!n) {
@@ -352,9 +354,15 @@ NetView net_view(const nvdb_model* m, int k) {
 template <int NIN, int W, int MODE>
 nvdb_status launch_tc(const NetView& nv, const EvalJob& job, int64_t ntiles, const char* base, cudaStream_t s) {
   const TcLayout<NIN, W, MODE> lay(nv.layers);
-  int occ = 0;
   CU(cudaFuncSetAttribute(mlp_tc_kernel<NIN, W, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lay.total));
-  CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, mlp_tc_kernel<NIN, W, MODE>, kTile, lay.total));
+  // Residency from the kernel's own limits (the runtime's occupancy query reports 1 for
+  // kernels that allocate tensor memory): registers, shared memory, and TMEM columns.
+  cudaFuncAttributes fa;
+  CU(cudaFuncGetAttributes(&fa, mlp_tc_kernel<NIN, W, MODE>));
+  const int regs = std::max(8, (fa.numRegs + 7) & ~7);
+  const int by_regs = 65536 / (regs * kTile);
+  const int by_smem = (int)(kSmemPerSm / (lay.total + 1024));
+  const int occ = std::min({by_regs, by_smem, (int)(512 / kTmemCols), 8});
   if (occ < 1) return fail(NVDB_ERR_UNSUPPORTED, "tensor-core kernel does not fit on an SM");
   const int64_t grid = std::min<int64_t>(ntiles, (int64_t)num_sms() * occ);
   KLAUNCH(eval_name(base, job.mode), s,
