@@ -177,117 +177,139 @@ __global__ void __launch_bounds__(kTile) mlp_f32_kernel(NetView net, EvalJob job
 //             (hi = bf16(v), lo = bf16(v - hi)); D = A_hi W_hi + A_lo W_hi + A_hi W_lo,
 //             three MMAs per K step, error ~2^-16 relative.
 //  TC_FP16  : FP16 activations and weights, one MMA per K step.
+// Layout per CTA (one 128-row tile in flight):
+//  * weights in shared memory, each layer a [W x (K+16)] tile in the canonical
+//    no-swizzle K-major layout; column K holds the bias, columns K+1.. are zero;
+//  * the A operand (16-bit activations) in tensor memory, two elements per
+//    32-bit column, written by each thread for its own row with tcgen05.st;
+//    column K/2 holds the constant 1 that multiplies the bias column;
+//  * the FP32 accumulator D in tensor memory columns [0, W).
 enum TcMode : int { TC_BF16X3 = 0, TC_FP16 = 1 };
 
-template <int MODE>
-__device__ __forceinline__ void pack8(const float* v, uint4& hi, uint4& lo) {
-  uint32_t h[4], l[4];
-#pragma unroll
-  for (int e = 0; e < 4; ++e) {
-    if (MODE == TC_FP16) {
-      __half2 x = __floats2half2_rn(v[2 * e], v[2 * e + 1]);
-      h[e] = *reinterpret_cast<uint32_t*>(&x);
-      l[e] = 0u;
-    } else {
-      __nv_bfloat162 x = __floats2bfloat162_rn(v[2 * e], v[2 * e + 1]);
-      const float2 back = __bfloat1622float2(x);
-      __nv_bfloat162 y = __floats2bfloat162_rn(v[2 * e] - back.x, v[2 * e + 1] - back.y);
-      h[e] = *reinterpret_cast<uint32_t*>(&x);
-      l[e] = *reinterpret_cast<uint32_t*>(&y);
-    }
-  }
-  hi = make_uint4(h[0], h[1], h[2], h[3]);
-  lo = make_uint4(l[0], l[1], l[2], l[3]);
+__host__ __device__ inline int64_t wtile_elems(int nin, int w, int L) {
+  return (int64_t)w * (nin + 16) + (int64_t)(L - 1) * w * (w + 16);
 }
 
-// Features of row r written into the A tile(s) (K = NIN): cos then sin.
-template <int NIN, int MODE>
-__device__ __forceinline__ void encode_tc_row(uint8_t* sa, uint8_t* sa_lo, int r, const uint32_t* sq, int cx, int cy,
-                                              int cz) {
-  constexpr int M = NIN / 2;
-  float c[M], s[M];
-#pragma unroll
-  for (int f = 0; f < M; ++f) {
-    const uint32_t ph = ffm_phase(sq, f, cx, cy, cz);
-    if (MODE == TC_FP16)
-      __sincosf((float)(int32_t)ph * 1.4629180792671596e-09f, &s[f], &c[f]);   // pi / 2^31
-    else
-      sincospif((float)(int32_t)ph * 0x1p-31f, &s[f], &c[f]);
-  }
-#pragma unroll
-  for (int g = 0; g < M / 8; ++g) {
-    uint4 hi, lo;
-    pack8<MODE>(c + 8 * g, hi, lo);
-    *reinterpret_cast<uint4*>(sa + canon_off(r, 8 * g, NIN)) = hi;
-    if (MODE == TC_BF16X3) *reinterpret_cast<uint4*>(sa_lo + canon_off(r, 8 * g, NIN)) = lo;
-    pack8<MODE>(s + 8 * g, hi, lo);
-    *reinterpret_cast<uint4*>(sa + canon_off(r, M + 8 * g, NIN)) = hi;
-    if (MODE == TC_BF16X3) *reinterpret_cast<uint4*>(sa_lo + canon_off(r, M + 8 * g, NIN)) = lo;
-  }
-}
+template <int NIN, int W, int MODE>
+struct TcCfg {
+  static constexpr int M = NIN / 2;                         // frequencies
+  static constexpr int K0 = NIN + 16, KH = W + 16;          // augmented K of layer 0 / hidden layers
+  static constexpr uint32_t COLS = MODE == TC_BF16X3 ? 256u : 128u;
+  static constexpr uint32_t A_HI = 64u, A_LO = 128u;        // TMEM columns of the A operand(s)
+  static constexpr int MAXC = (int)(512u / COLS);           // CTAs per SM that fit in TMEM
+  static constexpr int NCOPY = MODE == TC_BF16X3 ? 2 : 1;
+};
 
-constexpr uint32_t kTmemCols = 64;          // FP32 accumulator columns (width <= 64)
-constexpr size_t kTcMinSmem = 33 * 1024;    // caps residency at 6 CTAs/SM -> 6 x 64 <= 512 TMEM columns
-
-// Packed weight tiles per network: [FP16 tiles][BF16 hi tiles][BF16 lo tiles],
-// each set = layer 0 [W x n_in] then layers 1..L-1 [W x W], canonical layout.
-__host__ __device__ inline int64_t wtile_elems(int nin, int w, int L) { return (int64_t)w * nin + (int64_t)(L - 1) * w * w; }
+constexpr size_t kSmemPerSmDev = 233472;
 
 template <int NIN, int W, int MODE>
 struct TcLayout {
-  static constexpr int KA = NIN > W ? NIN : W;
-  static constexpr int NCOPY = MODE == TC_BF16X3 ? 2 : 1;
-  size_t w_bytes, a_off, alo_off, b_off, wh_off, q_off, bar_off, slot_off, total;
+  size_t w_bytes, t_off, p_off, wh_off, q_off, bar_off, slot_off, total;
   __host__ __device__ TcLayout(int L) {
-    w_bytes = (size_t)wtile_elems(NIN, W, L) * 2;              // one copy
-    a_off = ((NCOPY * w_bytes) + 127) & ~(size_t)127;
-    alo_off = a_off + (size_t)kTile * KA * 2;
-    b_off = a_off + (size_t)NCOPY * kTile * KA * 2;
-    wh_off = b_off + (size_t)L * W * 4;
+    using C = TcCfg<NIN, W, MODE>;
+    w_bytes = (size_t)wtile_elems(NIN, W, L) * 2;           // one copy
+    t_off = (C::NCOPY * w_bytes + 15) & ~(size_t)15;
+    p_off = t_off + (size_t)C::M * 64 * (MODE == TC_FP16 ? 4 : 8);   // T table [M][64]: half2 / float2
+    wh_off = p_off + (size_t)2 * C::M * 8;                   // P table: float2 [2][M]
     q_off = wh_off + (size_t)(W + 4) * 4;
-    bar_off = (q_off + (size_t)(NIN / 2) * 12 + 7) & ~(size_t)7;
+    bar_off = (q_off + (size_t)C::M * 12 + 7) & ~(size_t)7;
     slot_off = bar_off + 8;
     total = slot_off + 8;
-    if (total < kTcMinSmem) total = kTcMinSmem;
+    // at most MAXC CTAs may be resident per SM (TMEM): make a (MAXC+1)-th not fit
+    const size_t floor_bytes = kSmemPerSmDev / (C::MAXC + 1) - 1024 + 128;
+    if (total < floor_bytes) total = floor_bytes;
   }
 };
+
+template <int MODE>
+__device__ __forceinline__ void split_pair(float a, float b, uint32_t& hi, uint32_t& lo) {
+  if (MODE == TC_FP16) {
+    hi = cvt_f16x2(a, b);
+    lo = 0u;
+  } else {
+    hi = cvt_bf16x2(a, b);
+    const float ha = __uint_as_float(hi << 16), hb = __uint_as_float(hi & 0xFFFF0000u);
+    lo = cvt_bf16x2(a - ha, b - hb);
+  }
+}
+
+template <int MODE>
+__device__ __forceinline__ void relu_pair(float a, float b, uint32_t& hi, uint32_t& lo) {
+  if (MODE == TC_FP16) {
+    hi = cvt_relu_f16x2(a, b);
+    lo = 0u;
+  } else {
+    split_pair<MODE>(fmaxf(a, 0.f), fmaxf(b, 0.f), hi, lo);
+  }
+}
+
+template <int NW>
+__device__ __forceinline__ void tmem_st_cols(uint32_t taddr, const uint32_t* r) {
+  if (NW == 32) tmem_st32(taddr, r);
+  else if (NW == 16) tmem_st16(taddr, r);
+  else tmem_st8(taddr, r);
+}
+
+// Write one row of the A operand: NK 16-bit values (as NK/2 packed columns) plus the
+// 8-column constant chunk (1, 0, ..., 0) that multiplies the bias column.
+template <int NK, int MODE>
+__device__ __forceinline__ void store_a_row(uint32_t tlane, const uint32_t* hi, const uint32_t* lo) {
+  using C = TcCfg<32, 32, MODE>;
+  tmem_st_cols<NK / 2>(tlane + C::A_HI, hi);
+  uint32_t cst[8] = {MODE == TC_FP16 ? 0x3C00u : 0x3F80u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+  tmem_st8(tlane + C::A_HI + NK / 2, cst);
+  if (MODE == TC_BF16X3) {
+    tmem_st_cols<NK / 2>(tlane + C::A_LO, lo);
+    cst[0] = 0u;
+    tmem_st8(tlane + C::A_LO + NK / 2, cst);
+  }
+}
 
 template <int NIN, int W, int MODE>
 __global__ void __launch_bounds__(kTile, 1) mlp_tc_kernel(NetView net, EvalJob job) {
   static_assert(W == 32 || W == 64, "width");
   static_assert(NIN == 32 || NIN == 64, "encoding size");
+  using C = TcCfg<NIN, W, MODE>;
+  constexpr int M = C::M;
   extern __shared__ __align__(1024) uint8_t smem[];
   const int L = net.layers;
   const TcLayout<NIN, W, MODE> lay(L);
-  uint8_t* sw = smem;                              // hi (or FP16) weights
-  uint8_t* sw_lo = smem + lay.w_bytes;             // lo weights (BF16X3)
-  uint8_t* sa = smem + lay.a_off;
-  uint8_t* sa_lo = smem + lay.alo_off;
-  float* sb = reinterpret_cast<float*>(smem + lay.b_off);
+  uint8_t* sw = smem;                              // hi (or FP16) weight tiles
+  uint8_t* sw_lo = smem + lay.w_bytes;             // lo weight tiles (BF16X3)
+  float2* sT = reinterpret_cast<float2*>(smem + lay.t_off);      // BF16X3: FP32 table
+  __half2* sTh = reinterpret_cast<__half2*>(smem + lay.t_off);   // FP16: half table
+  float2* sP = reinterpret_cast<float2*>(smem + lay.p_off);
   float* swh = reinterpret_cast<float*>(smem + lay.wh_off);
   uint32_t* sq = reinterpret_cast<uint32_t*>(smem + lay.q_off);
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + lay.bar_off);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + lay.slot_off);
   const int tid = threadIdx.x, warp = tid >> 5;
 
-  // stage weight tiles, biases, head and Fourier matrix
+  // ---- stage weights, head, Fourier matrix; lattice table T[f][dy*8+dz]
   {
     const int64_t te = wtile_elems(NIN, W, L);
-    const uint8_t* base = reinterpret_cast<const uint8_t*>(net.wpk) + (MODE == TC_FP16 ? 0 : te * 2);
+    const uint8_t* base = net.wpk + (MODE == TC_FP16 ? 0 : te * 2);
     const uint4* src = reinterpret_cast<const uint4*>(base);
     uint4* dst = reinterpret_cast<uint4*>(sw);
-    const size_t n16 = lay.NCOPY * lay.w_bytes / 16;
+    const size_t n16 = C::NCOPY * lay.w_bytes / 16;
     for (size_t i = tid; i < n16; i += kTile) dst[i] = __ldg(src + i);
-    for (int l = 0; l < L; ++l) {
-      const int64_t off = l == 0 ? (int64_t)W * NIN : (int64_t)W * NIN + W + (int64_t)(l - 1) * (W * W + W) + W * W;
-      for (int o = tid; o < W; o += kTile) sb[l * W + o] = __ldg(net.p32 + off + o);
-    }
     const int64_t hoff = net_param_count(NIN, W, L) - W - 1;
     for (int o = tid; o <= W; o += kTile) swh[o] = __ldg(net.p32 + hoff + o);
-    for (int i = tid; i < 3 * (NIN / 2); i += kTile) sq[i] = __ldg(net.q + i);
+    for (int i = tid; i < 3 * M; i += kTile) sq[i] = __ldg(net.q + i);
+    __syncthreads();
+    if (job.mode == MODE_L0) {
+      for (int i = tid; i < M * 64; i += kTile) {
+        const int f = i >> 6, j = i & 63;
+        const uint32_t ph = sq[3 * f + 1] * (uint32_t)(j >> 3) + sq[3 * f + 2] * (uint32_t)(j & 7);
+        float sn, cs;
+        sincospif((float)(int32_t)ph * 0x1p-31f, &sn, &cs);
+        if (MODE == TC_FP16) sTh[i] = __floats2half2_rn(cs, sn);
+        else sT[i] = make_float2(cs, sn);
+      }
+    }
   }
   if (tid == 0) mbar_init(bar, 1);
-  if (warp == 0) tmem_alloc(tslot, kTmemCols);
+  if (warp == 0) tmem_alloc(tslot, C::COLS);
   fence_proxy_async_smem();
   tc_fence_before();
   __syncthreads();
@@ -302,25 +324,64 @@ __global__ void __launch_bounds__(kTile, 1) mlp_tc_kernel(NetView net, EvalJob j
   if (job.n_dev) job.n_items = *job.n_dev;
   const int64_t ntiles = job_tiles(job.mode, job.n_items);
   for (int64_t t = blockIdx.x; t < ntiles && !failed; t += gridDim.x) {
-    int cx, cy, cz;
-    const bool valid = job_coord(job, t, tid, cx, cy, cz);
-    encode_tc_row<NIN, MODE>(sa, sa_lo, tid, sq, cx, cy, cz);
-    fence_proxy_async_smem();
+    // ---- encoding -> A operand (layer 0) in TMEM
+    bool valid = true;
+    {
+      float z[NIN];
+      if (job.mode == MODE_L0) {
+        // angle addition: e^{i Phi(v)} = e^{i Phi(origin + dx e_x)} * e^{i Phi(dy e_y + dz e_z)}
+        const int4 o = __ldg(job.nodes + (t >> 2));
+        const int dx0 = 2 * (int)(t & 3);
+        if (tid < 2 * M) {
+          const int dxl = tid / M, f = tid % M;
+          const uint32_t ph = sq[3 * f] * (uint32_t)(o.x - job.ox + dx0 + dxl) + sq[3 * f + 1] * (uint32_t)(o.y - job.oy) +
+                              sq[3 * f + 2] * (uint32_t)(o.z - job.oz);
+          float sn, cs;
+          sincospif((float)(int32_t)ph * 0x1p-31f, &sn, &cs);
+          sP[tid] = make_float2(cs, sn);
+        }
+        __syncthreads();
+        const float2* P = sP + (tid >> 6) * M;
+#pragma unroll
+        for (int f = 0; f < M; ++f) {
+          const float2 p = P[f];
+          const float2 q = MODE == TC_FP16 ? __half22float2(sTh[f * 64 + (tid & 63)]) : sT[f * 64 + (tid & 63)];
+          z[f] = fmaf(p.x, q.x, -p.y * q.y);
+          z[M + f] = fmaf(p.x, q.y, p.y * q.x);
+        }
+      } else {
+        int cx, cy, cz;
+        valid = job_coord(job, t, tid, cx, cy, cz);
+#pragma unroll
+        for (int f = 0; f < M; ++f) {
+          const uint32_t ph = ffm_phase(sq, f, cx, cy, cz);
+          if (MODE == TC_FP16)
+            __sincosf((float)(int32_t)ph * 1.4629180792671596e-09f, &z[M + f], &z[f]);   // pi / 2^31
+          else
+            sincospif((float)(int32_t)ph * 0x1p-31f, &z[M + f], &z[f]);
+        }
+      }
+      uint32_t hi[NIN / 2], lo[NIN / 2];
+#pragma unroll
+      for (int p = 0; p < NIN / 2; ++p) split_pair<MODE>(z[2 * p], z[2 * p + 1], hi[p], lo[p]);
+      store_a_row<NIN, MODE>(tlane, hi, lo);
+    }
+    tmem_st_wait();
+    tc_fence_before();
     __syncthreads();
     float y = 0.f;
     for (int l = 0; l < L; ++l) {
-      const int K = l == 0 ? NIN : W;
+      const int K = l == 0 ? C::K0 : C::KH;
       if (tid == 0) {
         tc_fence_after();
-        const uint32_t woff = l == 0 ? 0u : (uint32_t)(W * NIN + (l - 1) * W * W) * 2u;
-        const uint32_t a0 = smem_u32(sa), b0 = smem_u32(sw) + woff;
+        const uint32_t woff = l == 0 ? 0u : (uint32_t)(W * C::K0 + (l - 1) * W * C::KH) * 2u;
+        const uint32_t b0 = smem_u32(sw) + woff, bl = smem_u32(sw_lo) + woff;
         for (int ks = 0; ks < K / 16; ++ks) {
-          mma_f16kind(tbase, smem_desc(a0 + ks * 256, 128, K * 16), smem_desc(b0 + ks * 256, 128, K * 16), idesc,
-                      ks > 0 ? 1u : 0u);
+          const uint64_t bd = smem_desc(b0 + ks * 256, 128, K * 16);
+          mma_f16kind_ts(tbase, tbase + C::A_HI + ks * 8, bd, idesc, ks > 0 ? 1u : 0u);
           if (MODE == TC_BF16X3) {
-            const uint32_t al = smem_u32(sa_lo), bl = smem_u32(sw_lo) + woff;
-            mma_f16kind(tbase, smem_desc(al + ks * 256, 128, K * 16), smem_desc(b0 + ks * 256, 128, K * 16), idesc, 1u);
-            mma_f16kind(tbase, smem_desc(a0 + ks * 256, 128, K * 16), smem_desc(bl + ks * 256, 128, K * 16), idesc, 1u);
+            mma_f16kind_ts(tbase, tbase + C::A_LO + ks * 8, bd, idesc, 1u);
+            mma_f16kind_ts(tbase, tbase + C::A_HI + ks * 8, smem_desc(bl + ks * 256, 128, K * 16), idesc, 1u);
           }
         }
         mma_commit(bar);
@@ -329,28 +390,23 @@ __global__ void __launch_bounds__(kTile, 1) mlp_tc_kernel(NetView net, EvalJob j
       phase ^= 1u;
       if (__syncthreads_or(!ok)) { failed = true; break; }
       tc_fence_after();
-      float acc[W];
-      tmem_ld32(tlane, acc);
-      if (W == 64) tmem_ld32(tlane + 32, acc + 32);
-      const float* b = sb + l * W;
+      uint32_t accu[W];
+      tmem_ld32_nowait(tlane, accu);
+      if (W == 64) tmem_ld32_nowait(tlane + 32, accu + 32);
+      tmem_ld_wait();
       if (l < L - 1) {
+        uint32_t hi[W / 2], lo[W / 2];
 #pragma unroll
-        for (int g = 0; g < W / 8; ++g) {
-          float v[8];
-#pragma unroll
-          for (int e = 0; e < 8; ++e) v[e] = fmaxf(acc[8 * g + e] + b[8 * g + e], 0.f);
-          uint4 hi, lo;
-          pack8<MODE>(v, hi, lo);
-          *reinterpret_cast<uint4*>(sa + canon_off(tid, 8 * g, W)) = hi;
-          if (MODE == TC_BF16X3) *reinterpret_cast<uint4*>(sa_lo + canon_off(tid, 8 * g, W)) = lo;
-        }
+        for (int p = 0; p < W / 2; ++p)
+          relu_pair<MODE>(__uint_as_float(accu[2 * p]), __uint_as_float(accu[2 * p + 1]), hi[p], lo[p]);
+        store_a_row<W, MODE>(tlane, hi, lo);
+        tmem_st_wait();
       } else {
         y = bh;
 #pragma unroll
-        for (int c = 0; c < W; ++c) y = fmaf(swh[c], fmaxf(acc[c] + b[c], 0.f), y);
+        for (int c = 0; c < W; ++c) y = fmaf(swh[c], fmaxf(__uint_as_float(accu[c]), 0.f), y);
       }
       tc_fence_before();
-      fence_proxy_async_smem();
       __syncthreads();
     }
     if (failed) break;
@@ -360,29 +416,30 @@ __global__ void __launch_bounds__(kTile, 1) mlp_tc_kernel(NetView net, EvalJob j
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (warp == 0) tmem_dealloc(tbase, kTmemCols);
+  if (warp == 0) tmem_dealloc(tbase, C::COLS);
 }
 
 // FP32 master weights -> FP16 tiles, BF16 hi tiles and BF16 lo tiles in the
-// canonical K-major layout (layer 0: [W x n_in], layers 1..L-1: [W x W]).
+// canonical K-major layout: layer 0 [W x (n_in+16)], layers 1..L-1 [W x (W+16)];
+// column K of a layer's tile is its bias, the 15 columns after it are zero.
 __global__ void pack_weights_kernel(const float* p32, uint8_t* wpk, int nin, int W, int L) {
-  const int64_t first = (int64_t)W * nin;
   const int64_t total = wtile_elems(nin, W, L);
+  const int64_t first = (int64_t)W * (nin + 16);
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    float v;
-    size_t off;
+    int l, K, o, i;
+    size_t base;
     if (e < first) {
-      const int o = (int)(e / nin), i = (int)(e % nin);
-      v = p32[e];
-      off = canon_off(o, i, nin);
+      l = 0; K = nin; o = (int)(e / (nin + 16)); i = (int)(e % (nin + 16)); base = 0;
     } else {
       const int64_t r = e - first;
-      const int l = 1 + (int)(r / ((int64_t)W * W));
-      const int rr = (int)(r % ((int64_t)W * W));
-      const int o = rr / W, i = rr % W;
-      v = p32[first + W + (int64_t)(l - 1) * (W * W + W) + rr];
-      off = (size_t)first * 2 + (size_t)(l - 1) * W * W * 2 + canon_off(o, i, W);
+      l = 1 + (int)(r / ((int64_t)W * (W + 16)));
+      const int rr = (int)(r % ((int64_t)W * (W + 16)));
+      K = W; o = rr / (W + 16); i = rr % (W + 16);
+      base = (size_t)first * 2 + (size_t)(l - 1) * W * (W + 16) * 2;
     }
+    const int64_t woff = l == 0 ? 0 : (int64_t)W * nin + W + (int64_t)(l - 1) * (W * W + W);
+    const float v = i < K ? p32[woff + (int64_t)o * K + i] : (i == K ? p32[woff + (int64_t)W * K + o] : 0.f);
+    const size_t off = base + canon_off(o, i, K + 16);
     const __nv_bfloat16 hi = __float2bfloat16_rn(v);
     *reinterpret_cast<__half*>(wpk + off) = __float2half_rn(v);
     *reinterpret_cast<__nv_bfloat16*>(wpk + total * 2 + off) = hi;

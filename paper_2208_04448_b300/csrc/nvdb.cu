@@ -362,7 +362,7 @@ nvdb_status launch_tc(const NetView& nv, const EvalJob& job, int64_t ntiles, con
   const int regs = std::max(8, (fa.numRegs + 7) & ~7);
   const int by_regs = 65536 / (regs * kTile);
   const int by_smem = (int)(kSmemPerSm / (lay.total + 1024));
-  const int occ = std::min({by_regs, by_smem, (int)(512 / kTmemCols), 8});
+  const int occ = std::min({by_regs, by_smem, TcCfg<NIN, W, MODE>::MAXC});
   if (occ < 1) return fail(NVDB_ERR_UNSUPPORTED, "tensor-core kernel does not fit on an SM");
   const int64_t grid = std::min<int64_t>(ntiles, (int64_t)num_sms() * occ);
   KLAUNCH(eval_name(base, job.mode), s,
