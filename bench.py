@@ -290,20 +290,39 @@ def main():
 
     by_prec = {}
     head_prec = PRECS[args.prec]
+    kern_by_prec = {}
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
         for name, p in PRECS.items():
-            ms, launches, kern = timed(p, args.steps, profile=(p == head_prec))
+            ms, launches, kern = timed(p, args.steps, profile=True)
             by_prec[name] = dict(ms_per_step=float(np.mean(ms)), voxels_per_s=n_active / (np.mean(ms) / 1e3),
                                  launches_per_step=launches / args.steps)
+            kern_by_prec[name] = kern
             if p == head_prec:
                 head_ms, head_launches, head_kern = ms, launches, kern
     torch.cuda.synchronize()
     for name, p in PRECS.items():
         by_prec[name]["max_abs_err_vs_oracle"] = decode_error(p)
         by_prec[name]["err_bound"] = 0.02 * 3.0
+
+    # ---- point queries (Section 3.5 random access): 2^22 points uniform in occupied level-1 nodes
+    from fixtures import query_points
+    qpts = query_points(ijk, 1 << 22, seed=5).cuda().contiguous()
+    qout = torch.empty(qpts.shape[0], dtype=torch.float32, device="cuda")
+    query = {}
+    for name, p in PRECS.items():
+        for _ in range(2):
+            nv.query(model, qpts, p, out=qout)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(5):
+            nv.query(model, qpts, p, out=qout)
+        b.record(stream)
+        b.synchronize()
+        query[name] = dict(points_per_s=5 * qpts.shape[0] / (a.elapsed_time(b) / 1e3))
 
     mean_ms = float(np.mean(head_ms))
     if dist is not None:
@@ -312,22 +331,27 @@ def main():
         mean_ms = float(t.item())
     value = world * n_active / (mean_ms / 1e3)
 
-    # ---- roofline of the dominant kernel (live CUDA events on the launching stream)
+    # ---- roofline of the dominant network kernel (live CUDA events on the launching stream)
     peaks = measured_peaks()
-    mlp = {k: v for k, v in head_kern.items() if k.startswith("mlp_") and "." in k}
-    dname, (dl, dms) = max(mlp.items(), key=lambda kv: kv[1][1])
-    n0, w1, L1 = FFM[1], NET_WIDTH[1], NET_LAYERS[1]
-    per_launch = {"L0": n_leaf * 512 * flops_per_eval(FFM[1], NET_WIDTH[1], NET_LAYERS[1]),
-                  "L1": n_l1 * 4096 * flops_per_eval(FFM[0], NET_WIDTH[0], NET_LAYERS[0]),
-                  "list": n_active * flops_per_eval(FFM[1], NET_WIDTH[2], NET_LAYERS[2])}[dname.split(".")[1]]
-    avg_s = dms / dl / 1e3
-    achieved = per_launch / avg_s / 1e12
-    if dname.startswith("mlp_f32"):
-        peak = 148 * 128 * 2 * peaks.get("sm_max_mhz", 2032.0) * 1e6 / 1e12
-        bound, peak_src = "alu", "derived: 148 SMs x 128 FFMA/clk x 2 x max SM clock"
-    else:
-        peak = peaks["bf16_tflops"]
-        bound, peak_src = "tensor", f"{peaks['source']} bf16 burst (16-bit kind::f16 rate)"
+
+    def roofline(kern):
+        mlp = {k: v for k, v in kern.items() if k.startswith("mlp_") and "." in k}
+        name, (nl, tms) = max(mlp.items(), key=lambda kv: kv[1][1])
+        per = {"L0": n_leaf * 512 * flops_per_eval(FFM[1], NET_WIDTH[1], NET_LAYERS[1]),
+               "L1": n_l1 * 4096 * flops_per_eval(FFM[0], NET_WIDTH[0], NET_LAYERS[0]),
+               "list": n_active * flops_per_eval(FFM[1], NET_WIDTH[2], NET_LAYERS[2])}[name.split(".")[1]]
+        ach = per / (tms / nl / 1e3) / 1e12
+        if name.startswith("mlp_f32"):
+            pk = 148 * 128 * 2 * peaks.get("sm_max_mhz", 2032.0) * 1e6 / 1e12
+            bd, src = "alu", "derived: 148 SMs x 128 FFMA/clk x 2 x max SM clock"
+        else:
+            pk = peaks["bf16_tflops"]
+            bd, src = "tensor", f"{peaks['source']} bf16 burst (16-bit kind::f16 rate)"
+        return dict(kernel=name, bound=bd, achieved=ach, peak=pk, unit="TFLOP/s", frac=ach / pk,
+                    flops_per_launch=per, avg_launch_ms=tms / nl, peak_source=src)
+
+    rl = roofline(head_kern)
+    dname = rl["kernel"]
     traffic = None
     tfile = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(tfile):
@@ -368,9 +392,9 @@ def main():
         config=dict(workload=WORKLOAD_DESC, n_active=n_active, n_leaf=n_leaf, n_l1=n_l1,
                     precision=args.prec, l2="flushed (256 MB write) between timed steps; output 16 B/voxel",
                     parallelism="replicas only" if world > 1 else "1 GPU"),
-        roofline=dict(kernel=dname, bound=bound, achieved=achieved, peak=peak, unit="TFLOP/s",
-                      frac=achieved / peak, traffic=traffic, flops_per_launch=per_launch,
-                      avg_launch_ms=dms / dl, peak_source=peak_src),
+        roofline=dict(rl, traffic=traffic),
+        roofline_by_precision={k: roofline(v) for k, v in kern_by_prec.items()},
+        query=query,
         cpu_baseline=cpu,
         e2e=dict(value=e2e_value, unit="voxels/s", h2d_bytes_per_step=len(blob_bytes),
                  d2h_bytes_per_step=16 * n_active),

@@ -104,6 +104,76 @@ __global__ void patch_count_kernel(uint32_t* words, int wpi, int64_t n_items, co
   counts[it] = c;
 }
 
+// Warp-per-item variant of patch_count_kernel: the item's words are staged in
+// shared memory, the patches are applied with shared-memory atomicXor (a
+// candidate appears at most once per list, so the result does not depend on
+// the order), the words are written back and counted.  8 warps per block;
+// wpi <= 128.
+__global__ void __launch_bounds__(256) patch_count_warp_kernel(uint32_t* words, int wpi, int64_t n_items,
+                                                              const uint32_t* poff, const uint16_t* pidx,
+                                                              uint32_t* counts) {
+  __shared__ uint32_t sw[8][128];
+  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t it = (int64_t)blockIdx.x * 8 + wib;
+  if (it >= n_items) return;
+  uint32_t* w = words + it * wpi;
+  for (int i = lane; i < wpi; i += 32) sw[wib][i] = w[i];
+  __syncwarp();
+  if (poff) {
+    for (uint32_t p = poff[it] + lane; p < poff[it + 1]; p += 32) {
+      const uint32_t b = pidx[p];
+      atomicXor(&sw[wib][b >> 5], 1u << (b & 31));
+    }
+  }
+  __syncwarp();
+  uint32_t c = 0;
+  for (int i = lane; i < wpi; i += 32) {
+    const uint32_t v = sw[wib][i];
+    w[i] = v;
+    c += __popc(v);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if (lane == 0) counts[it] = c;
+}
+
+// Rank-parallel variant of emit_voxels_kernel: lane l writes the voxels of rank
+// l, l+32, ... of its leaf, so consecutive lanes write consecutive outputs.
+__global__ void __launch_bounds__(256) emit_voxels_rank_kernel(const uint32_t* words, const int4* leaf_origin,
+                                                              int64_t n_leaf, const int64_t* off, int32_t* ijk,
+                                                              int64_t cap, uint32_t* status) {
+  __shared__ uint32_t sw[8][16], spre[8][17];
+  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t leaf = (int64_t)blockIdx.x * 8 + wib;
+  if (leaf >= n_leaf) return;
+  const uint32_t b = lane < 16 ? words[leaf * 16 + lane] : 0u;
+  int64_t tot;
+  const int64_t ex = warp_excl_scan(__popc(b), lane, tot);
+  if (lane < 16) { sw[wib][lane] = b; spre[wib][lane] = (uint32_t)ex; }
+  if (lane == 0) spre[wib][16] = (uint32_t)tot;
+  __syncwarp();
+  const int4 o = leaf_origin[leaf];
+  const int64_t base = off[leaf];
+  bool over = false;
+  for (int r = lane; r < (int)tot; r += 32) {
+    int k = 0;
+#pragma unroll
+    for (int step = 8; step > 0; step >>= 1)
+      if (spre[wib][k + step] <= (uint32_t)r) k += step;
+    const int bit = __fns(sw[wib][k], 0, r - (int)spre[wib][k] + 1);
+    const int v = k * 32 + bit;
+    const int64_t pos = base + r;
+    if (pos < cap) {
+      ijk[3 * pos] = o.x + (v >> 6);
+      ijk[3 * pos + 1] = o.y + ((v >> 3) & 7);
+      ijk[3 * pos + 2] = o.z + (v & 7);
+    } else {
+      over = true;
+    }
+  }
+  if (over) set_status(status, ST_CAPACITY);
+}
+
 // Level-1 child words -> leaf origins in canonical order.  One warp per node,
 // lane l owns words 4l..4l+3 (bits in slot order).
 __global__ void emit_leaves_kernel(const uint32_t* words, const int4* l1_origin, int64_t n_l1,

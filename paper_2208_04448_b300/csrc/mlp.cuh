@@ -324,10 +324,12 @@ __global__ void __launch_bounds__(kTile, 1) mlp_tc_kernel(NetView net, EvalJob j
   if (job.n_dev) job.n_items = *job.n_dev;
   const int64_t ntiles = job_tiles(job.mode, job.n_items);
   for (int64_t t = blockIdx.x; t < ntiles && !failed; t += gridDim.x) {
-    // ---- encoding -> A operand (layer 0) in TMEM
+    // ---- encoding -> A operand (layer 0) in TMEM.  Inside this kernel the features are
+    // ordered (cos_0, sin_0, cos_1, sin_1, ...): packed column f holds frequency f; the
+    // first-layer weight tile is packed with the matching column order.
     bool valid = true;
     {
-      float z[NIN];
+      uint32_t hi[NIN / 2], lo[NIN / 2];
       if (job.mode == MODE_L0) {
         // angle addition: e^{i Phi(v)} = e^{i Phi(origin + dx e_x)} * e^{i Phi(dy e_y + dz e_z)}
         const int4 o = __ldg(job.nodes + (t >> 2));
@@ -342,28 +344,38 @@ __global__ void __launch_bounds__(kTile, 1) mlp_tc_kernel(NetView net, EvalJob j
         }
         __syncthreads();
         const float2* P = sP + (tid >> 6) * M;
+        if (MODE == TC_FP16) {
+          // complex product in half2: (pc, pc) * (tc, ts) + (ps, ps) * (-ts, tc) = (cos, sin)
 #pragma unroll
-        for (int f = 0; f < M; ++f) {
-          const float2 p = P[f];
-          const float2 q = MODE == TC_FP16 ? __half22float2(sTh[f * 64 + (tid & 63)]) : sT[f * 64 + (tid & 63)];
-          z[f] = fmaf(p.x, q.x, -p.y * q.y);
-          z[M + f] = fmaf(p.x, q.y, p.y * q.x);
+          for (int f = 0; f < M; ++f) {
+            const float2 p = P[f];
+            const __half2 q = sTh[f * 64 + (tid & 63)];
+            const uint32_t qs = __byte_perm(*reinterpret_cast<const uint32_t*>(&q), 0, 0x1032) ^ 0x00008000u;
+            const __half2 z = __hfma2(__float2half2_rn(p.y), *reinterpret_cast<const __half2*>(&qs),
+                                      __hmul2(__float2half2_rn(p.x), q));
+            hi[f] = *reinterpret_cast<const uint32_t*>(&z);
+            lo[f] = 0u;
+          }
+        } else {
+#pragma unroll
+          for (int f = 0; f < M; ++f) {
+            const float2 p = P[f], q = sT[f * 64 + (tid & 63)];
+            split_pair<MODE>(fmaf(p.x, q.x, -p.y * q.y), fmaf(p.x, q.y, p.y * q.x), hi[f], lo[f]);
+          }
         }
       } else {
         int cx, cy, cz;
         valid = job_coord(job, t, tid, cx, cy, cz);
+        // MUFU sin/cos of the exact phase mapped to [-pi, pi): absolute error ~4e-7,
+        // below the 16-bit operand rounding of both modes
 #pragma unroll
         for (int f = 0; f < M; ++f) {
           const uint32_t ph = ffm_phase(sq, f, cx, cy, cz);
-          if (MODE == TC_FP16)
-            __sincosf((float)(int32_t)ph * 1.4629180792671596e-09f, &z[M + f], &z[f]);   // pi / 2^31
-          else
-            sincospif((float)(int32_t)ph * 0x1p-31f, &z[M + f], &z[f]);
+          float sn, cs;
+          __sincosf((float)(int32_t)ph * 1.4629180792671596e-09f, &sn, &cs);   // pi / 2^31
+          split_pair<MODE>(cs, sn, hi[f], lo[f]);
         }
       }
-      uint32_t hi[NIN / 2], lo[NIN / 2];
-#pragma unroll
-      for (int p = 0; p < NIN / 2; ++p) split_pair<MODE>(z[2 * p], z[2 * p + 1], hi[p], lo[p]);
       store_a_row<NIN, MODE>(tlane, hi, lo);
     }
     tmem_st_wait();
@@ -388,7 +400,6 @@ __global__ void __launch_bounds__(kTile, 1) mlp_tc_kernel(NetView net, EvalJob j
       }
       const bool ok = mbar_wait_bounded(bar, phase);
       phase ^= 1u;
-      if (__syncthreads_or(!ok)) { failed = true; break; }
       tc_fence_after();
       uint32_t accu[W];
       tmem_ld32_nowait(tlane, accu);
@@ -407,7 +418,7 @@ __global__ void __launch_bounds__(kTile, 1) mlp_tc_kernel(NetView net, EvalJob j
         for (int c = 0; c < W; ++c) y = fmaf(swh[c], fmaxf(__uint_as_float(accu[c]), 0.f), y);
       }
       tc_fence_before();
-      __syncthreads();
+      if (__syncthreads_or(!ok)) { failed = true; break; }   // all threads agree on a timeout
     }
     if (failed) break;
     job_output(job, t, tid, valid, y);
@@ -438,7 +449,10 @@ __global__ void pack_weights_kernel(const float* p32, uint8_t* wpk, int nin, int
       base = (size_t)first * 2 + (size_t)(l - 1) * W * (W + 16) * 2;
     }
     const int64_t woff = l == 0 ? 0 : (int64_t)W * nin + W + (int64_t)(l - 1) * (W * W + W);
-    const float v = i < K ? p32[woff + (int64_t)o * K + i] : (i == K ? p32[woff + (int64_t)W * K + o] : 0.f);
+    // layer 0: packed column i holds feature (i even: cos_{i/2}, i odd: sin_{i/2}),
+    // i.e. column i/2 or nin/2 + i/2 of W_0
+    const int src = (l == 0 && i < K) ? ((i & 1) ? nin / 2 + (i >> 1) : (i >> 1)) : i;
+    const float v = i < K ? p32[woff + (int64_t)o * K + src] : (i == K ? p32[woff + (int64_t)W * K + o] : 0.f);
     const size_t off = base + canon_off(o, i, K + 16);
     const __nv_bfloat16 hi = __float2bfloat16_rn(v);
     *reinterpret_cast<__half*>(wpk + off) = __float2half_rn(v);

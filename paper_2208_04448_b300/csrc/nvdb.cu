@@ -859,8 +859,8 @@ nvdb_status decode_topology(nvdb_model* m, const PatchSet* ps, nvdb_precision pr
   j1.words = d.l1_words;
   TRY(launch_eval(m, 0, prec, j1, s));
   if (m->n_l1)
-    KLAUNCH("patch_count", s, patch_count_kernel<<<blocks_for(m->n_l1, 128), 128, 0, s>>>(d.l1_words, 128, m->n_l1, ps->d_l1_off, ps->d_l1_idx,
-                                                               d.l1_counts));
+    KLAUNCH("patch_count", s, patch_count_warp_kernel<<<blocks_for(m->n_l1, 8), 256, 0, s>>>(d.l1_words, 128, m->n_l1,
+                                                                ps->d_l1_off, ps->d_l1_idx, d.l1_counts));
   TRY(m->scan.run(d.l1_counts, m->n_l1, d.l1_off, s));
   KLAUNCH("check_total", s, check_total_kernel<<<1, 1, 0, s>>>(m->scan.total, m->n_leaf, m->status));
   if (m->n_l1)
@@ -873,8 +873,8 @@ nvdb_status decode_topology(nvdb_model* m, const PatchSet* ps, nvdb_precision pr
   j0.words = d.leaf_words;
   TRY(launch_eval(m, 1, prec, j0, s));
   if (m->n_leaf)
-    KLAUNCH("patch_count", s, patch_count_kernel<<<blocks_for(m->n_leaf, 128), 128, 0, s>>>(d.leaf_words, 16, m->n_leaf, ps->d_l0_off,
-                                                                 ps->d_l0_idx, d.leaf_counts));
+    KLAUNCH("patch_count", s, patch_count_warp_kernel<<<blocks_for(m->n_leaf, 8), 256, 0, s>>>(d.leaf_words, 16, m->n_leaf,
+                                                                  ps->d_l0_off, ps->d_l0_idx, d.leaf_counts));
   TRY(m->scan.run(d.leaf_counts, m->n_leaf, d.leaf_off, s));
   KLAUNCH("check_total", s, check_total_kernel<<<1, 1, 0, s>>>(m->scan.total, m->n_active, m->status));
   CU(cudaGetLastError());
@@ -904,9 +904,9 @@ extern "C" nvdb_status nvdb_decompress(const nvdb_model* const* models, int n_mo
     TRY(decode_topology(m, m->patch_set(prec), prec, s));
     DecodeScratch& d = m->ds;
     if (m->n_leaf)
-      KLAUNCH("emit_voxels", s, emit_voxels_kernel<<<blocks_for(m->n_leaf * 32, 256), 256, 0, s>>>(d.leaf_words, d.leaf_origin, m->n_leaf,
-                                                                        d.leaf_off, d_ijk + 3 * base, m->n_active,
-                                                                        m->status));
+      KLAUNCH("emit_voxels", s, emit_voxels_rank_kernel<<<blocks_for(m->n_leaf, 8), 256, 0, s>>>(d.leaf_words, d.leaf_origin,
+                                                                  m->n_leaf, d.leaf_off, d_ijk + 3 * base, m->n_active,
+                                                                  m->status));
     EvalJob jr{};
     jr.mode = MODE_LIST;
     jr.ijk = d_ijk + 3 * base;
