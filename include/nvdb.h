@@ -157,6 +157,26 @@ nvdb_status nvdb_decompress(const nvdb_model* const* models, int n_models, nvdb_
                             int32_t* d_ijk, float* d_val, int64_t capacity, int64_t* counts,
                             nvdb_stream stream);
 
+/* Decode plan: the whole nvdb_decompress of `models` into the given output
+ * buffers, recorded once into a CUDA graph (the benchmark spec: batched, graph-captured
+ * decode).  Models with the same network shapes are decoded together, up to 48
+ * per launch of each stage (levels, chunks and frames of several models share
+ * one launch).  Building the plan runs the decode several times to pick the
+ * number of tensor-core CTAs per SM (the autotuner; 0 = the kernel's own
+ * limit), then captures it on `stream`.  The outputs are overwritten by every
+ * launch.  Synchronises the stream. */
+typedef struct nvdb_plan nvdb_plan;
+nvdb_status nvdb_decompress_plan(const nvdb_model* const* models, int n_models, nvdb_precision prec,
+                                 int32_t* d_ijk, float* d_val, int64_t capacity, nvdb_stream stream,
+                                 nvdb_plan** out);
+/* Replay the plan on `stream` (does not synchronise). */
+nvdb_status nvdb_plan_launch(nvdb_plan* plan, nvdb_stream stream);
+/* Synchronise `stream` and report device-detected errors of the last launch. */
+nvdb_status nvdb_plan_check(nvdb_plan* plan, nvdb_stream stream);
+/* Tuning result: tensor-core CTAs per SM chosen (0 = limit) and its decode time. */
+nvdb_status nvdb_plan_info(const nvdb_plan* plan, int* tc_ctas_per_sm, float* tuned_ms);
+nvdb_status nvdb_plan_free(nvdb_plan* plan);
+
 /* Random access on [Hash,5,4,NN(3)] (Section 3.5, online random access): for
  * each point p (float32 [n][3], index space) the 8 corners of the cell
  * floor(p) are looked up in the explicit topology (decoded once and cached in

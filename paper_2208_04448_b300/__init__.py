@@ -169,6 +169,45 @@ def decompress(models, prec: int = FP32, out=None, stream=None):
     return ijk[:total], val[:total], list(counts)
 
 
+class Plan:
+    """A graph-captured decode of fixed models into fixed output buffers (nvdb_plan)."""
+
+    def __init__(self, handle, models, ijk, val):
+        self._h, self._keep = handle, (models, ijk, val)   # keep models and outputs alive
+        self.ijk, self.val = ijk, val
+
+    def launch(self, stream=None):
+        _check(lib().nvdb_plan_launch(self._h, _stream(stream)))
+
+    def check(self, stream=None):
+        _check(lib().nvdb_plan_check(self._h, _stream(stream)))
+
+    def info(self) -> dict:
+        occ, ms = C.c_int(), C.c_float()
+        _check(lib().nvdb_plan_info(self._h, C.byref(occ), C.byref(ms)))
+        return dict(tc_ctas_per_sm=occ.value, tuned_ms=ms.value)
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.nvdb_plan_free(self._h)
+            self._h = None
+
+
+def decompress_plan(models, prec: int = FP32, stream=None) -> Plan:
+    if isinstance(models, Model):
+        models = [models]
+    arr = (C.c_void_p * len(models))(*[m.handle for m in models])
+    counts = (C.c_int64 * len(models))()
+    _check(lib().nvdb_decompress(arr, len(models), prec, None, None, 0, counts, _stream(stream)))
+    total = sum(counts)
+    ijk = torch.empty((total, 3), dtype=torch.int32, device="cuda")
+    val = torch.empty(total, dtype=torch.float32, device="cuda")
+    h = C.c_void_p()
+    _check(lib().nvdb_decompress_plan(arr, len(models), prec, _dptr(ijk, torch.int32, "ijk"),
+                                      _dptr(val, torch.float32, "val"), total, _stream(stream), C.byref(h)))
+    return Plan(h, list(models), ijk, val)
+
+
 def query(model: Model, xyz: torch.Tensor, prec: int = FP32, active: bool = False, out=None, stream=None):
     n = xyz.shape[0]
     res = out if out is not None else torch.empty(n, dtype=torch.float32, device="cuda")

@@ -301,4 +301,107 @@ __global__ void emit_patches_kernel(const uint32_t* mis, int wpi, int64_t n_item
   }
 }
 
+// ---------------------------------------------------------------- batched forms
+// Per-model tables passed by value; item g of the concatenation belongs to the
+// last model whose `start` is <= g.
+constexpr int kMaxBatchC = 48;
+
+template <class T>
+__device__ __forceinline__ int find_item(const T* it, int n, int64_t g) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (it[mid].start <= g) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+struct L2Item {
+  const uint64_t* mask;   // [n_l2][512] of this model
+  const int4* origin;     // [n_l2]
+  int64_t start;          // first level-2 node of this model in the concatenation
+};
+struct L2Batch {
+  int n;
+  L2Item it[kMaxBatchC];
+};
+
+struct PatchItem {
+  const uint32_t* off;    // CSR offsets of this model's patch list (level 1 or level 0)
+  const uint16_t* idx;
+  int64_t start;          // first item (node / leaf) of this model in the concatenation
+};
+struct PatchBatch {
+  int n;
+  PatchItem it[kMaxBatchC];
+};
+
+// Level-2 child-mask popcounts, one block (512 threads) per level-2 node of any model.
+__global__ void l2_count_batch_kernel(const __grid_constant__ L2Batch b, uint32_t* counts) {
+  __shared__ int64_t sh[33];
+  const int64_t g = blockIdx.x;
+  const int m = find_item(b.it, b.n, g);
+  const int64_t c = __popcll(b.it[m].mask[(g - b.it[m].start) * 512 + threadIdx.x]);
+  int64_t tot;
+  block_excl_scan(c, sh, tot);
+  if (threadIdx.x == 0) counts[g] = (uint32_t)tot;
+}
+
+// Level-1 node origins of all models, concatenated in model order, canonical within.
+__global__ void l2_emit_batch_kernel(const __grid_constant__ L2Batch b, const int64_t* off, int4* l1_origin,
+                                     int64_t cap, uint32_t* status) {
+  __shared__ int64_t sh[33];
+  const int64_t g = blockIdx.x;
+  const int m = find_item(b.it, b.n, g);
+  const int64_t local = g - b.it[m].start;
+  uint64_t w = b.it[m].mask[local * 512 + threadIdx.x];
+  int64_t tot;
+  int64_t pos = off[g] + block_excl_scan(__popcll(w), sh, tot);
+  const int4 o = b.it[m].origin[local];
+  bool over = false;
+  while (w) {
+    const int bit = __ffsll((long long)w) - 1;
+    w &= w - 1;
+    const int s = threadIdx.x * 64 + bit;
+    if (pos < cap)
+      l1_origin[pos] = make_int4(o.x + 128 * (s >> 10), o.y + 128 * ((s >> 5) & 31), o.z + 128 * (s & 31), 0);
+    else
+      over = true;
+    ++pos;
+  }
+  if (over) set_status(status, ST_CORRUPT);
+}
+
+// patch_count_warp_kernel over the concatenated items of several models.
+__global__ void __launch_bounds__(256) patch_count_batch_kernel(uint32_t* words, int wpi, int64_t n_items,
+                                                               const __grid_constant__ PatchBatch b,
+                                                               uint32_t* counts) {
+  __shared__ uint32_t sw[8][128];
+  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t g = (int64_t)blockIdx.x * 8 + wib;
+  if (g >= n_items) return;
+  const int m = find_item(b.it, b.n, g);
+  const int64_t local = g - b.it[m].start;
+  uint32_t* w = words + g * wpi;
+  for (int i = lane; i < wpi; i += 32) sw[wib][i] = w[i];
+  __syncwarp();
+  const uint32_t* poff = b.it[m].off;
+  if (poff) {
+    for (uint32_t p = poff[local] + lane; p < poff[local + 1]; p += 32) {
+      const uint32_t bit = b.it[m].idx[p];
+      atomicXor(&sw[wib][bit >> 5], 1u << (bit & 31));
+    }
+  }
+  __syncwarp();
+  uint32_t c = 0;
+  for (int i = lane; i < wpi; i += 32) {
+    const uint32_t v = sw[wib][i];
+    w[i] = v;
+    c += __popc(v);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if (lane == 0) counts[g] = c;
+}
+
 }  // namespace nvdb

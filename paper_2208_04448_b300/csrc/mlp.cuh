@@ -84,6 +84,41 @@ __device__ __forceinline__ void job_output(const EvalJob& j, int64_t t, int r, b
   }
 }
 
+// A batch of evaluations with the same network shape (e.g. the same level of
+// many animation frames), passed by value as the kernel parameter.  Item m owns
+// the global tiles [tile_start, tile_start + job_tiles(mode, n_items)); a
+// persistent CTA restages the network only when it crosses into another item.
+constexpr int kMaxBatch = 48;
+
+struct EvalItem {
+  NetView net;
+  EvalJob job;
+  int64_t tile_start;
+};
+
+struct EvalBatch {
+  int n;
+  EvalItem it[kMaxBatch];
+};
+
+__device__ __forceinline__ int batch_find(const EvalBatch& b, int64_t t) {
+  int lo = 0, hi = b.n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (b.it[mid].tile_start <= t) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Total tiles of a batch; a single item may take its length from device memory.
+__device__ __forceinline__ int64_t batch_total(const EvalBatch& b, int64_t& n0) {
+  const EvalJob& j0 = b.it[0].job;
+  n0 = (b.n == 1 && j0.n_dev) ? *j0.n_dev : j0.n_items;
+  if (b.n == 1) return job_tiles(j0.mode, n0);
+  const EvalItem& last = b.it[b.n - 1];
+  return last.tile_start + job_tiles(last.job.mode, last.job.n_items);
+}
+
 __host__ __device__ inline int64_t net_param_count(int nin, int w, int L) {
   return (int64_t)w * nin + w + (int64_t)(L - 1) * (w * w + w) + w + 1;
 }
@@ -152,22 +187,32 @@ __host__ __device__ inline size_t f32_smem_bytes(int L) {
 }
 
 template <int NIN, int W>
-__global__ void __launch_bounds__(kTile) mlp_f32_kernel(NetView net, EvalJob job) {
+__global__ void __launch_bounds__(kTile) mlp_f32_kernel(const __grid_constant__ EvalBatch b) {
   extern __shared__ float4 smem_f4[];
   float* sp = reinterpret_cast<float*>(smem_f4);
-  const int L = net.layers;
+  const int L = b.it[0].net.layers;
   const int64_t P = net_param_count(NIN, W, L);
   uint32_t* sq = reinterpret_cast<uint32_t*>(sp + ((P + 3) & ~3ll));
-  for (int64_t i = threadIdx.x; i < P; i += blockDim.x) sp[i] = __ldg(net.p32 + i);
-  for (int i = threadIdx.x; i < 3 * (NIN / 2); i += blockDim.x) sq[i] = __ldg(net.q + i);
-  __syncthreads();
-  if (job.n_dev) job.n_items = *job.n_dev;
-  const int64_t ntiles = job_tiles(job.mode, job.n_items);
+  int64_t n0;
+  const int64_t ntiles = batch_total(b, n0);
+  int cur = -1;
   for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int m = batch_find(b, t);
+    if (m != cur) {   // uniform across the CTA
+      __syncthreads();
+      const NetView& net = b.it[m].net;
+      for (int64_t i = threadIdx.x; i < P; i += blockDim.x) sp[i] = __ldg(net.p32 + i);
+      for (int i = threadIdx.x; i < 3 * (NIN / 2); i += blockDim.x) sq[i] = __ldg(net.q + i);
+      __syncthreads();
+      cur = m;
+    }
+    EvalJob job = b.it[m].job;
+    if (b.n == 1) job.n_items = n0;
+    const int64_t tl = t - b.it[m].tile_start;
     int cx, cy, cz;
-    const bool valid = job_coord(job, t, threadIdx.x, cx, cy, cz);
+    const bool valid = job_coord(job, tl, threadIdx.x, cx, cy, cz);
     const float y = forward_f32<NIN, W>(sp, sq, L, cx, cy, cz);
-    job_output(job, t, threadIdx.x, valid, y);
+    job_output(job, tl, threadIdx.x, valid, y);
   }
 }
 
@@ -265,14 +310,48 @@ __device__ __forceinline__ void store_a_row(uint32_t tlane, const uint32_t* hi, 
   }
 }
 
+// Stage network `net` into shared memory: weight tiles, head, Fourier matrix and
+// (level-0 lattice) the table T[f][dy*8+dz] = e^{i Phi(dy e_y + dz e_z)}.
 template <int NIN, int W, int MODE>
-__global__ void __launch_bounds__(kTile, 1) mlp_tc_kernel(NetView net, EvalJob job) {
+__device__ __forceinline__ void tc_stage(const NetView& net, int mode, const TcLayout<NIN, W, MODE>& lay, uint8_t* smem) {
+  using C = TcCfg<NIN, W, MODE>;
+  constexpr int M = C::M;
+  const int L = net.layers, tid = threadIdx.x;
+  float2* sT = reinterpret_cast<float2*>(smem + lay.t_off);
+  __half2* sTh = reinterpret_cast<__half2*>(smem + lay.t_off);
+  float* swh = reinterpret_cast<float*>(smem + lay.wh_off);
+  uint32_t* sq = reinterpret_cast<uint32_t*>(smem + lay.q_off);
+  const int64_t te = wtile_elems(NIN, W, L);
+  const uint8_t* base = net.wpk + (MODE == TC_FP16 ? 0 : te * 2);
+  const uint4* src = reinterpret_cast<const uint4*>(base);
+  uint4* dst = reinterpret_cast<uint4*>(smem);
+  const size_t n16 = C::NCOPY * lay.w_bytes / 16;
+  for (size_t i = tid; i < n16; i += kTile) dst[i] = __ldg(src + i);
+  const int64_t hoff = net_param_count(NIN, W, L) - W - 1;
+  for (int o = tid; o <= W; o += kTile) swh[o] = __ldg(net.p32 + hoff + o);
+  for (int i = tid; i < 3 * M; i += kTile) sq[i] = __ldg(net.q + i);
+  __syncthreads();
+  if (mode == MODE_L0) {
+    for (int i = tid; i < M * 64; i += kTile) {
+      const int f = i >> 6, j = i & 63;
+      const uint32_t ph = sq[3 * f + 1] * (uint32_t)(j >> 3) + sq[3 * f + 2] * (uint32_t)(j & 7);
+      float sn, cs;
+      sincospif((float)(int32_t)ph * 0x1p-31f, &sn, &cs);
+      if (MODE == TC_FP16) sTh[i] = __floats2half2_rn(cs, sn);
+      else sT[i] = make_float2(cs, sn);
+    }
+  }
+  fence_proxy_async_smem();   // the weight tiles are read by the tensor core (async proxy)
+}
+
+template <int NIN, int W, int MODE>
+__global__ void __launch_bounds__(kTile, 1) mlp_tc_kernel(const __grid_constant__ EvalBatch b) {
   static_assert(W == 32 || W == 64, "width");
   static_assert(NIN == 32 || NIN == 64, "encoding size");
   using C = TcCfg<NIN, W, MODE>;
   constexpr int M = C::M;
   extern __shared__ __align__(1024) uint8_t smem[];
-  const int L = net.layers;
+  const int L = b.it[0].net.layers;
   const TcLayout<NIN, W, MODE> lay(L);
   uint8_t* sw = smem;                              // hi (or FP16) weight tiles
   uint8_t* sw_lo = smem + lay.w_bytes;             // lo weight tiles (BF16X3)
@@ -285,29 +364,6 @@ __global__ void __launch_bounds__(kTile, 1) mlp_tc_kernel(NetView net, EvalJob j
   uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + lay.slot_off);
   const int tid = threadIdx.x, warp = tid >> 5;
 
-  // ---- stage weights, head, Fourier matrix; lattice table T[f][dy*8+dz]
-  {
-    const int64_t te = wtile_elems(NIN, W, L);
-    const uint8_t* base = net.wpk + (MODE == TC_FP16 ? 0 : te * 2);
-    const uint4* src = reinterpret_cast<const uint4*>(base);
-    uint4* dst = reinterpret_cast<uint4*>(sw);
-    const size_t n16 = C::NCOPY * lay.w_bytes / 16;
-    for (size_t i = tid; i < n16; i += kTile) dst[i] = __ldg(src + i);
-    const int64_t hoff = net_param_count(NIN, W, L) - W - 1;
-    for (int o = tid; o <= W; o += kTile) swh[o] = __ldg(net.p32 + hoff + o);
-    for (int i = tid; i < 3 * M; i += kTile) sq[i] = __ldg(net.q + i);
-    __syncthreads();
-    if (job.mode == MODE_L0) {
-      for (int i = tid; i < M * 64; i += kTile) {
-        const int f = i >> 6, j = i & 63;
-        const uint32_t ph = sq[3 * f + 1] * (uint32_t)(j >> 3) + sq[3 * f + 2] * (uint32_t)(j & 7);
-        float sn, cs;
-        sincospif((float)(int32_t)ph * 0x1p-31f, &sn, &cs);
-        if (MODE == TC_FP16) sTh[i] = __floats2half2_rn(cs, sn);
-        else sT[i] = make_float2(cs, sn);
-      }
-    }
-  }
   if (tid == 0) mbar_init(bar, 1);
   if (warp == 0) tmem_alloc(tslot, C::COLS);
   fence_proxy_async_smem();
@@ -316,14 +372,26 @@ __global__ void __launch_bounds__(kTile, 1) mlp_tc_kernel(NetView net, EvalJob j
   tc_fence_after();
   const uint32_t tbase = *tslot;
   const uint32_t tlane = tbase + ((uint32_t)(warp * 32) << 16);
-  const float bh = swh[W];
   const uint32_t idesc = MODE == TC_FP16 ? idesc_f16_f32(kTile, W) : idesc_bf16_f32(kTile, W);
 
   uint32_t phase = 0;
   bool failed = false;
-  if (job.n_dev) job.n_items = *job.n_dev;
-  const int64_t ntiles = job_tiles(job.mode, job.n_items);
-  for (int64_t t = blockIdx.x; t < ntiles && !failed; t += gridDim.x) {
+  int64_t n0;
+  const int64_t ntiles = batch_total(b, n0);
+  int cur = -1;
+  float bh = 0.f;
+  for (int64_t t0 = blockIdx.x; t0 < ntiles && !failed; t0 += gridDim.x) {
+    const int m = batch_find(b, t0);
+    if (m != cur) {   // uniform across the CTA: restage the item's network
+      __syncthreads();
+      tc_stage<NIN, W, MODE>(b.it[m].net, b.it[m].job.mode, lay, smem);
+      __syncthreads();
+      bh = swh[W];
+      cur = m;
+    }
+    EvalJob job = b.it[m].job;
+    if (b.n == 1) job.n_items = n0;
+    const int64_t t = t0 - b.it[m].tile_start;
     // ---- encoding -> A operand (layer 0) in TMEM.  Inside this kernel the features are
     // ordered (cos_0, sin_0, cos_1, sin_1, ...): packed column f holds frequency f; the
     // first-layer weight tile is packed with the matching column order.
@@ -423,7 +491,7 @@ __global__ void __launch_bounds__(kTile, 1) mlp_tc_kernel(NetView net, EvalJob j
     if (failed) break;
     job_output(job, t, tid, valid, y);
   }
-  if (failed && tid == 0) set_status(job.status, ST_TIMEOUT);
+  if (failed && tid == 0) set_status(b.it[0].job.status, ST_TIMEOUT);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();

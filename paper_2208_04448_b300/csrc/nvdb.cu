@@ -258,9 +258,10 @@ struct PatchSet {
   void release() { dfree(d_l1_off); dfree(d_l0_off); dfree(d_l1_idx); dfree(d_l0_idx); }
 };
 
-// Device scratch of the top-down decode of one model.
+// Device scratch of a top-down decode of one model or of several models whose
+// levels are concatenated in model order.
 struct DecodeScratch {
-  int64_t n_l1 = -1, n_leaf = -1;
+  int64_t cap2 = 0, cap1 = 0, capl = 0;
   uint32_t* l2_counts = nullptr;
   int64_t* l2_off = nullptr;
   int4* l1_origin = nullptr;
@@ -271,11 +272,27 @@ struct DecodeScratch {
   uint32_t* leaf_words = nullptr;
   uint32_t* leaf_counts = nullptr;
   int64_t* leaf_off = nullptr;
+  uint32_t* status = nullptr;
+  Scan scan;
+  nvdb_status reserve(int64_t n2, int64_t n1, int64_t nl) {
+    if (status && n2 <= cap2 && n1 <= cap1 && nl <= capl) return NVDB_OK;
+    release();
+    TRY(dalloc(&status, 1));
+    TRY(dalloc(&l2_counts, n2 + 1)); TRY(dalloc(&l2_off, n2 + 1));
+    TRY(dalloc(&l1_origin, n1 + 1)); TRY(dalloc(&l1_words, 128 * n1 + 4));
+    TRY(dalloc(&l1_counts, n1 + 1)); TRY(dalloc(&l1_off, n1 + 1));
+    TRY(dalloc(&leaf_origin, nl + 1)); TRY(dalloc(&leaf_words, 16 * nl + 4));
+    TRY(dalloc(&leaf_counts, nl + 1)); TRY(dalloc(&leaf_off, nl + 1));
+    TRY(scan.reserve(std::max<int64_t>(nl, std::max(n1, n2))));
+    cap2 = n2; cap1 = n1; capl = nl;
+    return NVDB_OK;
+  }
   void release() {
     dfree(l2_counts); dfree(l2_off); dfree(l1_origin); dfree(l1_words); dfree(l1_counts); dfree(l1_off);
-    dfree(leaf_origin); dfree(leaf_words); dfree(leaf_counts); dfree(leaf_off);
-    n_l1 = n_leaf = -1;
+    dfree(leaf_origin); dfree(leaf_words); dfree(leaf_counts); dfree(leaf_off); dfree(status);
+    cap2 = cap1 = capl = 0;
   }
+  ~DecodeScratch() { release(); }
 };
 
 // Topology cache of [Hash,5,4,NN(3)] plus the per-batch query scratch.
@@ -325,7 +342,6 @@ struct nvdb_model {
   ~nvdb_model() {
     dfree(q_dev[0]); dfree(q_dev[1]); dfree(l2_origin); dfree(l2_mask); dfree(status); dfree(partial);
     for (auto& p : patches) p.release();
-    ds.release();
     qc.release();
   }
   const PatchSet* patch_set(int prec) const {
@@ -351,9 +367,12 @@ NetView net_view(const nvdb_model* m, int k) {
   return v;
 }
 
+// Tensor-core CTAs per SM chosen by the decode-plan autotuner (0: from the kernel's limits).
+int g_occ_override = 0;
+
 template <int NIN, int W, int MODE>
-nvdb_status launch_tc(const NetView& nv, const EvalJob& job, int64_t ntiles, const char* base, cudaStream_t s) {
-  const TcLayout<NIN, W, MODE> lay(nv.layers);
+nvdb_status launch_tc(const EvalBatch& b, int64_t ntiles, const char* base, cudaStream_t s) {
+  const TcLayout<NIN, W, MODE> lay(b.it[0].net.layers);
   CU(cudaFuncSetAttribute(mlp_tc_kernel<NIN, W, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lay.total));
   // Residency from the kernel's own limits (the runtime's occupancy query reports 1 for
   // kernels that allocate tensor memory): registers, shared memory, and TMEM columns.
@@ -362,29 +381,28 @@ nvdb_status launch_tc(const NetView& nv, const EvalJob& job, int64_t ntiles, con
   const int regs = std::max(8, (fa.numRegs + 7) & ~7);
   const int by_regs = 65536 / (regs * kTile);
   const int by_smem = (int)(kSmemPerSm / (lay.total + 1024));
-  const int occ = std::min({by_regs, by_smem, TcCfg<NIN, W, MODE>::MAXC});
+  int occ = std::min({by_regs, by_smem, TcCfg<NIN, W, MODE>::MAXC});
   if (occ < 1) return fail(NVDB_ERR_UNSUPPORTED, "tensor-core kernel does not fit on an SM");
+  if (g_occ_override > 0) occ = std::min(occ, g_occ_override);
   const int64_t grid = std::min<int64_t>(ntiles, (int64_t)num_sms() * occ);
-  KLAUNCH(eval_name(base, job.mode), s,
-          mlp_tc_kernel<NIN, W, MODE><<<(unsigned)grid, kTile, lay.total, s>>>(nv, job));
+  KLAUNCH(eval_name(base, b.it[0].job.mode), s,
+          mlp_tc_kernel<NIN, W, MODE><<<(unsigned)grid, kTile, lay.total, s>>>(b));
   return NVDB_OK;
 }
 
 template <int NIN, int W>
-nvdb_status launch_eval_t(const NetView& nv, const EvalJob& job, nvdb_precision prec, cudaStream_t s) {
-  const int64_t ntiles = job_tiles(job.mode, job.n_items);
-  if (ntiles == 0) return NVDB_OK;
+nvdb_status launch_eval_t(const EvalBatch& b, int64_t ntiles, nvdb_precision prec, cudaStream_t s) {
   int occ = 0;
   if (prec == NVDB_FP32) {
-    const size_t smem = f32_smem_bytes<NIN, W>(nv.layers);
+    const size_t smem = f32_smem_bytes<NIN, W>(b.it[0].net.layers);
     CU(cudaFuncSetAttribute(mlp_f32_kernel<NIN, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, mlp_f32_kernel<NIN, W>, kTile, smem));
     const int64_t grid = std::min<int64_t>(ntiles, (int64_t)num_sms() * std::max(occ, 1));
-    KLAUNCH(eval_name("mlp_f32", job.mode), s, mlp_f32_kernel<NIN, W><<<(unsigned)grid, kTile, smem, s>>>(nv, job));
+    KLAUNCH(eval_name("mlp_f32", b.it[0].job.mode), s, mlp_f32_kernel<NIN, W><<<(unsigned)grid, kTile, smem, s>>>(b));
   } else if (prec == NVDB_BF16) {
-    TRY((launch_tc<NIN, W, TC_BF16X3>(nv, job, ntiles, "mlp_bf16x3", s)));
+    TRY((launch_tc<NIN, W, TC_BF16X3>(b, ntiles, "mlp_bf16x3", s)));
   } else if (prec == NVDB_FP16) {
-    TRY((launch_tc<NIN, W, TC_FP16>(nv, job, ntiles, "mlp_f16", s)));
+    TRY((launch_tc<NIN, W, TC_FP16>(b, ntiles, "mlp_f16", s)));
   } else {
     return fail(NVDB_ERR_UNSUPPORTED, "precision %d not implemented", (int)prec);
   }
@@ -392,17 +410,38 @@ nvdb_status launch_eval_t(const NetView& nv, const EvalJob& job, nvdb_precision 
   return NVDB_OK;
 }
 
-nvdb_status launch_eval(const nvdb_model* m, int k, nvdb_precision prec, EvalJob job, cudaStream_t s) {
-  const NetView nv = net_view(m, k);
+// Launch a batch whose items share one network shape; fills the tile offsets.
+nvdb_status launch_batch(EvalBatch& b, nvdb_precision prec, cudaStream_t s) {
+  int64_t tiles = 0;
+  for (int m = 0; m < b.n; ++m) {
+    b.it[m].tile_start = tiles;
+    tiles += job_tiles(b.it[m].job.mode, b.it[m].job.n_items);
+  }
+  if (tiles == 0) return NVDB_OK;
+  const NetView& nv = b.it[0].net;
+  if (nv.n_in == 32 && nv.width == 32) return launch_eval_t<32, 32>(b, tiles, prec, s);
+  if (nv.n_in == 32 && nv.width == 64) return launch_eval_t<32, 64>(b, tiles, prec, s);
+  if (nv.n_in == 64 && nv.width == 32) return launch_eval_t<64, 32>(b, tiles, prec, s);
+  if (nv.n_in == 64 && nv.width == 64) return launch_eval_t<64, 64>(b, tiles, prec, s);
+  return fail(NVDB_ERR_UNSUPPORTED, "network shape n=%d w=%d", nv.n_in, nv.width);
+}
+
+EvalItem eval_item(const nvdb_model* m, int k, EvalJob job) {
+  EvalItem it{};
+  it.net = net_view(m, k);
   job.ox = m->origin[0];
   job.oy = m->origin[1];
   job.oz = m->origin[2];
-  job.status = m->status;
-  if (nv.n_in == 32 && nv.width == 32) return launch_eval_t<32, 32>(nv, job, prec, s);
-  if (nv.n_in == 32 && nv.width == 64) return launch_eval_t<32, 64>(nv, job, prec, s);
-  if (nv.n_in == 64 && nv.width == 32) return launch_eval_t<64, 32>(nv, job, prec, s);
-  if (nv.n_in == 64 && nv.width == 64) return launch_eval_t<64, 64>(nv, job, prec, s);
-  return fail(NVDB_ERR_UNSUPPORTED, "network shape n=%d w=%d", nv.n_in, nv.width);
+  if (!job.status) job.status = m->status;
+  it.job = job;
+  return it;
+}
+
+nvdb_status launch_eval(const nvdb_model* m, int k, nvdb_precision prec, EvalJob job, cudaStream_t s) {
+  EvalBatch b;
+  b.n = 1;
+  b.it[0] = eval_item(m, k, job);
+  return launch_batch(b, prec, s);
 }
 
 template <int NIN, int W>
@@ -824,61 +863,114 @@ extern "C" nvdb_status nvdb_model_losses(const nvdb_model* m, int net, float* lo
 
 // ============================================================================ decompress
 namespace {
-nvdb_status ensure_decode_scratch(nvdb_model* m) {
-  DecodeScratch& d = m->ds;
-  if (d.n_l1 == m->n_l1 && d.n_leaf == m->n_leaf) return NVDB_OK;
-  d.release();
-  TRY(dalloc(&d.l2_counts, m->n_l2 + 1)); TRY(dalloc(&d.l2_off, m->n_l2 + 1));
-  TRY(dalloc(&d.l1_origin, m->n_l1 + 1)); TRY(dalloc(&d.l1_words, 128 * m->n_l1 + 4));
-  TRY(dalloc(&d.l1_counts, m->n_l1 + 1)); TRY(dalloc(&d.l1_off, m->n_l1 + 1));
-  TRY(dalloc(&d.leaf_origin, m->n_leaf + 1)); TRY(dalloc(&d.leaf_words, 16 * m->n_leaf + 4));
-  TRY(dalloc(&d.leaf_counts, m->n_leaf + 1)); TRY(dalloc(&d.leaf_off, m->n_leaf + 1));
-  TRY(m->scan.reserve(std::max<int64_t>(m->n_leaf, std::max(m->n_l1, m->n_l2))));
-  d.n_l1 = m->n_l1;
-  d.n_leaf = m->n_leaf;
+bool same_shape(const nvdb_model* a, const nvdb_model* b) {
+  if (a->ffm[0] != b->ffm[0] || a->ffm[1] != b->ffm[1]) return false;
+  for (int k = 0; k < 3; ++k)
+    if (a->width[k] != b->width[k] || a->layers[k] != b->layers[k]) return false;
+  return true;
+}
+
+// Top-down decode (Section 3.5) of n <= kMaxBatch models with the same network
+// shapes, in one launch per stage: level-1 origins from the level-2 child masks,
+// level-1 classification + patches -> leaf origins, level-0 classification +
+// patches -> voxel offsets; with an output, the voxels and their regressed
+// values (concatenated per model, canonical order).  Levels of the models are
+// concatenated in model order in `d`.
+nvdb_status decode_batch(nvdb_model* const* ms, int n, nvdb_precision prec, DecodeScratch& d, int32_t* out_ijk,
+                         float* out_val, cudaStream_t s) {
+  std::vector<int64_t> s2(n + 1, 0), s1(n + 1, 0), sl(n + 1, 0), sa(n + 1, 0);
+  for (int m = 0; m < n; ++m) {
+    s2[m + 1] = s2[m] + ms[m]->n_l2;
+    s1[m + 1] = s1[m] + ms[m]->n_l1;
+    sl[m + 1] = sl[m] + ms[m]->n_leaf;
+    sa[m + 1] = sa[m] + ms[m]->n_active;
+  }
+  const int64_t N2 = s2[n], N1 = s1[n], NL = sl[n], NA = sa[n];
+  TRY(d.reserve(N2, N1, NL));
+  CU(cudaMemsetAsync(d.status, 0, 4, s));
+  std::vector<const PatchSet*> ps(n);
+  for (int m = 0; m < n; ++m) ps[m] = ms[m]->patch_set(prec);
+  if (N2) {
+    L2Batch lb;
+    lb.n = n;
+    for (int m = 0; m < n; ++m)
+      lb.it[m] = L2Item{reinterpret_cast<const uint64_t*>(ms[m]->l2_mask), ms[m]->l2_origin, s2[m]};
+    KLAUNCH("l2_count", s, l2_count_batch_kernel<<<(unsigned)N2, 512, 0, s>>>(lb, d.l2_counts));
+    TRY(d.scan.run(d.l2_counts, N2, d.l2_off, s));
+    KLAUNCH("check_total", s, check_total_kernel<<<1, 1, 0, s>>>(d.scan.total, N1, d.status));
+    KLAUNCH("l2_emit", s, l2_emit_batch_kernel<<<(unsigned)N2, 512, 0, s>>>(lb, d.l2_off, d.l1_origin, N1, d.status));
+  }
+  EvalBatch b;
+  b.n = n;
+  for (int m = 0; m < n; ++m) {
+    EvalJob j{};
+    j.mode = MODE_L1;
+    j.nodes = d.l1_origin + s1[m];
+    j.n_items = ms[m]->n_l1;
+    j.words = d.l1_words + 128 * s1[m];
+    j.status = d.status;
+    b.it[m] = eval_item(ms[m], 0, j);
+  }
+  TRY(launch_batch(b, prec, s));
+  PatchBatch pb;
+  pb.n = n;
+  for (int m = 0; m < n; ++m) pb.it[m] = PatchItem{ps[m]->d_l1_off, ps[m]->d_l1_idx, s1[m]};
+  if (N1)
+    KLAUNCH("patch_count", s, patch_count_batch_kernel<<<blocks_for(N1, 8), 256, 0, s>>>(d.l1_words, 128, N1, pb,
+                                                                                      d.l1_counts));
+  TRY(d.scan.run(d.l1_counts, N1, d.l1_off, s));
+  KLAUNCH("check_total", s, check_total_kernel<<<1, 1, 0, s>>>(d.scan.total, NL, d.status));
+  if (N1)
+    KLAUNCH("emit_leaves", s, emit_leaves_kernel<<<blocks_for(N1 * 32, 256), 256, 0, s>>>(d.l1_words, d.l1_origin, N1,
+                                                                                       d.l1_off, d.leaf_origin, NL,
+                                                                                       d.status));
+  for (int m = 0; m < n; ++m) {
+    EvalJob j{};
+    j.mode = MODE_L0;
+    j.nodes = d.leaf_origin + sl[m];
+    j.n_items = ms[m]->n_leaf;
+    j.words = d.leaf_words + 16 * sl[m];
+    j.status = d.status;
+    b.it[m] = eval_item(ms[m], 1, j);
+  }
+  TRY(launch_batch(b, prec, s));
+  for (int m = 0; m < n; ++m) pb.it[m] = PatchItem{ps[m]->d_l0_off, ps[m]->d_l0_idx, sl[m]};
+  if (NL)
+    KLAUNCH("patch_count", s, patch_count_batch_kernel<<<blocks_for(NL, 8), 256, 0, s>>>(d.leaf_words, 16, NL, pb,
+                                                                                      d.leaf_counts));
+  TRY(d.scan.run(d.leaf_counts, NL, d.leaf_off, s));
+  KLAUNCH("check_total", s, check_total_kernel<<<1, 1, 0, s>>>(d.scan.total, NA, d.status));
+  if (out_ijk) {
+    if (NL)
+      KLAUNCH("emit_voxels", s, emit_voxels_rank_kernel<<<blocks_for(NL, 8), 256, 0, s>>>(d.leaf_words, d.leaf_origin,
+                                                                                        NL, d.leaf_off, out_ijk, NA,
+                                                                                        d.status));
+    for (int m = 0; m < n; ++m) {
+      EvalJob j{};
+      j.mode = MODE_LIST;
+      j.ijk = out_ijk + 3 * sa[m];
+      j.n_items = ms[m]->n_active;
+      j.out = out_val + sa[m];
+      j.scale = ms[m]->value_scale();
+      j.status = d.status;
+      b.it[m] = eval_item(ms[m], 2, j);
+    }
+    TRY(launch_batch(b, prec, s));
+  }
+  CU(cudaGetLastError());
   return NVDB_OK;
 }
 
-// Top-down topology decode (Section 3.5): level-1 origins, child bits, leaf
-// origins, active bits (all patched), leaf offsets of the active voxels.
-nvdb_status decode_topology(nvdb_model* m, const PatchSet* ps, nvdb_precision prec, cudaStream_t s) {
-  TRY(ensure_decode_scratch(m));
-  DecodeScratch& d = m->ds;
-  const uint64_t* l2m = reinterpret_cast<const uint64_t*>(m->l2_mask);
-  if (m->n_l2) {
-    KLAUNCH("l2_count", s, l2_count_kernel<<<(unsigned)m->n_l2, 512, 0, s>>>(l2m, m->n_l2, d.l2_counts));
-    TRY(m->scan.run(d.l2_counts, m->n_l2, d.l2_off, s));
-    KLAUNCH("check_total", s, check_total_kernel<<<1, 1, 0, s>>>(m->scan.total, m->n_l1, m->status));
-    KLAUNCH("l2_emit", s, l2_emit_kernel<<<(unsigned)m->n_l2, 512, 0, s>>>(l2m, m->l2_origin, m->n_l2, d.l2_off, d.l1_origin, m->n_l1,
-                                                     m->status));
+// Consecutive runs of models with the same shapes, at most kMaxBatch long.
+std::vector<std::pair<int, int>> batch_runs(const nvdb_model* const* models, int n_models) {
+  std::vector<std::pair<int, int>> runs;
+  for (int i = 0; i < n_models;) {
+    int j = i + 1;
+    while (j < n_models && j - i < kMaxBatch && same_shape(models[i], models[j])) ++j;
+    runs.emplace_back(i, j);
+    i = j;
   }
-  EvalJob j1{};
-  j1.mode = MODE_L1;
-  j1.nodes = d.l1_origin;
-  j1.n_items = m->n_l1;
-  j1.words = d.l1_words;
-  TRY(launch_eval(m, 0, prec, j1, s));
-  if (m->n_l1)
-    KLAUNCH("patch_count", s, patch_count_warp_kernel<<<blocks_for(m->n_l1, 8), 256, 0, s>>>(d.l1_words, 128, m->n_l1,
-                                                                ps->d_l1_off, ps->d_l1_idx, d.l1_counts));
-  TRY(m->scan.run(d.l1_counts, m->n_l1, d.l1_off, s));
-  KLAUNCH("check_total", s, check_total_kernel<<<1, 1, 0, s>>>(m->scan.total, m->n_leaf, m->status));
-  if (m->n_l1)
-    KLAUNCH("emit_leaves", s, emit_leaves_kernel<<<blocks_for(m->n_l1 * 32, 256), 256, 0, s>>>(d.l1_words, d.l1_origin, m->n_l1, d.l1_off,
-                                                                    d.leaf_origin, m->n_leaf, m->status));
-  EvalJob j0{};
-  j0.mode = MODE_L0;
-  j0.nodes = d.leaf_origin;
-  j0.n_items = m->n_leaf;
-  j0.words = d.leaf_words;
-  TRY(launch_eval(m, 1, prec, j0, s));
-  if (m->n_leaf)
-    KLAUNCH("patch_count", s, patch_count_warp_kernel<<<blocks_for(m->n_leaf, 8), 256, 0, s>>>(d.leaf_words, 16, m->n_leaf,
-                                                                  ps->d_l0_off, ps->d_l0_idx, d.leaf_counts));
-  TRY(m->scan.run(d.leaf_counts, m->n_leaf, d.leaf_off, s));
-  KLAUNCH("check_total", s, check_total_kernel<<<1, 1, 0, s>>>(m->scan.total, m->n_active, m->status));
-  CU(cudaGetLastError());
-  return NVDB_OK;
+  return runs;
 }
 }  // namespace
 
@@ -897,31 +989,32 @@ extern "C" nvdb_status nvdb_decompress(const nvdb_model* const* models, int n_mo
   if (!d_ijk) return NVDB_OK;
   if (need > capacity) return fail(NVDB_ERR_CAPACITY, "nvdb_decompress: need %lld voxels, capacity %lld", (long long)need, (long long)capacity);
   cudaStream_t s = (cudaStream_t)stream;
+  nvdb_model* const* ms = const_cast<nvdb_model* const*>(models);
   int64_t base = 0;
-  for (int i = 0; i < n_models; ++i) {
-    nvdb_model* m = const_cast<nvdb_model*>(models[i]);
-    CU(cudaMemsetAsync(m->status, 0, 4, s));
-    TRY(decode_topology(m, m->patch_set(prec), prec, s));
-    DecodeScratch& d = m->ds;
-    if (m->n_leaf)
-      KLAUNCH("emit_voxels", s, emit_voxels_rank_kernel<<<blocks_for(m->n_leaf, 8), 256, 0, s>>>(d.leaf_words, d.leaf_origin,
-                                                                  m->n_leaf, d.leaf_off, d_ijk + 3 * base, m->n_active,
-                                                                  m->status));
-    EvalJob jr{};
-    jr.mode = MODE_LIST;
-    jr.ijk = d_ijk + 3 * base;
-    jr.n_items = m->n_active;
-    jr.out = d_val + base;
-    jr.scale = m->value_scale();
-    TRY(launch_eval(m, 2, prec, jr, s));
-    base += m->n_active;
+  std::vector<DecodeScratch*> tmp;
+  nvdb_status st = NVDB_OK;
+  std::vector<uint32_t*> status_words;
+  for (const auto& r : batch_runs(models, n_models)) {
+    const int n = r.second - r.first;
+    DecodeScratch* d = &ms[r.first]->ds;
+    if (n > 1) {
+      tmp.push_back(new DecodeScratch());
+      d = tmp.back();
+    }
+    st = decode_batch(ms + r.first, n, prec, *d, d_ijk + 3 * base, d_val + base, s);
+    if (st != NVDB_OK) break;
+    status_words.push_back(d->status);
+    for (int m = r.first; m < r.second; ++m) base += ms[m]->n_active;
   }
-  for (int i = 0; i < n_models; ++i) {
+  for (uint32_t* sw : status_words) {
+    if (st != NVDB_OK) break;
     uint32_t hst = 0;
-    TRY(read_status(const_cast<nvdb_model*>(models[i])->status, s, &hst));
-    TRY(status_to_error(hst));
+    st = read_status(sw, s, &hst);
+    if (st == NVDB_OK) st = status_to_error(hst);
   }
-  return NVDB_OK;
+  if (!tmp.empty()) cudaStreamSynchronize(s);
+  for (auto* d : tmp) delete d;
+  return st;
 }
 
 // ============================================================================ query
@@ -935,8 +1028,8 @@ nvdb_status build_query_cache(nvdb_model* m, cudaStream_t s) {
   int prec = NVDB_FP32;
   if (!ps && !m->patches.empty()) { ps = &m->patches[0]; prec = ps->prec; }
   if (!ps) return fail(NVDB_ERR_UNSUPPORTED, "model has no patch set");
-  CU(cudaMemsetAsync(m->status, 0, 4, s));
-  TRY(decode_topology(m, ps, (nvdb_precision)prec, s));
+  nvdb_model* one[1] = {m};
+  TRY(decode_batch(one, 1, (nvdb_precision)prec, m->ds, nullptr, nullptr, s));
   TRY(dalloc(&q.l2_key, m->n_l2 + 1)); TRY(dalloc(&q.l2_pre, 512 * m->n_l2 + 1));
   TRY(dalloc(&q.l1_pre, 128 * m->n_l1 + 1));
   if (m->n_l2) {
@@ -950,7 +1043,7 @@ nvdb_status build_query_cache(nvdb_model* m, cudaStream_t s) {
   TRY(dalloc(&q.list, 3 * 8 * q.batch)); TRY(dalloc(&q.vals, 8 * q.batch));
   TRY(m->scan.reserve(q.batch));
   uint32_t hst = 0;
-  TRY(read_status(m->status, s, &hst));
+  TRY(read_status(m->ds.status, s, &hst));
   TRY(status_to_error(hst));
   q.ready = true;
   return NVDB_OK;
@@ -1365,5 +1458,143 @@ extern "C" nvdb_status nvdb_mlp_grad_static(const nvdb_model* m, int net, const 
   CU(cudaMemcpyAsync(&h, loss_slot, sizeof h, cudaMemcpyDeviceToHost, s));
   CU(cudaStreamSynchronize(s));
   if (loss) *loss = h;
+  return NVDB_OK;
+}
+
+// ============================================================================ decode plans (CUDA graphs)
+struct nvdb_plan {
+  std::vector<nvdb_model*> models;
+  nvdb_precision prec = NVDB_FP32;
+  int32_t* ijk = nullptr;
+  float* val = nullptr;
+  std::vector<std::pair<int, int>> runs;
+  std::vector<DecodeScratch*> scratch;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int occ = 0;
+  float best_ms = 0.f;
+  ~nvdb_plan() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    for (auto* d : scratch) delete d;
+  }
+};
+
+namespace {
+nvdb_status plan_run(nvdb_plan* p, cudaStream_t s) {
+  int64_t base = 0;
+  for (size_t i = 0; i < p->runs.size(); ++i) {
+    const auto& r = p->runs[i];
+    TRY(decode_batch(p->models.data() + r.first, r.second - r.first, p->prec, *p->scratch[i], p->ijk + 3 * base,
+                     p->val + base, s));
+    for (int m = r.first; m < r.second; ++m) base += p->models[m]->n_active;
+  }
+  return NVDB_OK;
+}
+}  // namespace
+
+extern "C" nvdb_status nvdb_decompress_plan(const nvdb_model* const* models, int n_models, nvdb_precision prec,
+                                            int32_t* d_ijk, float* d_val, int64_t capacity, nvdb_stream stream,
+                                            nvdb_plan** out) {
+  if (!out || !models || n_models <= 0 || !d_ijk || !d_val) return fail(NVDB_ERR_INVALID_ARG, "nvdb_decompress_plan: bad arguments");
+  *out = nullptr;
+  int64_t need = 0;
+  for (int i = 0; i < n_models; ++i) {
+    if (!models[i]) return fail(NVDB_ERR_INVALID_ARG, "nvdb_decompress_plan: NULL model");
+    if (!models[i]->patch_set(prec)) return fail(NVDB_ERR_UNSUPPORTED, "model %d has no patch set for precision %d", i, (int)prec);
+    need += models[i]->n_active;
+  }
+  if (need > capacity) return fail(NVDB_ERR_CAPACITY, "nvdb_decompress_plan: need %lld voxels, capacity %lld", (long long)need, (long long)capacity);
+  cudaStream_t s = (cudaStream_t)stream;
+  auto* p = new nvdb_plan();
+  p->models.assign(const_cast<nvdb_model* const*>(models), const_cast<nvdb_model* const*>(models) + n_models);
+  p->prec = prec;
+  p->ijk = d_ijk;
+  p->val = d_val;
+  p->runs = batch_runs(models, n_models);
+  for (size_t i = 0; i < p->runs.size(); ++i) p->scratch.push_back(new DecodeScratch());
+  const bool prof_on = prof::g_on.exchange(false);
+  auto run = [&]() -> nvdb_status {
+    // autotune: tensor-core CTAs per SM, timing the whole decode (events on the stream)
+    cudaEvent_t a, b;
+    CU(cudaEventCreate(&a));
+    CU(cudaEventCreate(&b));
+    float best = 1e30f;
+    int best_occ = 0;
+    const int cands[] = {0, 1, 2, 3, 4};
+    for (int c : cands) {
+      if (prec == NVDB_FP32 && c != 0) continue;
+      g_occ_override = c;
+      nvdb_status st = plan_run(p, s);                   // warm-up (and sizes the scratch)
+      if (st == NVDB_OK) {
+        cudaEventRecord(a, s);
+        st = plan_run(p, s);
+        cudaEventRecord(b, s);
+      }
+      g_occ_override = 0;
+      TRY(st);
+      CU(cudaEventSynchronize(b));
+      float ms = 0.f;
+      CU(cudaEventElapsedTime(&ms, a, b));
+      if (ms < best) { best = ms; best_occ = c; }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    for (auto* d : p->scratch) {
+      uint32_t hst = 0;
+      TRY(read_status(d->status, s, &hst));
+      TRY(status_to_error(hst));
+    }
+    p->occ = best_occ;
+    p->best_ms = best;
+    // capture the tuned decode into a graph, on a stream of our own (the caller's may be
+    // the legacy default stream, which cannot be captured); the stream is idle here
+    cudaStream_t cs = nullptr;
+    CU(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    g_occ_override = best_occ;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed);
+    nvdb_status st = e == cudaSuccess ? plan_run(p, cs) : fail(NVDB_ERR_CUDA, "stream capture: %s", cudaGetErrorString(e));
+    cudaGraph_t g = nullptr;
+    if (e == cudaSuccess) e = cudaStreamEndCapture(cs, &g);
+    g_occ_override = 0;
+    cudaStreamDestroy(cs);
+    TRY(st);
+    if (e != cudaSuccess) return fail(NVDB_ERR_CUDA, "stream capture: %s", cudaGetErrorString(e));
+    p->graph = g;
+    CU(cudaGraphInstantiate(&p->exec, p->graph, 0));
+    return NVDB_OK;
+  };
+  const nvdb_status st = run();
+  prof::g_on.store(prof_on);
+  if (st != NVDB_OK) { delete p; return st; }
+  *out = p;
+  return NVDB_OK;
+}
+
+extern "C" nvdb_status nvdb_plan_launch(nvdb_plan* p, nvdb_stream stream) {
+  if (!p || !p->exec) return fail(NVDB_ERR_INVALID_ARG, "nvdb_plan_launch: NULL plan");
+  CU(cudaGraphLaunch(p->exec, (cudaStream_t)stream));
+  return NVDB_OK;
+}
+
+extern "C" nvdb_status nvdb_plan_check(nvdb_plan* p, nvdb_stream stream) {
+  if (!p) return fail(NVDB_ERR_INVALID_ARG, "nvdb_plan_check: NULL plan");
+  for (auto* d : p->scratch) {
+    uint32_t hst = 0;
+    TRY(read_status(d->status, (cudaStream_t)stream, &hst));
+    TRY(status_to_error(hst));
+  }
+  return NVDB_OK;
+}
+
+extern "C" nvdb_status nvdb_plan_info(const nvdb_plan* p, int* tc_ctas_per_sm, float* tuned_ms) {
+  if (!p) return fail(NVDB_ERR_INVALID_ARG, "nvdb_plan_info: NULL plan");
+  if (tc_ctas_per_sm) *tc_ctas_per_sm = p->occ;
+  if (tuned_ms) *tuned_ms = p->best_ms;
+  return NVDB_OK;
+}
+
+extern "C" nvdb_status nvdb_plan_free(nvdb_plan* p) {
+  delete p;
   return NVDB_OK;
 }
