@@ -91,6 +91,9 @@ typedef struct {
   int32_t loss;         /* regressor loss: NVDB_LOSS_MSE or NVDB_LOSS_L1 */
   int32_t train_prec;   /* arithmetic of training: NVDB_FP32 */
   uint32_t patch_precs; /* bit p set = store patches for decoding at precision p (default: FP32|BF16|FP16) */
+  int32_t stop_window;  /* early stop (warm-started frames, Section 3.6): every stop_window steps ... */
+  float stop_loss[3];   /* ... network k stops once the mean of its last stop_window losses < stop_loss[k];
+                           0 = train all `steps` */
 } nvdb_train_opts;
 
 typedef struct {
@@ -124,7 +127,7 @@ nvdb_status nvdb_grid_free(nvdb_grid* grid);
 
 /* Fill opts with the defaults: widths 32, 3 layers, ffm_size 0, sigma 1.25,
  * 200 steps, batch 4096, lr 1e-3, decay 0.975 every 100 steps, MSE, FP32
- * training, patches for FP32, BF16 and FP16, seed 1. */
+ * training, patches for FP32, BF16 and FP16, seed 1, no early stop (window 50). */
 void nvdb_train_opts_default(nvdb_train_opts* opts);
 
 /* Encode a grid (Sections 3.2-3.3): initialise the three networks (Xavier
@@ -139,7 +142,8 @@ nvdb_status nvdb_compress(const nvdb_grid* grid, const nvdb_train_opts* opts, co
                           nvdb_stream stream, nvdb_model** out);
 
 /* Per-step mean training loss of network `net` of the last compress
- * (HOST buffer of cap floats); *count receives the number of steps. */
+ * (HOST buffer of cap floats); *count receives the number of steps run
+ * (fewer than opts->steps when the early stop triggered). */
 nvdb_status nvdb_model_losses(const nvdb_model* model, int net, float* losses, int64_t cap,
                               int64_t* count);
 

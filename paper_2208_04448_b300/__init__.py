@@ -135,10 +135,10 @@ def train_opts(**kw) -> N.TrainOpts:
     o = N.TrainOpts()
     lib().nvdb_train_opts_default(C.byref(o))
     for k, v in kw.items():
-        if k in ("width", "layers", "ffm_size"):
+        if k in ("width", "layers", "ffm_size", "stop_loss"):
             arr = getattr(o, k)
             for i, x in enumerate(v):
-                arr[i] = int(x)
+                arr[i] = float(x) if k == "stop_loss" else int(x)
         else:
             setattr(o, k, v)
     return o

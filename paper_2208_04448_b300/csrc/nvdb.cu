@@ -665,6 +665,7 @@ extern "C" void nvdb_train_opts_default(nvdb_train_opts* o) {
   o->loss = NVDB_LOSS_MSE;
   o->train_prec = NVDB_FP32;
   o->patch_precs = (1u << NVDB_FP32) | (1u << NVDB_BF16) | (1u << NVDB_FP16);
+  o->stop_window = 50;
 }
 
 namespace {
@@ -814,6 +815,8 @@ extern "C" nvdb_status nvdb_compress(const nvdb_grid* g, const nvdb_train_opts* 
       if ((st = ensure_partial(m, (int64_t)grid * (d.P + 1))) != NVDB_OK) break;
       TrainJob job = grid_train_job(g, k, o);
       job.partial = m->partial;
+      const bool early = o->stop_loss[k] > 0.f && o->stop_window > 0;
+      int ran = 0;
       for (int t = 1; t <= o->steps && st == NVDB_OK; ++t) {
         job.step = t;
         st = launch_train(m, k, job, grid, s);
@@ -823,11 +826,22 @@ extern "C" nvdb_status nvdb_compress(const nvdb_grid* g, const nvdb_train_opts* 
         KLAUNCH("adam_reduce", s, adam_reduce_kernel<<<blocks_for(d.P + 1, 256), 256, 0, s>>>(m->partial, grid, d.P, d.p32, d.m, d.v, t, lr_t,
                                                                     nullptr, d_loss + (t - 1), 1.f / (float)o->batch));
         if (cudaGetLastError() != cudaSuccess) st = fail(NVDB_ERR_CUDA, "adam launch failed");
+        ran = t;
+        if (early && t % o->stop_window == 0) {   // warm-start early stop (Section 3.6)
+          std::vector<float> w(o->stop_window);
+          cudaError_t e = cudaMemcpyAsync(w.data(), d_loss + (t - o->stop_window), o->stop_window * 4,
+                                          cudaMemcpyDeviceToHost, s);
+          if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+          if (e != cudaSuccess) { st = fail(NVDB_ERR_CUDA, "loss readback: %s", cudaGetErrorString(e)); break; }
+          double mean = 0.0;
+          for (float v : w) mean += v;
+          if (mean / o->stop_window < (double)o->stop_loss[k]) break;
+        }
       }
       if (st == NVDB_OK) {
-        m->losses[k].resize(o->steps);
-        if (o->steps) {
-          cudaError_t e = cudaMemcpyAsync(m->losses[k].data(), d_loss, o->steps * 4, cudaMemcpyDeviceToHost, s);
+        m->losses[k].resize(ran);
+        if (ran) {
+          cudaError_t e = cudaMemcpyAsync(m->losses[k].data(), d_loss, ran * 4, cudaMemcpyDeviceToHost, s);
           if (e == cudaSuccess) e = cudaStreamSynchronize(s);
           if (e != cudaSuccess) st = fail(NVDB_ERR_CUDA, "loss readback: %s", cudaGetErrorString(e));
         }

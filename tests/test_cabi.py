@@ -25,6 +25,6 @@ def test_library_exports_every_declared_symbol():
 
 def test_struct_layouts():
     import ctypes as C
-    assert C.sizeof(N.TrainOpts) == 80
+    assert C.sizeof(N.TrainOpts) == 96
     assert C.sizeof(N.Info) == 64 and N.Info.n_active.offset == 32
     assert C.sizeof(N.BuildOpts) == 8
