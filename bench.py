@@ -4,7 +4,8 @@
 Workload (default "union1024"): narrow-band SDF (half-width 3) of the union of
 32 spheres + 32 tori (seed 2) in a 1024^3 grid; three networks of 4 hidden
 layers x 64 (ReLU), Fourier features n = 64, sigma = 10 cycles per 1024 voxels;
-trained on the GPU (FP32, batch 65536, lr 1e-3 decayed 0.975 / 100 steps),
+trained on the GPU (tensor-core BF16 step by default, --train-prec; batch 65536,
+lr 1e-3 decayed 0.975 / 100 steps),
 then decoded in full.
 
 One timed step = one nvdb_decompress of the whole model: level-1 node origins
@@ -40,6 +41,7 @@ PRECS = {"fp32": 0, "bf16": 1, "fp16": 3}
 WORKLOAD_DESC = ("union of 32 spheres + 32 tori (seed 2), 1024^3, half-band 3; 3 nets 4x64 ReLU, "
                  "FFM n=64 sigma=10/1024vox; full decompress")
 NET_WIDTH, NET_LAYERS, FFM = [64, 64, 64], [4, 4, 4], [64, 64]
+TRAIN_KERNELS = ("train_fwd_bwd", "train_tc_bf16", "adam_reduce")
 
 
 def parse():
@@ -51,6 +53,7 @@ def parse():
     ap.add_argument("--prec", choices=list(PRECS), default="bf16")
     ap.add_argument("--train-steps", type=int, default=2500)
     ap.add_argument("--train-batch", type=int, default=65536)
+    ap.add_argument("--train-prec", choices=["fp32", "bf16"], default="bf16")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", choices=["union1024", "water2048"], default="union1024")
@@ -214,7 +217,8 @@ def run_water(args):
     import paper_2208_04448_b300 as nv
     from fixtures import water_frame
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-    shape = dict(width=NET_WIDTH, layers=NET_LAYERS, ffm_size=FFM, batch=args.train_batch, patch_precs=0b1011)
+    shape = dict(width=NET_WIDTH, layers=NET_LAYERS, ffm_size=FFM, batch=args.train_batch, patch_precs=0b1011,
+                 train_prec=PRECS[args.train_prec])
     models, steps, n_total, train_ms = [], [], 0, 0.0
     nv.profile_read()
     nv.profile_enable(True)
@@ -235,7 +239,7 @@ def run_water(args):
         models.append(m)
         del g, ijk, val
         prof = nv.profile_read()
-        train_ms += sum(v[1] for k, v in prof.items() if k in ("train_fwd_bwd", "adam_reduce"))
+        train_ms += sum(v[1] for k, v in prof.items() if k in TRAIN_KERNELS)
     nv.profile_enable(False)
     steps = np.array(steps)
     prec = PRECS[args.prec]
@@ -299,7 +303,8 @@ def main():
     n_active, n_leaf, n_l1 = info["n_active"], info["n_leaf"], info["n_l1"]
     opts = dict(seed=1, width=NET_WIDTH, layers=NET_LAYERS, ffm_size=FFM,
                 ffm_sigma=10.0 * (1 << info["log2_extent"]) / 1024.0, steps=args.train_steps,
-                batch=args.train_batch, lr=1e-3, lr_decay=0.975, lr_interval=100, patch_precs=0b1011)
+                batch=args.train_batch, lr=1e-3, lr_decay=0.975, lr_interval=100, patch_precs=0b1011,
+                train_prec=PRECS[args.train_prec])
     nv.profile_read()
     nv.profile_enable(True)
     torch.cuda.synchronize()
@@ -308,7 +313,7 @@ def main():
     train_wall = time.perf_counter() - t0
     prof = nv.profile_read()
     nv.profile_enable(False)
-    train_ms = sum(v[1] for k, v in prof.items() if k in ("train_fwd_bwd", "adam_reduce"))
+    train_ms = sum(v[1] for k, v in prof.items() if k in TRAIN_KERNELS)
     train_samples = 3 * args.train_steps * args.train_batch
     blob_bytes = model.export()
 
@@ -472,7 +477,7 @@ def main():
         train_samples_per_s=train_samples / (train_ms / 1e3) if train_ms > 0 else None,
         train=dict(steps=args.train_steps, batch=args.train_batch, wall_s=train_wall, kernel_ms=train_ms,
                    final_loss=[float(np.mean(model.losses(k)[-50:])) for k in range(3)] if args.train_steps else None,
-                   precision="fp32"),
+                   precision=args.train_prec),
         by_precision=by_prec,
         kernels={k: dict(launches=v[0], ms=v[1]) for k, v in sorted(head_kern.items(), key=lambda kv: -kv[1][1])},
     )

@@ -89,7 +89,7 @@ typedef struct {
   float lr_decay;       /* gamma: lr_t = lr * gamma^floor((t-1)/lr_interval) */
   int32_t lr_interval;  /* 0 = constant learning rate */
   int32_t loss;         /* regressor loss: NVDB_LOSS_MSE or NVDB_LOSS_L1 */
-  int32_t train_prec;   /* arithmetic of training: NVDB_FP32 */
+  int32_t train_prec;   /* arithmetic of training: NVDB_FP32 or NVDB_BF16 (tensor cores) */
   uint32_t patch_precs; /* bit p set = store patches for decoding at precision p (default: FP32|BF16|FP16) */
   int32_t stop_window;  /* early stop (warm-started frames, Section 3.6): every stop_window steps ... */
   float stop_loss[3];   /* ... network k stops once the mean of its last stop_window losses < stop_loss[k];
@@ -200,12 +200,16 @@ nvdb_status nvdb_mlp_eval(const nvdb_model* model, int net, nvdb_precision prec,
                           int64_t n, float* d_out, nvdb_stream stream);
 
 /* Gradient of the mean loss over n samples (d_ijk int32 [n][3], d_target
- * float [n]) w.r.t. the parameters of network `net`, FP32 (Section 3.2).
+ * float [n]) w.r.t. the parameters of network `net` (Section 3.2), in the
+ * arithmetic of one training step of precision `prec`: NVDB_FP32 (CUDA cores)
+ * or NVDB_BF16 (tensor cores: BF16 operands, FP32 accumulation, FP32 head and
+ * loss; at most 4 hidden layers); other precisions return NVDB_ERR_UNSUPPORTED.
  * d_grad float [nvdb_net_param_count] in storage order (W_0, b_0, ...,
  * W_{L-1}, b_{L-1}, w_h, b_h; W row-major [out][in]); *loss (HOST) the mean
  * loss.  loss_kind: NVDB_LOSS_*.  Synchronises the stream. */
-nvdb_status nvdb_mlp_grad(const nvdb_model* model, int net, const int32_t* d_ijk, const float* d_target,
-                          int64_t n, int loss_kind, float* d_grad, float* loss, nvdb_stream stream);
+nvdb_status nvdb_mlp_grad(const nvdb_model* model, int net, nvdb_precision prec, const int32_t* d_ijk,
+                          const float* d_target, int64_t n, int loss_kind, float* d_grad, float* loss,
+                          nvdb_stream stream);
 
 /* Same result as nvdb_mlp_grad, but allocates no device memory.  (The paper
  * has no counterpart; this exists for callers, not for the method.)  It is for
@@ -226,7 +230,7 @@ nvdb_status nvdb_mlp_grad(const nvdb_model* model, int net, const int32_t* d_ijk
  *    NVDB_ERR_CAPACITY.  Fewer thread blocks run than in nvdb_mlp_grad when the
  *    array cannot hold one partial per SM, so the summation order (and the
  *    last bits of the result) may differ.
- * Arguments, outputs and synchronisation as for nvdb_mlp_grad. */
+ * Arguments, outputs and synchronisation as for nvdb_mlp_grad with NVDB_FP32. */
 nvdb_status nvdb_mlp_grad_static(const nvdb_model* model, int net, const int32_t* d_ijk, const float* d_target,
                                  int64_t n, int loss_kind, float* d_grad, float* loss, nvdb_stream stream);
 

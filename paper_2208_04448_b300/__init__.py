@@ -225,11 +225,13 @@ def mlp_eval(model: Model, net: int, ijk: torch.Tensor, prec: int = FP32, stream
     return out
 
 
-def mlp_grad(model: Model, net: int, ijk: torch.Tensor, target: torch.Tensor, loss: int, stream=None):
+def mlp_grad(model: Model, net: int, ijk: torch.Tensor, target: torch.Tensor, loss: int, prec: int = FP32,
+             stream=None):
     g = torch.empty(model.param_count(net), dtype=torch.float32, device="cuda")
     lv = C.c_float()
-    _check(lib().nvdb_mlp_grad(model.handle, net, _dptr(ijk, torch.int32, "ijk"), _dptr(target, torch.float32, "target"),
-                               ijk.shape[0], loss, _dptr(g, torch.float32, "grad"), C.byref(lv), _stream(stream)))
+    _check(lib().nvdb_mlp_grad(model.handle, net, prec, _dptr(ijk, torch.int32, "ijk"),
+                               _dptr(target, torch.float32, "target"), ijk.shape[0], loss,
+                               _dptr(g, torch.float32, "grad"), C.byref(lv), _stream(stream)))
     return g, lv.value
 
 

@@ -51,7 +51,7 @@ SIGNATURES = {
     "nvdb_plan_free": ([_vp], _st),
     "nvdb_query": ([_vp, _vp, _i64, _i32, _vp, _vp, _vp], _st),
     "nvdb_mlp_eval": ([_vp, _i32, _i32, _vp, _i64, _vp, _vp], _st),
-    "nvdb_mlp_grad": ([_vp, _i32, _vp, _vp, _i64, _i32, _vp, _f32p, _vp], _st),
+    "nvdb_mlp_grad": ([_vp, _i32, _i32, _vp, _vp, _i64, _i32, _vp, _f32p, _vp], _st),
     "nvdb_mlp_grad_static": ([_vp, _i32, _vp, _vp, _i64, _i32, _vp, _f32p, _vp], _st),
     "nvdb_net_param_count": ([_vp, _i32], C.c_int64),
     "nvdb_model_info": ([_vp, C.POINTER(Info)], _st),

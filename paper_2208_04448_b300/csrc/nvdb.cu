@@ -23,6 +23,7 @@
 #include "mlp.cuh"
 #include "query.cuh"
 #include "train.cuh"
+#include "train_tc.cuh"
 
 using namespace nvdb;
 
@@ -241,7 +242,7 @@ struct DevNet {
   int n_in = 0, width = 0, layers = 0;
   int64_t P = 0;
   float* p32 = nullptr;
-  uint8_t* wpk = nullptr;   // [FP16 | BF16 hi | BF16 lo] weight tiles
+  uint8_t* wpk = nullptr;   // [FP16 | BF16 hi | BF16 lo] weight tiles, then BF16 W_l^T tiles
   float* m = nullptr;
   float* v = nullptr;
   ~DevNet() { dfree(p32); dfree(wpk); dfree(m); dfree(v); }
@@ -453,16 +454,50 @@ nvdb_status launch_train_t(const NetView& nv, const TrainJob& job, int grid, cud
   return NVDB_OK;
 }
 
-nvdb_status launch_train(const nvdb_model* m, int k, TrainJob job, int grid, cudaStream_t s) {
+template <int NIN, int W>
+nvdb_status launch_train_tc_t(const NetView& nv, const TrainJob& job, int grid, cudaStream_t s) {
+  const size_t smem = TrainTcLayout<NIN, W>(nv.layers).total;
+  if (smem > (size_t)kSmemPerSm - 1024) return fail(NVDB_ERR_UNSUPPORTED, "training tile needs %zu bytes of shared memory", smem);
+  CU(cudaFuncSetAttribute(train_tc_kernel<NIN, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  KLAUNCH("train_tc_bf16", s, train_tc_kernel<NIN, W><<<grid, kTile, smem, s>>>(nv, job));
+  CU(cudaGetLastError());
+  return NVDB_OK;
+}
+
+// Blocks of one training launch: one per 128-sample tile, at most one per SM (both
+// kernels are persistent over tiles).
+int train_grid(int64_t batch) { return (int)std::min<int64_t>((batch + kTile - 1) / kTile, num_sms()); }
+
+bool train_prec_ok(int prec) { return prec == NVDB_FP32 || prec == NVDB_BF16; }
+
+nvdb_status launch_train(const nvdb_model* m, int k, int prec, TrainJob job, int grid, cudaStream_t s) {
   const NetView nv = net_view(m, k);
   job.ox = m->origin[0];
   job.oy = m->origin[1];
   job.oz = m->origin[2];
-  if (nv.n_in == 32 && nv.width == 32) return launch_train_t<32, 32>(nv, job, grid, s);
-  if (nv.n_in == 32 && nv.width == 64) return launch_train_t<32, 64>(nv, job, grid, s);
-  if (nv.n_in == 64 && nv.width == 32) return launch_train_t<64, 32>(nv, job, grid, s);
-  if (nv.n_in == 64 && nv.width == 64) return launch_train_t<64, 64>(nv, job, grid, s);
+  if (!job.status) job.status = m->status;
+  if (prec == NVDB_BF16) {
+    if (nv.layers > kTrainTcMaxLayers)
+      return fail(NVDB_ERR_UNSUPPORTED, "BF16 training: at most %d hidden layers", kTrainTcMaxLayers);
+    if (nv.n_in == 32 && nv.width == 32) return launch_train_tc_t<32, 32>(nv, job, grid, s);
+    if (nv.n_in == 32 && nv.width == 64) return launch_train_tc_t<32, 64>(nv, job, grid, s);
+    if (nv.n_in == 64 && nv.width == 32) return launch_train_tc_t<64, 32>(nv, job, grid, s);
+    if (nv.n_in == 64 && nv.width == 64) return launch_train_tc_t<64, 64>(nv, job, grid, s);
+  } else if (prec == NVDB_FP32) {
+    if (nv.n_in == 32 && nv.width == 32) return launch_train_t<32, 32>(nv, job, grid, s);
+    if (nv.n_in == 32 && nv.width == 64) return launch_train_t<32, 64>(nv, job, grid, s);
+    if (nv.n_in == 64 && nv.width == 32) return launch_train_t<64, 32>(nv, job, grid, s);
+    if (nv.n_in == 64 && nv.width == 64) return launch_train_t<64, 64>(nv, job, grid, s);
+  } else {
+    return fail(NVDB_ERR_UNSUPPORTED, "training precision %d", prec);
+  }
   return fail(NVDB_ERR_UNSUPPORTED, "network shape n=%d w=%d", nv.n_in, nv.width);
+}
+
+Bf16Repack repack_of(const DevNet& d, int prec) {
+  Bf16Repack rp{};
+  if (prec == NVDB_BF16) rp = Bf16Repack{d.wpk, d.n_in, d.width, d.layers};
+  return rp;
 }
 
 nvdb_status read_status(uint32_t* d_status, cudaStream_t s, uint32_t* out) {
@@ -488,7 +523,7 @@ nvdb_status upload_net(nvdb_model* m, int k, const float* host_params, cudaStrea
   d.P = net_param_count(d.n_in, d.width, d.layers);
   dfree(d.p32); dfree(d.wpk); dfree(d.m); dfree(d.v);
   TRY(dalloc(&d.p32, (size_t)d.P));
-  TRY(dalloc(&d.wpk, (size_t)wtile_elems(d.n_in, d.width, d.layers) * 6 + 64));
+  TRY(dalloc(&d.wpk, (size_t)wpk_bytes(d.n_in, d.width, d.layers) + 64));
   if (host_params) CU(cudaMemcpyAsync(d.p32, host_params, d.P * 4, cudaMemcpyHostToDevice, s));
   return NVDB_OK;
 }
@@ -497,6 +532,10 @@ nvdb_status pack_net(nvdb_model* m, int k, cudaStream_t s) {
   DevNet& d = m->net[k];
   KLAUNCH("pack_weights", s, pack_weights_kernel<<<64, 256, 0, s>>>(d.p32, d.wpk, d.n_in, d.width, d.layers));
   CU(cudaGetLastError());
+  if (d.layers > 1) {
+    KLAUNCH("pack_weights_t", s, pack_weights_t_kernel<<<16, 256, 0, s>>>(d.p32, d.wpk, d.n_in, d.width, d.layers));
+    CU(cudaGetLastError());
+  }
   return NVDB_OK;
 }
 
@@ -749,7 +788,7 @@ extern "C" nvdb_status nvdb_compress(const nvdb_grid* g, const nvdb_train_opts* 
   if (o->steps < 0 || o->batch <= 0 || !(o->lr >= 0.f) || o->lr_interval < 0)
     return fail(NVDB_ERR_INVALID_ARG, "nvdb_compress: bad steps/batch/lr");
   if (o->loss != NVDB_LOSS_MSE && o->loss != NVDB_LOSS_L1) return fail(NVDB_ERR_INVALID_ARG, "loss must be MSE or L1");
-  if (o->train_prec != NVDB_FP32) return fail(NVDB_ERR_UNSUPPORTED, "training precision %d", o->train_prec);
+  if (!train_prec_ok(o->train_prec)) return fail(NVDB_ERR_UNSUPPORTED, "training precision %d", o->train_prec);
   if (g->n == 0) return fail(NVDB_ERR_INVALID_ARG, "nvdb_compress: empty grid");
   if ((uint64_t)g->n_leaf * 512 >= (1ull << 32) || (uint64_t)g->n_l1 * 4096 >= (1ull << 32))
     return fail(NVDB_ERR_UNSUPPORTED, "candidate population >= 2^32");
@@ -772,6 +811,11 @@ extern "C" nvdb_status nvdb_compress(const nvdb_grid* g, const nvdb_train_opts* 
       m->ffm[1] = o->ffm_size[1] ? o->ffm_size[1] : std::max(o->width[1], o->width[2]);
     }
     TRY(check_model_shapes(m));
+    if (o->train_prec == NVDB_BF16)
+      for (int k = 0; k < 3; ++k)
+        if (m->layers[k] > kTrainTcMaxLayers)
+          return fail(NVDB_ERR_UNSUPPORTED, "BF16 training: network %d has %d hidden layers (at most %d)", k,
+                      m->layers[k], kTrainTcMaxLayers);
     TRY(dalloc(&m->status, 1));
     CU(cudaMemsetAsync(m->status, 0, 4, s));
     const double E = std::ldexp(1.0, m->log2e);
@@ -806,7 +850,7 @@ extern "C" nvdb_status nvdb_compress(const nvdb_grid* g, const nvdb_train_opts* 
     TRY(copy_int4_to3(g->l2_origin, g->n_l2, m->l2_origin_host.data(), s));
     CU(cudaMemcpyAsync(m->l2_mask_host.data(), g->l2_mask, g->n_l2 * 4096, cudaMemcpyDeviceToHost, s));
     // training: each network for `steps` Adam steps
-    const int grid = (int)std::min<int64_t>((o->batch + kTile - 1) / kTile, num_sms());
+    const int grid = train_grid(o->batch);
     float* d_loss = nullptr;
     TRY(dalloc(&d_loss, (size_t)std::max(1, o->steps)));
     nvdb_status st = NVDB_OK;
@@ -815,16 +859,18 @@ extern "C" nvdb_status nvdb_compress(const nvdb_grid* g, const nvdb_train_opts* 
       if ((st = ensure_partial(m, (int64_t)grid * (d.P + 1))) != NVDB_OK) break;
       TrainJob job = grid_train_job(g, k, o);
       job.partial = m->partial;
+      if (o->train_prec == NVDB_BF16 && (st = pack_net(m, k, s)) != NVDB_OK) break;   // the BF16 tiles of step 1
       const bool early = o->stop_loss[k] > 0.f && o->stop_window > 0;
       int ran = 0;
       for (int t = 1; t <= o->steps && st == NVDB_OK; ++t) {
         job.step = t;
-        st = launch_train(m, k, job, grid, s);
+        st = launch_train(m, k, o->train_prec, job, grid, s);
         if (st != NVDB_OK) break;
         const float lr_t = o->lr_interval > 0 ? (float)((double)o->lr * std::pow((double)o->lr_decay, (double)((t - 1) / o->lr_interval)))
                                               : o->lr;
         KLAUNCH("adam_reduce", s, adam_reduce_kernel<<<blocks_for(d.P + 1, 256), 256, 0, s>>>(m->partial, grid, d.P, d.p32, d.m, d.v, t, lr_t,
-                                                                    nullptr, d_loss + (t - 1), 1.f / (float)o->batch));
+                                                                    nullptr, d_loss + (t - 1), 1.f / (float)o->batch,
+                                                                    repack_of(d, o->train_prec)));
         if (cudaGetLastError() != cudaSuccess) st = fail(NVDB_ERR_CUDA, "adam launch failed");
         ran = t;
         if (early && t % o->stop_window == 0) {   // warm-start early stop (Section 3.6)
@@ -1127,16 +1173,18 @@ extern "C" int64_t nvdb_net_param_count(const nvdb_model* m, int net) {
   return m->net[net].P;
 }
 
-extern "C" nvdb_status nvdb_mlp_grad(const nvdb_model* cm, int net, const int32_t* d_ijk, const float* d_target,
-                                     int64_t n, int loss_kind, float* d_grad, float* loss, nvdb_stream stream) {
+extern "C" nvdb_status nvdb_mlp_grad(const nvdb_model* cm, int net, nvdb_precision prec, const int32_t* d_ijk,
+                                     const float* d_target, int64_t n, int loss_kind, float* d_grad, float* loss,
+                                     nvdb_stream stream) {
   if (!cm || net < 0 || net > 2 || n <= 0 || !d_ijk || !d_target || !d_grad)
     return fail(NVDB_ERR_INVALID_ARG, "nvdb_mlp_grad: bad arguments");
+  if (!train_prec_ok(prec)) return fail(NVDB_ERR_UNSUPPORTED, "nvdb_mlp_grad: precision %d", (int)prec);
   if (loss_kind < 0 || loss_kind > 2) return fail(NVDB_ERR_INVALID_ARG, "unknown loss %d", loss_kind);
   if (n > (1ll << 31)) return fail(NVDB_ERR_UNSUPPORTED, "nvdb_mlp_grad: n >= 2^31");
   nvdb_model* m = const_cast<nvdb_model*>(cm);
   cudaStream_t s = (cudaStream_t)stream;
   const DevNet& d = m->net[net];
-  const int grid = (int)std::min<int64_t>((n + kTile - 1) / kTile, num_sms());
+  const int grid = train_grid(n);
   TRY(ensure_partial(m, (int64_t)grid * (d.P + 1)));
   TrainJob j{};
   j.net = net;
@@ -1146,16 +1194,21 @@ extern "C" nvdb_status nvdb_mlp_grad(const nvdb_model* cm, int net, const int32_
   j.ijk_list = d_ijk;
   j.target_list = d_target;
   j.partial = m->partial;
-  TRY(launch_train(m, net, j, grid, s));
+  TRY(launch_train(m, net, prec, j, grid, s));
   float* d_loss = nullptr;
   TRY(dalloc(&d_loss, 1));
   KLAUNCH("adam_reduce", s, adam_reduce_kernel<<<blocks_for(d.P + 1, 256), 256, 0, s>>>(m->partial, grid, d.P, nullptr, nullptr, nullptr, 1, 0.f,
-                                                              d_grad, d_loss, 1.f / (float)n));
+                                                              d_grad, d_loss, 1.f / (float)n, Bf16Repack{}));
   float h = 0.f;
   cudaError_t e = cudaMemcpyAsync(&h, d_loss, 4, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   dfree(d_loss);
   if (e != cudaSuccess) return fail(NVDB_ERR_CUDA, "nvdb_mlp_grad: %s", cudaGetErrorString(e));
+  if (prec == NVDB_BF16) {
+    uint32_t hst = 0;
+    TRY(read_status(m->status, s, &hst));
+    TRY(status_to_error(hst));
+  }
   if (loss) *loss = h;
   return NVDB_OK;
 }
@@ -1466,7 +1519,7 @@ extern "C" nvdb_status nvdb_mlp_grad_static(const nvdb_model* m, int net, const 
   else if (nv.n_in == 64 && nv.width == 64) TRY((launch_train_static<64, 64>(nv, j, grid, s)));
   else return fail(NVDB_ERR_UNSUPPORTED, "network shape n=%d w=%d", nv.n_in, nv.width);
   adam_reduce_kernel<<<blocks_for(d.P + 1, 256), 256, 0, s>>>(scratch, grid, d.P, nullptr, nullptr, nullptr, 1, 0.f,
-                                                              d_grad, loss_slot, 1.f / (float)n);
+                                                              d_grad, loss_slot, 1.f / (float)n, Bf16Repack{});
   CU(cudaGetLastError());
   float h = 0.f;
   CU(cudaMemcpyAsync(&h, loss_slot, sizeof h, cudaMemcpyDeviceToHost, s));

@@ -30,6 +30,7 @@ struct TrainJob {
   const int32_t* ijk; const float* val; int64_t n;
   float tscale;               // regressor target = val * tscale
   float* partial;             // [gridDim.x][P + 1]: gradient partials, then the loss sum
+  uint32_t* status;           // ST_* bits (tensor-core kernel: a timed-out wait)
 };
 
 enum : int { LOSS_MSE = 0, LOSS_L1 = 1, LOSS_BCE = 2 };
@@ -228,9 +229,52 @@ __global__ void __launch_bounds__(kTile, 1) train_fwd_bwd_kernel(NetView net, Tr
   }
 }
 
+// Transposed hidden-layer tiles W_l^T, l = 1..L-1: [W (in) x W (out)] BF16,
+// canonical K-major over `out`; stored after the three forward tile copies.
+__host__ __device__ inline int64_t wtile_t_elems(int w, int L) { return (int64_t)(L - 1) * w * w; }
+__host__ __device__ inline int64_t wpk_bytes(int nin, int w, int L) {
+  return wtile_elems(nin, w, L) * 6 + wtile_t_elems(w, L) * 2;
+}
+
+// Byte offsets, inside the packed buffer, of the BF16 copies of parameter e that the
+// training kernel reads: `fo` in the BF16 forward tile (layer-0 columns interleaved
+// as (cos_f, sin_f)), `to` in the transposed tile (hidden-layer weights only).
+// Head parameters have neither (-1).
+__device__ __forceinline__ void bf16_tile_offsets(int64_t e, int nin, int W, int L, int64_t& fo, int64_t& to) {
+  const int64_t te = wtile_elems(nin, W, L);
+  fo = -1;
+  to = -1;
+  int64_t base = 0, tbase = 0;
+  for (int l = 0; l < L; ++l) {
+    const int K = l == 0 ? nin : W;
+    const int64_t sz = (int64_t)W * K + W;
+    if (e < base + sz) {
+      const int64_t r = e - base;
+      if (r < (int64_t)W * K) {
+        const int o = (int)(r / K), j = (int)(r % K);
+        const int i = l == 0 ? (j < nin / 2 ? 2 * j : 2 * (j - nin / 2) + 1) : j;
+        fo = te * 2 + tbase * 2 + canon_off(o, i, K + 16);
+        if (l > 0) to = te * 6 + (int64_t)(l - 1) * W * W * 2 + canon_off(j, o, W);
+      } else {
+        fo = te * 2 + tbase * 2 + canon_off((int)(r - (int64_t)W * K), K, K + 16);
+      }
+      return;
+    }
+    base += sz;
+    tbase += (int64_t)W * (K + 16);
+  }
+}
+
+// Where the Adam step also refreshes the BF16 tiles the tensor-core training kernel reads.
+struct Bf16Repack {
+  uint8_t* wpk;               // nullptr: no refresh
+  int nin, W, L;
+};
+
 // Sum the per-CTA partials in CTA order; then Adam (or just write the gradient).
 __global__ void adam_reduce_kernel(const float* partial, int nparts, int64_t P, float* params, float* m, float* v,
-                                   int step, float lr_t, float* grad_out, float* loss_out, float loss_scale) {
+                                   int step, float lr_t, float* grad_out, float* loss_out, float loss_scale,
+                                   Bf16Repack rp) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e > P) return;
   float g = 0.f;
@@ -248,7 +292,15 @@ __global__ void adam_reduce_kernel(const float* partial, int nparts, int64_t P, 
     v[e] = vv;
     const float mhat = mm / (1.f - powf(b1, (float)step));
     const float vhat = vv / (1.f - powf(b2, (float)step));
-    params[e] -= lr_t * mhat / (sqrtf(vhat) + 1e-8f);
+    const float w = params[e] - lr_t * mhat / (sqrtf(vhat) + 1e-8f);
+    params[e] = w;
+    if (rp.wpk) {
+      int64_t fo, to;
+      bf16_tile_offsets(e, rp.nin, rp.W, rp.L, fo, to);
+      const __nv_bfloat16 b = __float2bfloat16_rn(w);
+      if (fo >= 0) *reinterpret_cast<__nv_bfloat16*>(rp.wpk + fo) = b;
+      if (to >= 0) *reinterpret_cast<__nv_bfloat16*>(rp.wpk + to) = b;
+    }
   }
 }
 

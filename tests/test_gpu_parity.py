@@ -21,6 +21,16 @@ pytestmark = pytest.mark.gpu
 FP32_TOL = 1e-5
 GRAD_TOL = 1e-4
 BF16_TOL = 2e-2
+# BF16 training arithmetic rounds each operand of the forward, delta and weight-gradient
+# products once to BF16 (unit roundoff u = 2^-9).  How much a gradient moves under
+# such roundings depends on the network and the loss (sign-based L1 gradients move
+# most), so the bar is relative to a measured sensitivity: per parameter block, the
+# relative L2 error may be at most BF16_GRAD_K times the relative change of the FP64
+# gradient when only the weights are rounded to BF16 (the kernel rounds weights,
+# activations and deltas: a few roundings of the same size), plus u as a floor.
+BF16_GRAD_K = 3.0
+BF16_U = 2.0 ** -9
+BF16_LOSS_TOL = 1e-2
 
 
 def _cuda(a, dtype):
@@ -129,12 +139,13 @@ def test_mlp_eval_parity(sphere128, shape, prec):
 
 # ---------------------------------------------------------------------------- gradients
 
-@pytest.mark.parametrize("net,loss", [(0, 2), (1, 2), (2, 0), (2, 1)])
-def test_gradient_parity(sphere128, net, loss):
+@pytest.mark.parametrize("net,loss,n", [(0, 2, 1000), (1, 2, 1000), (2, 0, 1000), (2, 1, 1000), (2, 0, 37965)])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_gradient_parity(sphere128, net, loss, n, prec):
+    """n = 37965: 297 tiles (ragged), so blocks accumulate two or three tiles each."""
     ijk, val, ref = sphere128
     om, m = _imported(ref, 9, [32, 64, 64], [3, 4, 4], [32, 64])
     r = np.random.default_rng(net * 3 + loss)
-    n = 1000
     pts = ref["ijk"][r.integers(0, ref["n"], n)].astype(np.int32)
     tgt = (r.random(n) > 0.5).astype(np.float32) if loss == 2 else r.standard_normal(n).astype(np.float32)
     y, cache = N.forward(om["nets"][net], N.encode(codec.level_coords(om, net, pts), codec.level_q(om, net)))
@@ -142,10 +153,43 @@ def test_gradient_parity(sphere128, net, loss):
         tgt = (y + np.where(r.random(n) > 0.5, 0.3, -0.3)).astype(np.float32)
     lref, gy = N.loss_and_grad(y, tgt.astype(np.float64), loss)
     gref = N.flatten(N.backward(om["nets"][net], cache, gy))
-    g, lgot = nv.mlp_grad(m, net, _cuda(pts, torch.int32), _cuda(tgt, torch.float32), loss)
+    g, lgot = nv.mlp_grad(m, net, _cuda(pts, torch.int32), _cuda(tgt, torch.float32), loss, prec)
     g = g.cpu().numpy()
-    assert np.abs(g - gref).max() <= GRAD_TOL * np.abs(gref).max()
-    assert abs(lgot - lref) <= 1e-5 * max(1.0, abs(lref))
+    if prec == 0:
+        assert np.abs(g - gref).max() <= GRAD_TOL * np.abs(gref).max()
+        assert abs(lgot - lref) <= 1e-5 * max(1.0, abs(lref))
+    else:
+        assert abs(lgot - lref) <= BF16_LOSS_TOL * max(1.0, abs(lref))
+        p = om["nets"][net]
+        pb = dict(W=[_round_bf16(W) for W in p["W"]], b=[_round_bf16(b) for b in p["b"]], wh=p["wh"], bh=p["bh"])
+        yb, cb = N.forward(pb, N.encode(codec.level_coords(om, net, pts), codec.level_q(om, net)))
+        gsens = N.flatten(N.backward(pb, cb, N.loss_and_grad(yb, tgt.astype(np.float64), loss)[1]))
+        sizes = [x for W, b in zip(p["W"], p["b"]) for x in (np.size(W), np.size(b))] + [np.size(p["wh"]), 1]
+        o = 0
+        for sz in sizes:   # blocks W_0, b_0, ..., W_{L-1}, b_{L-1}, w_h, b_h
+            a, b, c = g[o:o + sz], gref[o:o + sz], gsens[o:o + sz]
+            nb = max(np.linalg.norm(b), 1e-30)
+            sens = np.linalg.norm(c - b) / nb
+            assert np.linalg.norm(a - b) / nb <= BF16_GRAD_K * sens + BF16_U, (o, sz, sens)
+            o += sz
+        assert o == g.size
+
+
+def _round_bf16(a):
+    """Round to the nearest BF16 value (ties to even), returned as float64."""
+    u = np.asarray(a, np.float32).copy().view(np.uint32).astype(np.uint64)
+    u = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def test_gradient_precision_errors(sphere128):
+    ijk, val, ref = sphere128
+    om, m = _imported(ref, 9, [32, 64, 64], [3, 4, 4], [32, 64])
+    pts = _cuda(ref["ijk"][:256], torch.int32)
+    tgt = torch.zeros(256, device="cuda")
+    for bad in (2, 3, 7):
+        with pytest.raises(nv.NvdbError):
+            nv.mlp_grad(m, 2, pts, tgt, 0, bad)
 
 
 def test_first_adam_step_and_sample_stream(sphere128):
@@ -175,6 +219,39 @@ def test_training_trajectory_matches_oracle(sphere128):
         got = m.losses(k)
         assert abs(got[-20:].mean() - ls[-20:].mean()) <= 0.05 * ls[-20:].mean()
         assert abs(got[0] - ls[0]) <= 1e-5 * max(1.0, ls[0])
+
+
+def test_bf16_training_tracks_fp32(sphere128):
+    """Tensor-core (BF16) training from the same initial weights and Philox batches as FP32
+    training: the first loss agrees within the BF16 forward bar, the trained loss reaches the
+    FP32 run's level, and the trained model decodes with exact topology."""
+    ijk, val, ref = sphere128
+    g = _grid(ijk, val)
+    kw = dict(seed=3, ffm_sigma=1.25, steps=200, batch=4096, patch_precs=0b1011, width=[32, 64, 64],
+              layers=[3, 4, 4], ffm_size=[32, 64])
+    m32 = nv.compress(g, train_prec=0, **kw)
+    m16 = nv.compress(g, train_prec=1, **kw)
+    for k in range(3):
+        a, b = m32.losses(k), m16.losses(k)
+        assert len(a) == len(b) == 200
+        assert abs(b[0] - a[0]) <= BF16_LOSS_TOL * max(1.0, a[0])
+        assert b[-20:].mean() <= 1.25 * a[-20:].mean() + 1e-4
+    om = blob.read(m16.export())
+    for prec in (0, 3):
+        dijk, dval, cnt = nv.decompress(m16, prec)
+        assert cnt == [ref["n"]] and np.array_equal(dijk.cpu().numpy(), ref["ijk"])
+    want, scale = oracle_forward_scale(om, 2, ref["ijk"])
+    assert rel_err(nv.decompress(m16, 0)[1].cpu().numpy() / 3.0, want, scale).max() <= FP32_TOL
+
+
+def test_training_precision_errors(sphere128):
+    ijk, val, ref = sphere128
+    g = _grid(ijk, val)
+    for bad in (2, 3):
+        with pytest.raises(nv.NvdbError):
+            nv.compress(g, train_prec=bad, steps=1)
+    with pytest.raises(nv.NvdbError):   # the tensor-core step holds at most 4 hidden layers
+        nv.compress(g, train_prec=1, steps=1, layers=[5, 3, 3])
 
 
 # ---------------------------------------------------------------------------- decode
