@@ -144,29 +144,44 @@ def primitives_union(prims, grid: int, half_width: float = 3.0, device="cpu",
         pj = pj.repeat_interleave(off.shape[0])
         del nparent
         s = child
-    # voxel level: pairs (8^3 block, primitive) -> per-voxel min over the block's primitives
+    # voxel level: pairs (8^3 block, primitive) -> per-voxel min over the block's primitives,
+    # one chunk of blocks (in key order) at a time so that memory stays bounded
     assert s == 8
     key = (blk[:, 0] * grid + blk[:, 1]) * grid + blk[:, 2]
-    ublk, inv = torch.unique(key, return_inverse=True)
-    dmin = torch.full((ublk.shape[0], 512), float("inf"), dtype=F64, device=dev)
+    key, order = torch.sort(key)
+    pj = pj[order]
+    del blk, order
+    ublk, counts = torch.unique_consecutive(key, return_counts=True)
+    del key
+    ends = torch.cumsum(counts, 0)
+    ends_h = ends.cpu()
     off8 = _cube_offsets(8, dev)
-    step = max(1, chunk // 512)
-    for a in range(0, blk.shape[0], step):
-        b = blk[a:a + step]
-        vox = (b[:, None, :] + off8[None]).reshape(-1, 3)
-        jj = pj[a:a + step].repeat_interleave(512)
-        d = tab.sdf(vox.to(F64), jj).reshape(-1, 512)
-        idx = inv[a:a + step][:, None].expand(-1, 512)
-        dmin.scatter_reduce_(0, idx, d, reduce="amin")
-    bz = ublk % grid
-    by = (ublk // grid) % grid
-    bx = ublk // (grid * grid)
-    borg = torch.stack([bx, by, bz], 1)
-    vox = (borg[:, None, :] + off8[None]).reshape(-1, 3)
-    d = dmin.reshape(-1)
-    inside = ((vox >= 0) & (vox < grid)).all(1)
-    act = inside & (d.abs() < w)
-    return vox[act].to(torch.int32), d[act].to(torch.float32)
+    bstep = max(1, chunk // 512)
+    outs_ijk, outs_val = [], []
+    for a in range(0, ublk.shape[0], bstep):
+        b_hi = min(a + bstep, ublk.shape[0])
+        p_lo = int(ends_h[a - 1]) if a > 0 else 0
+        p_hi = int(ends_h[b_hi - 1])
+        ub = ublk[a:b_hi]
+        borg = torch.stack([ub // (grid * grid), (ub // grid) % grid, ub % grid], 1)
+        dmin = torch.full((b_hi - a, 512), float("inf"), dtype=F64, device=dev)
+        # block of each pair, relative to the chunk
+        rel = torch.repeat_interleave(torch.arange(b_hi - a, device=dev), counts[a:b_hi])
+        for q in range(p_lo, p_hi, bstep):
+            r = rel[q - p_lo:min(q + bstep, p_hi) - p_lo]
+            vox = (borg[r][:, None, :] + off8[None]).reshape(-1, 3)
+            jj = pj[q:q + r.shape[0]].repeat_interleave(512)
+            d = tab.sdf(vox.to(F64), jj).reshape(-1, 512)
+            dmin.scatter_reduce_(0, r[:, None].expand(-1, 512), d, reduce="amin")
+        vox = (borg[:, None, :] + off8[None]).reshape(-1, 3)
+        d = dmin.reshape(-1)
+        inside = ((vox >= 0) & (vox < grid)).all(1)
+        act = inside & (d.abs() < w)
+        outs_ijk.append(vox[act].to(torch.int32))
+        outs_val.append(d[act].to(torch.float32))
+    if not outs_ijk:
+        return torch.zeros((0, 3), dtype=torch.int32, device=dev), torch.zeros(0, dtype=torch.float32, device=dev)
+    return torch.cat(outs_ijk), torch.cat(outs_val)
 
 
 def sphere_band(grid=128, centre=(64.0, 64.0, 64.0), radius=40.0, half_width=3.0, device="cpu"):
@@ -316,7 +331,10 @@ def water_frame(frame: int, nx=2048, ny=256, nz=2048, y0=128.0, half_width=3.0, 
 
 def query_points(ijk: torch.Tensor, n: int, seed: int = 5) -> torch.Tensor:
     """n float32 points: an occupied 128^3 node picked uniformly, then a point uniform in its box."""
-    nodes = torch.unique(ijk.to(torch.int64).cpu() >> 7, dim=0).numpy()
+    node = ijk.to(torch.int64) >> 7                  # on the tensor's device
+    key = torch.unique((node[:, 0] << 42) | (node[:, 1] << 21) | node[:, 2]).cpu()   # lexicographic order
+    del node
+    nodes = torch.stack([key >> 42, (key >> 21) & ((1 << 21) - 1), key & ((1 << 21) - 1)], 1).numpy()
     rng = np.random.Generator(np.random.PCG64(seed))
     pick = rng.integers(0, nodes.shape[0], n)
     u = rng.uniform(0.0, 128.0, (n, 3))

@@ -1,0 +1,107 @@
+"""The fog configurations (Section 3.2: a fog volume's regressor learns the density itself,
+the background of inactive voxels is 0): a small 64^3 fBm fog checked in full against the
+FP64 oracle, and the 512^3 fBm fog with its own network shapes (regressor 4x64,
+classifiers 3x32, one FFM of size 64), 2000 BF16 training steps of batch 65536, decoded
+in full with exact topology and sampled values."""
+import numpy as np
+import pytest
+import torch
+
+import paper_2208_04448_b300 as nv
+from fixtures import query_points, workload
+from gpu_helpers import oracle_forward_scale, rel_err
+from oracle import blob, codec, vdb
+
+pytestmark = pytest.mark.gpu
+
+FP32_TOL = 1e-5
+TC_TOL = 2e-2        # density is regressed unscaled: the bar is 2e-2 absolute
+FOG_SHAPE = dict(width=[32, 32, 64], layers=[3, 3, 4], ffm_size=[64, 64])
+
+
+def _cuda(a, dtype):
+    return torch.as_tensor(np.ascontiguousarray(a)).to(device="cuda", dtype=dtype).contiguous()
+
+
+@pytest.fixture(scope="module")
+def fog64():
+    ijk, val, meta = workload("fog64")
+    assert meta["grid_class"] == 1
+    ijk, val = ijk.numpy(), val.numpy()
+    return ijk, val, vdb.build(ijk, val)
+
+
+def test_fog_build_bit_exact(fog64):
+    ijk, val, ref = fog64
+    g = nv.build(_cuda(ijk, torch.int32), _cuda(val, torch.float32), 1, 0.0)
+    got = g.read()
+    info = g.info()
+    assert info["grid_class"] == 1 and info["background"] == 0.0
+    for k in ("ijk", "val", "leaf_origin", "leaf_mask", "l1_origin", "l1_mask"):
+        assert np.array_equal(got[k], ref[k]), k
+
+
+@pytest.mark.parametrize("train_prec", [0, 1])
+def test_fog_decode_and_query_parity(fog64, train_prec):
+    ijk, val, ref = fog64
+    g = nv.build(_cuda(ijk, torch.int32), _cuda(val, torch.float32), 1, 0.0)
+    m = nv.compress(g, seed=8, ffm_sigma=1.25, steps=150, batch=8192, train_prec=train_prec, patch_precs=0b1011,
+                    **FOG_SHAPE)
+    om = blob.read(m.export())
+    assert om["grid_class"] == 1 and om["background"] == 0.0
+    want, scale = oracle_forward_scale(om, codec.REG, ref["ijk"])
+    for prec in (0, 1, 3):
+        dijk, dval, cnt = nv.decompress(m, prec)
+        assert cnt == [ref["n"]]
+        assert np.array_equal(dijk.cpu().numpy(), ref["ijk"])           # exact topology, canonical order
+        dv = dval.cpu().numpy().astype(np.float64)
+        if prec == 0:
+            assert rel_err(dv, want, scale).max() <= FP32_TOL            # density: no value scale
+        else:
+            assert np.abs(dv - want).max() <= TC_TOL
+    # queries: inactive corners take the fog background 0
+    pts = query_points(torch.from_numpy(ref["ijk"]), 20000, seed=11)
+    out, act = nv.query(m, pts.cuda().contiguous(), 0, active=True)
+    keys = np.sort(vdb.canonical_key(ref["ijk"]))
+    qwant, bits = codec.query(om, pts.numpy(), keys)
+    assert np.array_equal(act.cpu().numpy(), bits)
+    assert (bits != 255).any() and (bits == 0).any()
+    got = out.cpu().numpy()
+    assert np.all(got[bits == 0] == 0.0)
+    assert (np.abs(got - qwant) / np.maximum(np.abs(qwant), 1.0)).max() <= FP32_TOL
+    # the regressor learned the density (a gain over predicting the mean)
+    rmse = float(np.sqrt(np.mean((want - ref["val"]) ** 2)))
+    assert rmse < 0.8 * float(np.std(ref["val"]))
+
+
+@pytest.fixture(scope="module")
+def fog512():
+    ijk, val, meta = workload("fog512", device="cuda")
+    g = nv.build(ijk.contiguous(), val.contiguous(), 1, 0.0)
+    info = g.info()
+    m = nv.compress(g, seed=3, ffm_sigma=10.0 * (1 << info["log2_extent"]) / 1024.0, steps=2000, batch=65536,
+                    train_prec=1, patch_precs=0b1011, **FOG_SHAPE)
+    return g, m
+
+
+@pytest.mark.parametrize("prec", [0, 1, 3])
+def test_fog512_full_decode(fog512, prec):
+    g, m = fog512
+    ref = g.read()
+    n = ref["ijk"].shape[0]
+    assert n > 1_000_000
+    dijk, dval, cnt = nv.decompress(m, prec)
+    assert cnt == [n]
+    assert torch.equal(dijk, torch.from_numpy(ref["ijk"]).cuda())
+    om = blob.read(m.export())
+    r = np.random.default_rng(prec)
+    idx = r.choice(n, 4096, replace=False)
+    pv = dval[torch.from_numpy(idx).cuda()].cpu().numpy().astype(np.float64)
+    want, scale = oracle_forward_scale(om, codec.REG, ref["ijk"][idx])
+    if prec == 0:
+        assert rel_err(pv, want, scale).max() <= FP32_TOL
+    else:
+        assert np.abs(pv - want).max() <= TC_TOL
+    # learning error against the generated density (reported by the bench; here: a gain)
+    truth = ref["val"][idx].astype(np.float64)
+    assert np.sqrt(np.mean((pv - truth) ** 2)) < 0.8 * np.std(ref["val"])

@@ -1,0 +1,102 @@
+"""Scale: a 4096^3 union of 128 spheres + 128 tori (seed 5; about 1e9 active voxels,
+2.7e9 level-0 candidates, past every 32-bit index), three 4x64 networks with FFM 64
+trained by the BF16 tensor-core step, decoded in full at FP32 and BF16, and 2^26 point
+queries.  Topology and order are checked exactly on the device against the input
+sorted by canonical key; values and queries on samples the FP64 oracle computes one by
+one (the oracle gets the part of the topology that those samples touch)."""
+import numpy as np
+import pytest
+import torch
+
+import paper_2208_04448_b300 as nv
+from fixtures import query_points, workload
+from gpu_helpers import oracle_forward_scale, rel_err
+from oracle import blob, codec, vdb
+
+pytestmark = pytest.mark.gpu
+
+FP32_TOL, TC_TOL = 1e-5, 2e-2
+
+
+def _canonical_key_dev(ijk: torch.Tensor) -> torch.Tensor:
+    """Canonical VDB key (root | level-1 slot | leaf slot | voxel offset) on the device."""
+    i, j, k = (ijk[:, d].to(torch.int64) for d in range(3))
+    l2 = ((i >> 12) << 18) | ((j >> 12) << 9) | (k >> 12)
+    l1 = (((i >> 7) & 31) << 10) | (((j >> 7) & 31) << 5) | ((k >> 7) & 31)
+    lf = (((i >> 3) & 15) << 8) | (((j >> 3) & 15) << 4) | ((k >> 3) & 15)
+    off = ((i & 7) << 6) | ((j & 7) << 3) | (k & 7)
+    return (l2 << 36) | (l1 << 21) | (lf << 9) | off
+
+
+def test_key_helper_matches_oracle():
+    r = np.random.default_rng(0)
+    ijk = r.integers(0, 1 << 21, (5000, 3)).astype(np.int32)
+    assert np.array_equal(_canonical_key_dev(torch.from_numpy(ijk).cuda()).cpu().numpy(), vdb.canonical_key(ijk))
+
+
+@pytest.fixture(scope="module")
+def union4096():
+    ijk, val, _ = workload("union4096", device="cuda")
+    torch.cuda.empty_cache()                            # hand the generator's cached blocks back
+    n = ijk.shape[0]
+    g = nv.build(ijk, val, 0, 3.0)
+    del val
+    info = g.info()
+    assert info["n_active"] == n
+    keys = torch.sort(_canonical_key_dev(ijk)).values
+    pts = query_points(ijk, 1 << 26, seed=5)
+    del ijk
+    m = nv.compress(g, seed=1, width=[64, 64, 64], layers=[4, 4, 4], ffm_size=[64, 64],
+                    ffm_sigma=10.0 * (1 << info["log2_extent"]) / 1024.0, steps=300, batch=65536, train_prec=1,
+                    patch_precs=0b0011)
+    del g
+    torch.cuda.empty_cache()
+    return m, keys, pts, info, blob.read(m.export())
+
+
+def test_scale_counts(union4096):
+    m, keys, pts, info, om = union4096
+    assert info["n_active"] > 500_000_000
+    assert info["n_leaf"] * 512 > (1 << 31)            # level-0 candidates past 32-bit indices
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_scale_decode(union4096, prec):
+    m, keys, pts, info, om = union4096
+    n = info["n_active"]
+    dijk, dval, cnt = nv.decompress(m, prec)
+    assert cnt == [n]
+    dk = _canonical_key_dev(dijk)
+    assert torch.equal(dk, keys)                        # every voxel, canonical order
+    del dk
+    r = np.random.default_rng(prec)
+    idx = np.sort(r.choice(n, 4096, replace=False))
+    ti = torch.from_numpy(idx).cuda()
+    pi = dijk[ti].cpu().numpy()
+    pv = dval[ti].cpu().numpy().astype(np.float64)
+    want, scale = oracle_forward_scale(om, codec.REG, pi)
+    if prec == 0:
+        assert rel_err(pv / 3.0, want, scale).max() <= FP32_TOL
+    else:
+        assert np.abs(pv - 3.0 * want).max() <= TC_TOL * 3.0
+
+
+def test_scale_queries(union4096):
+    m, keys, pts, info, om = union4096
+    out, act = nv.query(m, pts.cuda().contiguous(), 0, active=True)
+    assert out.shape[0] == 1 << 26
+    r = np.random.default_rng(7)
+    act_np = act.cpu().numpy()
+    near = np.nonzero(act_np)[0]
+    idx = np.concatenate([r.choice(near, 1500, replace=False), r.choice(len(act_np), 500, replace=False)])
+    sp = pts.numpy()[idx]
+    # the active keys among the sampled points' corners, looked up in the sorted input keys
+    c0 = np.floor(sp.astype(np.float64)).astype(np.int64)
+    corners = np.concatenate([c0 + np.array([(c >> 2) & 1, (c >> 1) & 1, c & 1]) for c in range(8)])
+    ck = torch.from_numpy(vdb.canonical_key(np.clip(corners, 0, (1 << 21) - 1))).cuda()
+    pos = torch.searchsorted(keys, ck).clamp(max=keys.shape[0] - 1)
+    sub = np.unique(ck[keys[pos] == ck].cpu().numpy())
+    want, bits = codec.query(om, sp, sub)
+    assert np.array_equal(act_np[idx], bits)
+    got = out.cpu().numpy()[idx]
+    assert (np.abs(got - want) / np.maximum(np.abs(want), 3.0)).max() <= FP32_TOL
