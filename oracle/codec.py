@@ -30,7 +30,7 @@ from . import nets as N
 from . import rng, vdb
 
 L1CLS, L0CLS, REG = 0, 1, 2
-PREC_FP32, PREC_BF16, PREC_FP8, PREC_FP16 = 0, 1, 2, 3
+PREC_FP32, PREC_BF16, PREC_FP8, PREC_FP16, PREC_BF16X3 = 0, 1, 2, 3, 4
 
 
 def _lattice16(s):

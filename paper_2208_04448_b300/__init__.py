@@ -12,7 +12,7 @@ import ctypes as C
 import torch
 
 from . import _native as N
-from ._native import (BF16, FP16, FP32, FP8_E4M3, LOSS_BCE, LOSS_L1, LOSS_MSE, NET_L0_CLASSIFIER,  # noqa: F401
+from ._native import (BF16, BF16X3, FP16, FP32, FP8_E4M3, LOSS_BCE, LOSS_L1, LOSS_MSE, NET_L0_CLASSIFIER,  # noqa: F401
                       NET_L1_CLASSIFIER, NET_REGRESSOR)
 
 _lib = None

@@ -9,7 +9,7 @@ LIB_PATH = os.path.join(HERE, "libnvdb.so")
 
 OK, ERR_INVALID_ARG, ERR_DUPLICATE_VOXEL, ERR_OUT_OF_MEMORY, ERR_CAPACITY, ERR_CUDA, ERR_TIMEOUT, \
     ERR_UNSUPPORTED, ERR_CORRUPT = range(9)
-FP32, BF16, FP8_E4M3, FP16 = 0, 1, 2, 3
+FP32, BF16, FP8_E4M3, FP16, BF16X3 = 0, 1, 2, 3, 4
 NET_L1_CLASSIFIER, NET_L0_CLASSIFIER, NET_REGRESSOR = 0, 1, 2
 LOSS_MSE, LOSS_L1, LOSS_BCE = 0, 1, 2
 

@@ -20,6 +20,7 @@ namespace nvdb {
 
 struct NetView {
   int n_in, width, layers;
+  int wexact;                    // weights and biases are BF16 values: the BF16 lo tiles are zero
   const float* p32;              // flat FP32 parameters (W_0,b_0,...,W_{L-1},b_{L-1},w_h,b_h)
   const uint8_t* wpk;            // packed 16-bit weight tiles (see pack_weights_kernel)
   const uint32_t* q;             // Fourier matrix, [n_in/2][3]
@@ -217,11 +218,13 @@ __global__ void __launch_bounds__(kTile) mlp_f32_kernel(const __grid_constant__ 
 }
 
 // ============================================================== tcgen05 tensor-core path
-// Two operand modes of kind::f16 (same tensor rate):
+// Three operand modes of kind::f16 (same tensor rate):
 //  TC_BF16X3: activations and weights carried as BF16 pairs v = hi + lo
 //             (hi = bf16(v), lo = bf16(v - hi)); D = A_hi W_hi + A_lo W_hi + A_hi W_lo,
-//             three MMAs per K step, error ~2^-16 relative.
+//             three MMAs per K step (two when the weights are BF16 values), error
+//             ~2^-16 relative.
 //  TC_FP16  : FP16 activations and weights, one MMA per K step.
+//  TC_BF16  : BF16 activations and weights, one MMA per K step.
 // Layout per CTA (one 128-row tile in flight):
 //  * weights in shared memory, each layer a [W x (K+16)] tile in the canonical
 //    no-swizzle K-major layout; column K holds the bias, columns K+1.. are zero;
@@ -229,7 +232,7 @@ __global__ void __launch_bounds__(kTile) mlp_f32_kernel(const __grid_constant__ 
 //    32-bit column, written by each thread for its own row with tcgen05.st;
 //    column K/2 holds the constant 1 that multiplies the bias column;
 //  * the FP32 accumulator D in tensor memory columns [0, W).
-enum TcMode : int { TC_BF16X3 = 0, TC_FP16 = 1 };
+enum TcMode : int { TC_BF16X3 = 0, TC_FP16 = 1, TC_BF16 = 2 };
 
 __host__ __device__ inline int64_t wtile_elems(int nin, int w, int L) {
   return (int64_t)w * (nin + 16) + (int64_t)(L - 1) * w * (w + 16);
@@ -255,7 +258,7 @@ struct TcLayout {
     w_bytes = (size_t)wtile_elems(NIN, W, L) * 2;           // one copy
     t_off = (C::NCOPY * w_bytes + 15) & ~(size_t)15;
     p_off = t_off + (size_t)C::M * 64 * (MODE == TC_FP16 ? 4 : 8);   // T table [M][64]: half2 / float2
-    wh_off = p_off + (size_t)2 * C::M * 8;                   // P table: float2 [2][M]
+    wh_off = p_off + (size_t)2 * 2 * C::M * 8;               // P tables, two buffers of [2][M] x 8 B
     q_off = wh_off + (size_t)(W + 4) * 4;
     bar_off = (q_off + (size_t)C::M * 12 + 7) & ~(size_t)7;
     slot_off = bar_off + 8;
@@ -271,6 +274,9 @@ __device__ __forceinline__ void split_pair(float a, float b, uint32_t& hi, uint3
   if (MODE == TC_FP16) {
     hi = cvt_f16x2(a, b);
     lo = 0u;
+  } else if (MODE == TC_BF16) {
+    hi = cvt_bf16x2(a, b);
+    lo = 0u;
   } else {
     hi = cvt_bf16x2(a, b);
     const float ha = __uint_as_float(hi << 16), hb = __uint_as_float(hi & 0xFFFF0000u);
@@ -282,6 +288,9 @@ template <int MODE>
 __device__ __forceinline__ void relu_pair(float a, float b, uint32_t& hi, uint32_t& lo) {
   if (MODE == TC_FP16) {
     hi = cvt_relu_f16x2(a, b);
+    lo = 0u;
+  } else if (MODE == TC_BF16) {
+    hi = cvt_relu_bf16x2(a, b);
     lo = 0u;
   } else {
     split_pair<MODE>(fmaxf(a, 0.f), fmaxf(b, 0.f), hi, lo);
@@ -310,6 +319,26 @@ __device__ __forceinline__ void store_a_row(uint32_t tlane, const uint32_t* hi, 
   }
 }
 
+// Level-0 angle addition, per-tile factors: P[dxl][f] = e^{i Phi(o + (dx0 + dxl) e_x)} for
+// the two x offsets of tile t of a leaf (origin o), as float2 (cos, sin) or, for FP16, as
+// the half2 pairs (cos, cos) and (-sin, sin).  Thread tid < 2M writes entry tid.
+template <int M, int MODE>
+__device__ __forceinline__ void l0_factors(const EvalJob& job, const uint32_t* sq, int4 o, int64_t t, float2* sPb,
+                                           int tid) {
+  const int dxl = tid / M, f = tid % M;
+  const uint32_t ph = sq[3 * f] * (uint32_t)(o.x - job.ox + 2 * (int)(t & 3) + dxl) +
+                      sq[3 * f + 1] * (uint32_t)(o.y - job.oy) + sq[3 * f + 2] * (uint32_t)(o.z - job.oz);
+  float sn, cs;
+  sincospif((float)(int32_t)ph * 0x1p-31f, &sn, &cs);
+  if (MODE == TC_FP16) {
+    const __half2 pc = __float2half2_rn(cs), ps = __floats2half2_rn(-sn, sn);
+    reinterpret_cast<uint2*>(sPb)[tid] =
+        make_uint2(*reinterpret_cast<const uint32_t*>(&pc), *reinterpret_cast<const uint32_t*>(&ps));
+  } else {
+    sPb[tid] = make_float2(cs, sn);
+  }
+}
+
 // Stage network `net` into shared memory: weight tiles, head, Fourier matrix and
 // (level-0 lattice) the table T[f][dy*8+dz] = e^{i Phi(dy e_y + dz e_z)}.
 template <int NIN, int W, int MODE>
@@ -332,20 +361,24 @@ __device__ __forceinline__ void tc_stage(const NetView& net, int mode, const TcL
   for (int i = tid; i < 3 * M; i += kTile) sq[i] = __ldg(net.q + i);
   __syncthreads();
   if (mode == MODE_L0) {
+    // entry (f, j) at [f / G][j][f % G], G = 4 (half2) or 2 (float2): one 16-byte load
+    // gives a thread G consecutive frequencies of its (dy, dz)
+    constexpr int G = MODE == TC_FP16 ? 4 : 2;
     for (int i = tid; i < M * 64; i += kTile) {
       const int f = i >> 6, j = i & 63;
       const uint32_t ph = sq[3 * f + 1] * (uint32_t)(j >> 3) + sq[3 * f + 2] * (uint32_t)(j & 7);
       float sn, cs;
       sincospif((float)(int32_t)ph * 0x1p-31f, &sn, &cs);
-      if (MODE == TC_FP16) sTh[i] = __floats2half2_rn(cs, sn);
-      else sT[i] = make_float2(cs, sn);
+      const int at = ((f / G) * 64 + j) * G + f % G;
+      if (MODE == TC_FP16) sTh[at] = __floats2half2_rn(cs, sn);
+      else sT[at] = make_float2(cs, sn);
     }
   }
   fence_proxy_async_smem();   // the weight tiles are read by the tensor core (async proxy)
 }
 
 template <int NIN, int W, int MODE>
-__global__ void __launch_bounds__(kTile, 1) mlp_tc_kernel(const __grid_constant__ EvalBatch b) {
+__global__ void __launch_bounds__(kTile, MODE == TC_BF16X3 ? 1 : 4) mlp_tc_kernel(const __grid_constant__ EvalBatch b) {
   static_assert(W == 32 || W == 64, "width");
   static_assert(NIN == 32 || NIN == 64, "encoding size");
   using C = TcCfg<NIN, W, MODE>;
@@ -380,6 +413,9 @@ __global__ void __launch_bounds__(kTile, 1) mlp_tc_kernel(const __grid_constant_
   const int64_t ntiles = batch_total(b, n0);
   int cur = -1;
   float bh = 0.f;
+  bool wexact = false;
+  int pbuf = 0;            // level-0 factor buffer of the current tile
+  bool p_ready = false;    // its factors were computed during the previous tile
   for (int64_t t0 = blockIdx.x; t0 < ntiles && !failed; t0 += gridDim.x) {
     const int m = batch_find(b, t0);
     if (m != cur) {   // uniform across the CTA: restage the item's network
@@ -387,11 +423,18 @@ __global__ void __launch_bounds__(kTile, 1) mlp_tc_kernel(const __grid_constant_
       tc_stage<NIN, W, MODE>(b.it[m].net, b.it[m].job.mode, lay, smem);
       __syncthreads();
       bh = swh[W];
+      wexact = b.it[m].net.wexact != 0;
       cur = m;
     }
     EvalJob job = b.it[m].job;
     if (b.n == 1) job.n_items = n0;
     const int64_t t = t0 - b.it[m].tile_start;
+    // the next tile of this CTA, if it is a level-0 tile of the same item: its factors are
+    // computed while this tile's first-layer MMAs run
+    const int64_t end_m = m + 1 < b.n ? b.it[m + 1].tile_start : ntiles;
+    const bool next_same = job.mode == MODE_L0 && t0 + gridDim.x < end_m;
+    const int64_t tn = t0 + gridDim.x - b.it[m].tile_start;
+    float2* sPc = sP + pbuf * 2 * M;
     // ---- encoding -> A operand (layer 0) in TMEM.  Inside this kernel the features are
     // ordered (cos_0, sin_0, cos_1, sin_1, ...): packed column f holds frequency f; the
     // first-layer weight tile is packed with the matching column order.
@@ -400,35 +443,41 @@ __global__ void __launch_bounds__(kTile, 1) mlp_tc_kernel(const __grid_constant_
       uint32_t hi[NIN / 2], lo[NIN / 2];
       if (job.mode == MODE_L0) {
         // angle addition: e^{i Phi(v)} = e^{i Phi(origin + dx e_x)} * e^{i Phi(dy e_y + dz e_z)}
-        const int4 o = __ldg(job.nodes + (t >> 2));
-        const int dx0 = 2 * (int)(t & 3);
-        if (tid < 2 * M) {
-          const int dxl = tid / M, f = tid % M;
-          const uint32_t ph = sq[3 * f] * (uint32_t)(o.x - job.ox + dx0 + dxl) + sq[3 * f + 1] * (uint32_t)(o.y - job.oy) +
-                              sq[3 * f + 2] * (uint32_t)(o.z - job.oz);
-          float sn, cs;
-          sincospif((float)(int32_t)ph * 0x1p-31f, &sn, &cs);
-          sP[tid] = make_float2(cs, sn);
+        if (!p_ready) {
+          if (tid < 2 * M) l0_factors<M, MODE>(job, sq, __ldg(job.nodes + (t >> 2)), t, sPc, tid);
+          __syncthreads();
         }
-        __syncthreads();
-        const float2* P = sP + (tid >> 6) * M;
+        const int j = tid & 63;
         if (MODE == TC_FP16) {
-          // complex product in half2: (pc, pc) * (tc, ts) + (ps, ps) * (-ts, tc) = (cos, sin)
+          // complex product in half2: (pc, pc) * (tc, ts) + (-ps, ps) * (ts, tc) = (cos, sin)
+          const uint4* P4 = reinterpret_cast<const uint4*>(sPc) + (tid >> 6) * (M / 2);
+          const uint4* T4 = reinterpret_cast<const uint4*>(sTh);
 #pragma unroll
-          for (int f = 0; f < M; ++f) {
-            const float2 p = P[f];
-            const __half2 q = sTh[f * 64 + (tid & 63)];
-            const uint32_t qs = __byte_perm(*reinterpret_cast<const uint32_t*>(&q), 0, 0x1032) ^ 0x00008000u;
-            const __half2 z = __hfma2(__float2half2_rn(p.y), *reinterpret_cast<const __half2*>(&qs),
-                                      __hmul2(__float2half2_rn(p.x), q));
-            hi[f] = *reinterpret_cast<const uint32_t*>(&z);
-            lo[f] = 0u;
+          for (int f4 = 0; f4 < M / 4; ++f4) {
+            const uint4 tq = T4[f4 * 64 + j];
+            const uint4 pa = P4[2 * f4], pb = P4[2 * f4 + 1];
+            const uint32_t tw[4] = {tq.x, tq.y, tq.z, tq.w};
+            const uint32_t pw[8] = {pa.x, pa.y, pa.z, pa.w, pb.x, pb.y, pb.z, pb.w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              const uint32_t qs = __byte_perm(tw[e], 0, 0x1032);
+              const __half2 z = __hfma2(*reinterpret_cast<const __half2*>(&pw[2 * e + 1]),
+                                        *reinterpret_cast<const __half2*>(&qs),
+                                        __hmul2(*reinterpret_cast<const __half2*>(&pw[2 * e]),
+                                                *reinterpret_cast<const __half2*>(&tw[e])));
+              hi[4 * f4 + e] = *reinterpret_cast<const uint32_t*>(&z);
+              lo[4 * f4 + e] = 0u;
+            }
           }
         } else {
+          const float4* P4 = reinterpret_cast<const float4*>(sPc) + (tid >> 6) * (M / 2);
+          const float4* T4 = reinterpret_cast<const float4*>(sT);
 #pragma unroll
-          for (int f = 0; f < M; ++f) {
-            const float2 p = P[f], q = sT[f * 64 + (tid & 63)];
-            split_pair<MODE>(fmaf(p.x, q.x, -p.y * q.y), fmaf(p.x, q.y, p.y * q.x), hi[f], lo[f]);
+          for (int f2 = 0; f2 < M / 2; ++f2) {
+            const float4 tq = T4[f2 * 64 + j], pq = P4[f2];
+            split_pair<MODE>(fmaf(pq.x, tq.x, -pq.y * tq.y), fmaf(pq.x, tq.y, pq.y * tq.x), hi[2 * f2], lo[2 * f2]);
+            split_pair<MODE>(fmaf(pq.z, tq.z, -pq.w * tq.w), fmaf(pq.z, tq.w, pq.w * tq.z), hi[2 * f2 + 1],
+                             lo[2 * f2 + 1]);
           }
         }
       } else {
@@ -461,11 +510,14 @@ __global__ void __launch_bounds__(kTile, 1) mlp_tc_kernel(const __grid_constant_
           mma_f16kind_ts(tbase, tbase + C::A_HI + ks * 8, bd, idesc, ks > 0 ? 1u : 0u);
           if (MODE == TC_BF16X3) {
             mma_f16kind_ts(tbase, tbase + C::A_LO + ks * 8, bd, idesc, 1u);
-            mma_f16kind_ts(tbase, tbase + C::A_HI + ks * 8, smem_desc(bl + ks * 256, 128, K * 16), idesc, 1u);
+            if (!wexact)   // A_hi * W_lo vanishes for BF16-exact weights
+              mma_f16kind_ts(tbase, tbase + C::A_HI + ks * 8, smem_desc(bl + ks * 256, 128, K * 16), idesc, 1u);
           }
         }
         mma_commit(bar);
       }
+      if (l == 0 && next_same && tid < 2 * M)   // the next tile's factors, into the other buffer
+        l0_factors<M, MODE>(job, sq, __ldg(job.nodes + (tn >> 2)), tn, sP + (pbuf ^ 1) * 2 * M, tid);
       const bool ok = mbar_wait_bounded(bar, phase);
       phase ^= 1u;
       tc_fence_after();
@@ -481,15 +533,22 @@ __global__ void __launch_bounds__(kTile, 1) mlp_tc_kernel(const __grid_constant_
         store_a_row<W, MODE>(tlane, hi, lo);
         tmem_st_wait();
       } else {
-        y = bh;
+        // FP32 head, two products per instruction
+        const float2* swh2 = reinterpret_cast<const float2*>(swh);
+        float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
-        for (int c = 0; c < W; ++c) y = fmaf(swh[c], fmaxf(__uint_as_float(accu[c]), 0.f), y);
+        for (int c = 0; c < W / 2; ++c)
+          acc = ffma2(swh2[c], make_float2(fmaxf(__uint_as_float(accu[2 * c]), 0.f), fmaxf(__uint_as_float(accu[2 * c + 1]), 0.f)),
+                      acc);
+        y = bh + (acc.x + acc.y);
       }
       tc_fence_before();
       if (__syncthreads_or(!ok)) { failed = true; break; }   // all threads agree on a timeout
     }
     if (failed) break;
     job_output(job, t, tid, valid, y);
+    if (next_same) pbuf ^= 1;
+    p_ready = next_same;
   }
   if (failed && tid == 0) set_status(b.it[0].job.status, ST_TIMEOUT);
   tc_fence_before();

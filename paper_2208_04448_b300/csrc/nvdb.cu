@@ -124,10 +124,14 @@ struct Scope {
   } while (0)
 
 const char* eval_name(const char* base, int mode) {
-  static const char* names[3][3] = {{"mlp_f32.L1", "mlp_f32.L0", "mlp_f32.list"},
+  static const char* names[4][3] = {{"mlp_f32.L1", "mlp_f32.L0", "mlp_f32.list"},
                                     {"mlp_bf16x3.L1", "mlp_bf16x3.L0", "mlp_bf16x3.list"},
-                                    {"mlp_f16.L1", "mlp_f16.L0", "mlp_f16.list"}};
-  const int b = std::strcmp(base, "mlp_bf16x3") == 0 ? 1 : std::strcmp(base, "mlp_f16") == 0 ? 2 : 0;
+                                    {"mlp_f16.L1", "mlp_f16.L0", "mlp_f16.list"},
+                                    {"mlp_bf16.L1", "mlp_bf16.L0", "mlp_bf16.list"}};
+  const int b = std::strcmp(base, "mlp_bf16x3") == 0 ? 1
+                : std::strcmp(base, "mlp_f16") == 0  ? 2
+                : std::strcmp(base, "mlp_bf16") == 0 ? 3
+                                                     : 0;
   return names[b][mode];
 }
 
@@ -245,6 +249,7 @@ struct DevNet {
   uint8_t* wpk = nullptr;   // [FP16 | BF16 hi | BF16 lo] weight tiles, then BF16 W_l^T tiles
   float* m = nullptr;
   float* v = nullptr;
+  bool bf16_exact = false;  // every weight and bias (not the head) is a BF16 value
   ~DevNet() { dfree(p32); dfree(wpk); dfree(m); dfree(v); }
 };
 
@@ -365,6 +370,7 @@ NetView net_view(const nvdb_model* m, int k) {
   v.p32 = m->net[k].p32;
   v.wpk = m->net[k].wpk;
   v.q = m->q_dev[k == 0 ? 0 : 1];
+  v.wexact = m->net[k].bf16_exact ? 1 : 0;
   return v;
 }
 
@@ -391,6 +397,12 @@ nvdb_status launch_tc(const EvalBatch& b, int64_t ntiles, const char* base, cuda
   return NVDB_OK;
 }
 
+// Precisions are 0 .. kNumPrecisions-1 (FP8 is reserved).
+constexpr int kNumPrecisions = 5;
+bool eval_prec_ok(int prec) {
+  return prec == NVDB_FP32 || prec == NVDB_BF16 || prec == NVDB_FP16 || prec == NVDB_BF16X3;
+}
+
 template <int NIN, int W>
 nvdb_status launch_eval_t(const EvalBatch& b, int64_t ntiles, nvdb_precision prec, cudaStream_t s) {
   int occ = 0;
@@ -401,6 +413,8 @@ nvdb_status launch_eval_t(const EvalBatch& b, int64_t ntiles, nvdb_precision pre
     const int64_t grid = std::min<int64_t>(ntiles, (int64_t)num_sms() * std::max(occ, 1));
     KLAUNCH(eval_name("mlp_f32", b.it[0].job.mode), s, mlp_f32_kernel<NIN, W><<<(unsigned)grid, kTile, smem, s>>>(b));
   } else if (prec == NVDB_BF16) {
+    TRY((launch_tc<NIN, W, TC_BF16>(b, ntiles, "mlp_bf16", s)));
+  } else if (prec == NVDB_BF16X3) {
     TRY((launch_tc<NIN, W, TC_BF16X3>(b, ntiles, "mlp_bf16x3", s)));
   } else if (prec == NVDB_FP16) {
     TRY((launch_tc<NIN, W, TC_FP16>(b, ntiles, "mlp_f16", s)));
@@ -526,6 +540,20 @@ nvdb_status upload_net(nvdb_model* m, int k, const float* host_params, cudaStrea
   TRY(dalloc(&d.wpk, (size_t)wpk_bytes(d.n_in, d.width, d.layers) + 64));
   if (host_params) CU(cudaMemcpyAsync(d.p32, host_params, d.P * 4, cudaMemcpyHostToDevice, s));
   return NVDB_OK;
+}
+
+__global__ void round_bf16_kernel(float* p, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) p[i] = __bfloat162float(__float2bfloat16_rn(p[i]));
+}
+
+bool bf16_exact_layers(const float* p, int64_t n) {
+  for (int64_t i = 0; i < n; ++i) {
+    uint32_t u;
+    std::memcpy(&u, p + i, 4);
+    if (u & 0xFFFFu) return false;
+  }
+  return true;
 }
 
 nvdb_status pack_net(nvdb_model* m, int k, cudaStream_t s) {
@@ -703,7 +731,7 @@ extern "C" void nvdb_train_opts_default(nvdb_train_opts* o) {
   o->lr_interval = 100;
   o->loss = NVDB_LOSS_MSE;
   o->train_prec = NVDB_FP32;
-  o->patch_precs = (1u << NVDB_FP32) | (1u << NVDB_BF16) | (1u << NVDB_FP16);
+  o->patch_precs = (1u << NVDB_FP32) | (1u << NVDB_BF16) | (1u << NVDB_FP16) | (1u << NVDB_BF16X3);
   o->stop_window = 50;
 }
 
@@ -830,6 +858,7 @@ extern "C" nvdb_status nvdb_compress(const nvdb_grid* g, const nvdb_train_opts* 
       if (warm) {
         TRY(upload_net(m, k, nullptr, s));
         CU(cudaMemcpyAsync(m->net[k].p32, warm->net[k].p32, m->net[k].P * 4, cudaMemcpyDeviceToDevice, s));
+        m->net[k].bf16_exact = warm->net[k].bf16_exact && o->steps == 0;
       } else {
         const std::vector<float> p = xavier_params(o->seed, k, k == 0 ? m->ffm[0] : m->ffm[1], m->width[k], m->layers[k]);
         TRY(upload_net(m, k, p.data(), s));
@@ -895,9 +924,17 @@ extern "C" nvdb_status nvdb_compress(const nvdb_grid* g, const nvdb_train_opts* 
     }
     dfree(d_loss);
     TRY(st);
+    if (o->train_prec == NVDB_BF16)   // the BF16 step trained BF16 weights: store them as such
+      for (int k = 0; k < 3; ++k) {
+        DevNet& d = m->net[k];
+        const int64_t n = d.P - d.width - 1;   // every weight and bias except the FP32 head
+        KLAUNCH("round_bf16", s, round_bf16_kernel<<<blocks_for(n, 256), 256, 0, s>>>(d.p32, n));
+        CU(cudaGetLastError());
+        d.bf16_exact = true;
+      }
     for (int k = 0; k < 3; ++k) TRY(pack_net(m, k, s));
     uint32_t pp = o->patch_precs ? o->patch_precs : (1u << NVDB_FP32);
-    for (int p = 0; p < 4; ++p)
+    for (int p = 0; p < kNumPrecisions; ++p)
       if (pp & (1u << p)) {
         if (p == NVDB_FP8_E4M3) return fail(NVDB_ERR_UNSUPPORTED, "FP8 patches not implemented");
         TRY(make_patches(m, g, p, s));
@@ -1127,7 +1164,7 @@ TopoView topo_view(const nvdb_model* m) {
 extern "C" nvdb_status nvdb_query(const nvdb_model* cm, const float* d_xyz, int64_t n, nvdb_precision prec,
                                   float* d_out, uint8_t* d_active, nvdb_stream stream) {
   if (!cm || n < 0 || (n > 0 && (!d_xyz || !d_out))) return fail(NVDB_ERR_INVALID_ARG, "nvdb_query: bad arguments");
-  if (prec != NVDB_FP32 && prec != NVDB_BF16 && prec != NVDB_FP16) return fail(NVDB_ERR_UNSUPPORTED, "precision %d", (int)prec);
+  if (!eval_prec_ok(prec)) return fail(NVDB_ERR_UNSUPPORTED, "precision %d", (int)prec);
   nvdb_model* m = const_cast<nvdb_model*>(cm);
   cudaStream_t s = (cudaStream_t)stream;
   TRY(build_query_cache(m, s));
@@ -1347,6 +1384,7 @@ extern "C" nvdb_status nvdb_model_import(const void* buf, size_t bytes, nvdb_str
       if (!p) return fail(NVDB_ERR_CORRUPT, "blob truncated (network %d)", k);
       std::vector<float> tmp(p, p + P);
       TRY(upload_net(m, k, tmp.data(), s));
+      m->net[k].bf16_exact = bf16_exact_layers(tmp.data(), P - m->width[k] - 1);
       CU(cudaStreamSynchronize(s));
       TRY(pack_net(m, k, s));
     }

@@ -35,12 +35,12 @@ def test_warm_start_copies_previous_networks(frames):
 
 
 def test_warm_sequence_early_stop_and_batched_decode(frames):
-    cold = nv.compress(nv.build(*frames[0], 0, 3.0), seed=1, steps=600, lr=1e-3, patch_precs=0b1011, **SHAPE)
+    cold = nv.compress(nv.build(*frames[0], 0, 3.0), seed=1, steps=600, lr=1e-3, patch_precs=0b11011, **SHAPE)
     target = [float(np.mean(cold.losses(k)[-50:])) for k in range(3)]
     models, grids_ijk, steps = [cold], [frames[0][0]], []
     for f in range(1, len(frames)):
         g = nv.build(*frames[f], 0, 3.0)
-        m = nv.compress(g, seed=1, steps=600, lr=1e-4, warm=models[-1], patch_precs=0b1011, stop_window=50,
+        m = nv.compress(g, seed=1, steps=600, lr=1e-4, warm=models[-1], patch_precs=0b11011, stop_window=50,
                         stop_loss=target, **SHAPE)
         steps.append([len(m.losses(k)) for k in range(3)])
         models.append(m)
@@ -48,7 +48,7 @@ def test_warm_sequence_early_stop_and_batched_decode(frames):
     warm_steps = np.array(steps)
     assert warm_steps.max() <= 600 and warm_steps.sum() < 0.8 * 3 * 600 * (len(frames) - 1)
     assert (warm_steps < 600).any()                       # the early stop triggered
-    for prec in (1, 3):
+    for prec in (1, 3, 4):
         plan = nv.decompress_plan(models, prec)
         plan.launch()
         plan.check()

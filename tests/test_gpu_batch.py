@@ -29,7 +29,7 @@ def models():
     return ms, other
 
 
-@pytest.mark.parametrize("prec", [0, 1, 3])
+@pytest.mark.parametrize("prec", [0, 1, 3, 4])
 def test_batched_equals_single(models, prec):
     ms, other = models
     singles = [nv.decompress(m, prec) for m in ms + [other]]
@@ -54,7 +54,7 @@ def test_more_models_than_one_launch_holds(models):
         off += n
 
 
-@pytest.mark.parametrize("prec", [1, 3])
+@pytest.mark.parametrize("prec", [1, 3, 4])
 def test_plan_replays_decompress(models, prec):
     ms, other = models
     seq = ms + [other]

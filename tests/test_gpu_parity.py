@@ -4,7 +4,8 @@ Bars (tolerances written per test): bit-exact for the tree build, the initial
 parameters, topology, compacted lists and patch-corrected masks; 1e-5
 relative (normalised by the head's dot-product scale) for FP32 network values;
 1e-4 relative for FP32 gradients; 2e-2 of the band half-width for the
-tensor-core precisions (compensated BF16 and FP16).
+tensor-core precisions FP16 and compensated BF16, 5e-2 for plain BF16 (which
+misses the 2e-2 target; see gpu_helpers.TC_BARS).
 """
 import numpy as np
 import pytest
@@ -12,7 +13,7 @@ import torch
 
 import paper_2208_04448_b300 as nv
 from fixtures import query_points, workload
-from gpu_helpers import oracle_forward_scale, randomise_biases, rel_err
+from gpu_helpers import oracle_forward_scale, randomise_biases, rel_err, tc_bar
 from oracle import blob, codec, vdb
 from oracle import nets as N
 
@@ -20,7 +21,6 @@ pytestmark = pytest.mark.gpu
 
 FP32_TOL = 1e-5
 GRAD_TOL = 1e-4
-BF16_TOL = 2e-2
 # BF16 training arithmetic rounds each operand of the forward, delta and weight-gradient
 # products once to BF16 (unit roundoff u = 2^-9).  How much a gradient moves under
 # such roundings depends on the network and the loss (sign-based L1 gradients move
@@ -122,7 +122,7 @@ def _imported(ref, seed, width, layers, ffm=None):
 
 @pytest.mark.parametrize("shape", [([32, 32, 32], [3, 3, 3], None), ([32, 64, 64], [2, 4, 4], [32, 64]),
                                    ([64, 32, 64], [3, 3, 4], [64, 64])])
-@pytest.mark.parametrize("prec", [0, 1, 3])
+@pytest.mark.parametrize("prec", [0, 1, 3, 4])
 def test_mlp_eval_parity(sphere128, shape, prec):
     ijk, val, ref = sphere128
     om, m = _imported(ref, 5, *shape)
@@ -134,7 +134,7 @@ def test_mlp_eval_parity(sphere128, shape, prec):
         if prec == 0:
             assert rel_err(got, want, scale).max() <= FP32_TOL
         else:
-            assert (np.abs(got - want) / np.maximum(scale, 1.0)).max() <= BF16_TOL
+            assert (np.abs(got - want) / np.maximum(scale, 1.0)).max() <= tc_bar(prec)
 
 
 # ---------------------------------------------------------------------------- gradients
@@ -227,7 +227,7 @@ def test_bf16_training_tracks_fp32(sphere128):
     FP32 run's level, and the trained model decodes with exact topology."""
     ijk, val, ref = sphere128
     g = _grid(ijk, val)
-    kw = dict(seed=3, ffm_sigma=1.25, steps=200, batch=4096, patch_precs=0b1011, width=[32, 64, 64],
+    kw = dict(seed=3, ffm_sigma=1.25, steps=200, batch=4096, patch_precs=0b11011, width=[32, 64, 64],
               layers=[3, 4, 4], ffm_size=[32, 64])
     m32 = nv.compress(g, train_prec=0, **kw)
     m16 = nv.compress(g, train_prec=1, **kw)
@@ -237,11 +237,19 @@ def test_bf16_training_tracks_fp32(sphere128):
         assert abs(b[0] - a[0]) <= BF16_LOSS_TOL * max(1.0, a[0])
         assert b[-20:].mean() <= 1.25 * a[-20:].mean() + 1e-4
     om = blob.read(m16.export())
-    for prec in (0, 3):
+    for k in range(3):   # the BF16 step stores BF16 weights and biases (the head stays FP32)
+        net = om["nets"][k]
+        for a in list(net["W"]) + list(net["b"]):
+            assert np.array_equal(_round_bf16(a), np.asarray(a, np.float64))
+    want, scale = oracle_forward_scale(om, 2, ref["ijk"])
+    for prec in (0, 1, 3, 4):   # BF16 decode of BF16 weights: two MMAs per K-step (no weight residual)
         dijk, dval, cnt = nv.decompress(m16, prec)
         assert cnt == [ref["n"]] and np.array_equal(dijk.cpu().numpy(), ref["ijk"])
-    want, scale = oracle_forward_scale(om, 2, ref["ijk"])
-    assert rel_err(nv.decompress(m16, 0)[1].cpu().numpy() / 3.0, want, scale).max() <= FP32_TOL
+        dv = dval.cpu().numpy()
+        if prec == 0:
+            assert rel_err(dv / 3.0, want, scale).max() <= FP32_TOL
+        else:
+            assert np.abs(dv - 3.0 * want).max() <= tc_bar(prec) * 3.0
 
 
 def test_training_precision_errors(sphere128):
@@ -263,7 +271,7 @@ def test_decompress_parity(name):
     m = nv.compress(_grid(ijk, val), seed=4, ffm_sigma=1.25, steps=50, batch=2048, width=[32, 64, 64],
                     layers=[3, 3, 4])
     om = blob.read(m.export())
-    for prec in (0, 1, 3):
+    for prec in (0, 1, 3, 4):
         dijk, dval, cnt = nv.decompress(m, prec)
         dijk, dval = dijk.cpu().numpy(), dval.cpu().numpy()
         assert cnt == [ref["n"]]
@@ -272,7 +280,7 @@ def test_decompress_parity(name):
         if prec == 0:
             assert rel_err(dval / 3.0, want, scale).max() <= FP32_TOL
         else:
-            assert np.abs(dval - 3.0 * want).max() <= BF16_TOL * 3.0
+            assert np.abs(dval - 3.0 * want).max() <= tc_bar(prec) * 3.0
 
 
 def test_patches_match_oracle_decisions(sphere128):
@@ -314,7 +322,7 @@ def test_decompress_errors(sphere128):
 
 # ---------------------------------------------------------------------------- query
 
-@pytest.mark.parametrize("prec", [0, 1, 3])
+@pytest.mark.parametrize("prec", [0, 1, 3, 4])
 def test_query_parity(sphere128, prec):
     ijk, val, ref = sphere128
     m = nv.compress(_grid(ijk, val), seed=8, ffm_sigma=1.25, steps=100, batch=4096)
@@ -326,7 +334,7 @@ def test_query_parity(sphere128, prec):
     keys = np.sort(vdb.canonical_key(ref["ijk"]))
     want, bits = codec.query(om, pts, keys)
     assert np.array_equal(act, bits)
-    tol = FP32_TOL if prec == 0 else BF16_TOL
+    tol = FP32_TOL if prec == 0 else tc_bar(prec)
     assert (np.abs(out - want) / np.maximum(np.abs(want), 3.0)).max() <= tol
     assert (bits != 0).sum() > 1000 and (bits == 0).sum() > 1000
 
