@@ -508,10 +508,11 @@ nvdb_status launch_train(const nvdb_model* m, int k, int prec, TrainJob job, int
   return fail(NVDB_ERR_UNSUPPORTED, "network shape n=%d w=%d", nv.n_in, nv.width);
 }
 
-Bf16Repack repack_of(const DevNet& d, int prec) {
-  Bf16Repack rp{};
-  if (prec == NVDB_BF16) rp = Bf16Repack{d.wpk, d.n_in, d.width, d.layers};
-  return rp;
+// Adam's view of the training step at precision `prec`; `refresh`: rewrite the BF16 tiles.
+AdamAux adam_aux(const DevNet& d, int prec, bool refresh) {
+  AdamAux a{};
+  if (prec == NVDB_BF16) a = AdamAux{refresh ? d.wpk : nullptr, 1, d.n_in, d.width, d.layers};
+  return a;
 }
 
 nvdb_status read_status(uint32_t* d_status, cudaStream_t s, uint32_t* out) {
@@ -899,7 +900,7 @@ extern "C" nvdb_status nvdb_compress(const nvdb_grid* g, const nvdb_train_opts* 
                                               : o->lr;
         KLAUNCH("adam_reduce", s, adam_reduce_kernel<<<blocks_for(d.P + 1, 256), 256, 0, s>>>(m->partial, grid, d.P, d.p32, d.m, d.v, t, lr_t,
                                                                     nullptr, d_loss + (t - 1), 1.f / (float)o->batch,
-                                                                    repack_of(d, o->train_prec)));
+                                                                    adam_aux(d, o->train_prec, true)));
         if (cudaGetLastError() != cudaSuccess) st = fail(NVDB_ERR_CUDA, "adam launch failed");
         ran = t;
         if (early && t % o->stop_window == 0) {   // warm-start early stop (Section 3.6)
@@ -1235,7 +1236,7 @@ extern "C" nvdb_status nvdb_mlp_grad(const nvdb_model* cm, int net, nvdb_precisi
   float* d_loss = nullptr;
   TRY(dalloc(&d_loss, 1));
   KLAUNCH("adam_reduce", s, adam_reduce_kernel<<<blocks_for(d.P + 1, 256), 256, 0, s>>>(m->partial, grid, d.P, nullptr, nullptr, nullptr, 1, 0.f,
-                                                              d_grad, d_loss, 1.f / (float)n, Bf16Repack{}));
+                                                              d_grad, d_loss, 1.f / (float)n, adam_aux(d, prec, false)));
   float h = 0.f;
   cudaError_t e = cudaMemcpyAsync(&h, d_loss, 4, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -1557,7 +1558,7 @@ extern "C" nvdb_status nvdb_mlp_grad_static(const nvdb_model* m, int net, const 
   else if (nv.n_in == 64 && nv.width == 64) TRY((launch_train_static<64, 64>(nv, j, grid, s)));
   else return fail(NVDB_ERR_UNSUPPORTED, "network shape n=%d w=%d", nv.n_in, nv.width);
   adam_reduce_kernel<<<blocks_for(d.P + 1, 256), 256, 0, s>>>(scratch, grid, d.P, nullptr, nullptr, nullptr, 1, 0.f,
-                                                              d_grad, loss_slot, 1.f / (float)n, Bf16Repack{});
+                                                              d_grad, loss_slot, 1.f / (float)n, AdamAux{});
   CU(cudaGetLastError());
   float h = 0.f;
   CU(cudaMemcpyAsync(&h, loss_slot, sizeof h, cudaMemcpyDeviceToHost, s));

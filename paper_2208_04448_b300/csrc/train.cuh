@@ -265,20 +265,47 @@ __device__ __forceinline__ void bf16_tile_offsets(int64_t e, int nin, int W, int
   }
 }
 
-// Where the Adam step also refreshes the BF16 tiles the tensor-core training kernel reads.
-struct Bf16Repack {
-  uint8_t* wpk;               // nullptr: no refresh
+// What the reduction + Adam kernel needs to know about the tensor-core training kernel:
+// the BF16 tiles it reads (refreshed with every update) and the order of its partials.
+struct AdamAux {
+  uint8_t* wpk;               // BF16 tiles to refresh after the update (nullptr: none)
+  int tc_partials;            // partials are in the tensor-core order of partial_index()
   int nin, W, L;
 };
+
+// Slot of parameter e in a partial of the tensor-core training kernel: layer l's block
+// (same offset and size as its parameters W_l, b_l) holds column i of the TMEM weight
+// gradient at i*W + o, i in the kernel's feature order (layer 0 interleaved as
+// (cos_f, sin_f)), the bias at K*W + o; head and loss entries keep their places.
+__device__ __forceinline__ int64_t partial_index(int64_t e, int nin, int W, int L) {
+  int64_t base = 0;
+  for (int l = 0; l < L; ++l) {
+    const int K = l == 0 ? nin : W;
+    const int64_t sz = (int64_t)W * K + W;
+    if (e < base + sz) {
+      const int64_t r = e - base;
+      if (r < (int64_t)W * K) {
+        const int o = (int)(r / K), j = (int)(r % K);
+        const int i = l == 0 ? (j < nin / 2 ? 2 * j : 2 * (j - nin / 2) + 1) : j;
+        return base + (int64_t)i * W + o;
+      }
+      return base + (int64_t)K * W + (r - (int64_t)W * K);
+    }
+    base += sz;
+  }
+  return e;
+}
 
 // Sum the per-CTA partials in CTA order; then Adam (or just write the gradient).
 __global__ void adam_reduce_kernel(const float* partial, int nparts, int64_t P, float* params, float* m, float* v,
                                    int step, float lr_t, float* grad_out, float* loss_out, float loss_scale,
-                                   Bf16Repack rp) {
+                                   AdamAux rp) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e > P) return;
+  const int64_t pe = rp.tc_partials ? partial_index(e, rp.nin, rp.W, rp.L) : e;
   float g = 0.f;
-  for (int c = 0; c < nparts; ++c) g += partial[(int64_t)c * (P + 1) + e];
+#pragma unroll 8
+  for (int c = 0; c < nparts; ++c) g += __ldcs(partial + (int64_t)c * (P + 1) + pe);   // fixed order
   if (e == P) {
     if (loss_out) *loss_out = g * loss_scale;
     return;

@@ -112,35 +112,37 @@ __global__ void __launch_bounds__(kTile, 1) train_tc_kernel(NetView net, TrainJo
   const int64_t P = net_param_count(NIN, W, L);
   float* gpart = job.partial + (int64_t)blockIdx.x * (P + 1);
 
-  // ---- stage the BF16 forward and transposed tiles, head and Fourier matrix; clear delta^T
+  // ---- stage: the BF16 forward and transposed tiles by bulk copies (TMA) completing on the
+  // mbarrier's first phase; head and Fourier matrix by the threads; clear delta^T
+  const int64_t te = wtile_elems(NIN, W, L);
+  if (tid == 0) {
+    const uint32_t fb = (uint32_t)(te * 2), tb = (uint32_t)(wtile_t_elems(W, L) * 2);
+    mbar_init(bar, 1);
+    mbar_arrive_expect_tx(bar, fb + tb);
+    bulk_g2s(smem, net.wpk + te * 2, fb, bar);
+    if (tb) bulk_g2s(smem + lay.wt_off, net.wpk + te * 6, tb, bar);
+  }
+  for (int i = tid; i <= W; i += kTile) swh[i] = __ldg(net.p32 + (P - W - 1) + i);
+  for (int i = tid; i < 3 * M; i += kTile) sq[i] = __ldg(net.q + i);
   {
-    const int64_t te = wtile_elems(NIN, W, L);
-    const uint4* src = reinterpret_cast<const uint4*>(net.wpk + te * 2);
-    uint4* dst = reinterpret_cast<uint4*>(smem);
-    for (int64_t i = tid; i < te * 2 / 16; i += kTile) dst[i] = __ldg(src + i);
-    const uint4* srct = reinterpret_cast<const uint4*>(net.wpk + te * 6);
-    uint4* dstt = reinterpret_cast<uint4*>(smem + lay.wt_off);
-    for (int64_t i = tid; i < wtile_t_elems(W, L) * 2 / 16; i += kTile) dstt[i] = __ldg(srct + i);
-    for (int i = tid; i <= W; i += kTile) swh[i] = __ldg(net.p32 + (P - W - 1) + i);
-    for (int i = tid; i < 3 * M; i += kTile) sq[i] = __ldg(net.q + i);
     uint4* z = reinterpret_cast<uint4*>(sdt);
     for (int i = tid; i < kTile * kTile * 2 / 16; i += kTile) z[i] = make_uint4(0u, 0u, 0u, 0u);
-    for (int64_t e = tid; e <= P; e += kTile) gpart[e] = 0.f;
   }
-  if (tid == 0) mbar_init(bar, 1);
   if (warp == 0) tmem_alloc(tslot, C::TCOLS);
   fence_proxy_async_smem();
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
+  uint32_t phase = 0;
+  bool failed = !mbar_wait_bounded(bar, phase);   // the weight tiles have landed
+  phase ^= 1u;
+  failed = __syncthreads_or(failed) != 0;
   const uint32_t tbase = *tslot;
   const uint32_t tlane = tbase + ((uint32_t)(warp * 32) << 16);
   const float bh = swh[W];
   const float inv_b = 1.f / (float)job.batch;
   const uint32_t cst[8] = {0x3F80u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};   // BF16 1.0 then zeros
   float loss_acc = 0.f, gwh_acc = 0.f;   // thread c < W: dLoss/dw_h[c]; thread W: dLoss/db_h
-  uint32_t phase = 0;
-  bool failed = false;
   int ntile_done = 0;
   const int64_t ntiles = (job.batch + kTile - 1) / kTile;
   for (int64_t t = blockIdx.x; t < ntiles && !failed; t += gridDim.x, ++ntile_done) {
@@ -297,27 +299,27 @@ __global__ void __launch_bounds__(kTile, 1) train_tc_kernel(NetView net, TrainJo
       if (__syncthreads_or(!ok)) { failed = true; break; }
     }
   }
-  // ---- the TMEM gradient accumulators -> this CTA's partial slot (W_l [out][in], then b_l)
-  if (!failed && ntile_done > 0 && warp < W / 32) {
-    tc_fence_after();
+  // ---- the TMEM gradient accumulators -> this CTA's partial slot, in the order of
+  // partial_index(): column i of layer l's accumulator at i*W + o (coalesced over o)
+  if (warp < W / 32) {
+    const bool have = !failed && ntile_done > 0;
+    if (have) tc_fence_after();
     const int o = tid;
     for (int l = 0; l < L; ++l) {
       const int K = l == 0 ? NIN : W;
-      const int64_t woff = l == 0 ? 0 : (int64_t)W * NIN + W + (int64_t)(l - 1) * (W * W + W);
+      float* gl = gpart + (l == 0 ? 0 : (int64_t)W * NIN + W + (int64_t)(l - 1) * (W * W + W));
       for (int c0 = 0; c0 < K + 16; c0 += 16) {
         uint32_t v[16];
-        tmem_ld16_nowait(tlane + C::DW0 + l * C::DW_STRIDE + c0, v);
-        tmem_ld_wait();
+        if (have) {
+          tmem_ld16_nowait(tlane + C::DW0 + l * C::DW_STRIDE + c0, v);
+          tmem_ld_wait();
+        } else {
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const int i = c0 + j;
-          if (i < K) {   // layer 0: column i holds feature (i even: cos_{i/2}, odd: sin_{i/2})
-            const int src = l == 0 ? ((i & 1) ? NIN / 2 + (i >> 1) : (i >> 1)) : i;
-            gpart[woff + (int64_t)o * K + src] = __uint_as_float(v[j]);
-          } else if (i == K) {
-            gpart[woff + (int64_t)W * K + o] = __uint_as_float(v[j]);
-          }
+          for (int j = 0; j < 16; ++j) v[j] = 0u;
         }
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+          if (c0 + j <= K) gl[(int64_t)(c0 + j) * W + o] = __uint_as_float(v[j]);
       }
     }
   }
