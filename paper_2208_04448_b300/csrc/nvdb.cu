@@ -83,6 +83,21 @@ int num_sms() {
   return n;
 }
 
+// Raise a kernel's dynamic shared-memory limit on the current device, once per size: the
+// attribute call costs host time comparable to a launch, so repeated launches skip it.
+nvdb_status set_smem_limit(const void* kernel, size_t bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<const void*, int>, size_t> done;
+  int dev = 0;
+  CU(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(mu);
+  size_t& have = done[{kernel, dev}];
+  if (bytes <= have) return NVDB_OK;
+  CU(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  have = bytes;
+  return NVDB_OK;
+}
+
 inline unsigned blocks_for(int64_t n, int per) { return (unsigned)((n + per - 1) / per); }
 
 // ============================================================================ tracing
@@ -380,7 +395,7 @@ int g_occ_override = 0;
 template <int NIN, int W, int MODE>
 nvdb_status launch_tc(const EvalBatch& b, int64_t ntiles, const char* base, cudaStream_t s) {
   const TcLayout<NIN, W, MODE> lay(b.it[0].net.layers);
-  CU(cudaFuncSetAttribute(mlp_tc_kernel<NIN, W, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lay.total));
+  TRY(set_smem_limit((const void*)mlp_tc_kernel<NIN, W, MODE>, lay.total));
   // Residency from the kernel's own limits (the runtime's occupancy query reports 1 for
   // kernels that allocate tensor memory): registers, shared memory, and TMEM columns.
   cudaFuncAttributes fa;
@@ -408,7 +423,7 @@ nvdb_status launch_eval_t(const EvalBatch& b, int64_t ntiles, nvdb_precision pre
   int occ = 0;
   if (prec == NVDB_FP32) {
     const size_t smem = f32_smem_bytes<NIN, W>(b.it[0].net.layers);
-    CU(cudaFuncSetAttribute(mlp_f32_kernel<NIN, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    TRY(set_smem_limit((const void*)mlp_f32_kernel<NIN, W>, smem));
     CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, mlp_f32_kernel<NIN, W>, kTile, smem));
     const int64_t grid = std::min<int64_t>(ntiles, (int64_t)num_sms() * std::max(occ, 1));
     KLAUNCH(eval_name("mlp_f32", b.it[0].job.mode), s, mlp_f32_kernel<NIN, W><<<(unsigned)grid, kTile, smem, s>>>(b));
@@ -462,7 +477,7 @@ nvdb_status launch_eval(const nvdb_model* m, int k, nvdb_precision prec, EvalJob
 template <int NIN, int W>
 nvdb_status launch_train_t(const NetView& nv, const TrainJob& job, int grid, cudaStream_t s) {
   const size_t smem = TrainSmem<NIN, W>::bytes(nv.layers);
-  CU(cudaFuncSetAttribute(train_fwd_bwd_kernel<NIN, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  TRY(set_smem_limit((const void*)train_fwd_bwd_kernel<NIN, W>, smem));
   KLAUNCH("train_fwd_bwd", s, train_fwd_bwd_kernel<NIN, W><<<grid, kTile, smem, s>>>(nv, job));
   CU(cudaGetLastError());
   return NVDB_OK;
@@ -472,7 +487,7 @@ template <int NIN, int W>
 nvdb_status launch_train_tc_t(const NetView& nv, const TrainJob& job, int grid, cudaStream_t s) {
   const size_t smem = TrainTcLayout<NIN, W>(nv.layers).total;
   if (smem > (size_t)kSmemPerSm - 1024) return fail(NVDB_ERR_UNSUPPORTED, "training tile needs %zu bytes of shared memory", smem);
-  CU(cudaFuncSetAttribute(train_tc_kernel<NIN, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  TRY(set_smem_limit((const void*)train_tc_kernel<NIN, W>, smem));
   KLAUNCH("train_tc_bf16", s, train_tc_kernel<NIN, W><<<grid, kTile, smem, s>>>(nv, job));
   CU(cudaGetLastError());
   return NVDB_OK;
@@ -879,50 +894,100 @@ extern "C" nvdb_status nvdb_compress(const nvdb_grid* g, const nvdb_train_opts* 
     m->l2_mask_host.resize(512 * g->n_l2);
     TRY(copy_int4_to3(g->l2_origin, g->n_l2, m->l2_origin_host.data(), s));
     CU(cudaMemcpyAsync(m->l2_mask_host.data(), g->l2_mask, g->n_l2 * 4096, cudaMemcpyDeviceToHost, s));
-    // training: each network for `steps` Adam steps
+    // training: each network for `steps` Adam steps, on a stream of our own (the caller's
+    // may be the legacy default stream, which cannot be captured).  The step index lives in
+    // device memory, so one captured chunk of steps replays as a CUDA graph; profiled runs
+    // launch every step (per-kernel events would be recorded once per captured launch).
     const int grid = train_grid(o->batch);
     float* d_loss = nullptr;
-    TRY(dalloc(&d_loss, (size_t)std::max(1, o->steps)));
-    nvdb_status st = NVDB_OK;
+    int* d_step = nullptr;
+    cudaStream_t ts = nullptr;
+    cudaEvent_t ev = nullptr;
+    nvdb_status st = dalloc(&d_loss, (size_t)std::max(1, o->steps));
+    if (st == NVDB_OK) st = dalloc(&d_step, 2);
+    if (st == NVDB_OK && cudaStreamCreateWithFlags(&ts, cudaStreamNonBlocking) != cudaSuccess)
+      st = fail(NVDB_ERR_CUDA, "training stream");
+    if (st == NVDB_OK && cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess)
+      st = fail(NVDB_ERR_CUDA, "training event");
+    if (st == NVDB_OK && (cudaEventRecord(ev, s) != cudaSuccess || cudaStreamWaitEvent(ts, ev, 0) != cudaSuccess))
+      st = fail(NVDB_ERR_CUDA, "training stream order");
+    static const int kFirstStep = 1;
     for (int k = 0; k < 3 && st == NVDB_OK; ++k) {
       DevNet& d = m->net[k];
       if ((st = ensure_partial(m, (int64_t)grid * (d.P + 1))) != NVDB_OK) break;
       TrainJob job = grid_train_job(g, k, o);
       job.partial = m->partial;
-      if (o->train_prec == NVDB_BF16 && (st = pack_net(m, k, s)) != NVDB_OK) break;   // the BF16 tiles of step 1
+      job.step_dev = d_step;
+      if (o->train_prec == NVDB_BF16 && (st = pack_net(m, k, ts)) != NVDB_OK) break;   // the BF16 tiles of step 1
+      if (cudaMemcpyAsync(d_step, &kFirstStep, 4, cudaMemcpyHostToDevice, ts) != cudaSuccess) {
+        st = fail(NVDB_ERR_CUDA, "step counter");
+        break;
+      }
+      const AdamSched sc{d_step, o->lr, o->lr_decay, o->lr_interval, d_loss};
+      auto one_step = [&]() -> nvdb_status {
+        TRY(launch_train(m, k, o->train_prec, job, grid, ts));
+        KLAUNCH("adam_reduce", ts, adam_reduce_kernel<<<blocks_for(d.P + 1, 32), 32 * kRedGroups, 0, ts>>>(
+                                       m->partial, grid, d.P, d.p32, d.m, d.v, 0, 0.f, nullptr, nullptr,
+                                       1.f / (float)o->batch, adam_aux(d, o->train_prec, true), sc));
+        CU(cudaGetLastError());
+        return NVDB_OK;
+      };
       const bool early = o->stop_loss[k] > 0.f && o->stop_window > 0;
+      const int chunk = early ? o->stop_window : 50;
+      cudaGraphExec_t exec = nullptr;
       int ran = 0;
-      for (int t = 1; t <= o->steps && st == NVDB_OK; ++t) {
-        job.step = t;
-        st = launch_train(m, k, o->train_prec, job, grid, s);
-        if (st != NVDB_OK) break;
-        const float lr_t = o->lr_interval > 0 ? (float)((double)o->lr * std::pow((double)o->lr_decay, (double)((t - 1) / o->lr_interval)))
-                                              : o->lr;
-        KLAUNCH("adam_reduce", s, adam_reduce_kernel<<<blocks_for(d.P + 1, 256), 256, 0, s>>>(m->partial, grid, d.P, d.p32, d.m, d.v, t, lr_t,
-                                                                    nullptr, d_loss + (t - 1), 1.f / (float)o->batch,
-                                                                    adam_aux(d, o->train_prec, true)));
-        if (cudaGetLastError() != cudaSuccess) st = fail(NVDB_ERR_CUDA, "adam launch failed");
-        ran = t;
-        if (early && t % o->stop_window == 0) {   // warm-start early stop (Section 3.6)
+      while (ran < o->steps && st == NVDB_OK) {
+        const int n = std::min(chunk, o->steps - ran);
+        if (!exec && ran > 0 && n == chunk && !prof::g_on.load()) {   // capture after one eager chunk
+          cudaGraph_t gr = nullptr;
+          if (cudaStreamBeginCapture(ts, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+            st = fail(NVDB_ERR_CUDA, "training capture");
+            break;
+          }
+          nvdb_status cst = NVDB_OK;
+          for (int i = 0; i < chunk && cst == NVDB_OK; ++i) cst = one_step();
+          const cudaError_t e = cudaStreamEndCapture(ts, &gr);
+          if (cst == NVDB_OK && e == cudaSuccess && cudaGraphInstantiate(&exec, gr, 0) != cudaSuccess) exec = nullptr;
+          if (gr) cudaGraphDestroy(gr);
+          if (cst != NVDB_OK) { st = cst; break; }
+          if (e != cudaSuccess || !exec) { st = fail(NVDB_ERR_CUDA, "training graph: %s", cudaGetErrorString(e)); break; }
+        }
+        if (exec && n == chunk) {
+          if (cudaGraphLaunch(exec, ts) != cudaSuccess) { st = fail(NVDB_ERR_CUDA, "training graph launch"); break; }
+        } else {
+          for (int i = 0; i < n && st == NVDB_OK; ++i) st = one_step();
+          if (st != NVDB_OK) break;
+        }
+        ran += n;
+        if (early && ran % o->stop_window == 0) {   // warm-start early stop (Section 3.6)
           std::vector<float> w(o->stop_window);
-          cudaError_t e = cudaMemcpyAsync(w.data(), d_loss + (t - o->stop_window), o->stop_window * 4,
-                                          cudaMemcpyDeviceToHost, s);
-          if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+          cudaError_t e = cudaMemcpyAsync(w.data(), d_loss + (ran - o->stop_window), o->stop_window * 4,
+                                          cudaMemcpyDeviceToHost, ts);
+          if (e == cudaSuccess) e = cudaStreamSynchronize(ts);
           if (e != cudaSuccess) { st = fail(NVDB_ERR_CUDA, "loss readback: %s", cudaGetErrorString(e)); break; }
           double mean = 0.0;
           for (float v : w) mean += v;
           if (mean / o->stop_window < (double)o->stop_loss[k]) break;
         }
       }
+      if (exec) cudaGraphExecDestroy(exec);
       if (st == NVDB_OK) {
         m->losses[k].resize(ran);
         if (ran) {
-          cudaError_t e = cudaMemcpyAsync(m->losses[k].data(), d_loss, ran * 4, cudaMemcpyDeviceToHost, s);
-          if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+          cudaError_t e = cudaMemcpyAsync(m->losses[k].data(), d_loss, ran * 4, cudaMemcpyDeviceToHost, ts);
+          if (e == cudaSuccess) e = cudaStreamSynchronize(ts);
           if (e != cudaSuccess) st = fail(NVDB_ERR_CUDA, "loss readback: %s", cudaGetErrorString(e));
         }
       }
     }
+    if (ts) {   // the caller's stream continues after the training stream
+      if (st == NVDB_OK && (cudaEventRecord(ev, ts) != cudaSuccess || cudaStreamWaitEvent(s, ev, 0) != cudaSuccess))
+        st = fail(NVDB_ERR_CUDA, "training stream order");
+      cudaStreamSynchronize(ts);
+      cudaStreamDestroy(ts);
+    }
+    if (ev) cudaEventDestroy(ev);
+    dfree(d_step);
     dfree(d_loss);
     TRY(st);
     if (o->train_prec == NVDB_BF16)   // the BF16 step trained BF16 weights: store them as such
@@ -1235,8 +1300,9 @@ extern "C" nvdb_status nvdb_mlp_grad(const nvdb_model* cm, int net, nvdb_precisi
   TRY(launch_train(m, net, prec, j, grid, s));
   float* d_loss = nullptr;
   TRY(dalloc(&d_loss, 1));
-  KLAUNCH("adam_reduce", s, adam_reduce_kernel<<<blocks_for(d.P + 1, 256), 256, 0, s>>>(m->partial, grid, d.P, nullptr, nullptr, nullptr, 1, 0.f,
-                                                              d_grad, d_loss, 1.f / (float)n, adam_aux(d, prec, false)));
+  KLAUNCH("adam_reduce", s, adam_reduce_kernel<<<blocks_for(d.P + 1, 32), 32 * kRedGroups, 0, s>>>(m->partial, grid, d.P, nullptr, nullptr, nullptr, 1, 0.f,
+                                                              d_grad, d_loss, 1.f / (float)n, adam_aux(d, prec, false),
+                                                              AdamSched{}));
   float h = 0.f;
   cudaError_t e = cudaMemcpyAsync(&h, d_loss, 4, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -1502,7 +1568,7 @@ float* g_static_ptr[kMaxDevices] = {};
 template <int NIN, int W>
 nvdb_status launch_train_static(const NetView& nv, const TrainJob& job, int grid, cudaStream_t s) {
   const size_t smem = TrainSmem<NIN, W>::bytes(nv.layers);
-  CU(cudaFuncSetAttribute(train_fwd_bwd_kernel<NIN, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  TRY(set_smem_limit((const void*)train_fwd_bwd_kernel<NIN, W>, smem));
   train_fwd_bwd_kernel<NIN, W><<<grid, kTile, smem, s>>>(nv, job);
   CU(cudaGetLastError());
   return NVDB_OK;
@@ -1557,8 +1623,8 @@ extern "C" nvdb_status nvdb_mlp_grad_static(const nvdb_model* m, int net, const 
   else if (nv.n_in == 64 && nv.width == 32) TRY((launch_train_static<64, 32>(nv, j, grid, s)));
   else if (nv.n_in == 64 && nv.width == 64) TRY((launch_train_static<64, 64>(nv, j, grid, s)));
   else return fail(NVDB_ERR_UNSUPPORTED, "network shape n=%d w=%d", nv.n_in, nv.width);
-  adam_reduce_kernel<<<blocks_for(d.P + 1, 256), 256, 0, s>>>(scratch, grid, d.P, nullptr, nullptr, nullptr, 1, 0.f,
-                                                              d_grad, loss_slot, 1.f / (float)n, AdamAux{});
+  adam_reduce_kernel<<<blocks_for(d.P + 1, 32), 32 * kRedGroups, 0, s>>>(scratch, grid, d.P, nullptr, nullptr, nullptr, 1, 0.f,
+                                                              d_grad, loss_slot, 1.f / (float)n, AdamAux{}, AdamSched{});
   CU(cudaGetLastError());
   float h = 0.f;
   CU(cudaMemcpyAsync(&h, loss_slot, sizeof h, cudaMemcpyDeviceToHost, s));

@@ -31,7 +31,16 @@ struct TrainJob {
   float tscale;               // regressor target = val * tscale
   float* partial;             // [gridDim.x][P + 1]: gradient partials, then the loss sum
   uint32_t* status;           // ST_* bits (tensor-core kernel: a timed-out wait)
+  int* step_dev;              // if set: the step is step_dev[0] (a graph replays fixed launches);
+                              // block 0 copies it to step_dev[1] for the Adam kernel
 };
+
+// Read the step from device memory when the launch carries no fixed step.
+__device__ __forceinline__ void take_step(TrainJob& job) {
+  if (!job.step_dev) return;
+  job.step = job.step_dev[0];
+  if (blockIdx.x == 0 && threadIdx.x == 0) job.step_dev[1] = job.step;
+}
 
 enum : int { LOSS_MSE = 0, LOSS_L1 = 1, LOSS_BCE = 2 };
 
@@ -119,6 +128,7 @@ __device__ __forceinline__ void accum_dW(const float* D, int dstride, const floa
 template <int NIN, int W>
 __global__ void __launch_bounds__(kTile, 1) train_fwd_bwd_kernel(NetView net, TrainJob job) {
   extern __shared__ float4 smem_t4[];
+  take_step(job);
   constexpr int M = NIN / 2, KP = NIN + 1, WP = W + 1;
   const int L = net.layers;
   float* H0 = reinterpret_cast<float*>(smem_t4);            // [128][NIN+1] encoding
@@ -269,43 +279,75 @@ __device__ __forceinline__ void bf16_tile_offsets(int64_t e, int nin, int W, int
 // the BF16 tiles it reads (refreshed with every update) and the order of its partials.
 struct AdamAux {
   uint8_t* wpk;               // BF16 tiles to refresh after the update (nullptr: none)
-  int tc_partials;            // partials are in the tensor-core order of partial_index()
+  int tc_partials;            // partials are in the tensor-core order of partial_param()
   int nin, W, L;
 };
 
-// Slot of parameter e in a partial of the tensor-core training kernel: layer l's block
-// (same offset and size as its parameters W_l, b_l) holds column i of the TMEM weight
-// gradient at i*W + o, i in the kernel's feature order (layer 0 interleaved as
-// (cos_f, sin_f)), the bias at K*W + o; head and loss entries keep their places.
-__device__ __forceinline__ int64_t partial_index(int64_t e, int nin, int W, int L) {
+// Order of the partials of the tensor-core training kernel: layer l's block (same offset
+// and size as its parameters W_l, b_l) holds column i of the TMEM weight gradient at
+// i*W + o, i in the kernel's feature order (layer 0 interleaved as (cos_f, sin_f)), the
+// bias at K*W + o; head and loss entries keep their places.  Returns the parameter
+// index stored in slot pe.
+__device__ __forceinline__ int64_t partial_param(int64_t pe, int nin, int W, int L) {
   int64_t base = 0;
   for (int l = 0; l < L; ++l) {
     const int K = l == 0 ? nin : W;
     const int64_t sz = (int64_t)W * K + W;
-    if (e < base + sz) {
-      const int64_t r = e - base;
-      if (r < (int64_t)W * K) {
-        const int o = (int)(r / K), j = (int)(r % K);
-        const int i = l == 0 ? (j < nin / 2 ? 2 * j : 2 * (j - nin / 2) + 1) : j;
-        return base + (int64_t)i * W + o;
-      }
-      return base + (int64_t)K * W + (r - (int64_t)W * K);
+    if (pe < base + sz) {
+      const int64_t r = pe - base;
+      const int i = (int)(r / W), o = (int)(r % W);
+      if (i == K) return base + (int64_t)W * K + o;
+      const int j = l == 0 ? ((i & 1) ? nin / 2 + (i >> 1) : (i >> 1)) : i;
+      return base + (int64_t)o * K + j;
     }
     base += sz;
   }
-  return e;
+  return pe;
 }
 
-// Sum the per-CTA partials in CTA order; then Adam (or just write the gradient).
-__global__ void adam_reduce_kernel(const float* partial, int nparts, int64_t P, float* params, float* m, float* v,
-                                   int step, float lr_t, float* grad_out, float* loss_out, float loss_scale,
-                                   AdamAux rp) {
-  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e > P) return;
-  const int64_t pe = rp.tc_partials ? partial_index(e, rp.nin, rp.W, rp.L) : e;
+
+// Sum the per-CTA partials in a fixed order, then Adam (or just write the gradient).
+// Block = 32 slots x kRedGroups warps: warp q sums the partials of CTAs
+// [q n / G, (q+1) n / G) in CTA order (coalesced over the 32 slots), then the G chunk
+// sums are added in q order.
+constexpr int kRedGroups = 8;
+
+// Step-dependent inputs of the Adam kernel read from device memory (graph replay): the
+// step from step_dev[1], lr_t = lr * decay^floor((step - 1) / interval), the loss slot
+// loss_base[step - 1]; block 0 advances step_dev[0] for the next step.
+struct AdamSched {
+  int* step_dev;              // nullptr: use the launch's step, lr_t and loss_out
+  float lr, decay;
+  int interval;
+  float* loss_base;
+};
+
+__global__ void __launch_bounds__(32 * kRedGroups) adam_reduce_kernel(
+    const float* partial, int nparts, int64_t P, float* params, float* m, float* v, int step, float lr_t,
+    float* grad_out, float* loss_out, float loss_scale, AdamAux rp, AdamSched sc) {
+  __shared__ float red[kRedGroups][33];
+  if (sc.step_dev) {
+    step = sc.step_dev[1];
+    lr_t = sc.interval > 0 ? sc.lr * powf(sc.decay, (float)((step - 1) / sc.interval)) : sc.lr;
+    loss_out = sc.loss_base + (step - 1);
+    if (blockIdx.x == 0 && threadIdx.x == 0) sc.step_dev[0] = step + 1;
+  }
+  const int lane = threadIdx.x & 31, q = threadIdx.x >> 5;
+  // one slot per lane (coalesced over the partials), mapped to its parameter
+  const int64_t pe = (int64_t)blockIdx.x * 32 + lane;
+  float gq = 0.f;
+  if (pe <= P) {
+    const int c0 = (int)((int64_t)q * nparts / kRedGroups), c1 = (int)((int64_t)(q + 1) * nparts / kRedGroups);
+#pragma unroll 4
+    for (int c = c0; c < c1; ++c) gq += __ldcs(partial + (int64_t)c * (P + 1) + pe);
+  }
+  red[q][lane] = gq;
+  __syncthreads();
+  if (q != 0 || pe > P) return;
   float g = 0.f;
-#pragma unroll 8
-  for (int c = 0; c < nparts; ++c) g += __ldcs(partial + (int64_t)c * (P + 1) + pe);   // fixed order
+#pragma unroll
+  for (int k = 0; k < kRedGroups; ++k) g += red[k][lane];
+  const int64_t e = rp.tc_partials ? partial_param(pe, rp.nin, rp.W, rp.L) : pe;
   if (e == P) {
     if (loss_out) *loss_out = g * loss_scale;
     return;

@@ -95,6 +95,7 @@ struct TrainTcLayout {
 template <int NIN, int W>
 __global__ void __launch_bounds__(kTile, 1) train_tc_kernel(NetView net, TrainJob job) {
   static_assert(W == 32 || W == 64, "width");
+  take_step(job);
   static_assert(NIN == 32 || NIN == 64, "encoding size");
   using C = TrainTcCfg<NIN, W>;
   constexpr int M = C::M;
@@ -300,7 +301,7 @@ __global__ void __launch_bounds__(kTile, 1) train_tc_kernel(NetView net, TrainJo
     }
   }
   // ---- the TMEM gradient accumulators -> this CTA's partial slot, in the order of
-  // partial_index(): column i of layer l's accumulator at i*W + o (coalesced over o)
+  // partial_param(): column i of layer l's accumulator at i*W + o (coalesced over o)
   if (warp < W / 32) {
     const bool have = !failed && ntile_done > 0;
     if (have) tc_fence_after();

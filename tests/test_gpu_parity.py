@@ -252,6 +252,24 @@ def test_bf16_training_tracks_fp32(sphere128):
             assert np.abs(dv - 3.0 * want).max() <= tc_bar(prec) * 3.0
 
 
+def test_graph_replayed_training_equals_launched(sphere128):
+    """Chunks of 50 training steps replay as a CUDA graph unless profiling is on (then every
+    step is launched): 130 steps run a launched chunk, a replayed chunk and a launched
+    remainder, and both ways give the same bits."""
+    ijk, val, ref = sphere128
+    g = _grid(ijk, val)
+    kw = dict(seed=5, ffm_sigma=1.25, steps=130, batch=4096, patch_precs=1)
+    for prec in (0, 1):
+        nv.profile_enable(True)
+        launched = nv.compress(g, train_prec=prec, **kw)
+        nv.profile_enable(False)
+        nv.profile_read()
+        replayed = nv.compress(g, train_prec=prec, **kw)
+        assert launched.export() == replayed.export()
+        for k in range(3):
+            assert np.array_equal(launched.losses(k), replayed.losses(k)) and len(replayed.losses(k)) == 130
+
+
 def test_training_precision_errors(sphere128):
     ijk, val, ref = sphere128
     g = _grid(ijk, val)
