@@ -307,16 +307,32 @@ def main():
                 ffm_sigma=10.0 * (1 << info["log2_extent"]) / 1024.0, steps=args.train_steps,
                 batch=args.train_batch, lr=1e-3, lr_decay=0.975, lr_interval=100, patch_precs=0b11011,
                 train_prec=PRECS[args.train_prec])
+    # training, end to end: compress with all steps minus compress with none (the same
+    # setup and patch generation), unprofiled, so that chunks of steps replay as CUDA graphs
+    def compress_wall(**kw):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        mdl = nv.compress(g, **dict(opts, **kw))
+        torch.cuda.synchronize()
+        return mdl, time.perf_counter() - t
+    _, base_wall = compress_wall(steps=0)
+    model, full_wall = compress_wall()
+    train_wall = max(full_wall - base_wall, 1e-9)
+    train_samples = 3 * args.train_steps * args.train_batch
+    # per-kernel breakdown from a profiled run (every step launched, events per launch)
+    prof_steps = min(args.train_steps, 200)
     nv.profile_read()
     nv.profile_enable(True)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    model = nv.compress(g, **opts)
-    train_wall = time.perf_counter() - t0
+    compress_wall(steps=prof_steps, patch_precs=1 << PRECS["fp16"])
     prof = nv.profile_read()
     nv.profile_enable(False)
+    train_kern = {k: dict(launches=v[0], us_per_launch=1e3 * v[1] / max(v[0], 1)) for k, v in prof.items()
+                  if k in TRAIN_KERNELS}
     train_ms = sum(v[1] for k, v in prof.items() if k in TRAIN_KERNELS)
-    train_samples = 3 * args.train_steps * args.train_batch
+    n_in, w_, L_ = FFM[1], NET_WIDTH[1], NET_LAYERS[1]
+    f_net = 2 * (n_in * w_ + (L_ - 1) * w_ * w_ + w_)
+    train_flops_per_sample = 3 * f_net - 2 * n_in * w_          # forward, dW, delta (not into the encoding)
+    train_tflops = 3 * prof_steps * args.train_batch * train_flops_per_sample / (train_ms / 1e3) / 1e12 if train_ms else None
     blob_bytes = model.export()
 
     out_ijk = torch.empty((n_active, 3), dtype=torch.int32, device="cuda")
@@ -428,6 +444,19 @@ def main():
 
     rl = roofline(head_kern)
     dname = rl["kernel"]
+
+    # ---- compaction kernels against the measured HBM copy bandwidth: algorithmic bytes per
+    # launch (emit: 12 B written per voxel, 64 B words + 16 B origin + 8 B offset read per leaf;
+    # patch application over the leaf words: 64 B read and written, 4 B count per leaf)
+    comp_bytes = {"emit_voxels": 12 * n_active + 88 * n_leaf, "patch_count": 132 * n_leaf + 1028 * n_l1}
+    compaction = {}
+    for kname, nbytes in comp_bytes.items():
+        if kname in head_kern:
+            nl, tms = head_kern[kname]
+            per_launch = nbytes if kname == "emit_voxels" else nbytes / 2   # patch_count runs once per level
+            gbs = per_launch / (tms / nl / 1e3) / 1e9
+            compaction[kname] = dict(bytes_per_launch=per_launch, avg_launch_us=1e3 * tms / nl, achieved_gbs=gbs,
+                                     frac_of_hbm=gbs / peaks["hbm_gbs"])
     traffic = None
     tfile = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(tfile):
@@ -476,12 +505,17 @@ def main():
                  d2h_bytes_per_step=16 * n_active),
         gpu_launches=int(head_launches),
         clocks=clocks,
-        train_samples_per_s=train_samples / (train_ms / 1e3) if train_ms > 0 else None,
-        train=dict(steps=args.train_steps, batch=args.train_batch, wall_s=train_wall, kernel_ms=train_ms,
-                   final_loss=[float(np.mean(model.losses(k)[-50:])) for k in range(3)] if args.train_steps else None,
-                   precision=args.train_prec),
+        train_samples_per_s=train_samples / train_wall if args.train_steps else None,
+        train=dict(steps=args.train_steps, batch=args.train_batch, wall_s=train_wall, precision=args.train_prec,
+                   samples_per_s="end to end: (compress wall - compress wall with 0 steps), chunks of 50 steps "
+                                 "replayed as CUDA graphs",
+                   kernels=train_kern, kernel_tflops=train_tflops,
+                   kernel_frac_of_peak=(train_tflops / peaks["bf16_tflops"]) if train_tflops else None,
+                   flops_per_sample=train_flops_per_sample,
+                   final_loss=[float(np.mean(model.losses(k)[-50:])) for k in range(3)] if args.train_steps else None),
         by_precision=by_prec,
         kernels={k: dict(launches=v[0], ms=v[1]) for k, v in sorted(head_kern.items(), key=lambda kv: -kv[1][1])},
+        compaction=compaction,
     )
     if rank == 0:
         print(json.dumps(line))
