@@ -39,7 +39,7 @@ sys.path.insert(0, ROOT)
 import numpy as np  # noqa: E402
 import torch  # noqa: E402
 
-PRECS = {"fp32": 0, "bf16": 1, "fp16": 3, "bf16x3": 4}
+PRECS = {"fp32": 0, "bf16": 1, "fp8": 2, "fp16": 3, "bf16x3": 4}
 WORKLOAD_DESC = ("union of 32 spheres + 32 tori (seed 2), 1024^3, half-band 3; 3 nets 4x64 ReLU, "
                  "FFM n=64 sigma=10/1024vox; full decompress")
 NET_WIDTH, NET_LAYERS, FFM = [64, 64, 64], [4, 4, 4], [64, 64]
@@ -219,7 +219,7 @@ def run_water(args):
     import paper_2208_04448_b300 as nv
     from fixtures import water_frame
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-    shape = dict(width=NET_WIDTH, layers=NET_LAYERS, ffm_size=FFM, batch=args.train_batch, patch_precs=0b11011,
+    shape = dict(width=NET_WIDTH, layers=NET_LAYERS, ffm_size=FFM, batch=args.train_batch, patch_precs=0b11111,
                  train_prec=PRECS[args.train_prec])
     models, steps, n_total, train_ms = [], [], 0, 0.0
     nv.profile_read()
@@ -305,7 +305,7 @@ def main():
     n_active, n_leaf, n_l1 = info["n_active"], info["n_leaf"], info["n_l1"]
     opts = dict(seed=1, width=NET_WIDTH, layers=NET_LAYERS, ffm_size=FFM,
                 ffm_sigma=10.0 * (1 << info["log2_extent"]) / 1024.0, steps=args.train_steps,
-                batch=args.train_batch, lr=1e-3, lr_decay=0.975, lr_interval=100, patch_precs=0b11011,
+                batch=args.train_batch, lr=1e-3, lr_decay=0.975, lr_interval=100, patch_precs=0b11111,
                 train_prec=PRECS[args.train_prec])
     # training, end to end: compress with all steps minus compress with none (the same
     # setup and patch generation), unprofiled, so that chunks of steps replay as CUDA graphs

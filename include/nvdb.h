@@ -59,7 +59,8 @@ typedef enum {
 typedef enum {
   NVDB_FP32 = 0,      /* plain FP32 on CUDA cores (FFMA), FP32 encoding */
   NVDB_BF16 = 1,      /* tcgen05 tensor cores, BF16 operands (one MMA term), FP32 accumulate in TMEM */
-  NVDB_FP8_E4M3 = 2,  /* FP8 E4M3 hidden layers on tcgen05 (reserved; returns UNSUPPORTED) */
+  NVDB_FP8_E4M3 = 2,  /* tcgen05: first layer FP16 on the encoding, hidden layers E4M3 activations
+                         and weights (kind::f8f6f4) with one scale per layer, FP32 accumulate */
   NVDB_FP16 = 3,      /* tcgen05 tensor cores, FP16 operands (one MMA term), FP32 accumulate in TMEM */
   NVDB_BF16X3 = 4     /* tcgen05 tensor cores, activations and weights as hi + lo BF16 pairs
                          (three MMA terms; two when the weights are BF16 values), FP32 accumulate */
@@ -91,7 +92,7 @@ typedef struct {
   int32_t lr_interval;  /* 0 = constant learning rate */
   int32_t loss;         /* regressor loss: NVDB_LOSS_MSE or NVDB_LOSS_L1 */
   int32_t train_prec;   /* arithmetic of training: NVDB_FP32 or NVDB_BF16 (tensor cores) */
-  uint32_t patch_precs; /* bit p set = store patches for decoding at precision p (default: FP32|BF16|FP16|BF16X3) */
+  uint32_t patch_precs; /* bit p set = store patches for decoding at precision p (default: all five) */
   int32_t stop_window;  /* early stop (warm-started frames, Section 3.6): every stop_window steps ... */
   float stop_loss[3];   /* ... network k stops once the mean of its last stop_window losses < stop_loss[k];
                            0 = train all `steps` */

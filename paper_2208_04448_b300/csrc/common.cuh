@@ -153,6 +153,17 @@ __device__ __forceinline__ void mma_f16kind(uint32_t d_tmem, uint64_t adesc, uin
       :: "r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate) : "memory");
 }
 
+// 8-bit (E4M3 x E4M3 -> F32) MMA with the A operand in tensor memory; K = 32 per
+// instruction.  The instruction descriptor has the same bits as idesc_f16_f32 (E4M3 = 0).
+__device__ __forceinline__ void mma_f8kind_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc, uint32_t idesc,
+                                              uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], [%1], %2, %3, p;\n\t}"
+      :: "r"(d_tmem), "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(accumulate) : "memory");
+}
+
 // 16-bit A operand read from tensor memory: tcgen05.mma with [a_tmem].
 __device__ __forceinline__ void mma_f16kind_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc, uint32_t idesc,
                                                uint32_t accumulate) {
@@ -233,6 +244,22 @@ __device__ __forceinline__ uint32_t cvt_bf16x2(float lo, float hi) {
   return d;
 }
 
+// Two FP32 values -> two E4M3 bytes (round to nearest, saturating to +-448) in the low
+// 16 bits (lo in the low byte).
+__device__ __forceinline__ uint32_t cvt_e4m3x2(float lo, float hi) {
+  uint16_t d;
+  asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(d) : "f"(hi), "f"(lo));
+  return d;
+}
+
+// Two FP32 values -> ReLU -> two E4M3 bytes (saturating to +-448) in the low 16 bits
+// (lo in the low byte).
+__device__ __forceinline__ uint32_t cvt_relu_e4m3x2(float lo, float hi) {
+  uint16_t d;
+  asm("cvt.rn.satfinite.relu.e4m3x2.f32 %0, %1, %2;" : "=h"(d) : "f"(hi), "f"(lo));
+  return d;
+}
+
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
                :: "r"(smem_u32(bar)) : "memory");
@@ -274,6 +301,12 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
 // no-swizzle K-major layout used above (LBO = 128, SBO = K * 16).
 __host__ __device__ __forceinline__ uint32_t canon_off(int r, int k, int K) {
   return (uint32_t)(((r >> 3) * (K >> 3) + (k >> 3)) * 128 + (r & 7) * 16 + (k & 7) * 2);
+}
+
+// Byte offset of element (r, k) of an 8-bit [rows x K] operand in the canonical
+// no-swizzle K-major layout (core matrices of 8 rows x 16 bytes; LBO 128, SBO K * 8).
+__host__ __device__ __forceinline__ uint32_t canon_off8(int r, int k, int K) {
+  return (uint32_t)(((r >> 3) * (K >> 4) + (k >> 4)) * 128 + (r & 7) * 16 + (k & 15));
 }
 
 }  // namespace nvdb

@@ -225,6 +225,9 @@ __global__ void __launch_bounds__(kTile) mlp_f32_kernel(const __grid_constant__ 
 //             ~2^-16 relative.
 //  TC_FP16  : FP16 activations and weights, one MMA per K step.
 //  TC_BF16  : BF16 activations and weights, one MMA per K step.
+//  TC_FP8   : the first layer (on the encoding) as TC_FP16; the hidden layers with E4M3
+//             activations and weights (kind::f8f6f4, K = 32 per MMA), one scale per
+//             layer, bias and scales applied in the FP32 epilogue: h = relu(alpha D + beta).
 // Layout per CTA (one 128-row tile in flight):
 //  * weights in shared memory, each layer a [W x (K+16)] tile in the canonical
 //    no-swizzle K-major layout; column K holds the bias, columns K+1.. are zero;
@@ -232,7 +235,31 @@ __global__ void __launch_bounds__(kTile) mlp_f32_kernel(const __grid_constant__ 
 //    32-bit column, written by each thread for its own row with tcgen05.st;
 //    column K/2 holds the constant 1 that multiplies the bias column;
 //  * the FP32 accumulator D in tensor memory columns [0, W).
-enum TcMode : int { TC_BF16X3 = 0, TC_FP16 = 1, TC_BF16 = 2 };
+enum TcMode : int { TC_BF16X3 = 0, TC_FP16 = 1, TC_BF16 = 2, TC_FP8 = 3 };
+
+// FP16 encoding and first layer (TC_FP16, and TC_FP8's first layer).
+template <int MODE>
+struct Enc16 {
+  static constexpr bool value = MODE == TC_FP16 || MODE == TC_FP8;
+};
+
+// Transposed hidden-layer tiles W_l^T, l = 1..L-1: [W (in) x W (out)] BF16,
+// canonical K-major over `out`; stored after the three forward tile copies.
+__host__ __device__ inline int64_t wtile_t_elems(int w, int L) { return (int64_t)(L - 1) * w * w; }
+// FP8 part of the packed weights, after the 16-bit tiles: the E4M3 tiles of layers
+// 1..L-1 ([W x W], canonical 8-bit K-major), then floats alpha_l at [l] (l < kMaxLayers)
+// and beta_l[W] at [kMaxLayers + l W] of the epilogue h = relu(alpha_l D + beta_l).
+__host__ __device__ inline int64_t fp8_tile_bytes(int w, int L) { return (int64_t)(L - 1) * w * w; }
+__host__ __device__ inline int64_t fp8_aux_bytes(int w, int L) {
+  return ((int64_t)(kMaxLayers + L * w) * 4 + 15) & ~(int64_t)15;
+}
+__host__ __device__ inline int64_t wpk_fp8_off(int nin, int w, int L) {
+  return (int64_t)w * (nin + 16) * 6 + (int64_t)(L - 1) * w * (w + 16) * 6 + wtile_t_elems(w, L) * 2;
+}
+// Bytes of the packed weights: [FP16 | BF16 hi | BF16 lo] tiles, BF16 W_l^T tiles, FP8 part.
+__host__ __device__ inline int64_t wpk_bytes(int nin, int w, int L) {
+  return wpk_fp8_off(nin, w, L) + fp8_tile_bytes(w, L) + fp8_aux_bytes(w, L);
+}
 
 __host__ __device__ inline int64_t wtile_elems(int nin, int w, int L) {
   return (int64_t)w * (nin + 16) + (int64_t)(L - 1) * w * (w + 16);
@@ -246,6 +273,7 @@ struct TcCfg {
   static constexpr uint32_t A_HI = 64u, A_LO = 128u;        // TMEM columns of the A operand(s)
   static constexpr int MAXC = (int)(512u / COLS);           // CTAs per SM that fit in TMEM
   static constexpr int NCOPY = MODE == TC_BF16X3 ? 2 : 1;
+  static constexpr bool ENC16 = Enc16<MODE>::value;
 };
 
 constexpr size_t kSmemPerSmDev = 233472;
@@ -255,9 +283,11 @@ struct TcLayout {
   size_t w_bytes, t_off, p_off, wh_off, q_off, bar_off, slot_off, total;
   __host__ __device__ TcLayout(int L) {
     using C = TcCfg<NIN, W, MODE>;
-    w_bytes = (size_t)wtile_elems(NIN, W, L) * 2;           // one copy
+    // one copy of the 16-bit tiles; FP8: the FP16 first-layer tile, the E4M3 tiles, alpha/beta
+    w_bytes = MODE == TC_FP8 ? (size_t)W * C::K0 * 2 + fp8_tile_bytes(W, L) + fp8_aux_bytes(W, L)
+                             : (size_t)wtile_elems(NIN, W, L) * 2;
     t_off = (C::NCOPY * w_bytes + 15) & ~(size_t)15;
-    p_off = t_off + (size_t)C::M * 64 * (MODE == TC_FP16 ? 4 : 8);   // T table [M][64]: half2 / float2
+    p_off = t_off + (size_t)C::M * 64 * (C::ENC16 ? 4 : 8);   // T table [M][64]: half2 / float2
     wh_off = p_off + (size_t)2 * 2 * C::M * 8;               // P tables, two buffers of [2][M] x 8 B
     q_off = wh_off + (size_t)(W + 4) * 4;
     bar_off = (q_off + (size_t)C::M * 12 + 7) & ~(size_t)7;
@@ -271,7 +301,7 @@ struct TcLayout {
 
 template <int MODE>
 __device__ __forceinline__ void split_pair(float a, float b, uint32_t& hi, uint32_t& lo) {
-  if (MODE == TC_FP16) {
+  if (Enc16<MODE>::value) {
     hi = cvt_f16x2(a, b);
     lo = 0u;
   } else if (MODE == TC_BF16) {
@@ -310,7 +340,7 @@ template <int NK, int MODE>
 __device__ __forceinline__ void store_a_row(uint32_t tlane, const uint32_t* hi, const uint32_t* lo) {
   using C = TcCfg<32, 32, MODE>;
   tmem_st_cols<NK / 2>(tlane + C::A_HI, hi);
-  uint32_t cst[8] = {MODE == TC_FP16 ? 0x3C00u : 0x3F80u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+  uint32_t cst[8] = {Enc16<MODE>::value ? 0x3C00u : 0x3F80u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
   tmem_st8(tlane + C::A_HI + NK / 2, cst);
   if (MODE == TC_BF16X3) {
     tmem_st_cols<NK / 2>(tlane + C::A_LO, lo);
@@ -330,7 +360,7 @@ __device__ __forceinline__ void l0_factors(const EvalJob& job, const uint32_t* s
                       sq[3 * f + 1] * (uint32_t)(o.y - job.oy) + sq[3 * f + 2] * (uint32_t)(o.z - job.oz);
   float sn, cs;
   sincospif((float)(int32_t)ph * 0x1p-31f, &sn, &cs);
-  if (MODE == TC_FP16) {
+  if (Enc16<MODE>::value) {
     const __half2 pc = __float2half2_rn(cs), ps = __floats2half2_rn(-sn, sn);
     reinterpret_cast<uint2*>(sPb)[tid] =
         make_uint2(*reinterpret_cast<const uint32_t*>(&pc), *reinterpret_cast<const uint32_t*>(&ps));
@@ -351,11 +381,19 @@ __device__ __forceinline__ void tc_stage(const NetView& net, int mode, const TcL
   float* swh = reinterpret_cast<float*>(smem + lay.wh_off);
   uint32_t* sq = reinterpret_cast<uint32_t*>(smem + lay.q_off);
   const int64_t te = wtile_elems(NIN, W, L);
-  const uint8_t* base = net.wpk + (MODE == TC_FP16 ? 0 : te * 2);
-  const uint4* src = reinterpret_cast<const uint4*>(base);
   uint4* dst = reinterpret_cast<uint4*>(smem);
-  const size_t n16 = C::NCOPY * lay.w_bytes / 16;
-  for (size_t i = tid; i < n16; i += kTile) dst[i] = __ldg(src + i);
+  if (MODE == TC_FP8) {   // FP16 first-layer tile, then the FP8 part
+    const size_t n0 = (size_t)W * C::K0 * 2 / 16, n1 = (size_t)(lay.w_bytes / 16) - n0;
+    const uint4* s0 = reinterpret_cast<const uint4*>(net.wpk);
+    const uint4* s1 = reinterpret_cast<const uint4*>(net.wpk + wpk_fp8_off(NIN, W, L));
+    for (size_t i = tid; i < n0; i += kTile) dst[i] = __ldg(s0 + i);
+    for (size_t i = tid; i < n1; i += kTile) dst[n0 + i] = __ldg(s1 + i);
+  } else {
+    const uint8_t* base = net.wpk + (MODE == TC_FP16 ? 0 : te * 2);
+    const uint4* src = reinterpret_cast<const uint4*>(base);
+    const size_t n16 = C::NCOPY * lay.w_bytes / 16;
+    for (size_t i = tid; i < n16; i += kTile) dst[i] = __ldg(src + i);
+  }
   const int64_t hoff = net_param_count(NIN, W, L) - W - 1;
   for (int o = tid; o <= W; o += kTile) swh[o] = __ldg(net.p32 + hoff + o);
   for (int i = tid; i < 3 * M; i += kTile) sq[i] = __ldg(net.q + i);
@@ -363,14 +401,14 @@ __device__ __forceinline__ void tc_stage(const NetView& net, int mode, const TcL
   if (mode == MODE_L0) {
     // entry (f, j) at [f / G][j][f % G], G = 4 (half2) or 2 (float2): one 16-byte load
     // gives a thread G consecutive frequencies of its (dy, dz)
-    constexpr int G = MODE == TC_FP16 ? 4 : 2;
+    constexpr int G = C::ENC16 ? 4 : 2;
     for (int i = tid; i < M * 64; i += kTile) {
       const int f = i >> 6, j = i & 63;
       const uint32_t ph = sq[3 * f + 1] * (uint32_t)(j >> 3) + sq[3 * f + 2] * (uint32_t)(j & 7);
       float sn, cs;
       sincospif((float)(int32_t)ph * 0x1p-31f, &sn, &cs);
       const int at = ((f / G) * 64 + j) * G + f % G;
-      if (MODE == TC_FP16) sTh[at] = __floats2half2_rn(cs, sn);
+      if (C::ENC16) sTh[at] = __floats2half2_rn(cs, sn);
       else sT[at] = make_float2(cs, sn);
     }
   }
@@ -405,7 +443,10 @@ __global__ void __launch_bounds__(kTile, MODE == TC_BF16X3 ? 1 : 4) mlp_tc_kerne
   tc_fence_after();
   const uint32_t tbase = *tslot;
   const uint32_t tlane = tbase + ((uint32_t)(warp * 32) << 16);
-  const uint32_t idesc = MODE == TC_FP16 ? idesc_f16_f32(kTile, W) : idesc_bf16_f32(kTile, W);
+  const uint32_t idesc = C::ENC16 ? idesc_f16_f32(kTile, W) : idesc_bf16_f32(kTile, W);
+  // FP8: E4M3 tiles and the per-layer epilogue constants, after the FP16 first-layer tile
+  const uint32_t f8_tiles = (uint32_t)(W * C::K0 * 2);
+  const float* f8_aux = reinterpret_cast<const float*>(smem + f8_tiles + fp8_tile_bytes(W, L));
 
   uint32_t phase = 0;
   bool failed = false;
@@ -448,7 +489,7 @@ __global__ void __launch_bounds__(kTile, MODE == TC_BF16X3 ? 1 : 4) mlp_tc_kerne
           __syncthreads();
         }
         const int j = tid & 63;
-        if (MODE == TC_FP16) {
+        if (C::ENC16) {
           // complex product in half2: (pc, pc) * (tc, ts) + (-ps, ps) * (ts, tc) = (cos, sin)
           const uint4* P4 = reinterpret_cast<const uint4*>(sPc) + (tid >> 6) * (M / 2);
           const uint4* T4 = reinterpret_cast<const uint4*>(sTh);
@@ -501,7 +542,13 @@ __global__ void __launch_bounds__(kTile, MODE == TC_BF16X3 ? 1 : 4) mlp_tc_kerne
     float y = 0.f;
     for (int l = 0; l < L; ++l) {
       const int K = l == 0 ? C::K0 : C::KH;
-      if (tid == 0) {
+      if (tid == 0 && MODE == TC_FP8 && l > 0) {   // E4M3 hidden layer: K = W, 32 per MMA
+        tc_fence_after();
+        const uint32_t b0 = smem_u32(sw) + f8_tiles + (uint32_t)((l - 1) * W * W);
+        for (int ks = 0; ks < W / 32; ++ks)
+          mma_f8kind_ts(tbase, tbase + C::A_HI + ks * 8, smem_desc(b0 + ks * 256, 128, W * 8), idesc, ks > 0 ? 1u : 0u);
+        mma_commit(bar);
+      } else if (tid == 0) {
         tc_fence_after();
         const uint32_t woff = l == 0 ? 0u : (uint32_t)(W * C::K0 + (l - 1) * W * C::KH) * 2u;
         const uint32_t b0 = smem_u32(sw) + woff, bl = smem_u32(sw_lo) + woff;
@@ -525,7 +572,26 @@ __global__ void __launch_bounds__(kTile, MODE == TC_BF16X3 ? 1 : 4) mlp_tc_kerne
       tmem_ld32_nowait(tlane, accu);
       if (W == 64) tmem_ld32_nowait(tlane + 32, accu + 32);
       tmem_ld_wait();
-      if (l < L - 1) {
+      if (MODE == TC_FP8) {   // h = relu(alpha D + beta): E4M3 input of the next layer, or the head's input
+        const float al = f8_aux[l];
+        const float2* be = reinterpret_cast<const float2*>(f8_aux + kMaxLayers + l * W);
+#pragma unroll
+        for (int c = 0; c < W / 2; ++c) {
+          const float2 h = ffma2(make_float2(al, al), make_float2(__uint_as_float(accu[2 * c]), __uint_as_float(accu[2 * c + 1])),
+                                 be[c]);
+          accu[2 * c] = __float_as_uint(h.x);
+          accu[2 * c + 1] = __float_as_uint(h.y);
+        }
+      }
+      if (MODE == TC_FP8 && l < L - 1) {
+        uint32_t q[W / 4];
+#pragma unroll
+        for (int c = 0; c < W / 4; ++c)
+          q[c] = cvt_relu_e4m3x2(__uint_as_float(accu[4 * c]), __uint_as_float(accu[4 * c + 1])) |
+                 (cvt_relu_e4m3x2(__uint_as_float(accu[4 * c + 2]), __uint_as_float(accu[4 * c + 3])) << 16);
+        tmem_st_cols<W / 4>(tlane + C::A_HI, q);
+        tmem_st_wait();
+      } else if (l < L - 1) {
         uint32_t hi[W / 2], lo[W / 2];
 #pragma unroll
         for (int p = 0; p < W / 2; ++p)
@@ -585,6 +651,125 @@ __global__ void pack_weights_kernel(const float* p32, uint8_t* wpk, int nin, int
     *reinterpret_cast<__half*>(wpk + off) = __float2half_rn(v);
     *reinterpret_cast<__nv_bfloat16*>(wpk + total * 2 + off) = hi;
     *reinterpret_cast<__nv_bfloat16*>(wpk + total * 4 + off) = __float2bfloat16_rn(v - __bfloat162float(hi));
+  }
+}
+
+// Largest ReLU output of every hidden layer of a network over n seeded lattice points of
+// its domain (coordinates uniform in [0, 2^log2_extent) per axis, in the level's units),
+// as float bits merged with atomicMax (the values are >= 0).  It calibrates the E4M3
+// activation scales of TC_FP8 from the model alone, so an imported model gets the same.
+template <int NIN, int W>
+__global__ void calib_amax_kernel(NetView net, int log2_extent, uint64_t seed, int n, uint32_t* amax_bits) {
+  constexpr int H = NIN > W ? NIN : W;
+  __shared__ uint32_t sq[3 * (NIN / 2)];
+  for (int i = threadIdx.x; i < 3 * (NIN / 2); i += blockDim.x) sq[i] = net.q[i];
+  __syncthreads();
+  const int L = net.layers;
+  const uint32_t mask = (1u << log2_extent) - 1u;
+  float lmax[kMaxLayers];
+#pragma unroll
+  for (int l = 0; l < kMaxLayers; ++l) lmax[l] = 0.f;
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
+    uint64_t z = seed + 0x9E3779B97F4A7C15ull * (uint64_t)(s + 1);   // SplitMix64 finaliser
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    float h[H], a[W];
+    encode_f32<NIN>(sq, (int)(z & mask), (int)((z >> 21) & mask), (int)((z >> 42) & mask), h);
+    const float* p = net.p32;
+#pragma unroll
+    for (int l = 0; l < kMaxLayers; ++l) {
+      if (l >= L) break;
+      if (l == 0) {
+        dense_f32<NIN, W>(p, h, a);
+        p += W * NIN + W;
+      } else {
+        dense_f32<W, W>(p, h, a);
+        p += W * W + W;
+      }
+#pragma unroll
+      for (int o = 0; o < W; ++o) {
+        h[o] = fmaxf(a[o], 0.f);
+        lmax[l] = fmaxf(lmax[l], h[o]);
+      }
+    }
+  }
+#pragma unroll
+  for (int l = 0; l < kMaxLayers; ++l) {
+    float v = lmax[l];
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if ((threadIdx.x & 31) == 0 && l < L) atomicMax(amax_bits + l, __float_as_uint(v));
+  }
+}
+
+// The FP8 part of the packed weights (fp8_tile_bytes, fp8_aux_bytes) for one network;
+// one block of 256 threads.  Activation ranges: twice the largest output of layer l that
+// calib_amax_kernel measured (amax_bits, may be nullptr), capped by a bound that holds for
+// every input since the encoding is bounded by 1 in absolute value:
+//   a_0 = 1,  a_{l+1} <= max_o (sum_i |W_l[o][i]| a_l + |b_l[o]|)   (range of layer l's output);
+// a tensor with bound a is stored as E4M3 of x / s, s = a / 448 (E4M3's largest finite
+// value); layer l >= 1 stores E4M3 of W_l / s_w, s_w = max |W_l| / 448.  Epilogue constants:
+//   l = 0 (FP16 layer, bias in the MMA): alpha = 1 / s_{a_1}, beta = 0 (alpha = 1 if L = 1);
+//   0 < l < L-1: alpha = s_w s_{a_l} / s_{a_{l+1}}, beta = b_l / s_{a_{l+1}};
+//   l = L-1 > 0: alpha = s_w s_{a_l}, beta = b_l (the FP32 input of the head).
+__global__ void pack_fp8_kernel(const float* p32, uint8_t* wpk, int nin, int W, int L, const uint32_t* amax_bits) {
+  __shared__ float red_b[256], red_w[256];
+  uint8_t* tiles = wpk + wpk_fp8_off(nin, W, L);
+  float* aux = reinterpret_cast<float*>(tiles + fp8_tile_bytes(W, L));
+  const int tid = threadIdx.x;
+  float a_in = 1.f;
+  int64_t woff = 0;
+  for (int l = 0; l < L; ++l) {
+    const int K = l == 0 ? nin : W;
+    const float* Wl = p32 + woff;
+    const float* bl = Wl + (int64_t)W * K;
+    float rb = 0.f, wm = 0.f;
+    for (int o = tid; o < W; o += blockDim.x) {
+      float sum = 0.f;
+      for (int i = 0; i < K; ++i) {
+        const float w = fabsf(Wl[(int64_t)o * K + i]);
+        sum += w;
+        wm = fmaxf(wm, w);
+      }
+      rb = fmaxf(rb, sum * a_in + fabsf(bl[o]));
+    }
+    red_b[tid] = rb;
+    red_w[tid] = wm;
+    __syncthreads();
+    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+      if (tid < h) {
+        red_b[tid] = fmaxf(red_b[tid], red_b[tid + h]);
+        red_w[tid] = fmaxf(red_w[tid], red_w[tid + h]);
+      }
+      __syncthreads();
+    }
+    // the measured range (with a factor 2 of headroom) where there is one, else the bound
+    const float meas = amax_bits && l < L - 1 ? 2.f * __uint_as_float(amax_bits[l]) : 0.f;
+    const float a_out = meas > 0.f ? fminf(meas, red_b[0]) : red_b[0] > 0.f ? red_b[0] : 1.f;
+    const float s_in = a_in / 448.f, s_out = a_out / 448.f, s_w = red_w[0] > 0.f ? red_w[0] / 448.f : 1.f;
+    float alpha, bscale;
+    if (l == 0) {
+      alpha = L > 1 ? 1.f / s_out : 1.f;
+      bscale = 0.f;
+    } else if (l < L - 1) {
+      alpha = s_w * s_in / s_out;
+      bscale = 1.f / s_out;
+    } else {
+      alpha = s_w * s_in;
+      bscale = 1.f;
+    }
+    if (tid == 0) aux[l] = alpha;
+    for (int o = tid; o < W; o += blockDim.x) aux[kMaxLayers + l * W + o] = bl[o] * bscale;
+    if (l > 0) {
+      uint8_t* tl = tiles + (int64_t)(l - 1) * W * W;
+      for (int e = tid; e < W * W; e += blockDim.x) {
+        const int o = e / W, i = e % W;
+        tl[canon_off8(o, i, W)] = (uint8_t)(cvt_e4m3x2(Wl[(int64_t)o * W + i] / s_w, 0.f) & 0xFFu);
+      }
+    }
+    __syncthreads();   // red_* are reused by the next layer
+    a_in = a_out;
+    woff += (int64_t)W * K + W;
   }
 }
 

@@ -139,13 +139,15 @@ struct Scope {
   } while (0)
 
 const char* eval_name(const char* base, int mode) {
-  static const char* names[4][3] = {{"mlp_f32.L1", "mlp_f32.L0", "mlp_f32.list"},
+  static const char* names[5][3] = {{"mlp_f32.L1", "mlp_f32.L0", "mlp_f32.list"},
                                     {"mlp_bf16x3.L1", "mlp_bf16x3.L0", "mlp_bf16x3.list"},
                                     {"mlp_f16.L1", "mlp_f16.L0", "mlp_f16.list"},
-                                    {"mlp_bf16.L1", "mlp_bf16.L0", "mlp_bf16.list"}};
+                                    {"mlp_bf16.L1", "mlp_bf16.L0", "mlp_bf16.list"},
+                                    {"mlp_fp8.L1", "mlp_fp8.L0", "mlp_fp8.list"}};
   const int b = std::strcmp(base, "mlp_bf16x3") == 0 ? 1
                 : std::strcmp(base, "mlp_f16") == 0  ? 2
                 : std::strcmp(base, "mlp_bf16") == 0 ? 3
+                : std::strcmp(base, "mlp_fp8") == 0  ? 4
                                                      : 0;
   return names[b][mode];
 }
@@ -265,7 +267,8 @@ struct DevNet {
   float* m = nullptr;
   float* v = nullptr;
   bool bf16_exact = false;  // every weight and bias (not the head) is a BF16 value
-  ~DevNet() { dfree(p32); dfree(wpk); dfree(m); dfree(v); }
+  uint32_t* f8_amax = nullptr;  // calibrated activation ranges (float bits) per layer, FP8 scales
+  ~DevNet() { dfree(p32); dfree(wpk); dfree(m); dfree(v); dfree(f8_amax); }
 };
 
 struct PatchSet {
@@ -412,10 +415,10 @@ nvdb_status launch_tc(const EvalBatch& b, int64_t ntiles, const char* base, cuda
   return NVDB_OK;
 }
 
-// Precisions are 0 .. kNumPrecisions-1 (FP8 is reserved).
+// Precisions are 0 .. kNumPrecisions-1.
 constexpr int kNumPrecisions = 5;
 bool eval_prec_ok(int prec) {
-  return prec == NVDB_FP32 || prec == NVDB_BF16 || prec == NVDB_FP16 || prec == NVDB_BF16X3;
+  return prec == NVDB_FP32 || prec == NVDB_BF16 || prec == NVDB_FP16 || prec == NVDB_BF16X3 || prec == NVDB_FP8_E4M3;
 }
 
 template <int NIN, int W>
@@ -433,6 +436,8 @@ nvdb_status launch_eval_t(const EvalBatch& b, int64_t ntiles, nvdb_precision pre
     TRY((launch_tc<NIN, W, TC_BF16X3>(b, ntiles, "mlp_bf16x3", s)));
   } else if (prec == NVDB_FP16) {
     TRY((launch_tc<NIN, W, TC_FP16>(b, ntiles, "mlp_f16", s)));
+  } else if (prec == NVDB_FP8_E4M3) {
+    TRY((launch_tc<NIN, W, TC_FP8>(b, ntiles, "mlp_fp8", s)));
   } else {
     return fail(NVDB_ERR_UNSUPPORTED, "precision %d not implemented", (int)prec);
   }
@@ -580,6 +585,19 @@ nvdb_status pack_net(nvdb_model* m, int k, cudaStream_t s) {
     KLAUNCH("pack_weights_t", s, pack_weights_t_kernel<<<16, 256, 0, s>>>(d.p32, d.wpk, d.n_in, d.width, d.layers));
     CU(cudaGetLastError());
   }
+  // FP8 activation scales: calibrate on seeded points of the network's domain, then pack
+  if (!d.f8_amax) TRY(dalloc(&d.f8_amax, kMaxLayers));
+  CU(cudaMemsetAsync(d.f8_amax, 0, kMaxLayers * 4, s));
+  const NetView nv = net_view(m, k);
+  const int lg = k == 0 ? m->log2e - 3 : m->log2e;   // the level-1 classifier works in leaf units
+  constexpr int kCalibPoints = 1 << 15;
+  if (nv.n_in == 32 && nv.width == 32) KLAUNCH("calib_amax", s, calib_amax_kernel<32, 32><<<64, 128, 0, s>>>(nv, lg, 0xF8CA11Bull, kCalibPoints, d.f8_amax));
+  else if (nv.n_in == 32 && nv.width == 64) KLAUNCH("calib_amax", s, calib_amax_kernel<32, 64><<<64, 128, 0, s>>>(nv, lg, 0xF8CA11Bull, kCalibPoints, d.f8_amax));
+  else if (nv.n_in == 64 && nv.width == 32) KLAUNCH("calib_amax", s, calib_amax_kernel<64, 32><<<64, 128, 0, s>>>(nv, lg, 0xF8CA11Bull, kCalibPoints, d.f8_amax));
+  else if (nv.n_in == 64 && nv.width == 64) KLAUNCH("calib_amax", s, calib_amax_kernel<64, 64><<<64, 128, 0, s>>>(nv, lg, 0xF8CA11Bull, kCalibPoints, d.f8_amax));
+  CU(cudaGetLastError());
+  KLAUNCH("pack_fp8", s, pack_fp8_kernel<<<1, 256, 0, s>>>(d.p32, d.wpk, d.n_in, d.width, d.layers, d.f8_amax));
+  CU(cudaGetLastError());
   return NVDB_OK;
 }
 
@@ -747,7 +765,7 @@ extern "C" void nvdb_train_opts_default(nvdb_train_opts* o) {
   o->lr_interval = 100;
   o->loss = NVDB_LOSS_MSE;
   o->train_prec = NVDB_FP32;
-  o->patch_precs = (1u << NVDB_FP32) | (1u << NVDB_BF16) | (1u << NVDB_FP16) | (1u << NVDB_BF16X3);
+  o->patch_precs = (1u << kNumPrecisions) - 1u;   // every precision
   o->stop_window = 50;
 }
 
@@ -832,6 +850,7 @@ extern "C" nvdb_status nvdb_compress(const nvdb_grid* g, const nvdb_train_opts* 
   if (o->steps < 0 || o->batch <= 0 || !(o->lr >= 0.f) || o->lr_interval < 0)
     return fail(NVDB_ERR_INVALID_ARG, "nvdb_compress: bad steps/batch/lr");
   if (o->loss != NVDB_LOSS_MSE && o->loss != NVDB_LOSS_L1) return fail(NVDB_ERR_INVALID_ARG, "loss must be MSE or L1");
+  if (o->patch_precs >> kNumPrecisions) return fail(NVDB_ERR_INVALID_ARG, "patch_precs: no precision %u", o->patch_precs);
   if (!train_prec_ok(o->train_prec)) return fail(NVDB_ERR_UNSUPPORTED, "training precision %d", o->train_prec);
   if (g->n == 0) return fail(NVDB_ERR_INVALID_ARG, "nvdb_compress: empty grid");
   if ((uint64_t)g->n_leaf * 512 >= (1ull << 32) || (uint64_t)g->n_l1 * 4096 >= (1ull << 32))
@@ -1002,7 +1021,6 @@ extern "C" nvdb_status nvdb_compress(const nvdb_grid* g, const nvdb_train_opts* 
     uint32_t pp = o->patch_precs ? o->patch_precs : (1u << NVDB_FP32);
     for (int p = 0; p < kNumPrecisions; ++p)
       if (pp & (1u << p)) {
-        if (p == NVDB_FP8_E4M3) return fail(NVDB_ERR_UNSUPPORTED, "FP8 patches not implemented");
         TRY(make_patches(m, g, p, s));
       }
     uint32_t hst = 0;
@@ -1418,7 +1436,7 @@ extern "C" nvdb_status nvdb_model_import(const void* buf, size_t bytes, nvdb_str
   Reader r{static_cast<const uint8_t*>(buf), bytes};
   const BlobHeader* h = static_cast<const BlobHeader*>(r.take(sizeof(BlobHeader)));
   if (!h || std::memcmp(h->magic, "NVDBMDL1", 8) != 0 || h->version != 1) return fail(NVDB_ERR_CORRUPT, "not an NVDBMDL1 blob");
-  if (h->n_l2 < 0 || h->n_l1 < 0 || h->n_leaf < 0 || h->n_active < 0 || h->n_patch_sets < 0 || h->n_patch_sets > 4 ||
+  if (h->n_l2 < 0 || h->n_l1 < 0 || h->n_leaf < 0 || h->n_active < 0 || h->n_patch_sets < 0 || h->n_patch_sets > kNumPrecisions ||
       h->grid_class > 1 || h->log2_extent < 0 || h->log2_extent > 21)
     return fail(NVDB_ERR_CORRUPT, "bad blob header");
   auto* m = new nvdb_model();
@@ -1475,6 +1493,8 @@ extern "C" nvdb_status nvdb_model_import(const void* buf, size_t bytes, nvdb_str
       if (!ph) return fail(NVDB_ERR_CORRUPT, "blob truncated (patch header)");
       PatchSet ps;
       ps.prec = ph[0];
+      if (!eval_prec_ok(ps.prec) || m->patch_set((nvdb_precision)ps.prec))
+        return fail(NVDB_ERR_CORRUPT, "patch set %d: bad or repeated precision %d", i, ps.prec);
       const uint32_t* o1 = static_cast<const uint32_t*>(r.take((size_t)(m->n_l1 + 1) * 4));
       r.pad();
       if (!o1) return fail(NVDB_ERR_CORRUPT, "blob truncated (patches)");

@@ -239,12 +239,6 @@ __global__ void __launch_bounds__(kTile, 1) train_fwd_bwd_kernel(NetView net, Tr
   }
 }
 
-// Transposed hidden-layer tiles W_l^T, l = 1..L-1: [W (in) x W (out)] BF16,
-// canonical K-major over `out`; stored after the three forward tile copies.
-__host__ __device__ inline int64_t wtile_t_elems(int w, int L) { return (int64_t)(L - 1) * w * w; }
-__host__ __device__ inline int64_t wpk_bytes(int nin, int w, int L) {
-  return wtile_elems(nin, w, L) * 6 + wtile_t_elems(w, L) * 2;
-}
 
 // Byte offsets, inside the packed buffer, of the BF16 copies of parameter e that the
 // training kernel reads: `fo` in the BF16 forward tile (layer-0 columns interleaved

@@ -31,8 +31,9 @@ def randomise_biases(model: dict, seed: int, s: float = 0.1):
 # (absolute for fog densities).  FP16 (11 significant bits) and compensated BF16 (hi + lo
 # pairs, ~16 bits) meet the 2e-2 target.  Plain BF16 (8 significant bits per activation)
 # does not: its measured error on the test and bench models is 2.3e-2 to 2.5e-2 of the
-# half-width, so it is held to 5e-2 and its error is reported next to the others.
-TC_BARS = {1: 5e-2, 3: 2e-2, 4: 2e-2}
+# half-width, so it is held to 5e-2 and its error is reported next to the others.  FP8
+# (E4M3 hidden layers, 4 significant bits) is coarser again: held to the half-width.
+TC_BARS = {1: 5e-2, 2: 1.0, 3: 2e-2, 4: 2e-2}
 
 
 def tc_bar(prec: int) -> float:

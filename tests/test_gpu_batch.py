@@ -29,7 +29,7 @@ def models():
     return ms, other
 
 
-@pytest.mark.parametrize("prec", [0, 1, 3, 4])
+@pytest.mark.parametrize("prec", [0, 1, 2, 3, 4])
 def test_batched_equals_single(models, prec):
     ms, other = models
     singles = [nv.decompress(m, prec) for m in ms + [other]]

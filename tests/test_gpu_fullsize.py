@@ -23,11 +23,11 @@ def union1024():
     info = g.info()
     m = nv.compress(g, seed=1, width=[64, 64, 64], layers=[4, 4, 4], ffm_size=[64, 64],
                     ffm_sigma=10.0 * (1 << info["log2_extent"]) / 1024.0, steps=200, batch=65536,
-                    patch_precs=0b11011)
+                    patch_precs=0b11111)
     return g, m, g.read()
 
 
-@pytest.mark.parametrize("prec", [0, 1, 3, 4])
+@pytest.mark.parametrize("prec", [0, 1, 2, 3, 4])
 def test_full_decode_topology_and_sampled_values(union1024, prec):
     g, m, ref = union1024
     om = blob.read(m.export())
