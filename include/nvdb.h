@@ -69,7 +69,9 @@ typedef enum {
 /* Network indices (Section 3.3.1). */
 enum { NVDB_NET_L1_CLASSIFIER = 0, NVDB_NET_L0_CLASSIFIER = 1, NVDB_NET_REGRESSOR = 2 };
 /* Losses (Eq. 1 is MSE; BCE is used for the classifiers, Section 3.3.1). */
-enum { NVDB_LOSS_MSE = 0, NVDB_LOSS_L1 = 1, NVDB_LOSS_BCE = 2 };
+enum { NVDB_LOSS_MSE = 0, NVDB_LOSS_L1 = 1, NVDB_LOSS_BCE = 2,
+       NVDB_LOSS_LINEAR = 3 /* nvdb_mlp_grad only: d_target holds dL/dy per sample; the gradient is
+                               sum_s target_s dy_s/dtheta (a vector-Jacobian product) */ };
 
 typedef struct nvdb_grid nvdb_grid;    /* explicit [Hash,5,4,3] tree, device resident */
 typedef struct nvdb_model nvdb_model;  /* [Hash,5,NN(4),NN(3)]: upper tree + 3 networks + patches */
@@ -237,6 +239,20 @@ nvdb_status nvdb_mlp_grad_static(const nvdb_model* model, int net, const int32_t
                                  int64_t n, int loss_kind, float* d_grad, float* loss, nvdb_stream stream);
 
 int64_t nvdb_net_param_count(const nvdb_model* model, int net);
+
+/* Copy network `net`'s flat FP32 parameters (nvdb_net_param_count floats, storage order
+ * as for nvdb_mlp_grad) to / from DEVICE memory.  Stream-ordered, no synchronisation.
+ * Setting them (training the networks with an optimiser of the caller's, Section 3.2)
+ * repacks the tensor-core weight tiles and drops the model's patch sets and its query
+ * topology, which belonged to the old weights: until nvdb_model_repatch, decompress
+ * and query return NVDB_ERR_UNSUPPORTED; mlp_eval and mlp_grad work. */
+nvdb_status nvdb_net_params(const nvdb_model* model, int net, float* d_out, nvdb_stream stream);
+nvdb_status nvdb_net_set_params(nvdb_model* model, int net, const float* d_in, nvdb_stream stream);
+
+/* Recompute the patch sets (Section 3.3.2) of the model's current networks against the
+ * grid it encodes (same node counts, voxel count and domain; else INVALID_ARG): one set
+ * per bit of patch_precs, as nvdb_compress does.  Synchronises the stream. */
+nvdb_status nvdb_model_repatch(nvdb_model* model, const nvdb_grid* grid, uint32_t patch_precs, nvdb_stream stream);
 
 nvdb_status nvdb_model_info(const nvdb_model* model, nvdb_info* out);
 

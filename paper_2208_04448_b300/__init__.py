@@ -12,7 +12,8 @@ import ctypes as C
 import torch
 
 from . import _native as N
-from ._native import (BF16, BF16X3, FP16, FP32, FP8_E4M3, LOSS_BCE, LOSS_L1, LOSS_MSE, NET_L0_CLASSIFIER,  # noqa: F401
+from ._native import (BF16, BF16X3, FP16, FP32, FP8_E4M3, LOSS_BCE, LOSS_L1, LOSS_LINEAR, LOSS_MSE,  # noqa: F401
+                      NET_L0_CLASSIFIER,
                       NET_L1_CLASSIFIER, NET_REGRESSOR)
 
 _lib = None
@@ -108,6 +109,22 @@ class Model:
 
     def param_count(self, net: int) -> int:
         return int(lib().nvdb_net_param_count(self._h, net))
+
+    def params(self, net: int, stream=None) -> torch.Tensor:
+        """Flat FP32 parameters of network `net` (a copy on the device, storage order)."""
+        out = torch.empty(self.param_count(net), dtype=torch.float32, device="cuda")
+        _check(lib().nvdb_net_params(self._h, net, _dptr(out, torch.float32, "params"), _stream(stream)))
+        return out
+
+    def set_params(self, net: int, params: torch.Tensor, stream=None):
+        """Replace network `net`'s parameters (drops the patch sets until repatch)."""
+        if params.numel() != self.param_count(net):
+            raise ValueError(f"network {net} has {self.param_count(net)} parameters, got {params.numel()}")
+        _check(lib().nvdb_net_set_params(self._h, net, _dptr(params, torch.float32, "params"), _stream(stream)))
+
+    def repatch(self, grid: "Grid", patch_precs: int = 0b11111, stream=None):
+        """Patch sets of the current networks against the grid the model encodes."""
+        _check(lib().nvdb_model_repatch(self._h, grid.handle, patch_precs, _stream(stream)))
 
     def export(self) -> bytes:
         n = C.c_size_t()
@@ -245,6 +262,35 @@ def mlp_grad_static(model: Model, net: int, ijk: torch.Tensor, target: torch.Ten
                                       _dptr(target, torch.float32, "target"), ijk.shape[0], loss,
                                       _dptr(g, torch.float32, "grad"), C.byref(lv), _stream(stream)))
     return g, lv.value
+
+
+class NetworkFunction(torch.autograd.Function):
+    """y = network `net` of `model` at voxel coordinates ijk (int32 [n, 3]; leaf units for
+    the level-1 classifier as in mlp_eval), differentiable in the network's flat FP32
+    parameters.  Forward: the parameters go into the model, then the network kernel
+    (nvdb_mlp_eval).  Backward: the hand-written gradient kernel with the upstream dL/dy as
+    its linear loss (nvdb_mlp_grad, NVDB_LOSS_LINEAR), in the arithmetic of `prec` (FP32, or
+    BF16 on the tensor cores).  Coordinates get no gradient."""
+
+    @staticmethod
+    def forward(ctx, params: torch.Tensor, model: Model, net: int, ijk: torch.Tensor, prec: int = FP32):
+        if prec not in (FP32, BF16):
+            raise ValueError("NetworkFunction: precision FP32 or BF16")
+        model.set_params(net, params.detach().contiguous())
+        ctx.model, ctx.net, ctx.prec = model, net, prec
+        ctx.save_for_backward(ijk)
+        return mlp_eval(model, net, ijk, prec)
+
+    @staticmethod
+    def backward(ctx, grad_y: torch.Tensor):
+        (ijk,) = ctx.saved_tensors
+        g, _ = mlp_grad(ctx.model, ctx.net, ijk, grad_y.detach().float().contiguous(), LOSS_LINEAR, ctx.prec)
+        return g, None, None, None, None
+
+
+def network(params: torch.Tensor, model: Model, net: int, ijk: torch.Tensor, prec: int = FP32) -> torch.Tensor:
+    """NetworkFunction.apply: network `net` as a differentiable function of `params`."""
+    return NetworkFunction.apply(params, model, net, ijk, prec)
 
 
 def model_import(blob: bytes, stream=None) -> Model:

@@ -1300,7 +1300,7 @@ extern "C" nvdb_status nvdb_mlp_grad(const nvdb_model* cm, int net, nvdb_precisi
   if (!cm || net < 0 || net > 2 || n <= 0 || !d_ijk || !d_target || !d_grad)
     return fail(NVDB_ERR_INVALID_ARG, "nvdb_mlp_grad: bad arguments");
   if (!train_prec_ok(prec)) return fail(NVDB_ERR_UNSUPPORTED, "nvdb_mlp_grad: precision %d", (int)prec);
-  if (loss_kind < 0 || loss_kind > 2) return fail(NVDB_ERR_INVALID_ARG, "unknown loss %d", loss_kind);
+  if (loss_kind < 0 || loss_kind > 3) return fail(NVDB_ERR_INVALID_ARG, "unknown loss %d", loss_kind);
   if (n > (1ll << 31)) return fail(NVDB_ERR_UNSUPPORTED, "nvdb_mlp_grad: n >= 2^31");
   nvdb_model* m = const_cast<nvdb_model*>(cm);
   cudaStream_t s = (cudaStream_t)stream;
@@ -1333,6 +1333,43 @@ extern "C" nvdb_status nvdb_mlp_grad(const nvdb_model* cm, int net, nvdb_precisi
   }
   if (loss) *loss = h;
   return NVDB_OK;
+}
+
+// ============================================================================ parameters (autograd)
+extern "C" nvdb_status nvdb_net_params(const nvdb_model* m, int net, float* d_out, nvdb_stream stream) {
+  if (!m || net < 0 || net > 2 || !d_out) return fail(NVDB_ERR_INVALID_ARG, "nvdb_net_params: bad arguments");
+  const DevNet& d = m->net[net];
+  CU(cudaMemcpyAsync(d_out, d.p32, d.P * 4, cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+  return NVDB_OK;
+}
+
+extern "C" nvdb_status nvdb_net_set_params(nvdb_model* m, int net, const float* d_in, nvdb_stream stream) {
+  if (!m || net < 0 || net > 2 || !d_in) return fail(NVDB_ERR_INVALID_ARG, "nvdb_net_set_params: bad arguments");
+  cudaStream_t s = (cudaStream_t)stream;
+  DevNet& d = m->net[net];
+  CU(cudaMemcpyAsync(d.p32, d_in, d.P * 4, cudaMemcpyDeviceToDevice, s));
+  d.bf16_exact = false;
+  TRY(pack_net(m, net, s));
+  // the patches and the decoded topology belonged to the old weights
+  for (auto& p : m->patches) p.release();
+  m->patches.clear();
+  m->qc.release();
+  return NVDB_OK;
+}
+
+extern "C" nvdb_status nvdb_model_repatch(nvdb_model* m, const nvdb_grid* g, uint32_t patch_precs, nvdb_stream stream) {
+  if (!m || !g) return fail(NVDB_ERR_INVALID_ARG, "nvdb_model_repatch: NULL argument");
+  if (patch_precs >> kNumPrecisions) return fail(NVDB_ERR_INVALID_ARG, "patch_precs: no precision %u", patch_precs);
+  if (g->n_l1 != m->n_l1 || g->n_leaf != m->n_leaf || g->n != m->n_active || g->log2e != m->log2e ||
+      g->origin[0] != m->origin[0] || g->origin[1] != m->origin[1] || g->origin[2] != m->origin[2])
+    return fail(NVDB_ERR_INVALID_ARG, "nvdb_model_repatch: the grid is not the one the model encodes");
+  cudaStream_t s = (cudaStream_t)stream;
+  m->qc.release();
+  for (int p = 0; p < kNumPrecisions; ++p)
+    if (patch_precs & (1u << p)) TRY(make_patches(m, g, p, s));
+  uint32_t hst = 0;
+  TRY(read_status(m->status, s, &hst));
+  return status_to_error(hst);
 }
 
 // ============================================================================ info / export / import
@@ -1599,7 +1636,7 @@ extern "C" nvdb_status nvdb_mlp_grad_static(const nvdb_model* m, int net, const 
                                             int64_t n, int loss_kind, float* d_grad, float* loss, nvdb_stream stream) {
   if (!m || net < 0 || net > 2 || n <= 0 || !d_ijk || !d_target || !d_grad)
     return fail(NVDB_ERR_INVALID_ARG, "nvdb_mlp_grad_static: bad arguments");
-  if (loss_kind < 0 || loss_kind > 2) return fail(NVDB_ERR_INVALID_ARG, "unknown loss %d", loss_kind);
+  if (loss_kind < 0 || loss_kind > 3) return fail(NVDB_ERR_INVALID_ARG, "unknown loss %d", loss_kind);
   if (n > (1ll << 31)) return fail(NVDB_ERR_UNSUPPORTED, "nvdb_mlp_grad_static: n >= 2^31");
   const DevNet& d = m->net[net];
   // one CTA needs P + 1 floats of partials, plus one float for the loss

@@ -42,7 +42,9 @@ __device__ __forceinline__ void take_step(TrainJob& job) {
   if (blockIdx.x == 0 && threadIdx.x == 0) job.step_dev[1] = job.step;
 }
 
-enum : int { LOSS_MSE = 0, LOSS_L1 = 1, LOSS_BCE = 2 };
+// LOSS_LINEAR: the target is the caller's dL/dy per sample (a vector-Jacobian product,
+// as an autograd backward needs): loss term t y, gradient t, no 1/batch factor.
+enum : int { LOSS_MSE = 0, LOSS_L1 = 1, LOSS_BCE = 2, LOSS_LINEAR = 3 };
 
 __device__ __forceinline__ int64_t train_population(const TrainJob& j) {
   return j.net == 0 ? j.n_l1 * 4096 : j.net == 1 ? j.n_leaf * 512 : j.n;
@@ -92,10 +94,13 @@ __device__ __forceinline__ void row_loss(int kind, float y, float t, float inv_b
     const float d = y - t;
     l = d * d;
     g = 2.f * d * inv_b;
-  } else {
+  } else if (kind == LOSS_L1) {
     const float d = y - t;
     l = fabsf(d);
     g = (d > 0.f ? 1.f : d < 0.f ? -1.f : 0.f) * inv_b;
+  } else {   // LOSS_LINEAR
+    l = y * t;
+    g = t;
   }
 }
 

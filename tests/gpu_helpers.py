@@ -38,3 +38,18 @@ TC_BARS = {1: 5e-2, 2: 1.0, 3: 2e-2, 4: 2e-2}
 
 def tc_bar(prec: int) -> float:
     return TC_BARS[prec]
+
+
+def round_bf16(a):
+    """Round to the nearest BF16 value (ties to even), returned as float64."""
+    u = np.asarray(a, np.float32).copy().view(np.uint32).astype(np.uint64)
+    u = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def bf16_weight_sensitivity(net: dict, z: np.ndarray, gy_of) -> np.ndarray:
+    """FP64 gradient of the network with its weights and biases rounded to BF16 (the head
+    kept): how far one BF16 rounding moves the gradient.  gy_of(y) -> dL/dy."""
+    pb = dict(W=[round_bf16(W) for W in net["W"]], b=[round_bf16(b) for b in net["b"]], wh=net["wh"], bh=net["bh"])
+    y, cache = N.forward(pb, z)
+    return N.flatten(N.backward(pb, cache, gy_of(y)))

@@ -13,7 +13,7 @@ import torch
 
 import paper_2208_04448_b300 as nv
 from fixtures import query_points, workload
-from gpu_helpers import oracle_forward_scale, randomise_biases, rel_err, tc_bar
+from gpu_helpers import bf16_weight_sensitivity, oracle_forward_scale, randomise_biases, rel_err, round_bf16, tc_bar
 from oracle import blob, codec, vdb
 from oracle import nets as N
 
@@ -181,9 +181,8 @@ def test_gradient_parity(sphere128, net, loss, n, prec):
     else:
         assert abs(lgot - lref) <= BF16_LOSS_TOL * max(1.0, abs(lref))
         p = om["nets"][net]
-        pb = dict(W=[_round_bf16(W) for W in p["W"]], b=[_round_bf16(b) for b in p["b"]], wh=p["wh"], bh=p["bh"])
-        yb, cb = N.forward(pb, N.encode(codec.level_coords(om, net, pts), codec.level_q(om, net)))
-        gsens = N.flatten(N.backward(pb, cb, N.loss_and_grad(yb, tgt.astype(np.float64), loss)[1]))
+        gsens = bf16_weight_sensitivity(p, N.encode(codec.level_coords(om, net, pts), codec.level_q(om, net)),
+                                        lambda yb: N.loss_and_grad(yb, tgt.astype(np.float64), loss)[1])
         sizes = [x for W, b in zip(p["W"], p["b"]) for x in (np.size(W), np.size(b))] + [np.size(p["wh"]), 1]
         o = 0
         for sz in sizes:   # blocks W_0, b_0, ..., W_{L-1}, b_{L-1}, w_h, b_h
@@ -193,13 +192,6 @@ def test_gradient_parity(sphere128, net, loss, n, prec):
             assert np.linalg.norm(a - b) / nb <= BF16_GRAD_K * sens + BF16_U, (o, sz, sens)
             o += sz
         assert o == g.size
-
-
-def _round_bf16(a):
-    """Round to the nearest BF16 value (ties to even), returned as float64."""
-    u = np.asarray(a, np.float32).copy().view(np.uint32).astype(np.uint64)
-    u = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
-    return u.astype(np.uint32).view(np.float32).astype(np.float64)
 
 
 def test_gradient_precision_errors(sphere128):
@@ -260,7 +252,7 @@ def test_bf16_training_tracks_fp32(sphere128):
     for k in range(3):   # the BF16 step stores BF16 weights and biases (the head stays FP32)
         net = om["nets"][k]
         for a in list(net["W"]) + list(net["b"]):
-            assert np.array_equal(_round_bf16(a), np.asarray(a, np.float64))
+            assert np.array_equal(round_bf16(a), np.asarray(a, np.float64))
     want, scale = oracle_forward_scale(om, 2, ref["ijk"])
     for prec in (0, 1, 3, 4):   # BF16 decode of BF16 weights: two MMAs per K-step (no weight residual)
         dijk, dval, cnt = nv.decompress(m16, prec)
