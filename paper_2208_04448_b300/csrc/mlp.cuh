@@ -334,18 +334,19 @@ __device__ __forceinline__ void tmem_st_cols(uint32_t taddr, const uint32_t* r) 
   else tmem_st8(taddr, r);
 }
 
-// Write one row of the A operand: NK 16-bit values (as NK/2 packed columns) plus the
-// 8-column constant chunk (1, 0, ..., 0) that multiplies the bias column.
-template <int NK, int MODE>
+// Write one row of the A operand: NK 16-bit values (as NK/2 packed columns) plus, unless
+// CST is false (it is already in place), the 8-column constant chunk (1, 0, ..., 0) that
+// multiplies the bias column.
+template <int NK, int MODE, bool CST = true>
 __device__ __forceinline__ void store_a_row(uint32_t tlane, const uint32_t* hi, const uint32_t* lo) {
   using C = TcCfg<32, 32, MODE>;
   tmem_st_cols<NK / 2>(tlane + C::A_HI, hi);
   uint32_t cst[8] = {Enc16<MODE>::value ? 0x3C00u : 0x3F80u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
-  tmem_st8(tlane + C::A_HI + NK / 2, cst);
+  if (CST) tmem_st8(tlane + C::A_HI + NK / 2, cst);
   if (MODE == TC_BF16X3) {
     tmem_st_cols<NK / 2>(tlane + C::A_LO, lo);
     cst[0] = 0u;
-    tmem_st8(tlane + C::A_LO + NK / 2, cst);
+    if (CST) tmem_st8(tlane + C::A_LO + NK / 2, cst);
   }
 }
 
@@ -596,17 +597,24 @@ __global__ void __launch_bounds__(kTile, MODE == TC_BF16X3 ? 1 : 4) mlp_tc_kerne
 #pragma unroll
         for (int p = 0; p < W / 2; ++p)
           relu_pair<MODE>(__uint_as_float(accu[2 * p]), __uint_as_float(accu[2 * p + 1]), hi[p], lo[p]);
-        store_a_row<W, MODE>(tlane, hi, lo);
+        // equal widths: the constant chunk the tile's encoding wrote is still in place
+        store_a_row<W, MODE, NIN != W>(tlane, hi, lo);
         tmem_st_wait();
       } else {
-        // FP32 head, two products per instruction
-        const float2* swh2 = reinterpret_cast<const float2*>(swh);
-        float2 acc = make_float2(0.f, 0.f);
+        // FP32 head, two products per instruction, four independent partial sums
+        const float4* swh4 = reinterpret_cast<const float4*>(swh);
+        float2 acc[4] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
 #pragma unroll
-        for (int c = 0; c < W / 2; ++c)
-          acc = ffma2(swh2[c], make_float2(fmaxf(__uint_as_float(accu[2 * c]), 0.f), fmaxf(__uint_as_float(accu[2 * c + 1]), 0.f)),
-                      acc);
-        y = bh + (acc.x + acc.y);
+        for (int c = 0; c < W / 4; ++c) {
+          const float4 wv = swh4[c];
+          acc[(2 * c) & 3] = ffma2(make_float2(wv.x, wv.y),
+                                   make_float2(fmaxf(__uint_as_float(accu[4 * c]), 0.f), fmaxf(__uint_as_float(accu[4 * c + 1]), 0.f)),
+                                   acc[(2 * c) & 3]);
+          acc[(2 * c + 1) & 3] = ffma2(make_float2(wv.z, wv.w),
+                                       make_float2(fmaxf(__uint_as_float(accu[4 * c + 2]), 0.f), fmaxf(__uint_as_float(accu[4 * c + 3]), 0.f)),
+                                       acc[(2 * c + 1) & 3]);
+        }
+        y = bh + (((acc[0].x + acc[0].y) + (acc[1].x + acc[1].y)) + ((acc[2].x + acc[2].y) + (acc[3].x + acc[3].y)));
       }
       tc_fence_before();
       if (__syncthreads_or(!ok)) { failed = true; break; }   // all threads agree on a timeout
