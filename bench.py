@@ -46,6 +46,17 @@ NET_WIDTH, NET_LAYERS, FFM = [64, 64, 64], [4, 4, 4], [64, 64]
 TRAIN_KERNELS = ("train_fwd_bwd", "train_tc_bf16", "adam_reduce")
 
 
+def aggregate_replicas(local_ms: float, units_per_rank: int, dist=None, device="cpu"):
+    """Replicas (one process per GPU, the same work on each): the step time is the maximum
+    over ranks and the value counts every rank's units -> (max ms per step, units/s)."""
+    ms, world = local_ms, 1
+    if dist is not None:
+        t = torch.tensor([local_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms, world = float(t.item()), dist.get_world_size()
+    return ms, world * units_per_rank / (ms / 1e3)
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -395,6 +406,8 @@ def main():
             if p == head_prec:
                 head_ms, head_launches, head_kern = ms, launches, kern
     torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
     for name, p in PRECS.items():
         by_prec[name]["max_abs_err_vs_oracle"] = decode_error(p)
         by_prec[name]["err_bound"] = 0.02 * 3.0
@@ -416,12 +429,7 @@ def main():
         b.synchronize()
         query[name] = dict(points_per_s=5 * qpts.shape[0] / (a.elapsed_time(b) / 1e3))
 
-    mean_ms = float(np.mean(head_ms))
-    if dist is not None:
-        t = torch.tensor([mean_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        mean_ms = float(t.item())
-    value = world * n_active / (mean_ms / 1e3)
+    mean_ms, value = aggregate_replicas(float(np.mean(head_ms)), n_active, dist, "cuda")
 
     # ---- roofline of the dominant network kernel (live CUDA events on the launching stream)
     peaks = measured_peaks()
