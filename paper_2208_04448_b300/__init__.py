@@ -293,10 +293,17 @@ def network(params: torch.Tensor, model: Model, net: int, ijk: torch.Tensor, pre
     return NetworkFunction.apply(params, model, net, ijk, prec)
 
 
-def model_import(blob: bytes, stream=None) -> Model:
+def model_import(blob, stream=None) -> Model:
+    """nvdb_model_import from `bytes` or from a contiguous uint8 CPU tensor (pass a pinned
+    one to make the host-to-device copies direct); the buffer is read, not copied first."""
     h = C.c_void_p()
-    buf = C.create_string_buffer(blob, len(blob))
-    _check(lib().nvdb_model_import(buf, len(blob), _stream(stream), C.byref(h)))
+    if isinstance(blob, torch.Tensor):
+        if blob.device.type != "cpu" or blob.dtype != torch.uint8 or not blob.is_contiguous():
+            raise ValueError("model_import: a contiguous uint8 CPU tensor")
+        ptr, n = C.c_void_p(blob.data_ptr()), blob.numel()
+    else:
+        ptr, n = bytes(blob), len(blob)
+    _check(lib().nvdb_model_import(ptr, n, _stream(stream), C.byref(h)))
     return Model(h)
 
 

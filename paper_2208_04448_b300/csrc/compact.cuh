@@ -86,6 +86,19 @@ __global__ void scan_add_kernel(int64_t* out, int64_t n, const int64_t* sums) {
   if (i < n) out[i] += sums[i / kScanBlock];
 }
 
+// Validate an imported patch list: offsets off[0..items] start at 0, never decrease and
+// end at n; every index is below `bound` (candidates per item).  Any violation sets
+// ST_CORRUPT; the model is not returned then, so no decode reads the lists.
+__global__ void check_patches_kernel(const uint32_t* off, int64_t items, const uint16_t* idx, int64_t n,
+                                     uint32_t bound, uint32_t* status) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  bool bad = false;
+  if (i < items) bad = off[i] > off[i + 1];
+  if (i == 0) bad = bad || off[0] != 0u || (int64_t)off[items] != n;
+  for (int64_t j = i; j < n; j += (int64_t)gridDim.x * blockDim.x) bad = bad || idx[j] >= bound;
+  if (bad) set_status(status, ST_CORRUPT);
+}
+
 // Apply the patch list of every item (XOR, Section 3.3.2) to its candidate
 // words and count the resulting set bits.  One thread per item.
 __global__ void patch_count_kernel(uint32_t* words, int wpi, int64_t n_items, const uint32_t* poff,

@@ -271,10 +271,11 @@ struct DevNet {
   ~DevNet() { dfree(p32); dfree(wpk); dfree(m); dfree(v); dfree(f8_amax); }
 };
 
+// Patch lists of one precision (Section 3.3.2), on the device only: CSR offsets per
+// level-1 node / leaf and 16-bit candidate indices; n1, n0 = number of patches.
 struct PatchSet {
   int prec = 0;
-  std::vector<uint32_t> l1_off, l0_off;
-  std::vector<uint16_t> l1_idx, l0_idx;
+  int64_t n1 = 0, n0 = 0;
   uint32_t* d_l1_off = nullptr;
   uint32_t* d_l0_off = nullptr;
   uint16_t* d_l1_idx = nullptr;
@@ -601,18 +602,6 @@ nvdb_status pack_net(nvdb_model* m, int k, cudaStream_t s) {
   return NVDB_OK;
 }
 
-nvdb_status upload_patch_set(PatchSet& p) {
-  TRY(dalloc(&p.d_l1_off, p.l1_off.size()));
-  TRY(dalloc(&p.d_l0_off, p.l0_off.size()));
-  TRY(dalloc(&p.d_l1_idx, p.l1_idx.size() + 1));
-  TRY(dalloc(&p.d_l0_idx, p.l0_idx.size() + 1));
-  CU(cudaMemcpy(p.d_l1_off, p.l1_off.data(), p.l1_off.size() * 4, cudaMemcpyHostToDevice));
-  CU(cudaMemcpy(p.d_l0_off, p.l0_off.data(), p.l0_off.size() * 4, cudaMemcpyHostToDevice));
-  if (!p.l1_idx.empty()) CU(cudaMemcpy(p.d_l1_idx, p.l1_idx.data(), p.l1_idx.size() * 2, cudaMemcpyHostToDevice));
-  if (!p.l0_idx.empty()) CU(cudaMemcpy(p.d_l0_idx, p.l0_idx.data(), p.l0_idx.size() * 2, cudaMemcpyHostToDevice));
-  return NVDB_OK;
-}
-
 nvdb_status check_model_shapes(const nvdb_model* m) {
   for (int k = 0; k < 3; ++k) {
     const int nin = k == 0 ? m->ffm[0] : m->ffm[1];
@@ -823,20 +812,21 @@ nvdb_status make_patches(nvdb_model* m, const nvdb_grid* g, int prec, cudaStream
       TRY(dalloc(&idx, (size_t)total + 1));
       if (items) KLAUNCH("emit_patches", s, emit_patches_kernel<<<blocks_for(items, 128), 128, 0, s>>>(words, wpi, items, off, idx));
       CU(cudaGetLastError());
-      std::vector<uint32_t>& ho = lev == 0 ? ps.l1_off : ps.l0_off;
-      std::vector<uint16_t>& hi = lev == 0 ? ps.l1_idx : ps.l0_idx;
-      ho.resize(items + 1);
-      hi.resize(total);
-      CU(cudaMemcpyAsync(ho.data(), off32, (items + 1) * 4, cudaMemcpyDeviceToHost, s));
-      if (total) CU(cudaMemcpyAsync(hi.data(), idx, total * 2, cudaMemcpyDeviceToHost, s));
-      CU(cudaStreamSynchronize(s));
+      // the set keeps the device lists
+      (lev == 0 ? ps.d_l1_off : ps.d_l0_off) = off32;
+      (lev == 0 ? ps.d_l1_idx : ps.d_l0_idx) = idx;
+      (lev == 0 ? ps.n1 : ps.n0) = total;
+      off32 = nullptr;
+      idx = nullptr;
       return NVDB_OK;
     };
     const nvdb_status st = run();
     dfree(words); dfree(counts); dfree(off); dfree(off32); dfree(idx);
-    if (st != NVDB_OK) return st;
+    if (st != NVDB_OK) {
+      ps.release();
+      return st;
+    }
   }
-  TRY(upload_patch_set(ps));
   for (auto& p : m->patches)
     if (p.prec == prec) { p.release(); p = ps; return NVDB_OK; }
   m->patches.push_back(ps);
@@ -1454,10 +1444,17 @@ extern "C" nvdb_status nvdb_model_export(const nvdb_model* m, void* buf, size_t*
   for (const PatchSet* p : sets) {
     const int32_t hdr[2] = {p->prec, 0};
     w.put(hdr, 8);
-    w.put(p->l1_off.data(), p->l1_off.size() * 4); w.pad();
-    w.put(p->l1_idx.data(), p->l1_idx.size() * 2); w.pad();
-    w.put(p->l0_off.data(), p->l0_off.size() * 4); w.pad();
-    w.put(p->l0_idx.data(), p->l0_idx.size() * 2); w.pad();
+    const int64_t nitem[2] = {m->n_l1, m->n_leaf}, npatch[2] = {p->n1, p->n0};
+    const uint32_t* doff[2] = {p->d_l1_off, p->d_l0_off};
+    const uint16_t* didx[2] = {p->d_l1_idx, p->d_l0_idx};
+    for (int lev = 0; lev < 2; ++lev) {
+      std::vector<uint32_t> off((size_t)nitem[lev] + 1);
+      std::vector<uint16_t> idx((size_t)npatch[lev]);
+      CU(cudaMemcpy(off.data(), doff[lev], off.size() * 4, cudaMemcpyDeviceToHost));
+      if (!idx.empty()) CU(cudaMemcpy(idx.data(), didx[lev], idx.size() * 2, cudaMemcpyDeviceToHost));
+      w.put(off.data(), off.size() * 4); w.pad();
+      w.put(idx.data(), idx.size() * 2); w.pad();
+    }
   }
   if (!buf) { *bytes = w.b.size(); return NVDB_OK; }
   if (*bytes < w.b.size()) { *bytes = w.b.size(); return fail(NVDB_ERR_CAPACITY, "nvdb_model_export: buffer too small"); }
@@ -1532,33 +1529,41 @@ extern "C" nvdb_status nvdb_model_import(const void* buf, size_t bytes, nvdb_str
       ps.prec = ph[0];
       if (!eval_prec_ok(ps.prec) || m->patch_set((nvdb_precision)ps.prec))
         return fail(NVDB_ERR_CORRUPT, "patch set %d: bad or repeated precision %d", i, ps.prec);
-      const uint32_t* o1 = static_cast<const uint32_t*>(r.take((size_t)(m->n_l1 + 1) * 4));
-      r.pad();
-      if (!o1) return fail(NVDB_ERR_CORRUPT, "blob truncated (patches)");
-      ps.l1_off.assign(o1, o1 + m->n_l1 + 1);
-      const uint16_t* i1 = static_cast<const uint16_t*>(r.take((size_t)ps.l1_off.back() * 2));
-      r.pad();
-      if (!i1 && ps.l1_off.back()) return fail(NVDB_ERR_CORRUPT, "blob truncated (patches)");
-      if (i1) ps.l1_idx.assign(i1, i1 + ps.l1_off.back());
-      const uint32_t* o0 = static_cast<const uint32_t*>(r.take((size_t)(m->n_leaf + 1) * 4));
-      r.pad();
-      if (!o0) return fail(NVDB_ERR_CORRUPT, "blob truncated (patches)");
-      ps.l0_off.assign(o0, o0 + m->n_leaf + 1);
-      const uint16_t* i0 = static_cast<const uint16_t*>(r.take((size_t)ps.l0_off.back() * 2));
-      r.pad();
-      if (!i0 && ps.l0_off.back()) return fail(NVDB_ERR_CORRUPT, "blob truncated (patches)");
-      if (i0) ps.l0_idx.assign(i0, i0 + ps.l0_off.back());
-      for (size_t a = 0; a + 1 < ps.l1_off.size(); ++a)
-        if (ps.l1_off[a] > ps.l1_off[a + 1]) return fail(NVDB_ERR_CORRUPT, "patch offsets not monotone");
-      for (size_t a = 0; a + 1 < ps.l0_off.size(); ++a)
-        if (ps.l0_off[a] > ps.l0_off[a + 1]) return fail(NVDB_ERR_CORRUPT, "patch offsets not monotone");
-      for (uint16_t v : ps.l1_idx) if (v >= 4096) return fail(NVDB_ERR_CORRUPT, "level-1 patch index out of range");
-      for (uint16_t v : ps.l0_idx) if (v >= 512) return fail(NVDB_ERR_CORRUPT, "level-0 patch index out of range");
-      TRY(upload_patch_set(ps));
+      // both levels: offsets and indices straight from the blob to the device; the
+      // offsets (monotone, from 0 to the patch count) and the index ranges are checked
+      // on the device before the model is returned
+      const int64_t nitem[2] = {m->n_l1, m->n_leaf};
+      for (int lev = 0; lev < 2; ++lev) {
+        const uint32_t* o = static_cast<const uint32_t*>(r.take((size_t)(nitem[lev] + 1) * 4));
+        r.pad();
+        const int64_t n = o ? o[nitem[lev]] : 0;
+        const uint16_t* ix = o ? static_cast<const uint16_t*>(r.take((size_t)n * 2)) : nullptr;
+        r.pad();
+        if (!o || (!ix && n)) {
+          ps.release();
+          return fail(NVDB_ERR_CORRUPT, "blob truncated (patches)");
+        }
+        uint32_t*& doff = lev == 0 ? ps.d_l1_off : ps.d_l0_off;
+        uint16_t*& didx = lev == 0 ? ps.d_l1_idx : ps.d_l0_idx;
+        (lev == 0 ? ps.n1 : ps.n0) = n;
+        nvdb_status ast = dalloc(&doff, (size_t)nitem[lev] + 1);
+        if (ast == NVDB_OK) ast = dalloc(&didx, (size_t)n + 1);
+        if (ast != NVDB_OK) { ps.release(); return ast; }
+        if (cudaMemcpyAsync(doff, o, (nitem[lev] + 1) * 4, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+            (n && cudaMemcpyAsync(didx, ix, n * 2, cudaMemcpyHostToDevice, s) != cudaSuccess)) {
+          ps.release();
+          return fail(NVDB_ERR_CUDA, "patch upload");
+        }
+        const int64_t work = std::max<int64_t>(nitem[lev] + 1, std::min<int64_t>(n, 1 << 22));
+        KLAUNCH("check_patches", s, check_patches_kernel<<<blocks_for(work, 256), 256, 0, s>>>(
+                                        doff, nitem[lev], didx, n, lev == 0 ? 4096u : 512u, m->status));
+      }
       m->patches.push_back(ps);
     }
-    CU(cudaStreamSynchronize(s));
-    return NVDB_OK;
+    uint32_t hst = 0;
+    TRY(read_status(m->status, s, &hst));
+    if (hst & ST_CORRUPT) return fail(NVDB_ERR_CORRUPT, "patch offsets or indices out of range");
+    return status_to_error(hst);
   };
   const nvdb_status st = run();
   if (st != NVDB_OK) { delete m; return st; }

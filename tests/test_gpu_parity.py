@@ -335,6 +335,39 @@ def test_patches_match_oracle_decisions(sphere128):
         assert diff.sum() <= max(2, 1e-4 * len(cand))
 
 
+def test_import_rejects_corrupt_blobs(sphere128):
+    """Blob checks (header on the host; patch offsets and indices on the device): any
+    inconsistency is NVDB_ERR_CORRUPT and no model is returned."""
+    ijk, val, ref = sphere128
+    m = nv.compress(_grid(ijk, val), steps=5, batch=512, patch_precs=0b1001)
+    good = m.export()
+    assert nv.model_import(good).export() == good               # round trip, bit for bit
+    om = blob.read(good)
+    cases = []
+    bad = blob.read(good)
+    bad["patches"][0]["l0_idx"] = bad["patches"][0]["l0_idx"].copy()
+    bad["patches"][0]["l0_idx"][0] = 600                      # index >= 512 candidates of a leaf
+    cases.append(blob.write(bad))
+    bad = blob.read(good)
+    off = bad["patches"][3]["l1_off"].copy()
+    if len(off) > 2 and off[-1] > 0:
+        off[1] = off[-1] + 1                                  # not monotone (and past the list)
+        bad["patches"][3]["l1_off"] = off
+        cases.append(blob.write(bad))
+    bad = blob.read(good)
+    off = bad["patches"][0]["l0_off"].copy()
+    off[0] = 1                                                # does not start at 0
+    bad["patches"][0]["l0_off"] = off
+    cases.append(blob.write(bad))
+    cases.append(good[:len(good) // 2])                       # truncated
+    cases.append(b"NVDBMDL0" + good[8:])                      # wrong magic
+    for c in cases:
+        with pytest.raises(nv.NvdbError) as e:
+            nv.model_import(c)
+        assert e.value.status == 8
+    assert sorted(om["patches"]) == [0, 3]
+
+
 def test_decompress_errors(sphere128):
     ijk, val, ref = sphere128
     m = nv.compress(_grid(ijk, val), steps=5, batch=512, patch_precs=1)
