@@ -591,11 +591,11 @@ nvdb_status pack_net(nvdb_model* m, int k, cudaStream_t s) {
   CU(cudaMemsetAsync(d.f8_amax, 0, kMaxLayers * 4, s));
   const NetView nv = net_view(m, k);
   const int lg = k == 0 ? m->log2e - 3 : m->log2e;   // the level-1 classifier works in leaf units
-  constexpr int kCalibPoints = 1 << 15;
-  if (nv.n_in == 32 && nv.width == 32) KLAUNCH("calib_amax", s, calib_amax_kernel<32, 32><<<64, 128, 0, s>>>(nv, lg, 0xF8CA11Bull, kCalibPoints, d.f8_amax));
-  else if (nv.n_in == 32 && nv.width == 64) KLAUNCH("calib_amax", s, calib_amax_kernel<32, 64><<<64, 128, 0, s>>>(nv, lg, 0xF8CA11Bull, kCalibPoints, d.f8_amax));
-  else if (nv.n_in == 64 && nv.width == 32) KLAUNCH("calib_amax", s, calib_amax_kernel<64, 32><<<64, 128, 0, s>>>(nv, lg, 0xF8CA11Bull, kCalibPoints, d.f8_amax));
-  else if (nv.n_in == 64 && nv.width == 64) KLAUNCH("calib_amax", s, calib_amax_kernel<64, 64><<<64, 128, 0, s>>>(nv, lg, 0xF8CA11Bull, kCalibPoints, d.f8_amax));
+  constexpr int kCalibPoints = 1 << 12;   // one point per thread of 32 blocks
+  if (nv.n_in == 32 && nv.width == 32) KLAUNCH("calib_amax", s, calib_amax_kernel<32, 32><<<kCalibPoints / 128, 128, 0, s>>>(nv, lg, 0xF8CA11Bull, kCalibPoints, d.f8_amax));
+  else if (nv.n_in == 32 && nv.width == 64) KLAUNCH("calib_amax", s, calib_amax_kernel<32, 64><<<kCalibPoints / 128, 128, 0, s>>>(nv, lg, 0xF8CA11Bull, kCalibPoints, d.f8_amax));
+  else if (nv.n_in == 64 && nv.width == 32) KLAUNCH("calib_amax", s, calib_amax_kernel<64, 32><<<kCalibPoints / 128, 128, 0, s>>>(nv, lg, 0xF8CA11Bull, kCalibPoints, d.f8_amax));
+  else if (nv.n_in == 64 && nv.width == 64) KLAUNCH("calib_amax", s, calib_amax_kernel<64, 64><<<kCalibPoints / 128, 128, 0, s>>>(nv, lg, 0xF8CA11Bull, kCalibPoints, d.f8_amax));
   CU(cudaGetLastError());
   KLAUNCH("pack_fp8", s, pack_fp8_kernel<<<1, 256, 0, s>>>(d.p32, d.wpk, d.n_in, d.width, d.layers, d.f8_amax));
   CU(cudaGetLastError());
