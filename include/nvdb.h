@@ -98,6 +98,11 @@ typedef struct {
   int32_t stop_window;  /* early stop (warm-started frames, Section 3.6): every stop_window steps ... */
   float stop_loss[3];   /* ... network k stops once the mean of its last stop_window losses < stop_loss[k];
                            0 = train all `steps` */
+  int32_t resume;       /* with a warm model: continue its training (checkpoint / resume) -- its FP32
+                           master weights, Adam moments and step count, so that `steps` more steps
+                           equal the same steps of an uninterrupted run bit for bit (same options;
+                           the warm model must have been trained in this process, since exported
+                           blobs carry no Adam state); 0 = warm start (weights only, Section 3.6) */
 } nvdb_train_opts;
 
 typedef struct {

@@ -23,7 +23,7 @@ class TrainOpts(C.Structure):
                 ("ffm_size", C.c_int32 * 2), ("ffm_sigma", C.c_float), ("steps", C.c_int32),
                 ("batch", C.c_int32), ("lr", C.c_float), ("lr_decay", C.c_float), ("lr_interval", C.c_int32),
                 ("loss", C.c_int32), ("train_prec", C.c_int32), ("patch_precs", C.c_uint32),
-                ("stop_window", C.c_int32), ("stop_loss", C.c_float * 3)]
+                ("stop_window", C.c_int32), ("stop_loss", C.c_float * 3), ("resume", C.c_int32)]
 
 
 class Info(C.Structure):

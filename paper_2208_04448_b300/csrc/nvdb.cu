@@ -25,6 +25,8 @@
 #include "train.cuh"
 #include "train_tc.cuh"
 
+#include <nvtx3/nvToolsExt.h>
+
 using namespace nvdb;
 
 // ============================================================================ errors
@@ -152,6 +154,14 @@ const char* eval_name(const char* base, int mode) {
   return names[b][mode];
 }
 
+// NVTX range over a C-ABI call or one of its stages (visible in Nsight timelines).
+struct Range {
+  explicit Range(const char* name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+  Range(const Range&) = delete;
+  Range& operator=(const Range&) = delete;
+};
+
 // ============================================================================ scan helper
 struct Scan {
   int64_t* sums = nullptr;
@@ -266,9 +276,10 @@ struct DevNet {
   uint8_t* wpk = nullptr;   // [FP16 | BF16 hi | BF16 lo] weight tiles, then BF16 W_l^T tiles
   float* m = nullptr;
   float* v = nullptr;
+  float* master = nullptr;  // BF16 training: the FP32 master weights before the final rounding
   bool bf16_exact = false;  // every weight and bias (not the head) is a BF16 value
   uint32_t* f8_amax = nullptr;  // calibrated activation ranges (float bits) per layer, FP8 scales
-  ~DevNet() { dfree(p32); dfree(wpk); dfree(m); dfree(v); dfree(f8_amax); }
+  ~DevNet() { dfree(p32); dfree(wpk); dfree(m); dfree(v); dfree(master); dfree(f8_amax); }
 };
 
 // Patch lists of one precision (Section 3.3.2), on the device only: CSR offsets per
@@ -618,6 +629,7 @@ nvdb_status check_model_shapes(const nvdb_model* m) {
 // ============================================================================ build
 extern "C" nvdb_status nvdb_build(const int32_t* d_ijk, const float* d_val, int64_t n, const nvdb_build_opts* opts,
                                   nvdb_stream stream, nvdb_grid** out) {
+  const Range range("nvdb_build");
   if (!out || !opts || n < 0 || (n > 0 && (!d_ijk || !d_val))) return fail(NVDB_ERR_INVALID_ARG, "nvdb_build: bad arguments");
   if (opts->grid_class != 0 && opts->grid_class != 1) return fail(NVDB_ERR_INVALID_ARG, "grid_class must be 0 or 1");
   if (opts->grid_class == 0 && !(opts->half_width > 0.f)) return fail(NVDB_ERR_INVALID_ARG, "half_width must be > 0");
@@ -783,6 +795,7 @@ TrainJob grid_train_job(const nvdb_grid* g, int net, const nvdb_train_opts* o) {
 // Classify every candidate of the grid at `prec`; mismatches with the explicit
 // masks become the patch lists (Section 3.3.2).
 nvdb_status make_patches(nvdb_model* m, const nvdb_grid* g, int prec, cudaStream_t s) {
+  const Range range("patches");
   PatchSet ps;
   ps.prec = prec;
   for (int lev = 0; lev < 2; ++lev) {
@@ -836,6 +849,7 @@ nvdb_status make_patches(nvdb_model* m, const nvdb_grid* g, int prec, cudaStream
 
 extern "C" nvdb_status nvdb_compress(const nvdb_grid* g, const nvdb_train_opts* o, const nvdb_model* warm,
                                      nvdb_stream stream, nvdb_model** out) {
+  const Range range("nvdb_compress");
   if (!g || !o || !out) return fail(NVDB_ERR_INVALID_ARG, "nvdb_compress: NULL argument");
   if (o->steps < 0 || o->batch <= 0 || !(o->lr >= 0.f) || o->lr_interval < 0)
     return fail(NVDB_ERR_INVALID_ARG, "nvdb_compress: bad steps/batch/lr");
@@ -848,6 +862,7 @@ extern "C" nvdb_status nvdb_compress(const nvdb_grid* g, const nvdb_train_opts* 
   *out = nullptr;
   cudaStream_t s = (cudaStream_t)stream;
   auto* m = new nvdb_model();
+  const bool resume = o->resume != 0 && warm != nullptr;
   auto run = [&]() -> nvdb_status {
     m->grid_class = g->grid_class;
     m->background = g->background;
@@ -882,7 +897,8 @@ extern "C" nvdb_status nvdb_compress(const nvdb_grid* g, const nvdb_train_opts* 
     for (int k = 0; k < 3; ++k) {
       if (warm) {
         TRY(upload_net(m, k, nullptr, s));
-        CU(cudaMemcpyAsync(m->net[k].p32, warm->net[k].p32, m->net[k].P * 4, cudaMemcpyDeviceToDevice, s));
+        const float* src = resume && warm->net[k].master ? warm->net[k].master : warm->net[k].p32;
+        CU(cudaMemcpyAsync(m->net[k].p32, src, m->net[k].P * 4, cudaMemcpyDeviceToDevice, s));
         m->net[k].bf16_exact = warm->net[k].bf16_exact && o->steps == 0;
       } else {
         const std::vector<float> p = xavier_params(o->seed, k, k == 0 ? m->ffm[0] : m->ffm[1], m->width[k], m->layers[k]);
@@ -891,8 +907,14 @@ extern "C" nvdb_status nvdb_compress(const nvdb_grid* g, const nvdb_train_opts* 
       }
       TRY(dalloc(&m->net[k].m, m->net[k].P));
       TRY(dalloc(&m->net[k].v, m->net[k].P));
-      CU(cudaMemsetAsync(m->net[k].m, 0, m->net[k].P * 4, s));
-      CU(cudaMemsetAsync(m->net[k].v, 0, m->net[k].P * 4, s));
+      if (resume) {   // Adam state and history of the interrupted run
+        CU(cudaMemcpyAsync(m->net[k].m, warm->net[k].m, m->net[k].P * 4, cudaMemcpyDeviceToDevice, s));
+        CU(cudaMemcpyAsync(m->net[k].v, warm->net[k].v, m->net[k].P * 4, cudaMemcpyDeviceToDevice, s));
+        m->losses[k] = warm->losses[k];
+      } else {
+        CU(cudaMemsetAsync(m->net[k].m, 0, m->net[k].P * 4, s));
+        CU(cudaMemsetAsync(m->net[k].v, 0, m->net[k].P * 4, s));
+      }
     }
     // explicit upper tree (root + level-2 nodes) is kept as is (Section 3.3.1)
     TRY(dalloc(&m->l2_origin, g->n_l2));
@@ -920,19 +942,24 @@ extern "C" nvdb_status nvdb_compress(const nvdb_grid* g, const nvdb_train_opts* 
       st = fail(NVDB_ERR_CUDA, "training event");
     if (st == NVDB_OK && (cudaEventRecord(ev, s) != cudaSuccess || cudaStreamWaitEvent(ts, ev, 0) != cudaSuccess))
       st = fail(NVDB_ERR_CUDA, "training stream order");
-    static const int kFirstStep = 1;
+    static const char* kTrainRange[3] = {"train level-1 classifier", "train level-0 classifier", "train regressor"};
     for (int k = 0; k < 3 && st == NVDB_OK; ++k) {
+      const Range range(kTrainRange[k]);
       DevNet& d = m->net[k];
       if ((st = ensure_partial(m, (int64_t)grid * (d.P + 1))) != NVDB_OK) break;
       TrainJob job = grid_train_job(g, k, o);
       job.partial = m->partial;
       job.step_dev = d_step;
       if (o->train_prec == NVDB_BF16 && (st = pack_net(m, k, ts)) != NVDB_OK) break;   // the BF16 tiles of step 1
-      if (cudaMemcpyAsync(d_step, &kFirstStep, 4, cudaMemcpyHostToDevice, ts) != cudaSuccess) {
+      // the first step of this call: after the interrupted run's steps when resuming
+      const int done = (int)m->losses[k].size();
+      const int first = done + 1;
+      if (cudaMemcpyAsync(d_step, &first, 4, cudaMemcpyHostToDevice, ts) != cudaSuccess ||
+          cudaStreamSynchronize(ts) != cudaSuccess) {   // `first` is a stack value
         st = fail(NVDB_ERR_CUDA, "step counter");
         break;
       }
-      const AdamSched sc{d_step, o->lr, o->lr_decay, o->lr_interval, d_loss};
+      const AdamSched sc{d_step, o->lr, o->lr_decay, o->lr_interval, d_loss, first};
       auto one_step = [&]() -> nvdb_status {
         TRY(launch_train(m, k, o->train_prec, job, grid, ts));
         KLAUNCH("adam_reduce", ts, adam_reduce_kernel<<<blocks_for(d.P + 1, 32), 32 * kRedGroups, 0, ts>>>(
@@ -981,9 +1008,9 @@ extern "C" nvdb_status nvdb_compress(const nvdb_grid* g, const nvdb_train_opts* 
       }
       if (exec) cudaGraphExecDestroy(exec);
       if (st == NVDB_OK) {
-        m->losses[k].resize(ran);
+        m->losses[k].resize(done + ran);
         if (ran) {
-          cudaError_t e = cudaMemcpyAsync(m->losses[k].data(), d_loss, ran * 4, cudaMemcpyDeviceToHost, ts);
+          cudaError_t e = cudaMemcpyAsync(m->losses[k].data() + done, d_loss, ran * 4, cudaMemcpyDeviceToHost, ts);
           if (e == cudaSuccess) e = cudaStreamSynchronize(ts);
           if (e != cudaSuccess) st = fail(NVDB_ERR_CUDA, "loss readback: %s", cudaGetErrorString(e));
         }
@@ -1003,6 +1030,8 @@ extern "C" nvdb_status nvdb_compress(const nvdb_grid* g, const nvdb_train_opts* 
       for (int k = 0; k < 3; ++k) {
         DevNet& d = m->net[k];
         const int64_t n = d.P - d.width - 1;   // every weight and bias except the FP32 head
+        TRY(dalloc(&d.master, d.P));        // kept for a resumed run
+        CU(cudaMemcpyAsync(d.master, d.p32, d.P * 4, cudaMemcpyDeviceToDevice, s));
         KLAUNCH("round_bf16", s, round_bf16_kernel<<<blocks_for(n, 256), 256, 0, s>>>(d.p32, n));
         CU(cudaGetLastError());
         d.bf16_exact = true;
@@ -1082,7 +1111,10 @@ nvdb_status decode_batch(nvdb_model* const* ms, int n, nvdb_precision prec, Deco
     j.status = d.status;
     b.it[m] = eval_item(ms[m], 0, j);
   }
-  TRY(launch_batch(b, prec, s));
+  {
+    const Range range("decode: level-1 classification");
+    TRY(launch_batch(b, prec, s));
+  }
   PatchBatch pb;
   pb.n = n;
   for (int m = 0; m < n; ++m) pb.it[m] = PatchItem{ps[m]->d_l1_off, ps[m]->d_l1_idx, s1[m]};
@@ -1104,7 +1136,10 @@ nvdb_status decode_batch(nvdb_model* const* ms, int n, nvdb_precision prec, Deco
     j.status = d.status;
     b.it[m] = eval_item(ms[m], 1, j);
   }
-  TRY(launch_batch(b, prec, s));
+  {
+    const Range range("decode: level-0 classification");
+    TRY(launch_batch(b, prec, s));
+  }
   for (int m = 0; m < n; ++m) pb.it[m] = PatchItem{ps[m]->d_l0_off, ps[m]->d_l0_idx, sl[m]};
   if (NL)
     KLAUNCH("patch_count", s, patch_count_batch_kernel<<<blocks_for(NL, 8), 256, 0, s>>>(d.leaf_words, 16, NL, pb,
@@ -1126,7 +1161,10 @@ nvdb_status decode_batch(nvdb_model* const* ms, int n, nvdb_precision prec, Deco
       j.status = d.status;
       b.it[m] = eval_item(ms[m], 2, j);
     }
+    {
+    const Range range("decode: regression");
     TRY(launch_batch(b, prec, s));
+  }
   }
   CU(cudaGetLastError());
   return NVDB_OK;
@@ -1148,6 +1186,7 @@ std::vector<std::pair<int, int>> batch_runs(const nvdb_model* const* models, int
 extern "C" nvdb_status nvdb_decompress(const nvdb_model* const* models, int n_models, nvdb_precision prec,
                                        int32_t* d_ijk, float* d_val, int64_t capacity, int64_t* counts,
                                        nvdb_stream stream) {
+  const Range range("nvdb_decompress");
   if (!models || n_models < 0 || !counts || capacity < 0) return fail(NVDB_ERR_INVALID_ARG, "nvdb_decompress: bad arguments");
   if (d_ijk && !d_val) return fail(NVDB_ERR_INVALID_ARG, "nvdb_decompress: d_val is NULL");
   int64_t need = 0;
@@ -1237,6 +1276,7 @@ TopoView topo_view(const nvdb_model* m) {
 
 extern "C" nvdb_status nvdb_query(const nvdb_model* cm, const float* d_xyz, int64_t n, nvdb_precision prec,
                                   float* d_out, uint8_t* d_active, nvdb_stream stream) {
+  const Range range("nvdb_query");
   if (!cm || n < 0 || (n > 0 && (!d_xyz || !d_out))) return fail(NVDB_ERR_INVALID_ARG, "nvdb_query: bad arguments");
   if (!eval_prec_ok(prec)) return fail(NVDB_ERR_UNSUPPORTED, "precision %d", (int)prec);
   nvdb_model* m = const_cast<nvdb_model*>(cm);

@@ -313,12 +313,13 @@ constexpr int kRedGroups = 8;
 
 // Step-dependent inputs of the Adam kernel read from device memory (graph replay): the
 // step from step_dev[1], lr_t = lr * decay^floor((step - 1) / interval), the loss slot
-// loss_base[step - 1]; block 0 advances step_dev[0] for the next step.
+// loss_base[step - first_step]; block 0 advances step_dev[0] for the next step.
 struct AdamSched {
   int* step_dev;              // nullptr: use the launch's step, lr_t and loss_out
   float lr, decay;
   int interval;
-  float* loss_base;
+  float* loss_base;           // loss of step t at loss_base[t - first_step]
+  int first_step;
 };
 
 __global__ void __launch_bounds__(32 * kRedGroups) adam_reduce_kernel(
@@ -328,7 +329,7 @@ __global__ void __launch_bounds__(32 * kRedGroups) adam_reduce_kernel(
   if (sc.step_dev) {
     step = sc.step_dev[1];
     lr_t = sc.interval > 0 ? sc.lr * powf(sc.decay, (float)((step - 1) / sc.interval)) : sc.lr;
-    loss_out = sc.loss_base + (step - 1);
+    loss_out = sc.loss_base + (step - sc.first_step);
     if (blockIdx.x == 0 && threadIdx.x == 0) sc.step_dev[0] = step + 1;
   }
   const int lane = threadIdx.x & 31, q = threadIdx.x >> 5;
