@@ -198,13 +198,17 @@ nvdb_status nvdb_plan_free(nvdb_plan* plan);
  * trilinear blend with weights (w_x w_y) w_z, corners summed in the order
  * c = 4a + 2b + d for offset (a, b, d).  d_out float [n]; d_active (may be
  * NULL) uint8 [n] receives the active-corner bitmask (bit c).
- * Does not synchronise unless the topology cache is built by this call. */
+ * FP32 does not synchronise unless the topology cache is built by this call;
+ * the tensor-core precisions end with one stream synchronisation that reads
+ * the model's device status word (NVDB_ERR_TIMEOUT if a bounded wait ran out).
+ * Calls on one model that overlap on the GPU share that word. */
 nvdb_status nvdb_query(const nvdb_model* model, const float* d_xyz, int64_t n, nvdb_precision prec,
                        float* d_out, uint8_t* d_active, nvdb_stream stream);
 
 /* Raw output (logit or unscaled value) of network `net` at n voxel
  * coordinates d_ijk int32 [n][3]; the level-1 classifier takes leaf origins
- * (its input is ijk >> 3).  d_out float [n].  Does not synchronise. */
+ * (its input is ijk >> 3).  d_out float [n].  FP32 does not synchronise; the
+ * tensor-core precisions synchronise once to read the status word, as nvdb_query. */
 nvdb_status nvdb_mlp_eval(const nvdb_model* model, int net, nvdb_precision prec, const int32_t* d_ijk,
                           int64_t n, float* d_out, nvdb_stream stream);
 
@@ -273,6 +277,23 @@ nvdb_status nvdb_model_free(nvdb_model* model);
 
 /* Message of the last error of the calling thread ("" if none). */
 const char* nvdb_last_error(void);
+
+/* Fault injection for tests of the failure handling; nothing here faults the GPU.
+ *  NVDB_INJECT_WAIT_TIMEOUT: value != 0 makes every bounded device-side wait (the MMA
+ *    completion mbarriers, the training weight staging) report a timeout once its phase
+ *    has completed: the kernels take their timeout path with nothing in flight, and the
+ *    calls return NVDB_ERR_TIMEOUT; value 0 clears it.
+ *  NVDB_INJECT_ALLOC_BUDGET: value > 0 lets later device allocations of the library take
+ *    at most `value` bytes in total, after which they fail with NVDB_ERR_OUT_OF_MEMORY
+ *    (frees do not refund); value 0 removes the budget.
+ * Process-wide; not for production use. */
+enum { NVDB_INJECT_WAIT_TIMEOUT = 1, NVDB_INJECT_ALLOC_BUDGET = 2 };
+nvdb_status nvdb_debug_inject(int what, int64_t value);
+
+/* Self-test of the bounded wait: one kernel waits on an mbarrier phase that nothing
+ * completes, for limit_ns (at most 1 s), then returns NVDB_ERR_TIMEOUT; the device
+ * stays usable.  Synchronises the device. */
+nvdb_status nvdb_debug_wait_selftest(int64_t limit_ns);
 
 /* Tracing (a measurement aid; the paper reports wall-clock times only).
  * With profiling on, the library records a CUDA event pair on the launching

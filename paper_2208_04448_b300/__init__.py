@@ -12,7 +12,8 @@ import ctypes as C
 import torch
 
 from . import _native as N
-from ._native import (BF16, BF16X3, FP16, FP32, FP8_E4M3, LOSS_BCE, LOSS_L1, LOSS_LINEAR, LOSS_MSE,  # noqa: F401
+from ._native import (BF16, BF16X3, FP16, FP32, FP8_E4M3, INJECT_ALLOC_BUDGET, INJECT_WAIT_TIMEOUT,  # noqa: F401
+                      LOSS_BCE, LOSS_L1, LOSS_LINEAR, LOSS_MSE,
                       NET_L0_CLASSIFIER,
                       NET_L1_CLASSIFIER, NET_REGRESSOR)
 
@@ -305,6 +306,16 @@ def model_import(blob, stream=None) -> Model:
         ptr, n = bytes(blob), len(blob)
     _check(lib().nvdb_model_import(ptr, n, _stream(stream), C.byref(h)))
     return Model(h)
+
+
+def debug_inject(what: int, value: int):
+    """nvdb_debug_inject: fault injection for tests (INJECT_WAIT_TIMEOUT, INJECT_ALLOC_BUDGET)."""
+    _check(lib().nvdb_debug_inject(what, value))
+
+
+def debug_wait_selftest(limit_ns: int):
+    """nvdb_debug_wait_selftest: a bounded wait that runs out (raises NvdbError TIMEOUT)."""
+    _check(lib().nvdb_debug_wait_selftest(limit_ns))
 
 
 def profile_enable(on: bool = True):

@@ -12,6 +12,7 @@ OK, ERR_INVALID_ARG, ERR_DUPLICATE_VOXEL, ERR_OUT_OF_MEMORY, ERR_CAPACITY, ERR_C
 FP32, BF16, FP8_E4M3, FP16, BF16X3 = 0, 1, 2, 3, 4
 NET_L1_CLASSIFIER, NET_L0_CLASSIFIER, NET_REGRESSOR = 0, 1, 2
 LOSS_MSE, LOSS_L1, LOSS_BCE, LOSS_LINEAR = 0, 1, 2, 3
+INJECT_WAIT_TIMEOUT, INJECT_ALLOC_BUDGET = 1, 2
 
 
 class BuildOpts(C.Structure):
@@ -56,6 +57,8 @@ SIGNATURES = {
     "nvdb_net_params": ([_vp, _i32, _vp, _vp], _st),
     "nvdb_net_set_params": ([_vp, _i32, _vp, _vp], _st),
     "nvdb_model_repatch": ([_vp, _vp, C.c_uint32, _vp], _st),
+    "nvdb_debug_inject": ([_i32, _i64], _st),
+    "nvdb_debug_wait_selftest": ([_i64], _st),
     "nvdb_net_param_count": ([_vp, _i32], C.c_int64),
     "nvdb_model_info": ([_vp, C.POINTER(Info)], _st),
     "nvdb_model_export": ([_vp, _vp, C.POINTER(C.c_size_t)], _st),

@@ -95,15 +95,22 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
                :: "r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
 }
 
+// Test hook (nvdb_debug_inject): when set, every bounded wait reports a timeout after its
+// phase has completed, so kernels take their timeout path with nothing in flight.
+__device__ int g_fail_waits = 0;
+
 // Wait for phase `parity` of an mbarrier; returns false (and the caller flags
 // ST_TIMEOUT) if it has not completed within kWaitLimitNs.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const uint64_t t0 = global_ns();
-  for (uint32_t it = 1;; ++it) {
-    if (mbar_try_wait(bar, parity)) return true;
-    if ((it & 255) == 0 && global_ns() - t0 > kWaitLimitNs) return false;
+  bool done = mbar_try_wait(bar, parity);
+  if (!done) {
+    const uint64_t t0 = global_ns();
+    for (uint32_t it = 1; !done; ++it) {
+      done = mbar_try_wait(bar, parity);
+      if (!done && (it & 255) == 0 && global_ns() - t0 > kWaitLimitNs) return false;
+    }
   }
+  return !__ldg(&g_fail_waits);
 }
 
 __device__ __forceinline__ void fence_proxy_async_smem() {

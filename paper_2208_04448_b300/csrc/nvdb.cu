@@ -58,10 +58,18 @@ nvdb_status fail(nvdb_status s, const char* fmt, ...) {
     if (s_ != NVDB_OK) return s_;         \
   } while (0)
 
+// Test hook (nvdb_debug_inject): a budget of bytes for later device allocations.
+std::atomic<int64_t> g_alloc_budget{-1};   // -1: none
+
 template <class T>
 nvdb_status dalloc(T** p, size_t count) {
   *p = nullptr;
   if (count == 0) return NVDB_OK;
+  const int64_t bytes = (int64_t)(count * sizeof(T));
+  for (int64_t b = g_alloc_budget.load(); b >= 0;) {   // take the bytes from the budget, or fail
+    if (b < bytes) return fail(NVDB_ERR_OUT_OF_MEMORY, "device allocation of %lld bytes over the injected budget", (long long)bytes);
+    if (g_alloc_budget.compare_exchange_weak(b, b - bytes)) break;
+  }
   CU(cudaMalloc((void**)p, count * sizeof(T)));
   return NVDB_OK;
 }
@@ -560,6 +568,15 @@ nvdb_status status_to_error(uint32_t st) {
   if (st & ST_CAPACITY) return fail(NVDB_ERR_CAPACITY, "output capacity exceeded on the device");
   if (st & ST_CORRUPT) return fail(NVDB_ERR_CORRUPT, "decoded counts differ from the model header");
   return NVDB_OK;
+}
+
+// The tensor-core kernels' only device-side error is a timed-out wait; reading it costs
+// one stream synchronisation, which the FP32 path (no waits) does not pay.
+nvdb_status eval_status(const nvdb_model* m, nvdb_precision prec, cudaStream_t s) {
+  if (prec == NVDB_FP32) return NVDB_OK;
+  uint32_t hst = 0;
+  TRY(read_status(m->status, s, &hst));
+  return status_to_error(hst);
 }
 
 nvdb_status upload_net(nvdb_model* m, int k, const float* host_params, cudaStream_t s) {
@@ -1282,6 +1299,7 @@ extern "C" nvdb_status nvdb_query(const nvdb_model* cm, const float* d_xyz, int6
   nvdb_model* m = const_cast<nvdb_model*>(cm);
   cudaStream_t s = (cudaStream_t)stream;
   TRY(build_query_cache(m, s));
+  if (prec != NVDB_FP32) CU(cudaMemsetAsync(m->status, 0, 4, s));
   QueryCache& q = m->qc;
   const TopoView tv = topo_view(m);
   for (int64_t b0 = 0; b0 < n; b0 += q.batch) {
@@ -1302,7 +1320,7 @@ extern "C" nvdb_status nvdb_query(const nvdb_model* cm, const float* d_xyz, int6
     KLAUNCH("query_blend", s, query_blend_kernel<<<blocks_for(nb, 256), 256, 0, s>>>(xyz, nb, q.qmask, q.off, q.vals, m->background, d_out + b0));
     CU(cudaGetLastError());
   }
-  return NVDB_OK;
+  return eval_status(m, prec, s);
 }
 
 // ============================================================================ network-level calls
@@ -1316,7 +1334,10 @@ extern "C" nvdb_status nvdb_mlp_eval(const nvdb_model* m, int net, nvdb_precisio
   j.shift = net == 0 ? 3 : 0;
   j.out = d_out;
   j.scale = 1.f;
-  return launch_eval(m, net, prec, j, (cudaStream_t)stream);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (prec != NVDB_FP32) CU(cudaMemsetAsync(m->status, 0, 4, s));
+  TRY(launch_eval(m, net, prec, j, s));
+  return eval_status(m, prec, s);
 }
 
 extern "C" int64_t nvdb_net_param_count(const nvdb_model* m, int net) {
@@ -1337,6 +1358,7 @@ extern "C" nvdb_status nvdb_mlp_grad(const nvdb_model* cm, int net, nvdb_precisi
   const DevNet& d = m->net[net];
   const int grid = train_grid(n);
   TRY(ensure_partial(m, (int64_t)grid * (d.P + 1)));
+  CU(cudaMemsetAsync(m->status, 0, 4, s));   // this call's device-side errors only
   TrainJob j{};
   j.net = net;
   j.loss = loss_kind;
@@ -1363,6 +1385,50 @@ extern "C" nvdb_status nvdb_mlp_grad(const nvdb_model* cm, int net, nvdb_precisi
   }
   if (loss) *loss = h;
   return NVDB_OK;
+}
+
+// ============================================================================ fault injection (tests)
+namespace {
+// A kernel that waits on an mbarrier phase nothing completes, bounded by limit_ns.
+__global__ void wait_selftest_kernel(int64_t limit_ns, uint32_t* status) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) mbar_init(&bar, 1);
+  __syncthreads();
+  const uint64_t t0 = global_ns();
+  bool done = false;
+  while (!done && global_ns() - t0 < (uint64_t)limit_ns) done = mbar_try_wait(&bar, 0);
+  if (!done && threadIdx.x == 0) set_status(status, ST_TIMEOUT);
+}
+}  // namespace
+
+extern "C" nvdb_status nvdb_debug_inject(int what, int64_t value) {
+  if (what == NVDB_INJECT_WAIT_TIMEOUT) {
+    const int v = value != 0 ? 1 : 0;
+    CU(cudaMemcpyToSymbol(g_fail_waits, &v, sizeof v));
+    return NVDB_OK;
+  }
+  if (what == NVDB_INJECT_ALLOC_BUDGET) {
+    if (value < 0) return fail(NVDB_ERR_INVALID_ARG, "nvdb_debug_inject: negative budget");
+    g_alloc_budget.store(value > 0 ? value : -1);
+    return NVDB_OK;
+  }
+  return fail(NVDB_ERR_INVALID_ARG, "nvdb_debug_inject: unknown injection %d", what);
+}
+
+extern "C" nvdb_status nvdb_debug_wait_selftest(int64_t limit_ns) {
+  if (limit_ns <= 0 || limit_ns > (int64_t)kWaitLimitNs) return fail(NVDB_ERR_INVALID_ARG, "limit_ns in (0, 1 s]");
+  uint32_t* st = nullptr;
+  TRY(dalloc(&st, 1));
+  uint32_t h = 0;
+  cudaError_t e = cudaMemset(st, 0, 4);
+  if (e == cudaSuccess) {
+    wait_selftest_kernel<<<1, 32>>>(limit_ns, st);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(&h, st, 4, cudaMemcpyDeviceToHost);
+  dfree(st);
+  if (e != cudaSuccess) return fail(NVDB_ERR_CUDA, "nvdb_debug_wait_selftest: %s", cudaGetErrorString(e));
+  return status_to_error(h);
 }
 
 // ============================================================================ parameters (autograd)
@@ -1395,6 +1461,7 @@ extern "C" nvdb_status nvdb_model_repatch(nvdb_model* m, const nvdb_grid* g, uin
     return fail(NVDB_ERR_INVALID_ARG, "nvdb_model_repatch: the grid is not the one the model encodes");
   cudaStream_t s = (cudaStream_t)stream;
   m->qc.release();
+  CU(cudaMemsetAsync(m->status, 0, 4, s));
   for (int p = 0; p < kNumPrecisions; ++p)
     if (patch_precs & (1u << p)) TRY(make_patches(m, g, p, s));
   uint32_t hst = 0;
