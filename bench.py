@@ -474,7 +474,8 @@ def main():
     # ---- end to end through the C ABI with host buffers
     # input: the compressed model as shipped for this precision (the same deterministic
     # training, only this precision's patch set) in pinned host memory; output: the
-    # voxels, to pinned memory
+    # voxels and values in pinned host memory (nvdb_decompress_host: the voxel copy
+    # overlaps the regression)
     e2e_blob = nv.compress(g, **dict(opts, patch_precs=1 << head_prec)).export()
     blob_pinned = torch.frombuffer(bytearray(e2e_blob), dtype=torch.uint8).pin_memory()
     h_ijk = torch.empty((n_active, 3), dtype=torch.int32, pin_memory=True)
@@ -484,9 +485,7 @@ def main():
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         m2 = nv.model_import(blob_pinned)
-        nv.decompress(m2, head_prec, out=(out_ijk, out_val))
-        h_ijk.copy_(out_ijk, non_blocking=True)
-        h_val.copy_(out_val, non_blocking=True)
+        nv.decompress_host(m2, head_prec, host=(h_ijk, h_val), out=(out_ijk, out_val))
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
         del m2

@@ -170,6 +170,18 @@ nvdb_status nvdb_decompress(const nvdb_model* const* models, int n_models, nvdb_
                             int32_t* d_ijk, float* d_val, int64_t capacity, int64_t* counts,
                             nvdb_stream stream);
 
+/* nvdb_decompress with the result delivered to HOST memory as well: the
+ * voxels are decoded into d_ijk / d_val as above and copied to h_ijk int32
+ * [cap][3] / h_val float [cap] (caller-owned; page-locked memory lets the
+ * copies run asynchronously).  The voxel copy starts as soon as the voxels
+ * are emitted, on a stream of the library's own, and overlaps the
+ * regression; the value copy follows it.  Returns when both copies have
+ * landed.  h_ijk and h_val may be NULL only when d_ijk is (counts only).
+ * Errors as nvdb_decompress. */
+nvdb_status nvdb_decompress_host(const nvdb_model* const* models, int n_models, nvdb_precision prec,
+                                 int32_t* d_ijk, float* d_val, int32_t* h_ijk, float* h_val,
+                                 int64_t capacity, int64_t* counts, nvdb_stream stream);
+
 /* Decode plan: the whole nvdb_decompress of `models` into the given output
  * buffers, recorded once into a CUDA graph (the benchmark spec: batched, graph-captured
  * decode).  Models with the same network shapes are decoded together, up to 48

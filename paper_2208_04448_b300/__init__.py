@@ -187,6 +187,33 @@ def decompress(models, prec: int = FP32, out=None, stream=None):
     return ijk[:total], val[:total], list(counts)
 
 
+def decompress_host(models, prec: int = FP32, host=None, out=None, stream=None):
+    """Decode models into device buffers and, overlapped with the regression, into host
+    buffers (nvdb_decompress_host).  `host` = (ijk int32 [n,3], val float32 [n]) CPU
+    tensors, pinned for asynchronous copies (allocated pinned if None); `out` = device
+    buffers to reuse.  Returns (host ijk, host val, counts)."""
+    if isinstance(models, Model):
+        models = [models]
+    arr = (C.c_void_p * len(models))(*[m.handle for m in models])
+    counts = (C.c_int64 * len(models))()
+    _check(lib().nvdb_decompress_host(arr, len(models), prec, None, None, None, None, 0, counts, _stream(stream)))
+    total = sum(counts)
+    ijk, val = out if out is not None else (torch.empty((total, 3), dtype=torch.int32, device="cuda"),
+                                            torch.empty(total, dtype=torch.float32, device="cuda"))
+    if host is None:
+        host = (torch.empty((total, 3), dtype=torch.int32, pin_memory=True),
+                torch.empty(total, dtype=torch.float32, pin_memory=True))
+    h_ijk, h_val = host
+    for h, dt, nm in ((h_ijk, torch.int32, "host ijk"), (h_val, torch.float32, "host val")):
+        if h.device.type != "cpu" or h.dtype != dt or not h.is_contiguous() or h.shape[0] < total:
+            raise ValueError(f"{nm}: need a contiguous CPU {dt} tensor of at least {total} rows")
+    cap = min(ijk.shape[0], h_ijk.shape[0], h_val.shape[0])
+    _check(lib().nvdb_decompress_host(arr, len(models), prec, _dptr(ijk, torch.int32, "ijk"),
+                                      _dptr(val, torch.float32, "val"), h_ijk.data_ptr(), h_val.data_ptr(), cap,
+                                      counts, _stream(stream)))
+    return h_ijk[:total], h_val[:total], list(counts)
+
+
 class Plan:
     """A graph-captured decode of fixed models into fixed output buffers (nvdb_plan)."""
 

@@ -45,6 +45,7 @@ SIGNATURES = {
     "nvdb_compress": ([_vp, C.POINTER(TrainOpts), _vp, _vp, C.POINTER(_vp)], _st),
     "nvdb_model_losses": ([_vp, _i32, _f32p, _i64, C.POINTER(C.c_int64)], _st),
     "nvdb_decompress": ([C.POINTER(_vp), _i32, _i32, _vp, _vp, _i64, C.POINTER(C.c_int64), _vp], _st),
+    "nvdb_decompress_host": ([C.POINTER(_vp), _i32, _i32, _vp, _vp, _vp, _vp, _i64, C.POINTER(C.c_int64), _vp], _st),
     "nvdb_decompress_plan": ([C.POINTER(_vp), _i32, _i32, _vp, _vp, _i64, _vp, C.POINTER(_vp)], _st),
     "nvdb_plan_launch": ([_vp, _vp], _st),
     "nvdb_plan_check": ([_vp, _vp], _st),

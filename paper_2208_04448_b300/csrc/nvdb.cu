@@ -1093,8 +1093,35 @@ bool same_shape(const nvdb_model* a, const nvdb_model* b) {
 // patches -> voxel offsets; with an output, the voxels and their regressed
 // values (concatenated per model, canonical order).  Levels of the models are
 // concatenated in model order in `d`.
+// A non-blocking stream of the library's own for device-to-host copies that overlap
+// kernels of the caller's stream (one per device, created on first use).
+nvdb_status copy_stream(cudaStream_t* out) {
+  static std::mutex mu;
+  static std::map<int, cudaStream_t> streams;
+  int dev = 0;
+  CU(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = streams.find(dev);
+  if (it == streams.end()) {
+    cudaStream_t cs = nullptr;
+    CU(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    it = streams.emplace(dev, cs).first;
+  }
+  *out = it->second;
+  return NVDB_OK;
+}
+
+// Host destination of a decode: the voxels are copied on the library's copy stream as soon
+// as they are emitted (overlapping the regression), the values after the regression.
+struct HostSink {
+  int32_t* ijk;
+  float* val;
+  cudaStream_t copy;
+  cudaEvent_t ev;
+};
+
 nvdb_status decode_batch(nvdb_model* const* ms, int n, nvdb_precision prec, DecodeScratch& d, int32_t* out_ijk,
-                         float* out_val, cudaStream_t s) {
+                         float* out_val, cudaStream_t s, const HostSink* sink = nullptr) {
   std::vector<int64_t> s2(n + 1, 0), s1(n + 1, 0), sl(n + 1, 0), sa(n + 1, 0);
   for (int m = 0; m < n; ++m) {
     s2[m + 1] = s2[m] + ms[m]->n_l2;
@@ -1168,6 +1195,11 @@ nvdb_status decode_batch(nvdb_model* const* ms, int n, nvdb_precision prec, Deco
       KLAUNCH("emit_voxels", s, emit_voxels_rank_kernel<<<blocks_for(NL, 8), 256, 0, s>>>(d.leaf_words, d.leaf_origin,
                                                                                         NL, d.leaf_off, out_ijk, NA,
                                                                                         d.status));
+    if (sink && NA) {
+      CU(cudaEventRecord(sink->ev, s));
+      CU(cudaStreamWaitEvent(sink->copy, sink->ev, 0));
+      CU(cudaMemcpyAsync(sink->ijk, out_ijk, (size_t)NA * 12, cudaMemcpyDeviceToHost, sink->copy));
+    }
     for (int m = 0; m < n; ++m) {
       EvalJob j{};
       j.mode = MODE_LIST;
@@ -1182,6 +1214,11 @@ nvdb_status decode_batch(nvdb_model* const* ms, int n, nvdb_precision prec, Deco
     const Range range("decode: regression");
     TRY(launch_batch(b, prec, s));
   }
+    if (sink && NA) {
+      CU(cudaEventRecord(sink->ev, s));
+      CU(cudaStreamWaitEvent(sink->copy, sink->ev, 0));
+      CU(cudaMemcpyAsync(sink->val, out_val, (size_t)NA * 4, cudaMemcpyDeviceToHost, sink->copy));
+    }
   }
   CU(cudaGetLastError());
   return NVDB_OK;
@@ -1200,10 +1237,31 @@ std::vector<std::pair<int, int>> batch_runs(const nvdb_model* const* models, int
 }
 }  // namespace
 
+namespace {
+nvdb_status decompress_impl(const nvdb_model* const* models, int n_models, nvdb_precision prec, int32_t* d_ijk,
+                            float* d_val, int32_t* h_ijk, float* h_val, int64_t capacity, int64_t* counts,
+                            nvdb_stream stream);
+}
+
 extern "C" nvdb_status nvdb_decompress(const nvdb_model* const* models, int n_models, nvdb_precision prec,
                                        int32_t* d_ijk, float* d_val, int64_t capacity, int64_t* counts,
                                        nvdb_stream stream) {
   const Range range("nvdb_decompress");
+  return decompress_impl(models, n_models, prec, d_ijk, d_val, nullptr, nullptr, capacity, counts, stream);
+}
+
+extern "C" nvdb_status nvdb_decompress_host(const nvdb_model* const* models, int n_models, nvdb_precision prec,
+                                            int32_t* d_ijk, float* d_val, int32_t* h_ijk, float* h_val,
+                                            int64_t capacity, int64_t* counts, nvdb_stream stream) {
+  const Range range("nvdb_decompress_host");
+  if (d_ijk && (!h_ijk || !h_val)) return fail(NVDB_ERR_INVALID_ARG, "nvdb_decompress_host: NULL host buffer");
+  return decompress_impl(models, n_models, prec, d_ijk, d_val, h_ijk, h_val, capacity, counts, stream);
+}
+
+namespace {
+nvdb_status decompress_impl(const nvdb_model* const* models, int n_models, nvdb_precision prec, int32_t* d_ijk,
+                            float* d_val, int32_t* h_ijk, float* h_val, int64_t capacity, int64_t* counts,
+                            nvdb_stream stream) {
   if (!models || n_models < 0 || !counts || capacity < 0) return fail(NVDB_ERR_INVALID_ARG, "nvdb_decompress: bad arguments");
   if (d_ijk && !d_val) return fail(NVDB_ERR_INVALID_ARG, "nvdb_decompress: d_val is NULL");
   int64_t need = 0;
@@ -1221,6 +1279,11 @@ extern "C" nvdb_status nvdb_decompress(const nvdb_model* const* models, int n_mo
   std::vector<DecodeScratch*> tmp;
   nvdb_status st = NVDB_OK;
   std::vector<uint32_t*> status_words;
+  HostSink sink{};
+  if (h_ijk) {
+    TRY(copy_stream(&sink.copy));
+    CU(cudaEventCreateWithFlags(&sink.ev, cudaEventDisableTiming));
+  }
   for (const auto& r : batch_runs(models, n_models)) {
     const int n = r.second - r.first;
     DecodeScratch* d = &ms[r.first]->ds;
@@ -1228,10 +1291,17 @@ extern "C" nvdb_status nvdb_decompress(const nvdb_model* const* models, int n_mo
       tmp.push_back(new DecodeScratch());
       d = tmp.back();
     }
-    st = decode_batch(ms + r.first, n, prec, *d, d_ijk + 3 * base, d_val + base, s);
+    sink.ijk = h_ijk + 3 * base;
+    sink.val = h_val + base;
+    st = decode_batch(ms + r.first, n, prec, *d, d_ijk + 3 * base, d_val + base, s, h_ijk ? &sink : nullptr);
     if (st != NVDB_OK) break;
     status_words.push_back(d->status);
     for (int m = r.first; m < r.second; ++m) base += ms[m]->n_active;
+  }
+  if (h_ijk) {   // the caller's stream continues after the copies
+    const cudaError_t e1 = cudaEventRecord(sink.ev, sink.copy);
+    const cudaError_t e2 = e1 == cudaSuccess ? cudaStreamWaitEvent(s, sink.ev, 0) : e1;
+    if (st == NVDB_OK && e2 != cudaSuccess) st = fail(NVDB_ERR_CUDA, "copy stream: %s", cudaGetErrorString(e2));
   }
   for (uint32_t* sw : status_words) {
     if (st != NVDB_OK) break;
@@ -1239,10 +1309,12 @@ extern "C" nvdb_status nvdb_decompress(const nvdb_model* const* models, int n_mo
     st = read_status(sw, s, &hst);
     if (st == NVDB_OK) st = status_to_error(hst);
   }
-  if (!tmp.empty()) cudaStreamSynchronize(s);
+  if (!tmp.empty() || h_ijk) cudaStreamSynchronize(s);
   for (auto* d : tmp) delete d;
+  if (h_ijk) cudaEventDestroy(sink.ev);
   return st;
 }
+}  // namespace
 
 // ============================================================================ query
 namespace {

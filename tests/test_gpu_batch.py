@@ -42,6 +42,25 @@ def test_batched_equals_single(models, prec):
         off += n
 
 
+@pytest.mark.parametrize("pinned", [True, False])
+def test_decompress_to_host_equals_device_decode(models, pinned):
+    ms, other = models
+    seq = ms + [other, ms[0]]                                        # several runs: one host copy per run
+    ijk, val, counts = nv.decompress(seq, 3)
+    total = sum(counts)
+    host = (torch.full((total + 5, 3), -1, dtype=torch.int32, pin_memory=pinned),
+            torch.full((total + 5,), -1.0, dtype=torch.float32, pin_memory=pinned))
+    hijk, hval, hcounts = nv.decompress_host(seq, 3, host=host)
+    assert hcounts == counts
+    assert torch.equal(hijk, ijk.cpu()) and torch.equal(hval, val.cpu())
+    assert (host[0][total:] == -1).all() and (host[1][total:] == -1.0).all()   # nothing past the result
+    single = nv.decompress_host(ms[1], 1)                           # allocates pinned host buffers itself
+    ref = nv.decompress(ms[1], 1)
+    assert torch.equal(single[0], ref[0].cpu()) and torch.equal(single[1], ref[1].cpu())
+    with pytest.raises(ValueError):
+        nv.decompress_host(seq, 3, host=(host[0][:10], host[1]))
+
+
 def test_more_models_than_one_launch_holds(models):
     ms, _ = models
     seq = [ms[i % 3] for i in range(50)]                              # > 48: two launches per stage
