@@ -942,106 +942,144 @@ extern "C" nvdb_status nvdb_compress(const nvdb_grid* g, const nvdb_train_opts* 
     m->l2_mask_host.resize(512 * g->n_l2);
     TRY(copy_int4_to3(g->l2_origin, g->n_l2, m->l2_origin_host.data(), s));
     CU(cudaMemcpyAsync(m->l2_mask_host.data(), g->l2_mask, g->n_l2 * 4096, cudaMemcpyDeviceToHost, s));
-    // training: each network for `steps` Adam steps, on a stream of our own (the caller's
-    // may be the legacy default stream, which cannot be captured).  The step index lives in
-    // device memory, so one captured chunk of steps replays as a CUDA graph; profiled runs
-    // launch every step (per-kernel events would be recorded once per captured launch).
-    const int grid = train_grid(o->batch);
-    float* d_loss = nullptr;
-    int* d_step = nullptr;
-    cudaStream_t ts = nullptr;
-    cudaEvent_t ev = nullptr;
-    nvdb_status st = dalloc(&d_loss, (size_t)std::max(1, o->steps));
-    if (st == NVDB_OK) st = dalloc(&d_step, 2);
-    if (st == NVDB_OK && cudaStreamCreateWithFlags(&ts, cudaStreamNonBlocking) != cudaSuccess)
-      st = fail(NVDB_ERR_CUDA, "training stream");
-    if (st == NVDB_OK && cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess)
-      st = fail(NVDB_ERR_CUDA, "training event");
-    if (st == NVDB_OK && (cudaEventRecord(ev, s) != cudaSuccess || cudaStreamWaitEvent(ts, ev, 0) != cudaSuccess))
-      st = fail(NVDB_ERR_CUDA, "training stream order");
+    // training: each network for `steps` Adam steps.  The three networks share nothing
+    // (parameters, Adam state, samples, partial sums, step counter and losses are per
+    // network), so each trains on a stream of its own and their kernels overlap: a training
+    // launch holds one CTA per SM, and the SMs its last, partial round of tiles leaves idle
+    // take the next network's CTAs.  (The caller's stream may be the legacy default stream,
+    // which cannot be captured.)  The step index lives in device memory, so one captured
+    // chunk of steps replays as a CUDA graph.  Profiled runs launch every step and train the
+    // networks one after another (per-kernel events would overlap otherwise).
     static const char* kTrainRange[3] = {"train level-1 classifier", "train level-0 classifier", "train regressor"};
+    struct NetRun {
+      cudaStream_t ts = nullptr;
+      cudaEvent_t ev = nullptr;
+      float* d_loss = nullptr;
+      int* d_step = nullptr;
+      TrainJob job{};
+      AdamSched sc{};
+      cudaGraphExec_t exec = nullptr;
+      int done = 0, ran = 0, chunk = 50;
+      bool early = false, active = true;
+    };
+    const int grid = train_grid(o->batch);
+    const bool profiled = prof::g_on.load();
+    NetRun nr[3];
+    int64_t poff[4] = {0, 0, 0, 0};
+    for (int k = 0; k < 3; ++k) poff[k + 1] = poff[k] + (int64_t)grid * (m->net[k].P + 1);
+    nvdb_status st = ensure_partial(m, poff[3]);
     for (int k = 0; k < 3 && st == NVDB_OK; ++k) {
-      const Range range(kTrainRange[k]);
-      DevNet& d = m->net[k];
-      if ((st = ensure_partial(m, (int64_t)grid * (d.P + 1))) != NVDB_OK) break;
-      TrainJob job = grid_train_job(g, k, o);
-      job.partial = m->partial;
-      job.step_dev = d_step;
-      if (o->train_prec == NVDB_BF16 && (st = pack_net(m, k, ts)) != NVDB_OK) break;   // the BF16 tiles of step 1
+      NetRun& r = nr[k];
+      if (cudaStreamCreateWithFlags(&r.ts, cudaStreamNonBlocking) != cudaSuccess ||
+          cudaEventCreateWithFlags(&r.ev, cudaEventDisableTiming) != cudaSuccess) {
+        st = fail(NVDB_ERR_CUDA, "training stream");
+        break;
+      }
+      if (cudaEventRecord(r.ev, s) != cudaSuccess || cudaStreamWaitEvent(r.ts, r.ev, 0) != cudaSuccess) {
+        st = fail(NVDB_ERR_CUDA, "training stream order");
+        break;
+      }
+      if ((st = dalloc(&r.d_loss, (size_t)std::max(1, o->steps))) != NVDB_OK) break;
+      if ((st = dalloc(&r.d_step, 2)) != NVDB_OK) break;
+      r.job = grid_train_job(g, k, o);
+      r.job.partial = m->partial + poff[k];
+      r.job.step_dev = r.d_step;
+      if (o->train_prec == NVDB_BF16 && (st = pack_net(m, k, r.ts)) != NVDB_OK) break;   // the BF16 tiles of step 1
       // the first step of this call: after the interrupted run's steps when resuming
-      const int done = (int)m->losses[k].size();
-      const int first = done + 1;
-      if (cudaMemcpyAsync(d_step, &first, 4, cudaMemcpyHostToDevice, ts) != cudaSuccess ||
-          cudaStreamSynchronize(ts) != cudaSuccess) {   // `first` is a stack value
+      r.done = (int)m->losses[k].size();
+      const int first = r.done + 1;
+      if (cudaMemcpyAsync(r.d_step, &first, 4, cudaMemcpyHostToDevice, r.ts) != cudaSuccess ||
+          cudaStreamSynchronize(r.ts) != cudaSuccess) {   // `first` is a stack value
         st = fail(NVDB_ERR_CUDA, "step counter");
         break;
       }
-      const AdamSched sc{d_step, o->lr, o->lr_decay, o->lr_interval, d_loss, first};
-      auto one_step = [&]() -> nvdb_status {
-        TRY(launch_train(m, k, o->train_prec, job, grid, ts));
-        KLAUNCH("adam_reduce", ts, adam_reduce_kernel<<<blocks_for(d.P + 1, 32), 32 * kRedGroups, 0, ts>>>(
-                                       m->partial, grid, d.P, d.p32, d.m, d.v, 0, 0.f, nullptr, nullptr,
-                                       1.f / (float)o->batch, adam_aux(d, o->train_prec, true), sc));
-        CU(cudaGetLastError());
-        return NVDB_OK;
-      };
-      const bool early = o->stop_loss[k] > 0.f && o->stop_window > 0;
-      const int chunk = early ? o->stop_window : 50;
-      cudaGraphExec_t exec = nullptr;
-      int ran = 0;
-      while (ran < o->steps && st == NVDB_OK) {
-        const int n = std::min(chunk, o->steps - ran);
-        if (!exec && ran > 0 && n == chunk && !prof::g_on.load()) {   // capture after one eager chunk
-          cudaGraph_t gr = nullptr;
-          if (cudaStreamBeginCapture(ts, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
-            st = fail(NVDB_ERR_CUDA, "training capture");
-            break;
-          }
-          nvdb_status cst = NVDB_OK;
-          for (int i = 0; i < chunk && cst == NVDB_OK; ++i) cst = one_step();
-          const cudaError_t e = cudaStreamEndCapture(ts, &gr);
-          if (cst == NVDB_OK && e == cudaSuccess && cudaGraphInstantiate(&exec, gr, 0) != cudaSuccess) exec = nullptr;
-          if (gr) cudaGraphDestroy(gr);
-          if (cst != NVDB_OK) { st = cst; break; }
-          if (e != cudaSuccess || !exec) { st = fail(NVDB_ERR_CUDA, "training graph: %s", cudaGetErrorString(e)); break; }
-        }
-        if (exec && n == chunk) {
-          if (cudaGraphLaunch(exec, ts) != cudaSuccess) { st = fail(NVDB_ERR_CUDA, "training graph launch"); break; }
-        } else {
-          for (int i = 0; i < n && st == NVDB_OK; ++i) st = one_step();
-          if (st != NVDB_OK) break;
-        }
-        ran += n;
-        if (early && ran % o->stop_window == 0) {   // warm-start early stop (Section 3.6)
-          std::vector<float> w(o->stop_window);
-          cudaError_t e = cudaMemcpyAsync(w.data(), d_loss + (ran - o->stop_window), o->stop_window * 4,
-                                          cudaMemcpyDeviceToHost, ts);
-          if (e == cudaSuccess) e = cudaStreamSynchronize(ts);
-          if (e != cudaSuccess) { st = fail(NVDB_ERR_CUDA, "loss readback: %s", cudaGetErrorString(e)); break; }
-          double mean = 0.0;
-          for (float v : w) mean += v;
-          if (mean / o->stop_window < (double)o->stop_loss[k]) break;
-        }
+      r.sc = AdamSched{r.d_step, o->lr, o->lr_decay, o->lr_interval, r.d_loss, first};
+      r.early = o->stop_loss[k] > 0.f && o->stop_window > 0;
+      r.chunk = r.early ? o->stop_window : 50;
+      r.active = o->steps > 0;
+    }
+    auto one_step = [&](int k) -> nvdb_status {
+      NetRun& r = nr[k];
+      DevNet& d = m->net[k];
+      TRY(launch_train(m, k, o->train_prec, r.job, grid, r.ts));
+      KLAUNCH("adam_reduce", r.ts, adam_reduce_kernel<<<blocks_for(d.P + 1, 32), 32 * kRedGroups, 0, r.ts>>>(
+                                       r.job.partial, grid, d.P, d.p32, d.m, d.v, 0, 0.f, nullptr, nullptr,
+                                       1.f / (float)o->batch, adam_aux(d, o->train_prec, true), r.sc));
+      CU(cudaGetLastError());
+      return NVDB_OK;
+    };
+    // one chunk of network k's steps: eager first, then captured once and replayed
+    auto run_chunk = [&](int k) -> nvdb_status {
+      NetRun& r = nr[k];
+      const Range range(kTrainRange[k]);
+      const int n = std::min(r.chunk, o->steps - r.ran);
+      if (!r.exec && r.ran > 0 && n == r.chunk && !profiled) {
+        cudaGraph_t gr = nullptr;
+        if (cudaStreamBeginCapture(r.ts, cudaStreamCaptureModeRelaxed) != cudaSuccess)
+          return fail(NVDB_ERR_CUDA, "training capture");
+        nvdb_status cst = NVDB_OK;
+        for (int i = 0; i < r.chunk && cst == NVDB_OK; ++i) cst = one_step(k);
+        const cudaError_t e = cudaStreamEndCapture(r.ts, &gr);
+        if (cst == NVDB_OK && e == cudaSuccess && cudaGraphInstantiate(&r.exec, gr, 0) != cudaSuccess) r.exec = nullptr;
+        if (gr) cudaGraphDestroy(gr);
+        TRY(cst);
+        if (e != cudaSuccess || !r.exec) return fail(NVDB_ERR_CUDA, "training graph: %s", cudaGetErrorString(e));
       }
-      if (exec) cudaGraphExecDestroy(exec);
+      if (r.exec && n == r.chunk) {
+        if (cudaGraphLaunch(r.exec, r.ts) != cudaSuccess) return fail(NVDB_ERR_CUDA, "training graph launch");
+      } else {
+        for (int i = 0; i < n; ++i) TRY(one_step(k));
+      }
+      r.ran += n;
+      if (r.ran >= o->steps) r.active = false;
+      if (r.early && r.active && r.ran % o->stop_window == 0) {   // warm-start early stop (Section 3.6)
+        std::vector<float> w(o->stop_window);
+        cudaError_t e = cudaMemcpyAsync(w.data(), r.d_loss + (r.ran - o->stop_window), o->stop_window * 4,
+                                        cudaMemcpyDeviceToHost, r.ts);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(r.ts);
+        if (e != cudaSuccess) return fail(NVDB_ERR_CUDA, "loss readback: %s", cudaGetErrorString(e));
+        double mean = 0.0;
+        for (float v : w) mean += v;
+        if (mean / o->stop_window < (double)o->stop_loss[k]) r.active = false;
+      }
+      return NVDB_OK;
+    };
+    // concurrent: chunks of the three networks interleaved; profiled: one network at a time
+    for (int k0 = 0; k0 < (profiled ? 3 : 1) && st == NVDB_OK; ++k0) {
+      const int k1 = profiled ? k0 + 1 : 3;
+      for (bool any = true; any && st == NVDB_OK;) {
+        any = false;
+        for (int k = profiled ? k0 : 0; k < k1 && st == NVDB_OK; ++k)
+          if (nr[k].active) {
+            st = run_chunk(k);
+            any = true;
+          }
+      }
+      // profiled: the next network starts when this one's kernels have run
+      if (profiled && st == NVDB_OK && cudaStreamSynchronize(nr[k0].ts) != cudaSuccess)
+        st = fail(NVDB_ERR_CUDA, "training stream");
+    }
+    for (int k = 0; k < 3; ++k) {
+      NetRun& r = nr[k];
+      if (r.exec) cudaGraphExecDestroy(r.exec);
       if (st == NVDB_OK) {
-        m->losses[k].resize(done + ran);
-        if (ran) {
-          cudaError_t e = cudaMemcpyAsync(m->losses[k].data() + done, d_loss, ran * 4, cudaMemcpyDeviceToHost, ts);
-          if (e == cudaSuccess) e = cudaStreamSynchronize(ts);
+        m->losses[k].resize(r.done + r.ran);
+        if (r.ran) {
+          cudaError_t e = cudaMemcpyAsync(m->losses[k].data() + r.done, r.d_loss, r.ran * 4, cudaMemcpyDeviceToHost, r.ts);
+          if (e == cudaSuccess) e = cudaStreamSynchronize(r.ts);
           if (e != cudaSuccess) st = fail(NVDB_ERR_CUDA, "loss readback: %s", cudaGetErrorString(e));
         }
       }
+      if (r.ts) {   // the caller's stream continues after the training streams
+        if (st == NVDB_OK && (cudaEventRecord(r.ev, r.ts) != cudaSuccess || cudaStreamWaitEvent(s, r.ev, 0) != cudaSuccess))
+          st = fail(NVDB_ERR_CUDA, "training stream order");
+        cudaStreamSynchronize(r.ts);
+        cudaStreamDestroy(r.ts);
+      }
+      if (r.ev) cudaEventDestroy(r.ev);
+      dfree(r.d_step);
+      dfree(r.d_loss);
     }
-    if (ts) {   // the caller's stream continues after the training stream
-      if (st == NVDB_OK && (cudaEventRecord(ev, ts) != cudaSuccess || cudaStreamWaitEvent(s, ev, 0) != cudaSuccess))
-        st = fail(NVDB_ERR_CUDA, "training stream order");
-      cudaStreamSynchronize(ts);
-      cudaStreamDestroy(ts);
-    }
-    if (ev) cudaEventDestroy(ev);
-    dfree(d_step);
-    dfree(d_loss);
     TRY(st);
     if (o->train_prec == NVDB_BF16)   // the BF16 step trained BF16 weights: store them as such
       for (int k = 0; k < 3; ++k) {
