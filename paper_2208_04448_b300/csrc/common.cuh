@@ -97,7 +97,8 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
 
 // Test hook (nvdb_debug_inject): when set, every bounded wait reports a timeout after its
 // phase has completed, so kernels take their timeout path with nothing in flight.
-__device__ int g_fail_waits = 0;
+// (internal linkage: one copy per translation unit, set through runtime.cuh's setters)
+static __device__ int g_fail_waits = 0;
 
 // Wait for phase `parity` of an mbarrier; returns false (and the caller flags
 // ST_TIMEOUT) if it has not completed within kWaitLimitNs.

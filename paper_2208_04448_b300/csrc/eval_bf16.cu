@@ -1,0 +1,8 @@
+// Fused encode + MLP on tcgen05 tensor cores, TC_BF16 operands (mlp.cuh).
+#include "eval_launch.cuh"
+
+namespace nvdb {
+nvdb_status launch_eval_bf16(const EvalBatch& b, int64_t ntiles, cudaStream_t s) {
+  return launch_tc_shape<TC_BF16>(b, ntiles, "mlp_bf16", s);
+}
+}  // namespace nvdb

@@ -1,0 +1,41 @@
+// Launchers of the fused encode + MLP kernels, instantiated once per precision in the
+// eval_*.cu translation units.
+#pragma once
+#include <algorithm>
+
+#include "runtime.cuh"
+
+namespace nvdb {
+
+template <int NIN, int W, int MODE>
+nvdb_status launch_tc(const EvalBatch& b, int64_t ntiles, const char* base, cudaStream_t s) {
+  const TcLayout<NIN, W, MODE> lay(b.it[0].net.layers);
+  TRY(set_smem_limit((const void*)mlp_tc_kernel<NIN, W, MODE>, lay.total));
+  // Residency from the kernel's own limits (the runtime's occupancy query reports 1 for
+  // kernels that allocate tensor memory): registers, shared memory, and TMEM columns.
+  cudaFuncAttributes fa;
+  CU(cudaFuncGetAttributes(&fa, mlp_tc_kernel<NIN, W, MODE>));
+  const int regs = std::max(8, (fa.numRegs + 7) & ~7);
+  const int by_regs = 65536 / (regs * kTile);
+  const int by_smem = (int)(kSmemPerSm / (lay.total + 1024));
+  int occ = std::min({by_regs, by_smem, TcCfg<NIN, W, MODE>::MAXC});
+  if (occ < 1) return fail(NVDB_ERR_UNSUPPORTED, "tensor-core kernel does not fit on an SM");
+  if (g_occ_override > 0) occ = std::min(occ, g_occ_override);
+  const int64_t grid = std::min<int64_t>(ntiles, (int64_t)num_sms() * occ);
+  KLAUNCH(eval_name(base, b.it[0].job.mode), s,
+          mlp_tc_kernel<NIN, W, MODE><<<(unsigned)grid, kTile, lay.total, s>>>(b));
+  CU(cudaGetLastError());
+  return NVDB_OK;
+}
+
+template <int MODE>
+nvdb_status launch_tc_shape(const EvalBatch& b, int64_t ntiles, const char* base, cudaStream_t s) {
+  const NetView& nv = b.it[0].net;
+  if (nv.n_in == 32 && nv.width == 32) return launch_tc<32, 32, MODE>(b, ntiles, base, s);
+  if (nv.n_in == 32 && nv.width == 64) return launch_tc<32, 64, MODE>(b, ntiles, base, s);
+  if (nv.n_in == 64 && nv.width == 32) return launch_tc<64, 32, MODE>(b, ntiles, base, s);
+  if (nv.n_in == 64 && nv.width == 64) return launch_tc<64, 64, MODE>(b, ntiles, base, s);
+  return fail(NVDB_ERR_UNSUPPORTED, "network shape n=%d w=%d", nv.n_in, nv.width);
+}
+
+}  // namespace nvdb

@@ -634,7 +634,7 @@ __global__ void __launch_bounds__(kTile, MODE == TC_BF16X3 ? 1 : 4) mlp_tc_kerne
 // FP32 master weights -> FP16 tiles, BF16 hi tiles and BF16 lo tiles in the
 // canonical K-major layout: layer 0 [W x (n_in+16)], layers 1..L-1 [W x (W+16)];
 // column K of a layer's tile is its bias, the 15 columns after it are zero.
-__global__ void pack_weights_kernel(const float* p32, uint8_t* wpk, int nin, int W, int L) {
+static __global__ void pack_weights_kernel(const float* p32, uint8_t* wpk, int nin, int W, int L) {
   const int64_t total = wtile_elems(nin, W, L);
   const int64_t first = (int64_t)W * (nin + 16);
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
@@ -674,8 +674,7 @@ __global__ void calib_amax_kernel(NetView net, int log2_extent, uint64_t seed, i
   __syncthreads();
   const int L = net.layers;
   const uint32_t mask = (1u << log2_extent) - 1u;
-  float lmax[kMaxLayers];
-#pragma unroll
+  float lmax[kMaxLayers];   // the layer loop is not unrolled: this array lives in local memory
   for (int l = 0; l < kMaxLayers; ++l) lmax[l] = 0.f;
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
     uint64_t z = seed + 0x9E3779B97F4A7C15ull * (uint64_t)(s + 1);   // SplitMix64 finaliser
@@ -685,9 +684,8 @@ __global__ void calib_amax_kernel(NetView net, int log2_extent, uint64_t seed, i
     float h[H], a[W];
     encode_f32<NIN>(sq, (int)(z & mask), (int)((z >> 21) & mask), (int)((z >> 42) & mask), h);
     const float* p = net.p32;
-#pragma unroll
-    for (int l = 0; l < kMaxLayers; ++l) {
-      if (l >= L) break;
+#pragma unroll 1
+    for (int l = 0; l < L; ++l) {
       if (l == 0) {
         dense_f32<NIN, W>(p, h, a);
         p += W * NIN + W;
@@ -702,11 +700,10 @@ __global__ void calib_amax_kernel(NetView net, int log2_extent, uint64_t seed, i
       }
     }
   }
-#pragma unroll
-  for (int l = 0; l < kMaxLayers; ++l) {
+  for (int l = 0; l < L; ++l) {
     float v = lmax[l];
     for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
-    if ((threadIdx.x & 31) == 0 && l < L) atomicMax(amax_bits + l, __float_as_uint(v));
+    if ((threadIdx.x & 31) == 0) atomicMax(amax_bits + l, __float_as_uint(v));
   }
 }
 
@@ -720,7 +717,7 @@ __global__ void calib_amax_kernel(NetView net, int log2_extent, uint64_t seed, i
 //   l = 0 (FP16 layer, bias in the MMA): alpha = 1 / s_{a_1}, beta = 0 (alpha = 1 if L = 1);
 //   0 < l < L-1: alpha = s_w s_{a_l} / s_{a_{l+1}}, beta = b_l / s_{a_{l+1}};
 //   l = L-1 > 0: alpha = s_w s_{a_l}, beta = b_l (the FP32 input of the head).
-__global__ void pack_fp8_kernel(const float* p32, uint8_t* wpk, int nin, int W, int L, const uint32_t* amax_bits) {
+static __global__ void pack_fp8_kernel(const float* p32, uint8_t* wpk, int nin, int W, int L, const uint32_t* amax_bits) {
   __shared__ float red_b[256], red_w[256];
   uint8_t* tiles = wpk + wpk_fp8_off(nin, W, L);
   float* aux = reinterpret_cast<float*>(tiles + fp8_tile_bytes(W, L));

@@ -4,8 +4,6 @@
 // compaction), train.cuh (backward + Adam) and query.cuh (random access).
 #include "nvdb.h"
 
-#include <cub/cub.cuh>
-
 #include <algorithm>
 #include <atomic>
 #include <map>
@@ -19,157 +17,15 @@
 
 #include "build.cuh"
 #include "common.cuh"
+#include "runtime.cuh"
 #include "compact.cuh"
 #include "mlp.cuh"
 #include "query.cuh"
 #include "train.cuh"
-#include "train_tc.cuh"
-
-#include <nvtx3/nvToolsExt.h>
 
 using namespace nvdb;
 
-// ============================================================================ errors
 namespace {
-thread_local std::string g_err;
-
-nvdb_status fail(nvdb_status s, const char* fmt, ...) {
-  char buf[512];
-  va_list ap;
-  va_start(ap, fmt);
-  vsnprintf(buf, sizeof buf, fmt, ap);
-  va_end(ap);
-  g_err = buf;
-  return s;
-}
-
-#define CU(call)                                                                                   \
-  do {                                                                                             \
-    cudaError_t e_ = (call);                                                                       \
-    if (e_ != cudaSuccess) {                                                                       \
-      if (e_ == cudaErrorMemoryAllocation) return fail(NVDB_ERR_OUT_OF_MEMORY, "%s: out of memory", #call); \
-      return fail(NVDB_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_));                         \
-    }                                                                                              \
-  } while (0)
-
-#define TRY(expr)                         \
-  do {                                    \
-    nvdb_status s_ = (expr);              \
-    if (s_ != NVDB_OK) return s_;         \
-  } while (0)
-
-// Test hook (nvdb_debug_inject): a budget of bytes for later device allocations.
-std::atomic<int64_t> g_alloc_budget{-1};   // -1: none
-
-template <class T>
-nvdb_status dalloc(T** p, size_t count) {
-  *p = nullptr;
-  if (count == 0) return NVDB_OK;
-  const int64_t bytes = (int64_t)(count * sizeof(T));
-  for (int64_t b = g_alloc_budget.load(); b >= 0;) {   // take the bytes from the budget, or fail
-    if (b < bytes) return fail(NVDB_ERR_OUT_OF_MEMORY, "device allocation of %lld bytes over the injected budget", (long long)bytes);
-    if (g_alloc_budget.compare_exchange_weak(b, b - bytes)) break;
-  }
-  CU(cudaMalloc((void**)p, count * sizeof(T)));
-  return NVDB_OK;
-}
-
-template <class T>
-void dfree(T*& p) {
-  if (p) cudaFree((void*)p);
-  p = nullptr;
-}
-
-constexpr size_t kSmemPerSm = 233472;   // shared memory per SM on sm_103 (228 KiB)
-
-int num_sms() {
-  static int n = 0;
-  if (!n) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-    if (n <= 0) n = 1;
-  }
-  return n;
-}
-
-// Raise a kernel's dynamic shared-memory limit on the current device, once per size: the
-// attribute call costs host time comparable to a launch, so repeated launches skip it.
-nvdb_status set_smem_limit(const void* kernel, size_t bytes) {
-  static std::mutex mu;
-  static std::map<std::pair<const void*, int>, size_t> done;
-  int dev = 0;
-  CU(cudaGetDevice(&dev));
-  std::lock_guard<std::mutex> lk(mu);
-  size_t& have = done[{kernel, dev}];
-  if (bytes <= have) return NVDB_OK;
-  CU(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
-  have = bytes;
-  return NVDB_OK;
-}
-
-inline unsigned blocks_for(int64_t n, int per) { return (unsigned)((n + per - 1) / per); }
-
-// ============================================================================ tracing
-// Optional CUDA events around every kernel launch (on the launching stream)
-// and a running count of launches; read back with nvdb_profile_read.
-namespace prof {
-std::atomic<long long> g_launches{0};
-std::atomic<bool> g_on{false};
-struct Rec {
-  std::string name;
-  cudaEvent_t a, b;
-};
-std::mutex g_mu;
-std::vector<Rec> g_recs;
-struct Scope {
-  cudaEvent_t a = nullptr, b = nullptr;
-  const char* name;
-  cudaStream_t s;
-  Scope(const char* n, cudaStream_t st) : name(n), s(st) {
-    g_launches.fetch_add(1);
-    if (g_on.load() && cudaEventCreate(&a) == cudaSuccess) {
-      cudaEventCreate(&b);
-      cudaEventRecord(a, s);
-    }
-  }
-  ~Scope() {
-    if (!a) return;
-    cudaEventRecord(b, s);
-    std::lock_guard<std::mutex> lk(g_mu);
-    g_recs.push_back({name, a, b});
-  }
-};
-}  // namespace prof
-
-#define KLAUNCH(name, stream, ...)        \
-  do {                                    \
-    prof::Scope prof_scope_(name, stream); \
-    __VA_ARGS__;                          \
-  } while (0)
-
-const char* eval_name(const char* base, int mode) {
-  static const char* names[5][3] = {{"mlp_f32.L1", "mlp_f32.L0", "mlp_f32.list"},
-                                    {"mlp_bf16x3.L1", "mlp_bf16x3.L0", "mlp_bf16x3.list"},
-                                    {"mlp_f16.L1", "mlp_f16.L0", "mlp_f16.list"},
-                                    {"mlp_bf16.L1", "mlp_bf16.L0", "mlp_bf16.list"},
-                                    {"mlp_fp8.L1", "mlp_fp8.L0", "mlp_fp8.list"}};
-  const int b = std::strcmp(base, "mlp_bf16x3") == 0 ? 1
-                : std::strcmp(base, "mlp_f16") == 0  ? 2
-                : std::strcmp(base, "mlp_bf16") == 0 ? 3
-                : std::strcmp(base, "mlp_fp8") == 0  ? 4
-                                                     : 0;
-  return names[b][mode];
-}
-
-// NVTX range over a C-ABI call or one of its stages (visible in Nsight timelines).
-struct Range {
-  explicit Range(const char* name) { nvtxRangePushA(name); }
-  ~Range() { nvtxRangePop(); }
-  Range(const Range&) = delete;
-  Range& operator=(const Range&) = delete;
-};
-
 // ============================================================================ scan helper
 struct Scan {
   int64_t* sums = nullptr;
@@ -412,57 +268,21 @@ NetView net_view(const nvdb_model* m, int k) {
   return v;
 }
 
-// Tensor-core CTAs per SM chosen by the decode-plan autotuner (0: from the kernel's limits).
-int g_occ_override = 0;
-
-template <int NIN, int W, int MODE>
-nvdb_status launch_tc(const EvalBatch& b, int64_t ntiles, const char* base, cudaStream_t s) {
-  const TcLayout<NIN, W, MODE> lay(b.it[0].net.layers);
-  TRY(set_smem_limit((const void*)mlp_tc_kernel<NIN, W, MODE>, lay.total));
-  // Residency from the kernel's own limits (the runtime's occupancy query reports 1 for
-  // kernels that allocate tensor memory): registers, shared memory, and TMEM columns.
-  cudaFuncAttributes fa;
-  CU(cudaFuncGetAttributes(&fa, mlp_tc_kernel<NIN, W, MODE>));
-  const int regs = std::max(8, (fa.numRegs + 7) & ~7);
-  const int by_regs = 65536 / (regs * kTile);
-  const int by_smem = (int)(kSmemPerSm / (lay.total + 1024));
-  int occ = std::min({by_regs, by_smem, TcCfg<NIN, W, MODE>::MAXC});
-  if (occ < 1) return fail(NVDB_ERR_UNSUPPORTED, "tensor-core kernel does not fit on an SM");
-  if (g_occ_override > 0) occ = std::min(occ, g_occ_override);
-  const int64_t grid = std::min<int64_t>(ntiles, (int64_t)num_sms() * occ);
-  KLAUNCH(eval_name(base, b.it[0].job.mode), s,
-          mlp_tc_kernel<NIN, W, MODE><<<(unsigned)grid, kTile, lay.total, s>>>(b));
-  return NVDB_OK;
-}
-
 // Precisions are 0 .. kNumPrecisions-1.
 constexpr int kNumPrecisions = 5;
 bool eval_prec_ok(int prec) {
   return prec == NVDB_FP32 || prec == NVDB_BF16 || prec == NVDB_FP16 || prec == NVDB_BF16X3 || prec == NVDB_FP8_E4M3;
 }
 
-template <int NIN, int W>
-nvdb_status launch_eval_t(const EvalBatch& b, int64_t ntiles, nvdb_precision prec, cudaStream_t s) {
-  int occ = 0;
-  if (prec == NVDB_FP32) {
-    const size_t smem = f32_smem_bytes<NIN, W>(b.it[0].net.layers);
-    TRY(set_smem_limit((const void*)mlp_f32_kernel<NIN, W>, smem));
-    CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, mlp_f32_kernel<NIN, W>, kTile, smem));
-    const int64_t grid = std::min<int64_t>(ntiles, (int64_t)num_sms() * std::max(occ, 1));
-    KLAUNCH(eval_name("mlp_f32", b.it[0].job.mode), s, mlp_f32_kernel<NIN, W><<<(unsigned)grid, kTile, smem, s>>>(b));
-  } else if (prec == NVDB_BF16) {
-    TRY((launch_tc<NIN, W, TC_BF16>(b, ntiles, "mlp_bf16", s)));
-  } else if (prec == NVDB_BF16X3) {
-    TRY((launch_tc<NIN, W, TC_BF16X3>(b, ntiles, "mlp_bf16x3", s)));
-  } else if (prec == NVDB_FP16) {
-    TRY((launch_tc<NIN, W, TC_FP16>(b, ntiles, "mlp_f16", s)));
-  } else if (prec == NVDB_FP8_E4M3) {
-    TRY((launch_tc<NIN, W, TC_FP8>(b, ntiles, "mlp_fp8", s)));
-  } else {
-    return fail(NVDB_ERR_UNSUPPORTED, "precision %d not implemented", (int)prec);
+nvdb_status launch_eval_prec(const EvalBatch& b, int64_t ntiles, nvdb_precision prec, cudaStream_t s) {
+  switch (prec) {
+    case NVDB_FP32: return launch_eval_f32(b, ntiles, s);
+    case NVDB_BF16: return launch_eval_bf16(b, ntiles, s);
+    case NVDB_BF16X3: return launch_eval_bf16x3(b, ntiles, s);
+    case NVDB_FP16: return launch_eval_f16(b, ntiles, s);
+    case NVDB_FP8_E4M3: return launch_eval_fp8(b, ntiles, s);
   }
-  CU(cudaGetLastError());
-  return NVDB_OK;
+  return fail(NVDB_ERR_UNSUPPORTED, "precision %d not implemented", (int)prec);
 }
 
 // Launch a batch whose items share one network shape; fills the tile offsets.
@@ -473,12 +293,7 @@ nvdb_status launch_batch(EvalBatch& b, nvdb_precision prec, cudaStream_t s) {
     tiles += job_tiles(b.it[m].job.mode, b.it[m].job.n_items);
   }
   if (tiles == 0) return NVDB_OK;
-  const NetView& nv = b.it[0].net;
-  if (nv.n_in == 32 && nv.width == 32) return launch_eval_t<32, 32>(b, tiles, prec, s);
-  if (nv.n_in == 32 && nv.width == 64) return launch_eval_t<32, 64>(b, tiles, prec, s);
-  if (nv.n_in == 64 && nv.width == 32) return launch_eval_t<64, 32>(b, tiles, prec, s);
-  if (nv.n_in == 64 && nv.width == 64) return launch_eval_t<64, 64>(b, tiles, prec, s);
-  return fail(NVDB_ERR_UNSUPPORTED, "network shape n=%d w=%d", nv.n_in, nv.width);
+  return launch_eval_prec(b, tiles, prec, s);
 }
 
 EvalItem eval_item(const nvdb_model* m, int k, EvalJob job) {
@@ -508,16 +323,6 @@ nvdb_status launch_train_t(const NetView& nv, const TrainJob& job, int grid, cud
   return NVDB_OK;
 }
 
-template <int NIN, int W>
-nvdb_status launch_train_tc_t(const NetView& nv, const TrainJob& job, int grid, cudaStream_t s) {
-  const size_t smem = TrainTcLayout<NIN, W>(nv.layers).total;
-  if (smem > (size_t)kSmemPerSm - 1024) return fail(NVDB_ERR_UNSUPPORTED, "training tile needs %zu bytes of shared memory", smem);
-  TRY(set_smem_limit((const void*)train_tc_kernel<NIN, W>, smem));
-  KLAUNCH("train_tc_bf16", s, train_tc_kernel<NIN, W><<<grid, kTile, smem, s>>>(nv, job));
-  CU(cudaGetLastError());
-  return NVDB_OK;
-}
-
 // Blocks of one training launch: one per 128-sample tile, at most one per SM (both
 // kernels are persistent over tiles).
 int train_grid(int64_t batch) { return (int)std::min<int64_t>((batch + kTile - 1) / kTile, num_sms()); }
@@ -531,12 +336,7 @@ nvdb_status launch_train(const nvdb_model* m, int k, int prec, TrainJob job, int
   job.oz = m->origin[2];
   if (!job.status) job.status = m->status;
   if (prec == NVDB_BF16) {
-    if (nv.layers > kTrainTcMaxLayers)
-      return fail(NVDB_ERR_UNSUPPORTED, "BF16 training: at most %d hidden layers", kTrainTcMaxLayers);
-    if (nv.n_in == 32 && nv.width == 32) return launch_train_tc_t<32, 32>(nv, job, grid, s);
-    if (nv.n_in == 32 && nv.width == 64) return launch_train_tc_t<32, 64>(nv, job, grid, s);
-    if (nv.n_in == 64 && nv.width == 32) return launch_train_tc_t<64, 32>(nv, job, grid, s);
-    if (nv.n_in == 64 && nv.width == 64) return launch_train_tc_t<64, 64>(nv, job, grid, s);
+    return launch_train_tc(nv, job, grid, s);
   } else if (prec == NVDB_FP32) {
     if (nv.n_in == 32 && nv.width == 32) return launch_train_t<32, 32>(nv, job, grid, s);
     if (nv.n_in == 32 && nv.width == 64) return launch_train_t<32, 64>(nv, job, grid, s);
@@ -620,11 +420,7 @@ nvdb_status pack_net(nvdb_model* m, int k, cudaStream_t s) {
   const NetView nv = net_view(m, k);
   const int lg = k == 0 ? m->log2e - 3 : m->log2e;   // the level-1 classifier works in leaf units
   constexpr int kCalibPoints = 1 << 12;   // one point per thread of 32 blocks
-  if (nv.n_in == 32 && nv.width == 32) KLAUNCH("calib_amax", s, calib_amax_kernel<32, 32><<<kCalibPoints / 128, 128, 0, s>>>(nv, lg, 0xF8CA11Bull, kCalibPoints, d.f8_amax));
-  else if (nv.n_in == 32 && nv.width == 64) KLAUNCH("calib_amax", s, calib_amax_kernel<32, 64><<<kCalibPoints / 128, 128, 0, s>>>(nv, lg, 0xF8CA11Bull, kCalibPoints, d.f8_amax));
-  else if (nv.n_in == 64 && nv.width == 32) KLAUNCH("calib_amax", s, calib_amax_kernel<64, 32><<<kCalibPoints / 128, 128, 0, s>>>(nv, lg, 0xF8CA11Bull, kCalibPoints, d.f8_amax));
-  else if (nv.n_in == 64 && nv.width == 64) KLAUNCH("calib_amax", s, calib_amax_kernel<64, 64><<<kCalibPoints / 128, 128, 0, s>>>(nv, lg, 0xF8CA11Bull, kCalibPoints, d.f8_amax));
-  CU(cudaGetLastError());
+  TRY(launch_calib_amax(nv, lg, 0xF8CA11Bull, kCalibPoints, d.f8_amax, s));
   KLAUNCH("pack_fp8", s, pack_fp8_kernel<<<1, 256, 0, s>>>(d.p32, d.wpk, d.n_in, d.width, d.layers, d.f8_amax));
   CU(cudaGetLastError());
   return NVDB_OK;
@@ -662,10 +458,8 @@ extern "C" nvdb_status nvdb_build(const int32_t* d_ijk, const float* d_val, int6
   uint64_t *k0 = nullptr, *k1 = nullptr;
   uint32_t *i0 = nullptr, *i1 = nullptr, *h = nullptr, *status = nullptr;
   int64_t* e = nullptr;
-  void* tmp = nullptr;
   auto cleanup = [&]() {
     dfree(k0); dfree(k1); dfree(i0); dfree(i1); dfree(h); dfree(e); dfree(status);
-    if (tmp) cudaFree(tmp);
   };
   auto run = [&]() -> nvdb_status {
     if (n == 0) return NVDB_OK;
@@ -674,10 +468,7 @@ extern "C" nvdb_status nvdb_build(const int32_t* d_ijk, const float* d_val, int6
     TRY(dalloc(&g->ijk, 3 * (size_t)n)); TRY(dalloc(&g->val, n));
     CU(cudaMemsetAsync(status, 0, 4, s));
     KLAUNCH("build_keys", s, build_keys_kernel<<<blocks_for(n, 256), 256, 0, s>>>(d_ijk, n, k0, i0, status));
-    size_t tb = 0;
-    CU(cub::DeviceRadixSort::SortPairs(nullptr, tb, k0, k1, i0, i1, (int)n, 0, 63, s));
-    CU(cudaMalloc(&tmp, tb));
-    CU(cub::DeviceRadixSort::SortPairs(tmp, tb, k0, k1, i0, i1, (int)n, 0, 63, s));
+    TRY(sort_keys(k0, k1, i0, i1, (int)n, s));
     KLAUNCH("build_gather", s, build_gather_kernel<<<blocks_for(n, 256), 256, 0, s>>>(k1, i1, n, d_ijk, d_val, g->ijk, g->val, h, h + n,
                                                             h + 2 * n, status));
     CU(cudaGetLastError());
@@ -1514,7 +1305,7 @@ __global__ void wait_selftest_kernel(int64_t limit_ns, uint32_t* status) {
 extern "C" nvdb_status nvdb_debug_inject(int what, int64_t value) {
   if (what == NVDB_INJECT_WAIT_TIMEOUT) {
     const int v = value != 0 ? 1 : 0;
-    CU(cudaMemcpyToSymbol(g_fail_waits, &v, sizeof v));
+    for (FailWaitsSetter set : fail_waits_setters()) CU(set(v));
     return NVDB_OK;
   }
   if (what == NVDB_INJECT_ALLOC_BUDGET) {

@@ -245,6 +245,23 @@ __global__ void __launch_bounds__(kTile, 1) train_fwd_bwd_kernel(NetView net, Tr
 }
 
 
+// Transposed BF16 hidden-layer tiles W_l^T (l >= 1) read by the tensor-core training step's
+// delta propagation.
+constexpr int kTrainTcMaxLayers = 4;
+
+static __global__ void pack_weights_t_kernel(const float* p32, uint8_t* wpk, int nin, int W, int L) {
+  const int64_t te = wtile_elems(nin, W, L);
+  const int64_t total = wtile_t_elems(W, L);
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int l = 1 + (int)(e / ((int64_t)W * W));
+    const int rr = (int)(e % ((int64_t)W * W));
+    const int o = rr / W, i = rr % W;   // W_l[o][i] -> row i, column o
+    const int64_t woff = (int64_t)W * nin + W + (int64_t)(l - 1) * (W * W + W);
+    *reinterpret_cast<__nv_bfloat16*>(wpk + te * 6 + (int64_t)(l - 1) * W * W * 2 + canon_off(i, o, W)) =
+        __float2bfloat16_rn(p32[woff + (int64_t)o * W + i]);
+  }
+}
+
 // Byte offsets, inside the packed buffer, of the BF16 copies of parameter e that the
 // training kernel reads: `fo` in the BF16 forward tile (layer-0 columns interleaved
 // as (cos_f, sin_f)), `to` in the transposed tile (hidden-layer weights only).
@@ -322,7 +339,7 @@ struct AdamSched {
   int first_step;
 };
 
-__global__ void __launch_bounds__(32 * kRedGroups) adam_reduce_kernel(
+static __global__ void __launch_bounds__(32 * kRedGroups) adam_reduce_kernel(
     const float* partial, int nparts, int64_t P, float* params, float* m, float* v, int step, float lr_t,
     float* grad_out, float* loss_out, float loss_scale, AdamAux rp, AdamSched sc) {
   __shared__ float red[kRedGroups][33];

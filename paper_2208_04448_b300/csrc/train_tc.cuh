@@ -22,21 +22,6 @@
 
 namespace nvdb {
 
-constexpr int kTrainTcMaxLayers = 4;
-
-__global__ void pack_weights_t_kernel(const float* p32, uint8_t* wpk, int nin, int W, int L) {
-  const int64_t te = wtile_elems(nin, W, L);
-  const int64_t total = wtile_t_elems(W, L);
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int l = 1 + (int)(e / ((int64_t)W * W));
-    const int rr = (int)(e % ((int64_t)W * W));
-    const int o = rr / W, i = rr % W;   // W_l[o][i] -> row i, column o
-    const int64_t woff = (int64_t)W * nin + W + (int64_t)(l - 1) * (W * W + W);
-    *reinterpret_cast<__nv_bfloat16*>(wpk + te * 6 + (int64_t)(l - 1) * W * W * 2 + canon_off(i, o, W)) =
-        __float2bfloat16_rn(p32[woff + (int64_t)o * W + i]);
-  }
-}
-
 // Byte offset of element (mn, k) of a 16-bit MN-major no-swizzle operand: core
 // matrices of 8 k-rows x 16 bytes (8 consecutive mn); MN groups of 8 at `sbo`
 // bytes, K groups of 8 at `lbo` bytes.
