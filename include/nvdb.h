@@ -245,9 +245,13 @@ nvdb_status nvdb_mlp_grad(const nvdb_model* model, int net, nvdb_precision prec,
  * allocates on first use; this call keeps them, and the loss, in one static
  * device array of 2^20 floats (4 MiB) that every GPU loading the library holds
  * until the library is unloaded.
- *  - The first call on a device looks the array's device address up (once per
- *    device, with that device current); make that first call before any stream
- *    capture begins.
+ *  - Every call looks the array's device address up with cudaGetSymbolAddress
+ *    (which allocates nothing) on the current device; the first call on a device
+ *    loads the library's device code there, so make it before any stream capture
+ *    begins.  The library must not be used across a device reset of a live
+ *    context it has worked in.
+ *  - d_grad must hold nvdb_net_param_count(model, net) floats; the Python binding
+ *    checks this, and the shapes of d_ijk and d_target, before any launch.
  *  - All calls share the array, and each call overwrites it (every block clears
  *    its own part before use).  Calls that can overlap on the GPU -- on
  *    different streams, or from different threads -- race on it; serialise them.
@@ -298,8 +302,11 @@ const char* nvdb_last_error(void);
  *  NVDB_INJECT_ALLOC_BUDGET: value > 0 lets later device allocations of the library take
  *    at most `value` bytes in total, after which they fail with NVDB_ERR_OUT_OF_MEMORY
  *    (frees do not refund); value 0 removes the budget.
+ *  NVDB_INJECT_STATIC_LIMIT: value in (0, 2^20] makes nvdb_mlp_grad_static use only the
+ *    first `value` floats of its static array (so its capacity error can be reached with
+ *    the supported network shapes); value 0 restores the full array.
  * Process-wide; not for production use. */
-enum { NVDB_INJECT_WAIT_TIMEOUT = 1, NVDB_INJECT_ALLOC_BUDGET = 2 };
+enum { NVDB_INJECT_WAIT_TIMEOUT = 1, NVDB_INJECT_ALLOC_BUDGET = 2, NVDB_INJECT_STATIC_LIMIT = 3 };
 nvdb_status nvdb_debug_inject(int what, int64_t value);
 
 /* Self-test of the bounded wait: one kernel waits on an mbarrier phase that nothing

@@ -12,7 +12,8 @@ import ctypes as C
 import torch
 
 from . import _native as N
-from ._native import (BF16, BF16X3, FP16, FP32, FP8_E4M3, INJECT_ALLOC_BUDGET, INJECT_WAIT_TIMEOUT,  # noqa: F401
+from ._native import (BF16, BF16X3, FP16, FP32, FP8_E4M3, INJECT_ALLOC_BUDGET, INJECT_STATIC_LIMIT, INJECT_WAIT_TIMEOUT,  # noqa: F401
+                      ERR_CAPACITY, ERR_CORRUPT, ERR_INVALID_ARG, ERR_OUT_OF_MEMORY, ERR_TIMEOUT, ERR_UNSUPPORTED,
                       LOSS_BCE, LOSS_L1, LOSS_LINEAR, LOSS_MSE,
                       NET_L0_CLASSIFIER,
                       NET_L1_CLASSIFIER, NET_REGRESSOR)
@@ -270,8 +271,22 @@ def mlp_eval(model: Model, net: int, ijk: torch.Tensor, prec: int = FP32, stream
     return out
 
 
+def check_grad_args(param_count: int, ijk: torch.Tensor, target: torch.Tensor, out=None) -> int:
+    """Shapes of a gradient call, checked before anything is launched: ijk [n, 3], target [n],
+    out (if given) exactly param_count elements.  Returns n."""
+    if ijk.dim() != 2 or ijk.shape[1] != 3:
+        raise ValueError(f"ijk must be [n, 3], got {tuple(ijk.shape)}")
+    n = ijk.shape[0]
+    if target.numel() != n:
+        raise ValueError(f"target must hold n = {n} values, got {target.numel()}")
+    if out is not None and out.numel() != param_count:
+        raise ValueError(f"out must hold param_count = {param_count} floats, got {out.numel()}")
+    return n
+
+
 def mlp_grad(model: Model, net: int, ijk: torch.Tensor, target: torch.Tensor, loss: int, prec: int = FP32,
              stream=None):
+    check_grad_args(model.param_count(net), ijk, target)
     g = torch.empty(model.param_count(net), dtype=torch.float32, device="cuda")
     lv = C.c_float()
     _check(lib().nvdb_mlp_grad(model.handle, net, prec, _dptr(ijk, torch.int32, "ijk"),
@@ -284,6 +299,7 @@ def mlp_grad_static(model: Model, net: int, ijk: torch.Tensor, target: torch.Ten
                     stream=None):
     """nvdb_mlp_grad_static: the gradient of mlp_grad computed without any device allocation by the
     library.  `out` (a float32 CUDA tensor of param_count(net) elements) lets the caller own the output too."""
+    check_grad_args(model.param_count(net), ijk, target, out)
     g = out if out is not None else torch.empty(model.param_count(net), dtype=torch.float32, device="cuda")
     lv = C.c_float()
     _check(lib().nvdb_mlp_grad_static(model.handle, net, _dptr(ijk, torch.int32, "ijk"),
@@ -336,7 +352,8 @@ def model_import(blob, stream=None) -> Model:
 
 
 def debug_inject(what: int, value: int):
-    """nvdb_debug_inject: fault injection for tests (INJECT_WAIT_TIMEOUT, INJECT_ALLOC_BUDGET)."""
+    """nvdb_debug_inject: fault injection for tests (INJECT_WAIT_TIMEOUT, INJECT_ALLOC_BUDGET,
+    INJECT_STATIC_LIMIT)."""
     _check(lib().nvdb_debug_inject(what, value))
 
 

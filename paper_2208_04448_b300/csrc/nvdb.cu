@@ -1253,7 +1253,7 @@ extern "C" nvdb_status nvdb_mlp_grad(const nvdb_model* cm, int net, nvdb_precisi
     return fail(NVDB_ERR_INVALID_ARG, "nvdb_mlp_grad: bad arguments");
   if (!train_prec_ok(prec)) return fail(NVDB_ERR_UNSUPPORTED, "nvdb_mlp_grad: precision %d", (int)prec);
   if (loss_kind < 0 || loss_kind > 3) return fail(NVDB_ERR_INVALID_ARG, "unknown loss %d", loss_kind);
-  if (n > (1ll << 31)) return fail(NVDB_ERR_UNSUPPORTED, "nvdb_mlp_grad: n >= 2^31");
+  if (n >= (1ll << 31)) return fail(NVDB_ERR_UNSUPPORTED, "nvdb_mlp_grad: n >= 2^31");
   nvdb_model* m = const_cast<nvdb_model*>(cm);
   cudaStream_t s = (cudaStream_t)stream;
   const DevNet& d = m->net[net];
@@ -1290,6 +1290,12 @@ extern "C" nvdb_status nvdb_mlp_grad(const nvdb_model* cm, int net, nvdb_precisi
 
 // ============================================================================ fault injection (tests)
 namespace {
+// Floats of the allocation-free gradient's static scratch array (nvdb_mlp_grad_static).
+constexpr int64_t kStaticGradFloats = 1 << 20;
+// Test hook (nvdb_debug_inject, NVDB_INJECT_STATIC_LIMIT): use only this many floats of the
+// array, so that the capacity check can be exercised with networks of supported shapes.
+std::atomic<int64_t> g_static_limit{kStaticGradFloats};
+
 // A kernel that waits on an mbarrier phase nothing completes, bounded by limit_ns.
 __global__ void wait_selftest_kernel(int64_t limit_ns, uint32_t* status) {
   __shared__ uint64_t bar;
@@ -1306,6 +1312,11 @@ extern "C" nvdb_status nvdb_debug_inject(int what, int64_t value) {
   if (what == NVDB_INJECT_WAIT_TIMEOUT) {
     const int v = value != 0 ? 1 : 0;
     for (FailWaitsSetter set : fail_waits_setters()) CU(set(v));
+    return NVDB_OK;
+  }
+  if (what == NVDB_INJECT_STATIC_LIMIT) {
+    if (value < 0 || value > kStaticGradFloats) return fail(NVDB_ERR_INVALID_ARG, "nvdb_debug_inject: static limit");
+    g_static_limit.store(value > 0 ? value : kStaticGradFloats);
     return NVDB_OK;
   }
   if (what == NVDB_INJECT_ALLOC_BUDGET) {
@@ -1629,17 +1640,13 @@ extern "C" int nvdb_profile_read(char* names, int name_len, int64_t* launches, d
 // loss live in the file-scope array below (4 MiB, present on every device that
 // loads this library for as long as the library stays loaded).
 namespace {
-constexpr int64_t kStaticGradFloats = 1 << 20;
 static __device__ __align__(256) float g_grad_scratch[kStaticGradFloats];
-constexpr int kMaxDevices = 64;
-std::mutex g_static_mu;
-float* g_static_ptr[kMaxDevices] = {};
 
 template <int NIN, int W>
 nvdb_status launch_train_static(const NetView& nv, const TrainJob& job, int grid, cudaStream_t s) {
   const size_t smem = TrainSmem<NIN, W>::bytes(nv.layers);
   TRY(set_smem_limit((const void*)train_fwd_bwd_kernel<NIN, W>, smem));
-  train_fwd_bwd_kernel<NIN, W><<<grid, kTile, smem, s>>>(nv, job);
+  KLAUNCH("train_fwd_bwd", s, train_fwd_bwd_kernel<NIN, W><<<grid, kTile, smem, s>>>(nv, job));
   CU(cudaGetLastError());
   return NVDB_OK;
 }
@@ -1650,32 +1657,26 @@ extern "C" nvdb_status nvdb_mlp_grad_static(const nvdb_model* m, int net, const 
   if (!m || net < 0 || net > 2 || n <= 0 || !d_ijk || !d_target || !d_grad)
     return fail(NVDB_ERR_INVALID_ARG, "nvdb_mlp_grad_static: bad arguments");
   if (loss_kind < 0 || loss_kind > 3) return fail(NVDB_ERR_INVALID_ARG, "unknown loss %d", loss_kind);
-  if (n > (1ll << 31)) return fail(NVDB_ERR_UNSUPPORTED, "nvdb_mlp_grad_static: n >= 2^31");
+  if (n >= (1ll << 31)) return fail(NVDB_ERR_UNSUPPORTED, "nvdb_mlp_grad_static: n >= 2^31");
   const DevNet& d = m->net[net];
   // one CTA needs P + 1 floats of partials, plus one float for the loss
-  if (d.P + 2 > kStaticGradFloats)
+  const int64_t limit = g_static_limit.load();
+  if (d.P + 2 > limit)
     return fail(NVDB_ERR_CAPACITY, "nvdb_mlp_grad_static: network %d has %lld parameters; the static scratch "
-                "holds %lld floats (at most %lld parameters)", net, (long long)d.P, (long long)kStaticGradFloats,
-                (long long)(kStaticGradFloats - 2));
-  int dev = 0;
-  CU(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= kMaxDevices) return fail(NVDB_ERR_UNSUPPORTED, "device index %d", dev);
-  float* scratch = nullptr;
-  {
-    std::lock_guard<std::mutex> lk(g_static_mu);
-    if (!g_static_ptr[dev]) {
-      void* p = nullptr;
-      const cudaError_t e = cudaGetSymbolAddress(&p, g_grad_scratch);
-      if (e != cudaSuccess)
-        return fail(NVDB_ERR_CUDA, "cudaGetSymbolAddress(static gradient scratch): %s", cudaGetErrorString(e));
-      g_static_ptr[dev] = static_cast<float*>(p);
-    }
-    scratch = g_static_ptr[dev];
-  }
+                "holds %lld floats (at most %lld parameters)", net, (long long)d.P, (long long)limit,
+                (long long)(limit - 2));
+  // The array's device address, looked up on every call with the caller's device current:
+  // the lookup allocates nothing, and an address cached across a device reset (which reloads
+  // the module) could be stale.
+  void* sym = nullptr;
+  const cudaError_t se = cudaGetSymbolAddress(&sym, g_grad_scratch);
+  if (se != cudaSuccess)
+    return fail(NVDB_ERR_CUDA, "cudaGetSymbolAddress(static gradient scratch): %s", cudaGetErrorString(se));
+  float* scratch = static_cast<float*>(sym);
   cudaStream_t s = (cudaStream_t)stream;
-  const int64_t fit = (kStaticGradFloats - 1) / (d.P + 1);
+  const int64_t fit = (limit - 1) / (d.P + 1);
   const int grid = (int)std::min<int64_t>(std::min<int64_t>((n + kTile - 1) / kTile, num_sms()), fit);
-  float* loss_slot = scratch + (kStaticGradFloats - 1);
+  float* loss_slot = scratch + (limit - 1);
   TrainJob j{};
   j.net = net;
   j.loss = loss_kind;
@@ -1693,8 +1694,9 @@ extern "C" nvdb_status nvdb_mlp_grad_static(const nvdb_model* m, int net, const 
   else if (nv.n_in == 64 && nv.width == 32) TRY((launch_train_static<64, 32>(nv, j, grid, s)));
   else if (nv.n_in == 64 && nv.width == 64) TRY((launch_train_static<64, 64>(nv, j, grid, s)));
   else return fail(NVDB_ERR_UNSUPPORTED, "network shape n=%d w=%d", nv.n_in, nv.width);
-  adam_reduce_kernel<<<blocks_for(d.P + 1, 32), 32 * kRedGroups, 0, s>>>(scratch, grid, d.P, nullptr, nullptr, nullptr, 1, 0.f,
-                                                              d_grad, loss_slot, 1.f / (float)n, AdamAux{}, AdamSched{});
+  KLAUNCH("adam_reduce", s, adam_reduce_kernel<<<blocks_for(d.P + 1, 32), 32 * kRedGroups, 0, s>>>(
+                                scratch, grid, d.P, nullptr, nullptr, nullptr, 1, 0.f, d_grad, loss_slot,
+                                1.f / (float)n, AdamAux{}, AdamSched{}));
   CU(cudaGetLastError());
   float h = 0.f;
   CU(cudaMemcpyAsync(&h, loss_slot, sizeof h, cudaMemcpyDeviceToHost, s));

@@ -28,3 +28,21 @@ def test_struct_layouts():
     assert C.sizeof(N.TrainOpts) == 96
     assert C.sizeof(N.Info) == 64 and N.Info.n_active.offset == 32
     assert C.sizeof(N.BuildOpts) == 8
+
+
+def test_gradient_arguments_rejected_before_any_launch():
+    """A short `out`, or ijk / target of the wrong shape, raise before the library is called
+    (a short out would otherwise be written past its end on the device)."""
+    import pytest
+    import torch
+
+    import paper_2208_04448_b300 as nv
+    ijk = torch.zeros((10, 3), dtype=torch.int32)
+    tgt = torch.zeros(10)
+    assert nv.check_grad_args(100, ijk, tgt, torch.zeros(100)) == 10
+    with pytest.raises(ValueError, match="out must hold"):
+        nv.check_grad_args(100, ijk, tgt, torch.zeros(99))
+    with pytest.raises(ValueError, match="target must hold"):
+        nv.check_grad_args(100, ijk, torch.zeros(9))
+    with pytest.raises(ValueError, match="ijk must be"):
+        nv.check_grad_args(100, torch.zeros((10, 2), dtype=torch.int32), tgt)

@@ -60,3 +60,42 @@ def test_static_gradient_matches_allocating_entry_point_twice():
             assert abs(lgot - lref) <= 1e-5 * max(1.0, abs(lref)), (call, net)
     torch.cuda.synchronize()
     assert abs(torch.cuda.mem_get_info()[0] - free_before) < (2 << 20)
+    # A cudaMalloc / cudaFree pair inside a call would leave the free memory unchanged: run
+    # the calls again with a one-byte allocation budget, under which any library allocation
+    # fails (NVDB_ERR_OUT_OF_MEMORY), and check that they still succeed and agree.
+    nv.debug_inject(nv.INJECT_ALLOC_BUDGET, 1)
+    try:
+        for (net, loss, pts, tgt, ref, lref), out in zip(cases, outs):
+            out.fill_(float("nan"))
+            got, lgot = nv.mlp_grad_static(m, net, pts, tgt, loss, out=out)
+            assert np.abs(got.cpu().numpy() - ref).max() <= GRAD_TOL * np.abs(ref).max(), net
+            assert abs(lgot - lref) <= 1e-5 * max(1.0, abs(lref)), net
+        with pytest.raises(nv.NvdbError):   # the allocating entry point does fail under it
+            nv.mlp_grad(m, cases[0][0], cases[0][2], cases[0][3], cases[0][1])
+    finally:
+        nv.debug_inject(nv.INJECT_ALLOC_BUDGET, 0)
+
+
+def test_static_gradient_capacity_error():
+    """Networks whose partials do not fit the static array are rejected with CAPACITY (the
+    limit is lowered below one partial of the network, since no supported shape reaches
+    2^20 - 2 parameters), and a fitting limit with a single partial slot still agrees."""
+    g, m = _model()
+    r = np.random.default_rng(9)
+    n = 3000
+    pts = torch.from_numpy(g["ijk"][r.integers(0, g["n"], n)].astype(np.int32)).cuda()
+    tgt = torch.from_numpy(r.standard_normal(n).astype(np.float32)).cuda()
+    P = m.param_count(2)
+    ref, lref = nv.mlp_grad(m, 2, pts, tgt, nv.LOSS_MSE)
+    try:
+        nv.debug_inject(nv.INJECT_STATIC_LIMIT, P + 1)
+        with pytest.raises(nv.NvdbError) as e:
+            nv.mlp_grad_static(m, 2, pts, tgt, nv.LOSS_MSE)
+        assert e.value.status == nv.ERR_CAPACITY
+        nv.debug_inject(nv.INJECT_STATIC_LIMIT, P + 2)   # room for exactly one block's partial
+        got, lgot = nv.mlp_grad_static(m, 2, pts, tgt, nv.LOSS_MSE)
+        ref = ref.cpu().numpy()
+        assert np.abs(got.cpu().numpy() - ref).max() <= GRAD_TOL * np.abs(ref).max()
+        assert abs(lgot - lref) <= 1e-5 * max(1.0, abs(lref))
+    finally:
+        nv.debug_inject(nv.INJECT_STATIC_LIMIT, 0)
