@@ -9,7 +9,7 @@ namespace nvdb {
 
 template <int NIN, int W, int MODE>
 nvdb_status launch_tc(const EvalBatch& b, int64_t ntiles, const char* base, cudaStream_t s) {
-  const TcLayout<NIN, W, MODE> lay(b.it[0].net.layers);
+  const TcLayout<NIN, W, MODE> lay(b.it[0].net.layers, batch_wlo(b));
   TRY(set_smem_limit((const void*)mlp_tc_kernel<NIN, W, MODE>, lay.total));
   // Residency from the kernel's own limits (the runtime's occupancy query reports 1 for
   // kernels that allocate tensor memory): registers, shared memory, and TMEM columns.

@@ -218,22 +218,32 @@ __global__ void __launch_bounds__(kTile) mlp_f32_kernel(const __grid_constant__ 
 }
 
 // ============================================================== tcgen05 tensor-core path
-// Three operand modes of kind::f16 (same tensor rate):
+// Operand modes of kind::f16 (same tensor rate) and kind::f8f6f4:
 //  TC_BF16X3: activations and weights carried as BF16 pairs v = hi + lo
 //             (hi = bf16(v), lo = bf16(v - hi)); D = A_hi W_hi + A_lo W_hi + A_hi W_lo,
 //             three MMAs per K step (two when the weights are BF16 values), error
 //             ~2^-16 relative.
 //  TC_FP16  : FP16 activations and weights, one MMA per K step.
-//  TC_BF16  : BF16 activations and weights, one MMA per K step.
+//  TC_BF16  : BF16 operands.  The encoding and the inputs of every hidden layer but the
+//             last are carried as hi + lo pairs (two MMA terms), the last hidden layer's
+//             input as plain BF16 (one term); weights that are not BF16 values add the
+//             A_hi W_lo term.  Rounding the earlier activations to 8 bits costs the most
+//             accuracy, since every later layer amplifies it; the last layer's input
+//             rounding alone stays well inside the 2e-2 band bar.
 //  TC_FP8   : the first layer (on the encoding) as TC_FP16; the hidden layers with E4M3
 //             activations and weights (kind::f8f6f4, K = 32 per MMA), one scale per
-//             layer, bias and scales applied in the FP32 epilogue: h = relu(alpha D + beta).
+//             layer, applied in the FP32 epilogue: h = relu(alpha D + beta).
 // Layout per CTA (one 128-row tile in flight):
 //  * weights in shared memory, each layer a [W x (K+16)] tile in the canonical
-//    no-swizzle K-major layout; column K holds the bias, columns K+1.. are zero;
-//  * the A operand (16-bit activations) in tensor memory, two elements per
-//    32-bit column, written by each thread for its own row with tcgen05.st;
-//    column K/2 holds the constant 1 that multiplies the bias column;
+//    no-swizzle K-major layout; column K holds the bias (FP16 tiles: its FP16 value, and
+//    column K+1 the FP16 remainder b - fp16(b)), the other columns past K are zero;
+//  * the bias: FP16 takes it through the MMA (A carries the constant 1 in columns K and
+//    K+1: one more K step, no epilogue work); BF16 modes add the FP32 bias in the
+//    epilogue (their hi + lo operands fill the tensor-memory columns a constant chunk
+//    would need); FP8 folds it into the epilogue's beta;
+//  * the A operand (16-bit activations) in tensor memory, two elements per 32-bit
+//    column, written by each thread for its own row with tcgen05.st: hi at columns
+//    [64, 96) (FP16: [64, 104) with the constant chunk), lo at [96, 128);
 //  * the FP32 accumulator D in tensor memory columns [0, W).
 enum TcMode : int { TC_BF16X3 = 0, TC_FP16 = 1, TC_BF16 = 2, TC_FP8 = 3 };
 
@@ -242,6 +252,12 @@ template <int MODE>
 struct Enc16 {
   static constexpr bool value = MODE == TC_FP16 || MODE == TC_FP8;
 };
+
+// BF16 modes: the A operand of hidden layer l (of L) is a hi + lo pair.
+template <int MODE>
+__host__ __device__ __forceinline__ bool comp_in(int l, int L) {
+  return MODE == TC_BF16X3 || (MODE == TC_BF16 && l < L - 1);
+}
 
 // Transposed hidden-layer tiles W_l^T, l = 1..L-1: [W (in) x W (out)] BF16,
 // canonical K-major over `out`; stored after the three forward tile copies.
@@ -265,30 +281,41 @@ __host__ __device__ inline int64_t wtile_elems(int nin, int w, int L) {
   return (int64_t)w * (nin + 16) + (int64_t)(L - 1) * w * (w + 16);
 }
 
+// Offset of layer l's weights in the flat FP32 parameters.
+__host__ __device__ inline int64_t layer_offset(int nin, int w, int l) {
+  return l == 0 ? 0 : (int64_t)w * nin + w + (int64_t)(l - 1) * (w * w + w);
+}
+
 template <int NIN, int W, int MODE>
 struct TcCfg {
   static constexpr int M = NIN / 2;                         // frequencies
-  static constexpr int K0 = NIN + 16, KH = W + 16;          // augmented K of layer 0 / hidden layers
-  static constexpr uint32_t COLS = MODE == TC_BF16X3 ? 256u : 128u;
-  static constexpr uint32_t A_HI = 64u, A_LO = 128u;        // TMEM columns of the A operand(s)
+  static constexpr int K0 = NIN + 16, KH = W + 16;          // augmented widths of the packed tiles
+  static constexpr uint32_t COLS = 128u;
+  static constexpr uint32_t A_HI = 64u, A_LO = 96u;         // TMEM columns of the A operand(s)
   static constexpr int MAXC = (int)(512u / COLS);           // CTAs per SM that fit in TMEM
-  static constexpr int NCOPY = MODE == TC_BF16X3 ? 2 : 1;
   static constexpr bool ENC16 = Enc16<MODE>::value;
+  static constexpr bool WLO = MODE == TC_BF16X3 || MODE == TC_BF16;   // may read BF16 lo weight tiles
+  static constexpr bool BIAS_MMA = MODE == TC_FP16;                    // bias through a constant-1 K step
 };
 
 constexpr size_t kSmemPerSmDev = 233472;
 
+// Shared-memory layout of mlp_tc_kernel; `wlo`: the batch has a model whose weights are
+// not BF16 values, so the BF16 modes also stage the lo weight tiles.
 template <int NIN, int W, int MODE>
 struct TcLayout {
-  size_t w_bytes, t_off, p_off, wh_off, q_off, bar_off, slot_off, total;
-  __host__ __device__ TcLayout(int L) {
+  size_t w_bytes, t_off, p_off, b_off, wh_off, q_off, bar_off, slot_off, total;
+  int ncopy;
+  __host__ __device__ TcLayout(int L, bool wlo) {
     using C = TcCfg<NIN, W, MODE>;
+    ncopy = C::WLO && wlo ? 2 : 1;
     // one copy of the 16-bit tiles; FP8: the FP16 first-layer tile, the E4M3 tiles, alpha/beta
     w_bytes = MODE == TC_FP8 ? (size_t)W * C::K0 * 2 + fp8_tile_bytes(W, L) + fp8_aux_bytes(W, L)
                              : (size_t)wtile_elems(NIN, W, L) * 2;
-    t_off = (C::NCOPY * w_bytes + 15) & ~(size_t)15;
+    t_off = (ncopy * w_bytes + 15) & ~(size_t)15;
     p_off = t_off + (size_t)C::M * 64 * (C::ENC16 ? 4 : 8);   // T table [M][64]: half2 / float2
-    wh_off = p_off + (size_t)2 * 2 * C::M * 8;               // P tables, two buffers of [2][M] x 8 B
+    b_off = p_off + (size_t)2 * 2 * C::M * 8;                // P tables, two buffers of [2][M] x 8 B
+    wh_off = b_off + (size_t)L * W * 4;                      // FP32 biases [L][W]
     q_off = wh_off + (size_t)(W + 4) * 4;
     bar_off = (q_off + (size_t)C::M * 12 + 7) & ~(size_t)7;
     slot_off = bar_off + 8;
@@ -299,13 +326,17 @@ struct TcLayout {
   }
 };
 
+// Does any model of the batch need the BF16 lo weight tiles?
+__host__ __device__ inline bool batch_wlo(const EvalBatch& b) {
+  for (int m = 0; m < b.n; ++m)
+    if (!b.it[m].net.wexact) return true;
+  return false;
+}
+
 template <int MODE>
 __device__ __forceinline__ void split_pair(float a, float b, uint32_t& hi, uint32_t& lo) {
   if (Enc16<MODE>::value) {
     hi = cvt_f16x2(a, b);
-    lo = 0u;
-  } else if (MODE == TC_BF16) {
-    hi = cvt_bf16x2(a, b);
     lo = 0u;
   } else {
     hi = cvt_bf16x2(a, b);
@@ -314,12 +345,14 @@ __device__ __forceinline__ void split_pair(float a, float b, uint32_t& hi, uint3
   }
 }
 
+// ReLU and pack two FP32 values into the next layer's 16-bit A operand; BF16 modes carry
+// the rounding remainder in `lo` when `comp` (the next layer takes a hi + lo pair).
 template <int MODE>
-__device__ __forceinline__ void relu_pair(float a, float b, uint32_t& hi, uint32_t& lo) {
+__device__ __forceinline__ void relu_pair(float a, float b, bool comp, uint32_t& hi, uint32_t& lo) {
   if (MODE == TC_FP16) {
     hi = cvt_relu_f16x2(a, b);
     lo = 0u;
-  } else if (MODE == TC_BF16) {
+  } else if (!comp) {
     hi = cvt_relu_bf16x2(a, b);
     lo = 0u;
   } else {
@@ -334,20 +367,20 @@ __device__ __forceinline__ void tmem_st_cols(uint32_t taddr, const uint32_t* r) 
   else tmem_st8(taddr, r);
 }
 
-// Write one row of the A operand: NK 16-bit values (as NK/2 packed columns) plus, unless
-// CST is false (it is already in place), the 8-column constant chunk (1, 0, ..., 0) that
-// multiplies the bias column.
-template <int NK, int MODE, bool CST = true>
-__device__ __forceinline__ void store_a_row(uint32_t tlane, const uint32_t* hi, const uint32_t* lo) {
-  using C = TcCfg<32, 32, MODE>;
-  tmem_st_cols<NK / 2>(tlane + C::A_HI, hi);
-  uint32_t cst[8] = {Enc16<MODE>::value ? 0x3C00u : 0x3F80u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
-  if (CST) tmem_st8(tlane + C::A_HI + NK / 2, cst);
-  if (MODE == TC_BF16X3) {
-    tmem_st_cols<NK / 2>(tlane + C::A_LO, lo);
-    cst[0] = 0u;
-    if (CST) tmem_st8(tlane + C::A_LO + NK / 2, cst);
-  }
+// Write one row of the A operand: NK 16-bit values (NK/2 packed columns) at the hi
+// columns, and their remainders at the lo columns when `comp`.
+template <int NK>
+__device__ __forceinline__ void store_a_row(uint32_t tlane, const uint32_t* hi, const uint32_t* lo, bool comp) {
+  tmem_st_cols<NK / 2>(tlane + TcCfg<32, 32, TC_FP16>::A_HI, hi);
+  if (comp) tmem_st_cols<NK / 2>(tlane + TcCfg<32, 32, TC_FP16>::A_LO, lo);
+}
+
+// FP16 constant chunk after NK activations: the pair (1, 1) that multiplies the bias and
+// its remainder in the tile's columns K and K+1, then zeros.
+template <int NK>
+__device__ __forceinline__ void store_bias_chunk(uint32_t tlane) {
+  const uint32_t cst[8] = {0x3C003C00u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+  tmem_st8(tlane + TcCfg<32, 32, TC_FP16>::A_HI + NK / 2, cst);
 }
 
 // Level-0 angle addition, per-tile factors: P[dxl][f] = e^{i Phi(o + (dx0 + dxl) e_x)} for
@@ -370,7 +403,7 @@ __device__ __forceinline__ void l0_factors(const EvalJob& job, const uint32_t* s
   }
 }
 
-// Stage network `net` into shared memory: weight tiles, head, Fourier matrix and
+// Stage network `net` into shared memory: weight tiles, biases, head, Fourier matrix and
 // (level-0 lattice) the table T[f][dy*8+dz] = e^{i Phi(dy e_y + dz e_z)}.
 template <int NIN, int W, int MODE>
 __device__ __forceinline__ void tc_stage(const NetView& net, int mode, const TcLayout<NIN, W, MODE>& lay, uint8_t* smem) {
@@ -379,6 +412,7 @@ __device__ __forceinline__ void tc_stage(const NetView& net, int mode, const TcL
   const int L = net.layers, tid = threadIdx.x;
   float2* sT = reinterpret_cast<float2*>(smem + lay.t_off);
   __half2* sTh = reinterpret_cast<__half2*>(smem + lay.t_off);
+  float* sb = reinterpret_cast<float*>(smem + lay.b_off);
   float* swh = reinterpret_cast<float*>(smem + lay.wh_off);
   uint32_t* sq = reinterpret_cast<uint32_t*>(smem + lay.q_off);
   const int64_t te = wtile_elems(NIN, W, L);
@@ -392,8 +426,12 @@ __device__ __forceinline__ void tc_stage(const NetView& net, int mode, const TcL
   } else {
     const uint8_t* base = net.wpk + (MODE == TC_FP16 ? 0 : te * 2);
     const uint4* src = reinterpret_cast<const uint4*>(base);
-    const size_t n16 = C::NCOPY * lay.w_bytes / 16;
+    const size_t n16 = lay.ncopy * lay.w_bytes / 16;   // hi (or FP16) tiles, then the lo tiles
     for (size_t i = tid; i < n16; i += kTile) dst[i] = __ldg(src + i);
+  }
+  for (int l = 0; l < L; ++l) {
+    const int64_t bo = layer_offset(NIN, W, l) + (int64_t)W * (l == 0 ? NIN : W);
+    for (int o = tid; o < W; o += kTile) sb[l * W + o] = __ldg(net.p32 + bo + o);
   }
   const int64_t hoff = net_param_count(NIN, W, L) - W - 1;
   for (int o = tid; o <= W; o += kTile) swh[o] = __ldg(net.p32 + hoff + o);
@@ -417,19 +455,20 @@ __device__ __forceinline__ void tc_stage(const NetView& net, int mode, const TcL
 }
 
 template <int NIN, int W, int MODE>
-__global__ void __launch_bounds__(kTile, MODE == TC_BF16X3 ? 1 : 4) mlp_tc_kernel(const __grid_constant__ EvalBatch b) {
+__global__ void __launch_bounds__(kTile, 4) mlp_tc_kernel(const __grid_constant__ EvalBatch b) {
   static_assert(W == 32 || W == 64, "width");
   static_assert(NIN == 32 || NIN == 64, "encoding size");
   using C = TcCfg<NIN, W, MODE>;
   constexpr int M = C::M;
   extern __shared__ __align__(1024) uint8_t smem[];
   const int L = b.it[0].net.layers;
-  const TcLayout<NIN, W, MODE> lay(L);
+  const TcLayout<NIN, W, MODE> lay(L, batch_wlo(b));
   uint8_t* sw = smem;                              // hi (or FP16) weight tiles
-  uint8_t* sw_lo = smem + lay.w_bytes;             // lo weight tiles (BF16X3)
-  float2* sT = reinterpret_cast<float2*>(smem + lay.t_off);      // BF16X3: FP32 table
+  uint8_t* sw_lo = smem + lay.w_bytes;             // lo weight tiles (BF16 modes, inexact weights)
+  float2* sT = reinterpret_cast<float2*>(smem + lay.t_off);      // BF16 modes: FP32 table
   __half2* sTh = reinterpret_cast<__half2*>(smem + lay.t_off);   // FP16: half table
   float2* sP = reinterpret_cast<float2*>(smem + lay.p_off);
+  const float* sb = reinterpret_cast<const float*>(smem + lay.b_off);
   float* swh = reinterpret_cast<float*>(smem + lay.wh_off);
   uint32_t* sq = reinterpret_cast<uint32_t*>(smem + lay.q_off);
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + lay.bar_off);
@@ -458,6 +497,7 @@ __global__ void __launch_bounds__(kTile, MODE == TC_BF16X3 ? 1 : 4) mlp_tc_kerne
   bool wexact = false;
   int pbuf = 0;            // level-0 factor buffer of the current tile
   bool p_ready = false;    // its factors were computed during the previous tile
+  const bool comp0 = comp_in<MODE>(0, L);
   for (int64_t t0 = blockIdx.x; t0 < ntiles && !failed; t0 += gridDim.x) {
     const int m = batch_find(b, t0);
     if (m != cur) {   // uniform across the CTA: restage the item's network
@@ -535,14 +575,15 @@ __global__ void __launch_bounds__(kTile, MODE == TC_BF16X3 ? 1 : 4) mlp_tc_kerne
           split_pair<MODE>(cs, sn, hi[f], lo[f]);
         }
       }
-      store_a_row<NIN, MODE>(tlane, hi, lo);
+      store_a_row<NIN>(tlane, hi, lo, comp0);
+      if (C::BIAS_MMA) store_bias_chunk<NIN>(tlane);
     }
     tmem_st_wait();
     tc_fence_before();
     __syncthreads();
     float y = 0.f;
     for (int l = 0; l < L; ++l) {
-      const int K = l == 0 ? C::K0 : C::KH;
+      const int K = l == 0 ? NIN : W;                 // real columns; the tiles are K + 16 wide
       if (tid == 0 && MODE == TC_FP8 && l > 0) {   // E4M3 hidden layer: K = W, 32 per MMA
         tc_fence_after();
         const uint32_t b0 = smem_u32(sw) + f8_tiles + (uint32_t)((l - 1) * W * W);
@@ -553,13 +594,15 @@ __global__ void __launch_bounds__(kTile, MODE == TC_BF16X3 ? 1 : 4) mlp_tc_kerne
         tc_fence_after();
         const uint32_t woff = l == 0 ? 0u : (uint32_t)(W * C::K0 + (l - 1) * W * C::KH) * 2u;
         const uint32_t b0 = smem_u32(sw) + woff, bl = smem_u32(sw_lo) + woff;
-        for (int ks = 0; ks < K / 16; ++ks) {
-          const uint64_t bd = smem_desc(b0 + ks * 256, 128, K * 16);
+        const uint32_t sbo = (uint32_t)(K + 16) * 16u;
+        const bool comp = comp_in<MODE>(l, L);
+        for (int ks = 0; ks < K / 16 + (C::BIAS_MMA ? 1 : 0); ++ks) {
+          const uint64_t bd = smem_desc(b0 + ks * 256, 128, sbo);
           mma_f16kind_ts(tbase, tbase + C::A_HI + ks * 8, bd, idesc, ks > 0 ? 1u : 0u);
-          if (MODE == TC_BF16X3) {
-            mma_f16kind_ts(tbase, tbase + C::A_LO + ks * 8, bd, idesc, 1u);
+          if (C::WLO) {
+            if (comp) mma_f16kind_ts(tbase, tbase + C::A_LO + ks * 8, bd, idesc, 1u);
             if (!wexact)   // A_hi * W_lo vanishes for BF16-exact weights
-              mma_f16kind_ts(tbase, tbase + C::A_HI + ks * 8, smem_desc(bl + ks * 256, 128, K * 16), idesc, 1u);
+              mma_f16kind_ts(tbase, tbase + C::A_HI + ks * 8, smem_desc(bl + ks * 256, 128, sbo), idesc, 1u);
           }
         }
         mma_commit(bar);
@@ -583,6 +626,14 @@ __global__ void __launch_bounds__(kTile, MODE == TC_BF16X3 ? 1 : 4) mlp_tc_kerne
           accu[2 * c] = __float_as_uint(h.x);
           accu[2 * c + 1] = __float_as_uint(h.y);
         }
+      } else if (!C::BIAS_MMA) {   // FP32 bias
+        const float2* bl2 = reinterpret_cast<const float2*>(sb + l * W);
+#pragma unroll
+        for (int c = 0; c < W / 2; ++c) {
+          const float2 bv = bl2[c];
+          accu[2 * c] = __float_as_uint(__uint_as_float(accu[2 * c]) + bv.x);
+          accu[2 * c + 1] = __float_as_uint(__uint_as_float(accu[2 * c + 1]) + bv.y);
+        }
       }
       if (MODE == TC_FP8 && l < L - 1) {
         uint32_t q[W / 4];
@@ -593,12 +644,13 @@ __global__ void __launch_bounds__(kTile, MODE == TC_BF16X3 ? 1 : 4) mlp_tc_kerne
         tmem_st_cols<W / 4>(tlane + C::A_HI, q);
         tmem_st_wait();
       } else if (l < L - 1) {
+        const bool comp = comp_in<MODE>(l + 1, L);
         uint32_t hi[W / 2], lo[W / 2];
 #pragma unroll
         for (int p = 0; p < W / 2; ++p)
-          relu_pair<MODE>(__uint_as_float(accu[2 * p]), __uint_as_float(accu[2 * p + 1]), hi[p], lo[p]);
-        // equal widths: the constant chunk the tile's encoding wrote is still in place
-        store_a_row<W, MODE, NIN != W>(tlane, hi, lo);
+          relu_pair<MODE>(__uint_as_float(accu[2 * p]), __uint_as_float(accu[2 * p + 1]), comp, hi[p], lo[p]);
+        store_a_row<W>(tlane, hi, lo, comp);
+        if (C::BIAS_MMA && NIN != W) store_bias_chunk<W>(tlane);   // equal widths: still in place
         tmem_st_wait();
       } else {
         // FP32 head, two products per instruction, four independent partial sums
@@ -633,7 +685,8 @@ __global__ void __launch_bounds__(kTile, MODE == TC_BF16X3 ? 1 : 4) mlp_tc_kerne
 
 // FP32 master weights -> FP16 tiles, BF16 hi tiles and BF16 lo tiles in the
 // canonical K-major layout: layer 0 [W x (n_in+16)], layers 1..L-1 [W x (W+16)];
-// column K of a layer's tile is its bias, the 15 columns after it are zero.
+// column K of a layer's tile is its bias (FP16 tiles: column K+1 the FP16 remainder of the
+// bias), the other columns after it are zero.
 static __global__ void pack_weights_kernel(const float* p32, uint8_t* wpk, int nin, int W, int L) {
   const int64_t total = wtile_elems(nin, W, L);
   const int64_t first = (int64_t)W * (nin + 16);
@@ -656,7 +709,12 @@ static __global__ void pack_weights_kernel(const float* p32, uint8_t* wpk, int n
     const float v = i < K ? p32[woff + (int64_t)o * K + src] : (i == K ? p32[woff + (int64_t)W * K + o] : 0.f);
     const size_t off = base + canon_off(o, i, K + 16);
     const __nv_bfloat16 hi = __float2bfloat16_rn(v);
-    *reinterpret_cast<__half*>(wpk + off) = __float2half_rn(v);
+    if (i == K + 1) {   // FP16 tiles: the remainder of the bias, b - fp16(b)
+      const float bv = p32[woff + (int64_t)W * K + o];
+      *reinterpret_cast<__half*>(wpk + off) = __float2half_rn(bv - __half2float(__float2half_rn(bv)));
+    } else {
+      *reinterpret_cast<__half*>(wpk + off) = __float2half_rn(v);
+    }
     *reinterpret_cast<__nv_bfloat16*>(wpk + total * 2 + off) = hi;
     *reinterpret_cast<__nv_bfloat16*>(wpk + total * 4 + off) = __float2bfloat16_rn(v - __bfloat162float(hi));
   }
@@ -714,7 +772,7 @@ __global__ void calib_amax_kernel(NetView net, int log2_extent, uint64_t seed, i
 //   a_0 = 1,  a_{l+1} <= max_o (sum_i |W_l[o][i]| a_l + |b_l[o]|)   (range of layer l's output);
 // a tensor with bound a is stored as E4M3 of x / s, s = a / 448 (E4M3's largest finite
 // value); layer l >= 1 stores E4M3 of W_l / s_w, s_w = max |W_l| / 448.  Epilogue constants:
-//   l = 0 (FP16 layer, bias in the MMA): alpha = 1 / s_{a_1}, beta = 0 (alpha = 1 if L = 1);
+//   l = 0 (FP16 layer): alpha = 1 / s_{a_1}, beta = b_0 / s_{a_1} (alpha = 1, beta = b_0 if L = 1);
 //   0 < l < L-1: alpha = s_w s_{a_l} / s_{a_{l+1}}, beta = b_l / s_{a_{l+1}};
 //   l = L-1 > 0: alpha = s_w s_{a_l}, beta = b_l (the FP32 input of the head).
 static __global__ void pack_fp8_kernel(const float* p32, uint8_t* wpk, int nin, int W, int L, const uint32_t* amax_bits) {
@@ -753,9 +811,9 @@ static __global__ void pack_fp8_kernel(const float* p32, uint8_t* wpk, int nin, 
     const float a_out = meas > 0.f ? fminf(meas, red_b[0]) : red_b[0] > 0.f ? red_b[0] : 1.f;
     const float s_in = a_in / 448.f, s_out = a_out / 448.f, s_w = red_w[0] > 0.f ? red_w[0] / 448.f : 1.f;
     float alpha, bscale;
-    if (l == 0) {
+    if (l == 0) {   // FP16 layer; its bias is added in the epilogue like the others
       alpha = L > 1 ? 1.f / s_out : 1.f;
-      bscale = 0.f;
+      bscale = alpha;
     } else if (l < L - 1) {
       alpha = s_w * s_in / s_out;
       bscale = 1.f / s_out;

@@ -27,17 +27,35 @@ def randomise_biases(model: dict, seed: int, s: float = 0.1):
     return model
 
 
-# Decoded-value bars of the tensor-core precisions, as a fraction of the band half-width
-# (absolute for fog densities).  FP16 (11 significant bits) and compensated BF16 (hi + lo
-# pairs, ~16 bits) meet the 2e-2 target.  Plain BF16 (8 significant bits per activation)
-# does not: its measured error on the test and bench models is 2.3e-2 to 2.5e-2 of the
-# half-width, so it is held to 5e-2 and its error is reported next to the others.  FP8
-# (E4M3 hidden layers, 4 significant bits) is coarser again: held to the half-width.
-TC_BARS = {1: 5e-2, 2: 1.0, 3: 2e-2, 4: 2e-2}
+# Decoded-value bar of the tensor-core precisions FP16, BF16 and compensated BF16, as a
+# fraction of the band half-width (absolute for fog densities): the 2e-2 target.  FP8 (E4M3
+# hidden layers, 4 significant bits) does not reach it; it is held to its own stated
+# arithmetic instead (tc_check).
+TC_BARS = {1: 2e-2, 3: 2e-2, 4: 2e-2}
+FP8 = 2
 
 
 def tc_bar(prec: int) -> float:
     return TC_BARS[prec]
+
+
+def tc_check(prec: int, om: dict, net: int, ijk: np.ndarray, got: np.ndarray):
+    """Network outputs `got` (in network units, i.e. decoded values / half-width) of a
+    tensor-core precision at voxel coordinates ijk: within tc_bar of the FP64 oracle, or for
+    FP8 against oracle/quant.py's statement of its arithmetic (99% of rows within 2e-4 of
+    max(scale, 1), every row within 0.2: a few E4M3 rounding flips)."""
+    from oracle import quant
+    want, scale = oracle_forward_scale(om, net, ijk)
+    if prec != FP8:
+        err = float(np.abs(np.asarray(got, np.float64) - want).max())
+        assert err <= tc_bar(prec), (prec, err)
+        return err
+    z = N.encode(codec.level_coords(om, net, ijk), codec.level_q(om, net))
+    lg = om["log2_extent"] - (3 if net == 0 else 0)
+    spec = quant.forward(om["nets"][net], z, prec, codec.level_q(om, net), lg)
+    dev = np.abs(np.asarray(got, np.float64) - spec) / np.maximum(scale, 1.0)
+    assert np.quantile(dev, 0.99) <= 2e-4 and dev.max() <= 0.2, (np.quantile(dev, 0.99), dev.max())
+    return float(np.abs(np.asarray(got, np.float64) - want).max())
 
 
 def round_bf16(a):

@@ -8,7 +8,7 @@ import torch
 
 import paper_2208_04448_b300 as nv
 from fixtures import workload
-from gpu_helpers import oracle_forward_scale, rel_err, tc_bar
+from gpu_helpers import oracle_forward_scale, rel_err, tc_check
 from oracle import blob, codec, vdb
 
 pytestmark = pytest.mark.gpu
@@ -42,7 +42,7 @@ def test_full_decode_topology_and_sampled_values(union1024, prec):
     if prec == 0:
         assert rel_err(pv / 3.0, want, scale).max() <= FP32_TOL
     else:
-        assert np.abs(pv - 3.0 * want).max() <= tc_bar(prec) * 3.0
+        tc_check(prec, om, codec.REG, pi, pv / 3.0)
     # decoding twice gives identical bits
     dijk2, dval2, _ = nv.decompress(m, prec)
     assert torch.equal(dval, dval2) and torch.equal(dijk, dijk2)

@@ -4,8 +4,8 @@ Bars (tolerances written per test): bit-exact for the tree build, the initial
 parameters, topology, compacted lists and patch-corrected masks; 1e-5
 relative (normalised by the head's dot-product scale) for FP32 network values;
 1e-4 relative for FP32 gradients; 2e-2 of the band half-width for the
-tensor-core precisions FP16 and compensated BF16, 5e-2 for plain BF16 (which
-misses the 2e-2 target; see gpu_helpers.TC_BARS).
+tensor-core precisions FP16, BF16 and compensated BF16 (gpu_helpers.TC_BARS); FP8 is
+checked against the arithmetic it states in test_gpu_precision.py.
 """
 import numpy as np
 import pytest
@@ -13,7 +13,7 @@ import torch
 
 import paper_2208_04448_b300 as nv
 from fixtures import query_points, workload
-from gpu_helpers import bf16_weight_sensitivity, oracle_forward_scale, randomise_biases, rel_err, round_bf16, tc_bar
+from gpu_helpers import bf16_weight_sensitivity, oracle_forward_scale, randomise_biases, rel_err, round_bf16, tc_bar, tc_check
 from oracle import blob, codec, vdb
 from oracle import nets as N
 
@@ -135,26 +135,6 @@ def test_mlp_eval_parity(sphere128, shape, prec):
             assert rel_err(got, want, scale).max() <= FP32_TOL
         else:
             assert (np.abs(got - want) / np.maximum(scale, 1.0)).max() <= tc_bar(prec)
-
-
-@pytest.mark.parametrize("shape", [([32, 32, 32], [3, 3, 3], None), ([32, 64, 64], [2, 4, 4], [32, 64]),
-                                   ([64, 32, 64], [3, 3, 4], [64, 64])])
-def test_fp8_eval_tracks_oracle(sphere128, shape):
-    """FP8 (E4M3 hidden layers, 4 significant bits) misses the 2e-2 bar; its error is
-    reported and held to tc_bar(FP8).  Its output must still follow the FP64 oracle closely
-    (correlation), which a wrong operand layout or scale would break."""
-    ijk, val, ref = sphere128
-    om, m = _imported(ref, 5, *shape)
-    r = np.random.default_rng(2)
-    pts = np.concatenate([ref["ijk"][r.integers(0, ref["n"], 1000)], r.integers(0, 128, (333, 3))]).astype(np.int32)
-    for net in range(3):
-        want, scale = oracle_forward_scale(om, net, pts)
-        got = nv.mlp_eval(m, net, _cuda(pts, torch.int32), nv.FP8_E4M3).cpu().numpy()
-        err = np.abs(got - want) / np.maximum(scale, 1.0)
-        corr = float(np.corrcoef(got, want)[0, 1])
-        print(f"fp8 shape {shape[0]} net {net}: max err {err.max():.3g} rms {np.sqrt(np.mean(err ** 2)):.3g} corr {corr:.4f}")
-        assert corr > 0.9
-        assert err.max() <= tc_bar(nv.FP8_E4M3)
 
 
 # ---------------------------------------------------------------------------- gradients
@@ -310,7 +290,7 @@ def test_decompress_parity(name):
         if prec == 0:
             assert rel_err(dval / 3.0, want, scale).max() <= FP32_TOL
         else:
-            assert np.abs(dval - 3.0 * want).max() <= tc_bar(prec) * 3.0
+            tc_check(prec, om, 2, dijk, dval / 3.0)
 
 
 def test_patches_match_oracle_decisions(sphere128):

@@ -7,7 +7,7 @@ import torch
 
 import paper_2208_04448_b300 as nv
 from fixtures import workload
-from gpu_helpers import oracle_forward_scale, rel_err, tc_bar
+from gpu_helpers import oracle_forward_scale, rel_err, tc_check
 from oracle import blob, codec, vdb
 from oracle import nets as N
 
@@ -41,11 +41,10 @@ def test_shapes_train_and_decode(union, shape, train_prec):
     for prec in (0, 1, 2, 3, 4):
         dijk, dval, cnt = nv.decompress(m, prec)
         assert cnt == [ref["n"]] and np.array_equal(dijk.cpu().numpy(), ref["ijk"])
-        err = np.abs(dval.cpu().numpy() / 3.0 - want)
         if prec == 0:
             assert rel_err(dval.cpu().numpy() / 3.0, want, scale).max() <= 1e-5
         else:
-            assert err.max() <= tc_bar(prec)
+            tc_check(prec, om, codec.REG, ref["ijk"], dval.cpu().numpy() / 3.0)
 
 
 @pytest.mark.parametrize("shape", range(len(SHAPES)))
