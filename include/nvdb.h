@@ -198,8 +198,11 @@ nvdb_status nvdb_decompress_plan(const nvdb_model* const* models, int n_models, 
 nvdb_status nvdb_plan_launch(nvdb_plan* plan, nvdb_stream stream);
 /* Synchronise `stream` and report device-detected errors of the last launch. */
 nvdb_status nvdb_plan_check(nvdb_plan* plan, nvdb_stream stream);
-/* Tuning result: tensor-core CTAs per SM chosen (0 = limit) and its decode time. */
-nvdb_status nvdb_plan_info(const nvdb_plan* plan, int* tc_ctas_per_sm, float* tuned_ms);
+/* Tuning result (HOST outputs, any may be NULL): tensor-core CTAs per SM chosen (0 = the
+ * kernel's limit), the kernel variant chosen (0: 128 threads per tile; 1: 256 threads per
+ * tile, each half of the accumulator columns in its own warps, origins staged one tile
+ * ahead by bulk copies), and the tuned decode time in ms. */
+nvdb_status nvdb_plan_info(const nvdb_plan* plan, int* tc_ctas_per_sm, int* tc_variant, float* tuned_ms);
 nvdb_status nvdb_plan_free(nvdb_plan* plan);
 
 /* Random access on [Hash,5,4,NN(3)] (Section 3.5, online random access): for

@@ -229,9 +229,9 @@ class Plan:
         _check(lib().nvdb_plan_check(self._h, _stream(stream)))
 
     def info(self) -> dict:
-        occ, ms = C.c_int(), C.c_float()
-        _check(lib().nvdb_plan_info(self._h, C.byref(occ), C.byref(ms)))
-        return dict(tc_ctas_per_sm=occ.value, tuned_ms=ms.value)
+        occ, var, ms = C.c_int(), C.c_int(), C.c_float()
+        _check(lib().nvdb_plan_info(self._h, C.byref(occ), C.byref(var), C.byref(ms)))
+        return dict(tc_ctas_per_sm=occ.value, tc_variant=var.value, tuned_ms=ms.value)
 
     def __del__(self):
         if getattr(self, "_h", None) and _lib is not None:

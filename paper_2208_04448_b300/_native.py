@@ -49,7 +49,7 @@ SIGNATURES = {
     "nvdb_decompress_plan": ([C.POINTER(_vp), _i32, _i32, _vp, _vp, _i64, _vp, C.POINTER(_vp)], _st),
     "nvdb_plan_launch": ([_vp, _vp], _st),
     "nvdb_plan_check": ([_vp, _vp], _st),
-    "nvdb_plan_info": ([_vp, C.POINTER(C.c_int), C.POINTER(C.c_float)], _st),
+    "nvdb_plan_info": ([_vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_float)], _st),
     "nvdb_plan_free": ([_vp], _st),
     "nvdb_query": ([_vp, _vp, _i64, _i32, _vp, _vp, _vp], _st),
     "nvdb_mlp_eval": ([_vp, _i32, _i32, _vp, _i64, _vp, _vp], _st),

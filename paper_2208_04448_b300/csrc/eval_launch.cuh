@@ -3,6 +3,7 @@
 #pragma once
 #include <algorithm>
 
+#include "mlp_tc2.cuh"
 #include "runtime.cuh"
 
 namespace nvdb {
@@ -28,13 +29,33 @@ nvdb_status launch_tc(const EvalBatch& b, int64_t ntiles, const char* base, cuda
   return NVDB_OK;
 }
 
+template <int NIN, int W, int MODE>
+nvdb_status launch_tc2(const EvalBatch& b, int64_t ntiles, const char* base, cudaStream_t s) {
+  const Tc2Layout<NIN, W, MODE> lay(b.it[0].net.layers, batch_wlo(b));
+  TRY(set_smem_limit((const void*)mlp_tc2_kernel<NIN, W, MODE>, lay.total));
+  cudaFuncAttributes fa;
+  CU(cudaFuncGetAttributes(&fa, mlp_tc2_kernel<NIN, W, MODE>));
+  const int regs = std::max(8, (fa.numRegs + 7) & ~7);
+  const int by_regs = 65536 / (regs * kTc2Threads);
+  const int by_smem = (int)(kSmemPerSm / (lay.total + 1024));
+  int occ = std::min({by_regs, by_smem, TcCfg<NIN, W, MODE>::MAXC});
+  if (occ < 1) return fail(NVDB_ERR_UNSUPPORTED, "tensor-core kernel does not fit on an SM");
+  if (g_occ_override > 0) occ = std::min(occ, g_occ_override);
+  const int64_t grid = std::min<int64_t>(ntiles, (int64_t)num_sms() * occ);
+  KLAUNCH(eval_name(base, b.it[0].job.mode), s,
+          mlp_tc2_kernel<NIN, W, MODE><<<(unsigned)grid, kTc2Threads, lay.total, s>>>(b));
+  CU(cudaGetLastError());
+  return NVDB_OK;
+}
+
 template <int MODE>
 nvdb_status launch_tc_shape(const EvalBatch& b, int64_t ntiles, const char* base, cudaStream_t s) {
   const NetView& nv = b.it[0].net;
-  if (nv.n_in == 32 && nv.width == 32) return launch_tc<32, 32, MODE>(b, ntiles, base, s);
-  if (nv.n_in == 32 && nv.width == 64) return launch_tc<32, 64, MODE>(b, ntiles, base, s);
-  if (nv.n_in == 64 && nv.width == 32) return launch_tc<64, 32, MODE>(b, ntiles, base, s);
-  if (nv.n_in == 64 && nv.width == 64) return launch_tc<64, 64, MODE>(b, ntiles, base, s);
+  const bool v2 = tc_variant() == 1;
+  if (nv.n_in == 32 && nv.width == 32) return v2 ? launch_tc2<32, 32, MODE>(b, ntiles, base, s) : launch_tc<32, 32, MODE>(b, ntiles, base, s);
+  if (nv.n_in == 32 && nv.width == 64) return v2 ? launch_tc2<32, 64, MODE>(b, ntiles, base, s) : launch_tc<32, 64, MODE>(b, ntiles, base, s);
+  if (nv.n_in == 64 && nv.width == 32) return v2 ? launch_tc2<64, 32, MODE>(b, ntiles, base, s) : launch_tc<64, 32, MODE>(b, ntiles, base, s);
+  if (nv.n_in == 64 && nv.width == 64) return v2 ? launch_tc2<64, 64, MODE>(b, ntiles, base, s) : launch_tc<64, 64, MODE>(b, ntiles, base, s);
   return fail(NVDB_ERR_UNSUPPORTED, "network shape n=%d w=%d", nv.n_in, nv.width);
 }
 

@@ -362,9 +362,11 @@ __device__ __forceinline__ void relu_pair(float a, float b, bool comp, uint32_t&
 
 template <int NW>
 __device__ __forceinline__ void tmem_st_cols(uint32_t taddr, const uint32_t* r) {
+  static_assert(NW == 32 || NW == 16 || NW == 8 || NW == 4, "columns");
   if (NW == 32) tmem_st32(taddr, r);
   else if (NW == 16) tmem_st16(taddr, r);
-  else tmem_st8(taddr, r);
+  else if (NW == 8) tmem_st8(taddr, r);
+  else tmem_st4(taddr, r);
 }
 
 // Write one row of the A operand: NK 16-bit values (NK/2 packed columns) at the hi
@@ -405,8 +407,8 @@ __device__ __forceinline__ void l0_factors(const EvalJob& job, const uint32_t* s
 
 // Stage network `net` into shared memory: weight tiles, biases, head, Fourier matrix and
 // (level-0 lattice) the table T[f][dy*8+dz] = e^{i Phi(dy e_y + dz e_z)}.
-template <int NIN, int W, int MODE>
-__device__ __forceinline__ void tc_stage(const NetView& net, int mode, const TcLayout<NIN, W, MODE>& lay, uint8_t* smem) {
+template <int NIN, int W, int MODE, int NT = kTile, class Lay = TcLayout<NIN, W, MODE>>
+__device__ __forceinline__ void tc_stage(const NetView& net, int mode, const Lay& lay, uint8_t* smem) {
   using C = TcCfg<NIN, W, MODE>;
   constexpr int M = C::M;
   const int L = net.layers, tid = threadIdx.x;
@@ -421,27 +423,27 @@ __device__ __forceinline__ void tc_stage(const NetView& net, int mode, const TcL
     const size_t n0 = (size_t)W * C::K0 * 2 / 16, n1 = (size_t)(lay.w_bytes / 16) - n0;
     const uint4* s0 = reinterpret_cast<const uint4*>(net.wpk);
     const uint4* s1 = reinterpret_cast<const uint4*>(net.wpk + wpk_fp8_off(NIN, W, L));
-    for (size_t i = tid; i < n0; i += kTile) dst[i] = __ldg(s0 + i);
-    for (size_t i = tid; i < n1; i += kTile) dst[n0 + i] = __ldg(s1 + i);
+    for (size_t i = tid; i < n0; i += NT) dst[i] = __ldg(s0 + i);
+    for (size_t i = tid; i < n1; i += NT) dst[n0 + i] = __ldg(s1 + i);
   } else {
     const uint8_t* base = net.wpk + (MODE == TC_FP16 ? 0 : te * 2);
     const uint4* src = reinterpret_cast<const uint4*>(base);
     const size_t n16 = lay.ncopy * lay.w_bytes / 16;   // hi (or FP16) tiles, then the lo tiles
-    for (size_t i = tid; i < n16; i += kTile) dst[i] = __ldg(src + i);
+    for (size_t i = tid; i < n16; i += NT) dst[i] = __ldg(src + i);
   }
   for (int l = 0; l < L; ++l) {
     const int64_t bo = layer_offset(NIN, W, l) + (int64_t)W * (l == 0 ? NIN : W);
-    for (int o = tid; o < W; o += kTile) sb[l * W + o] = __ldg(net.p32 + bo + o);
+    for (int o = tid; o < W; o += NT) sb[l * W + o] = __ldg(net.p32 + bo + o);
   }
   const int64_t hoff = net_param_count(NIN, W, L) - W - 1;
-  for (int o = tid; o <= W; o += kTile) swh[o] = __ldg(net.p32 + hoff + o);
-  for (int i = tid; i < 3 * M; i += kTile) sq[i] = __ldg(net.q + i);
+  for (int o = tid; o <= W; o += NT) swh[o] = __ldg(net.p32 + hoff + o);
+  for (int i = tid; i < 3 * M; i += NT) sq[i] = __ldg(net.q + i);
   __syncthreads();
   if (mode == MODE_L0) {
     // entry (f, j) at [f / G][j][f % G], G = 4 (half2) or 2 (float2): one 16-byte load
     // gives a thread G consecutive frequencies of its (dy, dz)
     constexpr int G = C::ENC16 ? 4 : 2;
-    for (int i = tid; i < M * 64; i += kTile) {
+    for (int i = tid; i < M * 64; i += NT) {
       const int f = i >> 6, j = i & 63;
       const uint32_t ph = sq[3 * f + 1] * (uint32_t)(j >> 3) + sq[3 * f + 2] * (uint32_t)(j & 7);
       float sn, cs;
@@ -653,20 +655,25 @@ __global__ void __launch_bounds__(kTile, 4) mlp_tc_kernel(const __grid_constant_
         if (C::BIAS_MMA && NIN != W) store_bias_chunk<W>(tlane);   // equal widths: still in place
         tmem_st_wait();
       } else {
-        // FP32 head, two products per instruction, four independent partial sums
+        // FP32 head, two products per instruction.  The summation order is that of
+        // mlp_tc2_kernel (each half of the columns in two pair accumulators, then the
+        // halves added), so both variants give the same bits.
         const float4* swh4 = reinterpret_cast<const float4*>(swh);
-        float2 acc[4] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+        float part[2];
 #pragma unroll
-        for (int c = 0; c < W / 4; ++c) {
-          const float4 wv = swh4[c];
-          acc[(2 * c) & 3] = ffma2(make_float2(wv.x, wv.y),
-                                   make_float2(fmaxf(__uint_as_float(accu[4 * c]), 0.f), fmaxf(__uint_as_float(accu[4 * c + 1]), 0.f)),
-                                   acc[(2 * c) & 3]);
-          acc[(2 * c + 1) & 3] = ffma2(make_float2(wv.z, wv.w),
-                                       make_float2(fmaxf(__uint_as_float(accu[4 * c + 2]), 0.f), fmaxf(__uint_as_float(accu[4 * c + 3]), 0.f)),
-                                       acc[(2 * c + 1) & 3]);
+        for (int h = 0; h < 2; ++h) {
+          float2 acc[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+#pragma unroll
+          for (int c = h * (W / 8); c < (h + 1) * (W / 8); ++c) {
+            const float4 wv = swh4[c];
+            acc[0] = ffma2(make_float2(wv.x, wv.y),
+                           make_float2(fmaxf(__uint_as_float(accu[4 * c]), 0.f), fmaxf(__uint_as_float(accu[4 * c + 1]), 0.f)), acc[0]);
+            acc[1] = ffma2(make_float2(wv.z, wv.w),
+                           make_float2(fmaxf(__uint_as_float(accu[4 * c + 2]), 0.f), fmaxf(__uint_as_float(accu[4 * c + 3]), 0.f)), acc[1]);
+          }
+          part[h] = (acc[0].x + acc[0].y) + (acc[1].x + acc[1].y);
         }
-        y = bh + (((acc[0].x + acc[0].y) + (acc[1].x + acc[1].y)) + ((acc[2].x + acc[2].y) + (acc[3].x + acc[3].y)));
+        y = bh + (part[0] + part[1]);
       }
       tc_fence_before();
       if (__syncthreads_or(!ok)) { failed = true; break; }   // all threads agree on a timeout

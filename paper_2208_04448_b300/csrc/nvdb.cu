@@ -1715,7 +1715,7 @@ struct nvdb_plan {
   std::vector<DecodeScratch*> scratch;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
-  int occ = 0;
+  int occ = 0, variant = 1;
   float best_ms = 0.f;
   ~nvdb_plan() {
     if (exec) cudaGraphExecDestroy(exec);
@@ -1763,25 +1763,30 @@ extern "C" nvdb_status nvdb_decompress_plan(const nvdb_model* const* models, int
     cudaEvent_t a, b;
     CU(cudaEventCreate(&a));
     CU(cudaEventCreate(&b));
+    // candidates: kernel variant (0: 128 threads per tile, 1: 256 threads, split epilogue)
+    // x tensor-core CTAs per SM (0 = the kernel's own limit)
     float best = 1e30f;
-    int best_occ = 0;
-    const int cands[] = {0, 1, 2, 3, 4};
-    for (int c : cands) {
-      if (prec == NVDB_FP32 && c != 0) continue;
-      g_occ_override = c;
-      nvdb_status st = plan_run(p, s);                   // warm-up (and sizes the scratch)
-      if (st == NVDB_OK) {
-        cudaEventRecord(a, s);
-        st = plan_run(p, s);
-        cudaEventRecord(b, s);
+    int best_occ = 0, best_var = 1;
+    const int occs[] = {0, 2, 3};
+    for (int v = 0; v < 2; ++v)
+      for (int c : occs) {
+        if (prec == NVDB_FP32 && (c != 0 || v != 0)) continue;
+        g_occ_override = c;
+        g_variant_override = v;
+        nvdb_status st = plan_run(p, s);                   // warm-up (and sizes the scratch)
+        if (st == NVDB_OK) {
+          cudaEventRecord(a, s);
+          st = plan_run(p, s);
+          cudaEventRecord(b, s);
+        }
+        g_occ_override = 0;
+        g_variant_override = -1;
+        TRY(st);
+        CU(cudaEventSynchronize(b));
+        float ms = 0.f;
+        CU(cudaEventElapsedTime(&ms, a, b));
+        if (ms < best) { best = ms; best_occ = c; best_var = v; }
       }
-      g_occ_override = 0;
-      TRY(st);
-      CU(cudaEventSynchronize(b));
-      float ms = 0.f;
-      CU(cudaEventElapsedTime(&ms, a, b));
-      if (ms < best) { best = ms; best_occ = c; }
-    }
     cudaEventDestroy(a);
     cudaEventDestroy(b);
     for (auto* d : p->scratch) {
@@ -1790,17 +1795,20 @@ extern "C" nvdb_status nvdb_decompress_plan(const nvdb_model* const* models, int
       TRY(status_to_error(hst));
     }
     p->occ = best_occ;
+    p->variant = best_var;
     p->best_ms = best;
     // capture the tuned decode into a graph, on a stream of our own (the caller's may be
     // the legacy default stream, which cannot be captured); the stream is idle here
     cudaStream_t cs = nullptr;
     CU(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
     g_occ_override = best_occ;
+    g_variant_override = best_var;
     cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed);
     nvdb_status st = e == cudaSuccess ? plan_run(p, cs) : fail(NVDB_ERR_CUDA, "stream capture: %s", cudaGetErrorString(e));
     cudaGraph_t g = nullptr;
     if (e == cudaSuccess) e = cudaStreamEndCapture(cs, &g);
     g_occ_override = 0;
+    g_variant_override = -1;
     cudaStreamDestroy(cs);
     TRY(st);
     if (e != cudaSuccess) return fail(NVDB_ERR_CUDA, "stream capture: %s", cudaGetErrorString(e));
@@ -1831,9 +1839,10 @@ extern "C" nvdb_status nvdb_plan_check(nvdb_plan* p, nvdb_stream stream) {
   return NVDB_OK;
 }
 
-extern "C" nvdb_status nvdb_plan_info(const nvdb_plan* p, int* tc_ctas_per_sm, float* tuned_ms) {
+extern "C" nvdb_status nvdb_plan_info(const nvdb_plan* p, int* tc_ctas_per_sm, int* tc_variant, float* tuned_ms) {
   if (!p) return fail(NVDB_ERR_INVALID_ARG, "nvdb_plan_info: NULL plan");
   if (tc_ctas_per_sm) *tc_ctas_per_sm = p->occ;
+  if (tc_variant) *tc_variant = p->variant;
   if (tuned_ms) *tuned_ms = p->best_ms;
   return NVDB_OK;
 }

@@ -8,6 +8,7 @@
 #include <atomic>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -186,6 +187,18 @@ static FailWaitsHook g_fail_waits_hook(&set_fail_waits_here);
 // ---------------------------------------------------------------- per-precision launchers
 // Tensor-core CTAs per SM chosen by the decode-plan autotuner (0: from the kernel's limits).
 inline int g_occ_override = 0;
+// Tensor-core kernel variant: 0 = mlp_tc_kernel (128 threads per tile), 1 = mlp_tc2_kernel
+// (256 threads per tile, split epilogue, TMA-staged origins).  -1: the default, which the
+// environment variable NVDB_TC_VARIANT may set; the decode-plan autotuner overrides it.
+inline int g_variant_override = -1;
+inline int tc_variant() {
+  if (g_variant_override >= 0) return g_variant_override;
+  static const int v = [] {
+    const char* e = std::getenv("NVDB_TC_VARIANT");
+    return e && (e[0] == '0' || e[0] == '1') ? e[0] - '0' : 1;
+  }();
+  return v;
+}
 
 // One launch of the fused encode + MLP kernel over a batch of items of one network shape
 // (eval_f32.cu, eval_f16.cu, eval_bf16.cu, eval_bf16x3.cu, eval_fp8.cu).
