@@ -26,6 +26,7 @@ from __future__ import annotations
 
 import numpy as np
 
+from . import moe as MOE
 from . import nets as N
 from . import rng, vdb
 
@@ -45,7 +46,8 @@ def _lattice8(o):
 
 def default_opts(**kw) -> dict:
     o = dict(width=[32, 32, 32], layers=[3, 3, 3], ffm_size=None, sigma=10.0, seed=1,
-             steps=200, batch=4096, lr=1e-3, lr_decay=0.975, lr_interval=100, loss=N.LOSS_MSE)
+             steps=200, batch=4096, lr=1e-3, lr_decay=0.975, lr_interval=100, loss=N.LOSS_MSE,
+             subdomain=0, halo=8)
     o.update(kw)
     if o["ffm_size"] is None:
         o["ffm_size"] = [o["width"][0], max(o["width"][1], o["width"][2])]
@@ -56,17 +58,21 @@ def init_model(grid: dict, grid_class: int, half_width: float, opts: dict) -> di
     """Model with initial (untrained) networks and the grid's explicit upper tree."""
     origin, log2e = vdb.domain(grid["ijk"])
     E = 1 << log2e
+    moe = MOE.plan(grid["ijk"], origin, log2e, opts["subdomain"], opts["halo"]) if opts.get("subdomain") else None
+    if moe is not None:
+        E = moe["size"]          # each expert normalises over its subdomain (Section 3.4)
+    n_exp = 1 if moe is None else len(moe["origins"])
     ffm = opts["ffm_size"]
     q1 = rng.ffm_increments(opts["seed"], 1, ffm[0] // 2, opts["sigma"], E // 8)
     q0 = rng.ffm_increments(opts["seed"], 0, ffm[1] // 2, opts["sigma"], E)
-    nets = [rng.xavier_net(opts["seed"], k, ffm[0] if k == 0 else ffm[1], opts["width"][k], opts["layers"][k])
-            for k in range(3)]
+    nets = [rng.xavier_net(opts["seed"], 3 * e + k, ffm[0] if k == 0 else ffm[1], opts["width"][k], opts["layers"][k])
+            for e in range(n_exp) for k in range(3)]
     return dict(grid_class=grid_class, background=(half_width if grid_class == 0 else 0.0),
                 half_width=half_width, origin=origin, log2_extent=log2e, ffm_size=list(ffm),
                 width=list(opts["width"]), layers=list(opts["layers"]), q=[q1, q0], nets=nets,
                 l2_origin=grid["l2_origin"], l2_mask=grid["l2_mask"], n_l2=grid["l2_origin"].shape[0],
                 n_l1=grid["l1_origin"].shape[0], n_leaf=grid["leaf_origin"].shape[0], n_active=grid["n"],
-                patches={})
+                patches={}, moe=moe)
 
 
 def level_coords(model: dict, net: int, ijk: np.ndarray) -> np.ndarray:
@@ -80,7 +86,13 @@ def level_q(model: dict, net: int) -> np.ndarray:
 
 
 def evaluate(model: dict, net: int, ijk: np.ndarray, chunk: int = 1 << 16) -> np.ndarray:
-    """Raw network output at voxel coordinates (level-1 nets take leaf origins)."""
+    """Raw network output at voxel coordinates (level-1 nets take leaf origins); with a
+    domain decomposition, the gate-weighted average of the experts (oracle/moe.py)."""
+    if model.get("moe") is not None:
+        out = np.empty(len(ijk))
+        for a in range(0, len(ijk), chunk):
+            out[a:a + chunk] = MOE.evaluate(model, net, np.asarray(ijk)[a:a + chunk])
+        return out
     out = np.empty(len(ijk))
     for a in range(0, len(ijk), chunk):
         z = N.encode(level_coords(model, net, ijk[a:a + chunk]), level_q(model, net))
@@ -109,28 +121,33 @@ def population_size(grid: dict, net: int) -> int:
     return [grid["l1_origin"].shape[0] * 4096, grid["leaf_origin"].shape[0] * 512, grid["n"]][net]
 
 
-def train_net(grid: dict, model: dict, net: int, opts: dict, steps=None, log=None) -> list:
-    """Sparse-field training of one network with Adam (Section 3.2, Section 3.2.1)."""
-    p = model["nets"][net]
+def train_net(grid: dict, model: dict, net: int, opts: dict, steps=None, log=None, expert: int = 0) -> list:
+    """Sparse-field training of one network with Adam (Section 3.2, Section 3.2.1).  With a
+    domain decomposition, `expert`'s network on its support's candidates (oracle/moe.py)."""
+    moe = model.get("moe")
+    slot = 3 * expert + net
+    p = model["nets"][slot]
     theta = N.flatten(p)
     m = np.zeros_like(theta)
     v = np.zeros_like(theta)
     kind = N.LOSS_BCE if net != REG else opts["loss"]
     q = level_q(model, net)
-    npop = population_size(grid, net)
+    pop = None if moe is None else MOE.population(grid, model, expert, net)
+    npop = population_size(grid, net) if pop is None else len(pop)
     losses = []
     for t in range(1, (opts["steps"] if steps is None else steps) + 1):
-        idx = rng.sample_indices(opts["seed"], net, t, opts["batch"], npop)
-        ijk, lab = population(grid, model, net, idx)
+        idx = rng.sample_indices(opts["seed"], slot, t, opts["batch"], npop)
+        ijk, lab = population(grid, model, net, idx if pop is None else pop[idx])
         cur = N.unflatten(theta, p)
-        y, cache = N.forward(cur, N.encode(level_coords(model, net, ijk), q))
+        c = level_coords(model, net, ijk) if moe is None else MOE.expert_coords(model, expert, net, ijk)
+        y, cache = N.forward(cur, N.encode(c, q))
         loss, g = N.loss_and_grad(y, lab, kind)
         grads = N.backward(cur, cache, g)
         N.adam_step(theta, m, v, N.flatten(grads), t, N.lr_at(t, opts["lr"], opts["lr_decay"], opts["lr_interval"]))
         losses.append(loss)
         if log is not None:
             log(net, t, loss)
-    model["nets"][net] = N.unflatten(theta, p)
+    model["nets"][slot] = N.unflatten(theta, p)
     return losses
 
 

@@ -304,7 +304,7 @@ constexpr size_t kSmemPerSmDev = 233472;
 // not BF16 values, so the BF16 modes also stage the lo weight tiles.
 template <int NIN, int W, int MODE>
 struct TcLayout {
-  size_t w_bytes, t_off, p_off, b_off, wh_off, q_off, bar_off, slot_off, total;
+  size_t w_bytes, t_off, p_off, b_off, wh_off, q_off, org_off, bar_off, obar_off, slot_off, total;
   int ncopy;
   __host__ __device__ TcLayout(int L, bool wlo) {
     using C = TcCfg<NIN, W, MODE>;
@@ -317,8 +317,10 @@ struct TcLayout {
     b_off = p_off + (size_t)2 * 2 * C::M * 8;                // P tables, two buffers of [2][M] x 8 B
     wh_off = b_off + (size_t)L * W * 4;                      // FP32 biases [L][W]
     q_off = wh_off + (size_t)(W + 4) * 4;
-    bar_off = (q_off + (size_t)C::M * 12 + 7) & ~(size_t)7;
-    slot_off = bar_off + 8;
+    org_off = (q_off + (size_t)C::M * 12 + 15) & ~(size_t)15;   // two staged origins (int4)
+    bar_off = org_off + 32;
+    obar_off = bar_off + 8;
+    slot_off = obar_off + 16;
     total = slot_off + 8;
     // at most MAXC CTAs may be resident per SM (TMEM): make a (MAXC+1)-th not fit
     const size_t floor_bytes = kSmemPerSmDev / (C::MAXC + 1) - 1024 + 128;
@@ -474,10 +476,16 @@ __global__ void __launch_bounds__(kTile, 4) mlp_tc_kernel(const __grid_constant_
   float* swh = reinterpret_cast<float*>(smem + lay.wh_off);
   uint32_t* sq = reinterpret_cast<uint32_t*>(smem + lay.q_off);
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + lay.bar_off);
+  int4* sorg = reinterpret_cast<int4*>(smem + lay.org_off);
+  uint64_t* obar = reinterpret_cast<uint64_t*>(smem + lay.obar_off);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + lay.slot_off);
   const int tid = threadIdx.x, warp = tid >> 5;
 
-  if (tid == 0) mbar_init(bar, 1);
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    mbar_init(obar, 1);
+    mbar_init(obar + 1, 1);
+  }
   if (warp == 0) tmem_alloc(tslot, C::COLS);
   fence_proxy_async_smem();
   tc_fence_before();
@@ -500,7 +508,25 @@ __global__ void __launch_bounds__(kTile, 4) mlp_tc_kernel(const __grid_constant_
   int pbuf = 0;            // level-0 factor buffer of the current tile
   bool p_ready = false;    // its factors were computed during the previous tile
   const bool comp0 = comp_in<MODE>(0, L);
-  for (int64_t t0 = blockIdx.x; t0 < ntiles && !failed; t0 += gridDim.x) {
+  // Lattice modes: the node / leaf origin each tile reads is staged into shared memory by a
+  // bulk copy (the TMA unit) one tile ahead, alternating between two buffers, each with an
+  // mbarrier; counters of copies issued / waited for per buffer keep the phases.
+  const bool lattice = b.it[0].job.mode != MODE_LIST;   // one mode per launch (a decode stage)
+  auto origin_src = [&](int64_t g) -> const int4* {
+    const int mm = batch_find(b, g);
+    const int64_t tl = g - b.it[mm].tile_start;
+    return b.it[mm].job.nodes + (b.it[mm].job.mode == MODE_L1 ? (tl >> 5) : (tl >> 2));
+  };
+  uint32_t iss0 = 0u, iss1 = 0u, con0 = 0u, con1 = 0u;
+  if (lattice && (int64_t)blockIdx.x < ntiles) {
+    if (tid == 0) {
+      mbar_arrive_expect_tx(obar, 16);
+      bulk_g2s(sorg, origin_src(blockIdx.x), 16, obar);
+    }
+    iss0 = 1u;
+  }
+  int k = 0;               // tiles done by this CTA
+  for (int64_t t0 = blockIdx.x; t0 < ntiles && !failed; t0 += gridDim.x, ++k) {
     const int m = batch_find(b, t0);
     if (m != cur) {   // uniform across the CTA: restage the item's network
       __syncthreads();
@@ -518,6 +544,15 @@ __global__ void __launch_bounds__(kTile, 4) mlp_tc_kernel(const __grid_constant_
     const int64_t end_m = m + 1 < b.n ? b.it[m + 1].tile_start : ntiles;
     const bool next_same = job.mode == MODE_L0 && t0 + gridDim.x < end_m;
     const int64_t tn = t0 + gridDim.x - b.it[m].tile_start;
+    const int cb = k & 1, nb = cb ^ 1;    // origin buffers of this tile and the next
+    if (lattice && t0 + gridDim.x < ntiles) {   // the next tile's origin, one tile ahead
+      if (tid == 0) {
+        mbar_arrive_expect_tx(obar + nb, 16);
+        bulk_g2s(sorg + nb, origin_src(t0 + gridDim.x), 16, obar + nb);
+      }
+      if (nb) ++iss1; else ++iss0;
+    }
+    bool ok_enc = true;
     float2* sPc = sP + pbuf * 2 * M;
     // ---- encoding -> A operand (layer 0) in TMEM.  Inside this kernel the features are
     // ordered (cos_0, sin_0, cos_1, sin_1, ...): packed column f holds frequency f; the
@@ -528,7 +563,10 @@ __global__ void __launch_bounds__(kTile, 4) mlp_tc_kernel(const __grid_constant_
       if (job.mode == MODE_L0) {
         // angle addition: e^{i Phi(v)} = e^{i Phi(origin + dx e_x)} * e^{i Phi(dy e_y + dz e_z)}
         if (!p_ready) {
-          if (tid < 2 * M) l0_factors<M, MODE>(job, sq, __ldg(job.nodes + (t >> 2)), t, sPc, tid);
+          if (tid < 2 * M) {
+            ok_enc = mbar_wait_bounded(obar + cb, (cb ? con1 : con0) & 1u);
+            l0_factors<M, MODE>(job, sq, sorg[cb], t, sPc, tid);
+          }
           __syncthreads();
         }
         const int j = tid & 63;
@@ -566,7 +604,16 @@ __global__ void __launch_bounds__(kTile, 4) mlp_tc_kernel(const __grid_constant_
         }
       } else {
         int cx, cy, cz;
-        valid = job_coord(job, t, tid, cx, cy, cz);
+        if (job.mode == MODE_L1) {   // the staged origin of this tile's level-1 node
+          ok_enc = mbar_wait_bounded(obar + cb, (cb ? con1 : con0) & 1u);
+          const int4 o = sorg[cb];
+          const int sl = ((int)(t & 31) << 7) | tid;
+          cx = ((o.x - job.ox) >> 3) + (sl >> 8);
+          cy = ((o.y - job.oy) >> 3) + ((sl >> 4) & 15);
+          cz = ((o.z - job.oz) >> 3) + (sl & 15);
+        } else {
+          valid = job_coord(job, t, tid, cx, cy, cz);
+        }
         // MUFU sin/cos of the exact phase mapped to [-pi, pi): absolute error ~4e-7,
         // below the 16-bit operand rounding of both modes
 #pragma unroll
@@ -580,9 +627,12 @@ __global__ void __launch_bounds__(kTile, 4) mlp_tc_kernel(const __grid_constant_
       store_a_row<NIN>(tlane, hi, lo, comp0);
       if (C::BIAS_MMA) store_bias_chunk<NIN>(tlane);
     }
+    if (lattice && (job.mode == MODE_L1 || !p_ready)) {
+      if (cb) ++con1; else ++con0;
+    }
     tmem_st_wait();
     tc_fence_before();
-    __syncthreads();
+    if (__syncthreads_or(!ok_enc)) { failed = true; break; }
     float y = 0.f;
     for (int l = 0; l < L; ++l) {
       const int K = l == 0 ? NIN : W;                 // real columns; the tiles are K + 16 wide
@@ -609,9 +659,15 @@ __global__ void __launch_bounds__(kTile, 4) mlp_tc_kernel(const __grid_constant_
         }
         mma_commit(bar);
       }
-      if (l == 0 && next_same && tid < 2 * M)   // the next tile's factors, into the other buffer
-        l0_factors<M, MODE>(job, sq, __ldg(job.nodes + (tn >> 2)), tn, sP + (pbuf ^ 1) * 2 * M, tid);
-      const bool ok = mbar_wait_bounded(bar, phase);
+      bool ok = true;
+      if (l == 0 && next_same && tid < 2 * M) {   // the next tile's factors, into the other buffer
+        ok = mbar_wait_bounded(obar + nb, (nb ? con1 : con0) & 1u);
+        l0_factors<M, MODE>(job, sq, sorg[nb], tn, sP + (pbuf ^ 1) * 2 * M, tid);
+      }
+      if (l == 0 && next_same) {
+        if (nb) ++con1; else ++con0;
+      }
+      ok = mbar_wait_bounded(bar, phase) && ok;
       phase ^= 1u;
       tc_fence_after();
       uint32_t accu[W];
@@ -682,6 +738,12 @@ __global__ void __launch_bounds__(kTile, 4) mlp_tc_kernel(const __grid_constant_
     job_output(job, t, tid, valid, y);
     if (next_same) pbuf ^= 1;
     p_ready = next_same;
+  }
+  // copies still in flight (after a timeout): wait for them, bounded, before the shared
+  // memory they write is released
+  if (tid == 0 && lattice) {
+    for (; con0 < iss0 && !failed; ++con0) failed = !mbar_wait_bounded(obar, con0 & 1u);
+    for (; con1 < iss1 && !failed; ++con1) failed = !mbar_wait_bounded(obar + 1, con1 & 1u);
   }
   if (failed && tid == 0) set_status(b.it[0].job.status, ST_TIMEOUT);
   tc_fence_before();

@@ -195,7 +195,7 @@ inline int tc_variant() {
   if (g_variant_override >= 0) return g_variant_override;
   static const int v = [] {
     const char* e = std::getenv("NVDB_TC_VARIANT");
-    return e && (e[0] == '0' || e[0] == '1') ? e[0] - '0' : 1;
+    return e && (e[0] == '0' || e[0] == '1') ? e[0] - '0' : 0;
   }();
   return v;
 }
