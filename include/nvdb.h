@@ -103,6 +103,14 @@ typedef struct {
                            equal the same steps of an uninterrupted run bit for bit (same options;
                            the warm model must have been trained in this process, since exported
                            blobs carry no Adam state); 0 = warm start (weights only, Section 3.6) */
+  int32_t subdomain;    /* sparse domain decomposition (Section 3.4): subdomain size S in voxels, a
+                           multiple of 512; 0 = none (one network per level over the whole domain).
+                           Subdomains of a regular grid from the domain origin that hold voxels keep
+                           an expert each (the three networks, normalised over the subdomain); a
+                           point's output is the gate-weighted average of the experts whose clamped
+                           tent gate (subdomain plus halo) is non-zero there (Eq. 3).  A warm start
+                           takes the warm model's decomposition. */
+  int32_t halo;         /* halo width in voxels, a power of two in [8, S/4]; 0 = 8 */
 } nvdb_train_opts;
 
 typedef struct {
@@ -111,6 +119,8 @@ typedef struct {
   int32_t origin[3];     /* encoding domain origin (multiple of 128) */
   int32_t log2_extent;   /* encoding domain extent E = 2^log2_extent voxels */
   int64_t n_active, n_leaf, n_l1, n_l2;
+  int32_t n_experts;     /* models: experts of the domain decomposition (1 without one); grids: 0 */
+  int32_t subdomain;     /* models: subdomain size S (0 = no decomposition) */
 } nvdb_info;
 
 /* ------------------------------------------------------------------------ */
@@ -220,10 +230,12 @@ nvdb_status nvdb_plan_free(nvdb_plan* plan);
 nvdb_status nvdb_query(const nvdb_model* model, const float* d_xyz, int64_t n, nvdb_precision prec,
                        float* d_out, uint8_t* d_active, nvdb_stream stream);
 
-/* Raw output (logit or unscaled value) of network `net` at n voxel
+/* Raw output (logit or unscaled value) of network `net` (0, 1, 2) at n voxel
  * coordinates d_ijk int32 [n][3]; the level-1 classifier takes leaf origins
- * (its input is ijk >> 3).  d_out float [n].  FP32 does not synchronise; the
- * tensor-core precisions synchronise once to read the status word, as nvdb_query. */
+ * (its input is ijk >> 3).  For a decomposed model (Section 3.4) this is the
+ * gate-weighted average of its experts (Eq. 3), as decoding uses it.  d_out
+ * float [n].  FP32 does not synchronise; the tensor-core precisions synchronise
+ * once to read the status word, as nvdb_query. */
 nvdb_status nvdb_mlp_eval(const nvdb_model* model, int net, nvdb_precision prec, const int32_t* d_ijk,
                           int64_t n, float* d_out, nvdb_stream stream);
 
@@ -266,6 +278,8 @@ nvdb_status nvdb_mlp_grad(const nvdb_model* model, int net, nvdb_precision prec,
 nvdb_status nvdb_mlp_grad_static(const nvdb_model* model, int net, const int32_t* d_ijk, const float* d_target,
                                  int64_t n, int loss_kind, float* d_grad, float* loss, nvdb_stream stream);
 
+/* Network indices of the calls below (gradient, parameters, losses): network j of expert
+ * e is 3e + j, so 0, 1, 2 without a domain decomposition; 0 <= net < 3 n_experts. */
 int64_t nvdb_net_param_count(const nvdb_model* model, int net);
 
 /* Copy network `net`'s flat FP32 parameters (nvdb_net_param_count floats, storage order

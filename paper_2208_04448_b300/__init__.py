@@ -55,7 +55,7 @@ def _info(fn, h) -> dict:
     _check(fn(h, C.byref(i)))
     return dict(grid_class=i.grid_class, background=i.background, half_width=i.half_width,
                 origin=list(i.origin), log2_extent=i.log2_extent, n_active=i.n_active, n_leaf=i.n_leaf,
-                n_l1=i.n_l1, n_l2=i.n_l2)
+                n_l1=i.n_l1, n_l2=i.n_l2, n_experts=i.n_experts, subdomain=i.subdomain)
 
 
 class Grid:

@@ -24,13 +24,15 @@ class TrainOpts(C.Structure):
                 ("ffm_size", C.c_int32 * 2), ("ffm_sigma", C.c_float), ("steps", C.c_int32),
                 ("batch", C.c_int32), ("lr", C.c_float), ("lr_decay", C.c_float), ("lr_interval", C.c_int32),
                 ("loss", C.c_int32), ("train_prec", C.c_int32), ("patch_precs", C.c_uint32),
-                ("stop_window", C.c_int32), ("stop_loss", C.c_float * 3), ("resume", C.c_int32)]
+                ("stop_window", C.c_int32), ("stop_loss", C.c_float * 3), ("resume", C.c_int32),
+                ("subdomain", C.c_int32), ("halo", C.c_int32)]
 
 
 class Info(C.Structure):
     _fields_ = [("grid_class", C.c_int32), ("background", C.c_float), ("half_width", C.c_float),
                 ("origin", C.c_int32 * 3), ("log2_extent", C.c_int32), ("n_active", C.c_int64),
-                ("n_leaf", C.c_int64), ("n_l1", C.c_int64), ("n_l2", C.c_int64)]
+                ("n_leaf", C.c_int64), ("n_l1", C.c_int64), ("n_l2", C.c_int64), ("n_experts", C.c_int32),
+                ("subdomain", C.c_int32)]
 
 
 _vp, _i64, _i32, _f32p, _st = C.c_void_p, C.c_int64, C.c_int, C.POINTER(C.c_float), C.c_int

@@ -314,6 +314,34 @@ __global__ void emit_patches_kernel(const uint32_t* mis, int wpi, int64_t n_item
   }
 }
 
+// Membership in one expert's support (Section 3.4: a subdomain plus its halo), box [lo, hi)
+// in the level's units, of every element of a training population: net 0 the level-1
+// slots (index node * 4096 + slot, the slot's leaf coordinates tested), net 1 the leaves
+// (whole leaf inside; the box is leaf-aligned), net 2 the active voxels.
+__global__ void support_flags_kernel(int net, const int4* l1_origin, const int4* leaf_origin, const int32_t* ijk,
+                                     int64_t count, int4 lo, int4 hi, uint32_t* flags) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  int x, y, z, ext;
+  if (net == 0) {
+    const int4 o = l1_origin[i >> 12];
+    const int sl = (int)(i & 4095);
+    x = (o.x >> 3) + (sl >> 8); y = (o.y >> 3) + ((sl >> 4) & 15); z = (o.z >> 3) + (sl & 15); ext = 1;
+  } else if (net == 1) {
+    const int4 o = leaf_origin[i];
+    x = o.x; y = o.y; z = o.z; ext = 8;
+  } else {
+    x = ijk[3 * i]; y = ijk[3 * i + 1]; z = ijk[3 * i + 2]; ext = 1;
+  }
+  flags[i] = x >= lo.x && y >= lo.y && z >= lo.z && x + ext <= hi.x && y + ext <= hi.y && z + ext <= hi.z ? 1u : 0u;
+}
+
+// Indices of the set flags, in index order (off: exclusive scan of the flags).
+__global__ void compact_flags_kernel(const uint32_t* flags, const int64_t* off, int64_t count, uint32_t* out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < count && flags[i]) out[off[i]] = (uint32_t)i;
+}
+
 // ---------------------------------------------------------------- batched forms
 // Per-model tables passed by value; item g of the concatenation belongs to the
 // last model whose `start` is <= g.

@@ -8,14 +8,15 @@
 
 namespace nvdb {
 
-template <int NIN, int W, int MODE>
+template <int NIN, int W, int MODE, bool MOE = false>
 nvdb_status launch_tc(const EvalBatch& b, int64_t ntiles, const char* base, cudaStream_t s) {
+  if (!MOE && batch_moe(b)) return launch_tc<NIN, W, MODE, true>(b, ntiles, base, s);
   const TcLayout<NIN, W, MODE> lay(b.it[0].net.layers, batch_wlo(b));
-  TRY(set_smem_limit((const void*)mlp_tc_kernel<NIN, W, MODE>, lay.total));
+  TRY(set_smem_limit((const void*)mlp_tc_kernel<NIN, W, MODE, MOE>, lay.total));
   // Residency from the kernel's own limits (the runtime's occupancy query reports 1 for
   // kernels that allocate tensor memory): registers, shared memory, and TMEM columns.
   cudaFuncAttributes fa;
-  CU(cudaFuncGetAttributes(&fa, mlp_tc_kernel<NIN, W, MODE>));
+  CU(cudaFuncGetAttributes(&fa, mlp_tc_kernel<NIN, W, MODE, MOE>));
   const int regs = std::max(8, (fa.numRegs + 7) & ~7);
   const int by_regs = 65536 / (regs * kTile);
   const int by_smem = (int)(kSmemPerSm / (lay.total + 1024));
@@ -24,7 +25,7 @@ nvdb_status launch_tc(const EvalBatch& b, int64_t ntiles, const char* base, cuda
   if (g_occ_override > 0) occ = std::min(occ, g_occ_override);
   const int64_t grid = std::min<int64_t>(ntiles, (int64_t)num_sms() * occ);
   KLAUNCH(eval_name(base, b.it[0].job.mode), s,
-          mlp_tc_kernel<NIN, W, MODE><<<(unsigned)grid, kTile, lay.total, s>>>(b));
+          mlp_tc_kernel<NIN, W, MODE, MOE><<<(unsigned)grid, kTile, lay.total, s>>>(b));
   CU(cudaGetLastError());
   return NVDB_OK;
 }
@@ -51,7 +52,7 @@ nvdb_status launch_tc2(const EvalBatch& b, int64_t ntiles, const char* base, cud
 template <int MODE>
 nvdb_status launch_tc_shape(const EvalBatch& b, int64_t ntiles, const char* base, cudaStream_t s) {
   const NetView& nv = b.it[0].net;
-  const bool v2 = tc_variant() == 1;
+  const bool v2 = tc_variant() == 1 && !batch_moe(b);   // decomposed models: the 128-thread kernel
   if (nv.n_in == 32 && nv.width == 32) return v2 ? launch_tc2<32, 32, MODE>(b, ntiles, base, s) : launch_tc<32, 32, MODE>(b, ntiles, base, s);
   if (nv.n_in == 32 && nv.width == 64) return v2 ? launch_tc2<32, 64, MODE>(b, ntiles, base, s) : launch_tc<32, 64, MODE>(b, ntiles, base, s);
   if (nv.n_in == 64 && nv.width == 32) return v2 ? launch_tc2<64, 32, MODE>(b, ntiles, base, s) : launch_tc<64, 32, MODE>(b, ntiles, base, s);

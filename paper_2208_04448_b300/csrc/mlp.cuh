@@ -91,11 +91,65 @@ __device__ __forceinline__ void job_output(const EvalJob& j, int64_t t, int r, b
 // persistent CTA restages the network only when it crosses into another item.
 constexpr int kMaxBatch = 48;
 
+// Sparse domain decomposition (Section 3.4, Eq. 3) of one model: expert k's network of the
+// job's level is experts[k]; a row's output is sum_k G_k y_k / sum_k G_k over the kept
+// experts whose clamped-tent gate G_k is non-zero there (at most two subdomains per axis).
+// Coordinates are relative to the model's domain origin; the halo is a power of two >= 8.
+struct MoeView {
+  const NetView* experts;   // [n_exp] (device memory); nullptr: no decomposition
+  const int* expert_of;     // [dims^3] expert of each grid subdomain (x-major), -1 = discarded
+  const int4* origin;       // [n_exp] subdomain origins relative to the domain origin (voxels)
+  int n_exp, dims, size, halo;   // size, halo in voxels
+};
+
 struct EvalItem {
   NetView net;
   EvalJob job;
   int64_t tile_start;
+  MoeView moe;
 };
+
+// Gate of one axis at level coordinate `rel` for a subdomain starting at `a` (level units):
+// min(clamp((rel - a + h + 1/2) / 2h), clamp((a + S + h - 1/2 - rel) / 2h)); exact for a
+// power-of-two h.
+__device__ __forceinline__ float moe_axis_gate(int rel, int a, int S, int h) {
+  const float inv = 1.f / (float)(2 * h);
+  const float up = fminf(fmaxf(((float)(rel - a + h) + 0.5f) * inv, 0.f), 1.f);
+  const float dn = fminf(fmaxf(((float)(a + S + h - rel) - 0.5f) * inv, 0.f), 1.f);
+  return fminf(up, dn);
+}
+
+// The smallest kept expert id > last whose gate is non-zero at level coordinates r (INT_MAX
+// if none); `shift` = 3 for the level-1 classifier's leaf units.
+__device__ __forceinline__ int moe_next(const MoeView& v, int shift, int rx, int ry, int rz, int last) {
+  const int S = v.size >> shift, h = v.halo >> shift, n = v.dims;
+  int base[3], nb[3];
+  const int r[3] = {rx, ry, rz};
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    base[d] = r[d] / S;
+    const int off = r[d] - base[d] * S;
+    nb[d] = off < h && base[d] > 0 ? -1 : (S - off <= h && base[d] + 1 < n ? 1 : 0);
+  }
+  int best = 0x7FFFFFFF;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const int ix = base[0] + ((c >> 2) & 1) * nb[0], iy = base[1] + ((c >> 1) & 1) * nb[1], iz = base[2] + (c & 1) * nb[2];
+    if (((c >> 2) & 1 && !nb[0]) || ((c >> 1) & 1 && !nb[1]) || (c & 1 && !nb[2])) continue;
+    if (ix < 0 || iy < 0 || iz < 0 || ix >= n || iy >= n || iz >= n) continue;
+    const int e = __ldg(v.expert_of + (ix * n + iy) * n + iz);
+    if (e > last && e < best) best = e;
+  }
+  return best;
+}
+
+// Gate of expert e at level coordinates r (0 outside its support).
+__device__ __forceinline__ float moe_gate(const MoeView& v, int shift, int rx, int ry, int rz, int e) {
+  const int S = v.size >> shift, h = v.halo >> shift;
+  const int4 o = __ldg(v.origin + e);
+  return moe_axis_gate(rx, o.x >> shift, S, h) * moe_axis_gate(ry, o.y >> shift, S, h) *
+         moe_axis_gate(rz, o.z >> shift, S, h);
+}
 
 struct EvalBatch {
   int n;
@@ -196,23 +250,52 @@ __global__ void __launch_bounds__(kTile) mlp_f32_kernel(const __grid_constant__ 
   uint32_t* sq = reinterpret_cast<uint32_t*>(sp + ((P + 3) & ~3ll));
   int64_t n0;
   const int64_t ntiles = batch_total(b, n0);
-  int cur = -1;
+  __shared__ int smin;
+  const float* staged = nullptr;
+  auto stage = [&](const NetView& net) {   // uniform across the CTA
+    __syncthreads();
+    for (int64_t i = threadIdx.x; i < P; i += blockDim.x) sp[i] = __ldg(net.p32 + i);
+    for (int i = threadIdx.x; i < 3 * (NIN / 2); i += blockDim.x) sq[i] = __ldg(net.q + i);
+    __syncthreads();
+    staged = net.p32;
+  };
   for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const int m = batch_find(b, t);
-    if (m != cur) {   // uniform across the CTA
-      __syncthreads();
-      const NetView& net = b.it[m].net;
-      for (int64_t i = threadIdx.x; i < P; i += blockDim.x) sp[i] = __ldg(net.p32 + i);
-      for (int i = threadIdx.x; i < 3 * (NIN / 2); i += blockDim.x) sq[i] = __ldg(net.q + i);
-      __syncthreads();
-      cur = m;
-    }
+    const MoeView& mv = b.it[m].moe;
     EvalJob job = b.it[m].job;
     if (b.n == 1) job.n_items = n0;
     const int64_t tl = t - b.it[m].tile_start;
     int cx, cy, cz;
     const bool valid = job_coord(job, tl, threadIdx.x, cx, cy, cz);
-    const float y = forward_f32<NIN, W>(sp, sq, L, cx, cy, cz);
+    float y;
+    if (!mv.experts) {
+      if (staged != b.it[m].net.p32) stage(b.it[m].net);
+      y = forward_f32<NIN, W>(sp, sq, L, cx, cy, cz);
+    } else {
+      // decomposed model (Section 3.4): one pass per expert with a non-zero gate in the tile,
+      // ascending expert order, y = sum_k G_k y_k / sum_k G_k
+      const int shift = job.mode == MODE_L1 || job.shift == 3 ? 3 : 0;
+      float acc = 0.f, gs = 0.f;
+      for (int last = -1;;) {
+        const int mine = moe_next(mv, shift, cx, cy, cz, last);
+        if (threadIdx.x == 0) smin = 0x7FFFFFFF;
+        __syncthreads();
+        atomicMin(&smin, mine);
+        __syncthreads();
+        const int e = smin;
+        __syncthreads();
+        if (e == 0x7FFFFFFF) break;
+        const NetView ev = mv.experts[e];
+        if (staged != ev.p32) stage(ev);
+        const int4 eo = __ldg(mv.origin + e);
+        const float g = moe_gate(mv, shift, cx, cy, cz, e);
+        const float ye = forward_f32<NIN, W>(sp, sq, L, cx - (eo.x >> shift), cy - (eo.y >> shift), cz - (eo.z >> shift));
+        acc = fmaf(g, ye, acc);
+        gs += g;
+        last = e;
+      }
+      y = acc / gs;
+    }
     job_output(job, tl, threadIdx.x, valid, y);
   }
 }
@@ -304,7 +387,7 @@ constexpr size_t kSmemPerSmDev = 233472;
 // not BF16 values, so the BF16 modes also stage the lo weight tiles.
 template <int NIN, int W, int MODE>
 struct TcLayout {
-  size_t w_bytes, t_off, p_off, b_off, wh_off, q_off, org_off, bar_off, obar_off, slot_off, total;
+  size_t w_bytes, t_off, p_off, b_off, wh_off, q_off, org_off, bar_off, obar_off, slot_off, min_off, total;
   int ncopy;
   __host__ __device__ TcLayout(int L, bool wlo) {
     using C = TcCfg<NIN, W, MODE>;
@@ -317,21 +400,30 @@ struct TcLayout {
     b_off = p_off + (size_t)2 * 2 * C::M * 8;                // P tables, two buffers of [2][M] x 8 B
     wh_off = b_off + (size_t)L * W * 4;                      // FP32 biases [L][W]
     q_off = wh_off + (size_t)(W + 4) * 4;
-    org_off = (q_off + (size_t)C::M * 12 + 15) & ~(size_t)15;   // two staged origins (int4)
-    bar_off = org_off + 32;
+    org_off = (q_off + (size_t)C::M * 12 + 15) & ~(size_t)15;   // ring of four staged origins (int4)
+    bar_off = org_off + 64;
     obar_off = bar_off + 8;
-    slot_off = obar_off + 16;
-    total = slot_off + 8;
+    slot_off = obar_off + 32;
+    min_off = slot_off + 4;
+    total = min_off + 4;
     // at most MAXC CTAs may be resident per SM (TMEM): make a (MAXC+1)-th not fit
     const size_t floor_bytes = kSmemPerSmDev / (C::MAXC + 1) - 1024 + 128;
     if (total < floor_bytes) total = floor_bytes;
   }
 };
 
-// Does any model of the batch need the BF16 lo weight tiles?
+// Does any model of the batch need the BF16 lo weight tiles?  (A decomposed model's item
+// carries the experts' common wexact flag in its NetView.)
 __host__ __device__ inline bool batch_wlo(const EvalBatch& b) {
   for (int m = 0; m < b.n; ++m)
     if (!b.it[m].net.wexact) return true;
+  return false;
+}
+
+// Does any model of the batch use a domain decomposition?
+__host__ __device__ inline bool batch_moe(const EvalBatch& b) {
+  for (int m = 0; m < b.n; ++m)
+    if (b.it[m].moe.experts) return true;
   return false;
 }
 
@@ -410,7 +502,8 @@ __device__ __forceinline__ void l0_factors(const EvalJob& job, const uint32_t* s
 // Stage network `net` into shared memory: weight tiles, biases, head, Fourier matrix and
 // (level-0 lattice) the table T[f][dy*8+dz] = e^{i Phi(dy e_y + dz e_z)}.
 template <int NIN, int W, int MODE, int NT = kTile, class Lay = TcLayout<NIN, W, MODE>>
-__device__ __forceinline__ void tc_stage(const NetView& net, int mode, const Lay& lay, uint8_t* smem) {
+__device__ __forceinline__ void tc_stage(const NetView& net, int mode, const Lay& lay, uint8_t* smem,
+                                         bool table = true) {
   using C = TcCfg<NIN, W, MODE>;
   constexpr int M = C::M;
   const int L = net.layers, tid = threadIdx.x;
@@ -441,7 +534,7 @@ __device__ __forceinline__ void tc_stage(const NetView& net, int mode, const Lay
   for (int o = tid; o <= W; o += NT) swh[o] = __ldg(net.p32 + hoff + o);
   for (int i = tid; i < 3 * M; i += NT) sq[i] = __ldg(net.q + i);
   __syncthreads();
-  if (mode == MODE_L0) {
+  if (mode == MODE_L0 && table) {
     // entry (f, j) at [f / G][j][f % G], G = 4 (half2) or 2 (float2): one 16-byte load
     // gives a thread G consecutive frequencies of its (dy, dz)
     constexpr int G = C::ENC16 ? 4 : 2;
@@ -458,7 +551,9 @@ __device__ __forceinline__ void tc_stage(const NetView& net, int mode, const Lay
   fence_proxy_async_smem();   // the weight tiles are read by the tensor core (async proxy)
 }
 
-template <int NIN, int W, int MODE>
+// MOE: the batch holds decomposed models (Section 3.4); a separate instantiation, so the
+// undecomposed kernel carries none of the expert passes.
+template <int NIN, int W, int MODE, bool MOE = false>
 __global__ void __launch_bounds__(kTile, 4) mlp_tc_kernel(const __grid_constant__ EvalBatch b) {
   static_assert(W == 32 || W == 64, "width");
   static_assert(NIN == 32 || NIN == 64, "encoding size");
@@ -483,8 +578,7 @@ __global__ void __launch_bounds__(kTile, 4) mlp_tc_kernel(const __grid_constant_
 
   if (tid == 0) {
     mbar_init(bar, 1);
-    mbar_init(obar, 1);
-    mbar_init(obar + 1, 1);
+    for (int q = 0; q < 4; ++q) mbar_init(obar + q, 1);
   }
   if (warp == 0) tmem_alloc(tslot, C::COLS);
   fence_proxy_async_smem();
@@ -511,61 +605,106 @@ __global__ void __launch_bounds__(kTile, 4) mlp_tc_kernel(const __grid_constant_
   // Lattice modes: the node / leaf origin each tile reads is staged into shared memory by a
   // bulk copy (the TMA unit) one tile ahead, alternating between two buffers, each with an
   // mbarrier; counters of copies issued / waited for per buffer keep the phases.
-  const bool lattice = b.it[0].job.mode != MODE_LIST;   // one mode per launch (a decode stage)
+  // (decomposed models evaluate a tile once per expert, from __ldg origins, without either)
+  const bool moe_batch = MOE && batch_moe(b);
+  const bool lattice = b.it[0].job.mode != MODE_LIST && !moe_batch;   // one mode per launch (a decode stage)
   auto origin_src = [&](int64_t g) -> const int4* {
     const int mm = batch_find(b, g);
     const int64_t tl = g - b.it[mm].tile_start;
     return b.it[mm].job.nodes + (b.it[mm].job.mode == MODE_L1 ? (tl >> 5) : (tl >> 2));
   };
-  uint32_t iss0 = 0u, iss1 = 0u, con0 = 0u, con1 = 0u;
-  if (lattice && (int64_t)blockIdx.x < ntiles) {
+  int* smin = reinterpret_cast<int*>(smem + lay.min_off);   // block-wide minimum (experts)
+  const float* staged_p32 = nullptr;                          // the expert network staged
+  // ring of four buffers, each copy issued two tiles ahead: the CTA's tile k (k-th of its
+  // tiles) is in buffer k & 3 as that buffer's (k >> 2)-th copy, so its wait parity is
+  // (k >> 2) & 1; `issued` / `waited` count tiles for the drain on exit
+  int issued = 0, waited = 0;
+  auto issue = [&](int kk) {   // the copy of this CTA's kk-th tile, if it exists
+    const int64_t g = (int64_t)blockIdx.x + (int64_t)kk * gridDim.x;
+    if (g >= ntiles) return;
     if (tid == 0) {
-      mbar_arrive_expect_tx(obar, 16);
-      bulk_g2s(sorg, origin_src(blockIdx.x), 16, obar);
+      mbar_arrive_expect_tx(obar + (kk & 3), 16);
+      bulk_g2s(sorg + (kk & 3), origin_src(g), 16, obar + (kk & 3));
     }
-    iss0 = 1u;
+    issued = kk + 1;
+  };
+  if (lattice) {
+    issue(0);
+    issue(1);
   }
   int k = 0;               // tiles done by this CTA
   for (int64_t t0 = blockIdx.x; t0 < ntiles && !failed; t0 += gridDim.x, ++k) {
     const int m = batch_find(b, t0);
-    if (m != cur) {   // uniform across the CTA: restage the item's network
+    const MoeView& mv = b.it[m].moe;
+    const bool moe = MOE && mv.experts != nullptr;
+    if (m != cur && !moe) {   // uniform across the CTA: restage the item's network
       __syncthreads();
       tc_stage<NIN, W, MODE>(b.it[m].net, b.it[m].job.mode, lay, smem);
       __syncthreads();
       bh = swh[W];
       wexact = b.it[m].net.wexact != 0;
-      cur = m;
+      staged_p32 = b.it[m].net.p32;
     }
+    if (m != cur && moe) staged_p32 = nullptr;   // another model: its lattice table too
+    cur = m;
     EvalJob job = b.it[m].job;
     if (b.n == 1) job.n_items = n0;
     const int64_t t = t0 - b.it[m].tile_start;
     // the next tile of this CTA, if it is a level-0 tile of the same item: its factors are
     // computed while this tile's first-layer MMAs run
     const int64_t end_m = m + 1 < b.n ? b.it[m + 1].tile_start : ntiles;
-    const bool next_same = job.mode == MODE_L0 && t0 + gridDim.x < end_m;
+    const bool next_same = job.mode == MODE_L0 && t0 + gridDim.x < end_m && !moe_batch;
     const int64_t tn = t0 + gridDim.x - b.it[m].tile_start;
-    const int cb = k & 1, nb = cb ^ 1;    // origin buffers of this tile and the next
-    if (lattice && t0 + gridDim.x < ntiles) {   // the next tile's origin, one tile ahead
-      if (tid == 0) {
-        mbar_arrive_expect_tx(obar + nb, 16);
-        bulk_g2s(sorg + nb, origin_src(t0 + gridDim.x), 16, obar + nb);
-      }
-      if (nb) ++iss1; else ++iss0;
-    }
+    const int cb = k & 3, nb = (k + 1) & 3;   // origin buffers of this tile and the next
+    const uint32_t cpar = (uint32_t)(k >> 2) & 1u, npar = (uint32_t)((k + 1) >> 2) & 1u;
+    if (lattice) issue(k + 2);   // two tiles ahead; its buffer held tile k - 2, consumed by now
     bool ok_enc = true;
     float2* sPc = sP + pbuf * 2 * M;
+    bool valid = true;
+    // Decomposed model: the row's level coordinates relative to the domain origin, then one
+    // pass per expert with a non-zero gate somewhere in the tile, in ascending expert order
+    // (the same order for every row), accumulating G_k y_k and G_k.
+    const int shift = job.mode == MODE_L1 || job.shift == 3 ? 3 : 0;
+    int rx = 0, ry = 0, rz = 0;
+    if (moe) valid = job_coord(job, t, tid, rx, ry, rz);
+    const int dox = job.ox, doy = job.oy, doz = job.oz;
+    float macc = 0.f, mgs = 0.f, mg = 0.f, y = 0.f;
+    for (int pass = 0, last = -1;; ++pass) {
+    if (moe) {
+      const int mine = moe_next(mv, shift, rx, ry, rz, last);
+      if (tid == 0) *smin = 0x7FFFFFFF;
+      __syncthreads();
+      atomicMin(smin, mine);
+      __syncthreads();
+      const int e = *smin;
+      __syncthreads();
+      if (e == 0x7FFFFFFF) break;
+      const NetView ev = mv.experts[e];
+      if (ev.p32 != staged_p32) {   // uniform: restage (the level's lattice table is shared)
+        tc_stage<NIN, W, MODE>(ev, job.mode, lay, smem, staged_p32 == nullptr);
+        __syncthreads();
+        bh = swh[W];
+        wexact = ev.wexact != 0;
+        staged_p32 = ev.p32;
+      }
+      const int4 eo = __ldg(mv.origin + e);
+      job.ox = dox + eo.x; job.oy = doy + eo.y; job.oz = doz + eo.z;
+      mg = moe_gate(mv, shift, rx, ry, rz, e);
+      last = e;
+    } else if (pass > 0) {
+      break;
+    }
     // ---- encoding -> A operand (layer 0) in TMEM.  Inside this kernel the features are
     // ordered (cos_0, sin_0, cos_1, sin_1, ...): packed column f holds frequency f; the
     // first-layer weight tile is packed with the matching column order.
-    bool valid = true;
     {
       uint32_t hi[NIN / 2], lo[NIN / 2];
       if (job.mode == MODE_L0) {
         // angle addition: e^{i Phi(v)} = e^{i Phi(origin + dx e_x)} * e^{i Phi(dy e_y + dz e_z)}
         if (!p_ready) {
           if (tid < 2 * M) {
-            ok_enc = mbar_wait_bounded(obar + cb, (cb ? con1 : con0) & 1u);
-            l0_factors<M, MODE>(job, sq, sorg[cb], t, sPc, tid);
+            if (lattice) ok_enc = mbar_wait_bounded(obar + cb, cpar);
+            l0_factors<M, MODE>(job, sq, lattice ? sorg[cb] : __ldg(job.nodes + (t >> 2)), t, sPc, tid);
           }
           __syncthreads();
         }
@@ -604,8 +743,8 @@ __global__ void __launch_bounds__(kTile, 4) mlp_tc_kernel(const __grid_constant_
         }
       } else {
         int cx, cy, cz;
-        if (job.mode == MODE_L1) {   // the staged origin of this tile's level-1 node
-          ok_enc = mbar_wait_bounded(obar + cb, (cb ? con1 : con0) & 1u);
+        if (job.mode == MODE_L1 && lattice) {   // the staged origin of this tile's level-1 node
+          ok_enc = mbar_wait_bounded(obar + cb, cpar);
           const int4 o = sorg[cb];
           const int sl = ((int)(t & 31) << 7) | tid;
           cx = ((o.x - job.ox) >> 3) + (sl >> 8);
@@ -627,13 +766,10 @@ __global__ void __launch_bounds__(kTile, 4) mlp_tc_kernel(const __grid_constant_
       store_a_row<NIN>(tlane, hi, lo, comp0);
       if (C::BIAS_MMA) store_bias_chunk<NIN>(tlane);
     }
-    if (lattice && (job.mode == MODE_L1 || !p_ready)) {
-      if (cb) ++con1; else ++con0;
-    }
+    if (lattice && (job.mode == MODE_L1 || !p_ready)) waited = k + 1;
     tmem_st_wait();
     tc_fence_before();
     if (__syncthreads_or(!ok_enc)) { failed = true; break; }
-    float y = 0.f;
     for (int l = 0; l < L; ++l) {
       const int K = l == 0 ? NIN : W;                 // real columns; the tiles are K + 16 wide
       if (tid == 0 && MODE == TC_FP8 && l > 0) {   // E4M3 hidden layer: K = W, 32 per MMA
@@ -661,12 +797,10 @@ __global__ void __launch_bounds__(kTile, 4) mlp_tc_kernel(const __grid_constant_
       }
       bool ok = true;
       if (l == 0 && next_same && tid < 2 * M) {   // the next tile's factors, into the other buffer
-        ok = mbar_wait_bounded(obar + nb, (nb ? con1 : con0) & 1u);
+        ok = mbar_wait_bounded(obar + nb, npar);
         l0_factors<M, MODE>(job, sq, sorg[nb], tn, sP + (pbuf ^ 1) * 2 * M, tid);
       }
-      if (l == 0 && next_same) {
-        if (nb) ++con1; else ++con0;
-      }
+      if (l == 0 && next_same) waited = k + 2;
       ok = mbar_wait_bounded(bar, phase) && ok;
       phase ^= 1u;
       tc_fence_after();
@@ -735,16 +869,21 @@ __global__ void __launch_bounds__(kTile, 4) mlp_tc_kernel(const __grid_constant_
       if (__syncthreads_or(!ok)) { failed = true; break; }   // all threads agree on a timeout
     }
     if (failed) break;
+    if (moe) {
+      macc = fmaf(mg, y, macc);
+      mgs += mg;
+    }
+    }   // expert passes
+    if (failed) break;
+    if (moe) y = macc / mgs;
     job_output(job, t, tid, valid, y);
     if (next_same) pbuf ^= 1;
     p_ready = next_same;
   }
   // copies still in flight (after a timeout): wait for them, bounded, before the shared
   // memory they write is released
-  if (tid == 0 && lattice) {
-    for (; con0 < iss0 && !failed; ++con0) failed = !mbar_wait_bounded(obar, con0 & 1u);
-    for (; con1 < iss1 && !failed; ++con1) failed = !mbar_wait_bounded(obar + 1, con1 & 1u);
-  }
+  if (tid == 0 && lattice)
+    for (; waited < issued && !failed; ++waited) failed = !mbar_wait_bounded(obar + (waited & 3), (uint32_t)(waited >> 2) & 1u);
   if (failed && tid == 0) set_status(b.it[0].job.status, ST_TIMEOUT);
   tc_fence_before();
   __syncthreads();

@@ -7,6 +7,7 @@
 #include <algorithm>
 #include <atomic>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <cmath>
 #include <cstdarg>
@@ -226,13 +227,24 @@ struct nvdb_model {
   int64_t n_l2 = 0, n_l1 = 0, n_leaf = 0, n_active = 0;
   std::vector<uint32_t> q_host[2];
   uint32_t* q_dev[2] = {nullptr, nullptr};
-  DevNet net[3];
+  // Networks: expert e's network j (0 level-1 classifier, 1 level-0 classifier, 2 regressor)
+  // is net[3e + j]; one expert unless the domain is decomposed (Section 3.4).
+  int n_exp = 1;
+  std::unique_ptr<DevNet[]> net{new DevNet[3]};
+  std::vector<std::vector<float>> losses = std::vector<std::vector<float>>(3);
+  // Sparse domain decomposition: subdomain size (0 = none) and halo in voxels, grid of
+  // dims^3 subdomains from the domain origin, expert of each (-1 discarded), expert origins
+  // relative to the domain origin; per level, the experts' network views (device).
+  int sub_size = 0, sub_halo = 0, sub_dims = 0;
+  std::vector<int32_t> expert_of_host, exp_origin_host;
+  int* expert_of = nullptr;
+  int4* exp_origin = nullptr;
+  NetView* exp_views[3] = {nullptr, nullptr, nullptr};
   std::vector<int32_t> l2_origin_host;
   std::vector<uint64_t> l2_mask_host;
   int4* l2_origin = nullptr;
   unsigned long long* l2_mask = nullptr;
   std::vector<PatchSet> patches;
-  std::vector<float> losses[3];
   uint32_t* status = nullptr;
   DecodeScratch ds;
   QueryCache qc;
@@ -241,8 +253,17 @@ struct nvdb_model {
   int64_t partial_cap = 0;
   ~nvdb_model() {
     dfree(q_dev[0]); dfree(q_dev[1]); dfree(l2_origin); dfree(l2_mask); dfree(status); dfree(partial);
+    dfree(expert_of); dfree(exp_origin);
+    for (auto& v : exp_views) dfree(v);
     for (auto& p : patches) p.release();
     qc.release();
+  }
+  bool moe() const { return sub_size > 0; }
+  int n_net() const { return 3 * n_exp; }
+  void set_experts(int n) {
+    n_exp = n;
+    net.reset(new DevNet[3 * n]);
+    losses.assign(3 * n, {});
   }
   const PatchSet* patch_set(int prec) const {
     for (auto& p : patches)
@@ -256,6 +277,7 @@ struct nvdb_model {
 namespace {
 bool supported_shape(int nin, int w) { return (nin == 32 || nin == 64) && (w == 32 || w == 64); }
 
+// View of network k (expert k / 3, level k % 3).
 NetView net_view(const nvdb_model* m, int k) {
   NetView v;
   v.n_in = m->net[k].n_in;
@@ -263,9 +285,53 @@ NetView net_view(const nvdb_model* m, int k) {
   v.layers = m->net[k].layers;
   v.p32 = m->net[k].p32;
   v.wpk = m->net[k].wpk;
-  v.q = m->q_dev[k == 0 ? 0 : 1];
+  v.q = m->q_dev[k % 3 == 0 ? 0 : 1];
   v.wexact = m->net[k].bf16_exact ? 1 : 0;
   return v;
+}
+
+// Level j's view for a decode item: the decomposition's experts when there is one (the
+// item's NetView then carries expert 0's shape and the experts' common wexact flag).
+MoeView moe_view(const nvdb_model* m, int j) {
+  MoeView v{};
+  if (!m->moe()) return v;
+  v.experts = m->exp_views[j];
+  v.expert_of = m->expert_of;
+  v.origin = m->exp_origin;
+  v.n_exp = m->n_exp;
+  v.dims = m->sub_dims;
+  v.size = m->sub_size;
+  v.halo = m->sub_halo;
+  return v;
+}
+
+// Device copies of the experts' views (after the networks' buffers or flags change).
+nvdb_status upload_views(nvdb_model* m, cudaStream_t s) {
+  if (!m->moe()) return NVDB_OK;
+  for (int j = 0; j < 3; ++j) {
+    std::vector<NetView> h(m->n_exp);
+    for (int e = 0; e < m->n_exp; ++e) h[e] = net_view(m, 3 * e + j);
+    if (!m->exp_views[j]) TRY(dalloc(&m->exp_views[j], (size_t)m->n_exp));
+    CU(cudaMemcpyAsync(m->exp_views[j], h.data(), h.size() * sizeof(NetView), cudaMemcpyHostToDevice, s));
+    CU(cudaStreamSynchronize(s));   // h is a stack vector
+  }
+  return NVDB_OK;
+}
+
+// Geometry of a decomposition on the device (grid and origins from the host copies).
+nvdb_status upload_moe(nvdb_model* m, cudaStream_t s) {
+  if (!m->moe()) return NVDB_OK;
+  dfree(m->expert_of);
+  dfree(m->exp_origin);
+  TRY(dalloc(&m->expert_of, m->expert_of_host.size()));
+  TRY(dalloc(&m->exp_origin, (size_t)m->n_exp));
+  std::vector<int4> o(m->n_exp);
+  for (int e = 0; e < m->n_exp; ++e)
+    o[e] = make_int4(m->exp_origin_host[3 * e], m->exp_origin_host[3 * e + 1], m->exp_origin_host[3 * e + 2], 0);
+  CU(cudaMemcpyAsync(m->expert_of, m->expert_of_host.data(), m->expert_of_host.size() * 4, cudaMemcpyHostToDevice, s));
+  CU(cudaMemcpyAsync(m->exp_origin, o.data(), o.size() * sizeof(int4), cudaMemcpyHostToDevice, s));
+  CU(cudaStreamSynchronize(s));
+  return NVDB_OK;
 }
 
 // Precisions are 0 .. kNumPrecisions-1.
@@ -299,6 +365,9 @@ nvdb_status launch_batch(EvalBatch& b, nvdb_precision prec, cudaStream_t s) {
 EvalItem eval_item(const nvdb_model* m, int k, EvalJob job) {
   EvalItem it{};
   it.net = net_view(m, k);
+  it.moe = moe_view(m, k);
+  for (int e = 1; e < m->n_exp && m->moe(); ++e)
+    if (!m->net[3 * e + k].bf16_exact) it.net.wexact = 0;
   job.ox = m->origin[0];
   job.oy = m->origin[1];
   job.oz = m->origin[2];
@@ -331,9 +400,10 @@ bool train_prec_ok(int prec) { return prec == NVDB_FP32 || prec == NVDB_BF16; }
 
 nvdb_status launch_train(const nvdb_model* m, int k, int prec, TrainJob job, int grid, cudaStream_t s) {
   const NetView nv = net_view(m, k);
-  job.ox = m->origin[0];
-  job.oy = m->origin[1];
-  job.oz = m->origin[2];
+  const int e = k / 3;   // an expert normalises over its subdomain (Section 3.4)
+  job.ox = m->origin[0] + (m->moe() ? m->exp_origin_host[3 * e] : 0);
+  job.oy = m->origin[1] + (m->moe() ? m->exp_origin_host[3 * e + 1] : 0);
+  job.oz = m->origin[2] + (m->moe() ? m->exp_origin_host[3 * e + 2] : 0);
   if (!job.status) job.status = m->status;
   if (prec == NVDB_BF16) {
     return launch_train_tc(nv, job, grid, s);
@@ -381,9 +451,10 @@ nvdb_status eval_status(const nvdb_model* m, nvdb_precision prec, cudaStream_t s
 
 nvdb_status upload_net(nvdb_model* m, int k, const float* host_params, cudaStream_t s) {
   DevNet& d = m->net[k];
-  d.n_in = k == 0 ? m->ffm[0] : m->ffm[1];
-  d.width = m->width[k];
-  d.layers = m->layers[k];
+  const int j = k % 3;
+  d.n_in = j == 0 ? m->ffm[0] : m->ffm[1];
+  d.width = m->width[j];
+  d.layers = m->layers[j];
   d.P = net_param_count(d.n_in, d.width, d.layers);
   dfree(d.p32); dfree(d.wpk); dfree(d.m); dfree(d.v);
   TRY(dalloc(&d.p32, (size_t)d.P));
@@ -418,7 +489,12 @@ nvdb_status pack_net(nvdb_model* m, int k, cudaStream_t s) {
   if (!d.f8_amax) TRY(dalloc(&d.f8_amax, kMaxLayers));
   CU(cudaMemsetAsync(d.f8_amax, 0, kMaxLayers * 4, s));
   const NetView nv = net_view(m, k);
-  const int lg = k == 0 ? m->log2e - 3 : m->log2e;   // the level-1 classifier works in leaf units
+  // calibration domain: the model's extent, or the subdomain's (rounded up to a power of two)
+  int lgE = m->log2e;
+  if (m->moe())
+    for (lgE = 0; (1 << lgE) < m->sub_size; ++lgE) {
+    }
+  const int lg = k % 3 == 0 ? lgE - 3 : lgE;   // the level-1 classifier works in leaf units
   constexpr int kCalibPoints = 1 << 12;   // one point per thread of 32 blocks
   TRY(launch_calib_amax(nv, lg, 0xF8CA11Bull, kCalibPoints, d.f8_amax, s));
   KLAUNCH("pack_fp8", s, pack_fp8_kernel<<<1, 256, 0, s>>>(d.p32, d.wpk, d.n_in, d.width, d.layers, d.f8_amax));
@@ -530,6 +606,8 @@ extern "C" nvdb_status nvdb_grid_info(const nvdb_grid* g, nvdb_info* out) {
   out->n_leaf = g->n_leaf;
   out->n_l1 = g->n_l1;
   out->n_l2 = g->n_l2;
+  out->n_experts = 0;
+  out->subdomain = 0;
   return NVDB_OK;
 }
 
@@ -587,9 +665,59 @@ nvdb_status ensure_partial(nvdb_model* m, int64_t count) {
   return NVDB_OK;
 }
 
+// Training populations of one expert of a decomposed model (Section 3.4): per network, the
+// indices of the candidates inside the expert's support (level-1 slots, leaves, voxels).
+struct PopLists {
+  uint32_t* list[3] = {nullptr, nullptr, nullptr};
+  int64_t n[3] = {0, 0, 0};
+  ~PopLists() { for (auto& l : list) dfree(l); }
+};
+
+nvdb_status expert_populations(const nvdb_model* m, const nvdb_grid* g, int ex, PopLists& pl, cudaStream_t s) {
+  const Range range("expert populations");
+  for (int j = 0; j < 3; ++j) {
+    const int64_t count = j == 0 ? g->n_l1 * 4096 : j == 1 ? g->n_leaf : g->n;
+    const int sh = j == 0 ? 3 : 0;
+    int lo[3], hi[3];
+    for (int d = 0; d < 3; ++d) {
+      const int a = g->origin[d] + m->exp_origin_host[3 * ex + d];
+      lo[d] = (a >> sh) - (m->sub_halo >> sh);
+      hi[d] = ((a + m->sub_size) >> sh) + (m->sub_halo >> sh);
+    }
+    uint32_t* flags = nullptr;
+    int64_t* off = nullptr;
+    Scan sc;
+    auto run = [&]() -> nvdb_status {
+      TRY(dalloc(&flags, (size_t)count + 1));
+      TRY(dalloc(&off, (size_t)count + 1));
+      if (count)
+        KLAUNCH("support_flags", s, support_flags_kernel<<<blocks_for(count, 256), 256, 0, s>>>(
+                                        j, g->l1_origin, g->leaf_origin, g->ijk, count, make_int4(lo[0], lo[1], lo[2], 0),
+                                        make_int4(hi[0], hi[1], hi[2], 0), flags));
+      TRY(sc.run(flags, count, off, s));
+      int64_t total = 0;
+      CU(cudaMemcpyAsync(&total, sc.total, 8, cudaMemcpyDeviceToHost, s));
+      CU(cudaStreamSynchronize(s));
+      if (total == 0) return fail(NVDB_ERR_INVALID_ARG, "expert %d has no training candidates for network %d", ex, j);
+      TRY(dalloc(&pl.list[j], (size_t)total));
+      KLAUNCH("compact_flags", s, compact_flags_kernel<<<blocks_for(count, 256), 256, 0, s>>>(flags, off, count, pl.list[j]));
+      CU(cudaGetLastError());
+      pl.n[j] = total;
+      return NVDB_OK;
+    };
+    const nvdb_status st = run();
+    CU(cudaStreamSynchronize(s));
+    dfree(flags);
+    dfree(off);
+    TRY(st);
+  }
+  return NVDB_OK;
+}
+
 TrainJob grid_train_job(const nvdb_grid* g, int net, const nvdb_train_opts* o) {
   TrainJob j{};
   j.net = net;
+  j.stream = net;
   j.loss = net == 2 ? o->loss : LOSS_BCE;
   j.seed = o->seed;
   j.batch = o->batch;
@@ -667,6 +795,10 @@ extern "C" nvdb_status nvdb_compress(const nvdb_grid* g, const nvdb_train_opts* 
   if (g->n == 0) return fail(NVDB_ERR_INVALID_ARG, "nvdb_compress: empty grid");
   if ((uint64_t)g->n_leaf * 512 >= (1ull << 32) || (uint64_t)g->n_l1 * 4096 >= (1ull << 32))
     return fail(NVDB_ERR_UNSUPPORTED, "candidate population >= 2^32");
+  const int sub = warm ? warm->sub_size : o->subdomain;
+  const int halo = warm ? warm->sub_halo : (o->halo ? o->halo : 8);
+  if (sub < 0 || sub % 512 || (sub && (halo < 8 || (halo & (halo - 1)) || 4 * halo > sub)))
+    return fail(NVDB_ERR_INVALID_ARG, "subdomain must be a multiple of 512 and the halo a power of two in [8, subdomain/4]");
   *out = nullptr;
   cudaStream_t s = (cudaStream_t)stream;
   auto* m = new nvdb_model();
@@ -694,7 +826,45 @@ extern "C" nvdb_status nvdb_compress(const nvdb_grid* g, const nvdb_train_opts* 
                       m->layers[k], kTrainTcMaxLayers);
     TRY(dalloc(&m->status, 1));
     CU(cudaMemsetAsync(m->status, 0, 4, s));
-    const double E = std::ldexp(1.0, m->log2e);
+    double E = std::ldexp(1.0, m->log2e);
+    if (sub > 0) {   // sparse domain decomposition (Section 3.4): subdomains holding voxels
+      m->sub_size = sub;
+      m->sub_halo = halo;
+      m->sub_dims = (int)((std::ldexp(1.0, m->log2e) + sub - 1) / sub);
+      const int n = m->sub_dims;
+      if ((int64_t)n * n * n > (1 << 24)) return fail(NVDB_ERR_UNSUPPORTED, "more than 2^24 subdomains");
+      if (warm) {
+        m->expert_of_host = warm->expert_of_host;
+        m->exp_origin_host = warm->exp_origin_host;
+        m->set_experts(warm->n_exp);
+        if (g->origin[0] != warm->origin[0] || g->origin[1] != warm->origin[1] || g->origin[2] != warm->origin[2] ||
+            g->log2e != warm->log2e)
+          return fail(NVDB_ERR_INVALID_ARG, "warm start of a decomposed model: the grid's domain differs");
+      } else {
+        std::vector<int32_t> l1(3 * g->n_l1);
+        TRY(copy_int4_to3(g->l1_origin, g->n_l1, l1.data(), s));   // a level-1 node lies in one subdomain
+        std::vector<char> occ((size_t)n * n * n, 0);
+        for (int64_t i = 0; i < g->n_l1; ++i) {
+          const int ix = (l1[3 * i] - g->origin[0]) / sub, iy = (l1[3 * i + 1] - g->origin[1]) / sub,
+                    iz = (l1[3 * i + 2] - g->origin[2]) / sub;
+          occ[((size_t)ix * n + iy) * n + iz] = 1;
+        }
+        m->expert_of_host.assign((size_t)n * n * n, -1);
+        int ne = 0;
+        for (size_t c = 0; c < occ.size(); ++c)
+          if (occ[c]) {
+            m->expert_of_host[c] = ne++;
+            m->exp_origin_host.push_back((int32_t)(c / ((size_t)n * n)) * sub);
+            m->exp_origin_host.push_back((int32_t)((c / n) % n) * sub);
+            m->exp_origin_host.push_back((int32_t)(c % n) * sub);
+          }
+        m->set_experts(ne);
+      }
+      TRY(upload_moe(m, s));
+      E = sub;   // every expert normalises over its subdomain
+    } else if (warm && warm->moe()) {
+      return fail(NVDB_ERR_INVALID_ARG, "warm start: decomposition differs");
+    }
     for (int lev = 0; lev < 2; ++lev) {
       m->q_host[lev] = warm ? warm->q_host[lev]
                             : ffm_increments(o->seed, lev == 0 ? 1 : 0, m->ffm[lev] / 2, (double)o->ffm_sigma,
@@ -702,14 +872,15 @@ extern "C" nvdb_status nvdb_compress(const nvdb_grid* g, const nvdb_train_opts* 
       TRY(dalloc(&m->q_dev[lev], m->q_host[lev].size()));
       CU(cudaMemcpy(m->q_dev[lev], m->q_host[lev].data(), m->q_host[lev].size() * 4, cudaMemcpyHostToDevice));
     }
-    for (int k = 0; k < 3; ++k) {
+    for (int k = 0; k < m->n_net(); ++k) {
       if (warm) {
         TRY(upload_net(m, k, nullptr, s));
         const float* src = resume && warm->net[k].master ? warm->net[k].master : warm->net[k].p32;
         CU(cudaMemcpyAsync(m->net[k].p32, src, m->net[k].P * 4, cudaMemcpyDeviceToDevice, s));
         m->net[k].bf16_exact = warm->net[k].bf16_exact && o->steps == 0;
       } else {
-        const std::vector<float> p = xavier_params(o->seed, k, k == 0 ? m->ffm[0] : m->ffm[1], m->width[k], m->layers[k]);
+        const int j = k % 3;
+        const std::vector<float> p = xavier_params(o->seed, k, j == 0 ? m->ffm[0] : m->ffm[1], m->width[j], m->layers[j]);
         TRY(upload_net(m, k, p.data(), s));
         CU(cudaStreamSynchronize(s));
       }
@@ -755,10 +926,14 @@ extern "C" nvdb_status nvdb_compress(const nvdb_grid* g, const nvdb_train_opts* 
     };
     const int grid = train_grid(o->batch);
     const bool profiled = prof::g_on.load();
-    NetRun nr[3];
     int64_t poff[4] = {0, 0, 0, 0};
     for (int k = 0; k < 3; ++k) poff[k + 1] = poff[k] + (int64_t)grid * (m->net[k].P + 1);
     nvdb_status st = ensure_partial(m, poff[3]);
+    // a decomposed model trains expert after expert, each on the candidates of its support
+    for (int ex = 0; ex < m->n_exp && st == NVDB_OK; ++ex) {
+    PopLists pl;
+    if (m->moe() && o->steps > 0) st = expert_populations(m, g, ex, pl, s);
+    NetRun nr[3];
     for (int k = 0; k < 3 && st == NVDB_OK; ++k) {
       NetRun& r = nr[k];
       if (cudaStreamCreateWithFlags(&r.ts, cudaStreamNonBlocking) != cudaSuccess ||
@@ -773,11 +948,17 @@ extern "C" nvdb_status nvdb_compress(const nvdb_grid* g, const nvdb_train_opts* 
       if ((st = dalloc(&r.d_loss, (size_t)std::max(1, o->steps))) != NVDB_OK) break;
       if ((st = dalloc(&r.d_step, 2)) != NVDB_OK) break;
       r.job = grid_train_job(g, k, o);
+      r.job.stream = 3 * ex + k;
+      if (m->moe()) {
+        r.job.pop = pl.list[k];
+        r.job.pop_n = pl.n[k];
+        r.job.pop_shift = k == 1 ? 9 : 0;
+      }
       r.job.partial = m->partial + poff[k];
       r.job.step_dev = r.d_step;
-      if (o->train_prec == NVDB_BF16 && (st = pack_net(m, k, r.ts)) != NVDB_OK) break;   // the BF16 tiles of step 1
+      if (o->train_prec == NVDB_BF16 && (st = pack_net(m, 3 * ex + k, r.ts)) != NVDB_OK) break;   // the BF16 tiles of step 1
       // the first step of this call: after the interrupted run's steps when resuming
-      r.done = (int)m->losses[k].size();
+      r.done = (int)m->losses[3 * ex + k].size();
       const int first = r.done + 1;
       if (cudaMemcpyAsync(r.d_step, &first, 4, cudaMemcpyHostToDevice, r.ts) != cudaSuccess ||
           cudaStreamSynchronize(r.ts) != cudaSuccess) {   // `first` is a stack value
@@ -791,8 +972,8 @@ extern "C" nvdb_status nvdb_compress(const nvdb_grid* g, const nvdb_train_opts* 
     }
     auto one_step = [&](int k) -> nvdb_status {
       NetRun& r = nr[k];
-      DevNet& d = m->net[k];
-      TRY(launch_train(m, k, o->train_prec, r.job, grid, r.ts));
+      DevNet& d = m->net[3 * ex + k];
+      TRY(launch_train(m, 3 * ex + k, o->train_prec, r.job, grid, r.ts));
       KLAUNCH("adam_reduce", r.ts, adam_reduce_kernel<<<blocks_for(d.P + 1, 32), 32 * kRedGroups, 0, r.ts>>>(
                                        r.job.partial, grid, d.P, d.p32, d.m, d.v, 0, 0.f, nullptr, nullptr,
                                        1.f / (float)o->batch, adam_aux(d, o->train_prec, true), r.sc));
@@ -854,9 +1035,9 @@ extern "C" nvdb_status nvdb_compress(const nvdb_grid* g, const nvdb_train_opts* 
       NetRun& r = nr[k];
       if (r.exec) cudaGraphExecDestroy(r.exec);
       if (st == NVDB_OK) {
-        m->losses[k].resize(r.done + r.ran);
+        m->losses[3 * ex + k].resize(r.done + r.ran);
         if (r.ran) {
-          cudaError_t e = cudaMemcpyAsync(m->losses[k].data() + r.done, r.d_loss, r.ran * 4, cudaMemcpyDeviceToHost, r.ts);
+          cudaError_t e = cudaMemcpyAsync(m->losses[3 * ex + k].data() + r.done, r.d_loss, r.ran * 4, cudaMemcpyDeviceToHost, r.ts);
           if (e == cudaSuccess) e = cudaStreamSynchronize(r.ts);
           if (e != cudaSuccess) st = fail(NVDB_ERR_CUDA, "loss readback: %s", cudaGetErrorString(e));
         }
@@ -871,9 +1052,10 @@ extern "C" nvdb_status nvdb_compress(const nvdb_grid* g, const nvdb_train_opts* 
       dfree(r.d_step);
       dfree(r.d_loss);
     }
+    }   // experts
     TRY(st);
     if (o->train_prec == NVDB_BF16)   // the BF16 step trained BF16 weights: store them as such
-      for (int k = 0; k < 3; ++k) {
+      for (int k = 0; k < m->n_net(); ++k) {
         DevNet& d = m->net[k];
         const int64_t n = d.P - d.width - 1;   // every weight and bias except the FP32 head
         TRY(dalloc(&d.master, d.P));        // kept for a resumed run
@@ -882,7 +1064,8 @@ extern "C" nvdb_status nvdb_compress(const nvdb_grid* g, const nvdb_train_opts* 
         CU(cudaGetLastError());
         d.bf16_exact = true;
       }
-    for (int k = 0; k < 3; ++k) TRY(pack_net(m, k, s));
+    for (int k = 0; k < m->n_net(); ++k) TRY(pack_net(m, k, s));
+    TRY(upload_views(m, s));
     uint32_t pp = o->patch_precs ? o->patch_precs : (1u << NVDB_FP32);
     for (int p = 0; p < kNumPrecisions; ++p)
       if (pp & (1u << p)) {
@@ -900,7 +1083,7 @@ extern "C" nvdb_status nvdb_compress(const nvdb_grid* g, const nvdb_train_opts* 
 }
 
 extern "C" nvdb_status nvdb_model_losses(const nvdb_model* m, int net, float* losses, int64_t cap, int64_t* count) {
-  if (!m || net < 0 || net > 2 || (cap > 0 && !losses)) return fail(NVDB_ERR_INVALID_ARG, "nvdb_model_losses: bad arguments");
+  if (!m || net < 0 || net >= m->n_net() || (cap > 0 && !losses)) return fail(NVDB_ERR_INVALID_ARG, "nvdb_model_losses: bad arguments");
   const auto& l = m->losses[net];
   if (count) *count = (int64_t)l.size();
   for (int64_t i = 0; i < cap && i < (int64_t)l.size(); ++i) losses[i] = l[i];
@@ -1242,14 +1425,14 @@ extern "C" nvdb_status nvdb_mlp_eval(const nvdb_model* m, int net, nvdb_precisio
 }
 
 extern "C" int64_t nvdb_net_param_count(const nvdb_model* m, int net) {
-  if (!m || net < 0 || net > 2) return -1;
+  if (!m || net < 0 || net >= m->n_net()) return -1;
   return m->net[net].P;
 }
 
 extern "C" nvdb_status nvdb_mlp_grad(const nvdb_model* cm, int net, nvdb_precision prec, const int32_t* d_ijk,
                                      const float* d_target, int64_t n, int loss_kind, float* d_grad, float* loss,
                                      nvdb_stream stream) {
-  if (!cm || net < 0 || net > 2 || n <= 0 || !d_ijk || !d_target || !d_grad)
+  if (!cm || net < 0 || net >= cm->n_net() || n <= 0 || !d_ijk || !d_target || !d_grad)
     return fail(NVDB_ERR_INVALID_ARG, "nvdb_mlp_grad: bad arguments");
   if (!train_prec_ok(prec)) return fail(NVDB_ERR_UNSUPPORTED, "nvdb_mlp_grad: precision %d", (int)prec);
   if (loss_kind < 0 || loss_kind > 3) return fail(NVDB_ERR_INVALID_ARG, "unknown loss %d", loss_kind);
@@ -1261,7 +1444,8 @@ extern "C" nvdb_status nvdb_mlp_grad(const nvdb_model* cm, int net, nvdb_precisi
   TRY(ensure_partial(m, (int64_t)grid * (d.P + 1)));
   CU(cudaMemsetAsync(m->status, 0, 4, s));   // this call's device-side errors only
   TrainJob j{};
-  j.net = net;
+  j.net = net % 3;
+  j.stream = net;
   j.loss = loss_kind;
   j.step = 1;
   j.batch = n;
@@ -1345,19 +1529,20 @@ extern "C" nvdb_status nvdb_debug_wait_selftest(int64_t limit_ns) {
 
 // ============================================================================ parameters (autograd)
 extern "C" nvdb_status nvdb_net_params(const nvdb_model* m, int net, float* d_out, nvdb_stream stream) {
-  if (!m || net < 0 || net > 2 || !d_out) return fail(NVDB_ERR_INVALID_ARG, "nvdb_net_params: bad arguments");
+  if (!m || net < 0 || net >= m->n_net() || !d_out) return fail(NVDB_ERR_INVALID_ARG, "nvdb_net_params: bad arguments");
   const DevNet& d = m->net[net];
   CU(cudaMemcpyAsync(d_out, d.p32, d.P * 4, cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
   return NVDB_OK;
 }
 
 extern "C" nvdb_status nvdb_net_set_params(nvdb_model* m, int net, const float* d_in, nvdb_stream stream) {
-  if (!m || net < 0 || net > 2 || !d_in) return fail(NVDB_ERR_INVALID_ARG, "nvdb_net_set_params: bad arguments");
+  if (!m || net < 0 || net >= m->n_net() || !d_in) return fail(NVDB_ERR_INVALID_ARG, "nvdb_net_set_params: bad arguments");
   cudaStream_t s = (cudaStream_t)stream;
   DevNet& d = m->net[net];
   CU(cudaMemcpyAsync(d.p32, d_in, d.P * 4, cudaMemcpyDeviceToDevice, s));
   d.bf16_exact = false;
   TRY(pack_net(m, net, s));
+  TRY(upload_views(m, s));
   // the patches and the decoded topology belonged to the old weights
   for (auto& p : m->patches) p.release();
   m->patches.clear();
@@ -1393,6 +1578,8 @@ extern "C" nvdb_status nvdb_model_info(const nvdb_model* m, nvdb_info* out) {
   out->n_leaf = m->n_leaf;
   out->n_l1 = m->n_l1;
   out->n_l2 = m->n_l2;
+  out->n_experts = m->n_exp;
+  out->subdomain = m->sub_size;
   return NVDB_OK;
 }
 
@@ -1435,7 +1622,7 @@ extern "C" nvdb_status nvdb_model_export(const nvdb_model* m, void* buf, size_t*
   Writer w;
   BlobHeader h{};
   std::memcpy(h.magic, "NVDBMDL1", 8);
-  h.version = 1;
+  h.version = m->moe() ? 2 : 1;   // version 2 carries the domain decomposition
   h.grid_class = (uint32_t)m->grid_class;
   h.background = m->background;
   h.half_width = m->half_width;
@@ -1446,14 +1633,25 @@ extern "C" nvdb_status nvdb_model_export(const nvdb_model* m, void* buf, size_t*
   for (int k = 0; k < 3; ++k) { h.width[k] = m->width[k]; h.layers[k] = m->layers[k]; }
   h.n_patch_sets = (int32_t)m->patches.size();
   h.n_l2 = m->n_l2; h.n_l1 = m->n_l1; h.n_leaf = m->n_leaf; h.n_active = m->n_active;
+  if (m->moe()) {
+    h.reserved0 = m->n_exp;
+    h.reserved1[0] = (uint64_t)m->sub_size;
+    h.reserved1[1] = (uint64_t)m->sub_halo;
+  }
   w.put(&h, sizeof h);
   for (int lev = 0; lev < 2; ++lev) { w.put(m->q_host[lev].data(), m->q_host[lev].size() * 4); w.pad(); }
   CU(cudaDeviceSynchronize());
-  for (int k = 0; k < 3; ++k) {
+  for (int k = 0; k < m->n_net(); ++k) {
     std::vector<float> p(m->net[k].P);
     CU(cudaMemcpy(p.data(), m->net[k].p32, p.size() * 4, cudaMemcpyDeviceToHost));
     w.put(p.data(), p.size() * 4);
     w.pad();
+  }
+  if (m->moe()) {
+    const int32_t dims[3] = {m->sub_dims, m->sub_dims, m->sub_dims};
+    w.put(dims, sizeof dims); w.pad();
+    w.put(m->expert_of_host.data(), m->expert_of_host.size() * 4); w.pad();
+    w.put(m->exp_origin_host.data(), m->exp_origin_host.size() * 4); w.pad();
   }
   w.put(m->l2_origin_host.data(), m->l2_origin_host.size() * 4); w.pad();
   w.put(m->l2_mask_host.data(), m->l2_mask_host.size() * 8); w.pad();
@@ -1488,7 +1686,12 @@ extern "C" nvdb_status nvdb_model_import(const void* buf, size_t bytes, nvdb_str
   cudaStream_t s = (cudaStream_t)stream;
   Reader r{static_cast<const uint8_t*>(buf), bytes};
   const BlobHeader* h = static_cast<const BlobHeader*>(r.take(sizeof(BlobHeader)));
-  if (!h || std::memcmp(h->magic, "NVDBMDL1", 8) != 0 || h->version != 1) return fail(NVDB_ERR_CORRUPT, "not an NVDBMDL1 blob");
+  if (!h || std::memcmp(h->magic, "NVDBMDL1", 8) != 0 || (h->version != 1 && h->version != 2))
+    return fail(NVDB_ERR_CORRUPT, "not an NVDBMDL1 blob");
+  const bool moe = h->version == 2;
+  if (moe && (h->reserved0 < 1 || h->reserved0 > (1 << 20) || h->reserved1[0] == 0 || h->reserved1[0] % 512 ||
+              h->reserved1[1] < 8 || (h->reserved1[1] & (h->reserved1[1] - 1)) || 4 * h->reserved1[1] > h->reserved1[0]))
+    return fail(NVDB_ERR_CORRUPT, "bad decomposition header");
   if (h->n_l2 < 0 || h->n_l1 < 0 || h->n_leaf < 0 || h->n_active < 0 || h->n_patch_sets < 0 || h->n_patch_sets > kNumPrecisions ||
       h->grid_class > 1 || h->log2_extent < 0 || h->log2_extent > 21)
     return fail(NVDB_ERR_CORRUPT, "bad blob header");
@@ -1515,17 +1718,54 @@ extern "C" nvdb_status nvdb_model_import(const void* buf, size_t bytes, nvdb_str
       TRY(dalloc(&m->q_dev[lev], cnt));
       CU(cudaMemcpy(m->q_dev[lev], q, cnt * 4, cudaMemcpyHostToDevice));
     }
-    for (int k = 0; k < 3; ++k) {
-      const int64_t P = net_param_count(k == 0 ? m->ffm[0] : m->ffm[1], m->width[k], m->layers[k]);
+    if (moe) {
+      m->set_experts((int)h->reserved0);
+      m->sub_size = (int)h->reserved1[0];
+      m->sub_halo = (int)h->reserved1[1];
+    }
+    for (int k = 0; k < m->n_net(); ++k) {
+      const int j = k % 3;
+      const int64_t P = net_param_count(j == 0 ? m->ffm[0] : m->ffm[1], m->width[j], m->layers[j]);
       const float* p = static_cast<const float*>(r.take((size_t)P * 4));
       r.pad();
       if (!p) return fail(NVDB_ERR_CORRUPT, "blob truncated (network %d)", k);
       std::vector<float> tmp(p, p + P);
       TRY(upload_net(m, k, tmp.data(), s));
-      m->net[k].bf16_exact = bf16_exact_layers(tmp.data(), P - m->width[k] - 1);
+      m->net[k].bf16_exact = bf16_exact_layers(tmp.data(), P - m->width[j] - 1);
       CU(cudaStreamSynchronize(s));
-      TRY(pack_net(m, k, s));
     }
+    if (moe) {   // grid of subdomains and expert origins (Section 3.4)
+      const int32_t* dims = static_cast<const int32_t*>(r.take(12));
+      r.pad();
+      if (!dims) return fail(NVDB_ERR_CORRUPT, "blob truncated (decomposition)");
+      const int n = dims[0];
+      const int64_t need = (int64_t)1 << (m->log2e);
+      if (n < 1 || dims[1] != n || dims[2] != n || (int64_t)n * m->sub_size < need || (int64_t)(n - 1) * m->sub_size >= need)
+        return fail(NVDB_ERR_CORRUPT, "bad subdomain grid");
+      m->sub_dims = n;
+      const int32_t* eo = static_cast<const int32_t*>(r.take((size_t)n * n * n * 4));
+      r.pad();
+      const int32_t* og = static_cast<const int32_t*>(r.take((size_t)m->n_exp * 12));
+      r.pad();
+      if (!eo || !og) return fail(NVDB_ERR_CORRUPT, "blob truncated (decomposition)");
+      m->expert_of_host.assign(eo, eo + (size_t)n * n * n);
+      m->exp_origin_host.assign(og, og + 3 * (size_t)m->n_exp);
+      std::vector<int> seen(m->n_exp, 0);
+      for (size_t c = 0; c < m->expert_of_host.size(); ++c) {   // every expert once, at its own subdomain
+        const int e = m->expert_of_host[c];
+        if (e < -1 || e >= m->n_exp) return fail(NVDB_ERR_CORRUPT, "bad expert id");
+        if (e < 0) continue;
+        const int32_t want[3] = {(int32_t)(c / ((size_t)n * n)) * m->sub_size, (int32_t)((c / n) % n) * m->sub_size,
+                                 (int32_t)(c % n) * m->sub_size};
+        if (seen[e]++ || std::memcmp(want, &m->exp_origin_host[3 * e], 12) != 0)
+          return fail(NVDB_ERR_CORRUPT, "expert table inconsistent");
+      }
+      for (int e = 0; e < m->n_exp; ++e)
+        if (!seen[e]) return fail(NVDB_ERR_CORRUPT, "expert %d has no subdomain", e);
+      TRY(upload_moe(m, s));
+    }
+    for (int k = 0; k < m->n_net(); ++k) TRY(pack_net(m, k, s));
+    TRY(upload_views(m, s));
     const int32_t* l2o = static_cast<const int32_t*>(r.take((size_t)m->n_l2 * 12));
     r.pad();
     const uint64_t* l2m = static_cast<const uint64_t*>(r.take((size_t)m->n_l2 * 4096));
@@ -1654,7 +1894,7 @@ nvdb_status launch_train_static(const NetView& nv, const TrainJob& job, int grid
 
 extern "C" nvdb_status nvdb_mlp_grad_static(const nvdb_model* m, int net, const int32_t* d_ijk, const float* d_target,
                                             int64_t n, int loss_kind, float* d_grad, float* loss, nvdb_stream stream) {
-  if (!m || net < 0 || net > 2 || n <= 0 || !d_ijk || !d_target || !d_grad)
+  if (!m || net < 0 || net >= m->n_net() || n <= 0 || !d_ijk || !d_target || !d_grad)
     return fail(NVDB_ERR_INVALID_ARG, "nvdb_mlp_grad_static: bad arguments");
   if (loss_kind < 0 || loss_kind > 3) return fail(NVDB_ERR_INVALID_ARG, "unknown loss %d", loss_kind);
   if (n >= (1ll << 31)) return fail(NVDB_ERR_UNSUPPORTED, "nvdb_mlp_grad_static: n >= 2^31");
@@ -1678,16 +1918,18 @@ extern "C" nvdb_status nvdb_mlp_grad_static(const nvdb_model* m, int net, const 
   const int grid = (int)std::min<int64_t>(std::min<int64_t>((n + kTile - 1) / kTile, num_sms()), fit);
   float* loss_slot = scratch + (limit - 1);
   TrainJob j{};
-  j.net = net;
+  j.net = net % 3;
+  j.stream = net;
   j.loss = loss_kind;
   j.step = 1;
   j.batch = n;
   j.ijk_list = d_ijk;
   j.target_list = d_target;
   j.partial = scratch;   // every CTA zeroes its own slot before accumulating
-  j.ox = m->origin[0];
-  j.oy = m->origin[1];
-  j.oz = m->origin[2];
+  const int ex = net / 3;   // an expert's network works relative to its subdomain origin
+  j.ox = m->origin[0] + (m->moe() ? m->exp_origin_host[3 * ex] : 0);
+  j.oy = m->origin[1] + (m->moe() ? m->exp_origin_host[3 * ex + 1] : 0);
+  j.oz = m->origin[2] + (m->moe() ? m->exp_origin_host[3 * ex + 2] : 0);
   const NetView nv = net_view(m, net);
   if (nv.n_in == 32 && nv.width == 32) TRY((launch_train_static<32, 32>(nv, j, grid, s)));
   else if (nv.n_in == 32 && nv.width == 64) TRY((launch_train_static<32, 64>(nv, j, grid, s)));

@@ -16,6 +16,7 @@ namespace nvdb {
 
 struct TrainJob {
   int net;                    // 0 level-1 classifier, 1 level-0 classifier, 2 regressor
+  int stream;                 // sample stream of the network: 3 expert + net (net without experts)
   int loss;                   // LOSS_*
   int step;                   // Adam step (1-based), keys the sample stream
   uint64_t seed;
@@ -28,6 +29,10 @@ struct TrainJob {
   const int4* l1_origin; const unsigned long long* l1_mask; int64_t n_l1;
   const int4* leaf_origin; const unsigned long long* leaf_mask; int64_t n_leaf;
   const int32_t* ijk; const float* val; int64_t n;
+  // a domain decomposition's expert samples a sub-population (Section 3.4): element i is
+  // (pop[i >> pop_shift] << pop_shift) | (i & (2^pop_shift - 1)) of the population above,
+  // pop_n << pop_shift elements (pop_shift = 9 for the level-0 classifier: lists of leaves)
+  const uint32_t* pop; int64_t pop_n; int pop_shift;
   float tscale;               // regressor target = val * tscale
   float* partial;             // [gridDim.x][P + 1]: gradient partials, then the loss sum
   uint32_t* status;           // ST_* bits (tensor-core kernel: a timed-out wait)
@@ -47,6 +52,7 @@ __device__ __forceinline__ void take_step(TrainJob& job) {
 enum : int { LOSS_MSE = 0, LOSS_L1 = 1, LOSS_BCE = 2, LOSS_LINEAR = 3 };
 
 __device__ __forceinline__ int64_t train_population(const TrainJob& j) {
+  if (j.pop) return j.pop_n << j.pop_shift;
   return j.net == 0 ? j.n_l1 * 4096 : j.net == 1 ? j.n_leaf * 512 : j.n;
 }
 
@@ -60,7 +66,8 @@ __device__ __forceinline__ void train_sample(const TrainJob& j, int64_t s, int& 
     tgt = j.target_list[s];
     return;
   }
-  const uint64_t idx = sample_index(j.seed, j.net, j.step, (uint32_t)s, (uint64_t)train_population(j));
+  uint64_t idx = sample_index(j.seed, j.stream, j.step, (uint32_t)s, (uint64_t)train_population(j));
+  if (j.pop) idx = ((uint64_t)j.pop[idx >> j.pop_shift] << j.pop_shift) | (idx & ((1ull << j.pop_shift) - 1));
   if (j.net == 0) {
     const int64_t node = (int64_t)(idx >> 12);
     const int slot = (int)(idx & 4095);
