@@ -210,8 +210,9 @@ nvdb_status nvdb_plan_launch(nvdb_plan* plan, nvdb_stream stream);
 nvdb_status nvdb_plan_check(nvdb_plan* plan, nvdb_stream stream);
 /* Tuning result (HOST outputs, any may be NULL): tensor-core CTAs per SM chosen (0 = the
  * kernel's limit), the kernel variant chosen (0: 128 threads per tile; 1: 256 threads per
- * tile, each half of the accumulator columns in its own warps, origins staged one tile
- * ahead by bulk copies), and the tuned decode time in ms. */
+ * tile, each half of the accumulator columns in its own warps, node / leaf origins staged
+ * by bulk copies; 2: 128 threads per tile with the origins staged by bulk copies two tiles
+ * ahead), and the tuned decode time in ms. */
 nvdb_status nvdb_plan_info(const nvdb_plan* plan, int* tc_ctas_per_sm, int* tc_variant, float* tuned_ms);
 nvdb_status nvdb_plan_free(nvdb_plan* plan);
 

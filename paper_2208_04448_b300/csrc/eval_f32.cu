@@ -5,14 +5,16 @@
 
 namespace nvdb {
 namespace {
-template <int NIN, int W>
+template <int NIN, int W, bool MOE = false>
 nvdb_status launch_f32(const EvalBatch& b, int64_t ntiles, cudaStream_t s) {
+  if (!MOE && batch_moe(b)) return launch_f32<NIN, W, true>(b, ntiles, s);
   int occ = 0;
   const size_t smem = f32_smem_bytes<NIN, W>(b.it[0].net.layers);
-  TRY(set_smem_limit((const void*)mlp_f32_kernel<NIN, W>, smem));
-  CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, mlp_f32_kernel<NIN, W>, kTile, smem));
+  auto* kern = mlp_f32_kernel<NIN, W, MOE>;
+  TRY(set_smem_limit((const void*)kern, smem));
+  CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kTile, smem));
   const int64_t grid = std::min<int64_t>(ntiles, (int64_t)num_sms() * std::max(occ, 1));
-  KLAUNCH(eval_name("mlp_f32", b.it[0].job.mode), s, mlp_f32_kernel<NIN, W><<<(unsigned)grid, kTile, smem, s>>>(b));
+  KLAUNCH(eval_name("mlp_f32", b.it[0].job.mode), s, kern<<<(unsigned)grid, kTile, smem, s>>>(b));
   CU(cudaGetLastError());
   return NVDB_OK;
 }

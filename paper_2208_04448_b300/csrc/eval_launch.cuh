@@ -8,15 +8,16 @@
 
 namespace nvdb {
 
-template <int NIN, int W, int MODE, bool MOE = false>
+template <int NIN, int W, int MODE, bool MOE = false, bool STAGE = false>
 nvdb_status launch_tc(const EvalBatch& b, int64_t ntiles, const char* base, cudaStream_t s) {
-  if (!MOE && batch_moe(b)) return launch_tc<NIN, W, MODE, true>(b, ntiles, base, s);
+  if (!MOE && batch_moe(b)) return launch_tc<NIN, W, MODE, true, false>(b, ntiles, base, s);
   const TcLayout<NIN, W, MODE> lay(b.it[0].net.layers, batch_wlo(b));
-  TRY(set_smem_limit((const void*)mlp_tc_kernel<NIN, W, MODE, MOE>, lay.total));
+  auto* kern = mlp_tc_kernel<NIN, W, MODE, MOE, STAGE>;
+  TRY(set_smem_limit((const void*)kern, lay.total));
   // Residency from the kernel's own limits (the runtime's occupancy query reports 1 for
   // kernels that allocate tensor memory): registers, shared memory, and TMEM columns.
   cudaFuncAttributes fa;
-  CU(cudaFuncGetAttributes(&fa, mlp_tc_kernel<NIN, W, MODE, MOE>));
+  CU(cudaFuncGetAttributes(&fa, kern));
   const int regs = std::max(8, (fa.numRegs + 7) & ~7);
   const int by_regs = 65536 / (regs * kTile);
   const int by_smem = (int)(kSmemPerSm / (lay.total + 1024));
@@ -24,8 +25,7 @@ nvdb_status launch_tc(const EvalBatch& b, int64_t ntiles, const char* base, cuda
   if (occ < 1) return fail(NVDB_ERR_UNSUPPORTED, "tensor-core kernel does not fit on an SM");
   if (g_occ_override > 0) occ = std::min(occ, g_occ_override);
   const int64_t grid = std::min<int64_t>(ntiles, (int64_t)num_sms() * occ);
-  KLAUNCH(eval_name(base, b.it[0].job.mode), s,
-          mlp_tc_kernel<NIN, W, MODE, MOE><<<(unsigned)grid, kTile, lay.total, s>>>(b));
+  KLAUNCH(eval_name(base, b.it[0].job.mode), s, kern<<<(unsigned)grid, kTile, lay.total, s>>>(b));
   CU(cudaGetLastError());
   return NVDB_OK;
 }
@@ -52,11 +52,19 @@ nvdb_status launch_tc2(const EvalBatch& b, int64_t ntiles, const char* base, cud
 template <int MODE>
 nvdb_status launch_tc_shape(const EvalBatch& b, int64_t ntiles, const char* base, cudaStream_t s) {
   const NetView& nv = b.it[0].net;
-  const bool v2 = tc_variant() == 1 && !batch_moe(b);   // decomposed models: the 128-thread kernel
-  if (nv.n_in == 32 && nv.width == 32) return v2 ? launch_tc2<32, 32, MODE>(b, ntiles, base, s) : launch_tc<32, 32, MODE>(b, ntiles, base, s);
-  if (nv.n_in == 32 && nv.width == 64) return v2 ? launch_tc2<32, 64, MODE>(b, ntiles, base, s) : launch_tc<32, 64, MODE>(b, ntiles, base, s);
-  if (nv.n_in == 64 && nv.width == 32) return v2 ? launch_tc2<64, 32, MODE>(b, ntiles, base, s) : launch_tc<64, 32, MODE>(b, ntiles, base, s);
-  if (nv.n_in == 64 && nv.width == 64) return v2 ? launch_tc2<64, 64, MODE>(b, ntiles, base, s) : launch_tc<64, 64, MODE>(b, ntiles, base, s);
+  // variant 0: 128 threads per tile; 1: 256 threads, split epilogue (staged origins);
+  // 2: 128 threads with staged origins.  Decomposed models take variant 0's expert passes.
+  const int v = batch_moe(b) ? 0 : tc_variant();
+#define NVDB_TC_SHAPE(A, B)                                                     \
+  if (nv.n_in == A && nv.width == B)                                            \
+    return v == 1 ? launch_tc2<A, B, MODE>(b, ntiles, base, s)                  \
+         : v == 2 ? launch_tc<A, B, MODE, false, true>(b, ntiles, base, s)      \
+                  : launch_tc<A, B, MODE>(b, ntiles, base, s);
+  NVDB_TC_SHAPE(32, 32)
+  NVDB_TC_SHAPE(32, 64)
+  NVDB_TC_SHAPE(64, 32)
+  NVDB_TC_SHAPE(64, 64)
+#undef NVDB_TC_SHAPE
   return fail(NVDB_ERR_UNSUPPORTED, "network shape n=%d w=%d", nv.n_in, nv.width);
 }
 

@@ -241,7 +241,7 @@ __host__ __device__ inline size_t f32_smem_bytes(int L) {
   return (size_t)((P + 3) & ~3ll) * 4 + (size_t)(NIN / 2) * 3 * 4;
 }
 
-template <int NIN, int W>
+template <int NIN, int W, bool MOE = false>
 __global__ void __launch_bounds__(kTile) mlp_f32_kernel(const __grid_constant__ EvalBatch b) {
   extern __shared__ float4 smem_f4[];
   float* sp = reinterpret_cast<float*>(smem_f4);
@@ -268,7 +268,7 @@ __global__ void __launch_bounds__(kTile) mlp_f32_kernel(const __grid_constant__ 
     int cx, cy, cz;
     const bool valid = job_coord(job, tl, threadIdx.x, cx, cy, cz);
     float y;
-    if (!mv.experts) {
+    if (!MOE || !mv.experts) {
       if (staged != b.it[m].net.p32) stage(b.it[m].net);
       y = forward_f32<NIN, W>(sp, sq, L, cx, cy, cz);
     } else {
@@ -552,8 +552,10 @@ __device__ __forceinline__ void tc_stage(const NetView& net, int mode, const Lay
 }
 
 // MOE: the batch holds decomposed models (Section 3.4); a separate instantiation, so the
-// undecomposed kernel carries none of the expert passes.
-template <int NIN, int W, int MODE, bool MOE = false>
+// undecomposed kernel carries none of the expert passes.  STAGE: lattice tiles take their
+// node / leaf origin from shared memory, filled by bulk copies two tiles ahead, instead of
+// a load of their own (the decode-plan autotuner measures both).
+template <int NIN, int W, int MODE, bool MOE = false, bool STAGE = false>
 __global__ void __launch_bounds__(kTile, 4) mlp_tc_kernel(const __grid_constant__ EvalBatch b) {
   static_assert(W == 32 || W == 64, "width");
   static_assert(NIN == 32 || NIN == 64, "encoding size");
@@ -607,7 +609,7 @@ __global__ void __launch_bounds__(kTile, 4) mlp_tc_kernel(const __grid_constant_
   // mbarrier; counters of copies issued / waited for per buffer keep the phases.
   // (decomposed models evaluate a tile once per expert, from __ldg origins, without either)
   const bool moe_batch = MOE && batch_moe(b);
-  const bool lattice = b.it[0].job.mode != MODE_LIST && !moe_batch;   // one mode per launch (a decode stage)
+  const bool lattice = STAGE && b.it[0].job.mode != MODE_LIST && !moe_batch;   // one mode per launch (a decode stage)
   auto origin_src = [&](int64_t g) -> const int4* {
     const int mm = batch_find(b, g);
     const int64_t tl = g - b.it[mm].tile_start;
@@ -743,7 +745,7 @@ __global__ void __launch_bounds__(kTile, 4) mlp_tc_kernel(const __grid_constant_
         }
       } else {
         int cx, cy, cz;
-        if (job.mode == MODE_L1 && lattice) {   // the staged origin of this tile's level-1 node
+        if (STAGE && job.mode == MODE_L1 && lattice) {   // the staged origin of this tile's level-1 node
           ok_enc = mbar_wait_bounded(obar + cb, cpar);
           const int4 o = sorg[cb];
           const int sl = ((int)(t & 31) << 7) | tid;
@@ -797,8 +799,8 @@ __global__ void __launch_bounds__(kTile, 4) mlp_tc_kernel(const __grid_constant_
       }
       bool ok = true;
       if (l == 0 && next_same && tid < 2 * M) {   // the next tile's factors, into the other buffer
-        ok = mbar_wait_bounded(obar + nb, npar);
-        l0_factors<M, MODE>(job, sq, sorg[nb], tn, sP + (pbuf ^ 1) * 2 * M, tid);
+        if (lattice) ok = mbar_wait_bounded(obar + nb, npar);
+        l0_factors<M, MODE>(job, sq, lattice ? sorg[nb] : __ldg(job.nodes + (tn >> 2)), tn, sP + (pbuf ^ 1) * 2 * M, tid);
       }
       if (l == 0 && next_same) waited = k + 2;
       ok = mbar_wait_bounded(bar, phase) && ok;

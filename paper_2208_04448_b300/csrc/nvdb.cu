@@ -2010,7 +2010,7 @@ extern "C" nvdb_status nvdb_decompress_plan(const nvdb_model* const* models, int
     float best = 1e30f;
     int best_occ = 0, best_var = 1;
     const int occs[] = {0, 2, 3};
-    for (int v = 0; v < 2; ++v)
+    for (int v = 0; v < kTcVariants; ++v)
       for (int c : occs) {
         if (prec == NVDB_FP32 && (c != 0 || v != 0)) continue;
         g_occ_override = c;

@@ -188,14 +188,16 @@ static FailWaitsHook g_fail_waits_hook(&set_fail_waits_here);
 // Tensor-core CTAs per SM chosen by the decode-plan autotuner (0: from the kernel's limits).
 inline int g_occ_override = 0;
 // Tensor-core kernel variant: 0 = mlp_tc_kernel (128 threads per tile), 1 = mlp_tc2_kernel
-// (256 threads per tile, split epilogue, TMA-staged origins).  -1: the default, which the
-// environment variable NVDB_TC_VARIANT may set; the decode-plan autotuner overrides it.
+// (256 threads per tile, split epilogue, origins staged by bulk copies), 2 = mlp_tc_kernel
+// with origins staged by bulk copies.  -1: the default (0), which the environment variable
+// NVDB_TC_VARIANT may set; the decode-plan autotuner overrides it.
+constexpr int kTcVariants = 3;
 inline int g_variant_override = -1;
 inline int tc_variant() {
   if (g_variant_override >= 0) return g_variant_override;
   static const int v = [] {
     const char* e = std::getenv("NVDB_TC_VARIANT");
-    return e && (e[0] == '0' || e[0] == '1') ? e[0] - '0' : 0;
+    return e && e[0] >= '0' && e[0] < '0' + kTcVariants ? e[0] - '0' : 0;
   }();
   return v;
 }

@@ -131,7 +131,10 @@ def test_first_adam_step_of_every_expert(case):
             assert abs(m.losses(kk)[0] - ls[0]) <= 1e-5 * max(1.0, abs(ls[0])), (e, net)   # same samples
             dw_ref = N.flatten(om["nets"][kk]) - theta0[kk]
             dw_got = N.flatten(got["nets"][kk]) - theta0[kk]
-            big = np.abs(dw_ref) > 0.9e-3
+            # components whose FP64 gradient is resolved in FP32 (|g| > ~1e-5, i.e. the first
+            # step within 0.1% of lr): the steps agree; smaller ones may change sign
+            big = np.abs(dw_ref) > 0.999e-3
+            assert big.sum() > 0
             assert np.abs(dw_got[big] - dw_ref[big]).max() <= 2e-6, (e, net)
 
 
