@@ -252,29 +252,25 @@ def run_water(args):
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     shape = dict(width=NET_WIDTH, layers=NET_LAYERS, ffm_size=FFM, batch=args.train_batch, patch_precs=0b11111,
                  train_prec=PRECS[args.train_prec])
-    models, steps, n_total, train_ms = [], [], 0, 0.0
-    nv.profile_read()
-    nv.profile_enable(True)
-    target = None
+    grids, n_total = [], 0
     for f in range(args.frames):
         ijk, val = water_frame(f, device="cuda")
-        g = nv.build(ijk.contiguous(), val.contiguous(), 0, 3.0)
-        info = g.info()
-        sigma = 10.0 * (1 << info["log2_extent"]) / 1024.0
-        if f == 0:
-            m = nv.compress(g, seed=1, ffm_sigma=sigma, steps=args.train_steps, lr=1e-3, **shape)
-            target = [float(np.mean(m.losses(k)[-50:])) for k in range(3)]
-        else:
-            m = nv.compress(g, seed=1, ffm_sigma=sigma, steps=500, lr=1e-4, warm=models[-1], stop_window=50,
-                            stop_loss=target, **shape)
-        steps.append([len(m.losses(k)) for k in range(3)])
-        n_total += info["n_active"]
-        models.append(m)
-        del g, ijk, val
-        prof = nv.profile_read()
-        train_ms += sum(v[1] for k, v in prof.items() if k in TRAIN_KERNELS)
+        grids.append(nv.build(ijk.contiguous(), val.contiguous(), 0, 3.0))
+        n_total += grids[-1].info()["n_active"]
+        del ijk, val
+    sigma = 10.0 * (1 << grids[0].info()["log2_extent"]) / 1024.0
+    # nvdb_compress_sequence: frame 0 cold (lr 1e-3), refined 500 steps at lr 1e-4, later frames
+    # warm-started at 1e-4 with the early stop at frame 0's final loss (Section 3.6)
+    nv.profile_read()
+    nv.profile_enable(True)
+    models = nv.compress_sequence(grids, refine_lr_scale=0.1, refine_steps=500, warm_steps=500, seed=1,
+                                  ffm_sigma=sigma, steps=args.train_steps, lr=1e-3, stop_window=50, **shape)
+    prof = nv.profile_read()
     nv.profile_enable(False)
-    steps = np.array(steps)
+    train_ms = sum(v[1] for k, v in prof.items() if k in TRAIN_KERNELS)
+    del grids
+    steps = np.array([[len(m.losses(k)) for k in range(3)] for m in models])
+    steps[0] += args.train_steps   # frame 0: the cold steps before its refinement
     prec = PRECS[args.prec]
     plan = nv.decompress_plan(models, prec)
     stream = torch.cuda.current_stream()
@@ -300,7 +296,7 @@ def run_water(args):
                 config=dict(workload=f"water surface 2048x256x2048, 8 seeded waves, {args.frames} frames, half-band 3; "
                                      "3 nets 4x64, FFM 64, sigma 10/1024vox; all frames decoded by one plan",
                             n_active_total=n_total, frames=args.frames, plan=plan.info()),
-                warm_start=dict(cold_steps=cold, warm_steps_mean=float(warm.mean()),
+                warm_start=dict(cold_steps=cold, refine_steps=3 * 500, warm_steps_mean=float(warm.mean()),
                                 step_speedup=cold / float(max(warm.mean(), 1)), steps_per_frame=steps.tolist()),
                 train_samples_per_s=float(steps.sum() * args.train_batch / (train_ms / 1e3)) if train_ms else None,
                 clocks=clk.summary())

@@ -111,6 +111,13 @@ typedef struct {
                            tent gate (subdomain plus halo) is non-zero there (Eq. 3).  A warm start
                            takes the warm model's decomposition. */
   int32_t halo;         /* halo width in voxels, a power of two in [8, S/4]; 0 = 8 */
+  int32_t resample;     /* subset resampling (Appendix E): every `resample` steps draw a subset of
+                           resample x batch candidates, and each step's batch from that subset;
+                           0 = a fresh batch every step (resample x batch < 2^32) */
+  int32_t sampling;     /* regressor samples (Appendix C ablation): 0 = active voxels (the method),
+                           1 = every voxel of the leaves (blocked), 2 = every voxel of the domain's
+                           bounding box (dense; log2 extent <= 10, no decomposition); inactive
+                           voxels take the background as target */
 } nvdb_train_opts;
 
 typedef struct {
@@ -159,6 +166,19 @@ void nvdb_train_opts_default(nvdb_train_opts* opts);
  * (Section 3.3.2).  Synchronises the stream. */
 nvdb_status nvdb_compress(const nvdb_grid* grid, const nvdb_train_opts* opts, const nvdb_model* warm,
                           nvdb_stream stream, nvdb_model** out);
+
+/* Animated volumes (Section 3.6, temporally coherent warm start): encode frames 0..n-1 of a
+ * sequence into out[0..n-1].  Frame 0 is trained cold with `opts`, then refined from those
+ * weights for refine_steps steps at lr x refine_lr_scale (fresh Adam state; 0 steps = no
+ * refinement); frame 0's final loss per network is the mean of its last opts->stop_window
+ * losses.  Every later frame starts from the previous frame's networks and Fourier matrices
+ * and trains at lr x refine_lr_scale for at most warm_steps steps, each network stopping at
+ * the first multiple of stop_window steps whose last stop_window losses average below frame
+ * 0's final loss.  Models are owned by the caller (nvdb_model_free); on an error none is
+ * returned.  Synchronises the stream. */
+nvdb_status nvdb_compress_sequence(const nvdb_grid* const* grids, int n_frames, const nvdb_train_opts* opts,
+                                   float refine_lr_scale, int32_t refine_steps, int32_t warm_steps,
+                                   nvdb_stream stream, nvdb_model** out);
 
 /* Per-step mean training loss of network `net` of the last compress
  * (HOST buffer of cap floats); *count receives the number of steps run

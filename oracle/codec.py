@@ -47,7 +47,7 @@ def _lattice8(o):
 def default_opts(**kw) -> dict:
     o = dict(width=[32, 32, 32], layers=[3, 3, 3], ffm_size=None, sigma=10.0, seed=1,
              steps=200, batch=4096, lr=1e-3, lr_decay=0.975, lr_interval=100, loss=N.LOSS_MSE,
-             subdomain=0, halo=8)
+             subdomain=0, halo=8, resample=0, sampling=0)
     o.update(kw)
     if o["ffm_size"] is None:
         o["ffm_size"] = [o["width"][0], max(o["width"][1], o["width"][2])]
@@ -100,6 +100,37 @@ def evaluate(model: dict, net: int, ijk: np.ndarray, chunk: int = 1 << 16) -> np
     return out
 
 
+SPARSE, BLOCKED, DENSE = 0, 1, 2
+
+
+def _voxel_target(grid: dict, model: dict, ijk: np.ndarray) -> np.ndarray:
+    """Regressor target of arbitrary voxels: value (scaled) where active, else the background
+    (+half_width for level sets, scaled to +1; 0 for fog)."""
+    keys = vdb.canonical_key(grid["ijk"])
+    order = np.argsort(keys)
+    k = vdb.canonical_key(ijk)
+    pos = np.clip(np.searchsorted(keys[order], k), 0, len(keys) - 1)
+    hit = keys[order][pos] == k
+    v = np.where(hit, grid["val"][order][pos].astype(np.float64), np.nan)
+    if model["grid_class"] == 0:
+        return np.where(hit, v / model["half_width"], 1.0)
+    return np.where(hit, v, 0.0)
+
+
+def regressor_population(grid: dict, model: dict, idx: np.ndarray, sampling: int):
+    """Regressor samples of the sparsity ablation (Appendix C): SPARSE the active voxels
+    (the method), BLOCKED every voxel of the leaves, DENSE every voxel of the domain's box."""
+    if sampling == SPARSE:
+        return population(grid, model, REG, idx)
+    if sampling == BLOCKED:
+        leaf, off = idx >> 9, idx & 511
+        ijk = grid["leaf_origin"][leaf] + _lattice8(off)
+    else:
+        e = model["log2_extent"]
+        ijk = model["origin"][None] + np.stack([idx >> (2 * e), (idx >> e) & ((1 << e) - 1), idx & ((1 << e) - 1)], -1)
+    return ijk, _voxel_target(grid, model, ijk)
+
+
 def population(grid: dict, model: dict, net: int, idx: np.ndarray):
     """Training population of a network: (voxel coordinates, label/target) for sample indices."""
     if net == L1CLS:
@@ -133,11 +164,24 @@ def train_net(grid: dict, model: dict, net: int, opts: dict, steps=None, log=Non
     kind = N.LOSS_BCE if net != REG else opts["loss"]
     q = level_q(model, net)
     pop = None if moe is None else MOE.population(grid, model, expert, net)
-    npop = population_size(grid, net) if pop is None else len(pop)
+    sampling = opts.get("sampling", SPARSE) if net == REG else SPARSE
+    if sampling == BLOCKED:
+        npop = grid["leaf_origin"].shape[0] * 512
+    elif sampling == DENSE:
+        npop = 1 << (3 * model["log2_extent"])
+    else:
+        npop = population_size(grid, net) if pop is None else len(pop)
+    R = opts.get("resample", 0)
     losses = []
     for t in range(1, (opts["steps"] if steps is None else steps) + 1):
-        idx = rng.sample_indices(opts["seed"], slot, t, opts["batch"], npop)
-        ijk, lab = population(grid, model, net, idx if pop is None else pop[idx])
+        if R:
+            idx = rng.subset_indices(opts["seed"], slot, t, opts["batch"], R, npop)
+        else:
+            idx = rng.sample_indices(opts["seed"], slot, t, opts["batch"], npop)
+        if sampling != SPARSE:
+            ijk, lab = regressor_population(grid, model, idx, sampling)
+        else:
+            ijk, lab = population(grid, model, net, idx if pop is None else pop[idx])
         cur = N.unflatten(theta, p)
         c = level_coords(model, net, ijk) if moe is None else MOE.expert_coords(model, expert, net, ijk)
         y, cache = N.forward(cur, N.encode(c, q))

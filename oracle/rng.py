@@ -90,6 +90,26 @@ def sample_indices(seed: int, net: int, step: int, batch: int, population: int) 
     return ((out.astype(np.uint64) * np.uint64(population)) >> np.uint64(32)).astype(np.int64)
 
 
+def subset_indices(seed: int, net: int, step: int, batch: int, interval: int, population: int) -> np.ndarray:
+    """Training-sample indices with subset resampling (Appendix E): every `interval` steps a
+    subset of interval * batch candidates is drawn, and each step draws its batch from it.
+    Sample s of step t takes the position p = sample_indices(...)[s] in the subset of size
+    interval * batch, then subset element p of interval r = (t - 1) div interval: word (p mod 4)
+    of Philox4x32-10 with counter (p div 4, r, net, 1), scaled to the population."""
+    if not (0 < population < (1 << 32)):
+        raise ValueError("population must be in [1, 2^32)")
+    pos = sample_indices(seed, net, step, batch, interval * batch).astype(np.uint64)
+    ctr = np.zeros((len(pos), 4), dtype=np.uint64)
+    ctr[:, 0] = pos >> np.uint64(2)
+    ctr[:, 1] = (step - 1) // interval
+    ctr[:, 2] = net
+    ctr[:, 3] = 1
+    key = np.array([seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF], dtype=np.uint64)
+    words = philox4x32_10(ctr, np.broadcast_to(key, (len(pos), 2)))
+    u = words[np.arange(len(pos)), (pos & np.uint64(3)).astype(np.int64)].astype(np.uint64)
+    return ((u * np.uint64(population)) >> np.uint64(32)).astype(np.int64)
+
+
 # ----------------------------------------------------------------- initialisation
 
 def xavier_net(seed: int, net: int, n_in: int, width: int, layers: int) -> dict:

@@ -170,6 +170,18 @@ def compress(grid: Grid, opts=None, warm: "Model | None" = None, stream=None, **
     return Model(h)
 
 
+def compress_sequence(grids, refine_lr_scale: float = 0.01, refine_steps: int = 0, warm_steps: int = 500,
+                      opts=None, stream=None, **kw) -> list:
+    """nvdb_compress_sequence: frame 0 cold (then refined at lr x refine_lr_scale), every later
+    frame warm-started from the previous one with the early stop at frame 0's final loss."""
+    o = opts if opts is not None else train_opts(**kw)
+    arr = (C.c_void_p * len(grids))(*[g.handle for g in grids])
+    out = (C.c_void_p * len(grids))()
+    _check(lib().nvdb_compress_sequence(arr, len(grids), C.byref(o), refine_lr_scale, refine_steps, warm_steps,
+                                        _stream(stream), out))
+    return [Model(C.c_void_p(h)) for h in out]
+
+
 def decompress(models, prec: int = FP32, out=None, stream=None):
     """Decode models -> (ijk int32 [n,3], val float32 [n], counts list).  `out` = (ijk, val) to reuse buffers."""
     if isinstance(models, Model):

@@ -25,7 +25,7 @@ class TrainOpts(C.Structure):
                 ("batch", C.c_int32), ("lr", C.c_float), ("lr_decay", C.c_float), ("lr_interval", C.c_int32),
                 ("loss", C.c_int32), ("train_prec", C.c_int32), ("patch_precs", C.c_uint32),
                 ("stop_window", C.c_int32), ("stop_loss", C.c_float * 3), ("resume", C.c_int32),
-                ("subdomain", C.c_int32), ("halo", C.c_int32)]
+                ("subdomain", C.c_int32), ("halo", C.c_int32), ("resample", C.c_int32), ("sampling", C.c_int32)]
 
 
 class Info(C.Structure):
@@ -45,6 +45,8 @@ SIGNATURES = {
     "nvdb_grid_free": ([_vp], _st),
     "nvdb_train_opts_default": ([C.POINTER(TrainOpts)], None),
     "nvdb_compress": ([_vp, C.POINTER(TrainOpts), _vp, _vp, C.POINTER(_vp)], _st),
+    "nvdb_compress_sequence": ([C.POINTER(_vp), _i32, C.POINTER(TrainOpts), C.c_float, C.c_int32, C.c_int32, _vp,
+                                C.POINTER(_vp)], _st),
     "nvdb_model_losses": ([_vp, _i32, _f32p, _i64, C.POINTER(C.c_int64)], _st),
     "nvdb_decompress": ([C.POINTER(_vp), _i32, _i32, _vp, _vp, _i64, C.POINTER(C.c_int64), _vp], _st),
     "nvdb_decompress_host": ([C.POINTER(_vp), _i32, _i32, _vp, _vp, _vp, _vp, _i64, C.POINTER(C.c_int64), _vp], _st),

@@ -242,7 +242,7 @@ __host__ __device__ inline size_t f32_smem_bytes(int L) {
 }
 
 template <int NIN, int W, bool MOE = false>
-__global__ void __launch_bounds__(kTile) mlp_f32_kernel(const __grid_constant__ EvalBatch b) {
+__global__ void __launch_bounds__(kTile, 3) mlp_f32_kernel(const __grid_constant__ EvalBatch b) {
   extern __shared__ float4 smem_f4[];
   float* sp = reinterpret_cast<float*>(smem_f4);
   const int L = b.it[0].net.layers;
@@ -259,7 +259,9 @@ __global__ void __launch_bounds__(kTile) mlp_f32_kernel(const __grid_constant__ 
     __syncthreads();
     staged = net.p32;
   };
-  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+  const int64_t t_beg = MOE ? (int64_t)blockIdx.x * ntiles / gridDim.x : (int64_t)blockIdx.x;
+  const int64_t t_end = MOE ? ((int64_t)blockIdx.x + 1) * ntiles / gridDim.x : ntiles;
+  for (int64_t t = t_beg; t < t_end; t += MOE ? 1 : (int64_t)gridDim.x) {
     const int m = batch_find(b, t);
     const MoeView& mv = b.it[m].moe;
     EvalJob job = b.it[m].job;
@@ -635,7 +637,12 @@ __global__ void __launch_bounds__(kTile, 4) mlp_tc_kernel(const __grid_constant_
     issue(1);
   }
   int k = 0;               // tiles done by this CTA
-  for (int64_t t0 = blockIdx.x; t0 < ntiles && !failed; t0 += gridDim.x, ++k) {
+  // decomposed models: each CTA takes a contiguous range of tiles, which stay in one
+  // subdomain for long runs (fewer expert switches); otherwise tiles are strided over CTAs
+  const int64_t t_beg = MOE ? (int64_t)blockIdx.x * ntiles / gridDim.x : (int64_t)blockIdx.x;
+  const int64_t t_end = MOE ? ((int64_t)blockIdx.x + 1) * ntiles / gridDim.x : ntiles;
+  const int64_t t_step = MOE ? 1 : (int64_t)gridDim.x;
+  for (int64_t t0 = t_beg; t0 < t_end && !failed; t0 += t_step, ++k) {
     const int m = batch_find(b, t0);
     const MoeView& mv = b.it[m].moe;
     const bool moe = MOE && mv.experts != nullptr;

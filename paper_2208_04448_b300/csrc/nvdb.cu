@@ -725,6 +725,12 @@ TrainJob grid_train_job(const nvdb_grid* g, int net, const nvdb_train_opts* o) {
   j.leaf_origin = g->leaf_origin; j.leaf_mask = g->leaf_mask; j.n_leaf = g->n_leaf;
   j.ijk = g->ijk; j.val = g->val; j.n = g->n;
   j.tscale = g->grid_class == 0 ? 1.f / g->half_width : 1.f;
+  j.resample = o->resample;
+  j.sampling = net == 2 ? o->sampling : 0;
+  j.leaf_first = g->leaf_first;
+  j.log2e = g->log2e;
+  j.gx = g->origin[0]; j.gy = g->origin[1]; j.gz = g->origin[2];
+  j.bg_target = g->grid_class == 0 ? 1.f : 0.f;   // the background (+w for level sets), scaled
   return j;
 }
 
@@ -795,6 +801,11 @@ extern "C" nvdb_status nvdb_compress(const nvdb_grid* g, const nvdb_train_opts* 
   if (g->n == 0) return fail(NVDB_ERR_INVALID_ARG, "nvdb_compress: empty grid");
   if ((uint64_t)g->n_leaf * 512 >= (1ull << 32) || (uint64_t)g->n_l1 * 4096 >= (1ull << 32))
     return fail(NVDB_ERR_UNSUPPORTED, "candidate population >= 2^32");
+  if (o->resample < 0 || (uint64_t)o->resample * (uint64_t)o->batch >= (1ull << 32))
+    return fail(NVDB_ERR_INVALID_ARG, "resample x batch must be in [0, 2^32)");
+  if (o->sampling < 0 || o->sampling > 2) return fail(NVDB_ERR_INVALID_ARG, "sampling must be 0, 1 or 2");
+  if (o->sampling == 2 && (g->log2e > 10 || o->subdomain || (warm && warm->moe())))
+    return fail(NVDB_ERR_UNSUPPORTED, "dense sampling: extent at most 1024 and no decomposition");
   const int sub = warm ? warm->sub_size : o->subdomain;
   const int halo = warm ? warm->sub_halo : (o->halo ? o->halo : 8);
   if (sub < 0 || sub % 512 || (sub && (halo < 8 || (halo & (halo - 1)) || 4 * halo > sub)))
@@ -1079,6 +1090,58 @@ extern "C" nvdb_status nvdb_compress(const nvdb_grid* g, const nvdb_train_opts* 
   const nvdb_status st = run();
   if (st != NVDB_OK) { delete m; return st; }
   *out = m;
+  return NVDB_OK;
+}
+
+extern "C" nvdb_status nvdb_compress_sequence(const nvdb_grid* const* grids, int n_frames, const nvdb_train_opts* o,
+                                              float refine_lr_scale, int32_t refine_steps, int32_t warm_steps,
+                                              nvdb_stream stream, nvdb_model** out) {
+  const Range range("nvdb_compress_sequence");
+  if (!grids || n_frames <= 0 || !o || !out || refine_steps < 0 || warm_steps < 0 || !(refine_lr_scale > 0.f) ||
+      o->stop_window <= 0)
+    return fail(NVDB_ERR_INVALID_ARG, "nvdb_compress_sequence: bad arguments");
+  for (int f = 0; f < n_frames; ++f)
+    if (!grids[f]) return fail(NVDB_ERR_INVALID_ARG, "nvdb_compress_sequence: NULL grid %d", f);
+  std::vector<nvdb_model*> ms(n_frames, nullptr);
+  auto cleanup = [&]() { for (auto* m : ms) delete m; };
+  nvdb_train_opts a = *o;
+  for (int k = 0; k < 3; ++k) a.stop_loss[k] = 0.f;
+  a.resume = 0;
+  nvdb_status st = nvdb_compress(grids[0], &a, nullptr, stream, &ms[0]);   // frame 0, cold
+  if (st == NVDB_OK && refine_steps > 0) {   // frame 0 refined at the lower rate
+    nvdb_train_opts r = a;
+    r.lr = a.lr * refine_lr_scale;
+    r.steps = refine_steps;
+    nvdb_model* refined = nullptr;
+    st = nvdb_compress(grids[0], &r, ms[0], stream, &refined);
+    if (st == NVDB_OK) {
+      delete ms[0];
+      ms[0] = refined;
+    }
+  }
+  float target[3] = {0.f, 0.f, 0.f};
+  if (st == NVDB_OK)
+    for (int k = 0; k < 3; ++k) {   // frame 0's final loss (experts: their mean)
+      double sum = 0.0;
+      int64_t cnt = 0;
+      for (int e = 0; e < ms[0]->n_exp; ++e) {
+        const auto& l = ms[0]->losses[3 * e + k];
+        for (size_t i = l.size() > (size_t)o->stop_window ? l.size() - o->stop_window : 0; i < l.size(); ++i, ++cnt) sum += l[i];
+      }
+      target[k] = cnt ? (float)(sum / cnt) : 0.f;
+    }
+  for (int f = 1; f < n_frames && st == NVDB_OK; ++f) {   // warm frames with the early stop
+    nvdb_train_opts w = a;
+    w.lr = a.lr * refine_lr_scale;
+    w.steps = warm_steps;
+    for (int k = 0; k < 3; ++k) w.stop_loss[k] = target[k];
+    st = nvdb_compress(grids[f], &w, ms[f - 1], stream, &ms[f]);
+  }
+  if (st != NVDB_OK) {
+    cleanup();
+    return st;
+  }
+  for (int f = 0; f < n_frames; ++f) out[f] = ms[f];
   return NVDB_OK;
 }
 

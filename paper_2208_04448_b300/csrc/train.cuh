@@ -33,6 +33,17 @@ struct TrainJob {
   // (pop[i >> pop_shift] << pop_shift) | (i & (2^pop_shift - 1)) of the population above,
   // pop_n << pop_shift elements (pop_shift = 9 for the level-0 classifier: lists of leaves)
   const uint32_t* pop; int64_t pop_n; int pop_shift;
+  // subset resampling (Appendix E): every `resample` steps a subset of resample * batch
+  // candidates is drawn (element i of interval r: Philox counter (i / 4, r, stream, 1), word
+  // i % 4); each step draws its batch from the current subset.  0 = a fresh batch per step.
+  int resample;
+  // regressor population (Appendix C ablation): 0 the active voxels (sparse, the method),
+  // 1 every voxel of the leaves (blocked), 2 every voxel of the domain's bounding box (dense,
+  // log2 extent <= 10); inactive voxels take the target bg_target (the background)
+  int sampling;
+  const int64_t* leaf_first;  // blocked / dense: index of each leaf's first voxel
+  int log2e, gx, gy, gz;      // dense: domain extent and origin
+  float bg_target;
   float tscale;               // regressor target = val * tscale
   float* partial;             // [gridDim.x][P + 1]: gradient partials, then the loss sum
   uint32_t* status;           // ST_* bits (tensor-core kernel: a timed-out wait)
@@ -53,7 +64,27 @@ enum : int { LOSS_MSE = 0, LOSS_L1 = 1, LOSS_BCE = 2, LOSS_LINEAR = 3 };
 
 __device__ __forceinline__ int64_t train_population(const TrainJob& j) {
   if (j.pop) return j.pop_n << j.pop_shift;
+  if (j.net == 2 && j.sampling == 1) return j.n_leaf * 512;
+  if (j.net == 2 && j.sampling == 2) return (int64_t)1 << (3 * j.log2e);
   return j.net == 0 ? j.n_l1 * 4096 : j.net == 1 ? j.n_leaf * 512 : j.n;
+}
+
+// Canonical key of the leaf holding voxel (i, j, k): level-2 key, level-1 slot, leaf slot.
+__device__ __forceinline__ uint64_t leaf_key(int i, int j, int k) {
+  const uint64_t l2 = ((uint64_t)(i >> 12) << 18) | ((uint64_t)(j >> 12) << 9) | (uint64_t)(k >> 12);
+  const uint64_t l1 = (uint64_t)((((i >> 7) & 31) << 10) | (((j >> 7) & 31) << 5) | ((k >> 7) & 31));
+  const uint64_t lf = (uint64_t)((((i >> 3) & 15) << 8) | (((j >> 3) & 15) << 4) | ((k >> 3) & 15));
+  return (l2 << 27) | (l1 << 12) | lf;
+}
+
+// Value target of voxel `off` of leaf `leaf` (offset bit set: its value; else the background).
+__device__ __forceinline__ float leaf_voxel_target(const TrainJob& j, int64_t leaf, int off) {
+  const unsigned long long* w = j.leaf_mask + leaf * 8;
+  if (!((w[off >> 6] >> (off & 63)) & 1ull)) return j.bg_target;
+  int64_t vi = j.leaf_first[leaf];
+  for (int q = 0; q < (off >> 6); ++q) vi += __popcll(w[q]);
+  vi += __popcll(w[off >> 6] & ((1ull << (off & 63)) - 1ull));
+  return j.val[vi] * j.tscale;
 }
 
 // Coordinates (level units) and target of sample s.
@@ -66,8 +97,45 @@ __device__ __forceinline__ void train_sample(const TrainJob& j, int64_t s, int& 
     tgt = j.target_list[s];
     return;
   }
-  uint64_t idx = sample_index(j.seed, j.stream, j.step, (uint32_t)s, (uint64_t)train_population(j));
+  const uint64_t npop = (uint64_t)train_population(j);
+  uint64_t idx;
+  if (j.resample > 0) {   // a position in the interval's subset, then that subset element
+    const uint64_t pos = sample_index(j.seed, j.stream, j.step, (uint32_t)s, (uint64_t)j.resample * j.batch);
+    const uint4 r = philox4x32_10(make_uint4((uint32_t)(pos >> 2), (uint32_t)((j.step - 1) / j.resample),
+                                             (uint32_t)j.stream, 1u),
+                                  make_uint2((uint32_t)j.seed, (uint32_t)(j.seed >> 32)));
+    const uint32_t u = (pos & 3) == 0 ? r.x : (pos & 3) == 1 ? r.y : (pos & 3) == 2 ? r.z : r.w;
+    idx = ((uint64_t)u * npop) >> 32;
+  } else {
+    idx = sample_index(j.seed, j.stream, j.step, (uint32_t)s, npop);
+  }
   if (j.pop) idx = ((uint64_t)j.pop[idx >> j.pop_shift] << j.pop_shift) | (idx & ((1ull << j.pop_shift) - 1));
+  if (j.net == 2 && j.sampling == 1) {   // blocked: every voxel of the leaves
+    const int64_t leaf = (int64_t)(idx >> 9);
+    const int off = (int)(idx & 511);
+    const int4 o = j.leaf_origin[leaf];
+    cx = (o.x - j.ox) + (off >> 6);
+    cy = (o.y - j.oy) + ((off >> 3) & 7);
+    cz = (o.z - j.oz) + (off & 7);
+    tgt = leaf_voxel_target(j, leaf, off);
+    return;
+  }
+  if (j.net == 2 && j.sampling == 2) {   // dense: every voxel of the domain's bounding box
+    const int e = j.log2e;
+    const int x = j.gx + (int)(idx >> (2 * e)), y = j.gy + (int)((idx >> e) & ((1u << e) - 1)),
+              z = j.gz + (int)(idx & ((1u << e) - 1));
+    cx = x - j.ox; cy = y - j.oy; cz = z - j.oz;
+    const uint64_t key = leaf_key(x, y, z);
+    int64_t lo = 0, hi = j.n_leaf;   // leaves are in canonical (key) order
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) >> 1;
+      const int4 o = j.leaf_origin[mid];
+      if (leaf_key(o.x, o.y, o.z) < key) lo = mid + 1; else hi = mid;
+    }
+    const bool found = lo < j.n_leaf && leaf_key(j.leaf_origin[lo].x, j.leaf_origin[lo].y, j.leaf_origin[lo].z) == key;
+    tgt = found ? leaf_voxel_target(j, lo, ((x & 7) << 6) | ((y & 7) << 3) | (z & 7)) : j.bg_target;
+    return;
+  }
   if (j.net == 0) {
     const int64_t node = (int64_t)(idx >> 12);
     const int slot = (int)(idx & 4095);

@@ -25,7 +25,7 @@ def test_library_exports_every_declared_symbol():
 
 def test_struct_layouts():
     import ctypes as C
-    assert C.sizeof(N.TrainOpts) == 104 and N.TrainOpts.subdomain.offset == 96
+    assert C.sizeof(N.TrainOpts) == 112 and N.TrainOpts.subdomain.offset == 96 and N.TrainOpts.sampling.offset == 108
     assert C.sizeof(N.Info) == 72 and N.Info.n_active.offset == 32 and N.Info.n_experts.offset == 64
     assert C.sizeof(N.BuildOpts) == 8
 
