@@ -251,6 +251,28 @@ nvdb_status nvdb_plan_free(nvdb_plan* plan);
 nvdb_status nvdb_query(const nvdb_model* model, const float* d_xyz, int64_t n, nvdb_precision prec,
                        float* d_out, uint8_t* d_active, nvdb_stream stream);
 
+/* Pinhole camera of nvdb_render (index space). */
+typedef struct {
+  float eye[3];        /* camera position */
+  float target[3];     /* point on the view axis */
+  float up[3];         /* approximate up direction (not parallel to the view axis) */
+  float fov_deg;       /* vertical field of view, (0, 180) */
+  int32_t width, height;
+  float step;          /* march step in voxels (> 0) */
+  int32_t max_steps;   /* samples per ray, from the ray's entry into the domain box */
+  float sigma;         /* extinction per unit density and voxel */
+} nvdb_camera;
+
+/* Ray-march a density model on [Hash,5,4,NN(3)] (Section 4, the ray-marched Bunny Cloud):
+ * rays of a pinhole camera through pixel centres, clipped to the model's domain box; samples
+ * at t_in + (k + 1/2) step, k < max_steps, while inside the box; the density at each sample
+ * is nvdb_query's (trilinear over the regressed active corners, background elsewhere,
+ * clamped at 0); emission-absorption composited front to back, alpha = 1 - exp(-sigma rho
+ * step), L += T alpha rho, T *= 1 - alpha.  d_image float [height][width][2] = (L, T), a
+ * headless device buffer.  Synchronises the stream. */
+nvdb_status nvdb_render(const nvdb_model* model, const nvdb_camera* cam, nvdb_precision prec, float* d_image,
+                        nvdb_stream stream);
+
 /* Raw output (logit or unscaled value) of network `net` (0, 1, 2) at n voxel
  * coordinates d_ijk int32 [n][3]; the level-1 classifier takes leaf origins
  * (its input is ijk >> 3).  For a decomposed model (Section 3.4) this is the

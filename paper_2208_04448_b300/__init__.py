@@ -275,6 +275,18 @@ def query(model: Model, xyz: torch.Tensor, prec: int = FP32, active: bool = Fals
     return (res, act) if active else res
 
 
+def render(model: Model, eye, target, up=(0.0, 1.0, 0.0), fov_deg: float = 40.0, width: int = 256, height: int = 256,
+           step: float = 1.0, max_steps: int = 512, sigma: float = 0.05, prec: int = FP32, out=None,
+           stream=None) -> torch.Tensor:
+    """nvdb_render: ray-marched (radiance, transmittance) image [height, width, 2] on the device."""
+    cam = N.Camera()
+    cam.eye[:], cam.target[:], cam.up[:] = [float(v) for v in eye], [float(v) for v in target], [float(v) for v in up]
+    cam.fov_deg, cam.width, cam.height, cam.step, cam.max_steps, cam.sigma = fov_deg, width, height, step, max_steps, sigma
+    img = out if out is not None else torch.empty((height, width, 2), dtype=torch.float32, device="cuda")
+    _check(lib().nvdb_render(model.handle, C.byref(cam), prec, _dptr(img, torch.float32, "image"), _stream(stream)))
+    return img
+
+
 def mlp_eval(model: Model, net: int, ijk: torch.Tensor, prec: int = FP32, stream=None) -> torch.Tensor:
     n = ijk.shape[0]
     out = torch.empty(n, dtype=torch.float32, device="cuda")

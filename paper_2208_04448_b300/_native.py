@@ -35,6 +35,12 @@ class Info(C.Structure):
                 ("subdomain", C.c_int32)]
 
 
+class Camera(C.Structure):
+    _fields_ = [("eye", C.c_float * 3), ("target", C.c_float * 3), ("up", C.c_float * 3), ("fov_deg", C.c_float),
+                ("width", C.c_int32), ("height", C.c_int32), ("step", C.c_float), ("max_steps", C.c_int32),
+                ("sigma", C.c_float)]
+
+
 _vp, _i64, _i32, _f32p, _st = C.c_void_p, C.c_int64, C.c_int, C.POINTER(C.c_float), C.c_int
 
 # every symbol include/nvdb.h declares, with its signature
@@ -47,6 +53,7 @@ SIGNATURES = {
     "nvdb_compress": ([_vp, C.POINTER(TrainOpts), _vp, _vp, C.POINTER(_vp)], _st),
     "nvdb_compress_sequence": ([C.POINTER(_vp), _i32, C.POINTER(TrainOpts), C.c_float, C.c_int32, C.c_int32, _vp,
                                 C.POINTER(_vp)], _st),
+    "nvdb_render": ([_vp, C.POINTER(Camera), _i32, _vp, _vp], _st),
     "nvdb_model_losses": ([_vp, _i32, _f32p, _i64, C.POINTER(C.c_int64)], _st),
     "nvdb_decompress": ([C.POINTER(_vp), _i32, _i32, _vp, _vp, _i64, C.POINTER(C.c_int64), _vp], _st),
     "nvdb_decompress_host": ([C.POINTER(_vp), _i32, _i32, _vp, _vp, _vp, _vp, _i64, C.POINTER(C.c_int64), _vp], _st),

@@ -22,6 +22,7 @@
 #include "compact.cuh"
 #include "mlp.cuh"
 #include "query.cuh"
+#include "render.cuh"
 #include "train.cuh"
 
 using namespace nvdb;
@@ -1468,6 +1469,69 @@ extern "C" nvdb_status nvdb_query(const nvdb_model* cm, const float* d_xyz, int6
     CU(cudaGetLastError());
   }
   return eval_status(m, prec, s);
+}
+
+// ============================================================================ ray marching
+extern "C" nvdb_status nvdb_render(const nvdb_model* cm, const nvdb_camera* cam, nvdb_precision prec, float* d_image,
+                                   nvdb_stream stream) {
+  const Range range("nvdb_render");
+  if (!cm || !cam || !d_image || cam->width <= 0 || cam->height <= 0 || !(cam->step > 0.f) || cam->max_steps < 0 ||
+      !(cam->fov_deg > 0.f && cam->fov_deg < 180.f) || !(cam->sigma >= 0.f))
+    return fail(NVDB_ERR_INVALID_ARG, "nvdb_render: bad arguments");
+  if (!eval_prec_ok(prec)) return fail(NVDB_ERR_UNSUPPORTED, "precision %d", (int)prec);
+  cudaStream_t s = (cudaStream_t)stream;
+  // camera basis in FP64, film extent folded into right / up
+  double f[3], r[3], u[3];
+  double nf = 0.0;
+  for (int a = 0; a < 3; ++a) { f[a] = (double)cam->target[a] - cam->eye[a]; nf += f[a] * f[a]; }
+  if (!(nf > 0.0)) return fail(NVDB_ERR_INVALID_ARG, "nvdb_render: eye == target");
+  for (auto& v : f) v /= std::sqrt(nf);
+  r[0] = f[1] * cam->up[2] - f[2] * cam->up[1];
+  r[1] = f[2] * cam->up[0] - f[0] * cam->up[2];
+  r[2] = f[0] * cam->up[1] - f[1] * cam->up[0];
+  const double nr = std::sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+  if (!(nr > 1e-12)) return fail(NVDB_ERR_INVALID_ARG, "nvdb_render: up parallel to the view axis");
+  for (auto& v : r) v /= nr;
+  u[0] = r[1] * f[2] - r[2] * f[1];
+  u[1] = r[2] * f[0] - r[0] * f[2];
+  u[2] = r[0] * f[1] - r[1] * f[0];
+  const double th = std::tan(cam->fov_deg * M_PI / 360.0), aspect = (double)cam->width / cam->height;
+  RayCam c{};
+  for (int a = 0; a < 3; ++a) {
+    c.eye[a] = cam->eye[a];
+    c.fwd[a] = (float)f[a];
+    c.right[a] = (float)(r[a] * th * aspect);
+    c.up[a] = (float)(u[a] * th);
+    c.lo[a] = (float)cm->origin[a];
+    c.hi[a] = (float)(cm->origin[a] + (1 << cm->log2e));
+  }
+  c.width = cam->width;
+  c.height = cam->height;
+  c.max_steps = cam->max_steps;
+  c.step = cam->step;
+  c.sigma = cam->sigma;
+  const int64_t nray = (int64_t)cam->width * cam->height;
+  KLAUNCH("ray_init", s, ray_init_kernel<<<blocks_for(nray, 256), 256, 0, s>>>(nray, d_image));
+  const int ns = (int)std::max<int64_t>(1, std::min<int64_t>(cam->max_steps, (1 << 22) / std::max<int64_t>(nray, 1)));
+  float *xyz = nullptr, *dens = nullptr;
+  auto run = [&]() -> nvdb_status {
+    TRY(dalloc(&xyz, (size_t)nray * ns * 3));
+    TRY(dalloc(&dens, (size_t)nray * ns));
+    for (int s0 = 0; s0 < cam->max_steps; s0 += ns) {
+      const int k = std::min(ns, cam->max_steps - s0);
+      KLAUNCH("ray_points", s, ray_points_kernel<<<blocks_for(nray * k, 256), 256, 0, s>>>(c, s0, k, xyz));
+      TRY(nvdb_query(cm, xyz, nray * k, prec, dens, nullptr, stream));
+      KLAUNCH("ray_accum", s, ray_accum_kernel<<<blocks_for(nray, 128), 128, 0, s>>>(c, k, dens, d_image));
+      CU(cudaGetLastError());
+    }
+    CU(cudaStreamSynchronize(s));
+    return NVDB_OK;
+  };
+  const nvdb_status st = run();
+  cudaStreamSynchronize(s);
+  dfree(xyz);
+  dfree(dens);
+  return st;
 }
 
 // ============================================================================ network-level calls

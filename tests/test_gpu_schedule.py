@@ -63,15 +63,16 @@ def test_ablation_populations(sampling):
 def test_sparse_training_beats_dense():
     """Appendix C: with the same network and schedule, the regressor trained on the active
     voxels reconstructs them better than one trained on the blocked or dense grid."""
-    ijk, val, _ = workload("fog64")
-    g = nv.build(ijk.cuda().contiguous(), val.cuda().contiguous(), 1, 3.0)
+    ijk, val, _ = workload("fog512", device="cuda")
+    g = nv.build(ijk.contiguous(), val.contiguous(), 1, 0.0)
+    sigma = 10.0 * (1 << g.info()["log2_extent"]) / 1024.0
     rmse = {}
     for sampling in (0, 1, 2):
-        m = nv.compress(g, seed=5, ffm_sigma=2.0, steps=400, batch=8192, lr=2e-3, width=[32, 32, 64],
-                        layers=[3, 3, 3], ffm_size=[32, 64], patch_precs=1, sampling=sampling, train_prec=nv.BF16)
+        m = nv.compress(g, seed=5, ffm_sigma=sigma, steps=1000, batch=65536, width=[32, 32, 64], layers=[3, 3, 4],
+                        ffm_size=[64, 64], patch_precs=1, sampling=sampling, train_prec=nv.BF16)
         _, dval, _ = nv.decompress(m, nv.FP32)
-        rmse[sampling] = float(torch.sqrt(torch.mean((dval.cpu() - val) ** 2)))
-    print("rmse on active voxels (sparse, blocked, dense):", rmse)
+        rmse[sampling] = float(torch.sqrt(torch.mean((dval - val) ** 2)))
+    print("rmse on active voxels (sparse, blocked, dense):", rmse, "std", float(val.std()))
     assert rmse[0] < rmse[2] and rmse[0] <= rmse[1] * 1.05
 
 
@@ -83,10 +84,11 @@ def test_sequence_equals_chain_of_compress_calls():
     seq = nv.compress_sequence(grids, refine_lr_scale=0.05, refine_steps=60, warm_steps=200, steps=200, lr=1e-3,
                                **shape)
     m0 = nv.compress(grids[0], steps=200, lr=1e-3, **shape)
-    chain = [nv.compress(grids[0], steps=60, lr=5e-5, warm=m0, **shape)]
-    target = [float(np.mean(chain[0].losses(k)[-20:])) for k in range(3)]
+    lr1 = float(np.float32(1e-3) * np.float32(0.05))     # the library scales the rate in FP32
+    chain = [nv.compress(grids[0], steps=60, lr=lr1, warm=m0, **shape)]
+    target = [float(np.mean(chain[0].losses(k)[-20:].astype(np.float64))) for k in range(3)]
     for f in range(1, 4):
-        chain.append(nv.compress(grids[f], steps=200, lr=5e-5, warm=chain[-1], stop_loss=target, **shape))
+        chain.append(nv.compress(grids[f], steps=200, lr=lr1, warm=chain[-1], stop_loss=target, **shape))
     for a, b in zip(seq, chain):
         assert a.export() == b.export()
     assert len(seq[0].losses(0)) == 60                    # frame 0 is the refined model
