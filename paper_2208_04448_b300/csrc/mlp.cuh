@@ -259,9 +259,7 @@ __global__ void __launch_bounds__(kTile, 3) mlp_f32_kernel(const __grid_constant
     __syncthreads();
     staged = net.p32;
   };
-  const int64_t t_beg = MOE ? (int64_t)blockIdx.x * ntiles / gridDim.x : (int64_t)blockIdx.x;
-  const int64_t t_end = MOE ? ((int64_t)blockIdx.x + 1) * ntiles / gridDim.x : ntiles;
-  for (int64_t t = t_beg; t < t_end; t += MOE ? 1 : (int64_t)gridDim.x) {
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const int m = batch_find(b, t);
     const MoeView& mv = b.it[m].moe;
     EvalJob job = b.it[m].job;
@@ -637,12 +635,9 @@ __global__ void __launch_bounds__(kTile, 4) mlp_tc_kernel(const __grid_constant_
     issue(1);
   }
   int k = 0;               // tiles done by this CTA
-  // decomposed models: each CTA takes a contiguous range of tiles, which stay in one
-  // subdomain for long runs (fewer expert switches); otherwise tiles are strided over CTAs
-  const int64_t t_beg = MOE ? (int64_t)blockIdx.x * ntiles / gridDim.x : (int64_t)blockIdx.x;
-  const int64_t t_end = MOE ? ((int64_t)blockIdx.x + 1) * ntiles / gridDim.x : ntiles;
-  const int64_t t_step = MOE ? 1 : (int64_t)gridDim.x;
-  for (int64_t t0 = t_beg; t0 < t_end && !failed; t0 += t_step, ++k) {
+  // tiles strided over the CTAs (for decomposed models too: contiguous ranges measured
+  // slower, the tiles of the halos, which take several expert passes, bunch up in a few CTAs)
+  for (int64_t t0 = blockIdx.x; t0 < ntiles && !failed; t0 += gridDim.x, ++k) {
     const int m = batch_find(b, t0);
     const MoeView& mv = b.it[m].moe;
     const bool moe = MOE && mv.experts != nullptr;
