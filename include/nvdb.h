@@ -151,6 +151,31 @@ nvdb_status nvdb_grid_read(const nvdb_grid* grid, int32_t* ijk, float* val, int3
 
 nvdb_status nvdb_grid_free(nvdb_grid* grid);
 
+/* Point samples of the explicit grid (the comparison samplers of Section 4.4): order 0 the
+ * value of the voxel nearest p (floor(p + 1/2)), 1 trilinear over the cell's 8 corners
+ * (corner c = 4a + 2b + d, weight (wx wy) wz), 3 Catmull-Rom tricubic over the 4^3 voxels
+ * around the cell; inactive voxels take the background (+half_width for level sets, 0 for
+ * fog).  d_xyz float [n][3] (index space), d_out float [n].  The first call builds the
+ * grid's random-access structures (keys, per-word popcount prefixes, child bases) and
+ * synchronises; later calls do not. */
+nvdb_status nvdb_grid_sample(const nvdb_grid* grid, const float* d_xyz, int64_t n, int order, float* d_out,
+                             nvdb_stream stream);
+
+/* Zero crossings of a level-set grid along the +x, +y, +z edges of its active voxels whose
+ * neighbour is active with the other sign (the isosurface points of Eq. 4's mCD): v + t e_a,
+ * t = val(v) / (val(v) - val(v + e_a)), in canonical voxel order then axis order.  With
+ * d_pts NULL only *count is set; else d_pts float [capacity][3] (CAPACITY if too small).
+ * Synchronises the stream. */
+nvdb_status nvdb_grid_isosurface(const nvdb_grid* grid, float* d_pts, int64_t capacity, int64_t* count,
+                                 nvdb_stream stream);
+
+/* Modified Chamfer distance (Eq. 4) between a reference and a reconstructed level set:
+ * mCD = 1/(2 N1) sum_i |SDF_rec(v1_i)| + 1/(2 N2) sum_i |SDF_ref(v2_i)|, v1 / v2 the
+ * isosurface points of the reference / reconstruction (nvdb_grid_isosurface), each SDF
+ * sampled trilinearly from the other grid (nvdb_grid_sample, order 1).  *mcd (HOST) in
+ * voxels.  Synchronises the stream. */
+nvdb_status nvdb_mcd(const nvdb_grid* reference, const nvdb_grid* reconstruction, double* mcd, nvdb_stream stream);
+
 /* Fill opts with the defaults: widths 32, 3 layers, ffm_size 0, sigma 1.25,
  * 200 steps, batch 4096, lr 1e-3, decay 0.975 every 100 steps, MSE, FP32
  * training, patches for FP32, BF16 and FP16, seed 1, no early stop (window 50). */

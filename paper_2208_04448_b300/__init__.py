@@ -275,6 +275,33 @@ def query(model: Model, xyz: torch.Tensor, prec: int = FP32, active: bool = Fals
     return (res, act) if active else res
 
 
+def grid_sample(grid: Grid, xyz: torch.Tensor, order: int = 1, out=None, stream=None) -> torch.Tensor:
+    """nvdb_grid_sample: order-0 / 1 / 3 point samples of the explicit grid."""
+    n = xyz.shape[0]
+    res = out if out is not None else torch.empty(n, dtype=torch.float32, device="cuda")
+    _check(lib().nvdb_grid_sample(grid.handle, _dptr(xyz, torch.float32, "xyz"), n, order,
+                                  _dptr(res, torch.float32, "out"), _stream(stream)))
+    return res
+
+
+def grid_isosurface(grid: Grid, stream=None) -> torch.Tensor:
+    """nvdb_grid_isosurface: the level set's zero crossings along voxel edges, float [m, 3]."""
+    cnt = C.c_int64()
+    _check(lib().nvdb_grid_isosurface(grid.handle, None, 0, C.byref(cnt), _stream(stream)))
+    pts = torch.empty((cnt.value, 3), dtype=torch.float32, device="cuda")
+    if cnt.value:
+        _check(lib().nvdb_grid_isosurface(grid.handle, _dptr(pts, torch.float32, "pts"), cnt.value, C.byref(cnt),
+                                          _stream(stream)))
+    return pts
+
+
+def mcd(reference: Grid, reconstruction: Grid, stream=None) -> float:
+    """nvdb_mcd: modified Chamfer distance (Eq. 4) between two level-set grids, in voxels."""
+    v = C.c_double()
+    _check(lib().nvdb_mcd(reference.handle, reconstruction.handle, C.byref(v), _stream(stream)))
+    return v.value
+
+
 def render(model: Model, eye, target, up=(0.0, 1.0, 0.0), fov_deg: float = 40.0, width: int = 256, height: int = 256,
            step: float = 1.0, max_steps: int = 512, sigma: float = 0.05, prec: int = FP32, out=None,
            stream=None) -> torch.Tensor:

@@ -54,6 +54,9 @@ SIGNATURES = {
     "nvdb_compress_sequence": ([C.POINTER(_vp), _i32, C.POINTER(TrainOpts), C.c_float, C.c_int32, C.c_int32, _vp,
                                 C.POINTER(_vp)], _st),
     "nvdb_render": ([_vp, C.POINTER(Camera), _i32, _vp, _vp], _st),
+    "nvdb_grid_sample": ([_vp, _vp, _i64, _i32, _vp, _vp], _st),
+    "nvdb_grid_isosurface": ([_vp, _vp, _i64, C.POINTER(C.c_int64), _vp], _st),
+    "nvdb_mcd": ([_vp, _vp, C.POINTER(C.c_double), _vp], _st),
     "nvdb_model_losses": ([_vp, _i32, _f32p, _i64, C.POINTER(C.c_int64)], _st),
     "nvdb_decompress": ([C.POINTER(_vp), _i32, _i32, _vp, _vp, _i64, C.POINTER(C.c_int64), _vp], _st),
     "nvdb_decompress_host": ([C.POINTER(_vp), _i32, _i32, _vp, _vp, _vp, _vp, _i64, C.POINTER(C.c_int64), _vp], _st),

@@ -23,6 +23,7 @@
 #include "mlp.cuh"
 #include "query.cuh"
 #include "render.cuh"
+#include "sample.cuh"
 #include "train.cuh"
 
 using namespace nvdb;
@@ -128,9 +129,14 @@ struct nvdb_grid {
   unsigned long long* l1_mask = nullptr;
   int4* l2_origin = nullptr;
   unsigned long long* l2_mask = nullptr;
+  // random-access structures of the explicit tree (built on first use by the samplers)
+  uint64_t* l2_key = nullptr;
+  uint32_t *l2_pre = nullptr, *l1_pre = nullptr;
+  int64_t *l2_base = nullptr, *l1_base = nullptr;
   ~nvdb_grid() {
     dfree(ijk); dfree(val); dfree(leaf_origin); dfree(leaf_first); dfree(leaf_mask);
     dfree(l1_origin); dfree(l1_mask); dfree(l2_origin); dfree(l2_mask);
+    dfree(l2_key); dfree(l2_pre); dfree(l1_pre); dfree(l2_base); dfree(l1_base);
   }
 };
 
@@ -1469,6 +1475,168 @@ extern "C" nvdb_status nvdb_query(const nvdb_model* cm, const float* d_xyz, int6
     CU(cudaGetLastError());
   }
   return eval_status(m, prec, s);
+}
+
+// ============================================================================ explicit-grid sampling, mCD
+namespace {
+__global__ void mask_count64_kernel(const unsigned long long* words, int wpi, int64_t n, uint32_t* counts) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  uint32_t c = 0;
+  for (int w = 0; w < wpi; ++w) c += __popcll(words[t * wpi + w]);
+  counts[t] = c;
+}
+
+// The grid's random-access view; the key, prefix and base arrays are built once per grid.
+nvdb_status grid_view(nvdb_grid* g, cudaStream_t s, GridView* out) {
+  if (!g->l2_key && g->n > 0) {
+    Scan sc;
+    uint32_t* cnt = nullptr;
+    auto run = [&]() -> nvdb_status {
+      TRY(dalloc(&g->l2_key, g->n_l2)); TRY(dalloc(&g->l2_pre, 512 * g->n_l2)); TRY(dalloc(&g->l2_base, g->n_l2 + 1));
+      TRY(dalloc(&g->l1_pre, 64 * g->n_l1)); TRY(dalloc(&g->l1_base, g->n_l1 + 1));
+      TRY(dalloc(&cnt, (size_t)std::max(g->n_l2, g->n_l1) + 1));
+      KLAUNCH("l2_keys", s, l2_keys_kernel<<<blocks_for(g->n_l2, 128), 128, 0, s>>>(g->l2_origin, g->n_l2, g->l2_key));
+      KLAUNCH("word_prefix64", s, word_prefix64_kernel<<<blocks_for(g->n_l2, 128), 128, 0, s>>>(
+                                      reinterpret_cast<const uint64_t*>(g->l2_mask), 512, g->n_l2, g->l2_pre));
+      KLAUNCH("mask_count", s, mask_count64_kernel<<<blocks_for(g->n_l2, 128), 128, 0, s>>>(g->l2_mask, 512, g->n_l2, cnt));
+      TRY(sc.run(cnt, g->n_l2, g->l2_base, s));
+      KLAUNCH("word_prefix64", s, word_prefix64_kernel<<<blocks_for(g->n_l1, 128), 128, 0, s>>>(
+                                      reinterpret_cast<const uint64_t*>(g->l1_mask), 64, g->n_l1, g->l1_pre));
+      KLAUNCH("mask_count", s, mask_count64_kernel<<<blocks_for(g->n_l1, 128), 128, 0, s>>>(g->l1_mask, 64, g->n_l1, cnt));
+      TRY(sc.run(cnt, g->n_l1, g->l1_base, s));
+      CU(cudaStreamSynchronize(s));
+      return NVDB_OK;
+    };
+    const nvdb_status st = run();
+    dfree(cnt);
+    if (st != NVDB_OK) { dfree(g->l2_key); return st; }
+  }
+  GridView v;
+  v.n_l2 = g->n_l2;
+  v.l2_key = g->l2_key;
+  v.l2_mask = reinterpret_cast<const uint64_t*>(g->l2_mask);
+  v.l2_pre = g->l2_pre;
+  v.l2_base = g->l2_base;
+  v.l1_mask = reinterpret_cast<const uint64_t*>(g->l1_mask);
+  v.l1_pre = g->l1_pre;
+  v.l1_base = g->l1_base;
+  v.leaf_mask = reinterpret_cast<const uint64_t*>(g->leaf_mask);
+  v.leaf_first = g->leaf_first;
+  v.val = g->val;
+  v.background = g->background;
+  *out = v;
+  return NVDB_OK;
+}
+
+nvdb_status iso_points(nvdb_grid* g, cudaStream_t s, float** pts, int64_t* count) {
+  *pts = nullptr;
+  *count = 0;
+  if (g->n == 0) return NVDB_OK;
+  GridView v;
+  TRY(grid_view(g, s, &v));
+  uint32_t* cnt = nullptr;
+  int64_t* off = nullptr;
+  Scan sc;
+  auto run = [&]() -> nvdb_status {
+    TRY(dalloc(&cnt, g->n)); TRY(dalloc(&off, g->n));
+    KLAUNCH("iso_count", s, iso_count_kernel<<<blocks_for(g->n, 256), 256, 0, s>>>(v, g->ijk, g->n, cnt));
+    TRY(sc.run(cnt, g->n, off, s));
+    CU(cudaMemcpyAsync(count, sc.total, 8, cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    TRY(dalloc(pts, 3 * (size_t)*count + 3));
+    KLAUNCH("iso_emit", s, iso_emit_kernel<<<blocks_for(g->n, 256), 256, 0, s>>>(v, g->ijk, g->n, off, *pts));
+    CU(cudaGetLastError());
+    return NVDB_OK;
+  };
+  const nvdb_status st = run();
+  cudaStreamSynchronize(s);
+  dfree(cnt);
+  dfree(off);
+  if (st != NVDB_OK) dfree(*pts);
+  return st;
+}
+
+// sum_i |out_i| over a device array, blocks reduced in order
+nvdb_status abs_sum(const float* x, int64_t n, cudaStream_t s, double* out) {
+  *out = 0.0;
+  if (n == 0) return NVDB_OK;
+  const int nb = (int)std::min<int64_t>(blocks_for(n, 256), 1024);
+  double* bs = nullptr;
+  TRY(dalloc(&bs, nb));
+  std::vector<double> h(nb);
+  KLAUNCH("abs_sum", s, abs_sum_kernel<<<nb, 256, 0, s>>>(x, n, bs));
+  cudaError_t e = cudaMemcpyAsync(h.data(), bs, nb * 8, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  dfree(bs);
+  if (e != cudaSuccess) return fail(NVDB_ERR_CUDA, "abs_sum: %s", cudaGetErrorString(e));
+  for (double v : h) *out += v;
+  return NVDB_OK;
+}
+}  // namespace
+
+extern "C" nvdb_status nvdb_grid_sample(const nvdb_grid* cg, const float* d_xyz, int64_t n, int order, float* d_out,
+                                        nvdb_stream stream) {
+  if (!cg || n < 0 || (n > 0 && (!d_xyz || !d_out)) || (order != 0 && order != 1 && order != 3))
+    return fail(NVDB_ERR_INVALID_ARG, "nvdb_grid_sample: bad arguments");
+  if (n == 0) return NVDB_OK;
+  nvdb_grid* g = const_cast<nvdb_grid*>(cg);
+  cudaStream_t s = (cudaStream_t)stream;
+  GridView v;
+  TRY(grid_view(g, s, &v));
+  KLAUNCH("grid_sample", s, grid_sample_kernel<<<blocks_for(n, 256), 256, 0, s>>>(v, d_xyz, n, order, d_out));
+  CU(cudaGetLastError());
+  return NVDB_OK;
+}
+
+extern "C" nvdb_status nvdb_grid_isosurface(const nvdb_grid* cg, float* d_pts, int64_t capacity, int64_t* count,
+                                            nvdb_stream stream) {
+  if (!cg || !count || capacity < 0) return fail(NVDB_ERR_INVALID_ARG, "nvdb_grid_isosurface: bad arguments");
+  if (cg->grid_class != 0) return fail(NVDB_ERR_UNSUPPORTED, "nvdb_grid_isosurface: level sets only");
+  cudaStream_t s = (cudaStream_t)stream;
+  float* pts = nullptr;
+  TRY(iso_points(const_cast<nvdb_grid*>(cg), s, &pts, count));
+  nvdb_status st = NVDB_OK;
+  if (d_pts && *count > capacity) st = fail(NVDB_ERR_CAPACITY, "nvdb_grid_isosurface: %lld points", (long long)*count);
+  else if (d_pts && *count) {
+    const cudaError_t e = cudaMemcpyAsync(d_pts, pts, (size_t)*count * 12, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) cudaStreamSynchronize(s);
+    else st = fail(NVDB_ERR_CUDA, "isosurface copy: %s", cudaGetErrorString(e));
+  }
+  dfree(pts);
+  return st;
+}
+
+extern "C" nvdb_status nvdb_mcd(const nvdb_grid* ref, const nvdb_grid* rec, double* mcd, nvdb_stream stream) {
+  const Range range("nvdb_mcd");
+  if (!ref || !rec || !mcd) return fail(NVDB_ERR_INVALID_ARG, "nvdb_mcd: bad arguments");
+  if (ref->grid_class != 0 || rec->grid_class != 0) return fail(NVDB_ERR_UNSUPPORTED, "nvdb_mcd: level sets only");
+  cudaStream_t s = (cudaStream_t)stream;
+  nvdb_grid* g[2] = {const_cast<nvdb_grid*>(ref), const_cast<nvdb_grid*>(rec)};
+  double part[2] = {0.0, 0.0};
+  for (int a = 0; a < 2; ++a) {   // points of grid a's isosurface, sampled (trilinear) in the other grid
+    float *pts = nullptr, *sdf = nullptr;
+    int64_t n = 0;
+    auto run = [&]() -> nvdb_status {
+      TRY(iso_points(g[a], s, &pts, &n));
+      if (n == 0) return fail(NVDB_ERR_INVALID_ARG, "nvdb_mcd: grid %d has no zero crossing", a);
+      TRY(dalloc(&sdf, n));
+      GridView v;
+      TRY(grid_view(g[1 - a], s, &v));
+      KLAUNCH("grid_sample", s, grid_sample_kernel<<<blocks_for(n, 256), 256, 0, s>>>(v, pts, n, 1, sdf));
+      double sum = 0.0;
+      TRY(abs_sum(sdf, n, s, &sum));
+      part[a] = sum / (2.0 * (double)n);
+      return NVDB_OK;
+    };
+    const nvdb_status st = run();
+    cudaStreamSynchronize(s);
+    dfree(pts);
+    dfree(sdf);
+    TRY(st);
+  }
+  *mcd = part[0] + part[1];
+  return NVDB_OK;
 }
 
 // ============================================================================ ray marching
