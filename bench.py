@@ -204,6 +204,58 @@ def level_bytes(om: dict, prec: int) -> dict:
                 (explicit["level1_child_masks"] + explicit["leaf_active_masks"]))
 
 
+def sampling_error(nv, train_steps: int, n: int = 128, points: int = 1 << 20) -> dict:
+    """Random-sampling error at equal in-memory footprint (Section 4.4): a dense 128^3 fBm
+    density lattice encoded as [Hash,5,4,NN(3)] (explicit topology, regressor network)
+    against an explicit grid of the same noise on a coarser lattice whose values and
+    topology take about the same bytes, sampled with order 0, 1 and 3; RMSE against the
+    continuous noise at 2^20 uniform points."""
+    from fixtures import fbm_noise
+    a = torch.arange(n, device="cuda")
+    fine = torch.stack(torch.meshgrid(a, a, a, indexing="ij"), -1).reshape(-1, 3)
+    fv = fbm_noise(fine).to(torch.float32)
+    g = nv.build(fine.to(torch.int32).contiguous(), fv.contiguous(), 1, 0.0)
+    info = g.info()
+    m = nv.compress(g, seed=7, width=[32, 32, 64], layers=[3, 3, 4], ffm_size=[32, 64], ffm_sigma=6.0,
+                    steps=train_steps, batch=65536, train_prec=1, patch_precs=(1 << 0) | (1 << 3))
+    from oracle import blob
+    om = blob.read(m.export())
+    params = sum(int(sum(np.size(w) for w in net["W"]) + sum(np.size(b) for b in net["b"]) + np.size(net["wh"]) + 1)
+                 for net in om["nets"][2:3])
+    neural = 64 * info["n_leaf"] + 512 * info["n_l1"] + 4096 * info["n_l2"] + 4 * params
+
+    def explicit_bytes(c):
+        return 4 * c ** 3 + 64 * (-(-c // 8)) ** 3 + 512 * (-(-c // 128)) ** 3 + 4096
+    c = max(c for c in range(4, n + 1) if explicit_bytes(c) <= neural)
+    b = torch.arange(c, device="cuda")
+    coarse = torch.stack(torch.meshgrid(b, b, b, indexing="ij"), -1).reshape(-1, 3)
+    cv = fbm_noise(coarse.to(torch.float64) * ((n - 1) / (c - 1))).to(torch.float32)
+    gc = nv.build(coarse.to(torch.int32).contiguous(), cv.contiguous(), 1, 0.0)
+    r = torch.Generator(device="cuda").manual_seed(11)
+    p = 2.0 + (n - 5.0) * torch.rand((points, 3), generator=r, device="cuda", dtype=torch.float64)
+    truth = fbm_noise(p)
+    pf = p.to(torch.float32).contiguous()
+    pc = (p * ((c - 1) / (n - 1))).to(torch.float32).contiguous()
+    out = dict(fine_lattice=n, coarse_lattice=c, neural_bytes=neural, explicit_bytes=explicit_bytes(c), points=points)
+    for order in (0, 1, 3):
+        v = nv.grid_sample(gc, pc, order).to(torch.float64)
+        out[f"explicit_order{order}_rmse"] = float(torch.sqrt(torch.mean((v - truth) ** 2)))
+    for name, prec in (("fp32", 0), ("fp16", 3)):
+        v = nv.query(m, pf, prec).to(torch.float64)
+        out[f"neural_{name}_rmse"] = float(torch.sqrt(torch.mean((v - truth) ** 2)))
+    # the ray marcher on the same model: 512 x 512 pixels, 256 samples per ray (nvdb_render)
+    cam = dict(eye=[-80.0, 150.0, -120.0], target=[64.0, 64.0, 64.0], up=[0.0, 1.0, 0.0], fov_deg=40.0, width=512,
+               height=512, step=0.75, max_steps=256, sigma=0.05, prec=3)
+    img = nv.render(m, **cam)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    nv.render(m, out=img, **cam)
+    torch.cuda.synchronize()
+    out["render"] = dict(pixels="512x512", samples_per_ray=256, precision="fp16", ms=1e3 * (time.perf_counter() - t0),
+                         mean_transmittance=float(img[..., 1].mean()))
+    return out
+
+
 def blas_threads() -> int:
     try:
         from threadpoolctl import threadpool_info
@@ -525,6 +577,9 @@ def main():
                                                                  for e in range(moe_model.info()["n_experts"])])))
                                   for j in range(3)] if args.train_steps else None)
 
+    # ---- random-sampling error at equal footprint (Section 4.4), and the ray marcher
+    samp_err = sampling_error(nv, args.train_steps)
+
     # ---- end to end through the C ABI with host buffers
     # input: the compressed model as shipped for this precision (the same deterministic
     # training, only this precision's patch set) in pinned host memory; output: the
@@ -581,6 +636,7 @@ def main():
                    final_loss=[float(np.mean(model.losses(k)[-50:])) for k in range(3)] if args.train_steps else None),
         by_precision=by_prec,
         bytes_per_level=bytes_levels,
+        sampling_error=samp_err,
         decomposed=decomposed,
         kernels={k: dict(launches=v[0], ms=v[1]) for k, v in sorted(head_kern.items(), key=lambda kv: -kv[1][1])},
         compaction=compaction,

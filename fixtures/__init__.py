@@ -12,6 +12,7 @@ from .volumes import (  # noqa: F401
     primitives_union,
     random_primitives,
     fbm_fog,
+    fbm_noise,
     water_frame,
     water_waves,
     query_points,

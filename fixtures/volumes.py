@@ -235,6 +235,17 @@ def _value_noise(p: torch.Tensor, period: float, seed: int, octave: int) -> torc
     return out
 
 
+def fbm_noise(p: torch.Tensor, octaves=6, lacunarity=2.0, gain=0.5, seed=3, base_period=64.0) -> torch.Tensor:
+    """The fBm of fbm_fog remapped to [0, 1], at arbitrary (float) points p [N, 3]: a continuous
+    function (smoothstep-blended lattice values), the ground truth of the sampling-error study."""
+    p = p.to(F64)
+    norm = sum(gain ** o for o in range(octaves))
+    acc = torch.zeros(p.shape[0], dtype=F64, device=p.device)
+    for o in range(octaves):
+        acc = acc + (gain ** o) * _value_noise(p, base_period / (lacunarity ** o), seed, o)
+    return (acc / norm + 1.0) * 0.5
+
+
 def fbm_fog(grid=512, octaves=6, lacunarity=2.0, gain=0.5, seed=3, base_period=64.0,
             axes=(200.0, 150.0, 120.0), centre=None, threshold=0.05, device="cpu",
             chunk: int = 1 << 22):
