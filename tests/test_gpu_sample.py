@@ -32,7 +32,7 @@ def test_isosurface_and_mcd_match_oracle(grid):
     ref, g = grid
     got = nv.grid_isosurface(g).cpu().numpy()
     want = sample.isosurface(ref, 3.0)
-    assert got.shape == want.shape and np.abs(got - want).max() <= 2e-6
+    assert got.shape == want.shape and np.abs(got - want).max() <= 2e-5   # FP32 positions (~1e2 voxels)
     # a reconstruction: the same voxels, values moved by a smooth field
     ijk = ref["ijk"]
     val = ref["val"] + (0.05 * np.sin(ijk[:, 0] / 7.0)).astype(np.float32)
