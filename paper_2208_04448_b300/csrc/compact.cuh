@@ -280,9 +280,8 @@ __global__ void l2_emit_kernel(const uint64_t* l2_mask, const int4* l2_origin, i
   if (over) set_status(status, ST_CORRUPT);
 }
 
-__global__ void check_total_kernel(const int64_t* total, int64_t expect, uint32_t* status) {
-  if (*total != expect) set_status(status, ST_CORRUPT);
-}
+// A level with no items whose model header expects some: the decode is inconsistent.
+__global__ void flag_corrupt_kernel(uint32_t* status) { set_status(status, ST_CORRUPT); }
 
 // XOR of two word arrays (prediction vs truth) -> mismatch words, counted per item.
 __global__ void mismatch_count_kernel(uint32_t* pred, const uint32_t* truth, int wpi, int64_t n_items,
@@ -377,17 +376,6 @@ struct PatchBatch {
   PatchItem it[kMaxBatchC];
 };
 
-// Level-2 child-mask popcounts, one block (512 threads) per level-2 node of any model.
-__global__ void l2_count_batch_kernel(const __grid_constant__ L2Batch b, uint32_t* counts) {
-  __shared__ int64_t sh[33];
-  const int64_t g = blockIdx.x;
-  const int m = find_item(b.it, b.n, g);
-  const int64_t c = __popcll(b.it[m].mask[(g - b.it[m].start) * 512 + threadIdx.x]);
-  int64_t tot;
-  block_excl_scan(c, sh, tot);
-  if (threadIdx.x == 0) counts[g] = (uint32_t)tot;
-}
-
 // Level-1 node origins of all models, concatenated in model order, canonical within.
 __global__ void l2_emit_batch_kernel(const __grid_constant__ L2Batch b, const int64_t* off, int4* l1_origin,
                                      int64_t cap, uint32_t* status) {
@@ -413,36 +401,131 @@ __global__ void l2_emit_batch_kernel(const __grid_constant__ L2Batch b, const in
   if (over) set_status(status, ST_CORRUPT);
 }
 
-// patch_count_warp_kernel over the concatenated items of several models.
-__global__ void __launch_bounds__(256) patch_count_batch_kernel(uint32_t* words, int wpi, int64_t n_items,
-                                                               const __grid_constant__ PatchBatch b,
-                                                               uint32_t* counts) {
-  __shared__ uint32_t sw[8][128];
-  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t g = (int64_t)blockIdx.x * 8 + wib;
-  if (g >= n_items) return;
-  const int m = find_item(b.it, b.n, g);
-  const int64_t local = g - b.it[m].start;
-  uint32_t* w = words + g * wpi;
-  for (int i = lane; i < wpi; i += 32) sw[wib][i] = w[i];
-  __syncwarp();
-  const uint32_t* poff = b.it[m].off;
-  if (poff) {
-    for (uint32_t p = poff[local] + lane; p < poff[local + 1]; p += 32) {
-      const uint32_t bit = b.it[m].idx[p];
-      atomicXor(&sw[wib][bit >> 5], 1u << (bit & 31));
+}  // namespace nvdb
+
+namespace nvdb {
+
+// ---------------------------------------------------------------- single-pass scans
+// Decoupled look-back (Merrill & Garland, "Single-pass parallel prefix scan with decoupled
+// look-back", 2016): blocks take consecutive ids from a counter in the order they start, so
+// every predecessor of a block is running or done; each block publishes its aggregate, then
+// walks back over its predecessors' words until one holds an inclusive prefix, and publishes
+// its own.  Word b of `state`: bits 62-63 the flag (1 aggregate, 2 inclusive prefix), bits
+// 0-61 the value; word nblocks is the block counter.  The state is zeroed before each launch.
+// Every wait is bounded (kWaitLimitNs): on expiry the block flags ST_TIMEOUT and publishes
+// what it has, so no waiter behind it spins forever.
+constexpr uint64_t kLbAgg = 1ull << 62, kLbInc = 2ull << 62, kLbVal = (1ull << 62) - 1;
+
+__device__ __forceinline__ uint64_t lb_load(const uint64_t* p) {
+  uint64_t v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void lb_store(uint64_t* p, uint64_t v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" :: "l"(p), "l"(v) : "memory");
+}
+
+// Thread 0 of block `bid`: the sum of all earlier blocks' aggregates.
+__device__ int64_t lb_prefix(uint64_t* state, int64_t bid, int64_t agg, uint32_t* status) {
+  if (bid == 0) {
+    lb_store(state, kLbInc | (uint64_t)agg);
+    return 0;
+  }
+  lb_store(state + bid, kLbAgg | (uint64_t)agg);
+  int64_t prefix = 0;
+  const uint64_t t0 = global_ns();
+  for (int64_t p = bid - 1; p >= 0;) {
+    const uint64_t w = lb_load(state + p);
+    if ((w >> 62) == 0) {
+      if (global_ns() - t0 > kWaitLimitNs) { set_status(status, ST_TIMEOUT); break; }
+      continue;
     }
+    prefix += (int64_t)(w & kLbVal);
+    if ((w >> 62) == 2) break;
+    --p;
   }
-  __syncwarp();
-  uint32_t c = 0;
-  for (int i = lane; i < wpi; i += 32) {
-    const uint32_t v = sw[wib][i];
-    w[i] = v;
-    c += __popc(v);
+  lb_store(state + bid, kLbInc | (uint64_t)(prefix + agg));
+  return prefix;
+}
+
+__device__ __forceinline__ int64_t lb_block_id(uint64_t* state, int64_t nblocks, int64_t* sh) {
+  if (threadIdx.x == 0) *sh = (int64_t)atomicAdd(reinterpret_cast<unsigned long long*>(state + nblocks), 1ull);
+  __syncthreads();
+  return *sh;
+}
+
+// Level-2 child counts with their scan: one block (512 threads) per level-2 node of any model
+// of the batch, off[node] = level-1 nodes before it; the last block checks the total.
+__global__ void l2_scan_batch_kernel(const __grid_constant__ L2Batch b, int64_t n_nodes, int64_t* off,
+                                     int64_t expect, uint64_t* state, uint32_t* status) {
+  __shared__ int64_t sh[33];
+  __shared__ int64_t sid, spre;
+  const int64_t g = lb_block_id(state, n_nodes, &sid);
+  const int m = find_item(b.it, b.n, g);
+  const int64_t c = __popcll(b.it[m].mask[(g - b.it[m].start) * 512 + threadIdx.x]);
+  int64_t tot;
+  block_excl_scan(c, sh, tot);
+  if (threadIdx.x == 0) {
+    spre = lb_prefix(state, g, tot, status);
+    off[g] = spre;
+    if (g == n_nodes - 1 && spre + tot != expect) set_status(status, ST_CORRUPT);
   }
+}
+
+// Patch application (XOR, Section 3.3.2) and set-bit counts of the items of a level with
+// their scan: 32 items per block of 8 warps, four items per warp; off[item] = set bits
+// before it; the last block checks the total.
+constexpr int kPatchScanItems = 32;
+
+__global__ void __launch_bounds__(256) patch_scan_batch_kernel(uint32_t* words, int wpi, int64_t n_items,
+                                                              const __grid_constant__ PatchBatch b, int64_t* off,
+                                                              int64_t expect, uint64_t* state, uint32_t* status) {
+  __shared__ uint32_t sw[8][128];
+  __shared__ uint32_t scnt[kPatchScanItems];
+  __shared__ int64_t sid, spre;
+  const int64_t nblocks = (n_items + kPatchScanItems - 1) / kPatchScanItems;
+  const int64_t bid = lb_block_id(state, nblocks, &sid);
+  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int q = 0; q < kPatchScanItems / 8; ++q) {
+    const int li = wib * (kPatchScanItems / 8) + q;
+    const int64_t g = bid * kPatchScanItems + li;
+    uint32_t c = 0;
+    if (g < n_items) {
+      const int m = find_item(b.it, b.n, g);
+      const int64_t local = g - b.it[m].start;
+      uint32_t* w = words + g * wpi;
+      for (int i = lane; i < wpi; i += 32) sw[wib][i] = w[i];
+      __syncwarp();
+      const uint32_t* poff = b.it[m].off;
+      if (poff)
+        for (uint32_t p = poff[local] + lane; p < poff[local + 1]; p += 32) {
+          const uint32_t bit = b.it[m].idx[p];
+          atomicXor(&sw[wib][bit >> 5], 1u << (bit & 31));
+        }
+      __syncwarp();
+      for (int i = lane; i < wpi; i += 32) {
+        const uint32_t v = sw[wib][i];
+        w[i] = v;
+        c += __popc(v);
+      }
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-  if (lane == 0) counts[g] = c;
+      for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+      __syncwarp();
+    }
+    if (lane == 0) scnt[li] = c;
+  }
+  __syncthreads();
+  if (wib == 0) {
+    int64_t tot;
+    const int64_t ex = warp_excl_scan(scnt[lane], lane, tot);
+    if (lane == 0) {
+      spre = lb_prefix(state, bid, tot, status);
+      if (bid == nblocks - 1 && spre + tot != expect) set_status(status, ST_CORRUPT);
+    }
+    __syncwarp();
+    const int64_t g = bid * kPatchScanItems + lane;
+    if (g < n_items) off[g] = spre + ex;
+  }
 }
 
 }  // namespace nvdb

@@ -170,34 +170,40 @@ struct PatchSet {
 // levels are concatenated in model order.
 struct DecodeScratch {
   int64_t cap2 = 0, cap1 = 0, capl = 0;
-  uint32_t* l2_counts = nullptr;
   int64_t* l2_off = nullptr;
   int4* l1_origin = nullptr;
   uint32_t* l1_words = nullptr;
-  uint32_t* l1_counts = nullptr;
   int64_t* l1_off = nullptr;
   int4* leaf_origin = nullptr;
   uint32_t* leaf_words = nullptr;
-  uint32_t* leaf_counts = nullptr;
   int64_t* leaf_off = nullptr;
+  // One zero-initialised block, cleared by a single memset per decode: word 0 holds the
+  // status, then the single-pass scan states of level 2, level 1 and level 0 (one word per
+  // scan block plus the block counter).
+  uint64_t* lb = nullptr;
   uint32_t* status = nullptr;
-  Scan scan;
+  static int64_t blocks1(int64_t n) { return (n + kPatchScanItems - 1) / kPatchScanItems; }
+  static int64_t lb_words(int64_t n2, int64_t n1, int64_t nl) { return 1 + (n2 + 1) + (blocks1(n1) + 1) + (blocks1(nl) + 1); }
+  uint64_t* lb2() { return lb + 1; }
+  uint64_t* lb1() { return lb + 2 + cap2; }
+  uint64_t* lb0() { return lb + 3 + cap2 + blocks1(cap1); }
   nvdb_status reserve(int64_t n2, int64_t n1, int64_t nl) {
-    if (status && n2 <= cap2 && n1 <= cap1 && nl <= capl) return NVDB_OK;
+    if (lb && n2 <= cap2 && n1 <= cap1 && nl <= capl) return NVDB_OK;
     release();
-    TRY(dalloc(&status, 1));
-    TRY(dalloc(&l2_counts, n2 + 1)); TRY(dalloc(&l2_off, n2 + 1));
+    TRY(dalloc(&lb, (size_t)lb_words(n2, n1, nl)));
+    status = reinterpret_cast<uint32_t*>(lb);
+    TRY(dalloc(&l2_off, n2 + 1));
     TRY(dalloc(&l1_origin, n1 + 1)); TRY(dalloc(&l1_words, 128 * n1 + 4));
-    TRY(dalloc(&l1_counts, n1 + 1)); TRY(dalloc(&l1_off, n1 + 1));
+    TRY(dalloc(&l1_off, n1 + 1));
     TRY(dalloc(&leaf_origin, nl + 1)); TRY(dalloc(&leaf_words, 16 * nl + 4));
-    TRY(dalloc(&leaf_counts, nl + 1)); TRY(dalloc(&leaf_off, nl + 1));
-    TRY(scan.reserve(std::max<int64_t>(nl, std::max(n1, n2))));
+    TRY(dalloc(&leaf_off, nl + 1));
     cap2 = n2; cap1 = n1; capl = nl;
     return NVDB_OK;
   }
   void release() {
-    dfree(l2_counts); dfree(l2_off); dfree(l1_origin); dfree(l1_words); dfree(l1_counts); dfree(l1_off);
-    dfree(leaf_origin); dfree(leaf_words); dfree(leaf_counts); dfree(leaf_off); dfree(status);
+    dfree(l2_off); dfree(l1_origin); dfree(l1_words); dfree(l1_off);
+    dfree(leaf_origin); dfree(leaf_words); dfree(leaf_off); dfree(lb);
+    status = nullptr;
     cap2 = cap1 = capl = 0;
   }
   ~DecodeScratch() { release(); }
@@ -1213,7 +1219,7 @@ nvdb_status decode_batch(nvdb_model* const* ms, int n, nvdb_precision prec, Deco
   }
   const int64_t N2 = s2[n], N1 = s1[n], NL = sl[n], NA = sa[n];
   TRY(d.reserve(N2, N1, NL));
-  CU(cudaMemsetAsync(d.status, 0, 4, s));
+  CU(cudaMemsetAsync(d.lb, 0, (size_t)DecodeScratch::lb_words(d.cap2, d.cap1, d.capl) * 8, s));
   std::vector<const PatchSet*> ps(n);
   for (int m = 0; m < n; ++m) ps[m] = ms[m]->patch_set(prec);
   if (N2) {
@@ -1221,9 +1227,7 @@ nvdb_status decode_batch(nvdb_model* const* ms, int n, nvdb_precision prec, Deco
     lb.n = n;
     for (int m = 0; m < n; ++m)
       lb.it[m] = L2Item{reinterpret_cast<const uint64_t*>(ms[m]->l2_mask), ms[m]->l2_origin, s2[m]};
-    KLAUNCH("l2_count", s, l2_count_batch_kernel<<<(unsigned)N2, 512, 0, s>>>(lb, d.l2_counts));
-    TRY(d.scan.run(d.l2_counts, N2, d.l2_off, s));
-    KLAUNCH("check_total", s, check_total_kernel<<<1, 1, 0, s>>>(d.scan.total, N1, d.status));
+    KLAUNCH("l2_scan", s, l2_scan_batch_kernel<<<(unsigned)N2, 512, 0, s>>>(lb, N2, d.l2_off, N1, d.lb2(), d.status));
     KLAUNCH("l2_emit", s, l2_emit_batch_kernel<<<(unsigned)N2, 512, 0, s>>>(lb, d.l2_off, d.l1_origin, N1, d.status));
   }
   EvalBatch b;
@@ -1244,11 +1248,12 @@ nvdb_status decode_batch(nvdb_model* const* ms, int n, nvdb_precision prec, Deco
   PatchBatch pb;
   pb.n = n;
   for (int m = 0; m < n; ++m) pb.it[m] = PatchItem{ps[m]->d_l1_off, ps[m]->d_l1_idx, s1[m]};
-  if (N1)
-    KLAUNCH("patch_count", s, patch_count_batch_kernel<<<blocks_for(N1, 8), 256, 0, s>>>(d.l1_words, 128, N1, pb,
-                                                                                      d.l1_counts));
-  TRY(d.scan.run(d.l1_counts, N1, d.l1_off, s));
-  KLAUNCH("check_total", s, check_total_kernel<<<1, 1, 0, s>>>(d.scan.total, NL, d.status));
+  if (N1) {
+    KLAUNCH("patch_scan", s, patch_scan_batch_kernel<<<(unsigned)DecodeScratch::blocks1(N1), 256, 0, s>>>(
+                                 d.l1_words, 128, N1, pb, d.l1_off, NL, d.lb1(), d.status));
+  } else if (NL) {
+    KLAUNCH("flag_corrupt", s, flag_corrupt_kernel<<<1, 1, 0, s>>>(d.status));   // leaves expected, no nodes
+  }
   if (N1)
     KLAUNCH("emit_leaves", s, emit_leaves_kernel<<<blocks_for(N1 * 32, 256), 256, 0, s>>>(d.l1_words, d.l1_origin, N1,
                                                                                        d.l1_off, d.leaf_origin, NL,
@@ -1267,11 +1272,12 @@ nvdb_status decode_batch(nvdb_model* const* ms, int n, nvdb_precision prec, Deco
     TRY(launch_batch(b, prec, s));
   }
   for (int m = 0; m < n; ++m) pb.it[m] = PatchItem{ps[m]->d_l0_off, ps[m]->d_l0_idx, sl[m]};
-  if (NL)
-    KLAUNCH("patch_count", s, patch_count_batch_kernel<<<blocks_for(NL, 8), 256, 0, s>>>(d.leaf_words, 16, NL, pb,
-                                                                                      d.leaf_counts));
-  TRY(d.scan.run(d.leaf_counts, NL, d.leaf_off, s));
-  KLAUNCH("check_total", s, check_total_kernel<<<1, 1, 0, s>>>(d.scan.total, NA, d.status));
+  if (NL) {
+    KLAUNCH("patch_scan", s, patch_scan_batch_kernel<<<(unsigned)DecodeScratch::blocks1(NL), 256, 0, s>>>(
+                                 d.leaf_words, 16, NL, pb, d.leaf_off, NA, d.lb0(), d.status));
+  } else if (NA) {
+    KLAUNCH("flag_corrupt", s, flag_corrupt_kernel<<<1, 1, 0, s>>>(d.status));   // voxels expected, no leaves
+  }
   if (out_ijk) {
     if (NL)
       KLAUNCH("emit_voxels", s, emit_voxels_rank_kernel<<<blocks_for(NL, 8), 256, 0, s>>>(d.leaf_words, d.leaf_origin,
