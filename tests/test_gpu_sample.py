@@ -40,7 +40,9 @@ def test_isosurface_and_mcd_match_oracle(grid):
     g2 = nv.build(torch.from_numpy(ijk.astype(np.int32)).cuda(), torch.from_numpy(val).cuda(), 0, 3.0)
     m = nv.mcd(g, g2)
     assert abs(m - sample.mcd(ref, ref2, 3.0)) <= 1e-5 * max(1.0, m)
-    assert nv.mcd(g, g) == 0.0
+    # a grid against itself: the trilinear value at its own FP32 crossing points is zero up to
+    # the rounding of (1 - t) v0 + t v1 (a few ulp of |v| <= 3)
+    assert nv.mcd(g, g) <= 2e-6
 
 
 def test_mcd_of_a_decoded_model():
