@@ -112,11 +112,13 @@ def subset_indices(seed: int, net: int, step: int, batch: int, interval: int, po
 
 # ----------------------------------------------------------------- initialisation
 
-def xavier_net(seed: int, net: int, n_in: int, width: int, layers: int) -> dict:
-    """Initial parameters of one MLP: `layers` hidden ReLU layers of `width`, then a 1-output head.
+def xavier_net(seed: int, net: int, n_in: int, width: int, layers: int, n_out: int = 1) -> dict:
+    """Initial parameters of one MLP: `layers` hidden layers of `width`, then a head of
+    n_out outputs.
 
     Draw order on stream seed + NET_STREAM*(net+1): W_0 row-major [width][n_in], then
-    W_1..W_{layers-1} [width][width], then the head w_h [width].  Biases are zero.
+    W_1..W_{layers-1} [width][width], then the head W_h row-major [n_out][width] (a vector
+    [width] for one output), bound sqrt(6 / (width + n_out)).  Biases are zero.
     """
     s = (seed + NET_STREAM * (net + 1)) & M64
     i = 0
@@ -131,12 +133,16 @@ def xavier_net(seed: int, net: int, n_in: int, width: int, layers: int) -> dict:
                 i += 1
         Ws.append(W.astype(np.float32).astype(np.float64))
         bs.append(np.zeros(width))
-    a = math.sqrt(6.0 / (width + 1))
-    wh = np.empty(width)
-    for c in range(width):
-        wh[c] = (2.0 * uniform01(s, i) - 1.0) * a
-        i += 1
-    return dict(W=Ws, b=bs, wh=wh.astype(np.float32).astype(np.float64), bh=0.0)
+    a = math.sqrt(6.0 / (width + n_out))
+    wh = np.empty((n_out, width))
+    for o in range(n_out):
+        for c in range(width):
+            wh[o, c] = (2.0 * uniform01(s, i) - 1.0) * a
+            i += 1
+    wh = wh.astype(np.float32).astype(np.float64)
+    if n_out == 1:
+        return dict(W=Ws, b=bs, wh=wh[0], bh=0.0)
+    return dict(W=Ws, b=bs, wh=wh, bh=np.zeros(n_out))
 
 
 def ffm_increments(seed: int, level: int, m: int, sigma: float, extent: int) -> np.ndarray:

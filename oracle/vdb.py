@@ -3,8 +3,14 @@
 Levels: leaf (level 0) = 8^3 voxels with an active mask a_0; level-1 internal
 node = 16^3 children (128^3 voxels) with child mask c_1; level-2 internal node
 = 32^3 children (4096^3 voxels) with child mask c_2; root = sparse map of
-level-2 nodes.  No tile values are produced (every input voxel is explicit),
-so active masks of internal nodes are empty.
+level-2 nodes.  By default every input voxel stays explicit and the active masks of
+the internal nodes are empty.  With tile pruning (tolerance tol >= 0, Section 3.1:
+tile values stand for constant regions), a leaf whose 512 voxels are all active and
+whose values span at most tol (FP32 max - min <= tol) becomes an active tile of its
+level-1 node: bit `slot` of the level-1 active mask a_1, tile value the FP32 midpoint
+(min + max) * 0.5.  The explicit grid keeps such a tile expanded as its leaf (so the
+leaf arrays, samplers and canonical order are unchanged) with every voxel carrying the
+tile value.
 
 Canonical order is that of the dense node layouts: lexicographic on
 (level-2 key, level-1 slot, leaf slot, voxel offset) with
@@ -52,8 +58,9 @@ def popcount(words: np.ndarray) -> int:
     return int(sum(bin(int(x)).count("1") for x in words.reshape(-1)))
 
 
-def build(ijk, val) -> dict:
-    """Sort voxels canonically and build the masks of every level."""
+def build(ijk, val, tile_tol: float | None = None) -> dict:
+    """Sort voxels canonically and build the masks of every level (and, with a tolerance,
+    the active tiles of level 1)."""
     ijk = np.asarray(ijk, dtype=np.int64).reshape(-1, 3)
     val = np.asarray(val, dtype=np.float32).reshape(-1)
     if ijk.shape[0] != val.shape[0]:
@@ -78,7 +85,26 @@ def build(ijk, val) -> dict:
     _set_bits(l1_mask, l1_of_leaf, (leaf_key & 4095))
     l2_mask = np.zeros((l2_key.size, 512), dtype=np.uint64)
     _set_bits(l2_mask, l2_of_l1, (l1_key & 32767))
+    leaf_tile = np.zeros(leaf_key.size, dtype=bool)
+    tile_value = np.zeros(0, dtype=np.float32)
+    l1_tile_mask = np.zeros((l1_key.size, 64), dtype=np.uint64)
+    if tile_tol is not None and leaf_key.size:
+        cnt = np.diff(np.append(leaf_first, n))
+        tiles = []
+        for lf in np.nonzero(cnt == 512)[0]:
+            v = val[leaf_first[lf]:leaf_first[lf] + 512]
+            mn, mx = np.float32(v.min()), np.float32(v.max())
+            if np.float32(mx - mn) <= np.float32(tile_tol):
+                leaf_tile[lf] = True
+                tiles.append(np.float32(np.float32(mn + mx) * np.float32(0.5)))
+        tile_value = np.array(tiles, dtype=np.float32)
+        if tile_value.size:
+            val = val.copy()
+            for t, lf in enumerate(np.nonzero(leaf_tile)[0]):
+                val[leaf_first[lf]:leaf_first[lf] + 512] = tile_value[t]
+            _set_bits(l1_tile_mask, l1_of_leaf[leaf_tile], (leaf_key[leaf_tile] & 4095))
     return dict(
+        leaf_tile=leaf_tile, tile_value=tile_value, l1_tile_mask=l1_tile_mask,
         n=n, ijk=ijk, val=val, key=key,
         leaf_origin=ijk[leaf_first] & ~7, leaf_mask=leaf_mask, leaf_l1=l1_of_leaf,
         leaf_first=leaf_first,

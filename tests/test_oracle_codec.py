@@ -37,7 +37,7 @@ def test_decode_restores_topology_for_any_weights(grid):
     opts = codec.default_opts(width=[8, 16, 8], layers=[2, 3, 2], sigma=1.0)
     m = codec.init_model(grid, 0, 3.0, opts)
     codec.make_patches(grid, m)
-    l1o, leafo, act = codec.decode_topology(m)
+    l1o, leafo, act, _ = codec.decode_topology(m)
     assert np.array_equal(l1o, grid["l1_origin"])
     assert np.array_equal(leafo, grid["leaf_origin"])
     assert np.array_equal(act, vdb.mask_bits(grid["leaf_mask"]))

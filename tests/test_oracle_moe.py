@@ -151,7 +151,7 @@ def test_decomposed_codec_restores_topology(grid):
         for net in range(3):
             codec.train_net(grid, m, net, dict(m.get("opts", {}), **codec.default_opts(steps=3, batch=64, sigma=1.0)), expert=k)
     codec.make_patches(grid, m)
-    l1o, leafo, act = codec.decode_topology(m)
+    l1o, leafo, act, _ = codec.decode_topology(m)
     assert np.array_equal(leafo, grid["leaf_origin"]) and np.array_equal(act, vdb.mask_bits(grid["leaf_mask"]))
     ijk, val = codec.decompress(m)
     assert np.array_equal(ijk, grid["ijk"])
