@@ -13,6 +13,7 @@ from .volumes import (  # noqa: F401
     random_primitives,
     fbm_fog,
     fbm_noise,
+    tiled_fog,
     water_frame,
     water_waves,
     query_points,

@@ -286,6 +286,22 @@ def fbm_fog(grid=512, octaves=6, lacunarity=2.0, gain=0.5, seed=3, base_period=6
 
 # --------------------------------------------------------------------------- water
 
+def tiled_fog(nx: int = 32, ny: int = 24, nz: int = 24, const: float = 0.5):
+    """A fog block [0, nx) x [0, ny) x [0, nz) whose x < nx/2 half holds the constant density
+    `const` (its full leaves become active tiles under tile pruning), the rest a gradient;
+    the full leaf at x >= 24, y, z < 8 spans 0.0077 (a tile only with tolerance >= that), and
+    two voxels at x = 40, 41 form a partial leaf.  Returns (ijk int64 [n, 3], val float32 [n])."""
+    a = [np.arange(nx), np.arange(ny), np.arange(nz)]
+    g = np.stack(np.meshgrid(*a, indexing="ij"), -1).reshape(-1, 3)
+    v = np.where(g[:, 0] < nx // 2, const, 0.2 + 0.01 * g[:, 1] + 0.001 * g[:, 2])
+    near = (g[:, 0] >= 24) & (g[:, 0] < 32) & (g[:, 1] < 8) & (g[:, 2] < 8)
+    v = np.where(near, 0.3 + 0.001 * (g[:, 1] + g[:, 2]) / 2.0, v)
+    extra = np.array([[nx + 8, 0, 0], [nx + 9, 3, 2]])
+    g = np.concatenate([g, extra])
+    v = np.concatenate([v, [const, const]]).astype(np.float32)
+    return g.astype(np.int64), v
+
+
 def water_waves(seed=4, n_waves=8, amp=(2.0, 12.0), wavelength=(32.0, 400.0), speed=(0.5, 2.0)):
     """Seeded sine-wave parameters: amplitude, wavelength, direction angle, phase, speed (voxels/frame)."""
     rng = np.random.Generator(np.random.PCG64(seed))

@@ -66,8 +66,13 @@ typedef enum {
                          (three MMA terms; two when the weights are BF16 values), FP32 accumulate */
 } nvdb_precision;
 
-/* Network indices (Section 3.3.1). */
-enum { NVDB_NET_L1_CLASSIFIER = 0, NVDB_NET_L0_CLASSIFIER = 1, NVDB_NET_REGRESSOR = 2 };
+/* Network indices (Section 3.3.1).  A model of a grid with active tiles (nvdb_build_opts
+ * prune_tiles) has a fourth network, the tile value regressor, and its level-1 classifier is
+ * ternary: three logits per slot for the classes child leaf (0), active tile (1) and
+ * inactive (2), the class the first maximum. */
+enum { NVDB_NET_L1_CLASSIFIER = 0, NVDB_NET_L0_CLASSIFIER = 1, NVDB_NET_REGRESSOR = 2, NVDB_NET_TILE_REGRESSOR = 3 };
+/* Hidden activations (the activation appendix and the hyper-parameter table). */
+enum { NVDB_ACT_RELU = 0, NVDB_ACT_SIN = 1 /* sin(omega a) */ };
 /* Losses (Eq. 1 is MSE; BCE is used for the classifiers, Section 3.3.1). */
 enum { NVDB_LOSS_MSE = 0, NVDB_LOSS_L1 = 1, NVDB_LOSS_BCE = 2,
        NVDB_LOSS_LINEAR = 3 /* nvdb_mlp_grad only: d_target holds dL/dy per sample; the gradient is
@@ -79,6 +84,12 @@ typedef struct nvdb_model nvdb_model;  /* [Hash,5,NN(4),NN(3)]: upper tree + 3 n
 typedef struct {
   int32_t grid_class;   /* 0 = narrow-band level set (SDF), 1 = fog (density) */
   float half_width;     /* level sets: band half-width w in voxels (values lie in (-w, w)); fog: ignored */
+  int32_t prune_tiles;  /* 1: tile pruning (Section 3.1) -- a leaf whose 512 voxels are all active and
+                           whose values span at most tile_tolerance (FP32 max - min) becomes an active
+                           tile of its level-1 node with the FP32 midpoint (min + max) / 2 as value;
+                           the grid keeps it expanded as its leaf, every voxel carrying the tile value.
+                           0: every voxel stays explicit */
+  float tile_tolerance; /* >= 0 */
 } nvdb_build_opts;
 
 typedef struct {
@@ -118,6 +129,12 @@ typedef struct {
                            1 = every voxel of the leaves (blocked), 2 = every voxel of the domain's
                            bounding box (dense; log2 extent <= 10, no decomposition); inactive
                            voxels take the background as target */
+  int32_t activation;   /* hidden activation of every network: NVDB_ACT_RELU, or NVDB_ACT_SIN (sin(omega a);
+                           FP32 training and FP32 evaluation only, patch_precs = 1) */
+  float omega;          /* sin frequency (the paper's 1.5 .. 3.0) */
+  int32_t tile_width;   /* grids with active tiles: tile value regressor width (0 = width[0]) ... */
+  int32_t tile_layers;  /* ... and hidden layers (0 = layers[0]); it trains at train_prec, while the
+                           ternary level-1 classifier always trains and evaluates at FP32 */
 } nvdb_train_opts;
 
 typedef struct {
@@ -128,6 +145,7 @@ typedef struct {
   int64_t n_active, n_leaf, n_l1, n_l2;
   int32_t n_experts;     /* models: experts of the domain decomposition (1 without one); grids: 0 */
   int32_t subdomain;     /* models: subdomain size S (0 = no decomposition) */
+  int64_t n_tiles;       /* active tiles of level 1 (grids built with prune_tiles, and their models) */
 } nvdb_info;
 
 /* ------------------------------------------------------------------------ */
@@ -148,6 +166,11 @@ nvdb_status nvdb_grid_info(const nvdb_grid* grid, nvdb_info* out);
 nvdb_status nvdb_grid_read(const nvdb_grid* grid, int32_t* ijk, float* val, int32_t* leaf_origin,
                            uint64_t* leaf_mask, int32_t* l1_origin, uint64_t* l1_mask,
                            nvdb_stream stream);
+
+/* The grid's active tiles to HOST buffers (either may be NULL): leaf_tile [n_leaf] (1 = the
+ * leaf is an active tile), l1_tile_mask [n_l1][64] (the level-1 active masks a_1).  Zero for a
+ * grid built without tile pruning.  Synchronises the stream. */
+nvdb_status nvdb_grid_tiles(const nvdb_grid* grid, uint8_t* leaf_tile, uint64_t* l1_tile_mask, nvdb_stream stream);
 
 nvdb_status nvdb_grid_free(nvdb_grid* grid);
 

@@ -15,8 +15,7 @@ from . import _native as N
 from ._native import (BF16, BF16X3, FP16, FP32, FP8_E4M3, INJECT_ALLOC_BUDGET, INJECT_STATIC_LIMIT, INJECT_WAIT_TIMEOUT,  # noqa: F401
                       ERR_CAPACITY, ERR_CORRUPT, ERR_INVALID_ARG, ERR_OUT_OF_MEMORY, ERR_TIMEOUT, ERR_UNSUPPORTED,
                       LOSS_BCE, LOSS_L1, LOSS_LINEAR, LOSS_MSE,
-                      NET_L0_CLASSIFIER,
-                      NET_L1_CLASSIFIER, NET_REGRESSOR)
+                      NET_L0_CLASSIFIER, NET_L1_CLASSIFIER, NET_REGRESSOR, NET_TILE_REGRESSOR, ACT_RELU, ACT_SIN)
 
 _lib = None
 
@@ -55,7 +54,7 @@ def _info(fn, h) -> dict:
     _check(fn(h, C.byref(i)))
     return dict(grid_class=i.grid_class, background=i.background, half_width=i.half_width,
                 origin=list(i.origin), log2_extent=i.log2_extent, n_active=i.n_active, n_leaf=i.n_leaf,
-                n_l1=i.n_l1, n_l2=i.n_l2, n_experts=i.n_experts, subdomain=i.subdomain)
+                n_l1=i.n_l1, n_l2=i.n_l2, n_experts=i.n_experts, subdomain=i.subdomain, n_tiles=i.n_tiles)
 
 
 class Grid:
@@ -81,6 +80,15 @@ class Grid:
         p = [a[k].ctypes.data_as(C.c_void_p) for k in ("ijk", "val", "leaf_origin", "leaf_mask", "l1_origin", "l1_mask")]
         _check(lib().nvdb_grid_read(self._h, *p, _stream()))
         return a
+
+    def tiles(self) -> dict:
+        """Active tiles (tile pruning): leaf_tile [n_leaf] bool, l1_tile_mask [n_l1, 64] uint64."""
+        import numpy as np
+        i = self.info()
+        lt = np.empty(i["n_leaf"], np.uint8)
+        tm = np.empty((i["n_l1"], 64), np.uint64)
+        _check(lib().nvdb_grid_tiles(self._h, lt.ctypes.data_as(C.c_void_p), tm.ctypes.data_as(C.c_void_p), _stream()))
+        return dict(leaf_tile=lt.astype(bool), l1_tile_mask=tm)
 
     def __del__(self):
         if getattr(self, "_h", None) and _lib is not None:
@@ -141,9 +149,10 @@ class Model:
             self._h = None
 
 
-def build(ijk: torch.Tensor, val: torch.Tensor, grid_class: int = 0, half_width: float = 3.0, stream=None) -> Grid:
+def build(ijk: torch.Tensor, val: torch.Tensor, grid_class: int = 0, half_width: float = 3.0, stream=None,
+          prune_tiles: bool = False, tile_tolerance: float = 0.0) -> Grid:
     n = ijk.shape[0]
-    o = N.BuildOpts(grid_class, half_width)
+    o = N.BuildOpts(grid_class, half_width, 1 if prune_tiles else 0, tile_tolerance)
     h = C.c_void_p()
     _check(lib().nvdb_build(_dptr(ijk, torch.int32, "ijk"), _dptr(val, torch.float32, "val"), n, C.byref(o),
                             _stream(stream), C.byref(h)))
@@ -315,8 +324,11 @@ def render(model: Model, eye, target, up=(0.0, 1.0, 0.0), fov_deg: float = 40.0,
 
 
 def mlp_eval(model: Model, net: int, ijk: torch.Tensor, prec: int = FP32, stream=None) -> torch.Tensor:
+    """Raw network outputs at voxel coordinates ([n]; [n, 3] logits for the ternary level-1
+    classifier of a model with active tiles)."""
     n = ijk.shape[0]
-    out = torch.empty(n, dtype=torch.float32, device="cuda")
+    wide = net == 0 and model.info()["n_tiles"] > 0
+    out = torch.empty((n, 3) if wide else n, dtype=torch.float32, device="cuda")
     _check(lib().nvdb_mlp_eval(model.handle, net, prec, _dptr(ijk, torch.int32, "ijk"), n,
                                _dptr(out, torch.float32, "out"), _stream(stream)))
     return out

@@ -10,13 +10,15 @@ LIB_PATH = os.path.join(HERE, "libnvdb.so")
 OK, ERR_INVALID_ARG, ERR_DUPLICATE_VOXEL, ERR_OUT_OF_MEMORY, ERR_CAPACITY, ERR_CUDA, ERR_TIMEOUT, \
     ERR_UNSUPPORTED, ERR_CORRUPT = range(9)
 FP32, BF16, FP8_E4M3, FP16, BF16X3 = 0, 1, 2, 3, 4
-NET_L1_CLASSIFIER, NET_L0_CLASSIFIER, NET_REGRESSOR = 0, 1, 2
+NET_L1_CLASSIFIER, NET_L0_CLASSIFIER, NET_REGRESSOR, NET_TILE_REGRESSOR = 0, 1, 2, 3
+ACT_RELU, ACT_SIN = 0, 1
 LOSS_MSE, LOSS_L1, LOSS_BCE, LOSS_LINEAR = 0, 1, 2, 3
 INJECT_WAIT_TIMEOUT, INJECT_ALLOC_BUDGET, INJECT_STATIC_LIMIT = 1, 2, 3
 
 
 class BuildOpts(C.Structure):
-    _fields_ = [("grid_class", C.c_int32), ("half_width", C.c_float)]
+    _fields_ = [("grid_class", C.c_int32), ("half_width", C.c_float), ("prune_tiles", C.c_int32),
+                ("tile_tolerance", C.c_float)]
 
 
 class TrainOpts(C.Structure):
@@ -25,14 +27,15 @@ class TrainOpts(C.Structure):
                 ("batch", C.c_int32), ("lr", C.c_float), ("lr_decay", C.c_float), ("lr_interval", C.c_int32),
                 ("loss", C.c_int32), ("train_prec", C.c_int32), ("patch_precs", C.c_uint32),
                 ("stop_window", C.c_int32), ("stop_loss", C.c_float * 3), ("resume", C.c_int32),
-                ("subdomain", C.c_int32), ("halo", C.c_int32), ("resample", C.c_int32), ("sampling", C.c_int32)]
+                ("subdomain", C.c_int32), ("halo", C.c_int32), ("resample", C.c_int32), ("sampling", C.c_int32),
+                ("activation", C.c_int32), ("omega", C.c_float), ("tile_width", C.c_int32), ("tile_layers", C.c_int32)]
 
 
 class Info(C.Structure):
     _fields_ = [("grid_class", C.c_int32), ("background", C.c_float), ("half_width", C.c_float),
                 ("origin", C.c_int32 * 3), ("log2_extent", C.c_int32), ("n_active", C.c_int64),
                 ("n_leaf", C.c_int64), ("n_l1", C.c_int64), ("n_l2", C.c_int64), ("n_experts", C.c_int32),
-                ("subdomain", C.c_int32)]
+                ("subdomain", C.c_int32), ("n_tiles", C.c_int64)]
 
 
 class Camera(C.Structure):
@@ -48,6 +51,7 @@ SIGNATURES = {
     "nvdb_build": ([_vp, _vp, _i64, C.POINTER(BuildOpts), _vp, C.POINTER(_vp)], _st),
     "nvdb_grid_info": ([_vp, C.POINTER(Info)], _st),
     "nvdb_grid_read": ([_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp], _st),
+    "nvdb_grid_tiles": ([_vp, _vp, _vp, _vp], _st),
     "nvdb_grid_free": ([_vp], _st),
     "nvdb_train_opts_default": ([C.POINTER(TrainOpts)], None),
     "nvdb_compress": ([_vp, C.POINTER(TrainOpts), _vp, _vp, C.POINTER(_vp)], _st),

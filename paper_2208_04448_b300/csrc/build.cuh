@@ -48,13 +48,13 @@ __global__ void build_gather_kernel(const uint64_t* key, const uint32_t* idx, in
   h2[t] = (t == 0 || (p >> 36) != (k >> 36)) ? 1u : 0u;
 }
 
-// Node origins, first-voxel offsets and mask bits.  e* are the exclusive scans
+// Node origins, first-voxel offsets, mask bits and the level-1 node of every leaf.  e* are the exclusive scans
 // of the head flags, so the node index of voxel t is e[t] + h[t] - 1.
 __global__ void build_fill_kernel(const int32_t* ijk, int64_t n, const uint32_t* h0, const uint32_t* h1,
                                   const uint32_t* h2, const int64_t* e0, const int64_t* e1, const int64_t* e2,
                                   int4* leaf_origin, int64_t* leaf_first, unsigned long long* leaf_mask,
                                   int4* l1_origin, unsigned long long* l1_mask, int4* l2_origin,
-                                  unsigned long long* l2_mask) {
+                                  unsigned long long* l2_mask, int64_t* leaf_node) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n) return;
   const int i = ijk[3 * t], j = ijk[3 * t + 1], k = ijk[3 * t + 2];
@@ -64,6 +64,7 @@ __global__ void build_fill_kernel(const int32_t* ijk, int64_t n, const uint32_t*
   if (h0[t]) {
     leaf_origin[leaf] = make_int4(i & ~7, j & ~7, k & ~7, 0);
     leaf_first[leaf] = t;
+    leaf_node[leaf] = l1;
     const int s = (((i >> 3) & 15) << 8) | (((j >> 3) & 15) << 4) | ((k >> 3) & 15);
     atomicOr(l1_mask + l1 * 64 + (s >> 6), 1ull << (s & 63));
   }

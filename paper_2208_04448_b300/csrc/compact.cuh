@@ -188,14 +188,25 @@ __global__ void __launch_bounds__(256) emit_voxels_rank_kernel(const uint32_t* w
 }
 
 // Level-1 child words -> leaf origins in canonical order.  One warp per node,
-// lane l owns words 4l..4l+3 (bits in slot order).
+// lane l owns words 4l..4l+3 (bits in slot order).  With tile words t (ternary level 1,
+// toff their exclusive scan per node), a slot that is an active tile gets w = its tile rank
+// + 1 in the emitted origin (0 for a child leaf).
 __global__ void emit_leaves_kernel(const uint32_t* words, const int4* l1_origin, int64_t n_l1,
-                                   const int64_t* off, int4* leaf_origin, int64_t cap, uint32_t* status) {
+                                   const int64_t* off, int4* leaf_origin, int64_t cap, uint32_t* status,
+                                   const uint32_t* t = nullptr, const int64_t* toff = nullptr) {
   const int64_t node = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (node >= n_l1) return;
   const uint4 w = reinterpret_cast<const uint4*>(words + node * 128)[lane];
   const uint32_t ww[4] = {w.x, w.y, w.z, w.w};
+  uint32_t tt[4] = {0u, 0u, 0u, 0u};
+  int64_t trank = 0;
+  if (t) {
+    const uint4 v = reinterpret_cast<const uint4*>(t + node * 128)[lane];
+    tt[0] = v.x; tt[1] = v.y; tt[2] = v.z; tt[3] = v.w;
+    int64_t ttot;
+    trank = toff[node] + warp_excl_scan(__popc(v.x) + __popc(v.y) + __popc(v.z) + __popc(v.w), lane, ttot);
+  }
   const int64_t cnt = __popc(w.x) + __popc(w.y) + __popc(w.z) + __popc(w.w);
   int64_t tot;
   int64_t pos = off[node] + warp_excl_scan(cnt, lane, tot);
@@ -208,12 +219,14 @@ __global__ void emit_leaves_kernel(const uint32_t* words, const int4* l1_origin,
       const int bit = __ffs(b) - 1;
       b &= b - 1;
       const int s = (lane * 4 + q) * 32 + bit;
+      const int tw = (tt[q] >> bit) & 1u ? (int)(trank + __popc(tt[q] & ((1u << bit) - 1u))) + 1 : 0;
       if (pos < cap)
-        leaf_origin[pos] = make_int4(o.x + 8 * (s >> 8), o.y + 8 * ((s >> 4) & 15), o.z + 8 * (s & 15), 0);
+        leaf_origin[pos] = make_int4(o.x + 8 * (s >> 8), o.y + 8 * ((s >> 4) & 15), o.z + 8 * (s & 15), tw);
       else
         over = true;
       ++pos;
     }
+    trank += __popc(tt[q]);
   }
   if (over) set_status(status, ST_CORRUPT);
 }
@@ -474,12 +487,14 @@ __global__ void l2_scan_batch_kernel(const __grid_constant__ L2Batch b, int64_t 
 
 // Patch application (XOR, Section 3.3.2) and set-bit counts of the items of a level with
 // their scan: 32 items per block of 8 warps, four items per warp; off[item] = set bits
-// before it; the last block checks the total.
+// before it; the last block checks the total.  Items flagged as active tiles (tiles[g].w > 0)
+// become all ones.
 constexpr int kPatchScanItems = 32;
 
 __global__ void __launch_bounds__(256) patch_scan_batch_kernel(uint32_t* words, int wpi, int64_t n_items,
                                                               const __grid_constant__ PatchBatch b, int64_t* off,
-                                                              int64_t expect, uint64_t* state, uint32_t* status) {
+                                                              int64_t expect, uint64_t* state, uint32_t* status,
+                                                              const int4* tiles = nullptr) {
   __shared__ uint32_t sw[8][128];
   __shared__ uint32_t scnt[kPatchScanItems];
   __shared__ int64_t sid, spre;
@@ -494,10 +509,11 @@ __global__ void __launch_bounds__(256) patch_scan_batch_kernel(uint32_t* words, 
       const int m = find_item(b.it, b.n, g);
       const int64_t local = g - b.it[m].start;
       uint32_t* w = words + g * wpi;
-      for (int i = lane; i < wpi; i += 32) sw[wib][i] = w[i];
+      const bool full = tiles && tiles[g].w > 0;   // an active tile: every voxel, no patches
+      for (int i = lane; i < wpi; i += 32) sw[wib][i] = full ? ~0u : w[i];
       __syncwarp();
       const uint32_t* poff = b.it[m].off;
-      if (poff)
+      if (poff && !full)
         for (uint32_t p = poff[local] + lane; p < poff[local + 1]; p += 32) {
           const uint32_t bit = b.it[m].idx[p];
           atomicXor(&sw[wib][bit >> 5], 1u << (bit & 31));

@@ -9,7 +9,7 @@ template <int NIN, int W, bool MOE = false>
 nvdb_status launch_f32(const EvalBatch& b, int64_t ntiles, cudaStream_t s) {
   if (!MOE && batch_moe(b)) return launch_f32<NIN, W, true>(b, ntiles, s);
   int occ = 0;
-  const size_t smem = f32_smem_bytes<NIN, W>(b.it[0].net.layers);
+  const size_t smem = f32_smem_bytes<NIN, W>(b.it[0].net.layers, b.it[0].net.n_out);
   auto* kern = mlp_f32_kernel<NIN, W, MOE>;
   TRY(set_smem_limit((const void*)kern, smem));
   CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kTile, smem));

@@ -20,6 +20,9 @@ namespace nvdb {
 
 struct NetView {
   int n_in, width, layers;
+  int n_out;                     // head outputs: 1, or 3 for the ternary level-1 classifier
+  int act;                       // hidden activation: 0 ReLU, 1 sin(omega a)
+  float omega;
   int wexact;                    // weights and biases are BF16 values: the BF16 lo tiles are zero
   const float* p32;              // flat FP32 parameters (W_0,b_0,...,W_{L-1},b_{L-1},w_h,b_h)
   const uint8_t* wpk;            // packed 16-bit weight tiles (see pack_weights_kernel)
@@ -35,8 +38,10 @@ struct EvalJob {
   int64_t n_items;        // nodes / leaves / coordinates
   int ox, oy, oz;         // encoding domain origin
   int shift;              // MODE_LIST: 3 for the level-1 classifier (leaf units), else 0
-  uint32_t* words;        // MODE_L1/L0: candidate bits, word (tile*4 + warp)
-  float* out;             // MODE_LIST: outputs
+  uint32_t* words;        // MODE_L1/L0: candidate bits, word (tile*4 + warp); ternary level-1
+                          // classifier: the child-or-tile bits (class <= 1)
+  uint32_t* twords;       // ternary level-1 classifier, MODE_L1: the active-tile bits (class 1)
+  float* out;             // MODE_LIST: outputs (three per row for the ternary classifier)
   float scale;            // MODE_LIST: output multiplier
   const int64_t* n_dev;   // MODE_LIST: if set, the list length is read from device memory (<= n_items)
   uint32_t* status;
@@ -82,6 +87,31 @@ __device__ __forceinline__ void job_output(const EvalJob& j, int64_t t, int r, b
   } else {
     const uint32_t b = __ballot_sync(0xffffffffu, y > 0.f);
     if ((r & 31) == 0) j.words[t * 4 + (r >> 5)] = b;
+  }
+}
+
+// Class of three logits: the first maximum (ties go to the lower class).
+__device__ __forceinline__ int class3(float y0, float y1, float y2) {
+  int c = 0;
+  float b = y0;
+  if (y1 > b) { c = 1; b = y1; }
+  if (y2 > b) c = 2;
+  return c;
+}
+
+// Ternary output: list mode writes the three logits; lattice modes the child-or-tile bits
+// (class <= 1) and the active-tile bits (class 1).
+__device__ __forceinline__ void job_output3(const EvalJob& j, int64_t t, int r, bool valid, const float* y) {
+  if (j.mode == MODE_LIST) {
+    if (valid)
+      for (int c = 0; c < 3; ++c) j.out[3 * (t * kTile + r) + c] = y[c] * j.scale;
+  } else {
+    const int c = class3(y[0], y[1], y[2]);
+    const uint32_t u = __ballot_sync(0xffffffffu, c <= 1), tb = __ballot_sync(0xffffffffu, c == 1);
+    if ((r & 31) == 0) {
+      j.words[t * 4 + (r >> 5)] = u;
+      j.twords[t * 4 + (r >> 5)] = tb;
+    }
   }
 }
 
@@ -174,9 +204,10 @@ __device__ __forceinline__ int64_t batch_total(const EvalBatch& b, int64_t& n0) 
   return last.tile_start + job_tiles(last.job.mode, last.job.n_items);
 }
 
-__host__ __device__ inline int64_t net_param_count(int nin, int w, int L) {
-  return (int64_t)w * nin + w + (int64_t)(L - 1) * (w * w + w) + w + 1;
+__host__ __device__ inline int64_t net_param_count(int nin, int w, int L, int nout = 1) {
+  return (int64_t)w * nin + w + (int64_t)(L - 1) * (w * w + w) + (int64_t)nout * (w + 1);
 }
+
 
 // ============================================================== FP32 plain path
 
@@ -214,30 +245,44 @@ __device__ __forceinline__ void encode_f32(const uint32_t* sq, int cx, int cy, i
 }
 
 template <int NIN, int W>
-__device__ __forceinline__ float forward_f32(const float* sp, const uint32_t* sq, int L, int cx, int cy, int cz) {
+__device__ __forceinline__ void forward_f32(const float* sp, const uint32_t* sq, int L, int act, float om, int nout,
+                                            int cx, int cy, int cz, float* y) {
   constexpr int H = NIN > W ? NIN : W;
   float h[H], a[W];
   encode_f32<NIN>(sq, cx, cy, cz, h);
   const float* p = sp;
   dense_f32<NIN, W>(p, h, a);
   p += W * NIN + W;
+  if (act) {
 #pragma unroll
-  for (int o = 0; o < W; ++o) h[o] = fmaxf(a[o], 0.f);
-  for (int l = 1; l < L; ++l) {
-    dense_f32<W, W>(p, h, a);
-    p += W * W + W;
+    for (int o = 0; o < W; ++o) h[o] = sinf(om * a[o]);
+  } else {
 #pragma unroll
     for (int o = 0; o < W; ++o) h[o] = fmaxf(a[o], 0.f);
   }
-  float y = p[W];
+  for (int l = 1; l < L; ++l) {
+    dense_f32<W, W>(p, h, a);
+    p += W * W + W;
+    if (act) {
 #pragma unroll
-  for (int i = 0; i < W; ++i) y = fmaf(p[i], h[i], y);
-  return y;
+      for (int o = 0; o < W; ++o) h[o] = sinf(om * a[o]);
+    } else {
+#pragma unroll
+      for (int o = 0; o < W; ++o) h[o] = fmaxf(a[o], 0.f);
+    }
+  }
+  // head: W_h [nout][W] then b_h [nout]
+  for (int c = 0; c < nout; ++c) {
+    float acc = p[nout * W + c];
+#pragma unroll
+    for (int i = 0; i < W; ++i) acc = fmaf(p[c * W + i], h[i], acc);
+    y[c] = acc;
+  }
 }
 
 template <int NIN, int W>
-__host__ __device__ inline size_t f32_smem_bytes(int L) {
-  const int64_t P = net_param_count(NIN, W, L);
+__host__ __device__ inline size_t f32_smem_bytes(int L, int nout = 3) {
+  const int64_t P = net_param_count(NIN, W, L, nout);
   return (size_t)((P + 3) & ~3ll) * 4 + (size_t)(NIN / 2) * 3 * 4;
 }
 
@@ -246,7 +291,8 @@ __global__ void __launch_bounds__(kTile, 3) mlp_f32_kernel(const __grid_constant
   extern __shared__ float4 smem_f4[];
   float* sp = reinterpret_cast<float*>(smem_f4);
   const int L = b.it[0].net.layers;
-  const int64_t P = net_param_count(NIN, W, L);
+  const int nout = b.it[0].net.n_out;
+  const int64_t P = net_param_count(NIN, W, L, nout);
   uint32_t* sq = reinterpret_cast<uint32_t*>(sp + ((P + 3) & ~3ll));
   int64_t n0;
   const int64_t ntiles = batch_total(b, n0);
@@ -267,10 +313,17 @@ __global__ void __launch_bounds__(kTile, 3) mlp_f32_kernel(const __grid_constant
     const int64_t tl = t - b.it[m].tile_start;
     int cx, cy, cz;
     const bool valid = job_coord(job, tl, threadIdx.x, cx, cy, cz);
+    const NetView& nv = b.it[m].net;
     float y;
     if (!MOE || !mv.experts) {
-      if (staged != b.it[m].net.p32) stage(b.it[m].net);
-      y = forward_f32<NIN, W>(sp, sq, L, cx, cy, cz);
+      if (staged != nv.p32) stage(nv);
+      float yy[3];
+      forward_f32<NIN, W>(sp, sq, L, nv.act, nv.omega, nout, cx, cy, cz, yy);
+      if (nout == 3) {   // ternary level-1 classifier (Section 3.3.1)
+        job_output3(job, tl, threadIdx.x, valid, yy);
+        continue;
+      }
+      y = yy[0];
     } else {
       // decomposed model (Section 3.4): one pass per expert with a non-zero gate in the tile,
       // ascending expert order, y = sum_k G_k y_k / sum_k G_k
@@ -289,7 +342,8 @@ __global__ void __launch_bounds__(kTile, 3) mlp_f32_kernel(const __grid_constant
         if (staged != ev.p32) stage(ev);
         const int4 eo = __ldg(mv.origin + e);
         const float g = moe_gate(mv, shift, cx, cy, cz, e);
-        const float ye = forward_f32<NIN, W>(sp, sq, L, cx - (eo.x >> shift), cy - (eo.y >> shift), cz - (eo.z >> shift));
+        float ye;
+        forward_f32<NIN, W>(sp, sq, L, ev.act, ev.omega, 1, cx - (eo.x >> shift), cy - (eo.y >> shift), cz - (eo.z >> shift), &ye);
         acc = fmaf(g, ye, acc);
         gs += g;
         last = e;

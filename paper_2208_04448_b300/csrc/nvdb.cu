@@ -24,6 +24,7 @@
 #include "query.cuh"
 #include "render.cuh"
 #include "sample.cuh"
+#include "tiles.cuh"
 #include "train.cuh"
 
 using namespace nvdb;
@@ -79,10 +80,11 @@ uint64_t mix64(uint64_t z) {
 // Draw i of the SplitMix64 stream started at state s (Steele, Lea & Flood 2014).
 double uniform01(uint64_t s, uint64_t i) { return (double)(mix64(s + (i + 1) * kGolden) >> 11) * (1.0 / 9007199254740992.0); }
 
-// Xavier-uniform weights, zero biases; draw order W_0 (row-major), ..., W_{L-1}, w_h.
-std::vector<float> xavier_params(uint64_t seed, int net, int nin, int w, int L) {
+// Xavier-uniform weights, zero biases; draw order W_0 (row-major), ..., W_{L-1}, then the
+// head W_h [nout][w] row-major (bound sqrt(6 / (w + nout))).
+std::vector<float> xavier_params(uint64_t seed, int net, int nin, int w, int L, int nout = 1) {
   const uint64_t s = seed + kNetStream * (uint64_t)(net + 1);
-  std::vector<float> p((size_t)net_param_count(nin, w, L), 0.f);
+  std::vector<float> p((size_t)net_param_count(nin, w, L, nout), 0.f);
   uint64_t i = 0;
   size_t o = 0;
   for (int l = 0; l < L; ++l) {
@@ -92,8 +94,8 @@ std::vector<float> xavier_params(uint64_t seed, int net, int nin, int w, int L) 
       for (int c = 0; c < fan; ++c) p[o++] = (float)((2.0 * uniform01(s, i++) - 1.0) * a);
     o += w;   // bias = 0
   }
-  const double a = std::sqrt(6.0 / (double)(w + 1));
-  for (int c = 0; c < w; ++c) p[o++] = (float)((2.0 * uniform01(s, i++) - 1.0) * a);
+  const double a = std::sqrt(6.0 / (double)(w + nout));
+  for (int c = 0; c < nout * w; ++c) p[o++] = (float)((2.0 * uniform01(s, i++) - 1.0) * a);
   return p;   // b_h = 0
 }
 
@@ -129,6 +131,11 @@ struct nvdb_grid {
   unsigned long long* l1_mask = nullptr;
   int4* l2_origin = nullptr;
   unsigned long long* l2_mask = nullptr;
+  // active tiles of level 1 (tile pruning): per leaf 1 if it is a tile (kept expanded, its
+  // voxels carrying the tile value), per level-1 node the active mask a_1
+  int64_t n_tiles = 0;
+  uint8_t* leaf_tile = nullptr;
+  unsigned long long* l1_tile_mask = nullptr;
   // random-access structures of the explicit tree (built on first use by the samplers)
   uint64_t* l2_key = nullptr;
   uint32_t *l2_pre = nullptr, *l1_pre = nullptr;
@@ -136,13 +143,14 @@ struct nvdb_grid {
   ~nvdb_grid() {
     dfree(ijk); dfree(val); dfree(leaf_origin); dfree(leaf_first); dfree(leaf_mask);
     dfree(l1_origin); dfree(l1_mask); dfree(l2_origin); dfree(l2_mask);
+    dfree(leaf_tile); dfree(l1_tile_mask);
     dfree(l2_key); dfree(l2_pre); dfree(l1_pre); dfree(l2_base); dfree(l1_base);
   }
 };
 
 namespace {
 struct DevNet {
-  int n_in = 0, width = 0, layers = 0;
+  int n_in = 0, width = 0, layers = 0, n_out = 1;
   int64_t P = 0;
   float* p32 = nullptr;
   uint8_t* wpk = nullptr;   // [FP16 | BF16 hi | BF16 lo] weight tiles, then BF16 W_l^T tiles
@@ -178,15 +186,25 @@ struct DecodeScratch {
   uint32_t* leaf_words = nullptr;
   int64_t* leaf_off = nullptr;
   // One zero-initialised block, cleared by a single memset per decode: word 0 holds the
-  // status, then the single-pass scan states of level 2, level 1 and level 0 (one word per
-  // scan block plus the block counter).
+  // status, then the single-pass scan states of level 2, level 1, level 0 and the level-1
+  // tiles (one word per scan block plus the block counter).
   uint64_t* lb = nullptr;
   uint32_t* status = nullptr;
+  // ternary level 1 (models with active tiles): tile words, their scan, the tiles' origins
+  // and regressed values (concatenated per model, canonical order)
+  int64_t capt = 0;
+  uint32_t* t1_words = nullptr;
+  int64_t* t1_off = nullptr;
+  int32_t* tile_ijk = nullptr;
+  float* tval = nullptr;
   static int64_t blocks1(int64_t n) { return (n + kPatchScanItems - 1) / kPatchScanItems; }
-  static int64_t lb_words(int64_t n2, int64_t n1, int64_t nl) { return 1 + (n2 + 1) + (blocks1(n1) + 1) + (blocks1(nl) + 1); }
+  static int64_t lb_words(int64_t n2, int64_t n1, int64_t nl) {
+    return 1 + (n2 + 1) + 2 * (blocks1(n1) + 1) + (blocks1(nl) + 1);
+  }
   uint64_t* lb2() { return lb + 1; }
   uint64_t* lb1() { return lb + 2 + cap2; }
   uint64_t* lb0() { return lb + 3 + cap2 + blocks1(cap1); }
+  uint64_t* lbt() { return lb + 4 + cap2 + blocks1(cap1) + blocks1(capl); }
   nvdb_status reserve(int64_t n2, int64_t n1, int64_t nl) {
     if (lb && n2 <= cap2 && n1 <= cap1 && nl <= capl) return NVDB_OK;
     release();
@@ -200,11 +218,22 @@ struct DecodeScratch {
     cap2 = n2; cap1 = n1; capl = nl;
     return NVDB_OK;
   }
+  // after reserve(): the tile arrays for n1 level-1 nodes and nt tiles
+  nvdb_status reserve_tiles(int64_t nt) {
+    if (t1_words && nt <= capt) return NVDB_OK;
+    dfree(t1_words); dfree(t1_off); dfree(tile_ijk); dfree(tval);
+    capt = 0;
+    TRY(dalloc(&t1_words, 128 * cap1 + 4)); TRY(dalloc(&t1_off, cap1 + 1));
+    TRY(dalloc(&tile_ijk, 3 * nt + 3)); TRY(dalloc(&tval, nt + 1));
+    capt = nt;
+    return NVDB_OK;
+  }
   void release() {
     dfree(l2_off); dfree(l1_origin); dfree(l1_words); dfree(l1_off);
     dfree(leaf_origin); dfree(leaf_words); dfree(leaf_off); dfree(lb);
+    dfree(t1_words); dfree(t1_off); dfree(tile_ijk); dfree(tval);
     status = nullptr;
-    cap2 = cap1 = capl = 0;
+    cap2 = cap1 = capl = capt = 0;
   }
   ~DecodeScratch() { release(); }
 };
@@ -221,9 +250,11 @@ struct QueryCache {
   int64_t* off = nullptr;
   int32_t* list = nullptr;
   float* vals = nullptr;
+  uint8_t* qtile = nullptr;   // models with tiles: tile corners and their values
+  float* qtv = nullptr;
   void release() {
     dfree(l2_key); dfree(l2_pre); dfree(l1_pre);
-    dfree(qmask); dfree(counts); dfree(off); dfree(list); dfree(vals);
+    dfree(qmask); dfree(counts); dfree(off); dfree(list); dfree(vals); dfree(qtile); dfree(qtv);
     ready = false;
     batch = 0;
   }
@@ -241,8 +272,15 @@ struct nvdb_model {
   std::vector<uint32_t> q_host[2];
   uint32_t* q_dev[2] = {nullptr, nullptr};
   // Networks: expert e's network j (0 level-1 classifier, 1 level-0 classifier, 2 regressor)
-  // is net[3e + j]; one expert unless the domain is decomposed (Section 3.4).
+  // is net[3e + j]; one expert unless the domain is decomposed (Section 3.4).  With active
+  // tiles (a pruned source grid, one expert), net 0 is the ternary level-1 classifier and
+  // net 3 the tile value regressor on the level-1 encoding (Section 3.3.1).
   int n_exp = 1;
+  bool ternary = false;
+  int tile_width = 0, tile_layers = 0;
+  int64_t n_tiles = 0;
+  int act = 0;              // hidden activation of every network: 0 ReLU, 1 sin(omega a)
+  float omega = 1.f;
   std::unique_ptr<DevNet[]> net{new DevNet[3]};
   std::vector<std::vector<float>> losses = std::vector<std::vector<float>>(3);
   // Sparse domain decomposition: subdomain size (0 = none) and halo in voxels, grid of
@@ -272,12 +310,18 @@ struct nvdb_model {
     qc.release();
   }
   bool moe() const { return sub_size > 0; }
-  int n_net() const { return 3 * n_exp; }
+  int n_net() const { return 3 * n_exp + (ternary ? 1 : 0); }
   void set_experts(int n) {
     n_exp = n;
-    net.reset(new DevNet[3 * n]);
-    losses.assign(3 * n, {});
+    net.reset(new DevNet[n_net()]);
+    losses.assign(n_net(), {});
   }
+  void set_ternary(bool t) {   // before the networks are allocated
+    ternary = t;
+    set_experts(n_exp);
+  }
+  bool tile_net(int k) const { return ternary && k == 3 * n_exp; }
+  int net_level(int k) const { return k % 3 == 0 || tile_net(k) ? 1 : 0; }   // 1: level-1 encoding
   const PatchSet* patch_set(int prec) const {
     for (auto& p : patches)
       if (p.prec == prec) return &p;
@@ -290,15 +334,18 @@ struct nvdb_model {
 namespace {
 bool supported_shape(int nin, int w) { return (nin == 32 || nin == 64) && (w == 32 || w == 64); }
 
-// View of network k (expert k / 3, level k % 3).
+// View of network k (expert k / 3, level k % 3; or the tile value regressor).
 NetView net_view(const nvdb_model* m, int k) {
   NetView v;
   v.n_in = m->net[k].n_in;
   v.width = m->net[k].width;
   v.layers = m->net[k].layers;
+  v.n_out = m->net[k].n_out;
+  v.act = m->act;
+  v.omega = m->omega;
   v.p32 = m->net[k].p32;
   v.wpk = m->net[k].wpk;
-  v.q = m->q_dev[k % 3 == 0 ? 0 : 1];
+  v.q = m->q_dev[m->net_level(k) ? 0 : 1];
   v.wexact = m->net[k].bf16_exact ? 1 : 0;
   return v;
 }
@@ -396,11 +443,12 @@ nvdb_status launch_eval(const nvdb_model* m, int k, nvdb_precision prec, EvalJob
   return launch_batch(b, prec, s);
 }
 
-template <int NIN, int W>
+template <int NIN, int W, int NOUT = 1>
 nvdb_status launch_train_t(const NetView& nv, const TrainJob& job, int grid, cudaStream_t s) {
-  const size_t smem = TrainSmem<NIN, W>::bytes(nv.layers);
-  TRY(set_smem_limit((const void*)train_fwd_bwd_kernel<NIN, W>, smem));
-  KLAUNCH("train_fwd_bwd", s, train_fwd_bwd_kernel<NIN, W><<<grid, kTile, smem, s>>>(nv, job));
+  if (NOUT == 1 && nv.n_out == 3) return launch_train_t<NIN, W, 3>(nv, job, grid, s);
+  const size_t smem = TrainSmem<NIN, W, NOUT>::bytes(nv.layers);
+  TRY(set_smem_limit((const void*)train_fwd_bwd_kernel<NIN, W, NOUT>, smem));
+  KLAUNCH("train_fwd_bwd", s, train_fwd_bwd_kernel<NIN, W, NOUT><<<grid, kTile, smem, s>>>(nv, job));
   CU(cudaGetLastError());
   return NVDB_OK;
 }
@@ -419,6 +467,8 @@ nvdb_status launch_train(const nvdb_model* m, int k, int prec, TrainJob job, int
   job.oz = m->origin[2] + (m->moe() ? m->exp_origin_host[3 * e + 2] : 0);
   if (!job.status) job.status = m->status;
   if (prec == NVDB_BF16) {
+    if (nv.n_out != 1 || nv.act != 0)
+      return fail(NVDB_ERR_UNSUPPORTED, "BF16 training: ReLU networks with one output only");
     return launch_train_tc(nv, job, grid, s);
   } else if (prec == NVDB_FP32) {
     if (nv.n_in == 32 && nv.width == 32) return launch_train_t<32, 32>(nv, job, grid, s);
@@ -462,13 +512,23 @@ nvdb_status eval_status(const nvdb_model* m, nvdb_precision prec, cudaStream_t s
   return status_to_error(hst);
 }
 
+// Shape of network k: (encoding size, width, hidden layers, head outputs).
+void net_shape(const nvdb_model* m, int k, int& nin, int& w, int& L, int& nout) {
+  if (m->tile_net(k)) {
+    nin = m->ffm[0]; w = m->tile_width; L = m->tile_layers; nout = 1;
+    return;
+  }
+  const int j = k % 3;
+  nin = j == 0 ? m->ffm[0] : m->ffm[1];
+  w = m->width[j];
+  L = m->layers[j];
+  nout = j == 0 && m->ternary ? 3 : 1;
+}
+
 nvdb_status upload_net(nvdb_model* m, int k, const float* host_params, cudaStream_t s) {
   DevNet& d = m->net[k];
-  const int j = k % 3;
-  d.n_in = j == 0 ? m->ffm[0] : m->ffm[1];
-  d.width = m->width[j];
-  d.layers = m->layers[j];
-  d.P = net_param_count(d.n_in, d.width, d.layers);
+  net_shape(m, k, d.n_in, d.width, d.layers, d.n_out);
+  d.P = net_param_count(d.n_in, d.width, d.layers, d.n_out);
   dfree(d.p32); dfree(d.wpk); dfree(d.m); dfree(d.v);
   TRY(dalloc(&d.p32, (size_t)d.P));
   TRY(dalloc(&d.wpk, (size_t)wpk_bytes(d.n_in, d.width, d.layers) + 64));
@@ -492,6 +552,8 @@ bool bf16_exact_layers(const float* p, int64_t n) {
 
 nvdb_status pack_net(nvdb_model* m, int k, cudaStream_t s) {
   DevNet& d = m->net[k];
+  // the tensor-core tiles serve ReLU networks with one output (check_eval_prec)
+  if (m->act != 0 || d.n_out != 1) return NVDB_OK;
   KLAUNCH("pack_weights", s, pack_weights_kernel<<<64, 256, 0, s>>>(d.p32, d.wpk, d.n_in, d.width, d.layers));
   CU(cudaGetLastError());
   if (d.layers > 1) {
@@ -507,7 +569,7 @@ nvdb_status pack_net(nvdb_model* m, int k, cudaStream_t s) {
   if (m->moe())
     for (lgE = 0; (1 << lgE) < m->sub_size; ++lgE) {
     }
-  const int lg = k % 3 == 0 ? lgE - 3 : lgE;   // the level-1 classifier works in leaf units
+  const int lg = m->net_level(k) ? lgE - 3 : lgE;   // level-1 networks work in leaf units
   constexpr int kCalibPoints = 1 << 12;   // one point per thread of 32 blocks
   TRY(launch_calib_amax(nv, lg, 0xF8CA11Bull, kCalibPoints, d.f8_amax, s));
   KLAUNCH("pack_fp8", s, pack_fp8_kernel<<<1, 256, 0, s>>>(d.p32, d.wpk, d.n_in, d.width, d.layers, d.f8_amax));
@@ -516,14 +578,25 @@ nvdb_status pack_net(nvdb_model* m, int k, cudaStream_t s) {
 }
 
 nvdb_status check_model_shapes(const nvdb_model* m) {
-  for (int k = 0; k < 3; ++k) {
-    const int nin = k == 0 ? m->ffm[0] : m->ffm[1];
-    if (!supported_shape(nin, m->width[k]))
-      return fail(NVDB_ERR_UNSUPPORTED, "network %d: encoding size %d / width %d (supported: 32, 64)", k, nin,
-                  m->width[k]);
-    if (m->layers[k] < 1 || m->layers[k] > kMaxLayers)
-      return fail(NVDB_ERR_UNSUPPORTED, "network %d: %d hidden layers (supported: 1..%d)", k, m->layers[k], kMaxLayers);
+  for (int k = 0; k < (m->ternary ? 4 : 3); ++k) {
+    const int kk = k == 3 ? 3 * m->n_exp : k;
+    int nin, w, L, nout;
+    net_shape(m, kk, nin, w, L, nout);
+    if (!supported_shape(nin, w))
+      return fail(NVDB_ERR_UNSUPPORTED, "network %d: encoding size %d / width %d (supported: 32, 64)", k, nin, w);
+    if (L < 1 || L > kMaxLayers)
+      return fail(NVDB_ERR_UNSUPPORTED, "network %d: %d hidden layers (supported: 1..%d)", k, L, kMaxLayers);
   }
+  if (m->act != 0 && m->act != 1) return fail(NVDB_ERR_UNSUPPORTED, "activation %d", m->act);
+  return NVDB_OK;
+}
+
+// The tensor-core kernels implement ReLU networks with one output; a model with the sin
+// activation evaluates at FP32 only, and the ternary classifier always evaluates at FP32.
+nvdb_status check_eval_prec(const nvdb_model* m, int k, nvdb_precision prec) {
+  if (prec == NVDB_FP32) return NVDB_OK;
+  if (m->act != 0) return fail(NVDB_ERR_UNSUPPORTED, "sin activation: FP32 evaluation only");
+  if (m->net[k].n_out != 1) return fail(NVDB_ERR_UNSUPPORTED, "the ternary level-1 classifier evaluates at FP32");
   return NVDB_OK;
 }
 }  // namespace
@@ -536,6 +609,8 @@ extern "C" nvdb_status nvdb_build(const int32_t* d_ijk, const float* d_val, int6
   if (opts->grid_class != 0 && opts->grid_class != 1) return fail(NVDB_ERR_INVALID_ARG, "grid_class must be 0 or 1");
   if (opts->grid_class == 0 && !(opts->half_width > 0.f)) return fail(NVDB_ERR_INVALID_ARG, "half_width must be > 0");
   if (n >= (int64_t)INT32_MAX) return fail(NVDB_ERR_UNSUPPORTED, "nvdb_build: n >= 2^31");
+  if (opts->prune_tiles && !(opts->tile_tolerance >= 0.f))
+    return fail(NVDB_ERR_INVALID_ARG, "nvdb_build: tile_tolerance must be >= 0");
   *out = nullptr;
   cudaStream_t s = (cudaStream_t)stream;
   auto* g = new nvdb_grid();
@@ -546,9 +621,10 @@ extern "C" nvdb_status nvdb_build(const int32_t* d_ijk, const float* d_val, int6
   nvdb_status st = NVDB_OK;
   uint64_t *k0 = nullptr, *k1 = nullptr;
   uint32_t *i0 = nullptr, *i1 = nullptr, *h = nullptr, *status = nullptr;
-  int64_t* e = nullptr;
+  int64_t *e = nullptr, *leaf_node = nullptr;
+  unsigned long long* ntile = nullptr;
   auto cleanup = [&]() {
-    dfree(k0); dfree(k1); dfree(i0); dfree(i1); dfree(h); dfree(e); dfree(status);
+    dfree(k0); dfree(k1); dfree(i0); dfree(i1); dfree(h); dfree(e); dfree(status); dfree(leaf_node); dfree(ntile);
   };
   auto run = [&]() -> nvdb_status {
     if (n == 0) return NVDB_OK;
@@ -581,11 +657,24 @@ extern "C" nvdb_status nvdb_build(const int32_t* d_ijk, const float* d_val, int6
     CU(cudaMemsetAsync(g->leaf_mask, 0, 64 * g->n_leaf, s));
     CU(cudaMemsetAsync(g->l1_mask, 0, 512 * g->n_l1, s));
     CU(cudaMemsetAsync(g->l2_mask, 0, 4096 * g->n_l2, s));
+    TRY(dalloc(&leaf_node, g->n_leaf));
     KLAUNCH("build_fill", s, build_fill_kernel<<<blocks_for(n, 256), 256, 0, s>>>(g->ijk, n, h, h + n, h + 2 * n, e, e + n, e + 2 * n,
                                                           g->leaf_origin, g->leaf_first, g->leaf_mask, g->l1_origin,
-                                                          g->l1_mask, g->l2_origin, g->l2_mask));
+                                                          g->l1_mask, g->l2_origin, g->l2_mask, leaf_node));
     CU(cudaGetLastError());
     CU(cudaMemcpyAsync(g->leaf_first + g->n_leaf, &g->n, 8, cudaMemcpyHostToDevice, s));
+    if (opts->prune_tiles) {   // active tiles of level 1 (Section 3.1)
+      TRY(dalloc(&g->leaf_tile, g->n_leaf)); TRY(dalloc(&g->l1_tile_mask, 64 * g->n_l1)); TRY(dalloc(&ntile, 1));
+      CU(cudaMemsetAsync(g->l1_tile_mask, 0, 512 * g->n_l1, s));
+      CU(cudaMemsetAsync(ntile, 0, 8, s));
+      KLAUNCH("tile_prune", s, tile_prune_kernel<<<blocks_for(g->n_leaf * 32, 256), 256, 0, s>>>(
+                                   g->leaf_mask, g->leaf_first, g->leaf_origin, leaf_node, g->n_leaf,
+                                   opts->tile_tolerance, g->val, g->leaf_tile, g->l1_tile_mask, ntile));
+      unsigned long long nt = 0;
+      CU(cudaMemcpyAsync(&nt, ntile, 8, cudaMemcpyDeviceToHost, s));
+      CU(cudaStreamSynchronize(s));
+      g->n_tiles = (int64_t)nt;
+    }
     // encoding domain: level-1 aligned bounding box, power-of-two extent >= 128
     std::vector<int4> l1(g->n_l1);
     CU(cudaMemcpyAsync(l1.data(), g->l1_origin, g->n_l1 * sizeof(int4), cudaMemcpyDeviceToHost, s));
@@ -621,6 +710,23 @@ extern "C" nvdb_status nvdb_grid_info(const nvdb_grid* g, nvdb_info* out) {
   out->n_l2 = g->n_l2;
   out->n_experts = 0;
   out->subdomain = 0;
+  out->n_tiles = g->n_tiles;
+  return NVDB_OK;
+}
+
+extern "C" nvdb_status nvdb_grid_tiles(const nvdb_grid* g, uint8_t* leaf_tile, uint64_t* l1_tile_mask,
+                                       nvdb_stream stream) {
+  if (!g) return fail(NVDB_ERR_INVALID_ARG, "nvdb_grid_tiles: NULL grid");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (leaf_tile && g->n_leaf) {
+    if (g->leaf_tile) CU(cudaMemcpyAsync(leaf_tile, g->leaf_tile, g->n_leaf, cudaMemcpyDeviceToHost, s));
+    else std::memset(leaf_tile, 0, g->n_leaf);
+  }
+  if (l1_tile_mask && g->n_l1) {
+    if (g->l1_tile_mask) CU(cudaMemcpyAsync(l1_tile_mask, g->l1_tile_mask, 512 * g->n_l1, cudaMemcpyDeviceToHost, s));
+    else std::memset(l1_tile_mask, 0, 512 * g->n_l1);
+  }
+  CU(cudaStreamSynchronize(s));
   return NVDB_OK;
 }
 
@@ -681,10 +787,53 @@ nvdb_status ensure_partial(nvdb_model* m, int64_t count) {
 // Training populations of one expert of a decomposed model (Section 3.4): per network, the
 // indices of the candidates inside the expert's support (level-1 slots, leaves, voxels).
 struct PopLists {
-  uint32_t* list[3] = {nullptr, nullptr, nullptr};
-  int64_t n[3] = {0, 0, 0};
+  uint32_t* list[4] = {nullptr, nullptr, nullptr, nullptr};
+  int64_t n[4] = {0, 0, 0, 0};
   ~PopLists() { for (auto& l : list) dfree(l); }
 };
+
+// Indices of the set flags[0 .. count) into a new list (count of them in *total).
+nvdb_status compact_list(const uint32_t* flags, int64_t count, uint32_t** list, int64_t* total, cudaStream_t s) {
+  int64_t* off = nullptr;
+  Scan sc;
+  auto run = [&]() -> nvdb_status {
+    TRY(dalloc(&off, (size_t)count + 1));
+    TRY(sc.run(flags, count, off, s));
+    CU(cudaMemcpyAsync(total, sc.total, 8, cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    TRY(dalloc(list, (size_t)*total + 1));
+    if (count) KLAUNCH("compact_flags", s, compact_flags_kernel<<<blocks_for(count, 256), 256, 0, s>>>(flags, off, count, *list));
+    CU(cudaGetLastError());
+    CU(cudaStreamSynchronize(s));
+    return NVDB_OK;
+  };
+  const nvdb_status st = run();
+  dfree(off);
+  return st;
+}
+
+// Training populations of a model with active tiles (Section 3.3.1): the level-0 networks
+// train on the leaves that are not tiles (net 1: those leaves, net 2: their voxels), the
+// tile value regressor on the tiles (net 3: the tile leaves).
+nvdb_status tile_populations(const nvdb_grid* g, PopLists& pl, cudaStream_t s) {
+  const Range range("tile populations");
+  uint32_t* flags = nullptr;
+  auto run = [&]() -> nvdb_status {
+    TRY(dalloc(&flags, (size_t)std::max(g->n, g->n_leaf) + 1));
+    KLAUNCH("leaf_tile_flags", s, leaf_tile_flags_kernel<<<blocks_for(g->n_leaf, 256), 256, 0, s>>>(g->leaf_tile, g->n_leaf, 0u, flags));
+    TRY(compact_list(flags, g->n_leaf, &pl.list[1], &pl.n[1], s));
+    KLAUNCH("leaf_tile_flags", s, leaf_tile_flags_kernel<<<blocks_for(g->n_leaf, 256), 256, 0, s>>>(g->leaf_tile, g->n_leaf, 1u, flags));
+    TRY(compact_list(flags, g->n_leaf, &pl.list[3], &pl.n[3], s));
+    KLAUNCH("voxel_nontile_flags", s, voxel_nontile_flags_kernel<<<blocks_for(g->n_leaf * 32, 256), 256, 0, s>>>(
+                                          g->leaf_tile, g->leaf_first, g->n_leaf, flags));
+    TRY(compact_list(flags, g->n, &pl.list[2], &pl.n[2], s));
+    if (pl.n[1] == 0 || pl.n[2] == 0) return fail(NVDB_ERR_UNSUPPORTED, "every leaf is a tile: no level-0 networks to train");
+    return NVDB_OK;
+  };
+  const nvdb_status st = run();
+  dfree(flags);
+  return st;
+}
 
 nvdb_status expert_populations(const nvdb_model* m, const nvdb_grid* g, int ex, PopLists& pl, cudaStream_t s) {
   const Range range("expert populations");
@@ -731,10 +880,11 @@ TrainJob grid_train_job(const nvdb_grid* g, int net, const nvdb_train_opts* o) {
   TrainJob j{};
   j.net = net;
   j.stream = net;
-  j.loss = net == 2 ? o->loss : LOSS_BCE;
+  j.loss = net >= 2 ? o->loss : LOSS_BCE;
   j.seed = o->seed;
   j.batch = o->batch;
   j.l1_origin = g->l1_origin; j.l1_mask = g->l1_mask; j.n_l1 = g->n_l1;
+  j.l1_tile_mask = net == 0 && g->n_tiles > 0 ? g->l1_tile_mask : nullptr;
   j.leaf_origin = g->leaf_origin; j.leaf_mask = g->leaf_mask; j.n_leaf = g->n_leaf;
   j.ijk = g->ijk; j.val = g->val; j.n = g->n;
   j.tscale = g->grid_class == 0 ? 1.f / g->half_width : 1.f;
@@ -756,7 +906,7 @@ nvdb_status make_patches(nvdb_model* m, const nvdb_grid* g, int prec, cudaStream
   for (int lev = 0; lev < 2; ++lev) {
     const int64_t items = lev == 0 ? g->n_l1 : g->n_leaf;
     const int wpi = lev == 0 ? 128 : 16;
-    uint32_t *words = nullptr, *counts = nullptr, *off32 = nullptr;
+    uint32_t *words = nullptr, *twords = nullptr, *counts = nullptr, *off32 = nullptr;
     int64_t* off = nullptr;
     uint16_t* idx = nullptr;
     auto run = [&]() -> nvdb_status {
@@ -769,16 +919,31 @@ nvdb_status make_patches(nvdb_model* m, const nvdb_grid* g, int prec, cudaStream
       job.nodes = lev == 0 ? g->l1_origin : g->leaf_origin;
       job.n_items = items;
       job.words = words;
-      TRY(launch_eval(m, lev == 0 ? 0 : 1, (nvdb_precision)prec, job, s));
+      const bool tern1 = m->ternary && lev == 0;
+      if (tern1) TRY(dalloc(&twords, (size_t)items * wpi + 1));
+      job.twords = twords;
+      // the ternary level-1 classifier decides at FP32 whatever the set's precision
+      TRY(launch_eval(m, lev == 0 ? 0 : 1, tern1 ? NVDB_FP32 : (nvdb_precision)prec, job, s));
       const uint32_t* truth = reinterpret_cast<const uint32_t*>(lev == 0 ? g->l1_mask : g->leaf_mask);
-      if (items) KLAUNCH("mismatch_count", s, mismatch_count_kernel<<<blocks_for(items, 128), 128, 0, s>>>(words, truth, wpi, items, counts));
+      if (m->ternary && lev == 1 && items)   // tiles are not classified: no level-0 patches
+        KLAUNCH("tile_words_full", s, tile_words_full_kernel<<<blocks_for(items * 16, 256), 256, 0, s>>>(words, g->leaf_tile, items));
+      if (tern1 && items)
+        KLAUNCH("tern_mismatch", s, tern_mismatch_kernel<<<blocks_for(items, 128), 128, 0, s>>>(
+                                        words, twords, truth, reinterpret_cast<const uint32_t*>(g->l1_tile_mask), items,
+                                        counts));
+      else if (items)
+        KLAUNCH("mismatch_count", s, mismatch_count_kernel<<<blocks_for(items, 128), 128, 0, s>>>(words, truth, wpi, items, counts));
       TRY(m->scan.run(counts, items, off, s));
       KLAUNCH("offsets_to_u32", s, offsets_to_u32_kernel<<<blocks_for(items + 1, 256), 256, 0, s>>>(off, m->scan.total, items, off32));
       int64_t total = 0;
       CU(cudaMemcpyAsync(&total, m->scan.total, 8, cudaMemcpyDeviceToHost, s));
       CU(cudaStreamSynchronize(s));
       TRY(dalloc(&idx, (size_t)total + 1));
-      if (items) KLAUNCH("emit_patches", s, emit_patches_kernel<<<blocks_for(items, 128), 128, 0, s>>>(words, wpi, items, off, idx));
+      if (tern1 && items)   // entries slot | true class << 12
+        KLAUNCH("tern_emit_patches", s, tern_emit_patches_kernel<<<blocks_for(items, 128), 128, 0, s>>>(
+                                            words, truth, reinterpret_cast<const uint32_t*>(g->l1_tile_mask), items, off, idx));
+      else if (items)
+        KLAUNCH("emit_patches", s, emit_patches_kernel<<<blocks_for(items, 128), 128, 0, s>>>(words, wpi, items, off, idx));
       CU(cudaGetLastError());
       // the set keeps the device lists
       (lev == 0 ? ps.d_l1_off : ps.d_l0_off) = off32;
@@ -789,7 +954,7 @@ nvdb_status make_patches(nvdb_model* m, const nvdb_grid* g, int prec, cudaStream
       return NVDB_OK;
     };
     const nvdb_status st = run();
-    dfree(words); dfree(counts); dfree(off); dfree(off32); dfree(idx);
+    dfree(words); dfree(twords); dfree(counts); dfree(off); dfree(off32); dfree(idx);
     if (st != NVDB_OK) {
       ps.release();
       return st;
@@ -823,6 +988,16 @@ extern "C" nvdb_status nvdb_compress(const nvdb_grid* g, const nvdb_train_opts* 
   const int halo = warm ? warm->sub_halo : (o->halo ? o->halo : 8);
   if (sub < 0 || sub % 512 || (sub && (halo < 8 || (halo & (halo - 1)) || 4 * halo > sub)))
     return fail(NVDB_ERR_INVALID_ARG, "subdomain must be a multiple of 512 and the halo a power of two in [8, subdomain/4]");
+  const bool tern = g->n_tiles > 0;   // active tiles: ternary level 1 + tile value regressor
+  if (warm && warm->ternary != tern) return fail(NVDB_ERR_INVALID_ARG, "warm start: the grids differ in active tiles");
+  if (tern && (sub || o->sampling)) return fail(NVDB_ERR_UNSUPPORTED, "active tiles with a decomposition or ablation sampling");
+  const int act = warm ? warm->act : o->activation;
+  const float omega = warm ? warm->omega : (o->activation ? o->omega : 1.f);
+  if (act != 0 && act != 1) return fail(NVDB_ERR_INVALID_ARG, "activation must be 0 (ReLU) or 1 (sin)");
+  if (act == 1 && !(omega > 0.f)) return fail(NVDB_ERR_INVALID_ARG, "sin activation: omega must be > 0");
+  if (act == 1 && o->train_prec != NVDB_FP32) return fail(NVDB_ERR_UNSUPPORTED, "sin activation: FP32 training only");
+  if (act == 1 && (o->patch_precs & ~(1u << NVDB_FP32)))
+    return fail(NVDB_ERR_UNSUPPORTED, "sin activation: FP32 patch sets only (patch_precs = 1)");
   *out = nullptr;
   cudaStream_t s = (cudaStream_t)stream;
   auto* m = new nvdb_model();
@@ -834,20 +1009,31 @@ extern "C" nvdb_status nvdb_compress(const nvdb_grid* g, const nvdb_train_opts* 
     for (int d = 0; d < 3; ++d) m->origin[d] = g->origin[d];
     m->log2e = g->log2e;
     m->n_l2 = g->n_l2; m->n_l1 = g->n_l1; m->n_leaf = g->n_leaf; m->n_active = g->n;
+    m->act = act;
+    m->omega = omega;
+    m->n_tiles = g->n_tiles;
     if (warm) {
       m->ffm[0] = warm->ffm[0]; m->ffm[1] = warm->ffm[1];
       for (int k = 0; k < 3; ++k) { m->width[k] = warm->width[k]; m->layers[k] = warm->layers[k]; }
+      m->tile_width = warm->tile_width;
+      m->tile_layers = warm->tile_layers;
     } else {
       for (int k = 0; k < 3; ++k) { m->width[k] = o->width[k]; m->layers[k] = o->layers[k]; }
       m->ffm[0] = o->ffm_size[0] ? o->ffm_size[0] : o->width[0];
       m->ffm[1] = o->ffm_size[1] ? o->ffm_size[1] : std::max(o->width[1], o->width[2]);
+      m->tile_width = o->tile_width ? o->tile_width : o->width[0];
+      m->tile_layers = o->tile_layers ? o->tile_layers : o->layers[0];
     }
+    if (tern) m->set_ternary(true);
     TRY(check_model_shapes(m));
     if (o->train_prec == NVDB_BF16)
-      for (int k = 0; k < 3; ++k)
-        if (m->layers[k] > kTrainTcMaxLayers)
-          return fail(NVDB_ERR_UNSUPPORTED, "BF16 training: network %d has %d hidden layers (at most %d)", k,
-                      m->layers[k], kTrainTcMaxLayers);
+      for (int k = tern ? 1 : 0; k < (tern ? 4 : 3); ++k) {
+        int nin, w, L, nout;
+        net_shape(m, k, nin, w, L, nout);
+        if (L > kTrainTcMaxLayers)
+          return fail(NVDB_ERR_UNSUPPORTED, "BF16 training: network %d has %d hidden layers (at most %d)", k, L,
+                      kTrainTcMaxLayers);
+      }
     TRY(dalloc(&m->status, 1));
     CU(cudaMemsetAsync(m->status, 0, 4, s));
     double E = std::ldexp(1.0, m->log2e);
@@ -903,8 +1089,9 @@ extern "C" nvdb_status nvdb_compress(const nvdb_grid* g, const nvdb_train_opts* 
         CU(cudaMemcpyAsync(m->net[k].p32, src, m->net[k].P * 4, cudaMemcpyDeviceToDevice, s));
         m->net[k].bf16_exact = warm->net[k].bf16_exact && o->steps == 0;
       } else {
-        const int j = k % 3;
-        const std::vector<float> p = xavier_params(o->seed, k, j == 0 ? m->ffm[0] : m->ffm[1], m->width[j], m->layers[j]);
+        int nin, w, L, nout;
+        net_shape(m, k, nin, w, L, nout);
+        const std::vector<float> p = xavier_params(o->seed, k, nin, w, L, nout);
         TRY(upload_net(m, k, p.data(), s));
         CU(cudaStreamSynchronize(s));
       }
@@ -936,7 +1123,11 @@ extern "C" nvdb_status nvdb_compress(const nvdb_grid* g, const nvdb_train_opts* 
     // which cannot be captured.)  The step index lives in device memory, so one captured
     // chunk of steps replays as a CUDA graph.  Profiled runs launch every step and train the
     // networks one after another (per-kernel events would overlap otherwise).
-    static const char* kTrainRange[3] = {"train level-1 classifier", "train level-0 classifier", "train regressor"};
+    static const char* kTrainRange[4] = {"train level-1 classifier", "train level-0 classifier", "train regressor",
+                                         "train tile regressor"};
+    const int nk = tern ? 4 : 3;   // networks per expert
+    // arithmetic of each network's training: the ternary classifier trains at FP32
+    auto tprec = [&](int k) { return tern && k == 0 ? (int)NVDB_FP32 : o->train_prec; };
     struct NetRun {
       cudaStream_t ts = nullptr;
       cudaEvent_t ev = nullptr;
@@ -950,15 +1141,16 @@ extern "C" nvdb_status nvdb_compress(const nvdb_grid* g, const nvdb_train_opts* 
     };
     const int grid = train_grid(o->batch);
     const bool profiled = prof::g_on.load();
-    int64_t poff[4] = {0, 0, 0, 0};
-    for (int k = 0; k < 3; ++k) poff[k + 1] = poff[k] + (int64_t)grid * (m->net[k].P + 1);
-    nvdb_status st = ensure_partial(m, poff[3]);
+    int64_t poff[5] = {0, 0, 0, 0, 0};
+    for (int k = 0; k < nk; ++k) poff[k + 1] = poff[k] + (int64_t)grid * (m->net[k].P + 1);
+    nvdb_status st = ensure_partial(m, poff[nk]);
     // a decomposed model trains expert after expert, each on the candidates of its support
     for (int ex = 0; ex < m->n_exp && st == NVDB_OK; ++ex) {
     PopLists pl;
     if (m->moe() && o->steps > 0) st = expert_populations(m, g, ex, pl, s);
-    NetRun nr[3];
-    for (int k = 0; k < 3 && st == NVDB_OK; ++k) {
+    if (tern && o->steps > 0) st = tile_populations(g, pl, s);
+    NetRun nr[4];
+    for (int k = 0; k < nk && st == NVDB_OK; ++k) {
       NetRun& r = nr[k];
       if (cudaStreamCreateWithFlags(&r.ts, cudaStreamNonBlocking) != cudaSuccess ||
           cudaEventCreateWithFlags(&r.ev, cudaEventDisableTiming) != cudaSuccess) {
@@ -973,14 +1165,14 @@ extern "C" nvdb_status nvdb_compress(const nvdb_grid* g, const nvdb_train_opts* 
       if ((st = dalloc(&r.d_step, 2)) != NVDB_OK) break;
       r.job = grid_train_job(g, k, o);
       r.job.stream = 3 * ex + k;
-      if (m->moe()) {
+      if (m->moe() || (tern && k > 0)) {
         r.job.pop = pl.list[k];
         r.job.pop_n = pl.n[k];
         r.job.pop_shift = k == 1 ? 9 : 0;
       }
       r.job.partial = m->partial + poff[k];
       r.job.step_dev = r.d_step;
-      if (o->train_prec == NVDB_BF16 && (st = pack_net(m, 3 * ex + k, r.ts)) != NVDB_OK) break;   // the BF16 tiles of step 1
+      if (tprec(k) == NVDB_BF16 && (st = pack_net(m, 3 * ex + k, r.ts)) != NVDB_OK) break;   // the BF16 tiles of step 1
       // the first step of this call: after the interrupted run's steps when resuming
       r.done = (int)m->losses[3 * ex + k].size();
       const int first = r.done + 1;
@@ -990,17 +1182,17 @@ extern "C" nvdb_status nvdb_compress(const nvdb_grid* g, const nvdb_train_opts* 
         break;
       }
       r.sc = AdamSched{r.d_step, o->lr, o->lr_decay, o->lr_interval, r.d_loss, first};
-      r.early = o->stop_loss[k] > 0.f && o->stop_window > 0;
+      r.early = k < 3 && o->stop_loss[k] > 0.f && o->stop_window > 0;
       r.chunk = r.early ? o->stop_window : 50;
       r.active = o->steps > 0;
     }
     auto one_step = [&](int k) -> nvdb_status {
       NetRun& r = nr[k];
       DevNet& d = m->net[3 * ex + k];
-      TRY(launch_train(m, 3 * ex + k, o->train_prec, r.job, grid, r.ts));
+      TRY(launch_train(m, 3 * ex + k, tprec(k), r.job, grid, r.ts));
       KLAUNCH("adam_reduce", r.ts, adam_reduce_kernel<<<blocks_for(d.P + 1, 32), 32 * kRedGroups, 0, r.ts>>>(
                                        r.job.partial, grid, d.P, d.p32, d.m, d.v, 0, 0.f, nullptr, nullptr,
-                                       1.f / (float)o->batch, adam_aux(d, o->train_prec, true), r.sc));
+                                       1.f / (float)o->batch, adam_aux(d, tprec(k), true), r.sc));
       CU(cudaGetLastError());
       return NVDB_OK;
     };
@@ -1041,8 +1233,8 @@ extern "C" nvdb_status nvdb_compress(const nvdb_grid* g, const nvdb_train_opts* 
       return NVDB_OK;
     };
     // concurrent: chunks of the three networks interleaved; profiled: one network at a time
-    for (int k0 = 0; k0 < (profiled ? 3 : 1) && st == NVDB_OK; ++k0) {
-      const int k1 = profiled ? k0 + 1 : 3;
+    for (int k0 = 0; k0 < (profiled ? nk : 1) && st == NVDB_OK; ++k0) {
+      const int k1 = profiled ? k0 + 1 : nk;
       for (bool any = true; any && st == NVDB_OK;) {
         any = false;
         for (int k = profiled ? k0 : 0; k < k1 && st == NVDB_OK; ++k)
@@ -1055,7 +1247,7 @@ extern "C" nvdb_status nvdb_compress(const nvdb_grid* g, const nvdb_train_opts* 
       if (profiled && st == NVDB_OK && cudaStreamSynchronize(nr[k0].ts) != cudaSuccess)
         st = fail(NVDB_ERR_CUDA, "training stream");
     }
-    for (int k = 0; k < 3; ++k) {
+    for (int k = 0; k < nk; ++k) {
       NetRun& r = nr[k];
       if (r.exec) cudaGraphExecDestroy(r.exec);
       if (st == NVDB_OK) {
@@ -1080,8 +1272,9 @@ extern "C" nvdb_status nvdb_compress(const nvdb_grid* g, const nvdb_train_opts* 
     TRY(st);
     if (o->train_prec == NVDB_BF16)   // the BF16 step trained BF16 weights: store them as such
       for (int k = 0; k < m->n_net(); ++k) {
+        if (tprec(m->tile_net(k) ? 3 : k % 3) != NVDB_BF16) continue;
         DevNet& d = m->net[k];
-        const int64_t n = d.P - d.width - 1;   // every weight and bias except the FP32 head
+        const int64_t n = d.P - d.n_out * (d.width + 1);   // every weight and bias except the FP32 head
         TRY(dalloc(&d.master, d.P));        // kept for a resumed run
         CU(cudaMemcpyAsync(d.master, d.p32, d.P * 4, cudaMemcpyDeviceToDevice, s));
         KLAUNCH("round_bf16", s, round_bf16_kernel<<<blocks_for(n, 256), 256, 0, s>>>(d.p32, n));
@@ -1170,6 +1363,8 @@ extern "C" nvdb_status nvdb_model_losses(const nvdb_model* m, int net, float* lo
 namespace {
 bool same_shape(const nvdb_model* a, const nvdb_model* b) {
   if (a->ffm[0] != b->ffm[0] || a->ffm[1] != b->ffm[1]) return false;
+  if (a->ternary != b->ternary || a->act != b->act || a->omega != b->omega) return false;
+  if (a->ternary && (a->tile_width != b->tile_width || a->tile_layers != b->tile_layers)) return false;
   for (int k = 0; k < 3; ++k)
     if (a->width[k] != b->width[k] || a->layers[k] != b->layers[k]) return false;
   return true;
@@ -1218,7 +1413,12 @@ nvdb_status decode_batch(nvdb_model* const* ms, int n, nvdb_precision prec, Deco
     sa[m + 1] = sa[m] + ms[m]->n_active;
   }
   const int64_t N2 = s2[n], N1 = s1[n], NL = sl[n], NA = sa[n];
+  const bool tern = ms[0]->ternary;   // a batch holds models of one kind (same_shape)
+  std::vector<int64_t> st(n + 1, 0);
+  for (int m = 0; m < n; ++m) st[m + 1] = st[m] + ms[m]->n_tiles;
+  const int64_t NT = st[n];
   TRY(d.reserve(N2, N1, NL));
+  if (tern) TRY(d.reserve_tiles(NT));
   CU(cudaMemsetAsync(d.lb, 0, (size_t)DecodeScratch::lb_words(d.cap2, d.cap1, d.capl) * 8, s));
   std::vector<const PatchSet*> ps(n);
   for (int m = 0; m < n; ++m) ps[m] = ms[m]->patch_set(prec);
@@ -1238,26 +1438,39 @@ nvdb_status decode_batch(nvdb_model* const* ms, int n, nvdb_precision prec, Deco
     j.nodes = d.l1_origin + s1[m];
     j.n_items = ms[m]->n_l1;
     j.words = d.l1_words + 128 * s1[m];
+    j.twords = tern ? d.t1_words + 128 * s1[m] : nullptr;
     j.status = d.status;
     b.it[m] = eval_item(ms[m], 0, j);
   }
   {
     const Range range("decode: level-1 classification");
-    TRY(launch_batch(b, prec, s));
+    TRY(launch_batch(b, tern ? NVDB_FP32 : prec, s));   // the ternary classifier runs at FP32
   }
   PatchBatch pb;
   pb.n = n;
   for (int m = 0; m < n; ++m) pb.it[m] = PatchItem{ps[m]->d_l1_off, ps[m]->d_l1_idx, s1[m]};
-  if (N1) {
+  if (tern && N1) {   // ternary patches set each listed slot's class, then both masks are counted
+    KLAUNCH("tern_patch", s, tern_patch_batch_kernel<<<blocks_for(N1 * 32, 256), 256, 0, s>>>(d.l1_words, d.t1_words, N1, pb));
+    PatchBatch none = pb;
+    for (int m = 0; m < n; ++m) none.it[m].off = nullptr;
+    KLAUNCH("patch_scan", s, patch_scan_batch_kernel<<<(unsigned)DecodeScratch::blocks1(N1), 256, 0, s>>>(
+                                 d.l1_words, 128, N1, none, d.l1_off, NL, d.lb1(), d.status));
+    KLAUNCH("tile_scan", s, patch_scan_batch_kernel<<<(unsigned)DecodeScratch::blocks1(N1), 256, 0, s>>>(
+                                d.t1_words, 128, N1, none, d.t1_off, NT, d.lbt(), d.status));
+  } else if (N1) {
     KLAUNCH("patch_scan", s, patch_scan_batch_kernel<<<(unsigned)DecodeScratch::blocks1(N1), 256, 0, s>>>(
                                  d.l1_words, 128, N1, pb, d.l1_off, NL, d.lb1(), d.status));
   } else if (NL) {
     KLAUNCH("flag_corrupt", s, flag_corrupt_kernel<<<1, 1, 0, s>>>(d.status));   // leaves expected, no nodes
   }
-  if (N1)
-    KLAUNCH("emit_leaves", s, emit_leaves_kernel<<<blocks_for(N1 * 32, 256), 256, 0, s>>>(d.l1_words, d.l1_origin, N1,
-                                                                                       d.l1_off, d.leaf_origin, NL,
-                                                                                       d.status));
+  if (N1) {
+    KLAUNCH("emit_leaves", s, emit_leaves_kernel<<<blocks_for(N1 * 32, 256), 256, 0, s>>>(
+                                  d.l1_words, d.l1_origin, N1, d.l1_off, d.leaf_origin, NL, d.status,
+                                  tern ? d.t1_words : nullptr, tern ? d.t1_off : nullptr));
+    if (tern && NT)
+      KLAUNCH("emit_tiles", s, emit_tile_coords_kernel<<<blocks_for(N1 * 32, 256), 256, 0, s>>>(
+                                   d.t1_words, d.l1_origin, N1, d.t1_off, d.tile_ijk, NT, d.status));
+  }
   for (int m = 0; m < n; ++m) {
     EvalJob j{};
     j.mode = MODE_L0;
@@ -1274,7 +1487,8 @@ nvdb_status decode_batch(nvdb_model* const* ms, int n, nvdb_precision prec, Deco
   for (int m = 0; m < n; ++m) pb.it[m] = PatchItem{ps[m]->d_l0_off, ps[m]->d_l0_idx, sl[m]};
   if (NL) {
     KLAUNCH("patch_scan", s, patch_scan_batch_kernel<<<(unsigned)DecodeScratch::blocks1(NL), 256, 0, s>>>(
-                                 d.leaf_words, 16, NL, pb, d.leaf_off, NA, d.lb0(), d.status));
+                                 d.leaf_words, 16, NL, pb, d.leaf_off, NA, d.lb0(), d.status,
+                                 tern ? d.leaf_origin : nullptr));
   } else if (NA) {
     KLAUNCH("flag_corrupt", s, flag_corrupt_kernel<<<1, 1, 0, s>>>(d.status));   // voxels expected, no leaves
   }
@@ -1299,9 +1513,31 @@ nvdb_status decode_batch(nvdb_model* const* ms, int n, nvdb_precision prec, Deco
       b.it[m] = eval_item(ms[m], 2, j);
     }
     {
-    const Range range("decode: regression");
-    TRY(launch_batch(b, prec, s));
+      const Range range("decode: regression");
+      TRY(launch_batch(b, prec, s));
+    }
   }
+  if (tern && NT) {   // tile values (net 3 at the tile's leaf-unit coordinate), then the tiles' voxels
+    for (int m = 0; m < n; ++m) {
+      EvalJob j{};
+      j.mode = MODE_LIST;
+      j.ijk = d.tile_ijk + 3 * st[m];
+      j.n_items = ms[m]->n_tiles;
+      j.shift = 3;
+      j.out = d.tval + st[m];
+      j.scale = ms[m]->value_scale();
+      j.status = d.status;
+      b.it[m] = eval_item(ms[m], 3, j);
+    }
+    {
+      const Range range("decode: tile values");
+      TRY(launch_batch(b, prec, s));
+    }
+    if (out_val && NL)
+      KLAUNCH("tile_fill", s, tile_fill_kernel<<<blocks_for(NL * 32, 256), 256, 0, s>>>(d.leaf_origin, NL, d.leaf_off,
+                                                                                     d.tval, out_val, NA));
+  }
+  if (out_ijk) {
     if (sink && NA) {
       CU(cudaEventRecord(sink->ev, s));
       CU(cudaStreamWaitEvent(sink->copy, sink->ev, 0));
@@ -1358,6 +1594,7 @@ nvdb_status decompress_impl(const nvdb_model* const* models, int n_models, nvdb_
     counts[i] = models[i]->n_active;
     need += models[i]->n_active;
     if (!models[i]->patch_set(prec)) return fail(NVDB_ERR_UNSUPPORTED, "model %d has no patch set for precision %d", i, (int)prec);
+    TRY(check_eval_prec(models[i], 1, prec));
   }
   if (!d_ijk) return NVDB_OK;
   if (need > capacity) return fail(NVDB_ERR_CAPACITY, "nvdb_decompress: need %lld voxels, capacity %lld", (long long)need, (long long)capacity);
@@ -1428,6 +1665,7 @@ nvdb_status build_query_cache(nvdb_model* m, cudaStream_t s) {
   q.batch = kQueryBatch;
   TRY(dalloc(&q.qmask, q.batch)); TRY(dalloc(&q.counts, q.batch)); TRY(dalloc(&q.off, q.batch + 1));
   TRY(dalloc(&q.list, 3 * 8 * q.batch)); TRY(dalloc(&q.vals, 8 * q.batch));
+  if (m->ternary) { TRY(dalloc(&q.qtile, q.batch)); TRY(dalloc(&q.qtv, 8 * q.batch)); }
   TRY(m->scan.reserve(q.batch));
   uint32_t hst = 0;
   TRY(read_status(m->ds.status, s, &hst));
@@ -1447,6 +1685,8 @@ TopoView topo_view(const nvdb_model* m) {
   tv.l1_pre = m->qc.l1_pre;
   tv.l1_base = m->ds.l1_off;
   tv.leaf_words = m->ds.leaf_words;
+  tv.items = m->ternary ? m->ds.leaf_origin : nullptr;
+  tv.tval = m->ternary ? m->ds.tval : nullptr;
   return tv;
 }
 }  // namespace
@@ -1457,6 +1697,7 @@ extern "C" nvdb_status nvdb_query(const nvdb_model* cm, const float* d_xyz, int6
   if (!cm || n < 0 || (n > 0 && (!d_xyz || !d_out))) return fail(NVDB_ERR_INVALID_ARG, "nvdb_query: bad arguments");
   if (!eval_prec_ok(prec)) return fail(NVDB_ERR_UNSUPPORTED, "precision %d", (int)prec);
   nvdb_model* m = const_cast<nvdb_model*>(cm);
+  TRY(check_eval_prec(m, 2, prec));
   cudaStream_t s = (cudaStream_t)stream;
   TRY(build_query_cache(m, s));
   if (prec != NVDB_FP32) CU(cudaMemsetAsync(m->status, 0, 4, s));
@@ -1466,7 +1707,7 @@ extern "C" nvdb_status nvdb_query(const nvdb_model* cm, const float* d_xyz, int6
     const int64_t nb = std::min(q.batch, n - b0);
     const float* xyz = d_xyz + 3 * b0;
     KLAUNCH("query_lookup", s, query_lookup_kernel<<<blocks_for(nb, 256), 256, 0, s>>>(tv, xyz, nb, q.qmask, q.counts,
-                                                             d_active ? d_active + b0 : nullptr));
+                                                             d_active ? d_active + b0 : nullptr, q.qtile, q.qtv));
     TRY(m->scan.run(q.counts, nb, q.off, s));
     KLAUNCH("query_emit", s, query_emit_kernel<<<blocks_for(nb, 256), 256, 0, s>>>(xyz, nb, q.qmask, q.off, q.list));
     EvalJob jr{};
@@ -1477,7 +1718,8 @@ extern "C" nvdb_status nvdb_query(const nvdb_model* cm, const float* d_xyz, int6
     jr.out = q.vals;
     jr.scale = m->value_scale();
     TRY(launch_eval(m, 2, prec, jr, s));
-    KLAUNCH("query_blend", s, query_blend_kernel<<<blocks_for(nb, 256), 256, 0, s>>>(xyz, nb, q.qmask, q.off, q.vals, m->background, d_out + b0));
+    KLAUNCH("query_blend", s, query_blend_kernel<<<blocks_for(nb, 256), 256, 0, s>>>(xyz, nb, q.qmask, q.off, q.vals, m->background, d_out + b0,
+                                                            q.qtile, q.qtv));
     CU(cudaGetLastError());
   }
   return eval_status(m, prec, s);
@@ -1711,12 +1953,14 @@ extern "C" nvdb_status nvdb_render(const nvdb_model* cm, const nvdb_camera* cam,
 // ============================================================================ network-level calls
 extern "C" nvdb_status nvdb_mlp_eval(const nvdb_model* m, int net, nvdb_precision prec, const int32_t* d_ijk,
                                      int64_t n, float* d_out, nvdb_stream stream) {
-  if (!m || net < 0 || net > 2 || n < 0 || (n > 0 && (!d_ijk || !d_out))) return fail(NVDB_ERR_INVALID_ARG, "nvdb_mlp_eval: bad arguments");
+  if (!m || net < 0 || net >= m->n_net() || n < 0 || (n > 0 && (!d_ijk || !d_out)))
+    return fail(NVDB_ERR_INVALID_ARG, "nvdb_mlp_eval: bad arguments");
+  TRY(check_eval_prec(m, net, prec));
   EvalJob j{};
   j.mode = MODE_LIST;
   j.ijk = d_ijk;
   j.n_items = n;
-  j.shift = net == 0 ? 3 : 0;
+  j.shift = m->net_level(net) ? 3 : 0;
   j.out = d_out;
   j.scale = 1.f;
   cudaStream_t s = (cudaStream_t)stream;
@@ -1739,13 +1983,14 @@ extern "C" nvdb_status nvdb_mlp_grad(const nvdb_model* cm, int net, nvdb_precisi
   if (loss_kind < 0 || loss_kind > 3) return fail(NVDB_ERR_INVALID_ARG, "unknown loss %d", loss_kind);
   if (n >= (1ll << 31)) return fail(NVDB_ERR_UNSUPPORTED, "nvdb_mlp_grad: n >= 2^31");
   nvdb_model* m = const_cast<nvdb_model*>(cm);
+  if (m->net[net].n_out != 1) return fail(NVDB_ERR_UNSUPPORTED, "nvdb_mlp_grad: networks with one output only");
   cudaStream_t s = (cudaStream_t)stream;
   const DevNet& d = m->net[net];
   const int grid = train_grid(n);
   TRY(ensure_partial(m, (int64_t)grid * (d.P + 1)));
   CU(cudaMemsetAsync(m->status, 0, 4, s));   // this call's device-side errors only
   TrainJob j{};
-  j.net = net % 3;
+  j.net = m->tile_net(net) ? 3 : net % 3;
   j.stream = net;
   j.loss = loss_kind;
   j.step = 1;
@@ -1857,6 +2102,9 @@ extern "C" nvdb_status nvdb_model_repatch(nvdb_model* m, const nvdb_grid* g, uin
   if (g->n_l1 != m->n_l1 || g->n_leaf != m->n_leaf || g->n != m->n_active || g->log2e != m->log2e ||
       g->origin[0] != m->origin[0] || g->origin[1] != m->origin[1] || g->origin[2] != m->origin[2])
     return fail(NVDB_ERR_INVALID_ARG, "nvdb_model_repatch: the grid is not the one the model encodes");
+  if (g->n_tiles != m->n_tiles) return fail(NVDB_ERR_INVALID_ARG, "nvdb_model_repatch: the grid's tiles differ");
+  for (int p = 0; p < kNumPrecisions; ++p)
+    if (patch_precs & (1u << p)) TRY(check_eval_prec(m, 1, (nvdb_precision)p));
   cudaStream_t s = (cudaStream_t)stream;
   m->qc.release();
   CU(cudaMemsetAsync(m->status, 0, 4, s));
@@ -1881,6 +2129,7 @@ extern "C" nvdb_status nvdb_model_info(const nvdb_model* m, nvdb_info* out) {
   out->n_l2 = m->n_l2;
   out->n_experts = m->n_exp;
   out->subdomain = m->sub_size;
+  out->n_tiles = m->n_tiles;
   return NVDB_OK;
 }
 
@@ -1894,6 +2143,17 @@ struct BlobHeader {
   uint64_t reserved1[2];
 };
 static_assert(sizeof(BlobHeader) == 128, "blob header is 128 bytes");
+
+// Version 3 extension, after the header: ternary level 1 with a tile value regressor, and the
+// hidden activation.
+struct BlobExt {
+  int32_t flags;         // bit 0: ternary level-1 classifier + tile value regressor (net 3)
+  int32_t activation;    // 0 ReLU, 1 sin
+  float omega;
+  int32_t tile_width, tile_layers, reserved;
+  int64_t n_tiles;
+};
+static_assert(sizeof(BlobExt) == 32, "blob extension is 32 bytes");
 
 struct Writer {
   std::vector<uint8_t> b;
@@ -1923,7 +2183,8 @@ extern "C" nvdb_status nvdb_model_export(const nvdb_model* m, void* buf, size_t*
   Writer w;
   BlobHeader h{};
   std::memcpy(h.magic, "NVDBMDL1", 8);
-  h.version = m->moe() ? 2 : 1;   // version 2 carries the domain decomposition
+  const bool ext = m->ternary || m->act != 0;
+  h.version = ext ? 3 : (m->moe() ? 2 : 1);   // 2: the domain decomposition; 3: the extension
   h.grid_class = (uint32_t)m->grid_class;
   h.background = m->background;
   h.half_width = m->half_width;
@@ -1940,6 +2201,16 @@ extern "C" nvdb_status nvdb_model_export(const nvdb_model* m, void* buf, size_t*
     h.reserved1[1] = (uint64_t)m->sub_halo;
   }
   w.put(&h, sizeof h);
+  if (ext) {
+    BlobExt e{};
+    e.flags = m->ternary ? 1 : 0;
+    e.activation = m->act;
+    e.omega = m->omega;
+    e.tile_width = m->ternary ? m->tile_width : 0;
+    e.tile_layers = m->ternary ? m->tile_layers : 0;
+    e.n_tiles = m->n_tiles;
+    w.put(&e, sizeof e);
+  }
   for (int lev = 0; lev < 2; ++lev) { w.put(m->q_host[lev].data(), m->q_host[lev].size() * 4); w.pad(); }
   CU(cudaDeviceSynchronize());
   for (int k = 0; k < m->n_net(); ++k) {
@@ -1987,9 +2258,14 @@ extern "C" nvdb_status nvdb_model_import(const void* buf, size_t bytes, nvdb_str
   cudaStream_t s = (cudaStream_t)stream;
   Reader r{static_cast<const uint8_t*>(buf), bytes};
   const BlobHeader* h = static_cast<const BlobHeader*>(r.take(sizeof(BlobHeader)));
-  if (!h || std::memcmp(h->magic, "NVDBMDL1", 8) != 0 || (h->version != 1 && h->version != 2))
+  if (!h || std::memcmp(h->magic, "NVDBMDL1", 8) != 0 || h->version < 1 || h->version > 3)
     return fail(NVDB_ERR_CORRUPT, "not an NVDBMDL1 blob");
-  const bool moe = h->version == 2;
+  const bool moe = h->version == 2 || (h->version == 3 && h->reserved0 > 0);
+  const BlobExt* ex = h->version == 3 ? static_cast<const BlobExt*>(r.take(sizeof(BlobExt))) : nullptr;
+  if (h->version == 3 && (!ex || (ex->flags & ~1) || ex->activation < 0 || ex->activation > 1 ||
+                          (ex->activation == 1 && !(ex->omega > 0.f)) || ex->n_tiles < 0 ||
+                          ((ex->flags & 1) && (moe || ex->n_tiles == 0))))
+    return fail(NVDB_ERR_CORRUPT, "bad blob extension");
   if (moe && (h->reserved0 < 1 || h->reserved0 > (1 << 20) || h->reserved1[0] == 0 || h->reserved1[0] % 512 ||
               h->reserved1[1] < 8 || (h->reserved1[1] & (h->reserved1[1] - 1)) || 4 * h->reserved1[1] > h->reserved1[0]))
     return fail(NVDB_ERR_CORRUPT, "bad decomposition header");
@@ -2007,6 +2283,14 @@ extern "C" nvdb_status nvdb_model_import(const void* buf, size_t bytes, nvdb_str
     m->ffm[1] = h->ffm_size[1];
     for (int k = 0; k < 3; ++k) { m->width[k] = h->width[k]; m->layers[k] = h->layers[k]; }
     m->n_l2 = h->n_l2; m->n_l1 = h->n_l1; m->n_leaf = h->n_leaf; m->n_active = h->n_active;
+    if (ex) {
+      m->act = ex->activation;
+      m->omega = ex->activation ? ex->omega : 1.f;
+      m->n_tiles = ex->n_tiles;
+      m->tile_width = ex->tile_width;
+      m->tile_layers = ex->tile_layers;
+      if (ex->flags & 1) m->set_ternary(true);
+    }
     TRY(check_model_shapes(m));
     TRY(dalloc(&m->status, 1));
     CU(cudaMemsetAsync(m->status, 0, 4, s));
@@ -2020,19 +2304,21 @@ extern "C" nvdb_status nvdb_model_import(const void* buf, size_t bytes, nvdb_str
       CU(cudaMemcpy(m->q_dev[lev], q, cnt * 4, cudaMemcpyHostToDevice));
     }
     if (moe) {
+      if (m->ternary) return fail(NVDB_ERR_CORRUPT, "tiles with a decomposition");
       m->set_experts((int)h->reserved0);
       m->sub_size = (int)h->reserved1[0];
       m->sub_halo = (int)h->reserved1[1];
     }
     for (int k = 0; k < m->n_net(); ++k) {
-      const int j = k % 3;
-      const int64_t P = net_param_count(j == 0 ? m->ffm[0] : m->ffm[1], m->width[j], m->layers[j]);
+      int nin, w, L, nout;
+      net_shape(m, k, nin, w, L, nout);
+      const int64_t P = net_param_count(nin, w, L, nout);
       const float* p = static_cast<const float*>(r.take((size_t)P * 4));
       r.pad();
       if (!p) return fail(NVDB_ERR_CORRUPT, "blob truncated (network %d)", k);
       std::vector<float> tmp(p, p + P);
       TRY(upload_net(m, k, tmp.data(), s));
-      m->net[k].bf16_exact = bf16_exact_layers(tmp.data(), P - m->width[j] - 1);
+      m->net[k].bf16_exact = bf16_exact_layers(tmp.data(), P - (int64_t)nout * (w + 1));
       CU(cudaStreamSynchronize(s));
     }
     if (moe) {   // grid of subdomains and expert origins (Section 3.4)
@@ -2087,7 +2373,7 @@ extern "C" nvdb_status nvdb_model_import(const void* buf, size_t bytes, nvdb_str
       if (!ph) return fail(NVDB_ERR_CORRUPT, "blob truncated (patch header)");
       PatchSet ps;
       ps.prec = ph[0];
-      if (!eval_prec_ok(ps.prec) || m->patch_set((nvdb_precision)ps.prec))
+      if (!eval_prec_ok(ps.prec) || m->patch_set((nvdb_precision)ps.prec) || (m->act != 0 && ps.prec != NVDB_FP32))
         return fail(NVDB_ERR_CORRUPT, "patch set %d: bad or repeated precision %d", i, ps.prec);
       // both levels: offsets and indices straight from the blob to the device; the
       // offsets (monotone, from 0 to the patch count) and the index ranges are checked
@@ -2115,8 +2401,10 @@ extern "C" nvdb_status nvdb_model_import(const void* buf, size_t bytes, nvdb_str
           return fail(NVDB_ERR_CUDA, "patch upload");
         }
         const int64_t work = std::max<int64_t>(nitem[lev] + 1, std::min<int64_t>(n, 1 << 22));
+        // ternary level 1: entries slot | class << 12 with class <= 2
+        const uint32_t lim = lev == 0 ? (m->ternary ? 3u * 4096u : 4096u) : 512u;
         KLAUNCH("check_patches", s, check_patches_kernel<<<blocks_for(work, 256), 256, 0, s>>>(
-                                        doff, nitem[lev], didx, n, lev == 0 ? 4096u : 512u, m->status));
+                                        doff, nitem[lev], didx, n, lim, m->status));
       }
       m->patches.push_back(ps);
     }
@@ -2200,6 +2488,7 @@ extern "C" nvdb_status nvdb_mlp_grad_static(const nvdb_model* m, int net, const 
   if (loss_kind < 0 || loss_kind > 3) return fail(NVDB_ERR_INVALID_ARG, "unknown loss %d", loss_kind);
   if (n >= (1ll << 31)) return fail(NVDB_ERR_UNSUPPORTED, "nvdb_mlp_grad_static: n >= 2^31");
   const DevNet& d = m->net[net];
+  if (d.n_out != 1) return fail(NVDB_ERR_UNSUPPORTED, "nvdb_mlp_grad_static: networks with one output only");
   // one CTA needs P + 1 floats of partials, plus one float for the loss
   const int64_t limit = g_static_limit.load();
   if (d.P + 2 > limit)
@@ -2219,7 +2508,7 @@ extern "C" nvdb_status nvdb_mlp_grad_static(const nvdb_model* m, int net, const 
   const int grid = (int)std::min<int64_t>(std::min<int64_t>((n + kTile - 1) / kTile, num_sms()), fit);
   float* loss_slot = scratch + (limit - 1);
   TrainJob j{};
-  j.net = net % 3;
+  j.net = m->tile_net(net) ? 3 : net % 3;
   j.stream = net;
   j.loss = loss_kind;
   j.step = 1;
@@ -2289,6 +2578,7 @@ extern "C" nvdb_status nvdb_decompress_plan(const nvdb_model* const* models, int
   for (int i = 0; i < n_models; ++i) {
     if (!models[i]) return fail(NVDB_ERR_INVALID_ARG, "nvdb_decompress_plan: NULL model");
     if (!models[i]->patch_set(prec)) return fail(NVDB_ERR_UNSUPPORTED, "model %d has no patch set for precision %d", i, (int)prec);
+    TRY(check_eval_prec(models[i], 1, prec));
     need += models[i]->n_active;
   }
   if (need > capacity) return fail(NVDB_ERR_CAPACITY, "nvdb_decompress_plan: need %lld voxels, capacity %lld", (long long)need, (long long)capacity);

@@ -15,7 +15,7 @@
 namespace nvdb {
 
 struct TrainJob {
-  int net;                    // 0 level-1 classifier, 1 level-0 classifier, 2 regressor
+  int net;                    // 0 level-1 classifier, 1 level-0 classifier, 2 regressor, 3 tile regressor
   int stream;                 // sample stream of the network: 3 expert + net (net without experts)
   int loss;                   // LOSS_*
   int step;                   // Adam step (1-based), keys the sample stream
@@ -27,6 +27,10 @@ struct TrainJob {
   const float* target_list;
   // population from the explicit grid
   const int4* l1_origin; const unsigned long long* l1_mask; int64_t n_l1;
+  // active tiles (a pruned grid): the ternary level-1 label is 1 on a tile slot, 0 on a
+  // child leaf, 2 elsewhere; the tile regressor (net 3) samples tile leaves (via pop) and
+  // regresses the tile value at the slot's leaf-unit coordinate
+  const unsigned long long* l1_tile_mask;
   const int4* leaf_origin; const unsigned long long* leaf_mask; int64_t n_leaf;
   const int32_t* ijk; const float* val; int64_t n;
   // a domain decomposition's expert samples a sub-population (Section 3.4): element i is
@@ -66,7 +70,7 @@ __device__ __forceinline__ int64_t train_population(const TrainJob& j) {
   if (j.pop) return j.pop_n << j.pop_shift;
   if (j.net == 2 && j.sampling == 1) return j.n_leaf * 512;
   if (j.net == 2 && j.sampling == 2) return (int64_t)1 << (3 * j.log2e);
-  return j.net == 0 ? j.n_l1 * 4096 : j.net == 1 ? j.n_leaf * 512 : j.n;
+  return j.net == 0 ? j.n_l1 * 4096 : j.net == 1 ? j.n_leaf * 512 : j.net == 3 ? j.n_leaf : j.n;
 }
 
 // Canonical key of the leaf holding voxel (i, j, k): level-2 key, level-1 slot, leaf slot.
@@ -90,7 +94,7 @@ __device__ __forceinline__ float leaf_voxel_target(const TrainJob& j, int64_t le
 // Coordinates (level units) and target of sample s.
 __device__ __forceinline__ void train_sample(const TrainJob& j, int64_t s, int& cx, int& cy, int& cz, float& tgt) {
   if (j.ijk_list) {
-    const int sh = j.net == 0 ? 3 : 0;
+    const int sh = j.net == 0 || j.net == 3 ? 3 : 0;
     cx = (j.ijk_list[3 * s] - j.ox) >> sh;
     cy = (j.ijk_list[3 * s + 1] - j.oy) >> sh;
     cz = (j.ijk_list[3 * s + 2] - j.oz) >> sh;
@@ -143,7 +147,19 @@ __device__ __forceinline__ void train_sample(const TrainJob& j, int64_t s, int& 
     cx = ((o.x - j.ox) >> 3) + (slot >> 8);
     cy = ((o.y - j.oy) >> 3) + ((slot >> 4) & 15);
     cz = ((o.z - j.oz) >> 3) + (slot & 15);
-    tgt = (float)((j.l1_mask[node * 64 + (slot >> 6)] >> (slot & 63)) & 1ull);
+    const bool child = (j.l1_mask[node * 64 + (slot >> 6)] >> (slot & 63)) & 1ull;
+    if (j.l1_tile_mask) {
+      const bool tile = (j.l1_tile_mask[node * 64 + (slot >> 6)] >> (slot & 63)) & 1ull;
+      tgt = tile ? 1.f : child ? 0.f : 2.f;
+    } else {
+      tgt = child ? 1.f : 0.f;
+    }
+  } else if (j.net == 3) {
+    const int4 o = j.leaf_origin[idx];
+    cx = (o.x - j.ox) >> 3;
+    cy = (o.y - j.oy) >> 3;
+    cz = (o.z - j.oz) >> 3;
+    tgt = j.val[j.leaf_first[idx]] * j.tscale;
   } else if (j.net == 1) {
     const int64_t leaf = (int64_t)(idx >> 9);
     const int off = (int)(idx & 511);
@@ -179,25 +195,35 @@ __device__ __forceinline__ void row_loss(int kind, float y, float t, float inv_b
   }
 }
 
-template <int NIN, int W>
+template <int NIN, int W, int NOUT = 1>
 struct TrainSmem {
   static constexpr int KP = NIN + 1, WP = W + 1;
   __host__ __device__ static size_t bytes(int L) {
-    return ((size_t)kTile * KP + (size_t)(L + 1) * kTile * WP + kTile + 3 * (NIN / 2) + 64) * 4;
+    return ((size_t)kTile * KP + (size_t)(L + 1) * kTile * WP + NOUT * kTile + 3 * (NIN / 2) + 64) * 4;
   }
 };
 
+__device__ __forceinline__ float act_f(int act, float om, float a) { return act ? sinf(om * a) : fmaxf(a, 0.f); }
+
+// delta * act'(a): ReLU passes delta where a > 0; sin scales it by omega cos(omega a).
+__device__ __forceinline__ float act_back(int act, float om, float a, float delta) {
+  return act ? delta * (om * cosf(om * a)) : (a > 0.f ? delta : 0.f);
+}
+
 // dW[o][i] += sum_r D[r][o] H[r][i] for a [W x K] layer; thread t owns column
-// i = t % K and the OPT output rows starting at (t / K) * OPT.
+// i = t % K and the OPT output rows starting at (t / K) * OPT.  With act >= 0 the stored
+// H holds pre-activations and the layer input is act(H); act < 0: H is the input itself.
 template <int K, int W>
-__device__ __forceinline__ void accum_dW(const float* D, int dstride, const float* H, int hstride, float* gW) {
+__device__ __forceinline__ void accum_dW(const float* D, int dstride, const float* H, int hstride, float* gW, int act,
+                                         float om) {
   constexpr int OB = kTile / K, OPT = W / OB;
   const int i = threadIdx.x % K, o0 = (threadIdx.x / K) * OPT;
   float acc[OPT];
 #pragma unroll
   for (int k = 0; k < OPT; ++k) acc[k] = 0.f;
   for (int r = 0; r < kTile; ++r) {
-    const float h = H[r * hstride + i];
+    const float hv = H[r * hstride + i];
+    const float h = act < 0 ? hv : act_f(act, om, hv);
 #pragma unroll
     for (int k = 0; k < OPT; ++k) acc[k] = fmaf(D[r * dstride + o0 + k], h, acc[k]);
   }
@@ -205,23 +231,41 @@ __device__ __forceinline__ void accum_dW(const float* D, int dstride, const floa
   for (int k = 0; k < OPT; ++k) gW[(o0 + k) * K + i] += acc[k];
 }
 
-template <int NIN, int W>
+// Per-row softmax cross-entropy of three logits (Section 3.3.1, the ternary level-1
+// classifier) and its gradient of the batch mean; t is the class.
+__device__ __forceinline__ void row_loss3(const float* y, int t, float inv_b, float& l, float* g) {
+  const float mx = fmaxf(y[0], fmaxf(y[1], y[2]));
+  const float e0 = expf(y[0] - mx), e1 = expf(y[1] - mx), e2 = expf(y[2] - mx);
+  const float lse = mx + logf(e0 + e1 + e2);
+  l = lse - y[t];
+  const float inv = 1.f / (e0 + e1 + e2);
+  g[0] = (e0 * inv - (t == 0 ? 1.f : 0.f)) * inv_b;
+  g[1] = (e1 * inv - (t == 1 ? 1.f : 0.f)) * inv_b;
+  g[2] = (e2 * inv - (t == 2 ? 1.f : 0.f)) * inv_b;
+}
+
+// FP32 training step on CUDA cores: forward with the pre-activations of every hidden layer
+// kept in shared memory, head and loss, backward with per-CTA gradient partials summed in a
+// fixed order.  NOUT = 3: the ternary level-1 classifier's softmax cross-entropy head.
+template <int NIN, int W, int NOUT = 1>
 __global__ void __launch_bounds__(kTile, 1) train_fwd_bwd_kernel(NetView net, TrainJob job) {
   extern __shared__ float4 smem_t4[];
   take_step(job);
   constexpr int M = NIN / 2, KP = NIN + 1, WP = W + 1;
   const int L = net.layers;
+  const int act = net.act;
+  const float om = net.omega;
   float* H0 = reinterpret_cast<float*>(smem_t4);            // [128][NIN+1] encoding
-  float* Hl = H0 + kTile * KP;                               // H_1..H_L, then delta: [L+1][128][W+1]
+  float* Hl = H0 + kTile * KP;                               // A_1..A_L (pre-activations), then delta
   float* Dl = Hl + (size_t)L * kTile * WP;
-  float* gsh = Dl + kTile * WP;                              // dL/dy per row
-  uint32_t* sq = reinterpret_cast<uint32_t*>(gsh + kTile);
+  float* gsh = Dl + kTile * WP;                              // dL/dy per output and row [NOUT][128]
+  uint32_t* sq = reinterpret_cast<uint32_t*>(gsh + NOUT * kTile);
   float* red = reinterpret_cast<float*>(sq + 3 * M);         // 32 floats for the loss reduction
   const int r = threadIdx.x;
   for (int i = r; i < 3 * M; i += kTile) sq[i] = net.q[i];
   __syncthreads();
   const float* p = net.p32;
-  const int64_t P = net_param_count(NIN, W, L);
+  const int64_t P = net_param_count(NIN, W, L, NOUT);
   float* gpart = job.partial + (int64_t)blockIdx.x * (P + 1);
   for (int64_t e = r; e <= P; e += kTile) gpart[e] = 0.f;
   __syncthreads();
@@ -234,7 +278,7 @@ __global__ void __launch_bounds__(kTile, 1) train_fwd_bwd_kernel(NetView net, Tr
     int cx = 0, cy = 0, cz = 0;
     float tgt = 0.f;
     if (valid) train_sample(job, s, cx, cy, cz, tgt);
-    // ---- forward, saving activations
+    // ---- forward, saving pre-activations
     float h[NIN > W ? NIN : W], a[W];
     encode_f32<NIN>(sq, cx, cy, cz, h);
 #pragma unroll
@@ -245,33 +289,51 @@ __global__ void __launch_bounds__(kTile, 1) train_fwd_bwd_kernel(NetView net, Tr
       pl += (l == 0 ? W * NIN : W * W) + W;
       float* Hs = Hl + (size_t)l * kTile * WP + r * WP;
 #pragma unroll
-      for (int o = 0; o < W; ++o) { h[o] = fmaxf(a[o], 0.f); Hs[o] = h[o]; }
+      for (int o = 0; o < W; ++o) { h[o] = act_f(act, om, a[o]); Hs[o] = a[o]; }
     }
-    const float* wh = pl;
-    float y = wh[W];
+    const float* wh = pl;   // W_h [NOUT][W], then b_h [NOUT]
+    float y[NOUT], g[NOUT], lr_;
 #pragma unroll
-    for (int i = 0; i < W; ++i) y = fmaf(wh[i], h[i], y);
-    float lr_, g;
-    row_loss(job.loss, y, tgt, inv_b, lr_, g);
-    if (!valid) { lr_ = 0.f; g = 0.f; }
+    for (int c = 0; c < NOUT; ++c) {
+      y[c] = wh[NOUT * W + c];
+#pragma unroll
+      for (int i = 0; i < W; ++i) y[c] = fmaf(wh[c * W + i], h[i], y[c]);
+    }
+    if constexpr (NOUT == 3) row_loss3(y, (int)tgt, inv_b, lr_, g);
+    else row_loss(job.loss, y[0], tgt, inv_b, lr_, g[0]);
+    if (!valid) {
+      lr_ = 0.f;
+#pragma unroll
+      for (int c = 0; c < NOUT; ++c) g[c] = 0.f;
+    }
     loss_acc += lr_;
-    gsh[r] = g;
-    // delta_L = g * w_h * [h_L > 0]
 #pragma unroll
-    for (int o = 0; o < W; ++o) Dl[r * WP + o] = h[o] > 0.f ? g * wh[o] : 0.f;
+    for (int c = 0; c < NOUT; ++c) gsh[c * kTile + r] = g[c];
+    // delta_L = (sum_c g_c W_h[c]) * act'(a_L)
+#pragma unroll
+    for (int o = 0; o < W; ++o) {
+      float d = g[0] * wh[o];
+#pragma unroll
+      for (int c = 1; c < NOUT; ++c) d = fmaf(g[c], wh[c * W + o], d);
+      Dl[r * WP + o] = act_back(act, om, a[o], d);
+    }
     __syncthreads();
     // ---- head gradients
     {
       const float* HL = Hl + (size_t)(L - 1) * kTile * WP;
-      float* gwh = gpart + (P - W - 1);
+      float* gwh = gpart + (P - (int64_t)NOUT * (W + 1));
       if (r < W) {
-        float acc = 0.f;
-        for (int rr = 0; rr < kTile; ++rr) acc = fmaf(gsh[rr], HL[rr * WP + r], acc);
-        gwh[r] += acc;
+        for (int c = 0; c < NOUT; ++c) {
+          float acc = 0.f;
+          for (int rr = 0; rr < kTile; ++rr) acc = fmaf(gsh[c * kTile + rr], act_f(act, om, HL[rr * WP + r]), acc);
+          gwh[c * W + r] += acc;
+        }
       } else if (r == W) {
-        float acc = 0.f;
-        for (int rr = 0; rr < kTile; ++rr) acc += gsh[rr];
-        gwh[W] += acc;
+        for (int c = 0; c < NOUT; ++c) {
+          float acc = 0.f;
+          for (int rr = 0; rr < kTile; ++rr) acc += gsh[c * kTile + rr];
+          gwh[NOUT * W + c] += acc;
+        }
       }
     }
     // ---- hidden layers, top down
@@ -280,8 +342,8 @@ __global__ void __launch_bounds__(kTile, 1) train_fwd_bwd_kernel(NetView net, Tr
       const int K = l == 0 ? NIN : W;
       const float* Hin = l == 0 ? H0 : Hl + (size_t)(l - 1) * kTile * WP;
       const int hs = l == 0 ? KP : WP;
-      if (l == 0) accum_dW<NIN, W>(Dl, WP, Hin, hs, gpart + woff);
-      else accum_dW<W, W>(Dl, WP, Hin, hs, gpart + woff);
+      if (l == 0) accum_dW<NIN, W>(Dl, WP, Hin, hs, gpart + woff, -1, om);
+      else accum_dW<W, W>(Dl, WP, Hin, hs, gpart + woff, act, om);
       if (r < W) {
         float acc = 0.f;
         for (int rr = 0; rr < kTile; ++rr) acc += Dl[rr * WP + r];
@@ -289,7 +351,7 @@ __global__ void __launch_bounds__(kTile, 1) train_fwd_bwd_kernel(NetView net, Tr
       }
       __syncthreads();
       if (l > 0) {
-        // delta_l = (W_l^T delta_{l+1}) * [h_l > 0], own row only
+        // delta_l = (W_l^T delta_{l+1}) * act'(a_l), own row only
         float d[W];
 #pragma unroll
         for (int o = 0; o < W; ++o) d[o] = Dl[r * WP + o];
@@ -300,7 +362,7 @@ __global__ void __launch_bounds__(kTile, 1) train_fwd_bwd_kernel(NetView net, Tr
           float acc = 0.f;
 #pragma unroll
           for (int o = 0; o < W; ++o) acc = fmaf(__ldg(Wl + o * W + i), d[o], acc);
-          Dl[r * WP + i] = Hr[i] > 0.f ? acc : 0.f;
+          Dl[r * WP + i] = act_back(act, om, Hr[i], acc);
         }
         __syncthreads();
       }
@@ -313,9 +375,9 @@ __global__ void __launch_bounds__(kTile, 1) train_fwd_bwd_kernel(NetView net, Tr
   if ((r & 31) == 0) red[r >> 5] = v;
   __syncthreads();
   if (r == 0) {
-    float s = 0.f;
-    for (int w = 0; w < kTile / 32; ++w) s += red[w];
-    gpart[P] = s;
+    float sum = 0.f;
+    for (int w = 0; w < kTile / 32; ++w) sum += red[w];
+    gpart[P] = sum;
   }
 }
 

@@ -4,7 +4,8 @@ import re
 
 from paper_2208_04448_b300 import _native as N
 
-HDR = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "nvdb.h")
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HDR = os.path.join(ROOT, "include", "nvdb.h")
 
 
 def _declared():
@@ -24,10 +25,34 @@ def test_library_exports_every_declared_symbol():
 
 
 def test_struct_layouts():
+    """The ctypes structs agree field by field with the C compiler's layout of include/nvdb.h."""
     import ctypes as C
-    assert C.sizeof(N.TrainOpts) == 112 and N.TrainOpts.subdomain.offset == 96 and N.TrainOpts.sampling.offset == 108
-    assert C.sizeof(N.Info) == 72 and N.Info.n_active.offset == 32 and N.Info.n_experts.offset == 64
-    assert C.sizeof(N.BuildOpts) == 8
+    import shutil
+    import subprocess
+    import tempfile
+    structs = {"nvdb_train_opts": N.TrainOpts, "nvdb_info": N.Info, "nvdb_build_opts": N.BuildOpts,
+               "nvdb_camera": N.Camera}
+    assert C.sizeof(N.TrainOpts) == 128 and C.sizeof(N.Info) == 80 and C.sizeof(N.BuildOpts) == 16
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        return
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "nvdb.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            lines.append(f'  printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines += ["  return 0;", "}"]
+    with tempfile.TemporaryDirectory() as d:
+        src, exe = os.path.join(d, "l.c"), os.path.join(d, "l")
+        with open(src, "w") as fh:
+            fh.write("\n".join(lines))
+        subprocess.run([gcc, "-I", os.path.join(ROOT, "include"), src, "-o", exe], check=True)
+        out = subprocess.run([exe], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l}
+    for cname, py in structs.items():
+        assert got[(cname, "size")] == C.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert got[(cname, f)] == getattr(py, f).offset, (cname, f)
 
 
 def test_gradient_arguments_rejected_before_any_launch():

@@ -1,0 +1,185 @@
+"""Active tiles, the ternary level-1 classifier, the tile value regressor and the sin
+activation on the GPU against the FP64 oracle (Sections 3.1, 3.3.1, 3.5; the activation
+appendix).
+
+Tile pruning bit-exact (flags, masks, values); initial networks bit-exact; network outputs at
+1e-5 of the head scale (FP32) and the tensor-core bar (tile regressor); the first Adam step
+of every network on the same samples; the ternary decode restores the topology exactly with
+every tile voxel carrying its regressed value; queries answer tile corners from the tiles;
+blob round trip; sin models at FP32, and their tensor-core evaluation refused.
+"""
+import numpy as np
+import pytest
+import torch
+
+import paper_2208_04448_b300 as nv
+from fixtures import tiled_fog, workload
+from gpu_helpers import tc_bar
+from oracle import blob, codec, vdb
+from oracle import nets as N
+
+pytestmark = pytest.mark.gpu
+
+SEED, SIGMA = 9, 1.0
+SHAPE = dict(width=[32, 32, 32], layers=[2, 2, 2])
+
+
+def _grid(tol=0.0, big=False):
+    ijk, val = tiled_fog(96, 40, 40) if big else tiled_fog()
+    ref = vdb.build(ijk, val, tol)
+    g = nv.build(torch.from_numpy(ijk.astype(np.int32)).cuda(), torch.from_numpy(val).cuda(), 1, 0.0,
+                 prune_tiles=True, tile_tolerance=tol)
+    return ijk, val, ref, g
+
+
+@pytest.mark.parametrize("tol", [0.0, 0.01])
+def test_tile_pruning_bit_exact(tol):
+    ijk, val, ref, g = _grid(tol, big=True)
+    assert g.info()["n_tiles"] == int(ref["leaf_tile"].sum()) > 0
+    t = g.tiles()
+    assert np.array_equal(t["leaf_tile"], ref["leaf_tile"])
+    assert np.array_equal(t["l1_tile_mask"], ref["l1_tile_mask"])
+    r = g.read()
+    assert np.array_equal(r["ijk"], ref["ijk"]) and np.array_equal(r["val"], ref["val"])
+    g0 = nv.build(torch.from_numpy(ijk.astype(np.int32)).cuda(), torch.from_numpy(val).cuda(), 1, 0.0)
+    assert g0.info()["n_tiles"] == 0 and not g0.tiles()["leaf_tile"].any()
+
+
+def _opts(**kw):
+    return codec.default_opts(seed=SEED, sigma=SIGMA, **SHAPE, **kw)
+
+
+def test_ternary_initial_networks():
+    ijk, val, ref, g = _grid()
+    m = nv.compress(g, seed=SEED, ffm_sigma=SIGMA, steps=0, patch_precs=1, **SHAPE)
+    om = codec.init_model(ref, 1, 0.0, _opts())
+    got = blob.read(m.export())
+    assert got["ternary"] and got["n_tiles"] == om["n_tiles"] == 18 and len(got["nets"]) == 4
+    assert np.array_equal(got["q"][0], om["q"][0]) and np.array_equal(got["q"][1], om["q"][1])
+    for a, b in zip(got["nets"], om["nets"]):
+        assert np.shape(a["wh"]) == np.shape(b["wh"])
+        assert np.array_equal(N.flatten(a), N.flatten(b).astype(np.float32).astype(np.float64))
+
+
+def _scale(net, z):
+    _, (hs, _) = N.forward(net, z)
+    wh = np.atleast_2d(net["wh"])
+    return (np.abs(hs[-1][:, None, :] * wh[None]).sum(-1) + np.abs(np.atleast_1d(net["bh"]))[None]).max(1)
+
+
+@pytest.mark.parametrize("act", [N.ACT_RELU, N.ACT_SIN])
+def test_ternary_networks_match_oracle(act):
+    ijk, val, ref, g = _grid()
+    kw = dict(activation=act, omega=1.5) if act else {}
+    m = nv.compress(g, seed=SEED, ffm_sigma=SIGMA, steps=30, batch=1024, patch_precs=1, **SHAPE, **kw)
+    om = blob.read(m.export())
+    r = np.random.default_rng(2)
+    pts = (ijk[r.integers(0, len(ijk), 3000)]).astype(np.int32)
+    for net in range(4):
+        want = codec.evaluate(om, net, pts)
+        z = N.encode(codec.level_coords(om, net, pts), codec.level_q(om, net))
+        sc = _scale(om["nets"][net], z)
+        got = nv.mlp_eval(m, net, torch.from_numpy(pts).cuda(), nv.FP32).cpu().numpy()
+        err = np.abs(got - want) / np.maximum(sc, 1e-30)[:, None] if got.ndim == 2 else np.abs(got - want) / sc
+        assert err.max() <= 1e-5, (net, err.max())
+    if act == N.ACT_RELU:   # the tile regressor on the tensor cores
+        want = codec.evaluate(om, 3, pts)
+        sc = _scale(om["nets"][3], N.encode(codec.level_coords(om, 3, pts), codec.level_q(om, 3)))
+        for prec in (nv.FP16, nv.BF16X3):
+            got = nv.mlp_eval(m, 3, torch.from_numpy(pts).cuda(), prec).cpu().numpy()
+            assert (np.abs(got - want) / np.maximum(sc, 1.0)).max() <= tc_bar(prec)
+        with pytest.raises(nv.NvdbError) as e:
+            nv.mlp_eval(m, 0, torch.from_numpy(pts).cuda(), nv.FP16)
+        assert e.value.status == nv.ERR_UNSUPPORTED
+    else:
+        with pytest.raises(nv.NvdbError) as e:
+            nv.mlp_eval(m, 2, torch.from_numpy(pts).cuda(), nv.FP16)
+        assert e.value.status == nv.ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("act", [N.ACT_RELU, N.ACT_SIN])
+def test_first_adam_step_of_every_network(act):
+    ijk, val, ref, g = _grid()
+    kw = dict(activation=act, omega=1.5) if act else {}
+    m = nv.compress(g, seed=SEED, ffm_sigma=SIGMA, steps=1, batch=2048, lr=1e-3, patch_precs=1, **SHAPE, **kw)
+    opts = _opts(steps=1, batch=2048, lr=1e-3, act=act, omega=1.5 if act else 1.0)
+    om = codec.init_model(ref, 1, 0.0, opts)
+    theta0 = [N.flatten(n) for n in om["nets"]]
+    got = blob.read(m.export())
+    for net in range(4):
+        ls = codec.train_net(ref, om, net, opts)
+        assert abs(m.losses(net)[0] - ls[0]) <= 1e-5 * max(1.0, abs(ls[0])), (net, m.losses(net)[0], ls[0])
+        dw_ref = N.flatten(om["nets"][net]) - theta0[net]
+        dw_got = N.flatten(got["nets"][net]) - theta0[net]
+        big = np.abs(dw_ref) > 0.999e-3
+        assert big.sum() > 0
+        assert np.abs(dw_got[big] - dw_ref[big]).max() <= 2e-6, net
+
+
+@pytest.fixture(scope="module")
+def trained():
+    ijk, val, ref, g = _grid(big=True)
+    m = nv.compress(g, seed=SEED, ffm_sigma=SIGMA, steps=60, batch=4096, patch_precs=0b11011, **SHAPE)
+    return ijk, val, ref, g, m, blob.read(m.export())
+
+
+@pytest.mark.parametrize("prec", [nv.FP32, nv.FP16, nv.BF16X3, nv.BF16])
+def test_ternary_decode(trained, prec):
+    ijk, val, ref, g, m, om = trained
+    dijk, dval, cnt = nv.decompress(m, prec)
+    dijk, dval = dijk.cpu().numpy(), dval.cpu().numpy()
+    assert cnt == [ref["n"]] and np.array_equal(dijk, ref["ijk"])           # topology exact, tiles expanded
+    first, tiles = ref["leaf_first"], np.nonzero(ref["leaf_tile"])[0]
+    in_tile = np.zeros(ref["n"], bool)
+    for lf in tiles:
+        in_tile[first[lf]:first[lf] + 512] = True
+    want_t = codec.evaluate(om, 3, ref["leaf_origin"][tiles])
+    for t, lf in enumerate(tiles):
+        v = dval[first[lf]:first[lf] + 512]
+        assert np.all(v == v[0])
+    got_t = dval[first[tiles]]
+    want_v = codec.evaluate(om, 2, dijk[~in_tile])
+    if prec == nv.FP32:
+        assert np.abs(got_t - want_t).max() <= 1e-5 * max(1.0, np.abs(want_t).max())
+        assert np.abs(dval[~in_tile] - want_v).max() <= 1e-4
+    else:
+        assert np.abs(got_t - want_t).max() <= tc_bar(prec) * 2
+        assert np.abs(dval[~in_tile] - want_v).max() <= tc_bar(prec) * 2
+    # the oracle decodes the exported blob to the same topology
+    if prec == nv.FP32:
+        oijk, oval = codec.decompress(om, 0)
+        assert np.array_equal(oijk, dijk)
+        assert np.abs(oval - dval).max() <= 1e-4
+
+
+def test_ternary_blob_roundtrip_and_query(trained):
+    ijk, val, ref, g, m, om = trained
+    m2 = nv.model_import(m.export())
+    assert m2.export() == m.export()
+    a, b = nv.decompress(m, nv.FP16), nv.decompress(m2, nv.FP16)
+    assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
+    r = np.random.default_rng(5)
+    pts = (ref["ijk"][r.integers(0, ref["n"], 4000)] + r.uniform(-0.5, 1.0, (4000, 3))).astype(np.float32)
+    out, act = nv.query(m, torch.from_numpy(pts).cuda(), nv.FP32, active=True)
+    tile_keys = np.sort(vdb.canonical_key(ref["leaf_origin"][ref["leaf_tile"]]) >> 9)
+    want, bits = codec.query(om, pts, np.sort(vdb.canonical_key(ref["ijk"])), tile_keys)
+    assert np.array_equal(act.cpu().numpy(), bits)
+    assert np.abs(out.cpu().numpy() - want).max() <= 1e-4
+
+
+def test_sin_model_decodes_at_fp32():
+    ijk, val, _ = workload("sphere32")
+    ref = vdb.build(ijk.numpy(), val.numpy())
+    g = nv.build(ijk.cuda().contiguous(), val.cuda().contiguous(), 0, 3.0)
+    m = nv.compress(g, seed=3, ffm_sigma=1.25, steps=40, batch=2048, patch_precs=1, activation=nv.ACT_SIN, omega=2.0,
+                    **SHAPE)
+    om = blob.read(m.export())
+    assert om["act"] == N.ACT_SIN and om["omega"] == 2.0
+    dijk, dval, _ = nv.decompress(m, nv.FP32)
+    assert np.array_equal(dijk.cpu().numpy(), ref["ijk"])
+    want = codec.evaluate(om, 2, ref["ijk"]) * 3.0
+    assert np.abs(dval.cpu().numpy() - want).max() <= 1e-4
+    for bad in (dict(patch_precs=0b11), dict(patch_precs=1, train_prec=nv.BF16)):
+        with pytest.raises(nv.NvdbError) as e:
+            nv.compress(g, seed=3, steps=1, activation=nv.ACT_SIN, omega=2.0, **SHAPE, **bad)
+        assert e.value.status == nv.ERR_UNSUPPORTED

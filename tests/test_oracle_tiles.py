@@ -10,22 +10,13 @@ that set a slot's class) restores the source topology and tiles for untrained we
 import numpy as np
 import pytest
 
+from fixtures import tiled_fog
 from oracle import blob, codec, rng, vdb
 from oracle import nets as N
 
 
 def _fog_with_tiles():
-    """A 32 x 24 x 24 fog block: x < 16 holds constant density 0.5 (18 tiles of 8^3), the rest
-    varies; plus a partial leaf (not full) and a full leaf within 0.01 of constant."""
-    a = [np.arange(32), np.arange(24), np.arange(24)]
-    g = np.stack(np.meshgrid(*a, indexing="ij"), -1).reshape(-1, 3)
-    v = np.where(g[:, 0] < 16, 0.5, 0.2 + 0.01 * g[:, 1] + 0.001 * g[:, 2])
-    near = (g[:, 0] >= 24) & (g[:, 1] < 8) & (g[:, 2] < 8)          # a full leaf spanning 0.0077
-    v = np.where(near, 0.3 + 0.001 * (g[:, 1] + g[:, 2]) / 2.0, v)
-    extra = np.array([[40, 0, 0], [41, 3, 2]])                       # a partial leaf
-    g = np.concatenate([g, extra])
-    v = np.concatenate([v, [0.5, 0.5]]).astype(np.float32)
-    return g.astype(np.int64), v
+    return tiled_fog()
 
 
 def test_tile_pruning_brute_force():
