@@ -129,8 +129,9 @@ typedef struct {
                            1 = every voxel of the leaves (blocked), 2 = every voxel of the domain's
                            bounding box (dense; log2 extent <= 10, no decomposition); inactive
                            voxels take the background as target */
-  int32_t activation;   /* hidden activation of every network: NVDB_ACT_RELU, or NVDB_ACT_SIN (sin(omega a);
-                           FP32 training and FP32 evaluation only, patch_precs = 1) */
+  int32_t activation;   /* hidden activation of every network: NVDB_ACT_RELU, or NVDB_ACT_SIN (sin(omega a):
+                           FP32 training; evaluation at FP32, FP16, BF16, BF16X3 but not FP8, so
+                           patch_precs must leave out FP8; with a decomposition FP32 only) */
   float omega;          /* sin frequency (the paper's 1.5 .. 3.0) */
   int32_t tile_width;   /* grids with active tiles: tile value regressor width (0 = width[0]) ... */
   int32_t tile_layers;  /* ... and hidden layers (0 = layers[0]); it trains at train_prec, while the

@@ -10,6 +10,9 @@ code:
   bias       added in FP32 after the sum (FP16: it enters the sum as the pair
              fp16(b) + fp16(b - fp16(b))); ReLU; the next layer's operand is rounded again;
   head       an FP32 dot product on the last hidden layer's ReLU output.
+  sin        networks with the sin activation (16-bit modes only) take h = f32(sin(f32(omega a)))
+             on the FP32 pre-activation a in place of the ReLU (the kernels use the MUFU sine,
+             whose error sits far inside the parity bar).
 
   FP16     every operand FP16.
   BF16     the encoding and the inputs of every hidden layer except the last carried as a
@@ -144,12 +147,19 @@ def forward(net: dict, z: np.ndarray, prec: int, q=None, log2_extent=None) -> np
                 h = np.maximum(f32(pre), 0.0)
         return h @ net["wh"] + net["bh"]
     exact = _bf16_exact(net)
+    sin = net.get("act", 0) == 1
+    if sin and prec == PREC_FP8:
+        raise ValueError("sin networks: 16-bit precisions only")
+
+    def act(a):
+        a = f32(a)
+        return f32(np.sin(f32(net["omega"] * a))) if sin else np.maximum(a, 0.0)
     h = z
     for l, (W, b) in enumerate(zip(net["W"], net["b"])):
         if prec == PREC_FP16:
             bh = f16(b)
             a = f16(h) @ f16(W).T + bh + f16(f32(f32(b) - bh))
-            h = np.maximum(f32(a), 0.0)
+            h = act(a)
             continue
         else:
             comp = prec == PREC_BF16X3 or l < L - 1
@@ -160,5 +170,5 @@ def forward(net: dict, z: np.ndarray, prec: int, q=None, log2_extent=None) -> np
                 a = a + hl @ wh.T
             if not exact:
                 a = a + hh @ wl.T
-        h = np.maximum(f32(f32(a) + b), 0.0)
+        h = act(f32(a) + b)
     return h @ net["wh"] + net["bh"]

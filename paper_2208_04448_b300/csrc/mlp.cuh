@@ -508,6 +508,20 @@ __device__ __forceinline__ void relu_pair(float a, float b, bool comp, uint32_t&
   }
 }
 
+// sin(omega a) networks (activation appendix): the pair converted without the ReLU.
+template <int MODE>
+__device__ __forceinline__ void sin_pair(float a, float b, bool comp, uint32_t& hi, uint32_t& lo) {
+  if (MODE == TC_FP16) {
+    hi = cvt_f16x2(a, b);
+    lo = 0u;
+  } else if (!comp) {
+    hi = cvt_bf16x2(a, b);
+    lo = 0u;
+  } else {
+    split_pair<MODE>(a, b, hi, lo);
+  }
+}
+
 template <int NW>
 __device__ __forceinline__ void tmem_st_cols(uint32_t taddr, const uint32_t* r) {
   static_assert(NW == 32 || NW == 16 || NW == 8 || NW == 4, "columns");
@@ -609,9 +623,11 @@ __device__ __forceinline__ void tc_stage(const NetView& net, int mode, const Lay
 // undecomposed kernel carries none of the expert passes.  STAGE: lattice tiles take their
 // node / leaf origin from shared memory, filled by bulk copies two tiles ahead, instead of
 // a load of their own (the decode-plan autotuner measures both).
-template <int NIN, int W, int MODE, bool MOE = false, bool STAGE = false>
+template <int NIN, int W, int MODE, bool MOE = false, bool STAGE = false, bool SIN = false>
 __global__ void __launch_bounds__(kTile, 4) mlp_tc_kernel(const __grid_constant__ EvalBatch b) {
   static_assert(W == 32 || W == 64, "width");
+  static_assert(!SIN || (MODE != TC_FP8 && !MOE), "sin networks: 16-bit modes, no decomposition");
+  const float om = SIN ? b.it[0].net.omega : 0.f;   // one activation per batch (same shapes)
   static_assert(NIN == 32 || NIN == 64, "encoding size");
   using C = TcCfg<NIN, W, MODE>;
   constexpr int M = C::M;
@@ -885,6 +901,10 @@ __global__ void __launch_bounds__(kTile, 4) mlp_tc_kernel(const __grid_constant_
           accu[2 * c + 1] = __float_as_uint(__uint_as_float(accu[2 * c + 1]) + bv.y);
         }
       }
+      if constexpr (SIN) {   // h = sin(omega a), applied before the conversions below
+#pragma unroll
+        for (int c = 0; c < W; ++c) accu[c] = __float_as_uint(__sinf(om * __uint_as_float(accu[c])));
+      }
       if (MODE == TC_FP8 && l < L - 1) {
         uint32_t q[W / 4];
 #pragma unroll
@@ -897,8 +917,10 @@ __global__ void __launch_bounds__(kTile, 4) mlp_tc_kernel(const __grid_constant_
         const bool comp = comp_in<MODE>(l + 1, L);
         uint32_t hi[W / 2], lo[W / 2];
 #pragma unroll
-        for (int p = 0; p < W / 2; ++p)
-          relu_pair<MODE>(__uint_as_float(accu[2 * p]), __uint_as_float(accu[2 * p + 1]), comp, hi[p], lo[p]);
+        for (int p = 0; p < W / 2; ++p) {
+          if constexpr (SIN) sin_pair<MODE>(__uint_as_float(accu[2 * p]), __uint_as_float(accu[2 * p + 1]), comp, hi[p], lo[p]);
+          else relu_pair<MODE>(__uint_as_float(accu[2 * p]), __uint_as_float(accu[2 * p + 1]), comp, hi[p], lo[p]);
+        }
         store_a_row<W>(tlane, hi, lo, comp);
         if (C::BIAS_MMA && NIN != W) store_bias_chunk<W>(tlane);   // equal widths: still in place
         tmem_st_wait();
@@ -914,10 +936,11 @@ __global__ void __launch_bounds__(kTile, 4) mlp_tc_kernel(const __grid_constant_
 #pragma unroll
           for (int c = h * (W / 8); c < (h + 1) * (W / 8); ++c) {
             const float4 wv = swh4[c];
+            const float lo_ = SIN ? -3.4e38f : 0.f;   // sin outputs pass unclipped
             acc[0] = ffma2(make_float2(wv.x, wv.y),
-                           make_float2(fmaxf(__uint_as_float(accu[4 * c]), 0.f), fmaxf(__uint_as_float(accu[4 * c + 1]), 0.f)), acc[0]);
+                           make_float2(fmaxf(__uint_as_float(accu[4 * c]), lo_), fmaxf(__uint_as_float(accu[4 * c + 1]), lo_)), acc[0]);
             acc[1] = ffma2(make_float2(wv.z, wv.w),
-                           make_float2(fmaxf(__uint_as_float(accu[4 * c + 2]), 0.f), fmaxf(__uint_as_float(accu[4 * c + 3]), 0.f)), acc[1]);
+                           make_float2(fmaxf(__uint_as_float(accu[4 * c + 2]), lo_), fmaxf(__uint_as_float(accu[4 * c + 3]), lo_)), acc[1]);
           }
           part[h] = (acc[0].x + acc[0].y) + (acc[1].x + acc[1].y);
         }

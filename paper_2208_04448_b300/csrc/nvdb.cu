@@ -552,14 +552,15 @@ bool bf16_exact_layers(const float* p, int64_t n) {
 
 nvdb_status pack_net(nvdb_model* m, int k, cudaStream_t s) {
   DevNet& d = m->net[k];
-  // the tensor-core tiles serve ReLU networks with one output (check_eval_prec)
-  if (m->act != 0 || d.n_out != 1) return NVDB_OK;
+  // the tensor-core tiles serve networks with one output (check_eval_prec)
+  if (d.n_out != 1) return NVDB_OK;
   KLAUNCH("pack_weights", s, pack_weights_kernel<<<64, 256, 0, s>>>(d.p32, d.wpk, d.n_in, d.width, d.layers));
   CU(cudaGetLastError());
   if (d.layers > 1) {
     KLAUNCH("pack_weights_t", s, pack_weights_t_kernel<<<16, 256, 0, s>>>(d.p32, d.wpk, d.n_in, d.width, d.layers));
     CU(cudaGetLastError());
   }
+  if (m->act != 0) return NVDB_OK;   // FP8 tiles and scales: ReLU networks only
   // FP8 activation scales: calibrate on seeded points of the network's domain, then pack
   if (!d.f8_amax) TRY(dalloc(&d.f8_amax, kMaxLayers));
   CU(cudaMemsetAsync(d.f8_amax, 0, kMaxLayers * 4, s));
@@ -591,11 +592,13 @@ nvdb_status check_model_shapes(const nvdb_model* m) {
   return NVDB_OK;
 }
 
-// The tensor-core kernels implement ReLU networks with one output; a model with the sin
-// activation evaluates at FP32 only, and the ternary classifier always evaluates at FP32.
+// The tensor-core kernels implement networks with one output; sin networks evaluate in the
+// 16-bit modes without a decomposition (FP8's scale folding assumes ReLU), and the ternary
+// classifier always evaluates at FP32.
 nvdb_status check_eval_prec(const nvdb_model* m, int k, nvdb_precision prec) {
   if (prec == NVDB_FP32) return NVDB_OK;
-  if (m->act != 0) return fail(NVDB_ERR_UNSUPPORTED, "sin activation: FP32 evaluation only");
+  if (m->act != 0 && (prec == NVDB_FP8_E4M3 || m->moe()))
+    return fail(NVDB_ERR_UNSUPPORTED, "sin activation: no FP8, no tensor-core decomposition");
   if (m->net[k].n_out != 1) return fail(NVDB_ERR_UNSUPPORTED, "the ternary level-1 classifier evaluates at FP32");
   return NVDB_OK;
 }
@@ -996,8 +999,8 @@ extern "C" nvdb_status nvdb_compress(const nvdb_grid* g, const nvdb_train_opts* 
   if (act != 0 && act != 1) return fail(NVDB_ERR_INVALID_ARG, "activation must be 0 (ReLU) or 1 (sin)");
   if (act == 1 && !(omega > 0.f)) return fail(NVDB_ERR_INVALID_ARG, "sin activation: omega must be > 0");
   if (act == 1 && o->train_prec != NVDB_FP32) return fail(NVDB_ERR_UNSUPPORTED, "sin activation: FP32 training only");
-  if (act == 1 && (o->patch_precs & ~(1u << NVDB_FP32)))
-    return fail(NVDB_ERR_UNSUPPORTED, "sin activation: FP32 patch sets only (patch_precs = 1)");
+  if (act == 1 && ((o->patch_precs & (1u << NVDB_FP8_E4M3)) || (sub && (o->patch_precs & ~(1u << NVDB_FP32)))))
+    return fail(NVDB_ERR_UNSUPPORTED, "sin activation: no FP8 patch set (and FP32 only with a decomposition)");
   *out = nullptr;
   cudaStream_t s = (cudaStream_t)stream;
   auto* m = new nvdb_model();
@@ -2373,7 +2376,8 @@ extern "C" nvdb_status nvdb_model_import(const void* buf, size_t bytes, nvdb_str
       if (!ph) return fail(NVDB_ERR_CORRUPT, "blob truncated (patch header)");
       PatchSet ps;
       ps.prec = ph[0];
-      if (!eval_prec_ok(ps.prec) || m->patch_set((nvdb_precision)ps.prec) || (m->act != 0 && ps.prec != NVDB_FP32))
+      if (!eval_prec_ok(ps.prec) || m->patch_set((nvdb_precision)ps.prec) ||
+          (m->act != 0 && (ps.prec == NVDB_FP8_E4M3 || (m->moe() && ps.prec != NVDB_FP32))))
         return fail(NVDB_ERR_CORRUPT, "patch set %d: bad or repeated precision %d", i, ps.prec);
       // both levels: offsets and indices straight from the blob to the device; the
       // offsets (monotone, from 0 to the patch count) and the index ranges are checked
