@@ -531,17 +531,18 @@ def main():
     rl = roofline(head_kern)
     dname = rl["kernel"]
 
-    # ---- compaction kernels against the measured HBM copy bandwidth: algorithmic bytes per
-    # launch (emit: 12 B written per voxel, 64 B words + 16 B origin + 8 B offset read per leaf;
-    # patch application over the leaf words: 64 B read and written, 4 B count per leaf)
-    comp_bytes = {"emit_voxels": 12 * n_active + 88 * n_leaf, "patch_count": 132 * n_leaf + 1028 * n_l1}
+    # ---- compaction against the measured HBM copy bandwidth: the level-0 single-pass kernel
+    # (patches, counts, look-back scan and the voxel coordinates in one launch); algorithmic
+    # bytes per launch: leaf words 64 B read and 64 B written, origin 16 B, patch offset 4 B and
+    # voxel offset 8 B per leaf, 2 B per patch, 12 B written per voxel
+    n0_patches = int(om["patches"][head_prec]["l0_off"][-1])
+    comp_bytes = {"patch_scan_l0": 12 * n_active + 156 * n_leaf + 2 * n0_patches}
     compaction = {}
     for kname, nbytes in comp_bytes.items():
         if kname in head_kern:
             nl, tms = head_kern[kname]
-            per_launch = nbytes if kname == "emit_voxels" else nbytes / 2   # patch_count runs once per level
-            gbs = per_launch / (tms / nl / 1e3) / 1e9
-            compaction[kname] = dict(bytes_per_launch=per_launch, avg_launch_us=1e3 * tms / nl, achieved_gbs=gbs,
+            gbs = nbytes / (tms / nl / 1e3) / 1e9
+            compaction[kname] = dict(bytes_per_launch=nbytes, avg_launch_us=1e3 * tms / nl, achieved_gbs=gbs,
                                      frac_of_hbm=gbs / peaks["hbm_gbs"])
     traffic = None
     tfile = os.path.join(ROOT, "profiles", "traffic.json")

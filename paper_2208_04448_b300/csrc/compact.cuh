@@ -389,30 +389,6 @@ struct PatchBatch {
   PatchItem it[kMaxBatchC];
 };
 
-// Level-1 node origins of all models, concatenated in model order, canonical within.
-__global__ void l2_emit_batch_kernel(const __grid_constant__ L2Batch b, const int64_t* off, int4* l1_origin,
-                                     int64_t cap, uint32_t* status) {
-  __shared__ int64_t sh[33];
-  const int64_t g = blockIdx.x;
-  const int m = find_item(b.it, b.n, g);
-  const int64_t local = g - b.it[m].start;
-  uint64_t w = b.it[m].mask[local * 512 + threadIdx.x];
-  int64_t tot;
-  int64_t pos = off[g] + block_excl_scan(__popcll(w), sh, tot);
-  const int4 o = b.it[m].origin[local];
-  bool over = false;
-  while (w) {
-    const int bit = __ffsll((long long)w) - 1;
-    w &= w - 1;
-    const int s = threadIdx.x * 64 + bit;
-    if (pos < cap)
-      l1_origin[pos] = make_int4(o.x + 128 * (s >> 10), o.y + 128 * ((s >> 5) & 31), o.z + 128 * (s & 31), 0);
-    else
-      over = true;
-    ++pos;
-  }
-  if (over) set_status(status, ST_CORRUPT);
-}
 
 }  // namespace nvdb
 
@@ -467,36 +443,60 @@ __device__ __forceinline__ int64_t lb_block_id(uint64_t* state, int64_t nblocks,
   return *sh;
 }
 
-// Level-2 child counts with their scan: one block (512 threads) per level-2 node of any model
-// of the batch, off[node] = level-1 nodes before it; the last block checks the total.
+// Level-2 child counts with their scan, then the level-1 node origins: one block (512
+// threads) per level-2 node of any model of the batch; off[node] = level-1 nodes before it
+// (kept for the random-access lookup); the last block checks the total.
 __global__ void l2_scan_batch_kernel(const __grid_constant__ L2Batch b, int64_t n_nodes, int64_t* off,
-                                     int64_t expect, uint64_t* state, uint32_t* status) {
+                                     int64_t expect, uint64_t* state, uint32_t* status, int4* l1_origin) {
   __shared__ int64_t sh[33];
   __shared__ int64_t sid, spre;
   const int64_t g = lb_block_id(state, n_nodes, &sid);
   const int m = find_item(b.it, b.n, g);
-  const int64_t c = __popcll(b.it[m].mask[(g - b.it[m].start) * 512 + threadIdx.x]);
+  const int64_t local = g - b.it[m].start;
+  uint64_t w = b.it[m].mask[local * 512 + threadIdx.x];
   int64_t tot;
-  block_excl_scan(c, sh, tot);
+  const int64_t ex = block_excl_scan(__popcll(w), sh, tot);
   if (threadIdx.x == 0) {
     spre = lb_prefix(state, g, tot, status);
     off[g] = spre;
     if (g == n_nodes - 1 && spre + tot != expect) set_status(status, ST_CORRUPT);
   }
+  __syncthreads();
+  int64_t pos = spre + ex;
+  const int4 o = b.it[m].origin[local];
+  bool over = false;
+  while (w) {
+    const int bit = __ffsll((long long)w) - 1;
+    w &= w - 1;
+    const int sl = threadIdx.x * 64 + bit;
+    if (pos < expect)
+      l1_origin[pos] = make_int4(o.x + 128 * (sl >> 10), o.y + 128 * ((sl >> 5) & 31), o.z + 128 * (sl & 31), 0);
+    else
+      over = true;
+    ++pos;
+  }
+  if (over) set_status(status, ST_CORRUPT);
 }
 
 // Patch application (XOR, Section 3.3.2) and set-bit counts of the items of a level with
 // their scan: 32 items per block of 8 warps, four items per warp; off[item] = set bits
 // before it; the last block checks the total.  Items flagged as active tiles (tiles[g].w > 0)
-// become all ones.
+// become all ones.  Once the block's offsets are known, EMIT writes its items' children in
+// canonical order: kEmitLeaves the leaf origins of level-1 nodes (wpi 128), kEmitVoxels the
+// voxel coordinates of leaves (wpi 16, each lane writing ranks lane, lane + 32, ...).
 constexpr int kPatchScanItems = 32;
+enum : int { kEmitNone = 0, kEmitLeaves = 1, kEmitVoxels = 2 };
 
+template <int EMIT = kEmitNone>
 __global__ void __launch_bounds__(256) patch_scan_batch_kernel(uint32_t* words, int wpi, int64_t n_items,
                                                               const __grid_constant__ PatchBatch b, int64_t* off,
                                                               int64_t expect, uint64_t* state, uint32_t* status,
-                                                              const int4* tiles = nullptr) {
-  __shared__ uint32_t sw[8][128];
+                                                              const int4* tiles = nullptr,
+                                                              const int4* origin = nullptr, void* out = nullptr) {
+  __shared__ uint32_t sw[kPatchScanItems][128];
   __shared__ uint32_t scnt[kPatchScanItems];
+  __shared__ int64_t soff[kPatchScanItems];
+  __shared__ uint32_t wpre[8][17];
   __shared__ int64_t sid, spre;
   const int64_t nblocks = (n_items + kPatchScanItems - 1) / kPatchScanItems;
   const int64_t bid = lb_block_id(state, nblocks, &sid);
@@ -510,17 +510,17 @@ __global__ void __launch_bounds__(256) patch_scan_batch_kernel(uint32_t* words, 
       const int64_t local = g - b.it[m].start;
       uint32_t* w = words + g * wpi;
       const bool full = tiles && tiles[g].w > 0;   // an active tile: every voxel, no patches
-      for (int i = lane; i < wpi; i += 32) sw[wib][i] = full ? ~0u : w[i];
+      for (int i = lane; i < wpi; i += 32) sw[li][i] = full ? ~0u : w[i];
       __syncwarp();
       const uint32_t* poff = b.it[m].off;
       if (poff && !full)
         for (uint32_t p = poff[local] + lane; p < poff[local + 1]; p += 32) {
           const uint32_t bit = b.it[m].idx[p];
-          atomicXor(&sw[wib][bit >> 5], 1u << (bit & 31));
+          atomicXor(&sw[li][bit >> 5], 1u << (bit & 31));
         }
       __syncwarp();
       for (int i = lane; i < wpi; i += 32) {
-        const uint32_t v = sw[wib][i];
+        const uint32_t v = sw[li][i];
         w[i] = v;
         c += __popc(v);
       }
@@ -540,7 +540,64 @@ __global__ void __launch_bounds__(256) patch_scan_batch_kernel(uint32_t* words, 
     }
     __syncwarp();
     const int64_t g = bid * kPatchScanItems + lane;
+    soff[lane] = spre + ex;
     if (g < n_items) off[g] = spre + ex;
+  }
+  if constexpr (EMIT != kEmitNone) {
+    __syncthreads();
+    bool over = false;
+    for (int q = 0; q < kPatchScanItems / 8; ++q) {
+      const int li = wib * (kPatchScanItems / 8) + q;
+      const int64_t g = bid * kPatchScanItems + li;
+      if (g >= n_items) break;
+      const int4 o = origin[g];
+      if constexpr (EMIT == kEmitLeaves) {   // lane l owns words 4l .. 4l+3 (bits in slot order)
+        const uint32_t ww[4] = {sw[li][4 * lane], sw[li][4 * lane + 1], sw[li][4 * lane + 2], sw[li][4 * lane + 3]};
+        int64_t tot;
+        int64_t pos = soff[li] + warp_excl_scan(__popc(ww[0]) + __popc(ww[1]) + __popc(ww[2]) + __popc(ww[3]), lane, tot);
+        int4* leaf_origin = static_cast<int4*>(out);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          uint32_t bb = ww[k];
+          while (bb) {
+            const int bit = __ffs(bb) - 1;
+            bb &= bb - 1;
+            const int sl = (lane * 4 + k) * 32 + bit;
+            if (pos < expect)
+              leaf_origin[pos] = make_int4(o.x + 8 * (sl >> 8), o.y + 8 * ((sl >> 4) & 15), o.z + 8 * (sl & 15), 0);
+            else
+              over = true;
+            ++pos;
+          }
+        }
+      } else {   // voxels: lane r writes ranks r, r + 32, ... so consecutive lanes write consecutive outputs
+        const uint32_t bw = lane < 16 ? sw[li][lane] : 0u;
+        int64_t tot;
+        const int64_t ex = warp_excl_scan(__popc(bw), lane, tot);
+        if (lane < 16) wpre[wib][lane] = (uint32_t)ex;
+        if (lane == 0) wpre[wib][16] = (uint32_t)tot;
+        __syncwarp();
+        int32_t* ijk = static_cast<int32_t*>(out);
+        for (int r = lane; r < (int)tot; r += 32) {
+          int k = 0;
+#pragma unroll
+          for (int step = 8; step > 0; step >>= 1)
+            if (wpre[wib][k + step] <= (uint32_t)r) k += step;
+          const int bit = __fns(sw[li][k], 0, r - (int)wpre[wib][k] + 1);
+          const int v = k * 32 + bit;
+          const int64_t pos = soff[li] + r;
+          if (pos < expect) {
+            ijk[3 * pos] = o.x + (v >> 6);
+            ijk[3 * pos + 1] = o.y + ((v >> 3) & 7);
+            ijk[3 * pos + 2] = o.z + (v & 7);
+          } else {
+            over = true;
+          }
+        }
+        __syncwarp();
+      }
+    }
+    if (over) set_status(status, EMIT == kEmitVoxels ? ST_CAPACITY : ST_CORRUPT);
   }
 }
 

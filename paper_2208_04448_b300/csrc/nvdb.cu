@@ -1430,8 +1430,8 @@ nvdb_status decode_batch(nvdb_model* const* ms, int n, nvdb_precision prec, Deco
     lb.n = n;
     for (int m = 0; m < n; ++m)
       lb.it[m] = L2Item{reinterpret_cast<const uint64_t*>(ms[m]->l2_mask), ms[m]->l2_origin, s2[m]};
-    KLAUNCH("l2_scan", s, l2_scan_batch_kernel<<<(unsigned)N2, 512, 0, s>>>(lb, N2, d.l2_off, N1, d.lb2(), d.status));
-    KLAUNCH("l2_emit", s, l2_emit_batch_kernel<<<(unsigned)N2, 512, 0, s>>>(lb, d.l2_off, d.l1_origin, N1, d.status));
+    KLAUNCH("l2_scan", s, l2_scan_batch_kernel<<<(unsigned)N2, 512, 0, s>>>(lb, N2, d.l2_off, N1, d.lb2(), d.status,
+                                                                           d.l1_origin));
   }
   EvalBatch b;
   b.n = n;
@@ -1456,23 +1456,23 @@ nvdb_status decode_batch(nvdb_model* const* ms, int n, nvdb_precision prec, Deco
     KLAUNCH("tern_patch", s, tern_patch_batch_kernel<<<blocks_for(N1 * 32, 256), 256, 0, s>>>(d.l1_words, d.t1_words, N1, pb));
     PatchBatch none = pb;
     for (int m = 0; m < n; ++m) none.it[m].off = nullptr;
-    KLAUNCH("patch_scan", s, patch_scan_batch_kernel<<<(unsigned)DecodeScratch::blocks1(N1), 256, 0, s>>>(
-                                 d.l1_words, 128, N1, none, d.l1_off, NL, d.lb1(), d.status));
+    KLAUNCH("patch_scan_l1", s, patch_scan_batch_kernel<<<(unsigned)DecodeScratch::blocks1(N1), 256, 0, s>>>(
+                                    d.l1_words, 128, N1, none, d.l1_off, NL, d.lb1(), d.status));
     KLAUNCH("tile_scan", s, patch_scan_batch_kernel<<<(unsigned)DecodeScratch::blocks1(N1), 256, 0, s>>>(
                                 d.t1_words, 128, N1, none, d.t1_off, NT, d.lbt(), d.status));
-  } else if (N1) {
-    KLAUNCH("patch_scan", s, patch_scan_batch_kernel<<<(unsigned)DecodeScratch::blocks1(N1), 256, 0, s>>>(
-                                 d.l1_words, 128, N1, pb, d.l1_off, NL, d.lb1(), d.status));
-  } else if (NL) {
-    KLAUNCH("flag_corrupt", s, flag_corrupt_kernel<<<1, 1, 0, s>>>(d.status));   // leaves expected, no nodes
-  }
-  if (N1) {
+    // the leaf items with their tile ranks (which need the tile scan), then the tiles
     KLAUNCH("emit_leaves", s, emit_leaves_kernel<<<blocks_for(N1 * 32, 256), 256, 0, s>>>(
-                                  d.l1_words, d.l1_origin, N1, d.l1_off, d.leaf_origin, NL, d.status,
-                                  tern ? d.t1_words : nullptr, tern ? d.t1_off : nullptr));
-    if (tern && NT)
+                                  d.l1_words, d.l1_origin, N1, d.l1_off, d.leaf_origin, NL, d.status, d.t1_words,
+                                  d.t1_off));
+    if (NT)
       KLAUNCH("emit_tiles", s, emit_tile_coords_kernel<<<blocks_for(N1 * 32, 256), 256, 0, s>>>(
                                    d.t1_words, d.l1_origin, N1, d.t1_off, d.tile_ijk, NT, d.status));
+  } else if (N1) {   // patches, counts, scan and the leaf origins in one launch
+    KLAUNCH("patch_scan_l1", s, patch_scan_batch_kernel<kEmitLeaves><<<(unsigned)DecodeScratch::blocks1(N1), 256, 0, s>>>(
+                                 d.l1_words, 128, N1, pb, d.l1_off, NL, d.lb1(), d.status, nullptr, d.l1_origin,
+                                 d.leaf_origin));
+  } else if (NL) {
+    KLAUNCH("flag_corrupt", s, flag_corrupt_kernel<<<1, 1, 0, s>>>(d.status));   // leaves expected, no nodes
   }
   for (int m = 0; m < n; ++m) {
     EvalJob j{};
@@ -1488,18 +1488,18 @@ nvdb_status decode_batch(nvdb_model* const* ms, int n, nvdb_precision prec, Deco
     TRY(launch_batch(b, prec, s));
   }
   for (int m = 0; m < n; ++m) pb.it[m] = PatchItem{ps[m]->d_l0_off, ps[m]->d_l0_idx, sl[m]};
-  if (NL) {
-    KLAUNCH("patch_scan", s, patch_scan_batch_kernel<<<(unsigned)DecodeScratch::blocks1(NL), 256, 0, s>>>(
+  if (NL && out_ijk) {   // patches, counts, scan and the voxels in one launch
+    KLAUNCH("patch_scan_l0", s, patch_scan_batch_kernel<kEmitVoxels><<<(unsigned)DecodeScratch::blocks1(NL), 256, 0, s>>>(
+                                 d.leaf_words, 16, NL, pb, d.leaf_off, NA, d.lb0(), d.status,
+                                 tern ? d.leaf_origin : nullptr, d.leaf_origin, out_ijk));
+  } else if (NL) {
+    KLAUNCH("patch_scan_l0", s, patch_scan_batch_kernel<<<(unsigned)DecodeScratch::blocks1(NL), 256, 0, s>>>(
                                  d.leaf_words, 16, NL, pb, d.leaf_off, NA, d.lb0(), d.status,
                                  tern ? d.leaf_origin : nullptr));
   } else if (NA) {
     KLAUNCH("flag_corrupt", s, flag_corrupt_kernel<<<1, 1, 0, s>>>(d.status));   // voxels expected, no leaves
   }
   if (out_ijk) {
-    if (NL)
-      KLAUNCH("emit_voxels", s, emit_voxels_rank_kernel<<<blocks_for(NL, 8), 256, 0, s>>>(d.leaf_words, d.leaf_origin,
-                                                                                        NL, d.leaf_off, out_ijk, NA,
-                                                                                        d.status));
     if (sink && NA) {
       CU(cudaEventRecord(sink->ev, s));
       CU(cudaStreamWaitEvent(sink->copy, sink->ev, 0));
