@@ -479,31 +479,32 @@ __global__ void l2_scan_batch_kernel(const __grid_constant__ L2Batch b, int64_t 
 }
 
 // Patch application (XOR, Section 3.3.2) and set-bit counts of the items of a level with
-// their scan: 32 items per block of 8 warps, four items per warp; off[item] = set bits
+// their scan: IPB items per block of 8 warps (IPB / 8 per warp); off[item] = set bits
 // before it; the last block checks the total.  Items flagged as active tiles (tiles[g].w > 0)
 // become all ones.  Once the block's offsets are known, EMIT writes its items' children in
 // canonical order: kEmitLeaves the leaf origins of level-1 nodes (wpi 128), kEmitVoxels the
 // voxel coordinates of leaves (wpi 16, each lane writing ranks lane, lane + 32, ...).
-constexpr int kPatchScanItems = 32;
+constexpr int kPatchScanItems = 8;   // items per block of the decode's scans (one per warp)
 enum : int { kEmitNone = 0, kEmitLeaves = 1, kEmitVoxels = 2 };
 
-template <int EMIT = kEmitNone>
+template <int EMIT = kEmitNone, int IPB = kPatchScanItems>
 __global__ void __launch_bounds__(256) patch_scan_batch_kernel(uint32_t* words, int wpi, int64_t n_items,
                                                               const __grid_constant__ PatchBatch b, int64_t* off,
                                                               int64_t expect, uint64_t* state, uint32_t* status,
                                                               const int4* tiles = nullptr,
                                                               const int4* origin = nullptr, void* out = nullptr) {
-  __shared__ uint32_t sw[kPatchScanItems][128];
-  __shared__ uint32_t scnt[kPatchScanItems];
-  __shared__ int64_t soff[kPatchScanItems];
+  static_assert(IPB % 8 == 0 && IPB <= 32, "items per block");
+  __shared__ uint32_t sw[IPB][128];
+  __shared__ uint32_t scnt[IPB];
+  __shared__ int64_t soff[IPB];
   __shared__ uint32_t wpre[8][17];
   __shared__ int64_t sid, spre;
-  const int64_t nblocks = (n_items + kPatchScanItems - 1) / kPatchScanItems;
+  const int64_t nblocks = (n_items + IPB - 1) / IPB;
   const int64_t bid = lb_block_id(state, nblocks, &sid);
   const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int q = 0; q < kPatchScanItems / 8; ++q) {
-    const int li = wib * (kPatchScanItems / 8) + q;
-    const int64_t g = bid * kPatchScanItems + li;
+  for (int q = 0; q < IPB / 8; ++q) {
+    const int li = wib * (IPB / 8) + q;
+    const int64_t g = bid * IPB + li;
     uint32_t c = 0;
     if (g < n_items) {
       const int m = find_item(b.it, b.n, g);
@@ -533,22 +534,22 @@ __global__ void __launch_bounds__(256) patch_scan_batch_kernel(uint32_t* words, 
   __syncthreads();
   if (wib == 0) {
     int64_t tot;
-    const int64_t ex = warp_excl_scan(scnt[lane], lane, tot);
+    const int64_t ex = warp_excl_scan(lane < IPB ? scnt[lane] : 0u, lane, tot);
     if (lane == 0) {
       spre = lb_prefix(state, bid, tot, status);
       if (bid == nblocks - 1 && spre + tot != expect) set_status(status, ST_CORRUPT);
     }
     __syncwarp();
-    const int64_t g = bid * kPatchScanItems + lane;
-    soff[lane] = spre + ex;
-    if (g < n_items) off[g] = spre + ex;
+    const int64_t g = bid * IPB + lane;
+    if (lane < IPB) soff[lane] = spre + ex;
+    if (lane < IPB && g < n_items) off[g] = spre + ex;
   }
   if constexpr (EMIT != kEmitNone) {
     __syncthreads();
     bool over = false;
-    for (int q = 0; q < kPatchScanItems / 8; ++q) {
-      const int li = wib * (kPatchScanItems / 8) + q;
-      const int64_t g = bid * kPatchScanItems + li;
+    for (int q = 0; q < IPB / 8; ++q) {
+      const int li = wib * (IPB / 8) + q;
+      const int64_t g = bid * IPB + li;
       if (g >= n_items) break;
       const int4 o = origin[g];
       if constexpr (EMIT == kEmitLeaves) {   // lane l owns words 4l .. 4l+3 (bits in slot order)

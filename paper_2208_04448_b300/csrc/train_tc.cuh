@@ -131,12 +131,17 @@ __global__ void __launch_bounds__(kTile, 1) train_tc_kernel(NetView net, TrainJo
   float loss_acc = 0.f, gwh_acc = 0.f;   // thread c < W: dLoss/dw_h[c]; thread W: dLoss/db_h
   int ntile_done = 0;
   const int64_t ntiles = (job.batch + kTile - 1) / kTile;
+  // sample of row r of tile t (coordinates and target); the next tile's is fetched while the
+  // current tile's backward MMAs run, so its gathers overlap them
+  int ncx = 0, ncy = 0, ncz = 0;
+  float ntgt = 0.f;
+  if ((int64_t)blockIdx.x < ntiles && (int64_t)blockIdx.x * kTile + r < job.batch)
+    train_sample(job, (int64_t)blockIdx.x * kTile + r, ncx, ncy, ncz, ntgt);
   for (int64_t t = blockIdx.x; t < ntiles && !failed; t += gridDim.x, ++ntile_done) {
     const int64_t s = t * kTile + r;
     const bool valid = s < job.batch;
-    int cx = 0, cy = 0, cz = 0;
-    float tgt = 0.f;
-    if (valid) train_sample(job, s, cx, cy, cz, tgt);
+    const int cx = ncx, cy = ncy, cz = ncz;
+    const float tgt = ntgt;
     // ---- encoding: A operand of layer 0 (TMEM) and H_0 (shared memory), features
     // interleaved (cos_0, sin_0, cos_1, ...) as in the packed first-layer tile
     {
@@ -249,10 +254,14 @@ __global__ void __launch_bounds__(kTile, 1) train_tc_kernel(NetView net, TrainJo
         }
         mma_commit(bar);
       }
-      if (l == L - 1 && tid <= W) {   // fixed-order column sums of g h_L (and g), while the MMAs run
-        float acc = 0.f;
-        for (int rr = 0; rr < kTile; ++rr) acc += sgh[rr * (W + 1) + tid];
-        gwh_acc += acc;
+      if (l == L - 1) {
+        if (tid <= W) {   // fixed-order column sums of g h_L (and g), while the MMAs run
+          float acc = 0.f;
+          for (int rr = 0; rr < kTile; ++rr) acc += sgh[rr * (W + 1) + tid];
+          gwh_acc += acc;
+        }
+        const int64_t sn = (t + gridDim.x) * kTile + r;   // the next tile's sample
+        if (t + gridDim.x < ntiles && sn < job.batch) train_sample(job, sn, ncx, ncy, ncz, ntgt);
       }
       const bool ok = mbar_wait_bounded(bar, phase);
       phase ^= 1u;
