@@ -484,7 +484,10 @@ __global__ void l2_scan_batch_kernel(const __grid_constant__ L2Batch b, int64_t 
 // become all ones.  Once the block's offsets are known, EMIT writes its items' children in
 // canonical order: kEmitLeaves the leaf origins of level-1 nodes (wpi 128), kEmitVoxels the
 // voxel coordinates of leaves (wpi 16, each lane writing ranks lane, lane + 32, ...).
-constexpr int kPatchScanItems = 8;   // items per block of the decode's scans (one per warp)
+// Items per block of the decode's scans: level 1 has few items with much work each (one per
+// warp); level 0 many small ones, where larger blocks keep the look-back chain short.
+constexpr int kScanItemsL1 = 8, kScanItemsL0 = 32;
+constexpr int kPatchScanItems = kScanItemsL1;
 enum : int { kEmitNone = 0, kEmitLeaves = 1, kEmitVoxels = 2 };
 
 template <int EMIT = kEmitNone, int IPB = kPatchScanItems>

@@ -197,14 +197,15 @@ struct DecodeScratch {
   int64_t* t1_off = nullptr;
   int32_t* tile_ijk = nullptr;
   float* tval = nullptr;
-  static int64_t blocks1(int64_t n) { return (n + kPatchScanItems - 1) / kPatchScanItems; }
+  static int64_t blocks1(int64_t n) { return (n + kScanItemsL1 - 1) / kScanItemsL1; }
+  static int64_t blocks0(int64_t n) { return (n + kScanItemsL0 - 1) / kScanItemsL0; }
   static int64_t lb_words(int64_t n2, int64_t n1, int64_t nl) {
-    return 1 + (n2 + 1) + 2 * (blocks1(n1) + 1) + (blocks1(nl) + 1);
+    return 1 + (n2 + 1) + 2 * (blocks1(n1) + 1) + (blocks0(nl) + 1);
   }
   uint64_t* lb2() { return lb + 1; }
   uint64_t* lb1() { return lb + 2 + cap2; }
   uint64_t* lb0() { return lb + 3 + cap2 + blocks1(cap1); }
-  uint64_t* lbt() { return lb + 4 + cap2 + blocks1(cap1) + blocks1(capl); }
+  uint64_t* lbt() { return lb + 4 + cap2 + blocks1(cap1) + blocks0(capl); }
   nvdb_status reserve(int64_t n2, int64_t n1, int64_t nl) {
     if (lb && n2 <= cap2 && n1 <= cap1 && nl <= capl) return NVDB_OK;
     release();
@@ -1489,11 +1490,11 @@ nvdb_status decode_batch(nvdb_model* const* ms, int n, nvdb_precision prec, Deco
   }
   for (int m = 0; m < n; ++m) pb.it[m] = PatchItem{ps[m]->d_l0_off, ps[m]->d_l0_idx, sl[m]};
   if (NL && out_ijk) {   // patches, counts, scan and the voxels in one launch
-    KLAUNCH("patch_scan_l0", s, patch_scan_batch_kernel<kEmitVoxels><<<(unsigned)DecodeScratch::blocks1(NL), 256, 0, s>>>(
+    KLAUNCH("patch_scan_l0", s, patch_scan_batch_kernel<kEmitVoxels, kScanItemsL0><<<(unsigned)DecodeScratch::blocks0(NL), 256, 0, s>>>(
                                  d.leaf_words, 16, NL, pb, d.leaf_off, NA, d.lb0(), d.status,
                                  tern ? d.leaf_origin : nullptr, d.leaf_origin, out_ijk));
   } else if (NL) {
-    KLAUNCH("patch_scan_l0", s, patch_scan_batch_kernel<<<(unsigned)DecodeScratch::blocks1(NL), 256, 0, s>>>(
+    KLAUNCH("patch_scan_l0", s, patch_scan_batch_kernel<kEmitNone, kScanItemsL0><<<(unsigned)DecodeScratch::blocks0(NL), 256, 0, s>>>(
                                  d.leaf_words, 16, NL, pb, d.leaf_off, NA, d.lb0(), d.status,
                                  tern ? d.leaf_origin : nullptr));
   } else if (NA) {
