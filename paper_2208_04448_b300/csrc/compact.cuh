@@ -1,8 +1,10 @@
 // Stream compaction of classifier bitmasks into canonical lists (Section 3.5:
 // child masks -> leaf list, active masks -> voxel list) and the patch
-// correction of Section 3.3.2.  Deterministic: a three-phase exclusive scan
-// (block scans, one scan of the block sums, add-back) and warp-level popcount
-// prefixes; the output order is the canonical bit order.
+// correction of Section 3.3.2.  The decode uses single-pass scans with a decoupled
+// look-back that apply the patches, count, scan and emit in one launch per level (end of
+// this file); the build, the patch construction and the queries use a deterministic
+// three-phase exclusive scan (block scans, one scan of the block sums, add-back).  Output
+// order is the canonical bit order.
 #pragma once
 #include "common.cuh"
 
@@ -99,94 +101,6 @@ __global__ void check_patches_kernel(const uint32_t* off, int64_t items, const u
   if (bad) set_status(status, ST_CORRUPT);
 }
 
-// Apply the patch list of every item (XOR, Section 3.3.2) to its candidate
-// words and count the resulting set bits.  One thread per item.
-__global__ void patch_count_kernel(uint32_t* words, int wpi, int64_t n_items, const uint32_t* poff,
-                                   const uint16_t* pidx, uint32_t* counts) {
-  const int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (it >= n_items) return;
-  uint32_t* w = words + it * wpi;
-  if (poff) {
-    for (uint32_t p = poff[it]; p < poff[it + 1]; ++p) {
-      const uint32_t b = pidx[p];
-      w[b >> 5] ^= 1u << (b & 31);
-    }
-  }
-  uint32_t c = 0;
-  for (int i = 0; i < wpi; ++i) c += __popc(w[i]);
-  counts[it] = c;
-}
-
-// Warp-per-item variant of patch_count_kernel: the item's words are staged in
-// shared memory, the patches are applied with shared-memory atomicXor (a
-// candidate appears at most once per list, so the result does not depend on
-// the order), the words are written back and counted.  8 warps per block;
-// wpi <= 128.
-__global__ void __launch_bounds__(256) patch_count_warp_kernel(uint32_t* words, int wpi, int64_t n_items,
-                                                              const uint32_t* poff, const uint16_t* pidx,
-                                                              uint32_t* counts) {
-  __shared__ uint32_t sw[8][128];
-  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t it = (int64_t)blockIdx.x * 8 + wib;
-  if (it >= n_items) return;
-  uint32_t* w = words + it * wpi;
-  for (int i = lane; i < wpi; i += 32) sw[wib][i] = w[i];
-  __syncwarp();
-  if (poff) {
-    for (uint32_t p = poff[it] + lane; p < poff[it + 1]; p += 32) {
-      const uint32_t b = pidx[p];
-      atomicXor(&sw[wib][b >> 5], 1u << (b & 31));
-    }
-  }
-  __syncwarp();
-  uint32_t c = 0;
-  for (int i = lane; i < wpi; i += 32) {
-    const uint32_t v = sw[wib][i];
-    w[i] = v;
-    c += __popc(v);
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-  if (lane == 0) counts[it] = c;
-}
-
-// Rank-parallel variant of emit_voxels_kernel: lane l writes the voxels of rank
-// l, l+32, ... of its leaf, so consecutive lanes write consecutive outputs.
-__global__ void __launch_bounds__(256) emit_voxels_rank_kernel(const uint32_t* words, const int4* leaf_origin,
-                                                              int64_t n_leaf, const int64_t* off, int32_t* ijk,
-                                                              int64_t cap, uint32_t* status) {
-  __shared__ uint32_t sw[8][16], spre[8][17];
-  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t leaf = (int64_t)blockIdx.x * 8 + wib;
-  if (leaf >= n_leaf) return;
-  const uint32_t b = lane < 16 ? words[leaf * 16 + lane] : 0u;
-  int64_t tot;
-  const int64_t ex = warp_excl_scan(__popc(b), lane, tot);
-  if (lane < 16) { sw[wib][lane] = b; spre[wib][lane] = (uint32_t)ex; }
-  if (lane == 0) spre[wib][16] = (uint32_t)tot;
-  __syncwarp();
-  const int4 o = leaf_origin[leaf];
-  const int64_t base = off[leaf];
-  bool over = false;
-  for (int r = lane; r < (int)tot; r += 32) {
-    int k = 0;
-#pragma unroll
-    for (int step = 8; step > 0; step >>= 1)
-      if (spre[wib][k + step] <= (uint32_t)r) k += step;
-    const int bit = __fns(sw[wib][k], 0, r - (int)spre[wib][k] + 1);
-    const int v = k * 32 + bit;
-    const int64_t pos = base + r;
-    if (pos < cap) {
-      ijk[3 * pos] = o.x + (v >> 6);
-      ijk[3 * pos + 1] = o.y + ((v >> 3) & 7);
-      ijk[3 * pos + 2] = o.z + (v & 7);
-    } else {
-      over = true;
-    }
-  }
-  if (over) set_status(status, ST_CAPACITY);
-}
-
 // Level-1 child words -> leaf origins in canonical order.  One warp per node,
 // lane l owns words 4l..4l+3 (bits in slot order).  With tile words t (ternary level 1,
 // toff their exclusive scan per node), a slot that is an active tile gets w = its tile rank
@@ -227,68 +141,6 @@ __global__ void emit_leaves_kernel(const uint32_t* words, const int4* l1_origin,
       ++pos;
     }
     trank += __popc(tt[q]);
-  }
-  if (over) set_status(status, ST_CORRUPT);
-}
-
-// Leaf active words -> voxel coordinates in canonical order.  One warp per
-// leaf, lanes 0..15 own one word each.
-__global__ void emit_voxels_kernel(const uint32_t* words, const int4* leaf_origin, int64_t n_leaf,
-                                   const int64_t* off, int32_t* ijk, int64_t cap, uint32_t* status) {
-  const int64_t leaf = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (leaf >= n_leaf) return;
-  uint32_t b = lane < 16 ? words[leaf * 16 + lane] : 0u;
-  int64_t tot;
-  int64_t pos = off[leaf] + warp_excl_scan(__popc(b), lane, tot);
-  const int4 o = leaf_origin[leaf];
-  bool over = false;
-  while (b) {
-    const int bit = __ffs(b) - 1;
-    b &= b - 1;
-    const int v = lane * 32 + bit;
-    if (pos < cap) {
-      ijk[3 * pos] = o.x + (v >> 6);
-      ijk[3 * pos + 1] = o.y + ((v >> 3) & 7);
-      ijk[3 * pos + 2] = o.z + (v & 7);
-    } else {
-      over = true;
-    }
-    ++pos;
-  }
-  if (over) set_status(status, ST_CAPACITY);
-}
-
-// Level-1 node origins from the level-2 child masks (Section 3.5: the
-// coordinates of level-1 nodes follow from the level-2 child masks).
-// counts pass: one block (512 threads) per level-2 node.
-__global__ void l2_count_kernel(const uint64_t* l2_mask, int64_t n_l2, uint32_t* counts) {
-  __shared__ int64_t sh[33];
-  const int64_t n = blockIdx.x;
-  const int64_t c = __popcll(l2_mask[n * 512 + threadIdx.x]);
-  int64_t tot;
-  block_excl_scan(c, sh, tot);
-  if (threadIdx.x == 0) counts[n] = (uint32_t)tot;
-}
-
-__global__ void l2_emit_kernel(const uint64_t* l2_mask, const int4* l2_origin, int64_t n_l2, const int64_t* off,
-                               int4* l1_origin, int64_t cap, uint32_t* status) {
-  __shared__ int64_t sh[33];
-  const int64_t n = blockIdx.x;
-  uint64_t w = l2_mask[n * 512 + threadIdx.x];
-  int64_t tot;
-  int64_t pos = off[n] + block_excl_scan(__popcll(w), sh, tot);
-  const int4 o = l2_origin[n];
-  bool over = false;
-  while (w) {
-    const int bit = __ffsll((long long)w) - 1;
-    w &= w - 1;
-    const int s = threadIdx.x * 64 + bit;
-    if (pos < cap)
-      l1_origin[pos] = make_int4(o.x + 128 * (s >> 10), o.y + 128 * ((s >> 5) & 31), o.z + 128 * (s & 31), 0);
-    else
-      over = true;
-    ++pos;
   }
   if (over) set_status(status, ST_CORRUPT);
 }
