@@ -9,7 +9,8 @@ code:
   products   summed exactly (FP64 here, FP32 in tensor memory on the GPU);
   bias       added in FP32 after the sum (FP16: it enters the sum as the pair
              fp16(b) + fp16(b - fp16(b))); ReLU; the next layer's operand is rounded again;
-  head       an FP32 dot product on the last hidden layer's ReLU output.
+  head       an FP32 dot product on the last hidden layer's ReLU output (one per class for
+             the ternary level-1 classifier).
   sin        networks with the sin activation (16-bit modes only) take h = f32(sin(f32(omega a)))
              on the FP32 pre-activation a in place of the ReLU (the kernels use the MUFU sine,
              whose error sits far inside the parity bar).
@@ -146,7 +147,7 @@ def forward(net: dict, z: np.ndarray, prec: int, q=None, log2_extent=None) -> np
                 hq = e4m3(np.maximum(pre, 0.0))
             else:
                 h = np.maximum(f32(pre), 0.0)
-        return h @ net["wh"] + net["bh"]
+        return _head(net, h)
     exact = _bf16_exact(net)
     sin = net.get("act", 0) == 1
     if sin and prec == PREC_FP8:
@@ -172,4 +173,9 @@ def forward(net: dict, z: np.ndarray, prec: int, q=None, log2_extent=None) -> np
             if not exact:
                 a = a + hh @ wl.T
         h = act(f32(a) + b)
-    return h @ net["wh"] + net["bh"]
+    return _head(net, h)
+
+
+def _head(net: dict, h: np.ndarray) -> np.ndarray:
+    wh = np.asarray(net["wh"], dtype=np.float64)
+    return h @ (wh.T if wh.ndim == 2 else wh) + net["bh"]

@@ -8,11 +8,11 @@
 
 namespace nvdb {
 
-template <int NIN, int W, int MODE, bool MOE = false, bool STAGE = false, bool SIN = false>
+template <int NIN, int W, int MODE, bool MOE = false, bool STAGE = false, bool SIN = false, bool TERN = false>
 nvdb_status launch_tc(const EvalBatch& b, int64_t ntiles, const char* base, cudaStream_t s) {
-  if (!MOE && batch_moe(b)) return launch_tc<NIN, W, MODE, true, false>(b, ntiles, base, s);
+  if (!MOE && !TERN && batch_moe(b)) return launch_tc<NIN, W, MODE, true, false>(b, ntiles, base, s);
   const TcLayout<NIN, W, MODE> lay(b.it[0].net.layers, batch_wlo(b));
-  auto* kern = mlp_tc_kernel<NIN, W, MODE, MOE, STAGE, SIN>;
+  auto* kern = mlp_tc_kernel<NIN, W, MODE, MOE, STAGE, SIN, TERN>;
   TRY(set_smem_limit((const void*)kern, lay.total));
   // Residency from the kernel's own limits (the runtime's occupancy query reports 1 for
   // kernels that allocate tensor memory): registers, shared memory, and TMEM columns.
@@ -58,12 +58,17 @@ nvdb_status launch_tc_shape(const EvalBatch& b, int64_t ntiles, const char* base
   const int v = batch_moe(b) ? 0 : tc_variant();
   if (nv.act && (MODE == TC_FP8 || batch_moe(b)))
     return fail(NVDB_ERR_UNSUPPORTED, "sin activation: FP8 and decomposed models evaluate at FP32");
-#define NVDB_TC_SHAPE(A, B)                                                     \
-  if (nv.n_in == A && nv.width == B)                                            \
-    return nv.act ? launch_tc<A, B, MODE, false, false, MODE != TC_FP8>(b, ntiles, base, s) \
-         : v == 1 ? launch_tc2<A, B, MODE>(b, ntiles, base, s)                  \
-         : v == 2 ? launch_tc<A, B, MODE, false, true>(b, ntiles, base, s)      \
-                  : launch_tc<A, B, MODE>(b, ntiles, base, s);
+  // the ternary level-1 classifier (three logits) takes the TERN instantiation of variant 0
+#define NVDB_TC_SHAPE(A, B)                                                                       \
+  if (nv.n_in == A && nv.width == B) {                                                            \
+    if (nv.n_out == 3)                                                                            \
+      return nv.act ? launch_tc<A, B, MODE, false, false, MODE != TC_FP8, true>(b, ntiles, base, s) \
+                    : launch_tc<A, B, MODE, false, false, false, true>(b, ntiles, base, s);       \
+    return nv.act ? launch_tc<A, B, MODE, false, false, MODE != TC_FP8>(b, ntiles, base, s)      \
+         : v == 1 ? launch_tc2<A, B, MODE>(b, ntiles, base, s)                                    \
+         : v == 2 ? launch_tc<A, B, MODE, false, true>(b, ntiles, base, s)                        \
+                  : launch_tc<A, B, MODE>(b, ntiles, base, s);                                    \
+  }
   NVDB_TC_SHAPE(32, 32)
   NVDB_TC_SHAPE(32, 64)
   NVDB_TC_SHAPE(64, 32)

@@ -453,7 +453,7 @@ struct TcLayout {
     p_off = t_off + (size_t)C::M * 64 * (C::ENC16 ? 4 : 8);   // T table [M][64]: half2 / float2
     b_off = p_off + (size_t)2 * 2 * C::M * 8;                // P tables, two buffers of [2][M] x 8 B
     wh_off = b_off + (size_t)L * W * 4;                      // FP32 biases [L][W]
-    q_off = wh_off + (size_t)(W + 4) * 4;
+    q_off = wh_off + (size_t)(3 * W + 4) * 4;                // head: W_h [<= 3][W], b_h [<= 3]
     org_off = (q_off + (size_t)C::M * 12 + 15) & ~(size_t)15;   // ring of four staged origins (int4)
     bar_off = org_off + 64;
     obar_off = bar_off + 8;
@@ -598,8 +598,10 @@ __device__ __forceinline__ void tc_stage(const NetView& net, int mode, const Lay
     const int64_t bo = layer_offset(NIN, W, l) + (int64_t)W * (l == 0 ? NIN : W);
     for (int o = tid; o < W; o += NT) sb[l * W + o] = __ldg(net.p32 + bo + o);
   }
-  const int64_t hoff = net_param_count(NIN, W, L) - W - 1;
-  for (int o = tid; o <= W; o += NT) swh[o] = __ldg(net.p32 + hoff + o);
+  // head W_h [n_out][W] then b_h [n_out]: the biases at swh[n_out W + c]
+  const int nout = net.n_out;
+  const int64_t hoff = net_param_count(NIN, W, L, nout) - (int64_t)nout * (W + 1);
+  for (int o = tid; o < nout * (W + 1); o += NT) swh[o] = __ldg(net.p32 + hoff + o);
   for (int i = tid; i < 3 * M; i += NT) sq[i] = __ldg(net.q + i);
   __syncthreads();
   if (mode == MODE_L0 && table) {
@@ -623,10 +625,11 @@ __device__ __forceinline__ void tc_stage(const NetView& net, int mode, const Lay
 // undecomposed kernel carries none of the expert passes.  STAGE: lattice tiles take their
 // node / leaf origin from shared memory, filled by bulk copies two tiles ahead, instead of
 // a load of their own (the decode-plan autotuner measures both).
-template <int NIN, int W, int MODE, bool MOE = false, bool STAGE = false, bool SIN = false>
+template <int NIN, int W, int MODE, bool MOE = false, bool STAGE = false, bool SIN = false, bool TERN = false>
 __global__ void __launch_bounds__(kTile, 4) mlp_tc_kernel(const __grid_constant__ EvalBatch b) {
   static_assert(W == 32 || W == 64, "width");
   static_assert(!SIN || (MODE != TC_FP8 && !MOE), "sin networks: 16-bit modes, no decomposition");
+  static_assert(!TERN || !MOE, "the ternary classifier: no decomposition");
   const float om = SIN ? b.it[0].net.omega : 0.f;   // one activation per batch (same shapes)
   static_assert(NIN == 32 || NIN == 64, "encoding size");
   using C = TcCfg<NIN, W, MODE>;
@@ -715,7 +718,7 @@ __global__ void __launch_bounds__(kTile, 4) mlp_tc_kernel(const __grid_constant_
       __syncthreads();
       tc_stage<NIN, W, MODE>(b.it[m].net, b.it[m].job.mode, lay, smem);
       __syncthreads();
-      bh = swh[W];
+      bh = swh[TERN ? 3 * W : W];
       wexact = b.it[m].net.wexact != 0;
       staged_p32 = b.it[m].net.p32;
     }
@@ -743,6 +746,7 @@ __global__ void __launch_bounds__(kTile, 4) mlp_tc_kernel(const __grid_constant_
     if (moe) valid = job_coord(job, t, tid, rx, ry, rz);
     const int dox = job.ox, doy = job.oy, doz = job.oz;
     float macc = 0.f, mgs = 0.f, mg = 0.f, y = 0.f;
+    float y3[3] = {0.f, 0.f, 0.f};   // the ternary classifier's logits
     for (int pass = 0, last = -1;; ++pass) {
     if (moe) {
       const int mine = moe_next(mv, shift, rx, ry, rz, last);
@@ -927,24 +931,29 @@ __global__ void __launch_bounds__(kTile, 4) mlp_tc_kernel(const __grid_constant_
       } else {
         // FP32 head, two products per instruction.  The summation order is that of
         // mlp_tc2_kernel (each half of the columns in two pair accumulators, then the
-        // halves added), so both variants give the same bits.
-        const float4* swh4 = reinterpret_cast<const float4*>(swh);
-        float part[2];
+        // halves added), so both variants give the same bits.  The ternary classifier
+        // takes one such dot product per class.
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          float2 acc[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+        for (int cls = 0; cls < (TERN ? 3 : 1); ++cls) {
+          const float4* swh4 = reinterpret_cast<const float4*>(swh + cls * W);
+          float part[2];
 #pragma unroll
-          for (int c = h * (W / 8); c < (h + 1) * (W / 8); ++c) {
-            const float4 wv = swh4[c];
-            const float lo_ = SIN ? -3.4e38f : 0.f;   // sin outputs pass unclipped
-            acc[0] = ffma2(make_float2(wv.x, wv.y),
-                           make_float2(fmaxf(__uint_as_float(accu[4 * c]), lo_), fmaxf(__uint_as_float(accu[4 * c + 1]), lo_)), acc[0]);
-            acc[1] = ffma2(make_float2(wv.z, wv.w),
-                           make_float2(fmaxf(__uint_as_float(accu[4 * c + 2]), lo_), fmaxf(__uint_as_float(accu[4 * c + 3]), lo_)), acc[1]);
+          for (int h = 0; h < 2; ++h) {
+            float2 acc[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+#pragma unroll
+            for (int c = h * (W / 8); c < (h + 1) * (W / 8); ++c) {
+              const float4 wv = swh4[c];
+              const float lo_ = SIN ? -3.4e38f : 0.f;   // sin outputs pass unclipped
+              acc[0] = ffma2(make_float2(wv.x, wv.y),
+                             make_float2(fmaxf(__uint_as_float(accu[4 * c]), lo_), fmaxf(__uint_as_float(accu[4 * c + 1]), lo_)), acc[0]);
+              acc[1] = ffma2(make_float2(wv.z, wv.w),
+                             make_float2(fmaxf(__uint_as_float(accu[4 * c + 2]), lo_), fmaxf(__uint_as_float(accu[4 * c + 3]), lo_)), acc[1]);
+            }
+            part[h] = (acc[0].x + acc[0].y) + (acc[1].x + acc[1].y);
           }
-          part[h] = (acc[0].x + acc[0].y) + (acc[1].x + acc[1].y);
+          if constexpr (TERN) y3[cls] = swh[3 * W + cls] + (part[0] + part[1]);
+          else y = bh + (part[0] + part[1]);
         }
-        y = bh + (part[0] + part[1]);
       }
       tc_fence_before();
       if (__syncthreads_or(!ok)) { failed = true; break; }   // all threads agree on a timeout
@@ -957,7 +966,8 @@ __global__ void __launch_bounds__(kTile, 4) mlp_tc_kernel(const __grid_constant_
     }   // expert passes
     if (failed) break;
     if (moe) y = macc / mgs;
-    job_output(job, t, tid, valid, y);
+    if constexpr (TERN) job_output3(job, t, tid, valid, y3);
+    else job_output(job, t, tid, valid, y);
     if (next_same) pbuf ^= 1;
     p_ready = next_same;
   }

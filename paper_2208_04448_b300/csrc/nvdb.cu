@@ -553,8 +553,6 @@ bool bf16_exact_layers(const float* p, int64_t n) {
 
 nvdb_status pack_net(nvdb_model* m, int k, cudaStream_t s) {
   DevNet& d = m->net[k];
-  // the tensor-core tiles serve networks with one output (check_eval_prec)
-  if (d.n_out != 1) return NVDB_OK;
   KLAUNCH("pack_weights", s, pack_weights_kernel<<<64, 256, 0, s>>>(d.p32, d.wpk, d.n_in, d.width, d.layers));
   CU(cudaGetLastError());
   if (d.layers > 1) {
@@ -593,14 +591,13 @@ nvdb_status check_model_shapes(const nvdb_model* m) {
   return NVDB_OK;
 }
 
-// The tensor-core kernels implement networks with one output; sin networks evaluate in the
-// 16-bit modes without a decomposition (FP8's scale folding assumes ReLU), and the ternary
-// classifier always evaluates at FP32.
+// Sin networks evaluate in the 16-bit modes without a decomposition (FP8's scale folding
+// assumes ReLU).
 nvdb_status check_eval_prec(const nvdb_model* m, int k, nvdb_precision prec) {
+  (void)k;
   if (prec == NVDB_FP32) return NVDB_OK;
   if (m->act != 0 && (prec == NVDB_FP8_E4M3 || m->moe()))
     return fail(NVDB_ERR_UNSUPPORTED, "sin activation: no FP8, no tensor-core decomposition");
-  if (m->net[k].n_out != 1) return fail(NVDB_ERR_UNSUPPORTED, "the ternary level-1 classifier evaluates at FP32");
   return NVDB_OK;
 }
 }  // namespace
@@ -926,8 +923,7 @@ nvdb_status make_patches(nvdb_model* m, const nvdb_grid* g, int prec, cudaStream
       const bool tern1 = m->ternary && lev == 0;
       if (tern1) TRY(dalloc(&twords, (size_t)items * wpi + 1));
       job.twords = twords;
-      // the ternary level-1 classifier decides at FP32 whatever the set's precision
-      TRY(launch_eval(m, lev == 0 ? 0 : 1, tern1 ? NVDB_FP32 : (nvdb_precision)prec, job, s));
+      TRY(launch_eval(m, lev == 0 ? 0 : 1, (nvdb_precision)prec, job, s));
       const uint32_t* truth = reinterpret_cast<const uint32_t*>(lev == 0 ? g->l1_mask : g->leaf_mask);
       if (m->ternary && lev == 1 && items)   // tiles are not classified: no level-0 patches
         KLAUNCH("tile_words_full", s, tile_words_full_kernel<<<blocks_for(items * 16, 256), 256, 0, s>>>(words, g->leaf_tile, items));
@@ -1448,7 +1444,7 @@ nvdb_status decode_batch(nvdb_model* const* ms, int n, nvdb_precision prec, Deco
   }
   {
     const Range range("decode: level-1 classification");
-    TRY(launch_batch(b, tern ? NVDB_FP32 : prec, s));   // the ternary classifier runs at FP32
+    TRY(launch_batch(b, prec, s));
   }
   PatchBatch pb;
   pb.n = n;

@@ -83,16 +83,23 @@ def test_ternary_networks_match_oracle(act):
         got = nv.mlp_eval(m, net, torch.from_numpy(pts).cuda(), nv.FP32).cpu().numpy()
         err = np.abs(got - want) / np.maximum(sc, 1e-30)[:, None] if got.ndim == 2 else np.abs(got - want) / sc
         assert err.max() <= 1e-5, (net, err.max())
-    if act == N.ACT_RELU:   # the tile regressor on the tensor cores
-        want = codec.evaluate(om, 3, pts)
-        sc = _scale(om["nets"][3], N.encode(codec.level_coords(om, 3, pts), codec.level_q(om, 3)))
-        for prec in (nv.FP16, nv.BF16X3):
-            got = nv.mlp_eval(m, 3, torch.from_numpy(pts).cuda(), prec).cpu().numpy()
-            assert (np.abs(got - want) / np.maximum(sc, 1.0)).max() <= tc_bar(prec)
-        with pytest.raises(nv.NvdbError) as e:
-            nv.mlp_eval(m, 0, torch.from_numpy(pts).cuda(), nv.FP16)
-        assert e.value.status == nv.ERR_UNSUPPORTED
-    else:   # sin networks: 16-bit tensor-core modes, not FP8
+    # the ternary classifier (three logits) and the tile regressor on the tensor cores: against
+    # the FP64 network at the bar, and against the arithmetic each precision states
+    from oracle import quant
+    precs = (nv.FP16, nv.BF16X3, nv.BF16) + ((nv.FP8_E4M3,) if act == N.ACT_RELU else ())
+    for net in (0, 3):
+        want = codec.evaluate(om, net, pts)
+        z = N.encode(codec.level_coords(om, net, pts), codec.level_q(om, net))
+        sc = np.maximum(_scale(om["nets"][net], z), 1.0)
+        sc = sc[:, None] if net == 0 else sc
+        for prec in precs:
+            got = nv.mlp_eval(m, net, torch.from_numpy(pts).cuda(), prec).cpu().numpy()
+            spec = quant.forward(om["nets"][net], z, prec, codec.level_q(om, net), om["log2_extent"] - 3)
+            dev = np.abs(got - spec) / sc
+            assert np.quantile(dev, 0.99) <= 2e-4 and dev.max() <= 0.2, (net, prec, dev.max())
+            if prec != nv.FP8_E4M3:
+                assert (np.abs(got - want) / sc).max() <= tc_bar(prec), (net, prec)
+    if act == N.ACT_SIN:   # sin networks: 16-bit tensor-core modes, not FP8
         with pytest.raises(nv.NvdbError) as e:
             nv.mlp_eval(m, 2, torch.from_numpy(pts).cuda(), nv.FP8_E4M3)
         assert e.value.status == nv.ERR_UNSUPPORTED
