@@ -135,7 +135,8 @@ typedef struct {
   float omega;          /* sin frequency (the paper's 1.5 .. 3.0) */
   int32_t tile_width;   /* grids with active tiles: tile value regressor width (0 = width[0]) ... */
   int32_t tile_layers;  /* ... and hidden layers (0 = layers[0]); it trains at train_prec, while the
-                           ternary level-1 classifier always trains and evaluates at FP32 */
+                           ternary level-1 classifier always trains at FP32 (it evaluates at every
+                           precision) */
 } nvdb_train_opts;
 
 typedef struct {
