@@ -490,10 +490,16 @@ static __global__ void __launch_bounds__(32 * kRedGroups) adam_reduce_kernel(
   // one slot per lane (coalesced over the partials), mapped to its parameter
   const int64_t pe = (int64_t)blockIdx.x * 32 + lane;
   float gq = 0.f;
-  if (pe <= P) {
+  if (pe <= P) {   // 16 loads in flight, then their sum in CTA order
     const int c0 = (int)((int64_t)q * nparts / kRedGroups), c1 = (int)((int64_t)(q + 1) * nparts / kRedGroups);
-#pragma unroll 4
-    for (int c = c0; c < c1; ++c) gq += __ldcs(partial + (int64_t)c * (P + 1) + pe);
+    for (int cb = c0; cb < c1; cb += 16) {
+      float v[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) v[j] = cb + j < c1 ? __ldcs(partial + (int64_t)(cb + j) * (P + 1) + pe) : 0.f;
+#pragma unroll
+      for (int j = 0; j < 16; ++j)
+        if (cb + j < c1) gq += v[j];
+    }
   }
   red[q][lane] = gq;
   __syncthreads();
