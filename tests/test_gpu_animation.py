@@ -6,7 +6,8 @@ import torch
 
 import paper_2208_04448_b300 as nv
 from fixtures import water_frame
-from oracle import blob
+from gpu_helpers import oracle_forward_scale, rel_err, tc_bar
+from oracle import blob, codec
 from oracle import nets as N
 
 pytestmark = pytest.mark.gpu
@@ -58,4 +59,11 @@ def test_warm_sequence_early_stop_and_batched_decode(frames):
         for f, n in enumerate(counts):
             ref = grids_ijk[f] if f else nv.build(*frames[0], 0, 3.0).read()["ijk"]
             assert np.array_equal(ijk[off:off + n].cpu().numpy(), ref)   # every frame's topology, exact
+            # and every frame's values, warm-started ones included, against the oracle on the
+            # frame's own (warm-trained) weights
+            om = blob.read(models[f].export())
+            idx = np.random.default_rng(f).choice(n, 2048, replace=False)
+            pv = val[off:off + n][torch.from_numpy(idx).cuda()].cpu().numpy().astype(np.float64) / 3.0
+            want, scale = oracle_forward_scale(om, codec.REG, ref[idx])
+            assert np.abs(pv - want).max() <= tc_bar(prec), (f, prec)
             off += n

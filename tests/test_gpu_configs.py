@@ -11,6 +11,7 @@ import paper_2208_04448_b300 as nv
 from fixtures import query_points, workload
 from gpu_helpers import oracle_forward_scale, rel_err, tc_bar
 from oracle import blob, codec, vdb
+from oracle import nets as N
 
 pytestmark = pytest.mark.gpu
 
@@ -104,3 +105,26 @@ def test_fog512_full_decode(fog512, prec):
     # learning error against the generated density (reported by the bench; here: a gain)
     truth = ref["val"][idx].astype(np.float64)
     assert np.sqrt(np.mean((pv - truth) ** 2)) < 0.8 * np.std(ref["val"])
+
+
+def test_fog512_gradient_parity(fog512):
+    """Config 3's networks (regressor 4x64, classifiers 3x32) at fog size: the FP32 gradient of a
+    65,536-sample batch of the trained model's own active voxels (MSE on the density) and of
+    level-0 candidates (BCE), against the FP64 oracle on the same weights and samples."""
+    g, m = fog512
+    ref = g.read()
+    om = blob.read(m.export())
+    r = np.random.default_rng(12)
+    n = 65536
+    for net, loss in ((codec.REG, nv.LOSS_MSE), (codec.L0CLS, nv.LOSS_BCE)):
+        idx = r.integers(0, len(ref["ijk"]), n)
+        pts = ref["ijk"][idx].astype(np.int32)
+        tgt = ref["val"][idx].astype(np.float32) if net == codec.REG else (r.random(n) > 0.5).astype(np.float32)
+        z = N.encode(codec.level_coords(om, net, pts), codec.level_q(om, net))
+        y, cache = N.forward(om["nets"][net], z)
+        lref, gy = N.loss_and_grad(y, tgt.astype(np.float64), loss)
+        gref = N.flatten(N.backward(om["nets"][net], cache, gy))
+        got, lgot = nv.mlp_grad(m, net, torch.from_numpy(pts).cuda(), torch.from_numpy(tgt).cuda(), loss, nv.FP32)
+        got = got.cpu().numpy()
+        assert np.abs(got - gref).max() <= 1e-4 * np.abs(gref).max(), net
+        assert abs(lgot - lref) <= 1e-5 * max(1.0, abs(lref)), net
