@@ -460,7 +460,8 @@ int train_grid(int64_t batch) { return (int)std::min<int64_t>((batch + kTile - 1
 
 bool train_prec_ok(int prec) { return prec == NVDB_FP32 || prec == NVDB_BF16; }
 
-nvdb_status launch_train(const nvdb_model* m, int k, int prec, TrainJob job, int grid, cudaStream_t s) {
+nvdb_status launch_train(const nvdb_model* m, int k, int prec, TrainJob job, int grid, cudaStream_t s,
+                         const FusedAdam* fa = nullptr) {
   const NetView nv = net_view(m, k);
   const int e = k / 3;   // an expert normalises over its subdomain (Section 3.4)
   job.ox = m->origin[0] + (m->moe() ? m->exp_origin_host[3 * e] : 0);
@@ -470,7 +471,7 @@ nvdb_status launch_train(const nvdb_model* m, int k, int prec, TrainJob job, int
   if (prec == NVDB_BF16) {
     if (nv.n_out != 1 || nv.act != 0)
       return fail(NVDB_ERR_UNSUPPORTED, "BF16 training: ReLU networks with one output only");
-    return launch_train_tc(nv, job, grid, s);
+    return launch_train_tc(nv, job, grid, s, fa);
   } else if (prec == NVDB_FP32) {
     if (nv.n_in == 32 && nv.width == 32) return launch_train_t<32, 32>(nv, job, grid, s);
     if (nv.n_in == 32 && nv.width == 64) return launch_train_t<32, 64>(nv, job, grid, s);
@@ -1133,6 +1134,7 @@ extern "C" nvdb_status nvdb_compress(const nvdb_grid* g, const nvdb_train_opts* 
       cudaEvent_t ev = nullptr;
       float* d_loss = nullptr;
       int* d_step = nullptr;
+      uint32_t* d_sync = nullptr;   // grid barrier of the fused Adam step
       TrainJob job{};
       AdamSched sc{};
       cudaGraphExec_t exec = nullptr;
@@ -1163,6 +1165,11 @@ extern "C" nvdb_status nvdb_compress(const nvdb_grid* g, const nvdb_train_opts* 
       }
       if ((st = dalloc(&r.d_loss, (size_t)std::max(1, o->steps))) != NVDB_OK) break;
       if ((st = dalloc(&r.d_step, 2)) != NVDB_OK) break;
+      if ((st = dalloc(&r.d_sync, 2)) != NVDB_OK) break;
+      if (cudaMemsetAsync(r.d_sync, 0, 8, r.ts) != cudaSuccess) {
+        st = fail(NVDB_ERR_CUDA, "barrier words");
+        break;
+      }
       r.job = grid_train_job(g, k, o);
       r.job.stream = 3 * ex + k;
       if (m->moe() || (tern && k > 0)) {
@@ -1189,6 +1196,17 @@ extern "C" nvdb_status nvdb_compress(const nvdb_grid* g, const nvdb_train_opts* 
     auto one_step = [&](int k) -> nvdb_status {
       NetRun& r = nr[k];
       DevNet& d = m->net[3 * ex + k];
+      if (tprec(k) == NVDB_BF16 && fused_adam_enabled()) {   // gradient and Adam in one launch
+        FusedAdam fa{};
+        fa.sync = r.d_sync;
+        fa.params = d.p32;
+        fa.m = d.m;
+        fa.v = d.v;
+        fa.rp = adam_aux(d, NVDB_BF16, true);
+        fa.sc = r.sc;
+        fa.loss_scale = 1.f / (float)o->batch;
+        return launch_train(m, 3 * ex + k, tprec(k), r.job, grid, r.ts, &fa);
+      }
       TRY(launch_train(m, 3 * ex + k, tprec(k), r.job, grid, r.ts));
       KLAUNCH("adam_reduce", r.ts, adam_reduce_kernel<<<blocks_for(d.P + 1, 32), 32 * kRedGroups, 0, r.ts>>>(
                                        r.job.partial, grid, d.P, d.p32, d.m, d.v, 0, 0.f, nullptr, nullptr,
@@ -1267,6 +1285,7 @@ extern "C" nvdb_status nvdb_compress(const nvdb_grid* g, const nvdb_train_opts* 
       if (r.ev) cudaEventDestroy(r.ev);
       dfree(r.d_step);
       dfree(r.d_loss);
+      dfree(r.d_sync);
     }
     }   // experts
     TRY(st);

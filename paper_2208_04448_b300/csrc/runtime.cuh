@@ -215,7 +215,23 @@ nvdb_status launch_calib_amax(const NetView& nv, int log2_extent, uint64_t seed,
 // Radix sort of (key, index) pairs by the 63 key bits (sort.cu).
 nvdb_status sort_keys(const uint64_t* k_in, uint64_t* k_out, const uint32_t* i_in, uint32_t* i_out, int n,
                       cudaStream_t s);
-// One BF16 tensor-core training launch (train_tc.cu).
-nvdb_status launch_train_tc(const NetView& nv, const TrainJob& job, int grid, cudaStream_t s);
+// One BF16 tensor-core training launch (train_tc.cu); with `fa`, the Adam update fused into the
+// same (cooperative) launch.
+nvdb_status launch_train_tc(const NetView& nv, const TrainJob& job, int grid, cudaStream_t s,
+                            const FusedAdam* fa = nullptr);
+
+// The training step's Adam update fused into its launch (NVDB_FUSED_ADAM=0 keeps the separate
+// reduction kernel); needs cooperative launches on the device.
+inline bool fused_adam_enabled() {
+  static const bool on = [] {
+    const char* e = std::getenv("NVDB_FUSED_ADAM");
+    int coop = 0, dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess)
+      return false;
+    return coop != 0 && !(e && e[0] == '0');
+  }();
+  return on;
+}
 
 }  // namespace nvdb

@@ -476,37 +476,35 @@ struct AdamSched {
   int first_step;
 };
 
-static __global__ void __launch_bounds__(32 * kRedGroups) adam_reduce_kernel(
-    const float* partial, int nparts, int64_t P, float* params, float* m, float* v, int step, float lr_t,
-    float* grad_out, float* loss_out, float loss_scale, AdamAux rp, AdamSched sc) {
-  __shared__ float red[kRedGroups][33];
-  if (sc.step_dev) {
-    step = sc.step_dev[1];
-    lr_t = sc.interval > 0 ? sc.lr * powf(sc.decay, (float)((step - 1) / sc.interval)) : sc.lr;
-    loss_out = sc.loss_base + (step - sc.first_step);
-    if (blockIdx.x == 0 && threadIdx.x == 0) sc.step_dev[0] = step + 1;
-  }
-  const int lane = threadIdx.x & 31, q = threadIdx.x >> 5;
-  // one slot per lane (coalesced over the partials), mapped to its parameter
-  const int64_t pe = (int64_t)blockIdx.x * 32 + lane;
+// Learning rate of a step: lr * decay^floor((step - 1) / interval), constant if interval = 0.
+__device__ __forceinline__ float sched_lr(const AdamSched& sc, int step) {
+  return sc.interval > 0 ? sc.lr * powf(sc.decay, (float)((step - 1) / sc.interval)) : sc.lr;
+}
+
+// Sum of partial slot pe over the CTAs of group q, [q n / G, (q+1) n / G), in CTA order, with
+// 16 loads in flight.  L2 loads (CG): the partials of other CTAs of the same launch.
+template <bool CG>
+__device__ __forceinline__ float group_sum(const float* partial, int nparts, int64_t P, int64_t pe, int q) {
+  const int c0 = (int)((int64_t)q * nparts / kRedGroups), c1 = (int)((int64_t)(q + 1) * nparts / kRedGroups);
   float gq = 0.f;
-  if (pe <= P) {   // 16 loads in flight, then their sum in CTA order
-    const int c0 = (int)((int64_t)q * nparts / kRedGroups), c1 = (int)((int64_t)(q + 1) * nparts / kRedGroups);
-    for (int cb = c0; cb < c1; cb += 16) {
-      float v[16];
+  for (int cb = c0; cb < c1; cb += 16) {
+    float v[16];
 #pragma unroll
-      for (int j = 0; j < 16; ++j) v[j] = cb + j < c1 ? __ldcs(partial + (int64_t)(cb + j) * (P + 1) + pe) : 0.f;
-#pragma unroll
-      for (int j = 0; j < 16; ++j)
-        if (cb + j < c1) gq += v[j];
+    for (int j = 0; j < 16; ++j) {
+      const float* a = partial + (int64_t)(cb + j) * (P + 1) + pe;
+      v[j] = cb + j < c1 ? (CG ? __ldcg(a) : __ldcs(a)) : 0.f;
     }
-  }
-  red[q][lane] = gq;
-  __syncthreads();
-  if (q != 0 || pe > P) return;
-  float g = 0.f;
 #pragma unroll
-  for (int k = 0; k < kRedGroups; ++k) g += red[k][lane];
+    for (int j = 0; j < 16; ++j)
+      if (cb + j < c1) gq += v[j];
+  }
+  return gq;
+}
+
+// Adam on the parameter held in partial slot pe, gradient g (or the loss, slot P).
+__device__ __forceinline__ void adam_apply(int64_t pe, float g, int64_t P, float* params, float* m, float* v, int step,
+                                           float lr_t, float* grad_out, float* loss_out, float loss_scale,
+                                           const AdamAux& rp) {
   const int64_t e = rp.tc_partials ? partial_param(pe, rp.nin, rp.W, rp.L) : pe;
   if (e == P) {
     if (loss_out) *loss_out = g * loss_scale;
@@ -531,6 +529,92 @@ static __global__ void __launch_bounds__(32 * kRedGroups) adam_reduce_kernel(
       if (to >= 0) *reinterpret_cast<__nv_bfloat16*>(rp.wpk + to) = b;
     }
   }
+}
+
+static __global__ void __launch_bounds__(32 * kRedGroups) adam_reduce_kernel(
+    const float* partial, int nparts, int64_t P, float* params, float* m, float* v, int step, float lr_t,
+    float* grad_out, float* loss_out, float loss_scale, AdamAux rp, AdamSched sc) {
+  __shared__ float red[kRedGroups][33];
+  if (sc.step_dev) {
+    step = sc.step_dev[1];
+    lr_t = sched_lr(sc, step);
+    loss_out = sc.loss_base + (step - sc.first_step);
+    if (blockIdx.x == 0 && threadIdx.x == 0) sc.step_dev[0] = step + 1;
+  }
+  const int lane = threadIdx.x & 31, q = threadIdx.x >> 5;
+  // one slot per lane (coalesced over the partials), mapped to its parameter
+  const int64_t pe = (int64_t)blockIdx.x * 32 + lane;
+  red[q][lane] = pe <= P ? group_sum<false>(partial, nparts, P, pe, q) : 0.f;
+  __syncthreads();
+  if (q != 0 || pe > P) return;
+  float g = 0.f;
+#pragma unroll
+  for (int k = 0; k < kRedGroups; ++k) g += red[k][lane];
+  adam_apply(pe, g, P, params, m, v, step, lr_t, grad_out, loss_out, loss_scale, rp);
+}
+
+// The Adam update fused into the tensor-core training step (one launch per step): after a
+// grid-wide barrier every CTA reduces and updates a strided share of the partial slots, with
+// the arithmetic of adam_reduce_kernel (same group sums, same order, same update).
+struct FusedAdam {
+  uint32_t* sync;           // [2] arrival count, generation (zero-initialised); nullptr: not fused
+  float *params, *m, *v;
+  AdamAux rp;
+  AdamSched sc;             // sc.step_dev: step, rate and loss slot from device memory
+  float lr_t, loss_scale;   // without step_dev
+  float* loss_out;
+};
+
+// Grid-wide barrier of a cooperative launch (every CTA resident), bounded by kWaitLimitNs:
+// false on expiry.  Each CTA's earlier global writes are visible to every CTA after it.
+__device__ __forceinline__ bool grid_sync_bounded(uint32_t* sync) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    uint32_t gen;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(gen) : "l"(sync + 1) : "memory");
+    bool ok = true;
+    if (atomicAdd(sync, 1u) == gridDim.x - 1) {
+      atomicExch(sync, 0u);
+      __threadfence();
+      asm volatile("st.release.gpu.global.u32 [%0], %1;" :: "l"(sync + 1), "r"(gen + 1u) : "memory");
+    } else {
+      const uint64_t t0 = global_ns();
+      for (;;) {
+        uint32_t g;
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(g) : "l"(sync + 1) : "memory");
+        if (g != gen) break;
+        if (global_ns() - t0 > kWaitLimitNs) { ok = false; break; }
+      }
+    }
+    __threadfence();
+    s_ok = ok && !__ldg(&g_fail_waits);
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// The fused tail: barrier, then the slots pe = blockIdx.x * blockDim.x + tid, step
+// gridDim.x * blockDim.x.  A CTA that met a failed wait still arrives; nobody updates then.
+__device__ __forceinline__ void fused_adam_tail(const FusedAdam& fa, const float* partial, int64_t P, int step,
+                                                uint32_t* status) {
+  const bool ok = grid_sync_bounded(fa.sync);
+  uint32_t st = 0;
+  if (status) asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(st) : "l"(status) : "memory");
+  if (!ok) {
+    if (threadIdx.x == 0 && status) set_status(status, ST_TIMEOUT);
+    return;
+  }
+  if (st & ST_TIMEOUT) return;   // a CTA's step failed: no update
+  const float lr_t = fa.sc.step_dev ? sched_lr(fa.sc, step) : fa.lr_t;
+  float* loss_out = fa.sc.step_dev ? fa.sc.loss_base + (step - fa.sc.first_step) : fa.loss_out;
+  for (int64_t pe = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; pe <= P; pe += (int64_t)gridDim.x * blockDim.x) {
+    float g = 0.f;
+    for (int q = 0; q < kRedGroups; ++q) g += group_sum<true>(partial, gridDim.x, P, pe, q);
+    adam_apply(pe, g, P, fa.params, fa.m, fa.v, step, lr_t, nullptr, loss_out, fa.loss_scale, fa.rp);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0 && fa.sc.step_dev) fa.sc.step_dev[0] = step + 1;
 }
 
 }  // namespace nvdb

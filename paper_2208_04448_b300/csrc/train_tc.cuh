@@ -13,8 +13,10 @@
 //    W of them real, N = augmented input width, K = the tile's 128 samples),
 //    accumulated in TMEM across all tiles of the CTA;
 //    delta_{l-1} = (delta_l W_l) [H_l > 0]  (A = delta_l in TMEM, B = W_l^T);
-//  * at the end the TMEM accumulators go, once, into the CTA's partial slot,
-//    which adam_reduce_kernel sums in CTA order (deterministic).
+//  * at the end the TMEM accumulators go, once, into the CTA's partial slot; with a
+//    FusedAdam (cooperative launch) the CTAs then meet at a grid-wide barrier and each
+//    sums and updates a share of the slots in CTA order (deterministic), otherwise
+//    adam_reduce_kernel does that in a second launch.
 #pragma once
 #include "common.cuh"
 #include "mlp.cuh"
@@ -78,7 +80,7 @@ struct TrainTcLayout {
 };
 
 template <int NIN, int W>
-__global__ void __launch_bounds__(kTile, 1) train_tc_kernel(NetView net, TrainJob job) {
+__global__ void __launch_bounds__(kTile, 1) train_tc_kernel(NetView net, TrainJob job, FusedAdam fa) {
   static_assert(W == 32 || W == 64, "width");
   take_step(job);
   static_assert(NIN == 32 || NIN == 64, "encoding size");
@@ -335,6 +337,7 @@ __global__ void __launch_bounds__(kTile, 1) train_tc_kernel(NetView net, TrainJo
   __syncthreads();
   tc_fence_after();
   if (warp == 0) tmem_dealloc(tbase, C::TCOLS);
+  if (fa.sync) fused_adam_tail(fa, job.partial, P, job.step, job.status);
 }
 
 }  // namespace nvdb
