@@ -415,8 +415,13 @@ const char* nvdb_last_error(void);
  *  NVDB_INJECT_STATIC_LIMIT: value in (0, 2^20] makes nvdb_mlp_grad_static use only the
  *    first `value` floats of its static array (so its capacity error can be reached with
  *    the supported network shapes); value 0 restores the full array.
+ *  NVDB_INJECT_FUSED_ADAM: value 1 makes the BF16 training step apply Adam in its own
+ *    (cooperative) launch after a grid-wide barrier instead of a second reduction kernel (the
+ *    same result bits, measured slower); 0 the two-launch step; -1 the default (the
+ *    environment variable NVDB_FUSED_ADAM=1 selects the fused step).
  * Process-wide; not for production use. */
-enum { NVDB_INJECT_WAIT_TIMEOUT = 1, NVDB_INJECT_ALLOC_BUDGET = 2, NVDB_INJECT_STATIC_LIMIT = 3 };
+enum { NVDB_INJECT_WAIT_TIMEOUT = 1, NVDB_INJECT_ALLOC_BUDGET = 2, NVDB_INJECT_STATIC_LIMIT = 3,
+       NVDB_INJECT_FUSED_ADAM = 4 };
 nvdb_status nvdb_debug_inject(int what, int64_t value);
 
 /* Self-test of the bounded wait: one kernel waits on an mbarrier phase that nothing

@@ -2068,6 +2068,10 @@ extern "C" nvdb_status nvdb_debug_inject(int what, int64_t value) {
     g_static_limit.store(value > 0 ? value : kStaticGradFloats);
     return NVDB_OK;
   }
+  if (what == NVDB_INJECT_FUSED_ADAM) {
+    g_fused_override.store(value < 0 ? -1 : (value != 0 ? 1 : 0));
+    return NVDB_OK;
+  }
   if (what == NVDB_INJECT_ALLOC_BUDGET) {
     if (value < 0) return fail(NVDB_ERR_INVALID_ARG, "nvdb_debug_inject: negative budget");
     g_alloc_budget.store(value > 0 ? value : -1);

@@ -220,18 +220,21 @@ nvdb_status sort_keys(const uint64_t* k_in, uint64_t* k_out, const uint32_t* i_i
 nvdb_status launch_train_tc(const NetView& nv, const TrainJob& job, int grid, cudaStream_t s,
                             const FusedAdam* fa = nullptr);
 
-// The training step's Adam update fused into its launch (NVDB_FUSED_ADAM=0 keeps the separate
-// reduction kernel); needs cooperative launches on the device.
+// The training step's Adam update fused into its launch: off by default (measured slower: the
+// fused tail has fewer threads to hide the reduction's latency, and cooperative launches keep
+// the three networks' steps from overlapping); NVDB_FUSED_ADAM=1 or nvdb_debug_inject
+// (NVDB_INJECT_FUSED_ADAM) turns it on where the device supports cooperative launches.
+inline std::atomic<int> g_fused_override{-1};
 inline bool fused_adam_enabled() {
-  static const bool on = [] {
+  static const bool env = [] {
     const char* e = std::getenv("NVDB_FUSED_ADAM");
-    int coop = 0, dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess)
-      return false;
-    return coop != 0 && !(e && e[0] == '0');
+    return e && e[0] == '1';
   }();
-  return on;
+  const int o = g_fused_override.load();
+  if (!(o >= 0 ? o != 0 : env)) return false;
+  int coop = 0, dev = 0;
+  return cudaGetDevice(&dev) == cudaSuccess &&
+         cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) == cudaSuccess && coop != 0;
 }
 
 }  // namespace nvdb

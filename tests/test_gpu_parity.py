@@ -262,6 +262,24 @@ def test_graph_replayed_training_equals_launched(sphere128):
             assert np.array_equal(launched.losses(k), replayed.losses(k)) and len(replayed.losses(k)) == 130
 
 
+def test_fused_adam_step_gives_the_same_bits(sphere128):
+    """The BF16 step with Adam fused into its cooperative launch (grid barrier, then each CTA
+    reduces a share of the partial slots in the same group order) against the two-launch step:
+    identical model bytes and losses, over graph-replayed and launched chunks."""
+    ijk, val, ref = sphere128
+    g = _grid(ijk, val)
+    kw = dict(seed=6, ffm_sigma=1.25, steps=120, batch=8192, patch_precs=1, train_prec=nv.BF16)
+    try:
+        nv.debug_inject(nv.INJECT_FUSED_ADAM, 1)
+        fused = nv.compress(g, **kw)
+    finally:
+        nv.debug_inject(nv.INJECT_FUSED_ADAM, -1)
+    split = nv.compress(g, **kw)
+    assert fused.export() == split.export()
+    for k in range(3):
+        assert np.array_equal(fused.losses(k), split.losses(k))
+
+
 def test_training_precision_errors(sphere128):
     ijk, val, ref = sphere128
     g = _grid(ijk, val)
