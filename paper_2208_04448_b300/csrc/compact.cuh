@@ -289,6 +289,42 @@ __device__ int64_t lb_prefix(uint64_t* state, int64_t bid, int64_t agg, uint32_t
   return prefix;
 }
 
+// Warp 0 of block `bid` (all 32 lanes): the same prefix, walking back over windows of 32
+// predecessors at a time (one L2 round trip per window): the nearest inclusive prefix in the
+// window ends the walk, the aggregates after it are summed; a window with a predecessor that
+// has published nothing yet is read again.  Positions before block 0 count as an inclusive 0.
+__device__ int64_t lb_prefix_warp(uint64_t* state, int64_t bid, int64_t agg, uint32_t* status, int lane) {
+  if (bid == 0) {
+    if (lane == 0) lb_store(state, kLbInc | (uint64_t)agg);
+    return 0;
+  }
+  if (lane == 0) lb_store(state + bid, kLbAgg | (uint64_t)agg);
+  int64_t prefix = 0;
+  const uint64_t t0 = global_ns();
+  for (int64_t end = bid;;) {
+    const int64_t p = end - 32 + lane;
+    const uint64_t w = p >= 0 ? lb_load(state + p) : kLbInc;
+    const uint32_t flag = (uint32_t)(w >> 62);
+    const uint32_t inc = __ballot_sync(0xffffffffu, flag == 2);
+    const int last_inc = inc ? 31 - __clz(inc) : -1;
+    if (__ballot_sync(0xffffffffu, flag == 0 && lane > last_inc)) {   // not all published yet
+      if (global_ns() - t0 > kWaitLimitNs) {
+        if (lane == 0) set_status(status, ST_TIMEOUT);
+        break;
+      }
+      continue;
+    }
+    int64_t v = lane >= last_inc ? (int64_t)(w & kLbVal) : 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    prefix += v;
+    if (last_inc >= 0) break;
+    end -= 32;
+  }
+  if (lane == 0) lb_store(state + bid, kLbInc | (uint64_t)(prefix + agg));
+  return prefix;
+}
+
 __device__ __forceinline__ int64_t lb_block_id(uint64_t* state, int64_t nblocks, int64_t* sh) {
   if (threadIdx.x == 0) *sh = (int64_t)atomicAdd(reinterpret_cast<unsigned long long*>(state + nblocks), 1ull);
   __syncthreads();
@@ -390,9 +426,10 @@ __global__ void __launch_bounds__(256) patch_scan_batch_kernel(uint32_t* words, 
   if (wib == 0) {
     int64_t tot;
     const int64_t ex = warp_excl_scan(lane < IPB ? scnt[lane] : 0u, lane, tot);
+    const int64_t pre = lb_prefix_warp(state, bid, tot, status, lane);
     if (lane == 0) {
-      spre = lb_prefix(state, bid, tot, status);
-      if (bid == nblocks - 1 && spre + tot != expect) set_status(status, ST_CORRUPT);
+      spre = pre;
+      if (bid == nblocks - 1 && pre + tot != expect) set_status(status, ST_CORRUPT);
     }
     __syncwarp();
     const int64_t g = bid * IPB + lane;
