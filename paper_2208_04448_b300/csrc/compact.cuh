@@ -405,11 +405,17 @@ __global__ void __launch_bounds__(256) patch_scan_batch_kernel(uint32_t* words, 
       for (int i = lane; i < wpi; i += 32) sw[li][i] = full ? ~0u : w[i];
       __syncwarp();
       const uint32_t* poff = b.it[m].off;
-      if (poff && !full)
-        for (uint32_t p = poff[local] + lane; p < poff[local + 1]; p += 32) {
-          const uint32_t bit = b.it[m].idx[p];
-          atomicXor(&sw[li][bit >> 5], 1u << (bit & 31));
+      if (poff && !full) {   // eight index loads in flight per lane, then their XORs
+        const uint32_t p1 = poff[local + 1];
+        for (uint32_t p0 = poff[local] + lane; p0 < p1; p0 += 32 * 8) {
+          uint32_t bit[8];
+#pragma unroll
+          for (int j = 0; j < 8; ++j) bit[j] = p0 + 32 * j < p1 ? (uint32_t)b.it[m].idx[p0 + 32 * j] : 0xFFFFFFFFu;
+#pragma unroll
+          for (int j = 0; j < 8; ++j)
+            if (bit[j] != 0xFFFFFFFFu) atomicXor(&sw[li][bit[j] >> 5], 1u << (bit[j] & 31));
         }
+      }
       __syncwarp();
       for (int i = lane; i < wpi; i += 32) {
         const uint32_t v = sw[li][i];

@@ -94,6 +94,34 @@ def test_build_errors_and_empty():
     assert g.info()["n_leaf"] == 0
 
 
+@pytest.mark.parametrize("case", ["one_voxel", "corners", "one_full_leaf"])
+def test_tiny_and_extreme_grids_round_trip(case):
+    """Degenerate grids through compress and decompress at every precision: one voxel; two
+    voxels at opposite corners of the coordinate range (two level-2 nodes, extent 2^21); one
+    full leaf.  Topology and order exact; values at the oracle's bars."""
+    if case == "one_voxel":
+        ijk, val = np.array([[5, 9, 300]]), np.array([0.5])
+    elif case == "corners":
+        ijk, val = np.array([[0, 0, 0], [(1 << 21) - 1] * 3]), np.array([-1.0, 2.0])
+    else:
+        a = np.arange(8)
+        ijk = np.stack(np.meshgrid(a + 16, a + 8, a, indexing="ij"), -1).reshape(-1, 3)
+        val = np.linspace(-2.5, 2.5, len(ijk))
+    ijk, val = ijk.astype(np.int32), val.astype(np.float32)
+    ref = vdb.build(ijk, val)
+    m = nv.compress(_grid(ijk, val), seed=2, ffm_sigma=1.25, steps=5, batch=256, patch_precs=0b11111)
+    om = blob.read(m.export())
+    for prec in (0, 1, 2, 3, 4):
+        dijk, dval, cnt = nv.decompress(m, prec)
+        dijk, dval = dijk.cpu().numpy(), dval.cpu().numpy()
+        assert cnt == [ref["n"]] and np.array_equal(dijk, ref["ijk"]), (case, prec)
+        want, scale = oracle_forward_scale(om, 2, dijk)
+        if prec == 0:
+            assert rel_err(dval / 3.0, want, scale).max() <= FP32_TOL
+        else:
+            tc_check(prec, om, 2, dijk, dval / 3.0)
+
+
 # ---------------------------------------------------------------------------- initial parameters (bit-exact)
 
 def test_initial_parameters_bit_identical(sphere128):
