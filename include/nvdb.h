@@ -323,12 +323,13 @@ typedef struct {
 nvdb_status nvdb_render(const nvdb_model* model, const nvdb_camera* cam, nvdb_precision prec, float* d_image,
                         nvdb_stream stream);
 
-/* Raw output (logit or unscaled value) of network `net` (0, 1, 2) at n voxel
- * coordinates d_ijk int32 [n][3]; the level-1 classifier takes leaf origins
- * (its input is ijk >> 3).  For a decomposed model (Section 3.4) this is the
- * gate-weighted average of its experts (Eq. 3), as decoding uses it.  d_out
- * float [n].  FP32 does not synchronise; the tensor-core precisions synchronise
- * once to read the status word, as nvdb_query. */
+/* Raw output (logit or unscaled value) of network `net` (0, 1, 2; 3 the tile value
+ * regressor of a model with tiles) at n voxel coordinates d_ijk int32 [n][3]; the
+ * level-1 networks take leaf origins (their input is ijk >> 3).  For a decomposed
+ * model (Section 3.4) this is the gate-weighted average of its experts (Eq. 3), as
+ * decoding uses it.  d_out float [n], or [n][3] (the three class logits) for the
+ * ternary level-1 classifier.  Sin networks: no FP8.  FP32 does not synchronise; the
+ * tensor-core precisions synchronise once to read the status word, as nvdb_query. */
 nvdb_status nvdb_mlp_eval(const nvdb_model* model, int net, nvdb_precision prec, const int32_t* d_ijk,
                           int64_t n, float* d_out, nvdb_stream stream);
 
@@ -336,7 +337,8 @@ nvdb_status nvdb_mlp_eval(const nvdb_model* model, int net, nvdb_precision prec,
  * float [n]) w.r.t. the parameters of network `net` (Section 3.2), in the
  * arithmetic of one training step of precision `prec`: NVDB_FP32 (CUDA cores)
  * or NVDB_BF16 (tensor cores: BF16 operands, FP32 accumulation, FP32 head and
- * loss; at most 4 hidden layers); other precisions return NVDB_ERR_UNSUPPORTED.
+ * loss; at most 4 hidden layers; ReLU networks); other precisions return
+ * NVDB_ERR_UNSUPPORTED, as does the ternary classifier (three outputs).
  * d_grad float [nvdb_net_param_count] in storage order (W_0, b_0, ...,
  * W_{L-1}, b_{L-1}, w_h, b_h; W row-major [out][in]); *loss (HOST) the mean
  * loss.  loss_kind: NVDB_LOSS_*.  Synchronises the stream. */
@@ -372,7 +374,9 @@ nvdb_status nvdb_mlp_grad_static(const nvdb_model* model, int net, const int32_t
                                  int64_t n, int loss_kind, float* d_grad, float* loss, nvdb_stream stream);
 
 /* Network indices of the calls below (gradient, parameters, losses): network j of expert
- * e is 3e + j, so 0, 1, 2 without a domain decomposition; 0 <= net < 3 n_experts. */
+ * e is 3e + j, so 0, 1, 2 without a domain decomposition; 0 <= net < 3 n_experts; a model
+ * with tiles has net 3, the tile value regressor.  The ternary classifier's head is
+ * W_h [3][w] then b_h [3]. */
 int64_t nvdb_net_param_count(const nvdb_model* model, int net);
 
 /* Copy network `net`'s flat FP32 parameters (nvdb_net_param_count floats, storage order
