@@ -175,6 +175,25 @@ def test_ternary_blob_roundtrip_and_query(trained):
     assert np.abs(out.cpu().numpy() - want).max() <= 1e-4
 
 
+def test_ternary_plan_and_tensor_core_queries(trained):
+    """A ternary model through a graph-captured decode plan (same bits as nvdb_decompress) and
+    point queries at FP16 (regressed corners on the tensor cores, tile corners from the cached
+    tile values) against the oracle at the tensor-core bar."""
+    ijk, val, ref, g, m, om = trained
+    plan = nv.decompress_plan([m], nv.FP16)
+    plan.launch()
+    plan.check()
+    dijk, dval, _ = nv.decompress(m, nv.FP16)
+    assert torch.equal(plan.ijk, dijk) and torch.equal(plan.val, dval)
+    r = np.random.default_rng(9)
+    pts = (ref["ijk"][r.integers(0, ref["n"], 3000)] + r.uniform(-0.5, 1.0, (3000, 3))).astype(np.float32)
+    out, act = nv.query(m, torch.from_numpy(pts).cuda(), nv.FP16, active=True)
+    tile_keys = np.sort(vdb.canonical_key(ref["leaf_origin"][ref["leaf_tile"]]) >> 9)
+    want, bits = codec.query(om, pts, np.sort(vdb.canonical_key(ref["ijk"])), tile_keys)
+    assert np.array_equal(act.cpu().numpy(), bits)
+    assert np.abs(out.cpu().numpy() - want).max() <= tc_bar(nv.FP16)
+
+
 @pytest.fixture(scope="module")
 def sin_model():
     ijk, val, _ = workload("sphere32")
