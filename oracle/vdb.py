@@ -93,7 +93,7 @@ def build(ijk, val, tile_tol: float | None = None) -> dict:
         tiles = []
         for lf in np.nonzero(cnt == 512)[0]:
             v = val[leaf_first[lf]:leaf_first[lf] + 512]
-            mn, mx = np.float32(v.min()), np.float32(v.max())
+            mn, mx = np.float32(v.min()), np.float32(v.max())   # NaN propagates: never a tile
             if np.float32(mx - mn) <= np.float32(tile_tol):
                 leaf_tile[lf] = True
                 tiles.append(np.float32(np.float32(mn + mx) * np.float32(0.5)))

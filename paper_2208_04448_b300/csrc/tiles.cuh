@@ -28,8 +28,10 @@ __global__ void tile_prune_kernel(const unsigned long long* leaf_mask, const int
   if (full) {
     const int64_t f = leaf_first[lf];
     float mn = val[f + lane], mx = mn;
+    bool nan = mn != mn;
     for (int q = 1; q < 16; ++q) {
       const float v = val[f + lane + 32 * q];
+      nan |= v != v;
       mn = fminf(mn, v);
       mx = fmaxf(mx, v);
     }
@@ -38,7 +40,7 @@ __global__ void tile_prune_kernel(const unsigned long long* leaf_mask, const int
       mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
       mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     }
-    tile = mx - mn <= tol;
+    tile = mx - mn <= tol && !__any_sync(0xffffffffu, nan);   // a NaN value: no constant region
     tv = (mn + mx) * 0.5f;
     if (tile)
       for (int q = 0; q < 16; ++q) val[f + lane + 32 * q] = tv;

@@ -46,6 +46,18 @@ def test_tile_pruning_bit_exact(tol):
     assert g0.info()["n_tiles"] == 0 and not g0.tiles()["leaf_tile"].any()
 
 
+def test_tile_pruning_with_a_nan():
+    """A leaf holding a NaN value is not a constant region on either side."""
+    ijk, val = tiled_fog()
+    val = val.copy()
+    val[3] = np.nan                                       # inside the first constant leaf
+    ref = vdb.build(ijk, val, 0.0)
+    g = nv.build(torch.from_numpy(ijk.astype(np.int32)).cuda(), torch.from_numpy(val).cuda(), 1, 0.0,
+                 prune_tiles=True, tile_tolerance=0.0)
+    assert np.array_equal(g.tiles()["leaf_tile"], ref["leaf_tile"]) and not ref["leaf_tile"][0]
+    assert g.info()["n_tiles"] == int(ref["leaf_tile"].sum()) == 17
+
+
 def _opts(**kw):
     return codec.default_opts(seed=SEED, sigma=SIGMA, **SHAPE, **kw)
 
