@@ -76,7 +76,9 @@ enum { NVDB_ACT_RELU = 0, NVDB_ACT_SIN = 1 /* sin(omega a) */ };
 /* Losses (Eq. 1 is MSE; BCE is used for the classifiers, Section 3.3.1). */
 enum { NVDB_LOSS_MSE = 0, NVDB_LOSS_L1 = 1, NVDB_LOSS_BCE = 2,
        NVDB_LOSS_LINEAR = 3 /* nvdb_mlp_grad only: d_target holds dL/dy per sample; the gradient is
-                               sum_s target_s dy_s/dtheta (a vector-Jacobian product) */ };
+                               sum_s target_s dy_s/dtheta (a vector-Jacobian product) */,
+       NVDB_LOSS_CE = 4     /* softmax cross-entropy of the ternary classifier's three logits
+                               (Section 3.3.1); the target is the class 0, 1 or 2 as a float */ };
 
 typedef struct nvdb_grid nvdb_grid;    /* explicit [Hash,5,4,3] tree, device resident */
 typedef struct nvdb_model nvdb_model;  /* [Hash,5,NN(4),NN(3)]: upper tree + 3 networks + patches */
@@ -338,7 +340,10 @@ nvdb_status nvdb_mlp_eval(const nvdb_model* model, int net, nvdb_precision prec,
  * arithmetic of one training step of precision `prec`: NVDB_FP32 (CUDA cores)
  * or NVDB_BF16 (tensor cores: BF16 operands, FP32 accumulation, FP32 head and
  * loss; at most 4 hidden layers; ReLU networks); other precisions return
- * NVDB_ERR_UNSUPPORTED, as does the ternary classifier (three outputs).
+ * NVDB_ERR_UNSUPPORTED.  The ternary classifier (three outputs) takes loss_kind
+ * NVDB_LOSS_CE and class targets (0, 1, 2); another target value fails the call with
+ * NVDB_ERR_INVALID_ARG (its rows are left out of the gradient); the other networks
+ * take any other loss.
  * d_grad float [nvdb_net_param_count] in storage order (W_0, b_0, ...,
  * W_{L-1}, b_{L-1}, w_h, b_h; W row-major [out][in]); *loss (HOST) the mean
  * loss.  loss_kind: NVDB_LOSS_*.  Synchronises the stream. */

@@ -15,7 +15,7 @@ from . import _native as N
 from ._native import (BF16, BF16X3, FP16, FP32, FP8_E4M3, INJECT_ALLOC_BUDGET, INJECT_FUSED_ADAM,  # noqa: F401
                       INJECT_STATIC_LIMIT, INJECT_WAIT_TIMEOUT,
                       ERR_CAPACITY, ERR_CORRUPT, ERR_INVALID_ARG, ERR_OUT_OF_MEMORY, ERR_TIMEOUT, ERR_UNSUPPORTED,
-                      LOSS_BCE, LOSS_L1, LOSS_LINEAR, LOSS_MSE,
+                      LOSS_BCE, LOSS_CE, LOSS_L1, LOSS_LINEAR, LOSS_MSE,
                       NET_L0_CLASSIFIER, NET_L1_CLASSIFIER, NET_REGRESSOR, NET_TILE_REGRESSOR, ACT_RELU, ACT_SIN)
 
 _lib = None

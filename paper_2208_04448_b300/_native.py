@@ -12,7 +12,7 @@ OK, ERR_INVALID_ARG, ERR_DUPLICATE_VOXEL, ERR_OUT_OF_MEMORY, ERR_CAPACITY, ERR_C
 FP32, BF16, FP8_E4M3, FP16, BF16X3 = 0, 1, 2, 3, 4
 NET_L1_CLASSIFIER, NET_L0_CLASSIFIER, NET_REGRESSOR, NET_TILE_REGRESSOR = 0, 1, 2, 3
 ACT_RELU, ACT_SIN = 0, 1
-LOSS_MSE, LOSS_L1, LOSS_BCE, LOSS_LINEAR = 0, 1, 2, 3
+LOSS_MSE, LOSS_L1, LOSS_BCE, LOSS_LINEAR, LOSS_CE = 0, 1, 2, 3, 4
 INJECT_WAIT_TIMEOUT, INJECT_ALLOC_BUDGET, INJECT_STATIC_LIMIT, INJECT_FUSED_ADAM = 1, 2, 3, 4
 
 

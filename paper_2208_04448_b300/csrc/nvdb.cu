@@ -469,8 +469,8 @@ nvdb_status launch_train(const nvdb_model* m, int k, int prec, TrainJob job, int
   job.oz = m->origin[2] + (m->moe() ? m->exp_origin_host[3 * e + 2] : 0);
   if (!job.status) job.status = m->status;
   if (prec == NVDB_BF16) {
-    if (nv.n_out != 1 || nv.act != 0)
-      return fail(NVDB_ERR_UNSUPPORTED, "BF16 training: ReLU networks with one output only");
+    if ((nv.n_out != 1 && nv.n_out != 3) || nv.act != 0)
+      return fail(NVDB_ERR_UNSUPPORTED, "BF16 training: ReLU networks only");
     return launch_train_tc(nv, job, grid, s, fa);
   } else if (prec == NVDB_FP32) {
     if (nv.n_in == 32 && nv.width == 32) return launch_train_t<32, 32>(nv, job, grid, s);
@@ -1028,7 +1028,7 @@ extern "C" nvdb_status nvdb_compress(const nvdb_grid* g, const nvdb_train_opts* 
     if (tern) m->set_ternary(true);
     TRY(check_model_shapes(m));
     if (o->train_prec == NVDB_BF16)
-      for (int k = tern ? 1 : 0; k < (tern ? 4 : 3); ++k) {
+      for (int k = 0; k < (tern ? 4 : 3); ++k) {
         int nin, w, L, nout;
         net_shape(m, k, nin, w, L, nout);
         if (L > kTrainTcMaxLayers)
@@ -1127,8 +1127,8 @@ extern "C" nvdb_status nvdb_compress(const nvdb_grid* g, const nvdb_train_opts* 
     static const char* kTrainRange[4] = {"train level-1 classifier", "train level-0 classifier", "train regressor",
                                          "train tile regressor"};
     const int nk = tern ? 4 : 3;   // networks per expert
-    // arithmetic of each network's training: the ternary classifier trains at FP32
-    auto tprec = [&](int k) { return tern && k == 0 ? (int)NVDB_FP32 : o->train_prec; };
+    // arithmetic of each network's training (every network, the ternary classifier included)
+    auto tprec = [&](int) { return o->train_prec; };
     struct NetRun {
       cudaStream_t ts = nullptr;
       cudaEvent_t ev = nullptr;
@@ -1999,10 +1999,11 @@ extern "C" nvdb_status nvdb_mlp_grad(const nvdb_model* cm, int net, nvdb_precisi
   if (!cm || net < 0 || net >= cm->n_net() || n <= 0 || !d_ijk || !d_target || !d_grad)
     return fail(NVDB_ERR_INVALID_ARG, "nvdb_mlp_grad: bad arguments");
   if (!train_prec_ok(prec)) return fail(NVDB_ERR_UNSUPPORTED, "nvdb_mlp_grad: precision %d", (int)prec);
-  if (loss_kind < 0 || loss_kind > 3) return fail(NVDB_ERR_INVALID_ARG, "unknown loss %d", loss_kind);
+  if (loss_kind < 0 || loss_kind > NVDB_LOSS_CE) return fail(NVDB_ERR_INVALID_ARG, "unknown loss %d", loss_kind);
   if (n >= (1ll << 31)) return fail(NVDB_ERR_UNSUPPORTED, "nvdb_mlp_grad: n >= 2^31");
   nvdb_model* m = const_cast<nvdb_model*>(cm);
-  if (m->net[net].n_out != 1) return fail(NVDB_ERR_UNSUPPORTED, "nvdb_mlp_grad: networks with one output only");
+  if ((m->net[net].n_out == 3) != (loss_kind == NVDB_LOSS_CE))
+    return fail(NVDB_ERR_INVALID_ARG, "nvdb_mlp_grad: the ternary classifier takes NVDB_LOSS_CE, other networks not");
   cudaStream_t s = (cudaStream_t)stream;
   const DevNet& d = m->net[net];
   const int grid = train_grid(n);
@@ -2028,9 +2029,10 @@ extern "C" nvdb_status nvdb_mlp_grad(const nvdb_model* cm, int net, nvdb_precisi
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   dfree(d_loss);
   if (e != cudaSuccess) return fail(NVDB_ERR_CUDA, "nvdb_mlp_grad: %s", cudaGetErrorString(e));
-  if (prec == NVDB_BF16) {
+  if (prec == NVDB_BF16 || loss_kind == NVDB_LOSS_CE) {   // timed-out waits; targets that are not classes
     uint32_t hst = 0;
     TRY(read_status(m->status, s, &hst));
+    if (hst & ST_RANGE) return fail(NVDB_ERR_INVALID_ARG, "nvdb_mlp_grad: a target is not a class (0, 1 or 2)");
     TRY(status_to_error(hst));
   }
   if (loss) *loss = h;

@@ -64,7 +64,8 @@ __device__ __forceinline__ void take_step(TrainJob& job) {
 
 // LOSS_LINEAR: the target is the caller's dL/dy per sample (a vector-Jacobian product,
 // as an autograd backward needs): loss term t y, gradient t, no 1/batch factor.
-enum : int { LOSS_MSE = 0, LOSS_L1 = 1, LOSS_BCE = 2, LOSS_LINEAR = 3 };
+// LOSS_CE: softmax cross-entropy of the ternary classifier's three logits (its only loss).
+enum : int { LOSS_MSE = 0, LOSS_L1 = 1, LOSS_BCE = 2, LOSS_LINEAR = 3, LOSS_CE = 4 };
 
 __device__ __forceinline__ int64_t train_population(const TrainJob& j) {
   if (j.pop) return j.pop_n << j.pop_shift;
@@ -231,13 +232,17 @@ __device__ __forceinline__ void accum_dW(const float* D, int dstride, const floa
   for (int k = 0; k < OPT; ++k) gW[(o0 + k) * K + i] += acc[k];
 }
 
+// Class index of a ternary target: 0, 1 or 2, else -1 (a caller's target list may hold
+// anything; sampled targets are always classes).
+__device__ __forceinline__ int class_of(float t) { return t == 0.f ? 0 : t == 1.f ? 1 : t == 2.f ? 2 : -1; }
+
 // Per-row softmax cross-entropy of three logits (Section 3.3.1, the ternary level-1
-// classifier) and its gradient of the batch mean; t is the class.
+// classifier) and its gradient of the batch mean; t is the class (0, 1 or 2).
 __device__ __forceinline__ void row_loss3(const float* y, int t, float inv_b, float& l, float* g) {
   const float mx = fmaxf(y[0], fmaxf(y[1], y[2]));
   const float e0 = expf(y[0] - mx), e1 = expf(y[1] - mx), e2 = expf(y[2] - mx);
   const float lse = mx + logf(e0 + e1 + e2);
-  l = lse - y[t];
+  l = lse - (t == 0 ? y[0] : t == 1 ? y[1] : y[2]);
   const float inv = 1.f / (e0 + e1 + e2);
   g[0] = (e0 * inv - (t == 0 ? 1.f : 0.f)) * inv_b;
   g[1] = (e1 * inv - (t == 1 ? 1.f : 0.f)) * inv_b;
@@ -299,9 +304,18 @@ __global__ void __launch_bounds__(kTile, 1) train_fwd_bwd_kernel(NetView net, Tr
 #pragma unroll
       for (int i = 0; i < W; ++i) y[c] = fmaf(wh[c * W + i], h[i], y[c]);
     }
-    if constexpr (NOUT == 3) row_loss3(y, (int)tgt, inv_b, lr_, g);
-    else row_loss(job.loss, y[0], tgt, inv_b, lr_, g[0]);
-    if (!valid) {
+    bool use = valid;
+    if constexpr (NOUT == 3) {
+      const int cls = class_of(tgt);
+      if (valid && cls < 0) {   // not a class: the row is left out and the call fails
+        if (job.status) set_status(job.status, ST_RANGE);
+        use = false;
+      }
+      row_loss3(y, cls < 0 ? 0 : cls, inv_b, lr_, g);
+    } else {
+      row_loss(job.loss, y[0], tgt, inv_b, lr_, g[0]);
+    }
+    if (!use) {
       lr_ = 0.f;
 #pragma unroll
       for (int c = 0; c < NOUT; ++c) g[c] = 0.f;

@@ -7,7 +7,9 @@ Tile pruning bit-exact (flags, masks, values); initial networks bit-exact; netwo
 of every network on the same samples; the ternary decode restores the topology exactly with
 every tile voxel carrying its regressed value; queries answer tile corners from the tiles;
 blob round trip; sin models decoded at FP32 and on the 16-bit tensor-core modes, each kernel
-held to its precision's stated arithmetic; FP8 and BF16 training of sin networks refused.
+held to its precision's stated arithmetic; FP8 and BF16 training of sin networks refused; the
+ternary classifier's cross-entropy gradient at FP32 and on the BF16 tensor-core step, and
+BF16 training of a whole ternary model.
 """
 import numpy as np
 import pytest
@@ -15,7 +17,7 @@ import torch
 
 import paper_2208_04448_b300 as nv
 from fixtures import tiled_fog, workload
-from gpu_helpers import tc_bar
+from gpu_helpers import bf16_weight_sensitivity, tc_bar
 from oracle import blob, codec, vdb
 from oracle import nets as N
 
@@ -134,6 +136,91 @@ def test_first_adam_step_of_every_network(act):
         big = np.abs(dw_ref) > 0.999e-3
         assert big.sum() > 0
         assert np.abs(dw_got[big] - dw_ref[big]).max() <= 2e-6, net
+
+
+# BF16 gradient bars of the one-output networks' parity tests: per block, the relative L2
+# error at most BF16_GRAD_K times the relative change of the FP64 gradient under BF16
+# weights, plus u as a floor
+GRAD_TOL, BF16_GRAD_K, BF16_U, BF16_LOSS_TOL = 1e-4, 3.0, 2.0 ** -9, 1e-2
+
+
+@pytest.mark.parametrize("n", [1000, 37965])
+@pytest.mark.parametrize("prec", [nv.FP32, nv.BF16])
+@pytest.mark.parametrize("width,layers,ffm", [(32, 2, 32), (64, 4, 64)])
+def test_ternary_gradient_parity(width, layers, ffm, prec, n):
+    """The ternary classifier's softmax cross-entropy gradient (Section 3.3.1) through
+    nvdb_mlp_grad against the oracle's backward: FP32 at 1e-4 of the largest entry, the
+    tensor-core BF16 step at the BF16 bars.  n = 37965: 297 tiles, ragged."""
+    ijk, val, ref, g = _grid()
+    m = nv.compress(g, seed=SEED, ffm_sigma=SIGMA, steps=0, patch_precs=1, width=[width, 32, 32],
+                    layers=[layers, 2, 2], ffm_size=[ffm, 32])
+    om = blob.read(m.export())
+    r = np.random.default_rng(width + n)
+    pts = ijk[r.integers(0, len(ijk), n)].astype(np.int32)
+    cls = r.integers(0, 3, n)
+    net = om["nets"][0]
+    z = N.encode(codec.level_coords(om, 0, pts), codec.level_q(om, 0))
+    y, cache = N.forward(net, z)
+    lref, gy = N.loss_and_grad(y, cls, N.LOSS_CE)
+    gref = N.flatten(N.backward(net, cache, gy))
+    got, lgot = nv.mlp_grad(m, 0, torch.from_numpy(pts).cuda(), torch.from_numpy(cls.astype(np.float32)).cuda(),
+                            nv.LOSS_CE, prec)
+    got = got.cpu().numpy()
+    assert got.size == gref.size
+    if prec == nv.FP32:
+        assert np.abs(got - gref).max() <= GRAD_TOL * np.abs(gref).max()
+        assert abs(lgot - lref) <= 1e-5 * max(1.0, abs(lref))
+        return
+    assert abs(lgot - lref) <= BF16_LOSS_TOL * max(1.0, abs(lref))
+    gsens = bf16_weight_sensitivity(net, z, lambda yb: N.loss_and_grad(yb, cls, N.LOSS_CE)[1])
+    sizes = [x for W, b in zip(net["W"], net["b"]) for x in (np.size(W), np.size(b))] + [np.size(net["wh"]),
+                                                                                       np.size(net["bh"])]
+    o = 0
+    for sz in sizes:   # blocks W_0, b_0, ..., W_{L-1}, b_{L-1}, w_h [3][W], b_h [3]
+        a, b, c = got[o:o + sz], gref[o:o + sz], gsens[o:o + sz]
+        nb = max(np.linalg.norm(b), 1e-30)
+        sens = np.linalg.norm(c - b) / nb
+        assert np.linalg.norm(a - b) / nb <= BF16_GRAD_K * sens + BF16_U, (o, sz, sens)
+        o += sz
+    assert o == got.size
+
+
+@pytest.mark.parametrize("prec", [nv.FP32, nv.BF16])
+def test_ternary_gradient_refusals(prec):
+    """A target that is not a class fails the call; the ternary classifier takes only the
+    cross-entropy, the other networks not it."""
+    ijk, val, ref, g = _grid()
+    m = nv.compress(g, seed=SEED, ffm_sigma=SIGMA, steps=0, patch_precs=1, **SHAPE)
+    pts = torch.from_numpy(ijk[:300].astype(np.int32)).cuda()
+    tgt = torch.zeros(300, device="cuda")
+    tgt[17] = 0.5
+    with pytest.raises(nv.NvdbError) as e:
+        nv.mlp_grad(m, 0, pts, tgt, nv.LOSS_CE, prec)
+    assert e.value.status == nv.ERR_INVALID_ARG
+    tgt[17] = 2.0
+    nv.mlp_grad(m, 0, pts, tgt, nv.LOSS_CE, prec)          # the status was cleared
+    for net, loss in ((0, nv.LOSS_BCE), (2, nv.LOSS_CE)):
+        with pytest.raises(nv.NvdbError) as e:
+            nv.mlp_grad(m, net, pts, tgt, loss, prec)
+        assert e.value.status == nv.ERR_INVALID_ARG
+
+
+def test_ternary_bf16_training_tracks_fp32():
+    """Every network of a ternary model (the softmax-CE classifier included) trained by the
+    tensor-core BF16 step from the same weights and Philox batches as FP32 training: first
+    losses within the BF16 forward bar, trained losses at the FP32 run's level, and the
+    model decodes to the exact topology with its tiles."""
+    ijk, val, ref, g = _grid(big=True)
+    kw = dict(seed=SEED, ffm_sigma=SIGMA, steps=120, batch=4096, patch_precs=0b11011, **SHAPE)
+    m32 = nv.compress(g, train_prec=nv.FP32, **kw)
+    m16 = nv.compress(g, train_prec=nv.BF16, **kw)
+    for k in range(4):
+        a, b = m32.losses(k), m16.losses(k)
+        assert len(a) == len(b) == 120
+        assert abs(b[0] - a[0]) <= BF16_LOSS_TOL * max(1.0, a[0]), k
+        assert b[-20:].mean() <= 1.25 * a[-20:].mean() + 1e-4, (k, b[-20:].mean(), a[-20:].mean())
+    dijk, dval, cnt = nv.decompress(m16, nv.FP16)
+    assert cnt == [ref["n"]] and np.array_equal(dijk.cpu().numpy(), ref["ijk"])
 
 
 @pytest.fixture(scope="module")
