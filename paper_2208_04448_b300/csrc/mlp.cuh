@@ -12,6 +12,7 @@
 //                     FP32 accumulators in TMEM, bias + ReLU + repack in the
 //                     epilogue; the head stays FP32 on CUDA cores.
 #pragma once
+#include <type_traits>
 #include <cuda_fp16.h>
 
 #include "common.cuh"
@@ -859,18 +860,25 @@ __global__ void __launch_bounds__(kTile, 4) mlp_tc_kernel(const __grid_constant_
       } else if (tid == 0) {
         tc_fence_after();
         const uint32_t woff = l == 0 ? 0u : (uint32_t)(W * C::K0 + (l - 1) * W * C::KH) * 2u;
-        const uint32_t b0 = smem_u32(sw) + woff, bl = smem_u32(sw_lo) + woff;
         const uint32_t sbo = (uint32_t)(K + 16) * 16u;
+        // K step ks reads the tile 256 bytes further on: +16 in the descriptor's address
+        // field (addresses stay below 2^18, so the 14-bit field does not carry)
+        const uint64_t bd0 = smem_desc(smem_u32(sw) + woff, 128, sbo), bl0 = smem_desc(smem_u32(sw_lo) + woff, 128, sbo);
         const bool comp = comp_in<MODE>(l, L);
-        for (int ks = 0; ks < K / 16 + (C::BIAS_MMA ? 1 : 0); ++ks) {
-          const uint64_t bd = smem_desc(b0 + ks * 256, 128, sbo);
-          mma_f16kind_ts(tbase, tbase + C::A_HI + ks * 8, bd, idesc, ks > 0 ? 1u : 0u);
-          if (C::WLO) {
-            if (comp) mma_f16kind_ts(tbase, tbase + C::A_LO + ks * 8, bd, idesc, 1u);
-            if (!wexact)   // A_hi * W_lo vanishes for BF16-exact weights
-              mma_f16kind_ts(tbase, tbase + C::A_HI + ks * 8, smem_desc(bl + ks * 256, 128, sbo), idesc, 1u);
+        auto issue_layer = [&](auto nks) {   // nks K steps, unrolled
+#pragma unroll
+          for (int ks = 0; ks < decltype(nks)::value; ++ks) {
+            const uint64_t bd = bd0 + (uint64_t)(ks * 16);
+            mma_f16kind_ts(tbase, tbase + C::A_HI + ks * 8, bd, idesc, ks > 0 ? 1u : 0u);
+            if (C::WLO) {
+              if (comp) mma_f16kind_ts(tbase, tbase + C::A_LO + ks * 8, bd, idesc, 1u);
+              if (!wexact)   // A_hi * W_lo vanishes for BF16-exact weights
+                mma_f16kind_ts(tbase, tbase + C::A_HI + ks * 8, bl0 + (uint64_t)(ks * 16), idesc, 1u);
+            }
           }
-        }
+        };
+        if (l == 0) issue_layer(std::integral_constant<int, NIN / 16 + (C::BIAS_MMA ? 1 : 0)>{});
+        else issue_layer(std::integral_constant<int, W / 16 + (C::BIAS_MMA ? 1 : 0)>{});
         mma_commit(bar);
       }
       bool ok = true;
@@ -899,10 +907,11 @@ __global__ void __launch_bounds__(kTile, 4) mlp_tc_kernel(const __grid_constant_
       } else if (!C::BIAS_MMA) {   // FP32 bias
         const float2* bl2 = reinterpret_cast<const float2*>(sb + l * W);
 #pragma unroll
-        for (int c = 0; c < W / 2; ++c) {
-          const float2 bv = bl2[c];
-          accu[2 * c] = __float_as_uint(__uint_as_float(accu[2 * c]) + bv.x);
-          accu[2 * c + 1] = __float_as_uint(__uint_as_float(accu[2 * c + 1]) + bv.y);
+        for (int c = 0; c < W / 2; ++c) {   // 1 * D + b: one rounding, as an add
+          const float2 h = ffma2(make_float2(1.f, 1.f), make_float2(__uint_as_float(accu[2 * c]), __uint_as_float(accu[2 * c + 1])),
+                                 bl2[c]);
+          accu[2 * c] = __float_as_uint(h.x);
+          accu[2 * c + 1] = __float_as_uint(h.y);
         }
       }
       if constexpr (SIN) {   // h = sin(omega a), applied before the conversions below

@@ -268,10 +268,11 @@ __global__ void __launch_bounds__(kTc2Threads, 4) mlp_tc2_kernel(const __grid_co
       } else if (!C::BIAS_MMA) {
         const float2* bl2 = reinterpret_cast<const float2*>(sb + l * W + half * WH);
 #pragma unroll
-        for (int c = 0; c < WH / 2; ++c) {
-          const float2 bv = bl2[c];
-          accu[2 * c] = __float_as_uint(__uint_as_float(accu[2 * c]) + bv.x);
-          accu[2 * c + 1] = __float_as_uint(__uint_as_float(accu[2 * c + 1]) + bv.y);
+        for (int c = 0; c < WH / 2; ++c) {   // 1 * D + b: one rounding, as an add
+          const float2 h = ffma2(make_float2(1.f, 1.f), make_float2(__uint_as_float(accu[2 * c]), __uint_as_float(accu[2 * c + 1])),
+                                 bl2[c]);
+          accu[2 * c] = __float_as_uint(h.x);
+          accu[2 * c + 1] = __float_as_uint(h.y);
         }
       }
       if (MODE == TC_FP8 && l < L - 1) {
