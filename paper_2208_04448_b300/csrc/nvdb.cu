@@ -610,7 +610,7 @@ extern "C" nvdb_status nvdb_build(const int32_t* d_ijk, const float* d_val, int6
   if (!out || !opts || n < 0 || (n > 0 && (!d_ijk || !d_val))) return fail(NVDB_ERR_INVALID_ARG, "nvdb_build: bad arguments");
   if (opts->grid_class != 0 && opts->grid_class != 1) return fail(NVDB_ERR_INVALID_ARG, "grid_class must be 0 or 1");
   if (opts->grid_class == 0 && !(opts->half_width > 0.f)) return fail(NVDB_ERR_INVALID_ARG, "half_width must be > 0");
-  if (n >= (int64_t)INT32_MAX) return fail(NVDB_ERR_UNSUPPORTED, "nvdb_build: n >= 2^31");
+  if (n >= (int64_t)INT32_MAX) return fail(NVDB_ERR_UNSUPPORTED, "nvdb_build: n >= 2^31 - 1");
   if (opts->prune_tiles && !(opts->tile_tolerance >= 0.f))
     return fail(NVDB_ERR_INVALID_ARG, "nvdb_build: tile_tolerance must be >= 0");
   *out = nullptr;
