@@ -371,7 +371,7 @@ __global__ void l2_scan_batch_kernel(const __grid_constant__ L2Batch b, int64_t 
 // before it; the last block checks the total.  Items flagged as active tiles (tiles[g].w > 0)
 // become all ones.  Once the block's offsets are known, EMIT writes its items' children in
 // canonical order: kEmitLeaves the leaf origins of level-1 nodes (wpi 128), kEmitVoxels the
-// voxel coordinates of leaves (wpi 16, each lane writing ranks lane, lane + 32, ...).
+// voxel coordinates of leaves (wpi 16, the warp taking one 32-bit word at a time).
 // Items per block of the decode's scans: level 1 has few items with much work each (one per
 // warp); level 0 many small ones, where larger blocks keep the look-back chain short.
 constexpr int kScanItemsL1 = 8, kScanItemsL0 = 32;
@@ -388,7 +388,6 @@ __global__ void __launch_bounds__(256) patch_scan_batch_kernel(uint32_t* words, 
   __shared__ uint32_t sw[IPB][128];
   __shared__ uint32_t scnt[IPB];
   __shared__ int64_t soff[IPB];
-  __shared__ uint32_t wpre[8][17];
   __shared__ int64_t sid, spre;
   const int64_t nblocks = (n_items + IPB - 1) / IPB;
   const int64_t bid = lb_block_id(state, nblocks, &sid);
@@ -469,31 +468,25 @@ __global__ void __launch_bounds__(256) patch_scan_batch_kernel(uint32_t* words, 
             ++pos;
           }
         }
-      } else {   // voxels: lane r writes ranks r, r + 32, ... so consecutive lanes write consecutive outputs
-        const uint32_t bw = lane < 16 ? sw[li][lane] : 0u;
-        int64_t tot;
-        const int64_t ex = warp_excl_scan(__popc(bw), lane, tot);
-        if (lane < 16) wpre[wib][lane] = (uint32_t)ex;
-        if (lane == 0) wpre[wib][16] = (uint32_t)tot;
-        __syncwarp();
+      } else {   // voxels: word k in turn, lane j taking bit j; the set lanes write consecutive ranks
         int32_t* ijk = static_cast<int32_t*>(out);
-        for (int r = lane; r < (int)tot; r += 32) {
-          int k = 0;
-#pragma unroll
-          for (int step = 8; step > 0; step >>= 1)
-            if (wpre[wib][k + step] <= (uint32_t)r) k += step;
-          const int bit = __fns(sw[li][k], 0, r - (int)wpre[wib][k] + 1);
-          const int v = k * 32 + bit;
-          const int64_t pos = soff[li] + r;
-          if (pos < expect) {
-            ijk[3 * pos] = o.x + (v >> 6);
-            ijk[3 * pos + 1] = o.y + ((v >> 3) & 7);
-            ijk[3 * pos + 2] = o.z + (v & 7);
-          } else {
-            over = true;
+        int64_t pos = soff[li];
+        for (int k = 0; k < 16; ++k) {
+          const uint32_t wk = sw[li][k];
+          if (wk == 0u) continue;
+          if ((wk >> lane) & 1u) {
+            const int v = k * 32 + lane;
+            const int64_t p = pos + __popc(wk & ((1u << lane) - 1u));
+            if (p < expect) {
+              ijk[3 * p] = o.x + (v >> 6);
+              ijk[3 * p + 1] = o.y + ((v >> 3) & 7);
+              ijk[3 * p + 2] = o.z + (v & 7);
+            } else {
+              over = true;
+            }
           }
+          pos += __popc(wk);
         }
-        __syncwarp();
       }
     }
     if (over) set_status(status, EMIT == kEmitVoxels ? ST_CAPACITY : ST_CORRUPT);
