@@ -8,11 +8,12 @@
 
 namespace nvdb {
 
-template <int NIN, int W, int MODE, bool MOE = false, bool STAGE = false, bool SIN = false, bool TERN = false>
+template <int NIN, int W, int MODE, bool MOE = false, bool STAGE = false, bool SIN = false, bool TERN = false,
+          int KM = 0>
 nvdb_status launch_tc(const EvalBatch& b, int64_t ntiles, const char* base, cudaStream_t s) {
   if (!MOE && !TERN && batch_moe(b)) return launch_tc<NIN, W, MODE, true, false>(b, ntiles, base, s);
   const TcLayout<NIN, W, MODE> lay(b.it[0].net.layers, batch_wlo(b));
-  auto* kern = mlp_tc_kernel<NIN, W, MODE, MOE, STAGE, SIN, TERN>;
+  auto* kern = mlp_tc_kernel<NIN, W, MODE, MOE, STAGE, SIN, TERN, KM>;
   TRY(set_smem_limit((const void*)kern, lay.total));
   // Residency from the kernel's own limits (the runtime's occupancy query reports 1 for
   // kernels that allocate tensor memory): registers, shared memory, and TMEM columns.
@@ -49,6 +50,17 @@ nvdb_status launch_tc2(const EvalBatch& b, int64_t ntiles, const char* base, cud
   return NVDB_OK;
 }
 
+// The default kernel in its lattice-only or list-only instantiation when every item of the
+// batch has that kind of tiles (a decode stage, a query, a network evaluation).
+template <int NIN, int W, int MODE>
+nvdb_status launch_tc_km(const EvalBatch& b, int64_t ntiles, const char* base, cudaStream_t s) {
+  int lists = 0;
+  for (int i = 0; i < b.n; ++i) lists += b.it[i].job.mode == MODE_LIST;
+  if (!batch_moe(b) && lists == b.n) return launch_tc<NIN, W, MODE, false, false, false, false, 2>(b, ntiles, base, s);
+  if (!batch_moe(b) && lists == 0) return launch_tc<NIN, W, MODE, false, false, false, false, 1>(b, ntiles, base, s);
+  return launch_tc<NIN, W, MODE>(b, ntiles, base, s);
+}
+
 template <int MODE>
 nvdb_status launch_tc_shape(const EvalBatch& b, int64_t ntiles, const char* base, cudaStream_t s) {
   const NetView& nv = b.it[0].net;
@@ -67,7 +79,7 @@ nvdb_status launch_tc_shape(const EvalBatch& b, int64_t ntiles, const char* base
     return nv.act ? launch_tc<A, B, MODE, false, false, MODE != TC_FP8>(b, ntiles, base, s)      \
          : v == 1 ? launch_tc2<A, B, MODE>(b, ntiles, base, s)                                    \
          : v == 2 ? launch_tc<A, B, MODE, false, true>(b, ntiles, base, s)                        \
-                  : launch_tc<A, B, MODE>(b, ntiles, base, s);                                    \
+                  : launch_tc_km<A, B, MODE>(b, ntiles, base, s);                                 \
   }
   NVDB_TC_SHAPE(32, 32)
   NVDB_TC_SHAPE(32, 64)

@@ -625,8 +625,12 @@ __device__ __forceinline__ void tc_stage(const NetView& net, int mode, const Lay
 // MOE: the batch holds decomposed models (Section 3.4); a separate instantiation, so the
 // undecomposed kernel carries none of the expert passes.  STAGE: lattice tiles take their
 // node / leaf origin from shared memory, filled by bulk copies two tiles ahead, instead of
-// a load of their own (the decode-plan autotuner measures both).
-template <int NIN, int W, int MODE, bool MOE = false, bool STAGE = false, bool SIN = false, bool TERN = false>
+// a load of their own (the decode-plan autotuner measures both).  KM: the batch's tiles
+// are all lattice tiles (1) or all list tiles (2), so the kernel carries only that mode's
+// code; 0: either, decided per tile.  List-only kernels load the next tile's coordinates
+// during the current tile's first layer.
+template <int NIN, int W, int MODE, bool MOE = false, bool STAGE = false, bool SIN = false, bool TERN = false,
+          int KM = 0>
 __global__ void __launch_bounds__(kTile, 4) mlp_tc_kernel(const __grid_constant__ EvalBatch b) {
   static_assert(W == 32 || W == 64, "width");
   static_assert(!SIN || (MODE != TC_FP8 && !MOE), "sin networks: 16-bit modes, no decomposition");
@@ -677,6 +681,9 @@ __global__ void __launch_bounds__(kTile, 4) mlp_tc_kernel(const __grid_constant_
   bool wexact = false;
   int pbuf = 0;            // level-0 factor buffer of the current tile
   bool p_ready = false;    // its factors were computed during the previous tile
+  // list-only kernels: the row's raw coordinates, loaded during the previous tile's first layer
+  int pf_x = 0, pf_y = 0, pf_z = 0;
+  bool pf_ok = false, pf_ready = false;
   const bool comp0 = comp_in<MODE>(0, L);
   // Lattice modes: the node / leaf origin each tile reads is staged into shared memory by a
   // bulk copy (the TMA unit) one tile ahead, alternating between two buffers, each with an
@@ -727,11 +734,14 @@ __global__ void __launch_bounds__(kTile, 4) mlp_tc_kernel(const __grid_constant_
     cur = m;
     EvalJob job = b.it[m].job;
     if (b.n == 1) job.n_items = n0;
+    if constexpr (KM == 2) job.mode = MODE_LIST;
+    if constexpr (KM == 1) if (job.mode == MODE_LIST) __builtin_unreachable();
     const int64_t t = t0 - b.it[m].tile_start;
     // the next tile of this CTA, if it is a level-0 tile of the same item: its factors are
     // computed while this tile's first-layer MMAs run
     const int64_t end_m = m + 1 < b.n ? b.it[m + 1].tile_start : ntiles;
     const bool next_same = job.mode == MODE_L0 && t0 + gridDim.x < end_m && !moe_batch;
+    const bool next_list = KM == 2 && t0 + gridDim.x < end_m && !moe_batch;
     const int64_t tn = t0 + gridDim.x - b.it[m].tile_start;
     const int cb = k & 3, nb = (k + 1) & 3;   // origin buffers of this tile and the next
     const uint32_t cpar = (uint32_t)(k >> 2) & 1u, npar = (uint32_t)((k + 1) >> 2) & 1u;
@@ -829,6 +839,11 @@ __global__ void __launch_bounds__(kTile, 4) mlp_tc_kernel(const __grid_constant_
           cx = ((o.x - job.ox) >> 3) + (sl >> 8);
           cy = ((o.y - job.oy) >> 3) + ((sl >> 4) & 15);
           cz = ((o.z - job.oz) >> 3) + (sl & 15);
+        } else if (KM == 2 && pf_ready) {   // as job_coord, from the coordinates loaded ahead
+          cx = (pf_x - job.ox) >> job.shift;
+          cy = (pf_y - job.oy) >> job.shift;
+          cz = (pf_z - job.oz) >> job.shift;
+          valid = pf_ok;
         } else {
           valid = job_coord(job, t, tid, cx, cy, cz);
         }
@@ -887,6 +902,14 @@ __global__ void __launch_bounds__(kTile, 4) mlp_tc_kernel(const __grid_constant_
         l0_factors<M, MODE>(job, sq, lattice ? sorg[nb] : __ldg(job.nodes + (tn >> 2)), tn, sP + (pbuf ^ 1) * 2 * M, tid);
       }
       if (l == 0 && next_same) waited = k + 2;
+      if (KM == 2 && l == 0 && next_list) {   // the next tile's coordinates: used only at its encoding
+        int64_t i = tn * kTile + tid;
+        pf_ok = i < job.n_items;
+        if (!pf_ok) i = job.n_items - 1;
+        pf_x = __ldg(job.ijk + 3 * i);
+        pf_y = __ldg(job.ijk + 3 * i + 1);
+        pf_z = __ldg(job.ijk + 3 * i + 2);
+      }
       ok = mbar_wait_bounded(bar, phase) && ok;
       phase ^= 1u;
       tc_fence_after();
@@ -979,6 +1002,7 @@ __global__ void __launch_bounds__(kTile, 4) mlp_tc_kernel(const __grid_constant_
     else job_output(job, t, tid, valid, y);
     if (next_same) pbuf ^= 1;
     p_ready = next_same;
+    pf_ready = next_list;
   }
   // copies still in flight (after a timeout): wait for them, bounded, before the shared
   // memory they write is released
