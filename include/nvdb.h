@@ -136,9 +136,9 @@ typedef struct {
                            patch_precs must leave out FP8; with a decomposition FP32 only) */
   float omega;          /* sin frequency (the paper's 1.5 .. 3.0) */
   int32_t tile_width;   /* grids with active tiles: tile value regressor width (0 = width[0]) ... */
-  int32_t tile_layers;  /* ... and hidden layers (0 = layers[0]); it trains at train_prec, while the
-                           ternary level-1 classifier always trains at FP32 (it evaluates at every
-                           precision) */
+  int32_t tile_layers;  /* ... and hidden layers (0 = layers[0]); it and the ternary level-1
+                           classifier train at train_prec like the other networks (the classifier
+                           evaluates at every precision) */
 } nvdb_train_opts;
 
 typedef struct {

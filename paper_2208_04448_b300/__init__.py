@@ -350,6 +350,8 @@ def check_grad_args(param_count: int, ijk: torch.Tensor, target: torch.Tensor, o
 
 def mlp_grad(model: Model, net: int, ijk: torch.Tensor, target: torch.Tensor, loss: int, prec: int = FP32,
              stream=None):
+    """nvdb_mlp_grad: (gradient [param_count(net)], mean loss).  The ternary level-1 classifier
+    takes loss=LOSS_CE with class targets 0, 1, 2 (as floats); the other networks any other loss."""
     check_grad_args(model.param_count(net), ijk, target)
     g = torch.empty(model.param_count(net), dtype=torch.float32, device="cuda")
     lv = C.c_float()
