@@ -396,18 +396,25 @@ __global__ void __launch_bounds__(TrainTcCfg<NIN, W>::T, 1) train_tc_kernel(NetV
     for (int l = 0; l < L; ++l) {
       const int K = l == 0 ? NIN : W;
       float* gl = gpart + (l == 0 ? 0 : (int64_t)W * NIN + W + (int64_t)(l - 1) * (W * W + W));
-      for (int c0 = cg * 16; c0 < K + 16; c0 += G * 16) {
-        uint32_t v[16];
+      for (int c0 = cg * 16; c0 < K + 16; c0 += 2 * G * 16) {   // two 16-column loads in flight
+        const int c1 = c0 + G * 16;
+        uint32_t v[2][16];
         if (have) {
-          tmem_ld16_nowait(tlane + C::DW0 + l * C::DW_STRIDE + c0, v);
+          tmem_ld16_nowait(tlane + C::DW0 + l * C::DW_STRIDE + c0, v[0]);
+          if (c1 < K + 16) tmem_ld16_nowait(tlane + C::DW0 + l * C::DW_STRIDE + c1, v[1]);
           tmem_ld_wait();
         } else {
 #pragma unroll
-          for (int j = 0; j < 16; ++j) v[j] = 0u;
+          for (int j = 0; j < 16; ++j) v[0][j] = v[1][j] = 0u;
         }
 #pragma unroll
         for (int j = 0; j < 16; ++j)
-          if (c0 + j <= K) gl[(int64_t)(c0 + j) * W + o] = __uint_as_float(v[j]);
+          if (c0 + j <= K) gl[(int64_t)(c0 + j) * W + o] = __uint_as_float(v[0][j]);
+        if (c1 < K + 16) {
+#pragma unroll
+          for (int j = 0; j < 16; ++j)
+            if (c1 + j <= K) gl[(int64_t)(c1 + j) * W + o] = __uint_as_float(v[1][j]);
+        }
       }
     }
   }
