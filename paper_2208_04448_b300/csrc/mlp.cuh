@@ -897,9 +897,12 @@ __global__ void __launch_bounds__(kTile, 4) mlp_tc_kernel(const __grid_constant_
         mma_commit(bar);
       }
       bool ok = true;
-      if (l == 0 && next_same && tid < 2 * M) {   // the next tile's factors, into the other buffer
+      // the next tile's factors, into the other buffer, by the last 2M threads (warp 0 is
+      // busy issuing the MMAs, so its share would outlast them)
+      if (l == 0 && next_same && tid >= kTile - 2 * M) {
         if (lattice) ok = mbar_wait_bounded(obar + nb, npar);
-        l0_factors<M, MODE>(job, sq, lattice ? sorg[nb] : __ldg(job.nodes + (tn >> 2)), tn, sP + (pbuf ^ 1) * 2 * M, tid);
+        l0_factors<M, MODE>(job, sq, lattice ? sorg[nb] : __ldg(job.nodes + (tn >> 2)), tn, sP + (pbuf ^ 1) * 2 * M,
+                            tid - (kTile - 2 * M));
       }
       if (l == 0 && next_same) waited = k + 2;
       if (KM == 2 && l == 0 && next_list) {   // the next tile's coordinates: used only at its encoding
