@@ -61,7 +61,7 @@ struct TrainTcLayout {
   static constexpr int GH = NOUT == 1 ? W + 1 : W + 3;     // row stride of the head-gradient rows
   static constexpr int NH = NOUT * (W + 1);                // head parameters
   static constexpr int NI = 4 * NH;                        // head-gradient sums: parameter x row quarter
-  static_assert(NI <= 2 * C::T, "head-gradient items per thread");
+  static_assert(NI <= 2 * (C::T - 32), "head-gradient items per thread (warp 0 takes none)");
   size_t wt_off, dt_off, h0_off, gh_off, wh_off, yp_off, smp_off, q_off, red_off, bar_off, slot_off, total;
   // H_l: [128 samples x augmented width] BF16, MN-major
   __host__ __device__ size_t hin_off(int l) const {
@@ -159,7 +159,7 @@ __global__ void __launch_bounds__(TrainTcCfg<NIN, W>::T, 1) train_tc_kernel(NetV
       *reinterpret_cast<uint4*>(h + mn_off(n + 8 * (i & 1), i >> 1, 128u, C::h_lbo(K))) =
           make_uint4((i & 1) ? 0u : 0x3F80u, 0u, 0u, 0u);
   }
-  if (cg == 0) {
+  if (cg == G - 1) {
     int4 v = make_int4(0, 0, 0, 0);
     if ((int64_t)blockIdx.x < ntiles && (int64_t)blockIdx.x * kTile + r < job.batch) {
       float tg;
@@ -182,7 +182,9 @@ __global__ void __launch_bounds__(TrainTcCfg<NIN, W>::T, 1) train_tc_kernel(NetV
   const float inv_b = 1.f / (float)job.batch;
   const uint32_t cst[8] = {0x3F80u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};   // BF16 1.0 then zeros
   float loss_acc = 0.f;
-  float gacc[2] = {0.f, 0.f};   // head-gradient sums of items tid and tid + T
+  // head-gradient sums of items tid - 32 and tid - 32 + (T - 32): warp 0, whose thread 0
+  // issues the MMAs, takes none, nor the sample fetches (the last column group draws them)
+  float gacc[2] = {0.f, 0.f};
   int ntile_done = 0;
   for (int64_t t = blockIdx.x; t < ntiles && !failed; t += gridDim.x, ++ntile_done) {
     const bool valid = t * kTile + r < job.batch;
@@ -330,8 +332,8 @@ __global__ void __launch_bounds__(TrainTcCfg<NIN, W>::T, 1) train_tc_kernel(NetV
         // run: item i = (quarter, output, column)
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
-          const int i = tid + k * T;
-          if (i < NI) {
+          const int i = tid - 32 + k * (T - 32);
+          if (warp > 0 && i < NI) {
             const int rq = i / NH, rem = i % NH, o = rem / (W + 1), c = rem % (W + 1);
             const float* rows = sgh + rq * 32 * GH;
             float acc = 0.f;
@@ -344,7 +346,7 @@ __global__ void __launch_bounds__(TrainTcCfg<NIN, W>::T, 1) train_tc_kernel(NetV
           }
         }
         // the next tile's samples (this tile's were all read before the last barrier)
-        if (cg == 0) {
+        if (cg == G - 1) {
           const int64_t sn = (t + gridDim.x) * kTile + r;
           if (t + gridDim.x < ntiles) {
             int4 v = make_int4(0, 0, 0, 0);
@@ -422,7 +424,7 @@ __global__ void __launch_bounds__(TrainTcCfg<NIN, W>::T, 1) train_tc_kernel(NetV
   __syncthreads();
 #pragma unroll
   for (int k = 0; k < 2; ++k)
-    if (tid + k * T < NI) sgh[tid + k * T] = gacc[k];
+    if (warp > 0 && tid - 32 + k * (T - 32) < NI) sgh[tid - 32 + k * (T - 32)] = gacc[k];
   __syncthreads();
   for (int j = tid; j < NH; j += T) {
     float v = 0.f;
